@@ -1,0 +1,106 @@
+/*
+ * FP64 CPU oracle of the CosmoLattice-2.0 lattice time step -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference leg
+ * may load this code.  It shares nothing with the CUDA path (no headers, no
+ * tables, no helpers): it is a second, independent statement of the method,
+ * written as plain loops in double precision so that it can be read against the
+ * paper equation by equation.
+ *
+ * Program variables (section "Inherited capabilities", Eq. FieldSpaceTimeNaturalVariables):
+ * fields phi~ = phi/f_star, alpha-time eta~, comoving x~.  Momenta are pi = a^(3-alpha) phi'
+ * (the canonical choice the paper defers to its companion review), so that
+ * Eq. singletEOM becomes
+ *      phi' = a^(alpha-3) pi ,      pi' = a^(1+alpha) Lap phi - a^(3+alpha) dV/dphi .
+ * The scale factor obeys Eq. Friedmann1 with kappa = (f_star / m_p)^2,
+ *      a'' = a^(2 alpha + 1) (kappa/6) [ (2 alpha - 1) rho - 3 p ],
+ * and Eq. Friedmann2 (H^2 = a^(2 alpha) kappa rho / 3, H = a'/a) is the monitored constraint.
+ *
+ * Lattice operators (readings; the paper defers them to its companion review):
+ *      Lap f(n)   = sum_i [f(n+i) + f(n-i) - 2 f(n)] / dx^2          (7-point)
+ *      grad+_i f  = [f(n+i) - f(n)] / dx                              (forward)
+ * Site index: n = (z*N + y)*N + x, x fastest, periodic in every direction.
+ *
+ * Parity is pinned (tests/test_oracle_*.py) against closed forms, invariants and
+ * brute force; no function here is "parity unpinned" unless its comment says so.
+ */
+#ifndef CL_ORACLE_H
+#define CL_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Model description.  Potential in program units (two real singlets phi_0, phi_1):
+ *   V = m2[0]/2 phi0^2 + lam[0]/4 phi0^4 + m2[1]/2 phi1^2 + lam[1]/4 phi1^4 + g2/2 phi0^2 phi1^2
+ * which covers lambda phi^4, m^2 phi^2 and the phi^2 chi^2 preheating families. */
+typedef struct {
+    int32_t N;          /* sites per side                                   */
+    int32_t nf;         /* number of scalar fields (1 or 2)                 */
+    int32_t expansion;  /* 1: self-consistent FLRW; 0: a, a' frozen         */
+    int32_t gauge;      /* 0: none; 1: compact U(1) + axion coupling        */
+    double L;           /* box side, program units; dx = L/N                */
+    double alpha;       /* alpha-time exponent (0 cosmic, 1 conformal)      */
+    double kappa;       /* (f_star / m_p)^2                                       */
+    double m2[2];
+    double lam[2];
+    double g2;
+    /* gauge sector (gauge == 1): axion coupling alpha_L and the factor
+     * (omega_star / f_star)^2 that multiplies E.B in the axion equation.             */
+    double alphaL;
+    double ws2;
+} orc_model;
+
+/* Indices into the energies vector returned by orc_energies(). */
+enum {
+    ORC_E_K0 = 0, ORC_E_K1, ORC_E_G0, ORC_E_G1, ORC_E_V,
+    ORC_E_KEM, ORC_E_GEM,           /* U(1) electric / magnetic energies  */
+    ORC_E_RHO, ORC_E_P, ORC_E_HV,   /* rho, p, Hubble-constraint violation */
+    ORC_E_A, ORC_E_B,               /* a and a' the energies refer to      */
+    ORC_NE
+};
+
+/* Integrators (section "Non-symplectic evolvers" and the symplectic family it lists). */
+enum { ORC_VV2 = 0, ORC_YOSHIDA4 = 1, ORC_RK3_3 = 2, ORC_RK4_5 = 3 };
+
+/* ---- potential and lattice operators ---- */
+double orc_V(const orc_model* m, double f0, double f1);
+double orc_dV(const orc_model* m, int f, double f0, double f1);
+double orc_d2V(const orc_model* m, int f, double f0, double f1);
+void   orc_laplacian(int N, double dx, const double* f, double* out);
+double orc_grad2_sum(int N, const double* f);
+void   orc_kick_force(const orc_model* m, int f, const double* phi, double a, double* out);
+
+/* ---- volume averages and the Friedmann equations ---- */
+/* phi, pi: nf arrays of N^3 back to back.  abt = {a, a', t}.  out[ORC_NE]. */
+void   orc_energies(const orc_model* m, const double* phi, const double* pi,
+                    const double* links, const double* efield,
+                    const double* abt, double* out);
+double orc_addot(const orc_model* m, double a, double rho, double p);
+
+/* ---- time integration ----
+ * Scalar models: links = efield = NULL.
+ * U(1)+axion models (gauge == 1): nf = 1, links/efield are 3 arrays of N^3
+ * (theta_i = dx * A_i on the link n -> n+i, E_i on the same link). */
+void orc_step(const orc_model* m, int scheme, double h, int nsteps,
+              double* phi, double* pi, double* links, double* efield, double* abt);
+
+/* ---- U(1) + axion diagnostics ---- */
+void orc_u1_gauss(const orc_model* m, const double* phi, const double* links,
+                  const double* efield, double a, double* out_gauss /* N^3 */);
+
+/* ---- random numbers, initial conditions, spectra ---- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void orc_dft3(int N, int sign, double* re, double* im);
+void orc_vacuum(const orc_model* m, uint64_t seed, uint32_t member, double kcut, double amp2,
+                const double* fbar, const double* dfbar, double a0,
+                double* phi, double* pi, double* abt);
+int  orc_spectrum(int N, double L, const double* f, double dn, int type,
+                  double* k_out, double* delta_out, double* count_out, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

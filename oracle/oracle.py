@@ -1,0 +1,184 @@
+"""ctypes wrapper of the FP64 CPU oracle -- test infrastructure only.
+
+Arrays are numpy float64 in C order with shape (N, N, N) indexed [z, y, x]
+(x fastest), matching the oracle's site index n = (z*N + y)*N + x.  The
+functions only marshal arguments; every step of the arithmetic is in the C
+files of this folder.
+"""
+import ctypes as C
+import dataclasses
+
+import numpy as np
+
+from . import build_oracle
+
+VV2, YOSHIDA4, RK3_3, RK4_5 = 0, 1, 2, 3
+E_NAMES = ["K0", "K1", "G0", "G1", "V", "KEM", "GEM", "rho", "p", "hubble_violation", "a", "b"]
+
+
+class Model(C.Structure):
+    _fields_ = [("N", C.c_int32), ("nf", C.c_int32), ("expansion", C.c_int32), ("gauge", C.c_int32),
+                ("L", C.c_double), ("alpha", C.c_double), ("kappa", C.c_double),
+                ("m2", C.c_double * 2), ("lam", C.c_double * 2), ("g2", C.c_double),
+                ("alphaL", C.c_double), ("ws2", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build_oracle.build()
+        L = C.CDLL(path)
+        dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+        mp = C.POINTER(Model)
+        L.orc_V.restype = C.c_double
+        L.orc_V.argtypes = [mp, C.c_double, C.c_double]
+        L.orc_dV.restype = C.c_double
+        L.orc_dV.argtypes = [mp, C.c_int, C.c_double, C.c_double]
+        L.orc_laplacian.argtypes = [C.c_int, C.c_double, dp, dp]
+        L.orc_grad2_sum.restype = C.c_double
+        L.orc_grad2_sum.argtypes = [C.c_int, dp]
+        L.orc_kick_force.argtypes = [mp, C.c_int, dp, C.c_double, dp]
+        L.orc_energies.argtypes = [mp, dp, dp, C.c_void_p, C.c_void_p, dp, dp]
+        L.orc_addot.restype = C.c_double
+        L.orc_addot.argtypes = [mp, C.c_double, C.c_double, C.c_double]
+        L.orc_step.argtypes = [mp, C.c_int, C.c_double, C.c_int, dp, dp, C.c_void_p, C.c_void_p, dp]
+        L.orc_u1_gauss.argtypes = [mp, dp, dp, dp, C.c_double, dp]
+        L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+        L.orc_dft3.argtypes = [C.c_int, C.c_int, dp, dp]
+        L.orc_vacuum.argtypes = [mp, C.c_uint64, C.c_uint32, C.c_double, C.c_double, dp, dp, C.c_double,
+                                 dp, dp, dp]
+        L.orc_spectrum.restype = C.c_int
+        L.orc_spectrum.argtypes = [C.c_int, C.c_double, dp, C.c_double, C.c_int, dp, dp, dp, C.c_int]
+        _lib = L
+    return _lib
+
+
+def make_model(N, L, nf=1, alpha=1.0, kappa=0.0, expansion=False, m2=(0.0, 0.0), lam=(0.0, 0.0),
+               g2=0.0, gauge=0, alphaL=0.0, ws2=0.0):
+    m = Model()
+    m.N, m.nf, m.expansion, m.gauge = int(N), int(nf), int(bool(expansion)), int(gauge)
+    m.L, m.alpha, m.kappa = float(L), float(alpha), float(kappa)
+    m.m2[0], m.m2[1] = float(m2[0]), float(m2[1])
+    m.lam[0], m.lam[1] = float(lam[0]), float(lam[1])
+    m.g2, m.alphaL, m.ws2 = float(g2), float(alphaL), float(ws2)
+    return m
+
+
+@dataclasses.dataclass
+class State:
+    phi: np.ndarray            # (nf, N, N, N)
+    pi: np.ndarray             # (nf, N, N, N)
+    abt: np.ndarray            # (3,) = a, a', t
+    links: np.ndarray = None   # (3, N, N, N) theta_i = dx A_i
+    efield: np.ndarray = None  # (3, N, N, N)
+
+    def copy(self):
+        return State(self.phi.copy(), self.pi.copy(), self.abt.copy(),
+                     None if self.links is None else self.links.copy(),
+                     None if self.efield is None else self.efield.copy())
+
+
+def _c(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def new_state(model, a=1.0, b=0.0, t=0.0):
+    N, nf = model.N, model.nf
+    st = State(np.zeros((nf, N, N, N)), np.zeros((nf, N, N, N)), np.array([a, b, t], dtype=np.float64))
+    if model.gauge == 1:
+        st.links = np.zeros((3, N, N, N))
+        st.efield = np.zeros((3, N, N, N))
+    return st
+
+
+def step(model, st, scheme, h, nsteps=1):
+    """Advance `st` in place by nsteps steps of size h."""
+    st.phi, st.pi, st.abt = _c(st.phi), _c(st.pi), _c(st.abt)
+    if st.links is not None:
+        st.links, st.efield = _c(st.links), _c(st.efield)
+    lib().orc_step(C.byref(model), int(scheme), float(h), int(nsteps), st.phi, st.pi,
+                   _ptr(st.links), _ptr(st.efield), st.abt)
+    return st
+
+
+def energies(model, st):
+    out = np.zeros(len(E_NAMES))
+    lib().orc_energies(C.byref(model), _c(st.phi), _c(st.pi),
+                       _ptr(None if st.links is None else _c(st.links)),
+                       _ptr(None if st.efield is None else _c(st.efield)), _c(st.abt), out)
+    return dict(zip(E_NAMES, out))
+
+
+def addot(model, a, rho, p):
+    return lib().orc_addot(C.byref(model), float(a), float(rho), float(p))
+
+
+def potential(model, f0, f1=0.0):
+    return lib().orc_V(C.byref(model), float(f0), float(f1))
+
+
+def laplacian(N, dx, f):
+    out = np.zeros((N, N, N))
+    lib().orc_laplacian(int(N), float(dx), _c(f), out)
+    return out
+
+
+def grad2_sum(N, f):
+    return lib().orc_grad2_sum(int(N), _c(f))
+
+
+def kick_force(model, phi, f, a):
+    N = model.N
+    out = np.zeros((N, N, N))
+    lib().orc_kick_force(C.byref(model), int(f), _c(phi), float(a), out)
+    return out
+
+
+def u1_gauss(model, st):
+    N = model.N
+    out = np.zeros((N, N, N))
+    lib().orc_u1_gauss(C.byref(model), _c(st.phi), _c(st.links), _c(st.efield), float(st.abt[0]), out)
+    return out
+
+
+def philox4x32_10(ctr, key):
+    c = (C.c_uint32 * 4)(*[int(x) & 0xffffffff for x in ctr])
+    k = (C.c_uint32 * 2)(*[int(x) & 0xffffffff for x in key])
+    o = (C.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return [int(x) for x in o]
+
+
+def dft3(f_re, f_im=None, sign=-1):
+    N = f_re.shape[0]
+    re = _c(f_re).copy()
+    im = np.zeros_like(re) if f_im is None else _c(f_im).copy()
+    lib().orc_dft3(int(N), int(sign), re, im)
+    return re + 1j * im
+
+
+def vacuum(model, seed, kcut, amp2, fbar, dfbar, a0=1.0, member=0):
+    st = new_state(model, a=a0)
+    fb = np.zeros(2)
+    dfb = np.zeros(2)
+    fb[:len(fbar)] = fbar
+    dfb[:len(dfbar)] = dfbar
+    lib().orc_vacuum(C.byref(model), int(seed), int(member), float(kcut), float(amp2), fb, dfb, float(a0),
+                     st.phi, st.pi, st.abt)
+    return st
+
+
+def spectrum(N, L, f, dn=1.0, type_=1):
+    cap = int(np.floor(np.sqrt(3.0) * (N // 2) / dn + 0.5)) + 2
+    k = np.zeros(cap)
+    d = np.zeros(cap)
+    c = np.zeros(cap)
+    nb = lib().orc_spectrum(int(N), float(L), _c(f), float(dn), int(type_), k, d, c, cap)
+    return k[:nb], d[:nb], c[:nb]
