@@ -1,0 +1,330 @@
+"""Throughput of the lattice time step on GB300: Gsite-updates/s at 256^3.
+
+Workload (one "step"): two-field preheating V = m^2 phi^2/2 + g^2 phi^2 chi^2/2 with
+q = g^2 phi0^2/(4 m^2) = 1e4 (program units: m2 = 1, g2 = 4q), on a 256^3 periodic
+lattice, fields in FP32 with Kahan-compensated drifts, FP64 reductions and a(t),
+Yoshida-4 (three fused passes per step), dt = 0.005, self-consistent expansion,
+started from the library's own Philox vacuum state (seed 1234).  A site-update is
+one lattice site advanced by one full step.  The inputs (805 MB of state) are
+larger than L2 (129 MB), so no flush is needed between steps.
+
+Arms:
+  default          the CUDA path through the C ABI (libcl.so).
+  --impl reference the FP64 CPU oracle as it stands, one oracle Yoshida-4 step of the
+                   same 256^3 workload per timed step, on this host's cores.
+Extra keys: roofline (dominant kernel = the fused scalar pass), cpu_baseline (the
+oracle on a bounded sample), e2e (the same metric through the C ABI with host
+buffers: state upload, step, energies download each step), fp64_plain (the same
+workload in FP64 without compensation), clocks (nvidia-smi during the timed region).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N = 256
+L = 8.0 * math.pi
+DT = 0.005
+Q = 1.0e4
+G2 = 4.0 * Q
+KAPPA = 0.1
+ALPHA = 0.0
+AMP2 = 1.0e-9
+SEED = 1234
+METRIC = "Gsite-updates/s at 256^3"
+PASSES_PER_STEP = 3
+# algorithmic bytes of one fused pass per site: phi, pi, c for two fields, read + write, 4 B each
+BYTES_PER_SITE_PASS = 2 * 3 * 2 * 4
+BYTES_PER_SITE_PASS_FP64 = 2 * 2 * 2 * 8
+
+
+def config(extra=None):
+    c = {"workload": "two-field preheating m2phi2+g2phi2chi2, q=1e4, 256^3, Yoshida-4, FP32+Kahan, "
+                     "FP64 reductions, dt=0.005, self-consistent expansion",
+         "lattice": N, "fields": 2, "integrator": "yoshida4", "passes_per_step": PASSES_PER_STEP,
+         "l2": "inputs (805 MB) larger than L2; no flush"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ oracle legs
+REF_N = 64  # per-step sample of the reference arm: same per-site arithmetic on 64^3 sites
+
+
+def oracle_model(n=N):
+    from oracle import oracle as O
+    return O.make_model(n, L * n / N, nf=2, alpha=ALPHA, kappa=KAPPA, expansion=True, m2=(1.0, 0.0), g2=G2)
+
+
+def oracle_state(n=N):
+    """Seeded homogeneous-plus-noise state of the bench shape (the oracle's own vacuum state
+    at 256^3 would take minutes of direct DFTs, so the CPU legs start from this input)."""
+    import numpy as np
+    from oracle import oracle as O
+    from tests import inputs
+    phi, pi = inputs.scalar_state(n, 2, seed=SEED, fbar=(1.0, 0.0), amp=1e-5, pamp=1e-5)
+    st = O.State(phi, pi, np.array([1.0, 0.0, 0.0]))
+    st.abt[1] = math.sqrt(KAPPA * O.energies(oracle_model(n), st)["rho"] / 3.0)
+    return st
+
+
+def cpu_baseline(steps=2):
+    from oracle import oracle as O
+    m = oracle_model()
+    st = oracle_state()
+    t0 = time.perf_counter()
+    O.step(m, st, O.YOSHIDA4, DT, steps)
+    dt = time.perf_counter() - t0
+    return {"value": N ** 3 * steps / dt / 1e9, "unit": "Gsite-updates/s", "cores": 1, "kind": "oracle",
+            "sample": "%d oracle Yoshida-4 steps of the full 256^3 two-field lattice, FP64, single thread "
+                      "(%.1f s)" % (steps, dt)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    m = oracle_model(REF_N)
+    st = oracle_state(REF_N)
+    for _ in range(args.warmup):
+        O.step(m, st, O.YOSHIDA4, DT, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.step(m, st, O.YOSHIDA4, DT, 1)
+    el = time.perf_counter() - t0
+    v = REF_N ** 3 * args.steps / el / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gsite-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config({"impl": "FP64 CPU oracle, single thread"}),
+            "cpu_baseline": {"value": v, "unit": "Gsite-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": "per timed step one oracle Yoshida-4 step of the same two-field "
+                                       "workload on 64^3 sites (same per-site arithmetic as 256^3)"},
+            "e2e": {"value": v, "unit": "Gsite-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def make_lattice(cl, precision, stream):
+    g = cl.Lattice(N, L, 2, precision, cl.CL_INT_YOSHIDA4, expansion=True, alpha=ALPHA, kappa=KAPPA, dt=DT,
+                   stream=stream)
+    g.cl_set_potential(cl.CL_POT_M2_G2, [1.0, G2])
+    g.cl_init_vacuum(SEED, 1e30, AMP2, (1.0, 0.0), (0.0, 0.0))
+    return g
+
+
+def timed_steps(torch, g, stream, steps):
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    g.cl_sync()
+    start.record(stream)
+    launches = 0
+    for _ in range(steps):
+        g.cl_step(1)
+        launches += g.cl_last_launch_count()
+    stop.record(stream)
+    stop.synchronize()
+    g.cl_sync()
+    return start.elapsed_time(stop) / 1e3, launches
+
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2607_24978_gb300 import build_ext, cl
+    build_ext.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    peaks = load_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_src = "of measured" if peaks else "of fallback"
+
+    g = make_lattice(cl, cl.CL_PREC_FP32_KAHAN, stream.cuda_stream)
+    g.cl_step(args.warmup)
+    g.cl_sync()
+    barrier(world)
+    clk = Clocks(local)
+    with clk:
+        el, launches = timed_steps(torch, g, stream, args.steps)
+    barrier(world)
+    el_max = max_over_ranks(el, world)
+    value = world * N ** 3 * args.steps / el_max / 1e9
+    e = g.cl_energies()
+
+    # roofline of the dominant kernel: the fused scalar pass, PASSES_PER_STEP launches per step
+    pass_s = el / (args.steps * PASSES_PER_STEP)
+    bytes_launch = N ** 3 * BYTES_PER_SITE_PASS
+    achieved = bytes_launch / pass_s / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "scalar_pass_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("bytes_per_launch_256")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": traffic, "kernel": "k_scalar_pass<float,2,kahan,4>",
+                "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_src}
+
+    # end to end through the C ABI with host buffers
+    e2e_steps = max(2, min(args.steps, 5))
+    host = [torch.empty(N ** 3, dtype=torch.float32, pin_memory=True) for _ in range(4)]
+    for f in range(2):
+        g.cl_get_state(cl.CL_FIELD_PHI0 + f, host[f].numpy())
+        g.cl_get_state(cl.CL_FIELD_PI0 + f, host[2 + f].numpy())
+    arrs = [h.numpy() for h in host]
+    g.cl_sync()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for f in range(2):
+            g.cl_set_state(cl.CL_FIELD_PHI0 + f, arrs[f])
+            g.cl_set_state(cl.CL_FIELD_PI0 + f, arrs[2 + f])
+        g.cl_step(1)
+        g.cl_energies()
+    e2e_el = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": world * N ** 3 * e2e_steps / e2e_el / 1e9, "unit": "Gsite-updates/s",
+           "h2d_bytes_per_step": 4 * N ** 3 * 4, "d2h_bytes_per_step": 144,
+           "steps": e2e_steps, "path": "cl_set_state x4 (pinned host) + cl_step(1) + cl_energies"}
+    g.close()
+    del host, arrs
+
+    # the same workload in FP64 without compensation ("FP64 plain")
+    g64 = make_lattice(cl, cl.CL_PREC_FP64, stream.cuda_stream)
+    g64.cl_step(2)
+    n64 = max(2, min(args.steps, 10))
+    el64, _ = timed_steps(torch, g64, stream, n64)
+    g64.close()
+    fp64 = {"value": N ** 3 * n64 / el64 / 1e9, "unit": "Gsite-updates/s", "steps": n64,
+            "fp32_kahan_speedup": (N ** 3 * args.steps / el) / (N ** 3 * n64 / el64),
+            "achieved_GBps": N ** 3 * BYTES_PER_SITE_PASS_FP64 / (el64 / (n64 * PASSES_PER_STEP)) / 1e9}
+
+    line = {"metric": METRIC, "value": value, "unit": "Gsite-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el_max / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config({"parallelism": "replicas" if world > 1 else "single"}),
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+            "fp64_plain": fp64, "energies_end": {"a": e["a"], "rho": e["rho"], "hubble_violation": e["hubble_violation"]}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

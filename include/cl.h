@@ -1,0 +1,215 @@
+/*
+ * cl.h -- C ABI of the GB300 (sm_103a) lattice time-step library libcl.so.
+ *
+ * The library advances CosmoLattice-2.0-style lattice field theories: interacting
+ * real scalar singlets, optionally one axion coupled to compact U(1) links, on a
+ * periodic N^3 lattice in a self-consistently expanding FLRW background.  All
+ * quantities are in the paper's program variables (section "Inherited capabilities
+ * from CL 1.X", Eq. FieldSpaceTimeNaturalVariables): phi~ = phi/f_star,
+ * d eta~ = a^-alpha omega_star dt, x~ = omega_star x, A~ = A/omega_star.
+ *
+ * Conventions shared by every call
+ *   - Site index n = (z*N + y)*N + x (x fastest), periodic boundaries.  dx = L/N.
+ *   - Field momenta are pi = a^(3-alpha) phi', so Eq. singletEOM reads
+ *       phi' = a^(alpha-3) pi,   pi' = a^(1+alpha) Lap phi - a^(3+alpha) dV/dphi,
+ *     with the 7-point Laplacian; gradient energies use forward differences.
+ *   - The scale factor a and its alpha-time derivative a' ("adot") follow
+ *     Eq. Friedmann1; Eq. Friedmann2 is monitored (the "Hubble violation").
+ *   - Element type of every field array is double for CL_PREC_FP64 and float for
+ *     CL_PREC_FP32 and CL_PREC_FP32_KAHAN.  Energies, a, a' and t are always double.
+ *   - The library owns all device memory of a lattice.  Caller buffers are only
+ *     read or written during the call that receives them (host buffers), or in
+ *     stream order on the lattice's stream (device buffers, on_device = 1).
+ *   - Work is queued on the CUDA stream given at creation (NULL = legacy default
+ *     stream).  cl_step only queues work; device-side failures (a non-finite
+ *     energy, a Hubble violation above the limit) are reported by the next
+ *     synchronising call: cl_sync, cl_energies, cl_get_state, cl_spectrum.
+ *   - No call aborts the process.  Every call returns a cl_status; the text of
+ *     the last failure of a handle is available from cl_last_error.
+ *   - A handle must not be used from two host threads at the same time.
+ */
+#ifndef CL_H
+#define CL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cl_lattice cl_lattice; /* opaque, owned by the library */
+
+typedef enum {
+    CL_OK = 0,
+    CL_EINVAL = 1,        /* bad argument: size, enum value, NULL pointer, out-of-range member */
+    CL_ENOMEM = 2,        /* device or host allocation failed                                  */
+    CL_ECUDA = 3,         /* a CUDA runtime or cuFFT call failed                               */
+    CL_ENAN = 4,          /* a volume-averaged energy became non-finite                        */
+    CL_ECONSTRAINT = 5,   /* Hubble-constraint violation above the limit set by cl_set_hubble_limit */
+    CL_ETIMEOUT = 6,      /* reserved: a bounded device wait gave up                           */
+    CL_ESTATE = 7,        /* call not valid in the handle's current state                      */
+    CL_EUNSUPPORTED = 8   /* valid request that this build does not implement                  */
+} cl_status;
+
+/* Precision of field storage and arithmetic.  Reductions, a(t) and a'(t) are FP64 in all modes. */
+enum {
+    CL_PREC_FP64 = 0,       /* double fields                                            */
+    CL_PREC_FP32_KAHAN = 1, /* float fields, compensated (Kahan) drift of every field    */
+    CL_PREC_FP32 = 2        /* float fields, plain drift                                 */
+};
+
+/* Time integrators (section "Non-symplectic evolvers"). */
+enum {
+    CL_INT_VV2 = 0,      /* velocity Verlet, O(dt^2), one fused lattice pass per step           */
+    CL_INT_YOSHIDA4 = 1, /* Yoshida composition of three VV steps, O(dt^4), three passes/step   */
+    CL_INT_RK3_3 = 2,    /* low-storage 2N Runge-Kutta, 3rd order, 3 stages (Williamson 1980)   */
+    CL_INT_RK4_5 = 3     /* low-storage 2N Runge-Kutta, 4th order, 5 stages (Carpenter-Kennedy 1994) */
+};
+
+enum { CL_GAUGE_NONE = 0, CL_GAUGE_U1_AXION = 1 };
+
+/* Potentials in program units (cl_set_potential).  All are special cases of
+ *   V = m2_0/2 phi0^2 + lam_0/4 phi0^4 + m2_1/2 phi1^2 + lam_1/4 phi1^4 + g2/2 phi0^2 phi1^2. */
+enum {
+    CL_POT_LPHI4 = 0,    /* params {lam}:       V = lam/4 phi^4                      (1 field)  */
+    CL_POT_M2 = 1,       /* params {m2}:        V = m2/2 phi^2                       (1 field)  */
+    CL_POT_M2_G2 = 2,    /* params {m2, g2}:    V = m2/2 phi^2 + g2/2 phi^2 chi^2    (2 fields) */
+    CL_POT_LPHI4_G2 = 3, /* params {lam, g2}:   V = lam/4 phi^4 + g2/2 phi^2 chi^2   (2 fields) */
+    CL_POT_POLY = 4      /* params {m2_0, lam_0, m2_1, lam_1, g2}: the general form above       */
+};
+
+/* Field identifiers for cl_set_state / cl_get_state / cl_spectrum. */
+enum {
+    CL_FIELD_PHI0 = 0, CL_FIELD_PHI1 = 1, /* scalar fields                                  */
+    CL_FIELD_PI0 = 2, CL_FIELD_PI1 = 3,   /* their momenta pi = a^(3-alpha) phi'            */
+    CL_FIELD_THETA1 = 4, CL_FIELD_THETA2 = 5, CL_FIELD_THETA3 = 6, /* U(1) link angles dx*A_i on n -> n+i */
+    CL_FIELD_E1 = 7, CL_FIELD_E2 = 8, CL_FIELD_E3 = 9             /* electric field A_i' on the same links */
+};
+
+typedef struct {
+    int32_t N;            /* sites per side, 2 <= N <= 1536 (single lattice)                */
+    int32_t nfields;      /* scalar fields, 1 or 2 (1 when gauge = CL_GAUGE_U1_AXION)       */
+    int32_t precision;    /* CL_PREC_*                                                      */
+    int32_t integrator;   /* CL_INT_*                                                       */
+    int32_t gauge;        /* CL_GAUGE_*                                                     */
+    int32_t expansion;    /* 1: self-consistent expansion (Eq. Friedmann1); 0: a, a' frozen */
+    int32_t members;      /* ensemble size B; 0 or 1 = single lattice                       */
+    int32_t reserved;     /* must be 0                                                      */
+    const int32_t* member_N; /* B per-member sizes (copied) when members > 1, else NULL     */
+    const double* member_L;  /* B per-member box sides (copied), or NULL = L for all        */
+    double L;             /* box side in program units                                      */
+    double alpha;         /* alpha-time exponent (Eq. FLRWmetric): 0 cosmic, 1 conformal    */
+    double kappa;         /* (f_star/m_p)^2, sets the strength of Eq. Friedmann1/2          */
+    double dt;            /* time step in program units                                     */
+    double a0;            /* initial scale factor (a' starts at 0 until set)                */
+    void* stream;         /* cudaStream_t used for all work of this handle; NULL = default  */
+} cl_lattice_params;
+
+/* Vacuum initial conditions (section "Initial conditions", Eq. QuantumFlucts,
+ * Eq. fpr_influct, Eq. fpr_influct2): homogeneous values plus Gaussian modes of
+ * variance (N/dx)^3 P(k) per mode, P = amp2 / (2 a^2 omega_k), omega_k^2 = k^2 + a^2 V''(fbar),
+ * zero at k = 0 and for |k| > kcut.  Random numbers: Philox-4x32-10 with key = seed
+ * and counter = (mode index, field, member, 0). */
+typedef struct {
+    uint64_t seed;
+    double kcut;      /* momentum cut-off in program units (use a huge value for none) */
+    double amp2;      /* (omega_star/f_star)^2, the vacuum amplitude in program units  */
+    double fbar[2];   /* homogeneous field values                                      */
+    double dfbar[2];  /* homogeneous alpha-time derivatives phi'                       */
+} cl_vacuum_params;
+
+/* Volume averages at the most recent integer time (Eq. energy-contrib, Eq. rhoLocal). */
+typedef struct {
+    double t;                 /* alpha-time                                              */
+    double a, adot;           /* scale factor and a' at t                                */
+    double K[2], G[2];        /* kinetic and gradient energy of each scalar field        */
+    double V;                 /* potential energy                                        */
+    double KE, GB;            /* U(1) electric and magnetic energies (0 without gauge)   */
+    double rho, p;            /* energy density and pressure                             */
+    double hubble_violation;  /* |H^2 - a^(2 alpha) kappa rho/3| / H^2, H = a'/a (0 if H = 0) */
+    double gauss_violation;   /* U(1): max_n |Gauss(n)| / mean_n |div E(n)|; 0 without gauge */
+    int64_t step;             /* time steps taken since the state was set                */
+} cl_energy;
+
+/* Create a lattice.  Allocates all device memory (fields, their ping-pong copies,
+ * Kahan compensation arrays, reduction scratch) and zeroes it; a = a0, a' = 0, t = 0.
+ * Errors: CL_EINVAL (bad sizes/enums/NULL), CL_ENOMEM, CL_ECUDA. *out is NULL on error. */
+cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p);
+
+/* Release every resource of the handle (waits for its queued work).  NULL is ignored. */
+void cl_free(cl_lattice* l);
+
+/* Set the potential (kind = CL_POT_*).  params holds nparams values per member; for an
+ * ensemble, either one set (shared) or members sets back to back.  Errors: CL_EINVAL. */
+cl_status cl_set_potential(cl_lattice* l, int32_t kind, const double* params, int32_t nparams);
+
+/* Copy one field of one member in (set) or out (get).  src/dst hold N^3 elements of the
+ * lattice's element type, in host memory (on_device = 0) or device memory (on_device = 1).
+ * cl_set_state leaves the handle at an integer time: the next cl_step first opens the
+ * leapfrog with a half kick.  cl_get_state returns the values at the most recent
+ * integer time (momenta are synchronised on the fly; the evolving state is not altered).
+ * Errors: CL_EINVAL (field/member out of range, NULL), CL_ECUDA, CL_ENAN/CL_ECONSTRAINT. */
+cl_status cl_set_state(cl_lattice* l, int32_t member, int32_t field, const void* src, int32_t on_device);
+cl_status cl_get_state(cl_lattice* l, int32_t member, int32_t field, void* dst, int32_t on_device);
+
+/* Scale factor a, its derivative a' and the time t of one member (member = -1: all).
+ * Passing adot = NaN to cl_set_scalars computes a' from Eq. Friedmann2 with the lattice
+ * energy (expanding lattices only). */
+cl_status cl_set_scalars(cl_lattice* l, int32_t member, double a, double adot, double t);
+cl_status cl_get_scalars(cl_lattice* l, int32_t member, double* a, double* adot, double* t);
+
+/* Gaussian vacuum fluctuations over the homogeneous values for every scalar field of
+ * one member (member = -1: every member, each with its own Philox counter stream);
+ * momenta pi = a^(3-alpha) phi'; a' from Eq. Friedmann2 with the lattice energy.
+ * Uses cuFFT; not part of the timed step.  Errors: CL_EINVAL, CL_ECUDA, CL_ENOMEM. */
+cl_status cl_init_vacuum(cl_lattice* l, int32_t member, const cl_vacuum_params* v);
+
+/* Queue nsteps time steps of the configured integrator on the handle's stream (replayed
+ * from a captured CUDA graph when graphs are enabled).  Returns after queueing.
+ * Errors: CL_EINVAL (nsteps < 0), CL_ECUDA. */
+cl_status cl_step(cl_lattice* l, int32_t nsteps);
+
+/* Wait for the handle's queued work; report device-side failures (CL_ENAN, CL_ECONSTRAINT). */
+cl_status cl_sync(cl_lattice* l);
+
+/* Copy the energies of `count` members (starting at member 0) to host memory `out`.
+ * Synchronising.  Errors: CL_EINVAL, CL_ECUDA, CL_ENAN, CL_ECONSTRAINT. */
+cl_status cl_energies(cl_lattice* l, cl_energy* out, int32_t count);
+
+/* Binned spectrum of one field (section "Arbitrary binning and unbinned spectra",
+ * Eq. discretePST2, Eq. UpsilonII).  Bin l collects modes with floor(|n~|/dn + 1/2) = l;
+ * for l > 0, with n_l = l dn and S_l the sum of |f(n~)|^2 over the bin (DFT without
+ * normalisation):  type 1: Delta = n_l S_l / (N^6 dn);  type 2: Delta = 4 pi n_l^3 (S_l/#_l) / N^6.
+ * k_out[l] = (2 pi / L) n_l, count_out[l] = #_l (number of modes), delta_out[0] = 0.
+ * Writes min(cap, bins) host values and sets *nbins to the number of bins of the lattice.
+ * Uses cuFFT; synchronising.  Errors: CL_EINVAL, CL_ECUDA, CL_ENOMEM. */
+cl_status cl_spectrum(cl_lattice* l, int32_t member, int32_t field, double dn, int32_t type,
+                      double* k_out, double* delta_out, double* count_out, int32_t cap, int32_t* nbins);
+
+/* When limit > 0, a Hubble violation above it sets the device status CL_ECONSTRAINT
+ * (reported by the next synchronising call).  limit <= 0 disables the check (default). */
+cl_status cl_set_hubble_limit(cl_lattice* l, double limit);
+
+/* Options.  CL_OPT_GRAPH: 1 = replay steps from captured CUDA graphs (default), 0 = plain
+ * launches.  CL_OPT_TILE_BY: rows per block of the fused scalar pass (0 = library
+ * choice).  CL_OPT_TILE_DZ: planes per block (0 = library choice: the y tiles are cut into
+ * the same z chunks so that one wave of blocks covers the lattice; -1 = a persistent grid
+ * of one wave, each block a balanced contiguous range of planes).  CL_OPT_STAGES: TMA stage
+ * buffers of the fused pass, 2..6, or -1 for the loader without TMA staging (0 = library
+ * choice; rows that are not a multiple of 16 bytes always use the loader without TMA).
+ * Errors: CL_EINVAL. */
+enum { CL_OPT_GRAPH = 0, CL_OPT_TILE_BY = 1, CL_OPT_TILE_DZ = 2, CL_OPT_STAGES = 3 };
+cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value);
+
+/* Number of kernel launches queued by the most recent cl_step (graph replays count the
+ * kernels inside the graph). */
+int64_t cl_last_launch_count(const cl_lattice* l);
+
+const char* cl_strerror(cl_status s);
+const char* cl_last_error(const cl_lattice* l);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CL_H */

@@ -1,0 +1,230 @@
+"""Python binding of libcl.so (the C ABI declared in include/cl.h).
+
+Argument marshalling only: every step of the lattice evolution runs in the
+library's CUDA kernels.  Arrays may be numpy arrays (host) or torch CUDA
+tensors (device, passed by pointer); both must be C-contiguous with N^3
+elements of the lattice's element type (float64 for CL_PREC_FP64, float32
+otherwise).  The library must be built (``build_ext.build()``); importing this
+module without it raises, there is no fallback.
+"""
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcl.so")
+
+CL_OK, CL_EINVAL, CL_ENOMEM, CL_ECUDA, CL_ENAN, CL_ECONSTRAINT, CL_ETIMEOUT, CL_ESTATE, CL_EUNSUPPORTED = range(9)
+CL_PREC_FP64, CL_PREC_FP32_KAHAN, CL_PREC_FP32 = 0, 1, 2
+CL_INT_VV2, CL_INT_YOSHIDA4, CL_INT_RK3_3, CL_INT_RK4_5 = 0, 1, 2, 3
+CL_GAUGE_NONE, CL_GAUGE_U1_AXION = 0, 1
+CL_POT_LPHI4, CL_POT_M2, CL_POT_M2_G2, CL_POT_LPHI4_G2, CL_POT_POLY = 0, 1, 2, 3, 4
+CL_FIELD_PHI0, CL_FIELD_PHI1, CL_FIELD_PI0, CL_FIELD_PI1 = 0, 1, 2, 3
+CL_FIELD_THETA1, CL_FIELD_THETA2, CL_FIELD_THETA3, CL_FIELD_E1, CL_FIELD_E2, CL_FIELD_E3 = 4, 5, 6, 7, 8, 9
+CL_OPT_GRAPH, CL_OPT_TILE_BY, CL_OPT_TILE_DZ, CL_OPT_STAGES = 0, 1, 2, 3
+
+# Every exported entry point of include/cl.h.
+EXPORTS = ["cl_init_lattice", "cl_free", "cl_set_potential", "cl_set_state", "cl_get_state", "cl_set_scalars",
+           "cl_get_scalars", "cl_init_vacuum", "cl_step", "cl_sync", "cl_energies", "cl_spectrum",
+           "cl_set_hubble_limit", "cl_set_option", "cl_last_launch_count", "cl_strerror", "cl_last_error"]
+
+
+class cl_lattice_params(C.Structure):
+    _fields_ = [("N", C.c_int32), ("nfields", C.c_int32), ("precision", C.c_int32), ("integrator", C.c_int32),
+                ("gauge", C.c_int32), ("expansion", C.c_int32), ("members", C.c_int32), ("reserved", C.c_int32),
+                ("member_N", C.POINTER(C.c_int32)), ("member_L", C.POINTER(C.c_double)),
+                ("L", C.c_double), ("alpha", C.c_double), ("kappa", C.c_double), ("dt", C.c_double),
+                ("a0", C.c_double), ("stream", C.c_void_p)]
+
+
+class cl_vacuum_params(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("kcut", C.c_double), ("amp2", C.c_double),
+                ("fbar", C.c_double * 2), ("dfbar", C.c_double * 2)]
+
+
+class cl_energy(C.Structure):
+    _fields_ = [("t", C.c_double), ("a", C.c_double), ("adot", C.c_double), ("K", C.c_double * 2),
+                ("G", C.c_double * 2), ("V", C.c_double), ("KE", C.c_double), ("GB", C.c_double),
+                ("rho", C.c_double), ("p", C.c_double), ("hubble_violation", C.c_double),
+                ("gauss_violation", C.c_double), ("step", C.c_int64)]
+
+    def as_dict(self):
+        return {"t": self.t, "a": self.a, "adot": self.adot, "K0": self.K[0], "K1": self.K[1], "G0": self.G[0],
+                "G1": self.G[1], "V": self.V, "KE": self.KE, "GB": self.GB, "rho": self.rho, "p": self.p,
+                "hubble_violation": self.hubble_violation, "gauss_violation": self.gauss_violation,
+                "step": self.step}
+
+
+class CLError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (_strerror(status), status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libcl.so; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libcl.so is not built (run paper_2607_24978_gb300.build_ext.build())")
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER
+        L.cl_init_lattice.argtypes = [P(C.c_void_p), P(cl_lattice_params)]
+        L.cl_free.argtypes = [C.c_void_p]
+        L.cl_free.restype = None
+        L.cl_set_potential.argtypes = [C.c_void_p, C.c_int32, P(C.c_double), C.c_int32]
+        L.cl_set_state.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32]
+        L.cl_get_state.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32]
+        L.cl_set_scalars.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_double]
+        L.cl_get_scalars.argtypes = [C.c_void_p, C.c_int32, P(C.c_double), P(C.c_double), P(C.c_double)]
+        L.cl_init_vacuum.argtypes = [C.c_void_p, C.c_int32, P(cl_vacuum_params)]
+        L.cl_step.argtypes = [C.c_void_p, C.c_int32]
+        L.cl_sync.argtypes = [C.c_void_p]
+        L.cl_energies.argtypes = [C.c_void_p, P(cl_energy), C.c_int32]
+        L.cl_spectrum.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_int32, P(C.c_double),
+                                  P(C.c_double), P(C.c_double), C.c_int32, P(C.c_int32)]
+        L.cl_set_hubble_limit.argtypes = [C.c_void_p, C.c_double]
+        L.cl_set_option.argtypes = [C.c_void_p, C.c_int32, C.c_int64]
+        L.cl_last_launch_count.argtypes = [C.c_void_p]
+        L.cl_last_launch_count.restype = C.c_int64
+        L.cl_strerror.argtypes = [C.c_int]
+        L.cl_strerror.restype = C.c_char_p
+        L.cl_last_error.argtypes = [C.c_void_p]
+        L.cl_last_error.restype = C.c_char_p
+        for name in EXPORTS:
+            if name not in ("cl_free", "cl_last_launch_count", "cl_strerror", "cl_last_error"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _strerror(s):
+    try:
+        return lib().cl_strerror(int(s)).decode()
+    except ImportError:
+        return "status"
+
+
+def _check(h, s):
+    if s != CL_OK:
+        msg = lib().cl_last_error(h).decode() if h else ""
+        raise CLError(s, msg)
+
+
+def _buffer(arr, dtype, n):
+    """(pointer, on_device, keepalive) for a numpy array or torch CUDA tensor of n elements."""
+    if hasattr(arr, "data_ptr"):  # torch tensor
+        import torch
+        want = torch.float64 if dtype == np.float64 else torch.float32
+        if arr.dtype != want or not arr.is_contiguous() or arr.numel() != n:
+            raise ValueError("tensor must be contiguous %s with %d elements" % (want, n))
+        return C.c_void_p(arr.data_ptr()), int(arr.is_cuda), arr
+    a = np.ascontiguousarray(arr, dtype=dtype)
+    if a.size != n:
+        raise ValueError("array must have %d elements" % n)
+    return a.ctypes.data_as(C.c_void_p), 0, a
+
+
+class Lattice:
+    """Owns one cl_lattice handle.  Methods mirror the C calls."""
+
+    def __init__(self, N, L, nfields=1, precision=CL_PREC_FP64, integrator=CL_INT_VV2, gauge=CL_GAUGE_NONE,
+                 expansion=True, alpha=1.0, kappa=0.1, dt=0.01, a0=1.0, stream=None):
+        p = cl_lattice_params()
+        p.N, p.nfields, p.precision, p.integrator = int(N), int(nfields), int(precision), int(integrator)
+        p.gauge, p.expansion, p.members, p.reserved = int(gauge), int(bool(expansion)), 0, 0
+        p.L, p.alpha, p.kappa, p.dt, p.a0 = float(L), float(alpha), float(kappa), float(dt), float(a0)
+        p.stream = C.c_void_p(int(stream)) if stream else None
+        h = C.c_void_p()
+        s = lib().cl_init_lattice(C.byref(h), C.byref(p))
+        if s != CL_OK:
+            raise CLError(s, "cl_init_lattice")
+        self.h = h
+        self.N, self.nfields, self.precision = int(N), int(nfields), int(precision)
+        self.dtype = np.float64 if precision == CL_PREC_FP64 else np.float32
+        self.n = self.N ** 3
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cl_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def cl_set_potential(self, kind, params):
+        arr = (C.c_double * len(params))(*[float(x) for x in params])
+        _check(self.h, lib().cl_set_potential(self.h, int(kind), arr, len(params)))
+
+    def cl_set_state(self, field, data, member=0):
+        ptr, dev, keep = _buffer(data, self.dtype, self.n)
+        _check(self.h, lib().cl_set_state(self.h, int(member), int(field), ptr, dev))
+
+    def cl_get_state(self, field, out=None, member=0):
+        """Return the field at the latest integer time (numpy), or fill `out` (tensor or array)."""
+        if out is None:
+            out = np.empty((self.N, self.N, self.N), dtype=self.dtype)
+        ptr, dev, keep = _buffer(out, self.dtype, self.n)
+        _check(self.h, lib().cl_get_state(self.h, int(member), int(field), ptr, dev))
+        return out
+
+    def cl_set_scalars(self, a, adot=math.nan, t=0.0, member=0):
+        _check(self.h, lib().cl_set_scalars(self.h, int(member), float(a), float(adot), float(t)))
+
+    def cl_get_scalars(self, member=0):
+        a, b, t = C.c_double(), C.c_double(), C.c_double()
+        _check(self.h, lib().cl_get_scalars(self.h, int(member), C.byref(a), C.byref(b), C.byref(t)))
+        return a.value, b.value, t.value
+
+    def cl_init_vacuum(self, seed, kcut, amp2, fbar, dfbar=(0.0, 0.0), member=-1):
+        v = cl_vacuum_params()
+        v.seed, v.kcut, v.amp2 = int(seed), float(kcut), float(amp2)
+        for i in range(2):
+            v.fbar[i] = float(fbar[i]) if i < len(fbar) else 0.0
+            v.dfbar[i] = float(dfbar[i]) if i < len(dfbar) else 0.0
+        _check(self.h, lib().cl_init_vacuum(self.h, int(member), C.byref(v)))
+
+    def cl_step(self, nsteps=1):
+        _check(self.h, lib().cl_step(self.h, int(nsteps)))
+
+    def cl_sync(self):
+        _check(self.h, lib().cl_sync(self.h))
+
+    def cl_energies(self):
+        e = cl_energy()
+        _check(self.h, lib().cl_energies(self.h, C.byref(e), 1))
+        return e.as_dict()
+
+    def cl_spectrum(self, field, dn=1.0, type_=1, member=0):
+        nb = C.c_int32()
+        lib().cl_spectrum(self.h, int(member), int(field), float(dn), int(type_), None, None, None, 0, C.byref(nb))
+        n = nb.value
+        k, d, c = np.zeros(n), np.zeros(n), np.zeros(n)
+        dp = C.POINTER(C.c_double)
+        _check(self.h, lib().cl_spectrum(self.h, int(member), int(field), float(dn), int(type_),
+                                         k.ctypes.data_as(dp), d.ctypes.data_as(dp), c.ctypes.data_as(dp), n,
+                                         C.byref(nb)))
+        return k, d, c
+
+    def cl_set_hubble_limit(self, limit):
+        _check(self.h, lib().cl_set_hubble_limit(self.h, float(limit)))
+
+    def cl_set_option(self, option, value):
+        _check(self.h, lib().cl_set_option(self.h, int(option), int(value)))
+
+    def cl_last_launch_count(self):
+        return int(lib().cl_last_launch_count(self.h))

@@ -1,0 +1,781 @@
+// C ABI of libcl.so: handle management, state transfer, the integrator schedules and
+// CUDA-graph replay.  Every arithmetic step of the evolution runs in the kernels of
+// this folder; the host code here only orders launches and moves buffers.
+#include <cufft.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "cl_internal.cuh"
+
+using namespace clk;
+
+namespace {
+
+constexpr int kMaxN = 1536;
+
+// One pass of a kick-drift scheme in staggered form (see scalar_pass.cu):
+// drift by d, energies with pi + e F, kick by k.
+struct PassCoef {
+    double d, e, k;
+    int flags;
+};
+
+}  // namespace
+
+struct cl_lattice {
+    cl_lattice_params p{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int N = 0, nf = 1, es = 8, VW = 1, BY = 1, DZ = 1, nby = 1, nbz = 1, stages = 0, grid = 1;
+    int64_t V = 0;
+    double dx = 1.0;
+    void* phi[2][2] = {};  // [field][buffer]
+    void* pi[2][2] = {};
+    void* cc[2][2] = {};
+    int cur = 0;
+    DevScal* scal = nullptr;
+    double* partials = nullptr;
+    int partials_cap = 0;
+    double m2[2] = {0, 0}, lam[2] = {0, 0}, g2 = 0;
+    bool potential_set = false;
+    bool open = false;
+    bool diag_valid = false;
+    double hubble_limit = 0.0;
+    bool use_graph = true;
+    int opt_BY = 0, opt_DZ = 0, opt_stages = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t last_launches = 0;
+    char err[512] = {0};
+};
+
+namespace {
+
+cl_status fail(cl_lattice* l, cl_status s, const char* fmt, ...)
+{
+    if (l) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(l->err, sizeof(l->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+#define CUDA_TRY(l, call)                                                                                   \
+    do {                                                                                                    \
+        cudaError_t e_ = (call);                                                                            \
+        if (e_ != cudaSuccess) return fail((l), CL_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+bool is_fp64(const cl_lattice* l) { return l->p.precision == CL_PREC_FP64; }
+bool has_kahan(const cl_lattice* l) { return l->p.precision == CL_PREC_FP32_KAHAN; }
+
+void invalidate_graphs(cl_lattice* l)
+{
+    for (auto& g : l->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+cl_status query_blocks_per_sm(cl_lattice* l, int* per_sm);
+
+cl_status choose_tiles(cl_lattice* l)
+{
+    const int N = l->N, prec = l->p.precision;
+    l->VW = scalar_pass_vector_width(prec, N);
+    const int TX = N / l->VW;
+    // TMA staging needs rows of 16-byte multiples.  Default: as many stages as fit one
+    // block per SM in shared memory (loads kept in flight are what the pass needs).
+    const bool tma = l->opt_stages >= 0 && scalar_pass_tma_ok(prec, N);
+    int BY = l->opt_BY > 0 ? l->opt_BY : (TX >= 256 ? 1 : 256 / TX);
+    if (BY > N) BY = N;
+    if (BY < 1) BY = 1;
+    while (BY > 1 && scalar_pass_threads(prec, N, BY) > 512) BY /= 2;
+    int stages = 0;
+    if (tma) {
+        stages = l->opt_stages > 0 ? l->opt_stages : 6;
+        while (BY > 1 && scalar_pass_smem_bytes(prec, l->nf, N, BY, 2) > (size_t)kPassMaxSmem) BY /= 2;
+        while (stages > 2 && scalar_pass_smem_bytes(prec, l->nf, N, BY, stages) > (size_t)kPassMaxSmem) --stages;
+        if (scalar_pass_smem_bytes(prec, l->nf, N, BY, stages) > (size_t)kPassMaxSmem) stages = 0;
+    }
+    while (BY > 1 && scalar_pass_smem_bytes(prec, l->nf, N, BY, stages) > (size_t)kPassMaxSmem) BY /= 2;
+    if (scalar_pass_threads(prec, N, BY) > 512 || scalar_pass_smem_bytes(prec, l->nf, N, BY, stages) > (size_t)kPassMaxSmem)
+        return fail(l, CL_EINVAL, "lattice too large for the fused pass tiling (N=%d)", N);
+    const int nby = (N + BY - 1) / BY;
+    l->BY = BY;
+    l->stages = stages;
+    l->nby = nby;
+    // resident blocks of one wave
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        return fail(l, CL_ECUDA, "cannot query the SM count");
+    l->DZ = N;
+    l->nbz = 1;
+    l->grid = 1;
+    cl_status s = query_blocks_per_sm(l, &per_sm);
+    if (s != CL_OK) return s;
+    if (per_sm < 1) per_sm = 1;
+    const int64_t wave = (int64_t)per_sm * nsm;
+    int DZ;
+    if (l->opt_DZ > 0) {
+        DZ = l->opt_DZ > N ? N : l->opt_DZ;  // fixed chunks
+    } else if (l->opt_DZ < 0) {
+        DZ = -1;  // balanced persistent ranges over one wave
+    } else {
+        // lockstep: every y tile split into the same z chunks, all in one wave, so the blocks
+        // of neighbouring tiles march through the same planes together (halo rows hit L2)
+        int64_t nbz = wave / nby;
+        if (nbz < 1) nbz = 1;
+        if (nbz > N) nbz = N;
+        DZ = (int)((N + nbz - 1) / nbz);
+    }
+    l->DZ = DZ;
+    l->nbz = DZ > 0 ? (N + DZ - 1) / DZ : 1;
+    int nblocks = l->nby * l->nbz;
+    if (DZ < 0) {
+        const int64_t units = (int64_t)nby * N;
+        nblocks = (int)(units < wave ? units : wave);
+        l->grid = nblocks;
+    }
+    if (nblocks > l->partials_cap) {
+        if (l->partials) cudaFree(l->partials);
+        l->partials = nullptr;
+        if (cudaMalloc(&l->partials, sizeof(double) * kMaxQ * (size_t)nblocks) != cudaSuccess)
+            return fail(l, CL_ENOMEM, "cannot allocate %d reduction partials", nblocks);
+        l->partials_cap = nblocks;
+    }
+    invalidate_graphs(l);
+    return CL_OK;
+}
+
+// Launch one fused pass reading buffer `in` and writing buffer `out`
+// (occ != nullptr: only report resident blocks per SM of this configuration).
+cl_status run_pass_impl(cl_lattice* l, const PassCoef& pc, int in, int out, int* occ)
+{
+    const int flags = pc.flags | (l->p.expansion ? P_EXPANSION : 0);
+    cudaError_t e;
+    if (is_fp64(l)) {
+        ScalarPassArgs<double> A{};
+        for (int f = 0; f < l->nf; ++f) {
+            A.phi_in[f] = (const double*)l->phi[f][in];
+            A.pi_in[f] = (const double*)l->pi[f][in];
+            A.phi_out[f] = (double*)l->phi[f][out];
+            A.pi_out[f] = (double*)l->pi[f][out];
+        }
+        A.scal = l->scal;
+        A.partials = l->partials;
+        A.N = l->N; A.BY = l->BY; A.DZ = l->DZ; A.nby = l->nby; A.nbz = l->nbz;
+        A.dx = l->dx; A.alpha = l->p.alpha; A.kappa = l->p.kappa;
+        A.d = pc.d; A.e = pc.e; A.k = pc.k;
+        for (int f = 0; f < 2; ++f) { A.m2[f] = l->m2[f]; A.lam[f] = l->lam[f]; }
+        A.g2 = l->g2;
+        A.hubble_limit = l->hubble_limit;
+        A.flags = flags;
+        A.stages = l->stages;
+        A.grid = l->grid;
+        e = occ ? scalar_pass_blocks_per_sm(l->p.precision, l->nf, &A, l->VW, occ)
+                : launch_scalar_pass(l->p.precision, l->nf, &A, l->VW, l->stream);
+    } else {
+        ScalarPassArgs<float> A{};
+        for (int f = 0; f < l->nf; ++f) {
+            A.phi_in[f] = (const float*)l->phi[f][in];
+            A.pi_in[f] = (const float*)l->pi[f][in];
+            A.c_in[f] = (const float*)l->cc[f][in];
+            A.phi_out[f] = (float*)l->phi[f][out];
+            A.pi_out[f] = (float*)l->pi[f][out];
+            A.c_out[f] = (float*)l->cc[f][out];
+        }
+        A.scal = l->scal;
+        A.partials = l->partials;
+        A.N = l->N; A.BY = l->BY; A.DZ = l->DZ; A.nby = l->nby; A.nbz = l->nbz;
+        A.dx = l->dx; A.alpha = l->p.alpha; A.kappa = l->p.kappa;
+        A.d = pc.d; A.e = pc.e; A.k = pc.k;
+        for (int f = 0; f < 2; ++f) { A.m2[f] = l->m2[f]; A.lam[f] = l->lam[f]; }
+        A.g2 = l->g2;
+        A.hubble_limit = l->hubble_limit;
+        A.flags = flags;
+        A.stages = l->stages;
+        A.grid = l->grid;
+        e = occ ? scalar_pass_blocks_per_sm(l->p.precision, l->nf, &A, l->VW, occ)
+                : launch_scalar_pass(l->p.precision, l->nf, &A, l->VW, l->stream);
+    }
+    if (e != cudaSuccess) return fail(l, CL_ECUDA, "scalar pass launch failed: %s", cudaGetErrorString(e));
+    return CL_OK;
+}
+
+cl_status run_pass(cl_lattice* l, const PassCoef& pc, int in, int out)
+{
+    return run_pass_impl(l, pc, in, out, nullptr);
+}
+
+cl_status query_blocks_per_sm(cl_lattice* l, int* per_sm)
+{
+    return run_pass_impl(l, {0.0, 0.0, 0.0, 0}, 0, 1, per_sm);
+}
+
+// Yoshida (1990) fourth-order weights.
+void yoshida_weights(double& w1, double& w0)
+{
+    const double c = cbrt(2.0);
+    w1 = 1.0 / (2.0 - c);
+    w0 = -c / (2.0 - c);
+}
+
+// Pass schedule of one time step in staggered form, and the opening half-kick.
+std::vector<PassCoef> step_schedule(const cl_lattice* l)
+{
+    const double h = l->p.dt;
+    std::vector<PassCoef> s;
+    if (l->p.integrator == CL_INT_VV2) {
+        s.push_back({h, 0.5 * h, h, P_DRIFT | P_COMMIT | P_COUNT_STEP});
+    } else {
+        double w1, w0;
+        yoshida_weights(w1, w0);
+        s.push_back({w1 * h, 0.5 * w1 * h, 0.5 * (w1 + w0) * h, P_DRIFT | P_COMMIT});
+        s.push_back({w0 * h, 0.5 * w0 * h, 0.5 * (w0 + w1) * h, P_DRIFT | P_COMMIT});
+        s.push_back({w1 * h, 0.5 * w1 * h, w1 * h, P_DRIFT | P_COMMIT | P_COUNT_STEP});
+    }
+    return s;
+}
+
+double open_kick(const cl_lattice* l)
+{
+    if (l->p.integrator == CL_INT_VV2) return 0.5 * l->p.dt;
+    double w1, w0;
+    yoshida_weights(w1, w0);
+    return 0.5 * w1 * l->p.dt;
+}
+
+cl_status open_leapfrog(cl_lattice* l)
+{
+    if (l->open) return CL_OK;
+    const double hk = open_kick(l);
+    cl_status s = run_pass(l, {0.0, 0.0, hk, P_COMMIT}, l->cur, l->cur ^ 1);
+    if (s != CL_OK) return s;
+    l->cur ^= 1;
+    l->open = true;
+    l->diag_valid = true;
+    return CL_OK;
+}
+
+// Synchronise the momenta to the integer time.  commit = true makes it the state.
+cl_status close_leapfrog(cl_lattice* l, bool commit)
+{
+    if (!l->open) return CL_OK;
+    const double hk = open_kick(l);
+    cl_status s = run_pass(l, {0.0, -hk, -hk, commit ? P_COMMIT : 0}, l->cur, l->cur ^ 1);
+    if (s != CL_OK) return s;
+    if (commit) {
+        l->cur ^= 1;
+        l->open = false;
+    }
+    l->diag_valid = true;
+    return CL_OK;
+}
+
+cl_status energy_pass(cl_lattice* l, int extra_flags)
+{
+    cl_status s = run_pass(l, {0.0, 0.0, 0.0, extra_flags}, l->cur, l->cur ^ 1);
+    if (s != CL_OK) return s;
+    l->diag_valid = true;
+    return CL_OK;
+}
+
+cl_status read_status(cl_lattice* l, DevScal* host)
+{
+    CUDA_TRY(l, cudaMemcpyAsync(host, l->scal, sizeof(DevScal), cudaMemcpyDeviceToHost, l->stream));
+    CUDA_TRY(l, cudaStreamSynchronize(l->stream));
+    if (host->status) {
+        const int st = host->status;
+        CUDA_TRY(l, cudaMemsetAsync(&l->scal->status, 0, sizeof(int), l->stream));
+        CUDA_TRY(l, cudaStreamSynchronize(l->stream));
+        if (st & ST_NAN) return fail(l, CL_ENAN, "a volume-averaged energy became non-finite");
+        if (st & ST_CONSTRAINT) return fail(l, CL_ECONSTRAINT, "Hubble-constraint violation above %g", l->hubble_limit);
+    }
+    return CL_OK;
+}
+
+int field_kind(int field, int nf, int* f)
+{
+    if (field == CL_FIELD_PHI0 || field == CL_FIELD_PHI1) {
+        *f = field - CL_FIELD_PHI0;
+        return *f < nf ? 0 : -1;
+    }
+    if (field == CL_FIELD_PI0 || field == CL_FIELD_PI1) {
+        *f = field - CL_FIELD_PI0;
+        return *f < nf ? 1 : -1;
+    }
+    return -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cl_strerror(cl_status s)
+{
+    switch (s) {
+    case CL_OK: return "ok";
+    case CL_EINVAL: return "invalid argument";
+    case CL_ENOMEM: return "out of memory";
+    case CL_ECUDA: return "CUDA error";
+    case CL_ENAN: return "non-finite energy";
+    case CL_ECONSTRAINT: return "constraint violation above limit";
+    case CL_ETIMEOUT: return "device wait timed out";
+    case CL_ESTATE: return "call not valid in this state";
+    case CL_EUNSUPPORTED: return "not supported by this build";
+    }
+    return "unknown status";
+}
+
+const char* cl_last_error(const cl_lattice* l) { return l ? l->err : "null handle"; }
+
+int64_t cl_last_launch_count(const cl_lattice* l) { return l ? l->last_launches : 0; }
+
+void cl_free(cl_lattice* l)
+{
+    if (!l) return;
+    if (l->stream) cudaStreamSynchronize(l->stream);
+    invalidate_graphs(l);
+    for (int f = 0; f < 2; ++f)
+        for (int b = 0; b < 2; ++b) {
+            if (l->phi[f][b]) cudaFree(l->phi[f][b]);
+            if (l->pi[f][b]) cudaFree(l->pi[f][b]);
+            if (l->cc[f][b]) cudaFree(l->cc[f][b]);
+        }
+    if (l->scal) cudaFree(l->scal);
+    if (l->partials) cudaFree(l->partials);
+    if (l->own_stream && l->stream) cudaStreamDestroy(l->stream);
+    delete l;
+}
+
+cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
+{
+    if (!out) return CL_EINVAL;
+    *out = nullptr;
+    if (!p) return CL_EINVAL;
+    if (p->members > 1) return CL_EUNSUPPORTED;
+    if (p->N < 2 || p->N > kMaxN || p->nfields < 1 || p->nfields > 2 || p->precision < 0 || p->precision > 2 ||
+        p->integrator < 0 || p->integrator > 3 || p->gauge < 0 || p->gauge > 1 || !(p->L > 0) || !(p->dt > 0) ||
+        !(p->a0 > 0) || p->reserved != 0)
+        return CL_EINVAL;
+    if (p->gauge != CL_GAUGE_NONE || p->integrator == CL_INT_RK3_3 || p->integrator == CL_INT_RK4_5)
+        return CL_EUNSUPPORTED;
+    cl_lattice* l = new (std::nothrow) cl_lattice();
+    if (!l) return CL_ENOMEM;
+    l->p = *p;
+    l->p.member_N = nullptr;
+    l->p.member_L = nullptr;
+    l->N = p->N;
+    l->nf = p->nfields;
+    l->es = p->precision == CL_PREC_FP64 ? 8 : 4;
+    l->V = (int64_t)p->N * p->N * p->N;
+    l->dx = p->L / p->N;
+    if (p->stream) {
+        l->stream = (cudaStream_t)p->stream;
+    } else {
+        // a blocking stream: ordered with the legacy default stream, and capturable
+        if (cudaStreamCreate(&l->stream) != cudaSuccess) {
+            delete l;
+            return CL_ECUDA;
+        }
+        l->own_stream = true;
+    }
+    const size_t bytes = (size_t)l->V * l->es;
+    for (int f = 0; f < l->nf; ++f)
+        for (int b = 0; b < 2; ++b) {
+            if (cudaMalloc(&l->phi[f][b], bytes) != cudaSuccess || cudaMalloc(&l->pi[f][b], bytes) != cudaSuccess ||
+                (has_kahan(l) && cudaMalloc(&l->cc[f][b], bytes) != cudaSuccess)) {
+                cl_free(l);
+                return CL_ENOMEM;
+            }
+            cudaMemsetAsync(l->phi[f][b], 0, bytes, l->stream);
+            cudaMemsetAsync(l->pi[f][b], 0, bytes, l->stream);
+            if (has_kahan(l)) cudaMemsetAsync(l->cc[f][b], 0, bytes, l->stream);
+        }
+    if (cudaMalloc(&l->scal, sizeof(DevScal)) != cudaSuccess) {
+        cl_free(l);
+        return CL_ENOMEM;
+    }
+    DevScal h{};
+    h.a = p->a0;
+    cudaMemcpyAsync(l->scal, &h, sizeof(DevScal), cudaMemcpyHostToDevice, l->stream);
+    if (choose_tiles(l) != CL_OK) {
+        cl_free(l);
+        return CL_ENOMEM;
+    }
+    if (cudaStreamSynchronize(l->stream) != cudaSuccess) {
+        cl_free(l);
+        return CL_ECUDA;
+    }
+    *out = l;
+    return CL_OK;
+}
+
+cl_status cl_set_potential(cl_lattice* l, int32_t kind, const double* params, int32_t nparams)
+{
+    if (!l) return CL_EINVAL;
+    if (!params) return fail(l, CL_EINVAL, "params is NULL");
+    double m2[2] = {0, 0}, lam[2] = {0, 0}, g2 = 0;
+    switch (kind) {
+    case CL_POT_LPHI4:
+        if (nparams != 1) return fail(l, CL_EINVAL, "LPHI4 takes {lam}");
+        lam[0] = params[0];
+        break;
+    case CL_POT_M2:
+        if (nparams != 1) return fail(l, CL_EINVAL, "M2 takes {m2}");
+        m2[0] = params[0];
+        break;
+    case CL_POT_M2_G2:
+        if (nparams != 2 || l->nf != 2) return fail(l, CL_EINVAL, "M2_G2 takes {m2, g2} and two fields");
+        m2[0] = params[0];
+        g2 = params[1];
+        break;
+    case CL_POT_LPHI4_G2:
+        if (nparams != 2 || l->nf != 2) return fail(l, CL_EINVAL, "LPHI4_G2 takes {lam, g2} and two fields");
+        lam[0] = params[0];
+        g2 = params[1];
+        break;
+    case CL_POT_POLY:
+        if (nparams != 5) return fail(l, CL_EINVAL, "POLY takes {m2_0, lam_0, m2_1, lam_1, g2}");
+        m2[0] = params[0]; lam[0] = params[1]; m2[1] = params[2]; lam[1] = params[3]; g2 = params[4];
+        break;
+    default: return fail(l, CL_EINVAL, "unknown potential kind %d", kind);
+    }
+    if (l->nf == 1 && (m2[1] != 0 || lam[1] != 0 || g2 != 0))
+        return fail(l, CL_EINVAL, "second-field couplings on a one-field lattice");
+    for (int f = 0; f < 2; ++f) { l->m2[f] = m2[f]; l->lam[f] = lam[f]; }
+    l->g2 = g2;
+    l->potential_set = true;
+    l->diag_valid = false;
+    invalidate_graphs(l);
+    return CL_OK;
+}
+
+cl_status cl_set_state(cl_lattice* l, int32_t member, int32_t field, const void* src, int32_t on_device)
+{
+    if (!l) return CL_EINVAL;
+    if (member != 0 && member != -1) return fail(l, CL_EINVAL, "member %d out of range", member);
+    if (!src) return fail(l, CL_EINVAL, "src is NULL");
+    int f = 0;
+    const int kind = field_kind(field, l->nf, &f);
+    if (kind < 0) return fail(l, CL_EINVAL, "field %d not present", field);
+    cl_status s = close_leapfrog(l, true);
+    if (s != CL_OK) return s;
+    const size_t bytes = (size_t)l->V * l->es;
+    void* dst = kind == 0 ? l->phi[f][l->cur] : l->pi[f][l->cur];
+    CUDA_TRY(l, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                l->stream));
+    if (kind == 0 && has_kahan(l)) CUDA_TRY(l, cudaMemsetAsync(l->cc[f][l->cur], 0, bytes, l->stream));
+    if (!on_device) CUDA_TRY(l, cudaStreamSynchronize(l->stream));
+    l->diag_valid = false;
+    return CL_OK;
+}
+
+cl_status cl_get_state(cl_lattice* l, int32_t member, int32_t field, void* dst, int32_t on_device)
+{
+    if (!l) return CL_EINVAL;
+    if (member != 0) return fail(l, CL_EINVAL, "member %d out of range", member);
+    if (!dst) return fail(l, CL_EINVAL, "dst is NULL");
+    int f = 0;
+    const int kind = field_kind(field, l->nf, &f);
+    if (kind < 0) return fail(l, CL_EINVAL, "field %d not present", field);
+    int buf = l->cur;
+    if (l->open && kind == 1) {
+        cl_status s = close_leapfrog(l, false);  // integer-time momenta into the spare buffer
+        if (s != CL_OK) return s;
+        buf = l->cur ^ 1;
+    }
+    const size_t bytes = (size_t)l->V * l->es;
+    const void* srcp = kind == 0 ? l->phi[f][buf] : l->pi[f][buf];
+    CUDA_TRY(l, cudaMemcpyAsync(dst, srcp, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                l->stream));
+    DevScal h;
+    return read_status(l, &h);
+}
+
+cl_status cl_set_scalars(cl_lattice* l, int32_t member, double a, double adot, double t)
+{
+    if (!l) return CL_EINVAL;
+    if (member != 0 && member != -1) return fail(l, CL_EINVAL, "member %d out of range", member);
+    if (!(a > 0)) return fail(l, CL_EINVAL, "a must be positive");
+    cl_status s = close_leapfrog(l, true);
+    if (s != CL_OK) return s;
+    DevScal h;
+    s = read_status(l, &h);
+    if (s != CL_OK) return s;
+    h.a = a;
+    h.b = isnan(adot) ? 0.0 : adot;
+    h.t = t;
+    CUDA_TRY(l, cudaMemcpyAsync(l->scal, &h, sizeof(DevScal), cudaMemcpyHostToDevice, l->stream));
+    CUDA_TRY(l, cudaStreamSynchronize(l->stream));
+    l->diag_valid = false;
+    if (isnan(adot) && l->p.expansion) return energy_pass(l, P_HUBBLE_INIT | P_COMMIT);
+    return CL_OK;
+}
+
+cl_status cl_get_scalars(cl_lattice* l, int32_t member, double* a, double* adot, double* t)
+{
+    if (!l) return CL_EINVAL;
+    if (member != 0) return fail(l, CL_EINVAL, "member %d out of range", member);
+    if (l->open) {
+        cl_status s = close_leapfrog(l, false);
+        if (s != CL_OK) return s;
+    } else if (!l->diag_valid) {
+        cl_status s = energy_pass(l, 0);
+        if (s != CL_OK) return s;
+    }
+    DevScal h;
+    cl_status s = read_status(l, &h);
+    if (s != CL_OK) return s;
+    if (a) *a = h.diag[D_A];
+    if (adot) *adot = h.diag[D_ADOT];
+    if (t) *t = h.diag[D_T];
+    return CL_OK;
+}
+
+cl_status cl_set_hubble_limit(cl_lattice* l, double limit)
+{
+    if (!l) return CL_EINVAL;
+    l->hubble_limit = limit;
+    invalidate_graphs(l);
+    return CL_OK;
+}
+
+cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value)
+{
+    if (!l) return CL_EINVAL;
+    switch (option) {
+    case CL_OPT_GRAPH: l->use_graph = value != 0; return CL_OK;
+    case CL_OPT_TILE_BY:
+        if (value < 0 || value > l->N) return fail(l, CL_EINVAL, "tile BY out of range");
+        l->opt_BY = (int)value;
+        return choose_tiles(l);
+    case CL_OPT_TILE_DZ:
+        if (value < -1 || value > l->N) return fail(l, CL_EINVAL, "tile DZ out of range");
+        l->opt_DZ = (int)value;
+        return choose_tiles(l);
+    case CL_OPT_STAGES:
+        if (value < -1 || value == 1 || value > 6) return fail(l, CL_EINVAL, "stages must be -1, 0 or 2..6");
+        l->opt_stages = (int)value;
+        return choose_tiles(l);
+    }
+    return fail(l, CL_EINVAL, "unknown option %d", option);
+}
+
+cl_status cl_step(cl_lattice* l, int32_t nsteps)
+{
+    if (!l) return CL_EINVAL;
+    if (nsteps < 0) return fail(l, CL_EINVAL, "nsteps < 0");
+    if (!l->potential_set) return fail(l, CL_ESTATE, "cl_set_potential has not been called");
+    l->last_launches = 0;
+    if (nsteps == 0) return CL_OK;
+    if (!l->open) {
+        cl_status s = open_leapfrog(l);
+        if (s != CL_OK) return s;
+        l->last_launches += 1;
+    }
+    const std::vector<PassCoef> sched = step_schedule(l);
+    const int pps = (int)sched.size();
+    for (int i = 0; i < nsteps; ++i) {
+        if (l->use_graph) {
+            const int par = l->cur;
+            if (!l->graph[par]) {
+                cudaGraph_t g;
+                CUDA_TRY(l, cudaStreamBeginCapture(l->stream, cudaStreamCaptureModeThreadLocal));
+                int c = par;
+                cl_status s = CL_OK;
+                for (const auto& pc : sched) {
+                    s = run_pass(l, pc, c, c ^ 1);
+                    if (s != CL_OK) break;
+                    c ^= 1;
+                }
+                cudaError_t ee = cudaStreamEndCapture(l->stream, &g);
+                if (s != CL_OK) return s;
+                if (ee != cudaSuccess) return fail(l, CL_ECUDA, "graph capture failed: %s", cudaGetErrorString(ee));
+                ee = cudaGraphInstantiate(&l->graph[par], g, 0);
+                cudaGraphDestroy(g);
+                if (ee != cudaSuccess) return fail(l, CL_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ee));
+            }
+            CUDA_TRY(l, cudaGraphLaunch(l->graph[par], l->stream));
+            l->cur = (pps & 1) ? par ^ 1 : par;
+        } else {
+            for (const auto& pc : sched) {
+                cl_status s = run_pass(l, pc, l->cur, l->cur ^ 1);
+                if (s != CL_OK) return s;
+                l->cur ^= 1;
+            }
+        }
+        l->last_launches += pps;
+    }
+    l->diag_valid = true;
+    return CL_OK;
+}
+
+cl_status cl_sync(cl_lattice* l)
+{
+    if (!l) return CL_EINVAL;
+    DevScal h;
+    return read_status(l, &h);
+}
+
+cl_status cl_energies(cl_lattice* l, cl_energy* out, int32_t count)
+{
+    if (!l) return CL_EINVAL;
+    if (!out || count < 1 || count > 1) return fail(l, CL_EINVAL, "energies: bad output or count");
+    if (!l->diag_valid) {
+        cl_status s = energy_pass(l, 0);
+        if (s != CL_OK) return s;
+    }
+    DevScal h;
+    cl_status s = read_status(l, &h);
+    memset(out, 0, sizeof(cl_energy));
+    out->t = h.diag[D_T];
+    out->a = h.diag[D_A];
+    out->adot = h.diag[D_ADOT];
+    out->K[0] = h.diag[D_K0];
+    out->K[1] = h.diag[D_K1];
+    out->G[0] = h.diag[D_G0];
+    out->G[1] = h.diag[D_G1];
+    out->V = h.diag[D_V];
+    out->KE = h.diag[D_KE];
+    out->GB = h.diag[D_GB];
+    out->rho = h.diag[D_RHO];
+    out->p = h.diag[D_P];
+    out->hubble_violation = h.diag[D_HV];
+    out->gauss_violation = h.diag[D_GV];
+    out->step = h.step;
+    return s;
+}
+
+cl_status cl_init_vacuum(cl_lattice* l, int32_t member, const cl_vacuum_params* v)
+{
+    if (!l) return CL_EINVAL;
+    if (!v) return fail(l, CL_EINVAL, "vacuum params NULL");
+    if (member != 0 && member != -1) return fail(l, CL_EINVAL, "member %d out of range", member);
+    if (!l->potential_set) return fail(l, CL_ESTATE, "cl_set_potential has not been called");
+    const int N = l->N, nf = l->nf;
+    const double a = l->p.a0, al = l->p.alpha;
+    // homogeneous energy and Hubble rate (Eq. Friedmann2) for the momentum modes
+    const double f0 = v->fbar[0], f1 = nf > 1 ? v->fbar[1] : 0.0;
+    double rho_h = 0.5 * l->m2[0] * f0 * f0 + 0.25 * l->lam[0] * f0 * f0 * f0 * f0 + 0.5 * l->m2[1] * f1 * f1 +
+                   0.25 * l->lam[1] * f1 * f1 * f1 * f1 + 0.5 * l->g2 * f0 * f0 * f1 * f1;
+    for (int f = 0; f < nf; ++f) rho_h += v->dfbar[f] * v->dfbar[f] / (2.0 * pow(a, 2.0 * al));
+    const double H = l->p.expansion ? sqrt(pow(a, 2.0 * al) * l->p.kappa * rho_h / 3.0) : 0.0;
+
+    const size_t nh = (size_t)N * N * (N / 2 + 1);
+    double2 *fk = nullptr, *pk = nullptr;
+    double* real = nullptr;
+    cufftHandle plan = 0;
+    cl_status st = CL_OK;
+    if (cudaMalloc(&fk, nh * sizeof(double2)) != cudaSuccess || cudaMalloc(&pk, nh * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&real, (size_t)l->V * sizeof(double)) != cudaSuccess) {
+        st = fail(l, CL_ENOMEM, "vacuum scratch allocation failed");
+    }
+    if (st == CL_OK && cufftPlan3d(&plan, N, N, N, CUFFT_Z2D) != CUFFT_SUCCESS) st = fail(l, CL_ECUDA, "cufftPlan3d failed");
+    if (st == CL_OK && cufftSetStream(plan, l->stream) != CUFFT_SUCCESS) st = fail(l, CL_ECUDA, "cufftSetStream failed");
+    if (st == CL_OK) st = close_leapfrog(l, true);
+    for (int f = 0; st == CL_OK && f < nf; ++f) {
+        VacuumModeArgs A{};
+        A.N = N; A.field = f; A.member = 0; A.seed = v->seed;
+        A.L = l->p.L; A.kcut = v->kcut; A.amp2 = v->amp2; A.a = a; A.alpha = al; A.H = H;
+        A.m2eff = f == 0 ? l->m2[0] + 3.0 * l->lam[0] * f0 * f0 + l->g2 * f1 * f1
+                         : l->m2[1] + 3.0 * l->lam[1] * f1 * f1 + l->g2 * f0 * f0;
+        cudaError_t e = launch_vacuum_modes(A, fk, pk, l->stream);
+        if (e != cudaSuccess) { st = fail(l, CL_ECUDA, "vacuum modes: %s", cudaGetErrorString(e)); break; }
+        const double inv = 1.0 / (double)l->V;  // f(n) = N^-3 sum_k e^{+ikn} f(k)
+        if (cufftExecZ2D(plan, (cufftDoubleComplex*)fk, real) != CUFFT_SUCCESS) { st = fail(l, CL_ECUDA, "Z2D failed"); break; }
+        e = launch_real_to_field(l->p.precision, real, l->phi[f][l->cur], v->fbar[f], inv, l->V, l->stream);
+        if (e != cudaSuccess) { st = fail(l, CL_ECUDA, "convert: %s", cudaGetErrorString(e)); break; }
+        if (cufftExecZ2D(plan, (cufftDoubleComplex*)pk, real) != CUFFT_SUCCESS) { st = fail(l, CL_ECUDA, "Z2D failed"); break; }
+        e = launch_real_to_field(l->p.precision, real, l->pi[f][l->cur], pow(a, 3.0 - al) * v->dfbar[f], inv, l->V,
+                                 l->stream);
+        if (e != cudaSuccess) { st = fail(l, CL_ECUDA, "convert: %s", cudaGetErrorString(e)); break; }
+        if (has_kahan(l)) cudaMemsetAsync(l->cc[f][l->cur], 0, (size_t)l->V * l->es, l->stream);
+    }
+    if (st == CL_OK) {
+        DevScal h{};
+        h.a = a;
+        cudaError_t e = cudaMemcpyAsync(l->scal, &h, sizeof(DevScal), cudaMemcpyHostToDevice, l->stream);
+        if (e != cudaSuccess) st = fail(l, CL_ECUDA, "scalar upload: %s", cudaGetErrorString(e));
+    }
+    if (st == CL_OK) st = energy_pass(l, P_HUBBLE_INIT | P_COMMIT);
+    if (st == CL_OK && cudaStreamSynchronize(l->stream) != cudaSuccess) st = fail(l, CL_ECUDA, "sync failed");
+    if (plan) cufftDestroy(plan);
+    if (fk) cudaFree(fk);
+    if (pk) cudaFree(pk);
+    if (real) cudaFree(real);
+    l->open = false;
+    return st;
+}
+
+cl_status cl_spectrum(cl_lattice* l, int32_t member, int32_t field, double dn, int32_t type, double* k_out,
+                      double* delta_out, double* count_out, int32_t cap, int32_t* nbins)
+{
+    if (!l) return CL_EINVAL;
+    if (member != 0) return fail(l, CL_EINVAL, "member %d out of range", member);
+    if (!(dn > 0) || (type != 1 && type != 2) || cap < 0 || (cap > 0 && (!k_out || !delta_out || !count_out)))
+        return fail(l, CL_EINVAL, "spectrum: bad arguments");
+    int f = 0;
+    const int kind = field_kind(field, l->nf, &f);
+    if (kind < 0) return fail(l, CL_EINVAL, "field %d not present", field);
+    const int N = l->N;
+    const int nb = (int)floor(sqrt(3.0) * (N / 2) / dn + 0.5) + 1;
+    if (nbins) *nbins = nb;
+    if (cap == 0) return CL_OK;
+    int buf = l->cur;
+    if (l->open && kind == 1) {
+        cl_status s = close_leapfrog(l, false);
+        if (s != CL_OK) return s;
+        buf = l->cur ^ 1;
+    }
+    const void* src = kind == 0 ? l->phi[f][buf] : l->pi[f][buf];
+    const size_t nh = (size_t)N * N * (N / 2 + 1);
+    double* real = nullptr;
+    double2* F = nullptr;
+    double* bins = nullptr;  // S[nb], C[nb], k[nb], delta[nb]
+    cufftHandle plan = 0;
+    cl_status st = CL_OK;
+    if (cudaMalloc(&real, (size_t)l->V * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&F, nh * sizeof(double2)) != cudaSuccess || cudaMalloc(&bins, 4 * (size_t)nb * sizeof(double)) != cudaSuccess)
+        st = fail(l, CL_ENOMEM, "spectrum scratch allocation failed");
+    if (st == CL_OK && cufftPlan3d(&plan, N, N, N, CUFFT_D2Z) != CUFFT_SUCCESS) st = fail(l, CL_ECUDA, "cufftPlan3d failed");
+    if (st == CL_OK && cufftSetStream(plan, l->stream) != CUFFT_SUCCESS) st = fail(l, CL_ECUDA, "cufftSetStream failed");
+    if (st == CL_OK && launch_field_to_double(l->p.precision, src, real, l->V, l->stream) != cudaSuccess)
+        st = fail(l, CL_ECUDA, "field conversion failed");
+    if (st == CL_OK && cufftExecD2Z(plan, real, (cufftDoubleComplex*)F) != CUFFT_SUCCESS) st = fail(l, CL_ECUDA, "D2Z failed");
+    if (st == CL_OK && cudaMemsetAsync(bins, 0, 2 * (size_t)nb * sizeof(double), l->stream) != cudaSuccess)
+        st = fail(l, CL_ECUDA, "memset failed");
+    if (st == CL_OK && launch_spectrum_bins(F, N, dn, nb, bins, bins + nb, l->stream) != cudaSuccess)
+        st = fail(l, CL_ECUDA, "binning failed");
+    if (st == CL_OK &&
+        launch_spectrum_finish(bins, bins + nb, N, l->p.L, dn, type, nb, bins + 2 * nb, bins + 3 * nb, l->stream) != cudaSuccess)
+        st = fail(l, CL_ECUDA, "spectrum finish failed");
+    std::vector<double> h(4 * (size_t)nb);
+    if (st == CL_OK && cudaMemcpyAsync(h.data(), bins, 4 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, l->stream) != cudaSuccess)
+        st = fail(l, CL_ECUDA, "copy failed");
+    if (st == CL_OK && cudaStreamSynchronize(l->stream) != cudaSuccess) st = fail(l, CL_ECUDA, "sync failed");
+    if (st == CL_OK) {
+        const int n = cap < nb ? cap : nb;
+        for (int i = 0; i < n; ++i) {
+            count_out[i] = h[nb + i];
+            k_out[i] = h[2 * nb + i];
+            delta_out[i] = h[3 * nb + i];
+        }
+    }
+    if (plan) cufftDestroy(plan);
+    if (real) cudaFree(real);
+    if (F) cudaFree(F);
+    if (bins) cudaFree(bins);
+    return st;
+}
+
+}  // extern "C"

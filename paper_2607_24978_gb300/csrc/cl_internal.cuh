@@ -1,0 +1,100 @@
+// Internal declarations of libcl.so (CUDA sm_103a).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cl.h"
+
+namespace clk {
+
+// Status bits of the device status word.
+enum : int { ST_NAN = 1, ST_CONSTRAINT = 2, ST_TIMEOUT = 4 };
+
+// Diagnostics written by the last block of every fused pass (energies at the pass's
+// integer time).  Index names follow cl_energy.
+enum {
+    D_T = 0, D_A, D_ADOT, D_K0, D_K1, D_G0, D_G1, D_V, D_KE, D_GB, D_RHO, D_P, D_HV, D_GV, D_NDIAG
+};
+
+// Device-resident scalar state of one lattice (one ensemble member).
+struct DevScal {
+    double a;       // scale factor at the time of the stored field values
+    double b;       // a' at the staggered (open) or integer (closed) position
+    double t;       // alpha-time of the stored field values
+    double diag[D_NDIAG];
+    long long step;
+    unsigned int counter;  // last-block-done arrival counter; the last block resets it to 0
+    int status;            // ST_* bits, sticky until read by the host
+    double pad[2];
+};
+
+// Flags of one fused scalar pass.
+enum : int {
+    P_DRIFT = 1,        // apply the drift phi += d a_half^(alpha-3) pi before the kick
+    P_COMMIT = 2,       // update a, a', t and step in DevScal (else only diag)
+    P_EXPANSION = 4,    // self-consistent expansion (Eq. Friedmann1)
+    P_HUBBLE_INIT = 8,  // set a' from Eq. Friedmann2 with this pass's energies first
+    P_COUNT_STEP = 16,  // this pass ends a time step
+};
+
+// Largest dynamic shared memory a fused-pass block may use (227 KB per block on sm_103a,
+// less the kernels' static shared memory).
+constexpr int kPassMaxSmem = 227 * 1024 - 2048;
+
+// Quantities reduced by the scalar pass: per field sum pi^2 and sum (grad+ phi)^2, and sum V.
+constexpr int kMaxQ = 5;
+
+template <typename T>
+struct ScalarPassArgs {
+    const T* phi_in[2];
+    const T* pi_in[2];
+    const T* c_in[2];
+    T* phi_out[2];
+    T* pi_out[2];
+    T* c_out[2];
+    DevScal* scal;
+    double* partials;   // [gridDim.x][kMaxQ]
+    int N, BY, DZ, nby, nbz;
+    double dx, alpha, kappa;
+    double d, e, k;     // drift, energy-kick and kick coefficients of this pass (already x dt)
+    double m2[2], lam[2], g2;
+    double hubble_limit;
+    int flags;
+    int stages;         // TMA stage buffers (2..6), 0 = general loader
+    int grid;           // persistent grid size (used when DZ < 0)
+};
+
+// Launch one fused scalar pass (drift -> stencil kick -> energies -> scale-factor update).
+// Returns the CUDA error of the launch.
+cudaError_t launch_scalar_pass(int precision, int nf, const void* args, int vw, cudaStream_t s);
+// Resident blocks per SM of the pass configured by args (tiles, stages).
+cudaError_t scalar_pass_blocks_per_sm(int precision, int nf, const void* args, int vw, int* blocks);
+int scalar_pass_vector_width(int precision, int N);
+size_t scalar_pass_smem(int precision, int nf, int N, int BY);
+size_t scalar_pass_smem_bytes(int precision, int nf, int N, int BY, int stages);
+bool scalar_pass_tma_ok(int precision, int N);
+int scalar_pass_threads(int precision, int N, int BY);
+
+// Vacuum initial conditions: fills the half spectrum (kx in [0, N/2]) of delta f and
+// delta pi for one field into two complex-double buffers of N*N*(N/2+1) entries.
+struct VacuumModeArgs {
+    int N, field;
+    uint32_t member;
+    uint64_t seed;
+    double L, kcut, amp2, a, alpha, H, m2eff;
+};
+cudaError_t launch_vacuum_modes(const VacuumModeArgs& a, double2* fk, double2* pk, cudaStream_t s);
+// out[n] = base + scale * in[n], converted to the field's element type.
+cudaError_t launch_real_to_field(int precision, const double* in, void* out, double base, double scale,
+                                 int64_t n, cudaStream_t s);
+cudaError_t launch_field_to_double(int precision, const void* in, double* out, int64_t n, cudaStream_t s);
+// Shell binning of |F|^2 over a real-to-complex half spectrum: S[l], C[l] (zeroed by the caller).
+cudaError_t launch_spectrum_bins(const double2* F, int N, double dn, int nbins, double* S, double* C,
+                                 cudaStream_t s);
+// delta[l] from S, C per the spectrum formula of cl_spectrum.
+cudaError_t launch_spectrum_finish(const double* S, const double* C, int N, double L, double dn, int type,
+                                   int nbins, double* k_out, double* delta_out, cudaStream_t s);
+cudaError_t launch_fill(void* p, int precision, int64_t n, double v, cudaStream_t s);
+
+}  // namespace clk

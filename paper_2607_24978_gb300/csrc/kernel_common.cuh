@@ -1,0 +1,182 @@
+// Device helpers shared by the lattice kernels (vector access, exact rounding,
+// per-thread accumulators, fixed-order block reductions, TMA bulk copies and
+// bounded mbarrier waits).
+#pragma once
+
+#include <stdint.h>
+
+#include "cl_internal.cuh"
+
+namespace clk {
+
+template <typename T, int VW> struct VT;
+template <> struct VT<float, 4> { using type = float4; };
+template <> struct VT<float, 2> { using type = float2; };
+template <> struct VT<float, 1> { using type = float; };
+template <> struct VT<double, 2> { using type = double2; };
+template <> struct VT<double, 1> { using type = double; };
+
+template <typename T, int VW>
+__device__ __forceinline__ void vload(T (&d)[VW], const T* __restrict__ p)
+{
+    using V = typename VT<T, VW>::type;
+    V v = __ldg(reinterpret_cast<const V*>(p));
+    const T* q = reinterpret_cast<const T*>(&v);
+#pragma unroll
+    for (int i = 0; i < VW; ++i) d[i] = q[i];
+}
+
+template <typename T, int VW>
+__device__ __forceinline__ void vload_smem(T (&d)[VW], const T* p)
+{
+    using V = typename VT<T, VW>::type;
+    V v = *reinterpret_cast<const V*>(p);
+    const T* q = reinterpret_cast<const T*>(&v);
+#pragma unroll
+    for (int i = 0; i < VW; ++i) d[i] = q[i];
+}
+
+template <typename T, int VW>
+__device__ __forceinline__ void vstore(T* p, const T (&s)[VW])
+{
+    using V = typename VT<T, VW>::type;
+    V v;
+    T* q = reinterpret_cast<T*>(&v);
+#pragma unroll
+    for (int i = 0; i < VW; ++i) q[i] = s[i];
+    *reinterpret_cast<V*>(p) = v;
+}
+
+// Explicitly rounded operations: the drift of a halo element must be bit-identical
+// to the owner's drift of the same element, so no contraction choice is left to
+// the compiler.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
+// phi += cd * pi, with Kahan compensation c when KAHAN.
+template <typename T, bool KAHAN>
+__device__ __forceinline__ void drift(T& phi, T& c, T pi, T cd)
+{
+    if (KAHAN) {
+        const T y = fma_rn(cd, pi, -c);
+        const T t = add_rn(phi, y);
+        c = sub_rn(sub_rn(t, phi), y);
+        phi = t;
+    } else {
+        phi = fma_rn(cd, pi, phi);
+    }
+}
+
+// Per-thread accumulator: compensated float sum for FP32 fields, plain double for FP64.
+template <typename T> struct Acc;
+template <> struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = __fsub_rn(x, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+// Sum v[q] over the block; the result is valid in thread 0.  Fixed reduction order.
+template <int Q>
+__device__ __forceinline__ void block_reduce(double (&v)[Q], double (*s_red)[kMaxQ], int tid, int nthr)
+{
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+        for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+    const int warp = tid >> 5, lane = tid & 31, nw = (nthr + 31) >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) s_red[warp][q] = v[q];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            double x = lane < nw ? s_red[lane][q] : 0.0;
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            v[q] = x;
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- TMA / mbarrier
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Make initialised barriers visible to the asynchronous (TMA) proxy.
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Generic-proxy accesses to shared memory before this point are ordered before later
+// asynchronous-proxy (TMA) writes to it.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// One bulk (non-tensor) TMA copy global -> shared, completing on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar` to complete, giving up after limit_ns.
+// Returns false on timeout (the caller records it; it never spins unbounded).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns)
+{
+    uint32_t done = 0;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (true) {
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (global_timer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+}  // namespace clk
