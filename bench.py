@@ -202,11 +202,18 @@ def run_reference(args, world, rank):
 
 
 # ------------------------------------------------------------------ GPU arm
-def make_lattice(cl, precision, stream):
+def make_lattice(cl, precision, stream, args=None):
     g = cl.Lattice(N, L, 2, precision, cl.CL_INT_YOSHIDA4, expansion=True, alpha=ALPHA, kappa=KAPPA, dt=DT,
                    stream=stream)
     g.cl_set_potential(cl.CL_POT_M2_G2, [1.0, G2])
     g.cl_init_vacuum(SEED, 1e30, AMP2, (1.0, 0.0), (0.0, 0.0))
+    if args is not None:  # tile overrides (profiling and tuning runs)
+        if args.stages is not None:
+            g.cl_set_option(cl.CL_OPT_STAGES, args.stages)
+        if args.by is not None:
+            g.cl_set_option(cl.CL_OPT_TILE_BY, args.by)
+        if args.dz is not None:
+            g.cl_set_option(cl.CL_OPT_TILE_DZ, args.dz)
     return g
 
 
@@ -237,7 +244,7 @@ def run_gpu(args, world, rank, local):
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     peak_src = "of measured" if peaks else "of fallback"
 
-    g = make_lattice(cl, cl.CL_PREC_FP32_KAHAN, stream.cuda_stream)
+    g = make_lattice(cl, cl.CL_PREC_FP32_KAHAN, stream.cuda_stream, args)
     g.cl_step(args.warmup)
     g.cl_sync()
     barrier(world)
@@ -263,6 +270,13 @@ def run_gpu(args, world, rank, local):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "traffic": traffic, "kernel": "k_scalar_pass<float,2,kahan,4>",
                 "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_src}
+
+    if args.profile:
+        print(json.dumps({"metric": METRIC, "value": value, "unit": "Gsite-updates/s", "profile": True,
+                          "steps": args.steps, "roofline_frac": roofline["frac"],
+                          "gpu_launches": launches}), flush=True)
+        g.close()
+        return
 
     # end to end through the C ABI with host buffers
     e2e_steps = max(2, min(args.steps, 5))
@@ -315,6 +329,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="time the device steps only (no e2e, FP64 or CPU legs): the command profiled with ncu")
+    ap.add_argument("--stages", type=int, default=None, help="override CL_OPT_STAGES")
+    ap.add_argument("--by", type=int, default=None, help="override CL_OPT_TILE_BY")
+    ap.add_argument("--dz", type=int, default=None, help="override CL_OPT_TILE_DZ")
     args = ap.parse_args()
     world, rank, local = dist_init(args)
     if args.impl == "reference":

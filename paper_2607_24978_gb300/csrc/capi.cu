@@ -93,14 +93,23 @@ cl_status choose_tiles(cl_lattice* l)
     const int TX = N / l->VW;
     // TMA staging needs rows of 16-byte multiples.  Default: as many stages as fit one
     // block per SM in shared memory (loads kept in flight are what the pass needs).
-    const bool tma = l->opt_stages >= 0 && scalar_pass_tma_ok(prec, N);
-    int BY = l->opt_BY > 0 ? l->opt_BY : (TX >= 256 ? 1 : 256 / TX);
+    // The TMA kernel adds a producer warp to the consumer threads; blocks stay <= 512 threads.
+    // FP64 passes are bound by GB300's FP64 rate, not by memory: they default to the
+    // direct loader, which measured faster for them.
+    bool tma = l->opt_stages >= 0 && scalar_pass_tma_ok(prec, N) && scalar_pass_threads(prec, N, 1) <= 480 &&
+               !(prec == CL_PREC_FP64 && l->opt_stages == 0);
+    const int max_consumers = tma ? 480 : 512;
+    // Default tile: as many rows as the consumer threads allow (more warps per SM), with
+    // three TMA stages; measured best on GB300 for 256^3 and 512^3 lattices.
+    int BY = l->opt_BY > 0 ? l->opt_BY : (tma ? max_consumers / TX : (TX >= 256 ? 1 : 256 / TX));
     if (BY > N) BY = N;
     if (BY < 1) BY = 1;
-    while (BY > 1 && scalar_pass_threads(prec, N, BY) > 512) BY /= 2;
+    while (BY > 1 && scalar_pass_threads(prec, N, BY) > max_consumers) --BY;
     int stages = 0;
     if (tma) {
-        stages = l->opt_stages > 0 ? l->opt_stages : 6;
+        stages = l->opt_stages > 0 ? l->opt_stages : 3;
+        if (l->opt_BY <= 0)
+            while (BY > 1 && scalar_pass_smem_bytes(prec, l->nf, N, BY, stages) > (size_t)kPassMaxSmem) --BY;
         while (BY > 1 && scalar_pass_smem_bytes(prec, l->nf, N, BY, 2) > (size_t)kPassMaxSmem) BY /= 2;
         while (stages > 2 && scalar_pass_smem_bytes(prec, l->nf, N, BY, stages) > (size_t)kPassMaxSmem) --stages;
         if (scalar_pass_smem_bytes(prec, l->nf, N, BY, stages) > (size_t)kPassMaxSmem) stages = 0;

@@ -336,176 +336,17 @@ __global__ void __launch_bounds__(512) k_scalar_pass(const ScalarPassArgs<T> A)
     finish_pass<T, NF>(A, accK, accG, accV, s_coef, s_red, &s_last, tid, nthr, 0);
 }
 
-// ------------------------------------------------------------------ TMA-staged loader
-template <typename T, int NF, bool KAHAN, int VW, int S>
-__global__ void __launch_bounds__(512) k_scalar_pass_tma(const ScalarPassArgs<T> A)
-{
-    constexpr int KPF = KAHAN ? 3 : 2;  // arrays per field in a stage: phi, pi (, c)
-    constexpr int NARR = NF * KPF;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t s_bar[S];
-    __shared__ double s_coef[4];
-    __shared__ double s_red[32][kMaxQ];
-    __shared__ int s_last, s_timeout;
-
-    const int N = A.N, BY = A.BY;
-    const int TX = N / VW;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int r = tid < BY * TX ? tid / TX : BY, tx = tid < BY * TX ? tid % TX : 0;
-    const int x0 = tx * VW;
-    const int arr_stride = (BY + 2) * N;  // elements of one array in one stage / ring slot
-    const int stage_stride = NARR * arr_stride;
-    T* stage = reinterpret_cast<T*>(smem_raw);
-    T* ring = stage + S * stage_stride;  // [3][NF][BY+2][N] drifted fields
-    const int ring_slot = NF * arr_stride;
-    long long u0, u1;
-    block_units(N, A.nby, A.DZ, u0, u1);
-    // current segment (set in the loop below): tile rows y0 .. y0+R-1, planes z0 .. z0+NZ-1,
-    // pipelined as nplanes = NZ + 2 planes z0-1 .. z0+NZ; jg counts planes over all segments
-    // of the block and selects the stage (jg % S) and the mbarrier phase (jg / S).
-    int y0 = 0, z0 = 0, R = 1, NZ = 0, nplanes = 0, ylo = 0, yhi = 0, jg = 0;
-    uint32_t plane_bytes = 0;
-
-    if (tid == 0) {
-        pass_coefficients(A.scal->a, A.scal->b, A.d, A.alpha, A.dx, (A.flags & P_EXPANSION) != 0, s_coef);
-#pragma unroll
-        for (int s = 0; s < S; ++s) mbar_init(&s_bar[s], 1);
-        mbar_fence_init();
-        s_timeout = 0;
-    }
-    __syncthreads();
-    const T cd = (T)s_coef[0], cL = (T)s_coef[1], cV = (T)s_coef[2];
-    const T ce = (T)A.e, ck = (T)A.k;
-    const bool do_drift = (A.flags & P_DRIFT) != 0;
-    const PotCoef<T> P(A.m2, A.lam, A.g2);
-    Acc<T> accK[NF], accG[NF], accV;
-
-    // Warp 0: copy plane j (z = z0 - 1 + j) of every array into stage (jg + j) % S.
-    auto issue = [&](int j) {
-        int zz = z0 - 1 + j;
-        zz = zz < 0 ? zz + N : (zz >= N ? zz - N : zz);
-        const int st = (jg + j) % S;
-        if (tid == 0) mbar_arrive_expect_tx(&s_bar[st], plane_bytes);
-        __syncwarp();
-        if (tid < 3 * NARR) {
-            const int a = tid / 3, part = tid - 3 * (tid / 3);
-            const int f = a / KPF, kind = a - KPF * (a / KPF);
-            const T* src = kind == 0 ? A.phi_in[f] : (kind == 1 ? A.pi_in[f] : A.c_in[f]);
-            const int y = part == 0 ? ylo : (part == 1 ? y0 : yhi);
-            const int srow = part == 0 ? 0 : (part == 1 ? 1 : R + 1);
-            const int nrows = part == 1 ? R : 1;
-            T* dst = stage + st * stage_stride + a * arr_stride + srow * N;
-            tma_bulk_g2s(dst, src + ((size_t)zz * N + y) * N, (uint32_t)(nrows * N * sizeof(T)), &s_bar[st]);
-        }
-    };
-
-    T pcur[NF][VW], pnext[NF][VW];
-    for (long long u = u0; u < u1;) {
-    const int tile = (int)(u / N);
-    z0 = (int)(u - (long long)tile * N);
-    NZ = (int)min((long long)(N - z0), u1 - u);
-    y0 = tile * BY;
-    R = min(BY, N - y0);
-    u += NZ;
-    nplanes = NZ + 2;
-    plane_bytes = (uint32_t)(NARR * (R + 2) * N * sizeof(T));
-    ylo = y0 == 0 ? N - 1 : y0 - 1;
-    yhi = y0 + R == N ? 0 : y0 + R;
-    if (tid < 32) {
-        fence_proxy_async_smem();  // stages were read by the previous segment
-        for (int j = 0; j < S && j < nplanes; ++j) issue(j);
-    }
-    for (int j = 0; j < nplanes; ++j) {
-        const int st = (jg + j) % S;
-        if (!mbar_wait_bounded(&s_bar[st], (uint32_t)(((jg + j) / S) & 1), s_timeout ? 1000000ull : 2000000000ull))
-            s_timeout = 1;
-        const T* sb = stage + st * stage_stride;
-        T* rs = ring + (j % 3) * ring_slot;
-        const bool write_out = j >= 1 && j <= NZ;
-        // drift own rows (and write them out), keep their momenta for the kick
-        if (r < R) {
-            int zz = z0 - 1 + j;
-            zz = zz < 0 ? zz + N : (zz >= N ? zz - N : zz);
-            const size_t base = ((size_t)zz * N + (y0 + r)) * N + x0;
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                T ph[VW], pv[VW], cv[VW];
-                const T* sa = sb + f * KPF * arr_stride + (r + 1) * N + x0;
-                vload_smem<T, VW>(ph, sa);
-                vload_smem<T, VW>(pv, sa + arr_stride);
-                if (KAHAN) vload_smem<T, VW>(cv, sa + 2 * arr_stride);
-                if (do_drift) {
-#pragma unroll
-                    for (int i = 0; i < VW; ++i) drift<T, KAHAN>(ph[i], cv[i], pv[i], cd);
-                }
-                vstore<T, VW>(rs + f * arr_stride + (r + 1) * N + x0, ph);
-                if (write_out) {
-                    vstore<T, VW>(A.phi_out[f] + base, ph);
-                    if (KAHAN) vstore<T, VW>(A.c_out[f] + base, cv);
-                }
-#pragma unroll
-                for (int i = 0; i < VW; ++i) pnext[f][i] = pv[i];
-            }
-        }
-        // drift the two halo rows
-        for (int h = tid; h < 2 * TX; h += nthr) {
-            const int sel = h / TX, vx = (h - sel * TX) * VW;
-            const int srow = sel == 0 ? 0 : R + 1;
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                T ph[VW], pv[VW], cv[VW];
-                const T* sa = sb + f * KPF * arr_stride + srow * N + vx;
-                vload_smem<T, VW>(ph, sa);
-                if (do_drift) {
-                    vload_smem<T, VW>(pv, sa + arr_stride);
-                    if (KAHAN) vload_smem<T, VW>(cv, sa + 2 * arr_stride);
-#pragma unroll
-                    for (int i = 0; i < VW; ++i) drift<T, KAHAN>(ph[i], cv[i], pv[i], cd);
-                }
-                vstore<T, VW>(rs + f * arr_stride + srow * N + vx, ph);
-            }
-        }
-        __syncthreads();  // stage st consumed, ring slot j % 3 complete
-        if (tid < 32 && j + S < nplanes) {
-            fence_proxy_async_smem();
-            issue(j + S);
-        }
-        if (j >= 2 && r < R) {
-            const T* Sc[NF];
-            const T* Szm[NF];
-            const T* Szp[NF];
-            const T* rl = ring + ((j - 2) % 3) * ring_slot;
-            const T* rc = ring + ((j - 1) % 3) * ring_slot;
-            const T* ru = ring + (j % 3) * ring_slot;
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                Sc[f] = rc + f * arr_stride + (r + 1) * N;
-                Szm[f] = rl + f * arr_stride + (r + 1) * N;
-                Szp[f] = ru + f * arr_stride + (r + 1) * N;
-            }
-            const size_t base = ((size_t)(z0 + j - 2) * N + (y0 + r)) * N + x0;
-            kick_vector<T, NF, VW>(Sc, Szm, Szp, N, x0, pcur, cL, cV, ce, ck, P, A.pi_out, base, accK, accG, accV);
-        }
-#pragma unroll
-        for (int f = 0; f < NF; ++f)
-#pragma unroll
-            for (int i = 0; i < VW; ++i) pcur[f][i] = pnext[f][i];
-        __syncthreads();  // ring slot (j+1) % 3 may be overwritten next
-    }
-    jg += nplanes;
-    }  // segments
-    finish_pass<T, NF>(A, accK, accG, accV, s_coef, s_red, &s_last, tid, nthr, s_timeout);
-}
+#include "scalar_pass_tma.cuh"
 
 // ------------------------------------------------------------------ launchers
 size_t scalar_pass_smem_bytes(int precision, int nf, int N, int BY, int stages)
 {
     const size_t es = precision == CL_PREC_FP64 ? 8 : 4;
     const size_t rows = (size_t)(BY + 2) * N * es;
-    const size_t ring = (size_t)nf * 3 * rows;
-    if (stages <= 0) return ring;
+    if (stages <= 0) return (size_t)nf * 3 * rows;  // direct loader: three-plane ring
+    // TMA loader: three-slot ring of drifted fields plus the stage buffers
     const size_t narr = (size_t)nf * (precision == CL_PREC_FP32_KAHAN ? 3 : 2);
-    return ring + (size_t)stages * narr * rows;
+    return (size_t)nf * 3 * rows + (size_t)stages * narr * rows;
 }
 
 template <typename K>
@@ -520,7 +361,7 @@ static cudaError_t launch_one(const ScalarPassArgs<T>& A, cudaStream_t s, int* o
 {
     const int prec = sizeof(T) == 8 ? CL_PREC_FP64 : (KAHAN ? CL_PREC_FP32_KAHAN : CL_PREC_FP32);
     const int TX = A.N / VW;
-    dim3 block(((TX * A.BY + 31) / 32) * 32);
+    dim3 block(((TX * A.BY + 31) / 32) * 32 + (A.stages > 0 ? 32 : 0));  // + producer warp
     dim3 grid(A.DZ > 0 ? A.nby * A.nbz : A.grid);  // DZ < 0: balanced persistent ranges
     const size_t smem = scalar_pass_smem_bytes(prec, NF, A.N, A.BY, A.stages);
     static bool attr_set[8] = {false, false, false, false, false, false, false, false};
