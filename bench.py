@@ -55,6 +55,27 @@ def config(extra=None):
     return c
 
 
+KERNEL_SOURCES = ["paper_2607_24978_gb300/csrc/scalar_pass.cu", "paper_2607_24978_gb300/csrc/scalar_pass_tma.cuh",
+                  "paper_2607_24978_gb300/csrc/kernel_common.cuh", "paper_2607_24978_gb300/csrc/cl_internal.cuh"]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the fused pass from the committed ncu summary, or None when
+    the kernel sources changed since those counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "scalar_pass_256_yoshida4_fp32kahan.md")
+    try:
+        fields = dict(l.split(":", 1) for l in open(path) if l.startswith(("traffic_bytes", "kernel_sources")))
+        h = hashlib.sha256()
+        for s in KERNEL_SOURCES:
+            h.update(open(os.path.join(ROOT, s), "rb").read())
+        if h.hexdigest()[:16] != fields["kernel_sources_sha256_16"].strip():
+            return None
+        return int(fields["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -260,15 +281,9 @@ def run_gpu(args, world, rank, local):
     pass_s = el / (args.steps * PASSES_PER_STEP)
     bytes_launch = N ** 3 * BYTES_PER_SITE_PASS
     achieved = bytes_launch / pass_s / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "scalar_pass_traffic.json")
-    if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get("bytes_per_launch_256")
-        except Exception:
-            traffic = None
+    traffic = profiled_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": traffic, "kernel": "k_scalar_pass<float,2,kahan,4>",
+                "traffic": traffic, "kernel": "k_scalar_pass_tma<float,2,kahan,4,3>",
                 "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_src}
 
     if args.profile:
