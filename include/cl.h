@@ -202,6 +202,51 @@ cl_status cl_set_hubble_limit(cl_lattice* l, double limit);
 enum { CL_OPT_GRAPH = 0, CL_OPT_TILE_BY = 1, CL_OPT_TILE_DZ = 2, CL_OPT_STAGES = 3 };
 cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value);
 
+/* ---- Allocation-free pass (the paper has no counterpart; this serves callers that cannot
+ * allocate device memory when they step: code inside an application that owns a fixed memory
+ * arena, hosts that forbid allocation after start-up, frameworks that hand over only
+ * pre-allocated buffers).
+ *
+ * cl_fused_pass_noalloc runs one fused pass of the same kernel cl_step uses, on device arrays
+ * the caller owns, and allocates nothing: no cudaMalloc/cudaFree and no allocating library
+ * call.  One pass drifts phi by `drift` (with a' and a drifted alongside), kicks pi by `kick`,
+ * evaluates the energies with pi + energy_kick * F and advances a' by kick * a''.  Velocity
+ * Verlet in staggered form is, with h = dt: an opening pass {0, 0, h/2}, then {h, h/2, h} per
+ * step; {0, -h/2, -h/2} returns the momenta to the integer time.
+ *
+ * Scratch (block partials of the energy reduction, the arrival counter, the working copy of
+ * a, a', t) lives in one fixed array of static device memory inside the library, 327,936
+ * bytes (320 KiB), which every GPU that loads the library holds until the process exits.  It limits a
+ * pass to 8192 blocks of the direct-load kernel, which covers every N the library accepts;
+ * a request it cannot serve returns CL_EINVAL.  The first call on a device looks up that
+ * array's device address (with the device current); make that first call before any stream
+ * capture.  All calls share the array and each clears what must start at zero: calls whose
+ * GPU work overlaps (other streams, other host threads) race and must be serialised by the
+ * caller.  Work is queued on `stream`; the call does not synchronise.
+ *
+ * Arrays: N^3 elements of the precision's type (double for CL_PREC_FP64, float otherwise),
+ * site index (z*N + y)*N + x; inputs and outputs must be distinct buffers; c_in/c_out (the
+ * Kahan compensations) are used with CL_PREC_FP32_KAHAN only.  scalars: device, 3 doubles
+ * {a, a', t}, read and then overwritten with the values after the pass.  energies: device,
+ * 14 doubles {t, a, a', K0, K1, G0, G1, V, KE, GB, rho, p, hubble_violation, gauss_violation}
+ * at the pass's integer time, or NULL.  Errors: CL_EINVAL (bad descriptor), CL_ECUDA. */
+typedef struct {
+    int32_t N, nfields, precision, expansion;
+    double L, alpha, kappa;
+    double m2[2], lam[2], g2;           /* potential, as for CL_POT_POLY */
+    double drift, energy_kick, kick;    /* pass coefficients, already multiplied by dt */
+    const void* phi_in[2];
+    const void* pi_in[2];
+    const void* c_in[2];
+    void* phi_out[2];
+    void* pi_out[2];
+    void* c_out[2];
+    double* scalars;
+    double* energies;
+    void* stream;                       /* cudaStream_t, NULL = legacy default stream */
+} cl_pass_noalloc_desc;
+cl_status cl_fused_pass_noalloc(const cl_pass_noalloc_desc* d);
+
 /* Number of kernel launches queued by the most recent cl_step (graph replays count the
  * kernels inside the graph). */
 int64_t cl_last_launch_count(const cl_lattice* l);

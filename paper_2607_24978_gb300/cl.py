@@ -28,7 +28,8 @@ CL_OPT_GRAPH, CL_OPT_TILE_BY, CL_OPT_TILE_DZ, CL_OPT_STAGES = 0, 1, 2, 3
 # Every exported entry point of include/cl.h.
 EXPORTS = ["cl_init_lattice", "cl_free", "cl_set_potential", "cl_set_state", "cl_get_state", "cl_set_scalars",
            "cl_get_scalars", "cl_init_vacuum", "cl_step", "cl_sync", "cl_energies", "cl_spectrum",
-           "cl_set_hubble_limit", "cl_set_option", "cl_last_launch_count", "cl_strerror", "cl_last_error"]
+           "cl_set_hubble_limit", "cl_set_option", "cl_last_launch_count", "cl_strerror", "cl_last_error",
+           "cl_fused_pass_noalloc"]
 
 
 class cl_lattice_params(C.Structure):
@@ -55,6 +56,17 @@ class cl_energy(C.Structure):
                 "G1": self.G[1], "V": self.V, "KE": self.KE, "GB": self.GB, "rho": self.rho, "p": self.p,
                 "hubble_violation": self.hubble_violation, "gauss_violation": self.gauss_violation,
                 "step": self.step}
+
+
+class cl_pass_noalloc_desc(C.Structure):
+    """One fused pass on caller-owned device arrays (see cl_fused_pass_noalloc in cl.h)."""
+    _fields_ = [("N", C.c_int32), ("nfields", C.c_int32), ("precision", C.c_int32), ("expansion", C.c_int32),
+                ("L", C.c_double), ("alpha", C.c_double), ("kappa", C.c_double),
+                ("m2", C.c_double * 2), ("lam", C.c_double * 2), ("g2", C.c_double),
+                ("drift", C.c_double), ("energy_kick", C.c_double), ("kick", C.c_double),
+                ("phi_in", C.c_void_p * 2), ("pi_in", C.c_void_p * 2), ("c_in", C.c_void_p * 2),
+                ("phi_out", C.c_void_p * 2), ("pi_out", C.c_void_p * 2), ("c_out", C.c_void_p * 2),
+                ("scalars", C.c_void_p), ("energies", C.c_void_p), ("stream", C.c_void_p)]
 
 
 class CLError(RuntimeError):
@@ -96,6 +108,7 @@ def lib():
         L.cl_strerror.restype = C.c_char_p
         L.cl_last_error.argtypes = [C.c_void_p]
         L.cl_last_error.restype = C.c_char_p
+        L.cl_fused_pass_noalloc.argtypes = [P(cl_pass_noalloc_desc)]
         for name in EXPORTS:
             if name not in ("cl_free", "cl_last_launch_count", "cl_strerror", "cl_last_error"):
                 getattr(L, name).restype = C.c_int
@@ -228,3 +241,11 @@ class Lattice:
 
     def cl_last_launch_count(self):
         return int(lib().cl_last_launch_count(self.h))
+
+
+def cl_fused_pass_noalloc(desc):
+    """Queue one fused pass on caller-owned device arrays; allocates nothing.  `desc` is a
+    cl_pass_noalloc_desc whose pointers are device addresses (e.g. tensor.data_ptr())."""
+    s = lib().cl_fused_pass_noalloc(C.byref(desc))
+    if s != CL_OK:
+        raise CLError(s, "cl_fused_pass_noalloc")
