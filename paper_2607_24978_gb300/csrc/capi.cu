@@ -21,9 +21,13 @@ constexpr int kMaxN = 1536;
 // One pass of a kick-drift scheme in staggered form (see scalar_pass.cu):
 // drift by d, energies with pi + e F, kick by k.
 struct PassCoef {
-    double d, e, k;
+    double d, e, k;   // leapfrog pass: drift, energy-kick and kick coefficients
     int flags;
+    int rk = 0;       // 1: a 2N Runge-Kutta stage with coefficients A, B instead
+    double A = 0.0, B = 0.0;
 };
+
+bool is_rk(int integrator) { return integrator == CL_INT_RK3_3 || integrator == CL_INT_RK4_5; }
 
 }  // namespace
 
@@ -37,6 +41,9 @@ struct cl_lattice {
     void* phi[2][2] = {};  // [field][buffer]
     void* pi[2][2] = {};
     void* cc[2][2] = {};
+    void* kphi[2][2] = {};  // Runge-Kutta auxiliaries (RK integrators only)
+    void* kpi[2][2] = {};
+    int rk_BY = 1, rk_DZ = 1, rk_nby = 1, rk_nbz = 1;
     int cur = 0;
     DevScal* scal = nullptr;
     double* partials = nullptr;
@@ -154,6 +161,22 @@ cl_status choose_tiles(cl_lattice* l)
         nblocks = (int)(units < wave ? units : wave);
         l->grid = nblocks;
     }
+    if (is_rk(l->p.integrator)) {
+        // Runge-Kutta stage kernel (direct loads): about 256 threads per block, two blocks per
+        // SM, the y tiles cut into the same z chunks so that about one wave covers the lattice
+        int rby = TX >= 256 ? 1 : 256 / TX;
+        if (rby > N) rby = N;
+        const size_t es = (size_t)l->es;
+        while (rby > 1 && (size_t)l->nf * 3 * (rby + 2) * N * es > (size_t)kPassMaxSmem / 2) --rby;
+        l->rk_BY = rby;
+        l->rk_nby = (N + rby - 1) / rby;
+        int64_t nbz = (2 * (int64_t)nsm) / l->rk_nby;
+        if (nbz < 1) nbz = 1;
+        if (nbz > N) nbz = N;
+        l->rk_DZ = (int)((N + nbz - 1) / nbz);
+        l->rk_nbz = (N + l->rk_DZ - 1) / l->rk_DZ;
+        if (l->rk_nby * l->rk_nbz > nblocks) nblocks = l->rk_nby * l->rk_nbz;
+    }
     if (nblocks > l->partials_cap) {
         if (l->partials) cudaFree(l->partials);
         l->partials = nullptr;
@@ -220,9 +243,58 @@ cl_status run_pass_impl(cl_lattice* l, const PassCoef& pc, int in, int out, int*
     return CL_OK;
 }
 
+// One 2N Runge-Kutta stage reading buffer `in` and writing buffer `out`.
+template <typename T>
+cl_status run_rk_stage_t(cl_lattice* l, const PassCoef& pc, int in, int out)
+{
+    RkStageArgs<T> A{};
+    for (int f = 0; f < l->nf; ++f) {
+        A.phi_in[f] = (const T*)l->phi[f][in];
+        A.pi_in[f] = (const T*)l->pi[f][in];
+        A.c_in[f] = (const T*)l->cc[f][in];
+        A.kphi_in[f] = (const T*)l->kphi[f][in];
+        A.kpi_in[f] = (const T*)l->kpi[f][in];
+        A.phi_out[f] = (T*)l->phi[f][out];
+        A.pi_out[f] = (T*)l->pi[f][out];
+        A.c_out[f] = (T*)l->cc[f][out];
+        A.kphi_out[f] = (T*)l->kphi[f][out];
+        A.kpi_out[f] = (T*)l->kpi[f][out];
+    }
+    A.scal = l->scal;
+    A.partials = l->partials;
+    A.N = l->N; A.BY = l->rk_BY; A.DZ = l->rk_DZ; A.nby = l->rk_nby; A.nbz = l->rk_nbz;
+    A.dx = l->dx; A.alpha = l->p.alpha; A.kappa = l->p.kappa;
+    A.A = pc.A; A.B = pc.B; A.h = l->p.dt;
+    for (int f = 0; f < 2; ++f) { A.m2[f] = l->m2[f]; A.lam[f] = l->lam[f]; }
+    A.g2 = l->g2;
+    A.hubble_limit = l->hubble_limit;
+    A.flags = pc.flags | (l->p.expansion ? P_EXPANSION : 0);
+    cudaError_t e = launch_rk_stage(l->p.precision, l->nf, &A, l->VW, l->stream);
+    if (e != cudaSuccess) return fail(l, CL_ECUDA, "Runge-Kutta stage launch failed: %s", cudaGetErrorString(e));
+    return CL_OK;
+}
+
 cl_status run_pass(cl_lattice* l, const PassCoef& pc, int in, int out)
 {
+    if (pc.rk) return is_fp64(l) ? run_rk_stage_t<double>(l, pc, in, out) : run_rk_stage_t<float>(l, pc, in, out);
     return run_pass_impl(l, pc, in, out, nullptr);
+}
+
+// Low-storage 2N Runge-Kutta coefficients (A_s, B_s), as published:
+// RK3-3: Williamson, J. Comput. Phys. 35 (1980) 48.
+// RK4-5: Carpenter & Kennedy, NASA TM-109112 (1994), the five-stage fourth-order scheme.
+void rk_tables(int integrator, std::vector<double>& A, std::vector<double>& B)
+{
+    if (integrator == CL_INT_RK3_3) {
+        A = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+        B = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+    } else {
+        A = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+             -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+        B = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+             1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+             2277821191437.0 / 14882151754819.0};
+    }
 }
 
 cl_status query_blocks_per_sm(cl_lattice* l, int* per_sm)
@@ -243,7 +315,17 @@ std::vector<PassCoef> step_schedule(const cl_lattice* l)
 {
     const double h = l->p.dt;
     std::vector<PassCoef> s;
-    if (l->p.integrator == CL_INT_VV2) {
+    if (is_rk(l->p.integrator)) {
+        std::vector<double> A, B;
+        rk_tables(l->p.integrator, A, B);
+        for (size_t i = 0; i < A.size(); ++i) {
+            PassCoef pc{0.0, 0.0, 0.0, (i == 0 ? P_FIRST_STAGE : 0) | (i + 1 == A.size() ? P_COUNT_STEP : 0)};
+            pc.rk = 1;
+            pc.A = A[i];
+            pc.B = B[i];
+            s.push_back(pc);
+        }
+    } else if (l->p.integrator == CL_INT_VV2) {
         s.push_back({h, 0.5 * h, h, P_DRIFT | P_COMMIT | P_COUNT_STEP});
     } else {
         double w1, w0;
@@ -359,6 +441,8 @@ void cl_free(cl_lattice* l)
             if (l->phi[f][b]) cudaFree(l->phi[f][b]);
             if (l->pi[f][b]) cudaFree(l->pi[f][b]);
             if (l->cc[f][b]) cudaFree(l->cc[f][b]);
+            if (l->kphi[f][b]) cudaFree(l->kphi[f][b]);
+            if (l->kpi[f][b]) cudaFree(l->kpi[f][b]);
         }
     if (l->scal) cudaFree(l->scal);
     if (l->partials) cudaFree(l->partials);
@@ -376,8 +460,7 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
         p->integrator < 0 || p->integrator > 3 || p->gauge < 0 || p->gauge > 1 || !(p->L > 0) || !(p->dt > 0) ||
         !(p->a0 > 0) || p->reserved != 0)
         return CL_EINVAL;
-    if (p->gauge != CL_GAUGE_NONE || p->integrator == CL_INT_RK3_3 || p->integrator == CL_INT_RK4_5)
-        return CL_EUNSUPPORTED;
+    if (p->gauge != CL_GAUGE_NONE) return CL_EUNSUPPORTED;
     cl_lattice* l = new (std::nothrow) cl_lattice();
     if (!l) return CL_ENOMEM;
     l->p = *p;
@@ -402,7 +485,9 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
     for (int f = 0; f < l->nf; ++f)
         for (int b = 0; b < 2; ++b) {
             if (cudaMalloc(&l->phi[f][b], bytes) != cudaSuccess || cudaMalloc(&l->pi[f][b], bytes) != cudaSuccess ||
-                (has_kahan(l) && cudaMalloc(&l->cc[f][b], bytes) != cudaSuccess)) {
+                (has_kahan(l) && cudaMalloc(&l->cc[f][b], bytes) != cudaSuccess) ||
+                (is_rk(p->integrator) && (cudaMalloc(&l->kphi[f][b], bytes) != cudaSuccess ||
+                                          cudaMalloc(&l->kpi[f][b], bytes) != cudaSuccess))) {
                 cl_free(l);
                 return CL_ENOMEM;
             }
@@ -587,7 +672,8 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
     if (!l->potential_set) return fail(l, CL_ESTATE, "cl_set_potential has not been called");
     l->last_launches = 0;
     if (nsteps == 0) return CL_OK;
-    if (!l->open) {
+    const bool rk = is_rk(l->p.integrator);  // Runge-Kutta states stay at integer times
+    if (!l->open && !rk) {
         cl_status s = open_leapfrog(l);
         if (s != CL_OK) return s;
         l->last_launches += 1;
@@ -625,7 +711,9 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
         }
         l->last_launches += pps;
     }
-    l->diag_valid = true;
+    // a leapfrog step ends with the energies of its integer time; a Runge-Kutta stage
+    // reports those of the state it started from, so they are recomputed on demand
+    l->diag_valid = !rk;
     return CL_OK;
 }
 

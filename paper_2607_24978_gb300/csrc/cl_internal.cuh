@@ -26,7 +26,7 @@ struct DevScal {
     long long step;
     unsigned int counter;  // last-block-done arrival counter; the last block resets it to 0
     int status;            // ST_* bits, sticky until read by the host
-    double pad[2];
+    double rk[2];          // 2N Runge-Kutta auxiliaries of a and a' (k_a, k_a')
 };
 
 // Flags of one fused scalar pass.
@@ -36,6 +36,7 @@ enum : int {
     P_EXPANSION = 4,    // self-consistent expansion (Eq. Friedmann1)
     P_HUBBLE_INIT = 8,  // set a' from Eq. Friedmann2 with this pass's energies first
     P_COUNT_STEP = 16,  // this pass ends a time step
+    P_FIRST_STAGE = 32, // Runge-Kutta: first stage of a step (A = 0, k is not read)
 };
 
 // Largest dynamic shared memory a fused-pass block may use (227 KB per block on sm_103a,
@@ -75,6 +76,30 @@ size_t scalar_pass_smem(int precision, int nf, int N, int BY);
 size_t scalar_pass_smem_bytes(int precision, int nf, int N, int BY, int stages);
 bool scalar_pass_tma_ok(int precision, int N);
 int scalar_pass_threads(int precision, int N, int BY);
+
+// One 2N Runge-Kutta stage of the scalar fields and the scale factor.
+template <typename T>
+struct RkStageArgs {
+    const T* phi_in[2];
+    const T* pi_in[2];
+    const T* c_in[2];
+    const T* kphi_in[2];
+    const T* kpi_in[2];
+    T* phi_out[2];
+    T* pi_out[2];
+    T* c_out[2];
+    T* kphi_out[2];
+    T* kpi_out[2];
+    DevScal* scal;
+    double* partials;   // [gridDim.x][kMaxQ]
+    int N, BY, DZ, nby, nbz;
+    double dx, alpha, kappa;
+    double A, B, h;     // stage coefficients and the step size
+    double m2[2], lam[2], g2;
+    double hubble_limit;
+    int flags;          // P_EXPANSION, P_FIRST_STAGE, P_COUNT_STEP
+};
+cudaError_t launch_rk_stage(int precision, int nf, const void* args, int vw, cudaStream_t s);
 
 // Vacuum initial conditions: fills the half spectrum (kx in [0, N/2]) of delta f and
 // delta pi for one field into two complex-double buffers of N*N*(N/2+1) entries.

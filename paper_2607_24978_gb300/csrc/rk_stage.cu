@@ -1,0 +1,283 @@
+// One stage of a low-storage (2N) Runge-Kutta scheme for the scalar fields and the
+// scale factor (section "Non-symplectic evolvers"; RK3-3 of Williamson 1980 and RK4-5
+// of Carpenter & Kennedy 1994).  For the state y = (phi, pi, a, a') with
+//
+//   F(y) = (a^(alpha-3) pi,  a^(1+alpha) Lap phi - a^(3+alpha) dV/dphi,  a',  a''(a, rho(y), p(y)))
+//
+// a stage does  k <- A k + h F(y);  y <- y + B k  with one auxiliary array per field
+// degree of freedom.  The field part is one launch: each site needs the 7-point
+// stencil of the old phi only, so a block marches up z with a three-plane ring of the
+// old field in shared memory (full x rows, BY rows plus one halo row each side) and
+// reads pi, k_phi, k_pi (and the Kahan compensation of phi) of its own sites straight
+// from global memory.  The same launch reduces the volume-averaged energies of the old
+// state (FP64 across threads and blocks, fixed order), and the last block to arrive
+// uses them for the a' component of F, advancing a, a' and their own k values.  The
+// first stage (A = 0) does not read k.  Inputs and outputs are ping-pong buffers.
+#include <math.h>
+
+#include "cl_internal.cuh"
+#include "kernel_common.cuh"
+
+namespace clk {
+
+template <typename T, int NF, bool KAHAN, int VW>
+__global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);  // [NF][3][BY+2][N] old field
+    __shared__ double s_coef[4];
+    __shared__ double s_red[32][kMaxQ];
+    __shared__ int s_last;
+
+    const int N = A.N, BY = A.BY;
+    const int TX = N / VW;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int r = tid < BY * TX ? tid / TX : BY, tx = tid < BY * TX ? tid % TX : 0;
+    const int slot_stride = (BY + 2) * N, field_stride = 3 * slot_stride;
+    const int x0 = tx * VW;
+    const bool first = (A.flags & P_FIRST_STAGE) != 0;
+    long long u0, u1;
+    block_units(N, A.nby, A.DZ, u0, u1);
+
+    if (tid == 0) {
+        const double a = A.scal->a;
+        s_coef[0] = A.h * pow(a, A.alpha - 3.0);
+        s_coef[1] = A.h * pow(a, 1.0 + A.alpha) / (A.dx * A.dx);
+        s_coef[2] = A.h * pow(a, 3.0 + A.alpha);
+        s_coef[3] = a;
+    }
+    __syncthreads();
+    const T cphi = (T)s_coef[0], cL = (T)s_coef[1], cV = (T)s_coef[2];
+    const T cA = (T)A.A, cB = (T)A.B;
+    const PotCoef<T> P(A.m2, A.lam, A.g2);
+    Acc<T> accK[NF], accG[NF], accV;
+
+    int y0 = 0, z0 = 0, R = 1;
+    // Load plane z0 + zrel of own and halo rows of the old fields into ring slot `slot`.
+    auto fill = [&](int zrel, int slot) {
+        int zz = z0 + zrel;
+        zz = zz < 0 ? zz + N : (zz >= N ? zz - N : zz);
+        if (r < R) {
+            const size_t base = ((size_t)zz * N + (y0 + r)) * N + x0;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                T ph[VW];
+                vload<T, VW>(ph, A.phi_in[f] + base);
+                vstore<T, VW>(sm + f * field_stride + slot * slot_stride + (r + 1) * N + x0, ph);
+            }
+        }
+        for (int h = tid; h < NF * 2 * TX; h += nthr) {
+            const int f = h / (2 * TX), hv = h - f * 2 * TX;
+            const int sel = hv / TX, vx = (hv - sel * TX) * VW;
+            int y = sel == 0 ? y0 - 1 : y0 + R;
+            y = y < 0 ? y + N : (y >= N ? y - N : y);
+            const int srow = sel == 0 ? 0 : R + 1;
+            T ph[VW];
+            vload<T, VW>(ph, A.phi_in[f] + ((size_t)zz * N + y) * N + vx);
+            vstore<T, VW>(sm + f * field_stride + slot * slot_stride + srow * N + vx, ph);
+        }
+    };
+
+    for (long long u = u0; u < u1;) {
+        const int tile = (int)(u / N);
+        z0 = (int)(u - (long long)tile * N);
+        const int NZ = (int)min((long long)(N - z0), u1 - u);
+        y0 = tile * BY;
+        R = min(BY, N - y0);
+        u += NZ;
+        fill(-1, 0);
+        fill(0, 1);
+        for (int zr = 0; zr < NZ; ++zr) {
+            const int sl = zr % 3, sc = (zr + 1) % 3, su = (zr + 2) % 3;
+            fill(zr + 1, su);
+            __syncthreads();
+            if (r < R) {
+                const size_t base = ((size_t)(z0 + zr) * N + (y0 + r)) * N + x0;
+                T phc[NF][VW], lap[NF][VW];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const T* Sc = sm + f * field_stride + sc * slot_stride + (r + 1) * N;
+                    const T* Szm = sm + f * field_stride + sl * slot_stride + (r + 1) * N;
+                    const T* Szp = sm + f * field_stride + su * slot_stride + (r + 1) * N;
+                    T c[VW], ym[VW], yp[VW], zm[VW], zp[VW];
+                    vload_smem<T, VW>(c, Sc + x0);
+                    vload_smem<T, VW>(ym, Sc - N + x0);
+                    vload_smem<T, VW>(yp, Sc + N + x0);
+                    vload_smem<T, VW>(zm, Szm + x0);
+                    vload_smem<T, VW>(zp, Szp + x0);
+                    const T xm_edge = Sc[x0 == 0 ? N - 1 : x0 - 1];
+                    const T xp_edge = Sc[x0 + VW == N ? 0 : x0 + VW];
+                    T g = (T)0;
+#pragma unroll
+                    for (int i = 0; i < VW; ++i) {
+                        const T xm = i == 0 ? xm_edge : c[i - 1];
+                        const T xp = i == VW - 1 ? xp_edge : c[i + 1];
+                        lap[f][i] = ((xp + xm) + (yp[i] + ym[i]) + (zp[i] + zm[i])) - (T)6 * c[i];
+                        const T gx = xp - c[i], gy = yp[i] - c[i], gz = zp[i] - c[i];
+                        g += gx * gx + gy * gy + gz * gz;
+                        phc[f][i] = c[i];
+                    }
+                    accG[f].add(g);
+                }
+                T vsum = (T)0;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    T pv[VW], kf[VW], kp[VW], cv[VW], ksum = (T)0;
+                    vload<T, VW>(pv, A.pi_in[f] + base);
+                    if (!first) {
+                        vload<T, VW>(kf, A.kphi_in[f] + base);
+                        vload<T, VW>(kp, A.kpi_in[f] + base);
+                    }
+                    if (KAHAN) vload<T, VW>(cv, A.c_in[f] + base);
+                    T ph[VW], po[VW];
+#pragma unroll
+                    for (int i = 0; i < VW; ++i) {
+                        const T p0 = phc[0][i];
+                        const T p1 = NF > 1 ? phc[NF - 1][i] : (T)0;
+                        T dV;
+                        if (f == 0) dV = p0 * (P.m20 + P.l0 * p0 * p0 + (NF > 1 ? P.g2 * p1 * p1 : (T)0));
+                        else dV = p1 * (P.m21 + P.l1 * p1 * p1 + P.g2 * p0 * p0);
+                        ksum += pv[i] * pv[i];
+                        const T fphi = cphi * pv[i];
+                        const T fpi = cL * lap[f][i] - cV * dV;
+                        kf[i] = first ? fphi : cA * kf[i] + fphi;
+                        kp[i] = first ? fpi : cA * kp[i] + fpi;
+                        ph[i] = phc[f][i];
+                        drift<T, KAHAN>(ph[i], cv[i], kf[i], cB);  // phi += B k_phi (compensated in FP32)
+                        po[i] = pv[i] + cB * kp[i];
+                        if (f == 0) {
+                            T v = p0 * p0 * (P.h_m20 + P.q_l0 * p0 * p0);
+                            if (NF > 1) v += p1 * p1 * (P.h_m21 + P.q_l1 * p1 * p1) + P.h_g2 * p0 * p0 * p1 * p1;
+                            vsum += v;
+                        }
+                    }
+                    accK[f].add(ksum);
+                    vstore<T, VW>(A.phi_out[f] + base, ph);
+                    vstore<T, VW>(A.pi_out[f] + base, po);
+                    vstore<T, VW>(A.kphi_out[f] + base, kf);
+                    vstore<T, VW>(A.kpi_out[f] + base, kp);
+                    if (KAHAN) vstore<T, VW>(A.c_out[f] + base, cv);
+                }
+                accV.add(vsum);
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- block partials, last block: energies of the old state and the (a, a') stage ----
+    double v[kMaxQ];
+    v[0] = accK[0].value();
+    v[1] = NF > 1 ? accK[NF - 1].value() : 0.0;
+    v[2] = accG[0].value();
+    v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
+    v[4] = accV.value();
+    block_reduce<kMaxQ>(v, s_red, tid, nthr);
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < kMaxQ; ++q) A.partials[(size_t)blockIdx.x * kMaxQ + q] = v[q];
+        __threadfence();
+        const unsigned prev = atomicAdd(&A.scal->counter, 1u);
+        s_last = (prev + 1u == gridDim.x);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double w[kMaxQ];
+#pragma unroll
+    for (int q = 0; q < kMaxQ; ++q) w[q] = 0.0;
+    for (int b = tid; b < (int)gridDim.x; b += nthr)
+#pragma unroll
+        for (int q = 0; q < kMaxQ; ++q) w[q] += __ldcg(&A.partials[(size_t)b * kMaxQ + q]);
+    block_reduce<kMaxQ>(w, s_red, tid, nthr);
+    if (tid == 0) {
+        DevScal* S = A.scal;
+        const double vol = (double)N * N * N;
+        const double a = s_coef[3], b = S->b;
+        const double a2 = a * a, a6 = a2 * a2 * a2;
+        const double K0 = w[0] / (2.0 * a6 * vol), K1 = w[1] / (2.0 * a6 * vol);
+        const double G0 = w[2] / (A.dx * A.dx * 2.0 * a2 * vol), G1 = w[3] / (A.dx * A.dx * 2.0 * a2 * vol);
+        const double Vp = w[4] / vol;
+        const double K = K0 + K1, G = G0 + G1;
+        const double rho = K + G + Vp, p = K - G / 3.0 - Vp;
+        const bool expand = (A.flags & P_EXPANSION) != 0;
+        const double a2al = pow(a, 2.0 * A.alpha);
+        const double H = b / a;
+        const double hv = H != 0.0 ? fabs(H * H - a2al * A.kappa * rho / 3.0) / (H * H) : 0.0;
+        S->diag[D_T] = S->t;
+        S->diag[D_A] = a;
+        S->diag[D_ADOT] = b;
+        S->diag[D_K0] = K0;
+        S->diag[D_K1] = K1;
+        S->diag[D_G0] = G0;
+        S->diag[D_G1] = G1;
+        S->diag[D_V] = Vp;
+        S->diag[D_KE] = 0.0;
+        S->diag[D_GB] = 0.0;
+        S->diag[D_RHO] = rho;
+        S->diag[D_P] = p;
+        S->diag[D_HV] = hv;
+        S->diag[D_GV] = 0.0;
+        if (expand) {
+            const double Fa = b;
+            const double Fb = pow(a, 2.0 * A.alpha + 1.0) * (A.kappa / 6.0) * ((2.0 * A.alpha - 1.0) * rho - 3.0 * p);
+            const double ka = first ? A.h * Fa : A.A * S->rk[0] + A.h * Fa;
+            const double kb = first ? A.h * Fb : A.A * S->rk[1] + A.h * Fb;
+            S->rk[0] = ka;
+            S->rk[1] = kb;
+            S->a = a + A.B * ka;
+            S->b = b + A.B * kb;
+        }
+        if (A.flags & P_COUNT_STEP) {
+            S->t += A.h;
+            S->step += 1;
+        }
+        int st = 0;
+        if (!isfinite(rho) || !isfinite(p)) st |= ST_NAN;
+        if (first && A.hubble_limit > 0.0 && hv > A.hubble_limit) st |= ST_CONSTRAINT;
+        if (st) atomicOr(&S->status, st);
+        S->counter = 0u;
+    }
+}
+
+template <typename T, int NF, bool KAHAN, int VW>
+static cudaError_t launch_rk(const RkStageArgs<T>& A, cudaStream_t s)
+{
+    const int TX = A.N / VW;
+    dim3 block(((TX * A.BY + 31) / 32) * 32);
+    dim3 grid(A.nby * A.nbz);
+    const size_t smem = (size_t)NF * 3 * (A.BY + 2) * A.N * sizeof(T);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_rk_stage<T, NF, KAHAN, VW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kPassMaxSmem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_rk_stage<T, NF, KAHAN, VW><<<grid, block, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <typename T, int NF, bool KAHAN>
+static cudaError_t rk_vw(const RkStageArgs<T>& A, int vw, cudaStream_t s)
+{
+    if (vw == 1) return launch_rk<T, NF, KAHAN, 1>(A, s);
+    if (vw == 2) return launch_rk<T, NF, KAHAN, 2>(A, s);
+    if constexpr (sizeof(T) == 4) {
+        if (vw == 4) return launch_rk<T, NF, KAHAN, 4>(A, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rk_stage(int precision, int nf, const void* args, int vw, cudaStream_t s)
+{
+    if (precision == CL_PREC_FP64) {
+        const auto& A = *static_cast<const RkStageArgs<double>*>(args);
+        return nf == 1 ? rk_vw<double, 1, false>(A, vw, s) : rk_vw<double, 2, false>(A, vw, s);
+    }
+    const auto& A = *static_cast<const RkStageArgs<float>*>(args);
+    if (precision == CL_PREC_FP32_KAHAN)
+        return nf == 1 ? rk_vw<float, 1, true>(A, vw, s) : rk_vw<float, 2, true>(A, vw, s);
+    return nf == 1 ? rk_vw<float, 1, false>(A, vw, s) : rk_vw<float, 2, false>(A, vw, s);
+}
+
+}  // namespace clk

@@ -40,25 +40,6 @@
 
 namespace clk {
 
-// Work units are (y tile, z plane) pairs in tile-major order, U = nby * N of them.
-// Fixed chunks (DZ > 0): block b owns tile b % nby, planes [bz DZ, bz DZ + DZ) with
-// bz = b / nby.  Persistent (DZ < 0): block b owns the contiguous balanced range
-// [b U / G, (b+1) U / G) of a grid of G blocks, so every SM gets the same number of
-// planes and a block's pipeline restarts only where its range crosses a tile.
-// (The host turns "automatic" DZ into a fixed DZ; the kernels only see DZ > 0 or DZ < 0.)
-__device__ __forceinline__ void block_units(int N, int nby, int DZ, long long& u0, long long& u1)
-{
-    if (DZ > 0) {
-        const int by = blockIdx.x % nby, bz = blockIdx.x / nby;
-        u0 = (long long)by * N + (long long)bz * DZ;
-        u1 = u0 + min(DZ, N - bz * DZ);
-    } else {
-        const long long U = (long long)nby * N;
-        u0 = U * blockIdx.x / gridDim.x;
-        u1 = U * (blockIdx.x + 1) / gridDim.x;
-    }
-}
-
 // Scalar prefactors of a pass, computed once per block by thread 0.
 __device__ __forceinline__ void pass_coefficients(const double a_old, const double b_old, const double d,
                                                   const double alpha, const double dx, const bool expand,
@@ -71,16 +52,6 @@ __device__ __forceinline__ void pass_coefficients(const double a_old, const doub
     s_coef[2] = pow(a_new, 3.0 + alpha);
     s_coef[3] = a_new;
 }
-
-template <typename T>
-struct PotCoef {
-    T m20, m21, l0, l1, g2, h_m20, h_m21, q_l0, q_l1, h_g2;
-    __device__ __forceinline__ PotCoef(const double (&m2)[2], const double (&lam)[2], double g)
-        : m20((T)m2[0]), m21((T)m2[1]), l0((T)lam[0]), l1((T)lam[1]), g2((T)g), h_m20((T)(0.5 * m2[0])),
-          h_m21((T)(0.5 * m2[1])), q_l0((T)(0.25 * lam[0])), q_l1((T)(0.25 * lam[1])), h_g2((T)(0.5 * g))
-    {
-    }
-};
 
 // Kick of one own-row vector of a plane.  S*[f] point at row (r+1) of the centre
 // (Sc), lower (Szm) and upper (Szp) planes of field f; rows r and r+2 of the

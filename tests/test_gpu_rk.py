@@ -1,0 +1,88 @@
+"""GPU parity of the low-storage Runge-Kutta stages (RK3-3, RK4-5) against the oracle.
+
+Tolerances as for the leapfrog path: 1e-10 relative L2 in FP64, 1e-4 in FP32.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cl():
+    from paper_2607_24978_gb300 import build_ext, cl as clmod
+    build_ext.build()
+    clmod.lib()
+    return clmod
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def run_pair(cl, N, nf, prec, integ, scheme, nsteps, dt=0.01, graph=1, seed=31, expansion=True):
+    L = 0.8 * N
+    pot = [0.6, 1.0, 0.3, 0.0, 2.5 if nf == 2 else 0.0]
+    if nf == 1:
+        pot[2] = 0.0
+    phi, pi = inputs.scalar_state(N, nf, seed=seed, fbar=(0.9, 0.1), amp=0.05, pamp=0.05)
+    m = O.make_model(N, L, nf=nf, alpha=0.5, kappa=0.4, expansion=expansion, m2=(pot[0], pot[2]),
+                     lam=(pot[1], pot[3]), g2=pot[4])
+    st = O.State(phi.copy(), pi.copy(), np.array([1.0, 0.0, 0.0]))
+    if expansion:
+        st.abt[1] = math.sqrt(0.4 * O.energies(m, st)["rho"] / 3.0)  # a = 1, alpha-time
+    dtype = np.float64 if prec == 0 else np.float32
+    with cl.Lattice(N, L, nf, prec, integ, expansion=expansion, alpha=0.5, kappa=0.4, dt=dt) as g:
+        g.cl_set_potential(cl.CL_POT_POLY, pot)
+        g.cl_set_option(cl.CL_OPT_GRAPH, graph)
+        for f in range(nf):
+            g.cl_set_state(cl.CL_FIELD_PHI0 + f, st.phi[f].astype(dtype))
+            g.cl_set_state(cl.CL_FIELD_PI0 + f, st.pi[f].astype(dtype))
+        g.cl_set_scalars(st.abt[0], st.abt[1], 0.0)
+        g.cl_step(nsteps)
+        gphi = np.stack([g.cl_get_state(cl.CL_FIELD_PHI0 + f) for f in range(nf)])
+        gpi = np.stack([g.cl_get_state(cl.CL_FIELD_PI0 + f) for f in range(nf)])
+        e = g.cl_energies()
+        launches = g.cl_last_launch_count()
+    O.step(m, st, scheme, dt, nsteps)
+    return gphi, gpi, e, st, O.energies(m, st), launches
+
+
+@pytest.mark.parametrize("integ,scheme,stages", [(2, O.RK3_3, 3), (3, O.RK4_5, 5)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4), (2, 1e-4)])
+def test_rk_parity(cl, integ, scheme, stages, prec, tol):
+    gphi, gpi, e, st, eo, launches = run_pair(cl, 16, 2, prec, integ, scheme, 30)
+    assert rel_l2(gphi, st.phi) < tol
+    assert rel_l2(gpi, st.pi) < tol
+    assert e["a"] == pytest.approx(st.abt[0], rel=tol)
+    assert e["adot"] == pytest.approx(st.abt[1], rel=tol)
+    assert e["t"] == pytest.approx(st.abt[2], rel=1e-12)
+    assert e["rho"] == pytest.approx(eo["rho"], rel=max(tol, 1e-9))
+    assert e["step"] == 30
+    assert launches == 30 * stages  # no opening pass for Runge-Kutta
+
+
+@pytest.mark.parametrize("N", [7, 10, 24])
+def test_rk_ragged_sizes(cl, N):
+    gphi, gpi, e, st, eo, _ = run_pair(cl, N, 2, 0, cl.CL_INT_RK4_5, O.RK4_5, 12)
+    assert rel_l2(gphi, st.phi) < 1e-12
+    assert rel_l2(gpi, st.pi) < 1e-12
+
+
+def test_rk_graph_equals_plain(cl):
+    a = run_pair(cl, 16, 1, 1, cl.CL_INT_RK3_3, O.RK3_3, 11, graph=1)
+    b = run_pair(cl, 16, 1, 1, cl.CL_INT_RK3_3, O.RK3_3, 11, graph=0)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_rk_without_expansion(cl):
+    gphi, gpi, e, st, eo, _ = run_pair(cl, 12, 1, 0, cl.CL_INT_RK4_5, O.RK4_5, 20, expansion=False)
+    assert rel_l2(gphi, st.phi) < 1e-12
+    assert e["a"] == 1.0
