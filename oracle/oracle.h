@@ -87,7 +87,10 @@ double orc_addot(const orc_model* m, double a, double rho, double p);
 void orc_step(const orc_model* m, int scheme, double h, int nsteps,
               double* phi, double* pi, double* links, double* efield, double* abt);
 
-/* ---- U(1) + axion diagnostics ---- */
+/* ---- U(1) + axion: right-hand side of the coupled system and the Gauss charge ---- */
+void orc_u1_rhs(const orc_model* m, const double* phi, const double* pi, const double* links,
+                const double* efield, const double* abt,
+                double* dphi, double* dpi, double* dlinks, double* defield);
 void orc_u1_gauss(const orc_model* m, const double* phi, const double* links,
                   const double* efield, double a, double* out_gauss /* N^3 */);
 

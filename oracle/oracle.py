@@ -46,6 +46,7 @@ def lib():
         L.orc_addot.argtypes = [mp, C.c_double, C.c_double, C.c_double]
         L.orc_step.argtypes = [mp, C.c_int, C.c_double, C.c_int, dp, dp, C.c_void_p, C.c_void_p, dp]
         L.orc_u1_gauss.argtypes = [mp, dp, dp, dp, C.c_double, dp]
+        L.orc_u1_rhs.argtypes = [mp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
         L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
         L.orc_dft3.argtypes = [C.c_int, C.c_int, dp, dp]
         L.orc_vacuum.argtypes = [mp, C.c_uint64, C.c_uint32, C.c_double, C.c_double, dp, dp, C.c_double,
@@ -182,3 +183,11 @@ def spectrum(N, L, f, dn=1.0, type_=1):
     c = np.zeros(cap)
     nb = lib().orc_spectrum(int(N), float(L), _c(f), float(dn), int(type_), k, d, c, cap)
     return k[:nb], d[:nb], c[:nb]
+
+
+def u1_rhs(model, st):
+    """Right-hand side (dphi, dpi, dtheta, dE) of the axion-U(1) system at st (a, a' fixed)."""
+    N = model.N
+    out = [np.zeros((1, N, N, N)), np.zeros((1, N, N, N)), np.zeros((3, N, N, N)), np.zeros((3, N, N, N))]
+    lib().orc_u1_rhs(C.byref(model), _c(st.phi), _c(st.pi), _c(st.links), _c(st.efield), _c(st.abt), *out)
+    return out

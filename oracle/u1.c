@@ -1,8 +1,32 @@
 /*
  * FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY (see oracle.h).
  *
- * Compact U(1) gauge links with the axion coupling (section "ALP-gauge
- * interactions", Eq. AxionInfEOM).  Placeholder until that sector is written.
+ * Axion coupled to compact U(1) links (section "ALP-gauge interactions",
+ * Eq. AxionInfEOM: phi'' gains +(alpha_L/(a^3 m_p)) E.B, E' gains
+ * -(alpha_L/(a m_p)) (phi' B - grad phi x E); the Gauss law becomes
+ * div E = -(alpha_L/(a m_p)) grad phi . B), recast in alpha-time and solved with the
+ * low-storage Runge-Kutta schemes, as that section prescribes.
+ *
+ * The paper gives only continuum equations; the lattice equations here are the
+ * Euler-Lagrange equations of the lattice Lagrangian (program units, one site):
+ *   L = 1/2 a^(3-alpha) phi'^2 - 1/2 a^(1+alpha) sum_i (grad+_i phi)^2 - a^(3+alpha) V(phi)
+ *     + ws2 [ 1/2 a^(1-alpha) sum_i E_i^2 - a^(alpha-1) sum_{i<j} (1 - cos theta_ij)/dx^4
+ *             + g phi Ebar . Bbar ]
+ * with link angles theta_i(n) = dx A_i on n -> n+i, E_i = A_i' on the same link,
+ * plaquettes theta_ij(n) = theta_i(n) + theta_j(n+i) - theta_i(n+j) - theta_j(n),
+ * Ebar_i(n) = (E_i(n) + E_i(n-i))/2 (two-link average), Bbar_i(n) the average of
+ * sin theta_jk/dx^2 over the four plaquettes of the (j,k) plane around n ((i,j,k)
+ * cyclic, the "clover"), g = alpha_L sqrt(kappa) (kappa = (f_star/m_p)^2) and
+ * ws2 = (omega_star/f_star)^2.  Its equations of motion:
+ *   pi'  = a^(1+alpha) Lap phi - a^(3+alpha) V' + ws2 g Ebar.Bbar
+ *   d/deta [a^(1-alpha) E_i + g W_i] = -a^(alpha-1) Mag_i + g C_i
+ *     W_i(n)   = (phi(n) Bbar_i(n) + phi(n+i) Bbar_i(n+i))/2
+ *     Mag_i    = dx d/dtheta_i sum (1 - cos theta_P)/dx^4
+ *     C_i      = dx d/dtheta_i sum_m phi(m) Ebar(m).Bbar(m)
+ * Gauge invariance makes G(n) = div- [a^(1-alpha) E + g W] a conserved charge of the
+ * continuous-time flow (the lattice Gauss law), and the Chern-Simons term drops out
+ * of the energy.  All derivatives below are taken literally: every plaquette's
+ * derivative is scattered onto its four links.
  */
 #include "oracle.h"
 
@@ -10,16 +34,195 @@
 #include <stdlib.h>
 #include <string.h>
 
-double orc_u1_magnetic_sum(int N, const double* links) { (void)N; (void)links; return 0.0; }
-
-void orc_u1_rk_step(const orc_model* m, int scheme, double h,
-                    double* phi, double* pi, double* links, double* efield, double* abt)
+static int64_t shift(int N, int64_t n, int d, int s)
 {
-    (void)m; (void)scheme; (void)h; (void)phi; (void)pi; (void)links; (void)efield; (void)abt;
+    int c[3];
+    c[0] = (int)(n % N);
+    c[1] = (int)((n / N) % N);
+    c[2] = (int)(n / ((int64_t)N * N));
+    c[d] = ((c[d] + s) % N + N) % N;
+    return ((int64_t)c[2] * N + c[1]) * N + c[0];
 }
 
-void orc_u1_gauss(const orc_model* m, const double* phi, const double* links,
-                  const double* efield, double a, double* out_gauss)
+/* theta_ij(n) = theta_i(n) + theta_j(n+i) - theta_i(n+j) - theta_j(n) */
+static double plaq(int N, const double* th, int64_t n, int i, int j)
 {
-    (void)m; (void)phi; (void)links; (void)efield; (void)a; (void)out_gauss;
+    const int64_t V = (int64_t)N * N * N;
+    return th[i * V + n] + th[j * V + shift(N, n, i, 1)] - th[i * V + shift(N, n, j, 1)] - th[j * V + n];
+}
+
+/* Link rate of a plaquette: d theta_ij(n)/d eta = dx (E_i(n) + E_j(n+i) - E_i(n+j) - E_j(n)) */
+static double plaq_rate(int N, double dx, const double* E, int64_t n, int i, int j)
+{
+    const int64_t V = (int64_t)N * N * N;
+    return dx * (E[i * V + n] + E[j * V + shift(N, n, i, 1)] - E[i * V + shift(N, n, j, 1)] - E[j * V + n]);
+}
+
+/* Add c * d theta_ij(q)/d theta_l to every link l of the plaquette (i, j) at q. */
+static void scatter_plaq(int N, double* F, int64_t q, int i, int j, double c)
+{
+    const int64_t V = (int64_t)N * N * N;
+    F[i * V + q] += c;
+    F[j * V + shift(N, q, i, 1)] += c;
+    F[i * V + shift(N, q, j, 1)] -= c;
+    F[j * V + q] -= c;
+}
+
+double orc_u1_magnetic_sum(int N, const double* th)
+{
+    const int64_t V = (int64_t)N * N * N;
+    double s = 0.0;
+    for (int64_t n = 0; n < V; ++n)
+        for (int i = 0; i < 3; ++i)
+            for (int j = i + 1; j < 3; ++j) s += 1.0 - cos(plaq(N, th, n, i, j));
+    return s;
+}
+
+/* Clover-averaged Bbar_k(m) and its rate, and the two-link Ebar_k(m). */
+static void clover_fields(int N, double dx, const double* th, const double* E, double* Bbar, double* Bdot,
+                          double* Ebar)
+{
+    const int64_t V = (int64_t)N * N * N;
+    for (int64_t m = 0; m < V; ++m)
+        for (int k = 0; k < 3; ++k) {
+            const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+            const int64_t q[4] = {m, shift(N, m, k1, -1), shift(N, m, k2, -1), shift(N, shift(N, m, k1, -1), k2, -1)};
+            double b = 0.0, bd = 0.0;
+            for (int c = 0; c < 4; ++c) {
+                const double p = plaq(N, th, q[c], k1, k2);
+                b += sin(p);
+                if (Bdot) bd += cos(p) * plaq_rate(N, dx, E, q[c], k1, k2);
+            }
+            Bbar[k * V + m] = b / (4.0 * dx * dx);
+            if (Bdot) Bdot[k * V + m] = bd / (4.0 * dx * dx);
+            Ebar[k * V + m] = 0.5 * (E[k * V + m] + E[k * V + shift(N, m, k, -1)]);
+        }
+}
+
+/* Right-hand side of the coupled system at fixed (a, a'). */
+static void u1_rhs(const orc_model* m, const double* phi, const double* pi, const double* th, const double* E,
+                   double a, double b, double* dphi, double* dpi, double* dth, double* dE)
+{
+    const int N = m->N;
+    const int64_t V = (int64_t)N * N * N;
+    const double dx = m->L / N, al = m->alpha;
+    const double g = m->alphaL * sqrt(m->kappa);
+    double* Bbar = malloc(sizeof(double) * 3 * V);
+    double* Bdot = malloc(sizeof(double) * 3 * V);
+    double* Ebar = malloc(sizeof(double) * 3 * V);
+    double* Mag = calloc((size_t)(3 * V), sizeof(double));
+    double* Ccs = calloc((size_t)(3 * V), sizeof(double));
+    clover_fields(N, dx, th, E, Bbar, Bdot, Ebar);
+
+    /* scalar: phi' = a^(alpha-3) pi;  pi' = a^(1+alpha) Lap phi - a^(3+alpha) V' + ws2 g Ebar.Bbar */
+    orc_kick_force(m, 0, phi, a, dpi);
+    for (int64_t n = 0; n < V; ++n) {
+        dphi[n] = pow(a, al - 3.0) * pi[n];
+        double eb = 0.0;
+        for (int k = 0; k < 3; ++k) eb += Ebar[k * V + n] * Bbar[k * V + n];
+        dpi[n] += m->ws2 * g * eb;
+    }
+    /* links: theta_i' = dx E_i */
+    for (int64_t l = 0; l < 3 * V; ++l) dth[l] = dx * E[l];
+
+    /* magnetic force: Mag_l = sum_P sin theta_P d theta_P/d theta_l / dx^3 */
+    for (int64_t q = 0; q < V; ++q)
+        for (int i = 0; i < 3; ++i)
+            for (int j = i + 1; j < 3; ++j) scatter_plaq(N, Mag, q, i, j, sin(plaq(N, th, q, i, j)) / (dx * dx * dx));
+
+    /* Chern-Simons force: C_l = dx d/d theta_l sum_m phi(m) sum_k Ebar_k(m) Bbar_k(m) */
+    for (int64_t mm = 0; mm < V; ++mm)
+        for (int k = 0; k < 3; ++k) {
+            const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+            const double coef = dx * phi[mm] * Ebar[k * V + mm] / (4.0 * dx * dx);
+            const int64_t q[4] = {mm, shift(N, mm, k1, -1), shift(N, mm, k2, -1),
+                                  shift(N, shift(N, mm, k1, -1), k2, -1)};
+            for (int c = 0; c < 4; ++c) scatter_plaq(N, Ccs, q[c], k1, k2, coef * cos(plaq(N, th, q[c], k1, k2)));
+        }
+
+    /* E_i' = a^(alpha-1) [ -a^(alpha-1) Mag_i + g (C_i - W_i') ] - (1 - alpha) (a'/a) E_i */
+    for (int i = 0; i < 3; ++i)
+        for (int64_t n = 0; n < V; ++n) {
+            const int64_t np = shift(N, n, i, 1);
+            const double Wdot = 0.5 * (dphi[n] * Bbar[i * V + n] + phi[n] * Bdot[i * V + n] +
+                                       dphi[np] * Bbar[i * V + np] + phi[np] * Bdot[i * V + np]);
+            const int64_t l = i * V + n;
+            dE[l] = pow(a, al - 1.0) * (-pow(a, al - 1.0) * Mag[l] + g * (Ccs[l] - Wdot)) - (1.0 - al) * (b / a) * E[l];
+        }
+    free(Bbar); free(Bdot); free(Ebar); free(Mag); free(Ccs);
+}
+
+void orc_u1_rhs(const orc_model* m, const double* phi, const double* pi, const double* links, const double* efield,
+                const double* abt, double* dphi, double* dpi, double* dlinks, double* defield)
+{
+    /* without expansion a is frozen, so its rate a' is zero */
+    u1_rhs(m, phi, pi, links, efield, abt[0], m->expansion ? abt[1] : 0.0, dphi, dpi, dlinks, defield);
+}
+
+/* Lattice Gauss charge G(n) = sum_i [(a^(1-alpha) E_i + g W_i)(n) - (same)(n - i)] / dx. */
+void orc_u1_gauss(const orc_model* m, const double* phi, const double* links, const double* efield, double a,
+                  double* out)
+{
+    const int N = m->N;
+    const int64_t V = (int64_t)N * N * N;
+    const double dx = m->L / N;
+    const double g = m->alphaL * sqrt(m->kappa);
+    double* Bbar = malloc(sizeof(double) * 3 * V);
+    double* Ebar = malloc(sizeof(double) * 3 * V);
+    double* P = malloc(sizeof(double) * 3 * V);
+    clover_fields(N, dx, links, efield, Bbar, NULL, Ebar);
+    for (int i = 0; i < 3; ++i)
+        for (int64_t n = 0; n < V; ++n) {
+            const int64_t np = shift(N, n, i, 1);
+            const double W = 0.5 * (phi[n] * Bbar[i * V + n] + phi[np] * Bbar[i * V + np]);
+            P[i * V + n] = pow(a, 1.0 - m->alpha) * efield[i * V + n] + g * W;
+        }
+    for (int64_t n = 0; n < V; ++n) {
+        double s = 0.0;
+        for (int i = 0; i < 3; ++i) s += P[i * V + n] - P[i * V + shift(N, n, i, -1)];
+        out[n] = s / dx;
+    }
+    free(Bbar); free(Ebar); free(P);
+}
+
+/* One 2N Runge-Kutta step of y = (phi, pi, theta, E, a, a'). */
+int orc_rk_coeffs(int scheme, const double** A, const double** B);
+
+void orc_u1_rk_step(const orc_model* m, int scheme, double h, double* phi, double* pi, double* links,
+                    double* efield, double* abt)
+{
+    const int N = m->N;
+    const int64_t V = (int64_t)N * N * N;
+    const double *A, *B;
+    const int S = orc_rk_coeffs(scheme, &A, &B);
+    const int64_t nd = 8 * V;  /* phi, pi, 3 links, 3 electric */
+    double* k = calloc((size_t)nd, sizeof(double));
+    double* F = malloc(sizeof(double) * (size_t)nd);
+    double ka = 0.0, kb = 0.0;
+    for (int s = 0; s < S; ++s) {
+        const double a = abt[0], b = m->expansion ? abt[1] : 0.0;
+        double Fa = 0.0, Fb = 0.0;
+        if (m->expansion) {
+            double e[ORC_NE];
+            orc_energies(m, phi, pi, links, efield, abt, e);
+            Fa = b;
+            Fb = orc_addot(m, a, e[ORC_E_RHO], e[ORC_E_P]);
+        }
+        u1_rhs(m, phi, pi, links, efield, a, b, F, F + V, F + 2 * V, F + 5 * V);
+        double* y[4] = {phi, pi, links, efield};
+        const int64_t off[4] = {0, V, 2 * V, 5 * V};
+        const int64_t len[4] = {V, V, 3 * V, 3 * V};
+        for (int p = 0; p < 4; ++p)
+            for (int64_t n = 0; n < len[p]; ++n) {
+                k[off[p] + n] = A[s] * k[off[p] + n] + h * F[off[p] + n];
+                y[p][n] += B[s] * k[off[p] + n];
+            }
+        ka = A[s] * ka + h * Fa;
+        kb = A[s] * kb + h * Fb;
+        abt[0] += B[s] * ka;
+        abt[1] += B[s] * kb;
+    }
+    abt[2] += h;
+    free(k);
+    free(F);
 }
