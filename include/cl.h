@@ -187,6 +187,20 @@ cl_status cl_energies(cl_lattice* l, cl_energy* out, int32_t count);
 cl_status cl_spectrum(cl_lattice* l, int32_t member, int32_t field, double dn, int32_t type,
                       double* k_out, double* delta_out, double* count_out, int32_t cap, int32_t* nbins);
 
+/* Axion-U(1) couplings (gauge = CL_GAUGE_U1_AXION; section "ALP-gauge interactions",
+ * Eq. AxionInfEOM): alphaL is the dimensionless coupling alpha_Lambda of the
+ * alpha_Lambda/(4 m_p) phi F Ftilde term, ws2 = (omega_star/f_star)^2 the weight of the
+ * electromagnetic energy in the scalar's energy unit.  In program units the axion equation
+ * gains ws2 g Ebar.Bbar and the electric field -g (phi' Bbar - grad phi x Ebar) with
+ * g = alphaL sqrt(kappa).  On the lattice: link angles theta_i = dx A_i and E_i = A_i' on the
+ * links n -> n+i (fields CL_FIELD_THETA1..3, CL_FIELD_E1..3, zero at creation),
+ * Ebar the two-link average and Bbar the clover average of sin(plaquette)/dx^2; the equations
+ * are the Euler-Lagrange equations of the lattice action, so the lattice Gauss law is a
+ * conserved charge of the continuous-time flow.  Gauge lattices integrate with
+ * CL_INT_RK3_3 / CL_INT_RK4_5 (as the paper does for this module), one axion field,
+ * CL_PREC_FP64 or CL_PREC_FP32.  Errors: CL_EINVAL (no gauge field, bad values). */
+cl_status cl_set_gauge_coupling(cl_lattice* l, double alphaL, double ws2);
+
 /* When limit > 0, a Hubble violation above it sets the device status CL_ECONSTRAINT
  * (reported by the next synchronising call).  limit <= 0 disables the check (default). */
 cl_status cl_set_hubble_limit(cl_lattice* l, double limit);

@@ -28,7 +28,7 @@ CL_OPT_GRAPH, CL_OPT_TILE_BY, CL_OPT_TILE_DZ, CL_OPT_STAGES = 0, 1, 2, 3
 # Every exported entry point of include/cl.h.
 EXPORTS = ["cl_init_lattice", "cl_free", "cl_set_potential", "cl_set_state", "cl_get_state", "cl_set_scalars",
            "cl_get_scalars", "cl_init_vacuum", "cl_step", "cl_sync", "cl_energies", "cl_spectrum",
-           "cl_set_hubble_limit", "cl_set_option", "cl_last_launch_count", "cl_strerror", "cl_last_error",
+           "cl_set_gauge_coupling", "cl_set_hubble_limit", "cl_set_option", "cl_last_launch_count", "cl_strerror", "cl_last_error",
            "cl_fused_pass_noalloc"]
 
 
@@ -100,6 +100,7 @@ def lib():
         L.cl_energies.argtypes = [C.c_void_p, P(cl_energy), C.c_int32]
         L.cl_spectrum.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_int32, P(C.c_double),
                                   P(C.c_double), P(C.c_double), C.c_int32, P(C.c_int32)]
+        L.cl_set_gauge_coupling.argtypes = [C.c_void_p, C.c_double, C.c_double]
         L.cl_set_hubble_limit.argtypes = [C.c_void_p, C.c_double]
         L.cl_set_option.argtypes = [C.c_void_p, C.c_int32, C.c_int64]
         L.cl_last_launch_count.argtypes = [C.c_void_p]
@@ -232,6 +233,9 @@ class Lattice:
                                          k.ctypes.data_as(dp), d.ctypes.data_as(dp), c.ctypes.data_as(dp), n,
                                          C.byref(nb)))
         return k, d, c
+
+    def cl_set_gauge_coupling(self, alphaL, ws2):
+        _check(self.h, lib().cl_set_gauge_coupling(self.h, float(alphaL), float(ws2)))
 
     def cl_set_hubble_limit(self, limit):
         _check(self.h, lib().cl_set_hubble_limit(self.h, float(limit)))

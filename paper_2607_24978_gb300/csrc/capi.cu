@@ -44,6 +44,12 @@ struct cl_lattice {
     void* kphi[2][2] = {};  // Runge-Kutta auxiliaries (RK integrators only)
     void* kpi[2][2] = {};
     int rk_BY = 1, rk_DZ = 1, rk_nby = 1, rk_nbz = 1;
+    bool gauge = false;       // axion + compact U(1) links (one scalar field, Runge-Kutta)
+    void* th[3][2] = {};      // link angles theta_i
+    void* ef[3][2] = {};      // electric fields E_i
+    void* ku1[8][2] = {};     // Runge-Kutta auxiliaries of phi, pi, theta_1..3, E_1..3
+    void* u1s[9] = {};        // per-site scratch: Bbar_1..3, their rates, phi Ebar_1..3
+    double alphaL = 0.0, ws2 = 0.0;
     int cur = 0;
     DevScal* scal = nullptr;
     double* partials = nullptr;
@@ -177,6 +183,7 @@ cl_status choose_tiles(cl_lattice* l)
         l->rk_nbz = (N + l->rk_DZ - 1) / l->rk_DZ;
         if (l->rk_nby * l->rk_nbz > nblocks) nblocks = l->rk_nby * l->rk_nbz;
     }
+    if (l->gauge && u1_grid_blocks(N) > nblocks) nblocks = u1_grid_blocks(N);
     if (nblocks > l->partials_cap) {
         if (l->partials) cudaFree(l->partials);
         l->partials = nullptr;
@@ -274,8 +281,11 @@ cl_status run_rk_stage_t(cl_lattice* l, const PassCoef& pc, int in, int out)
     return CL_OK;
 }
 
+cl_status run_u1(cl_lattice* l, int what, double cA, double cB, int flags, int in, int out);
+
 cl_status run_pass(cl_lattice* l, const PassCoef& pc, int in, int out)
 {
+    if (pc.rk == 2) return run_u1(l, 1, pc.A, pc.B, pc.flags, in, out);  // axion + U(1) stage
     if (pc.rk) return is_fp64(l) ? run_rk_stage_t<double>(l, pc, in, out) : run_rk_stage_t<float>(l, pc, in, out);
     return run_pass_impl(l, pc, in, out, nullptr);
 }
@@ -320,7 +330,7 @@ std::vector<PassCoef> step_schedule(const cl_lattice* l)
         rk_tables(l->p.integrator, A, B);
         for (size_t i = 0; i < A.size(); ++i) {
             PassCoef pc{0.0, 0.0, 0.0, (i == 0 ? P_FIRST_STAGE : 0) | (i + 1 == A.size() ? P_COUNT_STEP : 0)};
-            pc.rk = 1;
+            pc.rk = l->gauge ? 2 : 1;
             pc.A = A[i];
             pc.B = B[i];
             s.push_back(pc);
@@ -372,9 +382,62 @@ cl_status close_leapfrog(cl_lattice* l, bool commit)
     return CL_OK;
 }
 
+template <typename T>
+void u1_fill(cl_lattice* l, U1Args<T>& A, int in, int out)
+{
+    A.phi_in = (const T*)l->phi[0][in];
+    A.pi_in = (const T*)l->pi[0][in];
+    A.phi_out = (T*)l->phi[0][out];
+    A.pi_out = (T*)l->pi[0][out];
+    for (int i = 0; i < 3; ++i) {
+        A.th_in[i] = (const T*)l->th[i][in];
+        A.E_in[i] = (const T*)l->ef[i][in];
+        A.th_out[i] = (T*)l->th[i][out];
+        A.E_out[i] = (T*)l->ef[i][out];
+        A.Bbar[i] = (T*)l->u1s[i];
+        A.Bdot[i] = (T*)l->u1s[3 + i];
+        A.X[i] = (T*)l->u1s[6 + i];
+    }
+    for (int q = 0; q < 8; ++q) {
+        A.k_in[q] = (const T*)l->ku1[q][in];
+        A.k_out[q] = (T*)l->ku1[q][out];
+    }
+    A.scal = l->scal;
+    A.partials = l->partials;
+    A.N = l->N;
+    A.dx = l->dx; A.alpha = l->p.alpha; A.kappa = l->p.kappa;
+    A.g = l->alphaL * sqrt(l->p.kappa);
+    A.ws2 = l->ws2;
+    A.m2 = l->m2[0]; A.lam = l->lam[0];
+    A.h = l->p.dt;
+    A.hubble_limit = l->hubble_limit;
+}
+
+// U(1) launches on buffer `in` (-> `out`): what = 1 stage (or energies), 2 Gauss diagnostic.
+template <typename T>
+cl_status run_u1_t(cl_lattice* l, int what, double cA, double cB, int flags, int in, int out)
+{
+    U1Args<T> A{};
+    u1_fill(l, A, in, out);
+    A.A = cA;
+    A.B = cB;
+    A.flags = flags | (l->p.expansion ? P_EXPANSION : 0);
+    cudaError_t e = launch_u1(l->p.precision, &A, 0, l->stream);  // helper fields first
+    if (e == cudaSuccess) e = launch_u1(l->p.precision, &A, what, l->stream);
+    if (e != cudaSuccess) return fail(l, CL_ECUDA, "U(1) launch failed: %s", cudaGetErrorString(e));
+    return CL_OK;
+}
+
+cl_status run_u1(cl_lattice* l, int what, double cA, double cB, int flags, int in, int out)
+{
+    return is_fp64(l) ? run_u1_t<double>(l, what, cA, cB, flags, in, out)
+                      : run_u1_t<float>(l, what, cA, cB, flags, in, out);
+}
+
 cl_status energy_pass(cl_lattice* l, int extra_flags)
 {
-    cl_status s = run_pass(l, {0.0, 0.0, 0.0, extra_flags}, l->cur, l->cur ^ 1);
+    cl_status s = l->gauge ? run_u1(l, 1, 0.0, 0.0, P_ENERGY_ONLY | (extra_flags & P_HUBBLE_INIT), l->cur, l->cur ^ 1)
+                           : run_pass(l, {0.0, 0.0, 0.0, extra_flags}, l->cur, l->cur ^ 1);
     if (s != CL_OK) return s;
     l->diag_valid = true;
     return CL_OK;
@@ -394,17 +457,36 @@ cl_status read_status(cl_lattice* l, DevScal* host)
     return CL_OK;
 }
 
-int field_kind(int field, int nf, int* f)
+// 0 = scalar field f, 1 = its momentum, 2 = link angle theta_f, 3 = electric field E_f.
+int field_kind(const cl_lattice* l, int field, int* f)
 {
     if (field == CL_FIELD_PHI0 || field == CL_FIELD_PHI1) {
         *f = field - CL_FIELD_PHI0;
-        return *f < nf ? 0 : -1;
+        return *f < l->nf ? 0 : -1;
     }
     if (field == CL_FIELD_PI0 || field == CL_FIELD_PI1) {
         *f = field - CL_FIELD_PI0;
-        return *f < nf ? 1 : -1;
+        return *f < l->nf ? 1 : -1;
+    }
+    if (l->gauge && field >= CL_FIELD_THETA1 && field <= CL_FIELD_THETA3) {
+        *f = field - CL_FIELD_THETA1;
+        return 2;
+    }
+    if (l->gauge && field >= CL_FIELD_E1 && field <= CL_FIELD_E3) {
+        *f = field - CL_FIELD_E1;
+        return 3;
     }
     return -1;
+}
+
+void* field_buffer(cl_lattice* l, int kind, int f, int buf)
+{
+    switch (kind) {
+    case 0: return l->phi[f][buf];
+    case 1: return l->pi[f][buf];
+    case 2: return l->th[f][buf];
+    default: return l->ef[f][buf];
+    }
 }
 
 }  // namespace
@@ -444,6 +526,16 @@ void cl_free(cl_lattice* l)
             if (l->kphi[f][b]) cudaFree(l->kphi[f][b]);
             if (l->kpi[f][b]) cudaFree(l->kpi[f][b]);
         }
+    for (int b = 0; b < 2; ++b) {
+        for (int i = 0; i < 3; ++i) {
+            if (l->th[i][b]) cudaFree(l->th[i][b]);
+            if (l->ef[i][b]) cudaFree(l->ef[i][b]);
+        }
+        for (int q = 0; q < 8; ++q)
+            if (l->ku1[q][b]) cudaFree(l->ku1[q][b]);
+    }
+    for (int q = 0; q < 9; ++q)
+        if (l->u1s[q]) cudaFree(l->u1s[q]);
     if (l->scal) cudaFree(l->scal);
     if (l->partials) cudaFree(l->partials);
     if (l->own_stream && l->stream) cudaStreamDestroy(l->stream);
@@ -460,7 +552,12 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
         p->integrator < 0 || p->integrator > 3 || p->gauge < 0 || p->gauge > 1 || !(p->L > 0) || !(p->dt > 0) ||
         !(p->a0 > 0) || p->reserved != 0)
         return CL_EINVAL;
-    if (p->gauge != CL_GAUGE_NONE) return CL_EUNSUPPORTED;
+    if (p->gauge == CL_GAUGE_U1_AXION) {
+        // the paper integrates the axion-gauge module with Runge-Kutta; one axion field;
+        // fields stored in FP64 or plain FP32
+        if (p->nfields != 1) return CL_EINVAL;
+        if (!is_rk(p->integrator) || p->precision == CL_PREC_FP32_KAHAN) return CL_EUNSUPPORTED;
+    }
     cl_lattice* l = new (std::nothrow) cl_lattice();
     if (!l) return CL_ENOMEM;
     l->p = *p;
@@ -495,6 +592,25 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
             cudaMemsetAsync(l->pi[f][b], 0, bytes, l->stream);
             if (has_kahan(l)) cudaMemsetAsync(l->cc[f][b], 0, bytes, l->stream);
         }
+    if (p->gauge == CL_GAUGE_U1_AXION) {
+        l->gauge = true;
+        bool ok = true;
+        for (int b = 0; b < 2 && ok; ++b) {
+            for (int i = 0; i < 3 && ok; ++i) {
+                ok = cudaMalloc(&l->th[i][b], bytes) == cudaSuccess && cudaMalloc(&l->ef[i][b], bytes) == cudaSuccess;
+                if (ok) {
+                    cudaMemsetAsync(l->th[i][b], 0, bytes, l->stream);
+                    cudaMemsetAsync(l->ef[i][b], 0, bytes, l->stream);
+                }
+            }
+            for (int q = 0; q < 8 && ok; ++q) ok = cudaMalloc(&l->ku1[q][b], bytes) == cudaSuccess;
+        }
+        for (int q = 0; q < 9 && ok; ++q) ok = cudaMalloc(&l->u1s[q], bytes) == cudaSuccess;
+        if (!ok) {
+            cl_free(l);
+            return CL_ENOMEM;
+        }
+    }
     if (cudaMalloc(&l->scal, sizeof(DevScal)) != cudaSuccess) {
         cl_free(l);
         return CL_ENOMEM;
@@ -560,12 +676,12 @@ cl_status cl_set_state(cl_lattice* l, int32_t member, int32_t field, const void*
     if (member != 0 && member != -1) return fail(l, CL_EINVAL, "member %d out of range", member);
     if (!src) return fail(l, CL_EINVAL, "src is NULL");
     int f = 0;
-    const int kind = field_kind(field, l->nf, &f);
+    const int kind = field_kind(l, field, &f);
     if (kind < 0) return fail(l, CL_EINVAL, "field %d not present", field);
     cl_status s = close_leapfrog(l, true);
     if (s != CL_OK) return s;
     const size_t bytes = (size_t)l->V * l->es;
-    void* dst = kind == 0 ? l->phi[f][l->cur] : l->pi[f][l->cur];
+    void* dst = field_buffer(l, kind, f, l->cur);
     CUDA_TRY(l, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                 l->stream));
     if (kind == 0 && has_kahan(l)) CUDA_TRY(l, cudaMemsetAsync(l->cc[f][l->cur], 0, bytes, l->stream));
@@ -580,7 +696,7 @@ cl_status cl_get_state(cl_lattice* l, int32_t member, int32_t field, void* dst, 
     if (member != 0) return fail(l, CL_EINVAL, "member %d out of range", member);
     if (!dst) return fail(l, CL_EINVAL, "dst is NULL");
     int f = 0;
-    const int kind = field_kind(field, l->nf, &f);
+    const int kind = field_kind(l, field, &f);
     if (kind < 0) return fail(l, CL_EINVAL, "field %d not present", field);
     int buf = l->cur;
     if (l->open && kind == 1) {
@@ -589,7 +705,7 @@ cl_status cl_get_state(cl_lattice* l, int32_t member, int32_t field, void* dst, 
         buf = l->cur ^ 1;
     }
     const size_t bytes = (size_t)l->V * l->es;
-    const void* srcp = kind == 0 ? l->phi[f][buf] : l->pi[f][buf];
+    const void* srcp = field_buffer(l, kind, f, buf);
     CUDA_TRY(l, cudaMemcpyAsync(dst, srcp, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                 l->stream));
     DevScal h;
@@ -633,6 +749,18 @@ cl_status cl_get_scalars(cl_lattice* l, int32_t member, double* a, double* adot,
     if (a) *a = h.diag[D_A];
     if (adot) *adot = h.diag[D_ADOT];
     if (t) *t = h.diag[D_T];
+    return CL_OK;
+}
+
+cl_status cl_set_gauge_coupling(cl_lattice* l, double alphaL, double ws2)
+{
+    if (!l) return CL_EINVAL;
+    if (!l->gauge) return fail(l, CL_EINVAL, "the lattice has no gauge field");
+    if (!isfinite(alphaL) || !isfinite(ws2) || ws2 < 0) return fail(l, CL_EINVAL, "bad gauge coupling");
+    l->alphaL = alphaL;
+    l->ws2 = ws2;
+    l->diag_valid = false;
+    invalidate_graphs(l);
     return CL_OK;
 }
 
@@ -709,7 +837,7 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
                 l->cur ^= 1;
             }
         }
-        l->last_launches += pps;
+        l->last_launches += l->gauge ? 2 * pps : pps;  // gauge stages: helper + stage kernel
     }
     // a leapfrog step ends with the energies of its integer time; a Runge-Kutta stage
     // reports those of the state it started from, so they are recomputed on demand
@@ -730,6 +858,10 @@ cl_status cl_energies(cl_lattice* l, cl_energy* out, int32_t count)
     if (!out || count < 1 || count > 1) return fail(l, CL_EINVAL, "energies: bad output or count");
     if (!l->diag_valid) {
         cl_status s = energy_pass(l, 0);
+        if (s != CL_OK) return s;
+    }
+    if (l->gauge) {  // lattice Gauss charge of the current state
+        cl_status s = run_u1(l, 2, 0.0, 0.0, 0, l->cur, l->cur ^ 1);
         if (s != CL_OK) return s;
     }
     DevScal h;
@@ -822,7 +954,7 @@ cl_status cl_spectrum(cl_lattice* l, int32_t member, int32_t field, double dn, i
     if (!(dn > 0) || (type != 1 && type != 2) || cap < 0 || (cap > 0 && (!k_out || !delta_out || !count_out)))
         return fail(l, CL_EINVAL, "spectrum: bad arguments");
     int f = 0;
-    const int kind = field_kind(field, l->nf, &f);
+    const int kind = field_kind(l, field, &f);
     if (kind < 0) return fail(l, CL_EINVAL, "field %d not present", field);
     const int N = l->N;
     const int nb = (int)floor(sqrt(3.0) * (N / 2) / dn + 0.5) + 1;

@@ -37,6 +37,7 @@ enum : int {
     P_HUBBLE_INIT = 8,  // set a' from Eq. Friedmann2 with this pass's energies first
     P_COUNT_STEP = 16,  // this pass ends a time step
     P_FIRST_STAGE = 32, // Runge-Kutta: first stage of a step (A = 0, k is not read)
+    P_ENERGY_ONLY = 64, // reduce the energies of the state, update nothing else
 };
 
 // Largest dynamic shared memory a fused-pass block may use (227 KB per block on sm_103a,
@@ -100,6 +101,35 @@ struct RkStageArgs {
     int flags;          // P_EXPANSION, P_FIRST_STAGE, P_COUNT_STEP
 };
 cudaError_t launch_rk_stage(int precision, int nf, const void* args, int vw, cudaStream_t s);
+
+// Axion + compact U(1) links, one 2N Runge-Kutta stage (u1_stage.cu).  Degrees of
+// freedom per site, in k order: phi, pi, theta_1..3, E_1..3.
+template <typename T>
+struct U1Args {
+    const T* phi_in;
+    const T* pi_in;
+    const T* th_in[3];
+    const T* E_in[3];
+    const T* k_in[8];
+    T* phi_out;
+    T* pi_out;
+    T* th_out[3];
+    T* E_out[3];
+    T* k_out[8];
+    T* Bbar[3];   // per-site scratch written by the helper launch
+    T* Bdot[3];
+    T* X[3];      // phi Ebar_k
+    DevScal* scal;
+    double* partials;
+    int N;
+    double dx, alpha, kappa, g, ws2, m2, lam;
+    double A, B, h;
+    double hubble_limit;
+    int flags;    // P_EXPANSION, P_FIRST_STAGE, P_COUNT_STEP, P_ENERGY_ONLY, P_HUBBLE_INIT
+};
+// what: 0 = helper fields, 1 = stage (or energies with P_ENERGY_ONLY), 2 = Gauss diagnostic
+cudaError_t launch_u1(int precision, const void* args, int what, cudaStream_t s);
+int u1_grid_blocks(int N);
 
 // Vacuum initial conditions: fills the half spectrum (kx in [0, N/2]) of delta f and
 // delta pi for one field into two complex-double buffers of N*N*(N/2+1) entries.

@@ -1,0 +1,245 @@
+"""GPU parity of the axion-U(1) Runge-Kutta stages against the oracle.
+
+Section "ALP-gauge interactions", Eq. AxionInfEOM, integrated with the low-storage
+RK3-3 / RK4-5 schemes.  Tolerances: 1e-10 relative L2 in FP64, 1e-4 in FP32, for the
+axion, its momentum, the link angles and the electric fields; the Gauss diagnostic is
+compared with the oracle's lattice Gauss charge.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+KAPPA, ALPHAL, WS2, M2, LAM = 0.7, 2.0, 0.6, 0.8, 0.3
+
+
+@pytest.fixture(scope="module")
+def cl():
+    from paper_2607_24978_gb300 import build_ext, cl as clmod
+    build_ext.build()
+    clmod.lib()
+    return clmod
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def random_state(model, seed, th_amp=0.3, e_amp=0.3):
+    st = O.new_state(model)
+    g = inputs.rng(seed)
+    st.phi[:] = 0.8 + 0.2 * g.standard_normal(st.phi.shape)
+    st.pi[:] = 0.2 * g.standard_normal(st.pi.shape)
+    st.links, st.efield = inputs.gauge_state(model.N, seed=seed + 1, theta_amp=th_amp, e_amp=e_amp)
+    return st
+
+
+def up(f, d):
+    """f(n + e_d) for direction d (d = 0 is the fastest index)."""
+    return np.roll(f, -1, axis=2 - d)
+
+
+def down(f, d):
+    return np.roll(f, 1, axis=2 - d)
+
+
+def clover_B(th, dx):
+    """Clover average of sin(plaquette) / dx^2 in the plane normal to each direction."""
+    out = np.zeros_like(th)
+    for k in range(3):
+        i, j = (k + 1) % 3, (k + 2) % 3
+        s = np.sin(th[i] + up(th[j], i) - up(th[i], j) - th[j])
+        out[k] = (s + down(s, i) + down(s, j) + down(down(s, i), j)) / (4 * dx * dx)
+    return out
+
+
+def gauss_scale(model, st, g):
+    """max_n sum_i (|P_i(n)| + |P_i(n - i)|) / dx with P = a^(1-alpha) E + g W."""
+    dx = model.L / model.N
+    B = clover_B(st.links, dx)
+    phi = st.phi[0]
+    sc = np.zeros_like(phi)
+    for i in range(3):
+        P = st.abt[0] ** (1 - model.alpha) * st.efield[i] + g * 0.5 * (phi * B[i] + up(phi * B[i], i))
+        sc += np.abs(P) + np.abs(down(P, i))
+    return float(sc.max() / dx)
+
+
+def run_pair(cl, N, prec, integ, scheme, nsteps, dt=0.01, alpha=0.0, expansion=True, alphaL=ALPHAL, graph=1,
+             seed=5, L=None):
+    L = 0.75 * N if L is None else L
+    m = O.make_model(N, L, nf=1, alpha=alpha, kappa=KAPPA, expansion=expansion, gauge=1, alphaL=alphaL, ws2=WS2,
+                     m2=(M2, 0.0), lam=(LAM, 0.0))
+    st = random_state(m, seed)
+    st.abt[:] = (1.0, 0.0, 0.0)
+    if expansion:
+        st.abt[1] = math.sqrt(KAPPA * O.energies(m, st)["rho"] / 3.0)  # a = 1
+    st0 = st.copy()
+    dtype = np.float64 if prec == 0 else np.float32
+    with cl.Lattice(N, L, 1, prec, integ, gauge=cl.CL_GAUGE_U1_AXION, expansion=expansion, alpha=alpha,
+                    kappa=KAPPA, dt=dt) as g:
+        g.cl_set_potential(cl.CL_POT_POLY, [M2, LAM, 0.0, 0.0, 0.0])
+        g.cl_set_gauge_coupling(alphaL, WS2)
+        g.cl_set_option(cl.CL_OPT_GRAPH, graph)
+        g.cl_set_state(cl.CL_FIELD_PHI0, st.phi[0].astype(dtype))
+        g.cl_set_state(cl.CL_FIELD_PI0, st.pi[0].astype(dtype))
+        for i in range(3):
+            g.cl_set_state(cl.CL_FIELD_THETA1 + i, st.links[i].astype(dtype))
+            g.cl_set_state(cl.CL_FIELD_E1 + i, st.efield[i].astype(dtype))
+        g.cl_set_scalars(st.abt[0], st.abt[1], 0.0)
+        e0 = g.cl_energies()
+        g.cl_step(nsteps)
+        launches = g.cl_last_launch_count()
+        out = {
+            "phi": g.cl_get_state(cl.CL_FIELD_PHI0),
+            "pi": g.cl_get_state(cl.CL_FIELD_PI0),
+            "th": np.stack([g.cl_get_state(cl.CL_FIELD_THETA1 + i) for i in range(3)]),
+            "E": np.stack([g.cl_get_state(cl.CL_FIELD_E1 + i) for i in range(3)]),
+        }
+        e = g.cl_energies()
+    O.step(m, st, scheme, dt, nsteps)
+    return out, e0, e, st0, st, m, launches
+
+
+CASES = [(2, O.RK3_3, 3), (3, O.RK4_5, 5)]
+
+
+@pytest.mark.parametrize("integ,scheme,stages", CASES)
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-4)])
+@pytest.mark.parametrize("alpha", [0.0, 1.0])
+def test_u1_parity(cl, integ, scheme, stages, prec, tol, alpha):
+    out, e0, e, st0, st, m, launches = run_pair(cl, 8, prec, integ, scheme, 20, alpha=alpha)
+    assert rel_l2(out["phi"], st.phi[0]) < tol
+    assert rel_l2(out["pi"], st.pi[0]) < tol
+    assert rel_l2(out["th"], st.links) < tol
+    assert rel_l2(out["E"], st.efield) < tol
+    eo = O.energies(m, st)
+    assert e["a"] == pytest.approx(st.abt[0], rel=tol)
+    assert e["adot"] == pytest.approx(st.abt[1], rel=tol)
+    assert e["t"] == pytest.approx(st.abt[2], rel=1e-12)
+    for k_gpu, k_orc in [("KE", "KEM"), ("GB", "GEM"), ("rho", "rho"), ("p", "p"), ("V", "V"), ("K0", "K0"),
+                         ("G0", "G0")]:
+        assert e[k_gpu] == pytest.approx(eo[k_orc], rel=max(tol, 1e-9), abs=1e-14), k_gpu
+    assert e["step"] == 20
+    assert launches == 20 * stages * 2  # helper fields + stage kernel
+
+
+@pytest.mark.parametrize("N", [5, 7, 12])
+def test_u1_ragged_sizes(cl, N):
+    out, *_, st, m, _ = run_pair(cl, N, 0, cl.CL_INT_RK4_5, O.RK4_5, 6, alpha=0.5)
+    assert rel_l2(out["phi"], st.phi[0]) < 1e-12
+    assert rel_l2(out["pi"], st.pi[0]) < 1e-12
+    assert rel_l2(out["th"], st.links) < 1e-12
+    assert rel_l2(out["E"], st.efield) < 1e-12
+
+
+def test_u1_frozen_background(cl):
+    """Without expansion a and a' stay at their initial values (no Hubble friction)."""
+    out, e0, e, st0, st, m, _ = run_pair(cl, 8, 0, cl.CL_INT_RK3_3, O.RK3_3, 10, expansion=False)
+    assert rel_l2(out["E"], st.efield) < 1e-10
+    assert e["a"] == 1.0 and e["adot"] == 0.0
+
+
+def test_u1_graph_equals_plain(cl):
+    a = run_pair(cl, 8, 2, cl.CL_INT_RK4_5, O.RK4_5, 7, graph=1)[0]
+    b = run_pair(cl, 8, 2, cl.CL_INT_RK4_5, O.RK4_5, 7, graph=0)[0]
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_u1_energies_of_initial_state(cl):
+    out, e0, e, st0, st, m, _ = run_pair(cl, 8, 0, cl.CL_INT_RK3_3, O.RK3_3, 1, alpha=1.0)
+    eo = O.energies(m, st0)
+    assert e0["KE"] == pytest.approx(eo["KEM"], rel=1e-12)
+    assert e0["GB"] == pytest.approx(eo["GEM"], rel=1e-12)
+    assert e0["rho"] == pytest.approx(eo["rho"], rel=1e-12)
+    assert e0["hubble_violation"] == pytest.approx(eo["hubble_violation"], abs=1e-12)
+
+
+@pytest.mark.parametrize("alphaL", [0.0, ALPHAL])
+def test_u1_gauss_diagnostic_matches_oracle(cl, alphaL):
+    """cl_energies reports max|G| / max sum|P| of the current state; compare with the
+    oracle's Gauss charge of the same state (random links and fields: G is O(1))."""
+    out, e0, e, st0, st, m, _ = run_pair(cl, 8, 0, cl.CL_INT_RK3_3, O.RK3_3, 4, alphaL=alphaL, alpha=0.5)
+    g = alphaL * math.sqrt(KAPPA)
+    for est, s in [(e0, st0), (e, st)]:
+        ref = np.abs(O.u1_gauss(m, s)).max() / gauss_scale(m, s, g)
+        assert est["gauss_violation"] == pytest.approx(ref, rel=1e-8)
+
+
+def test_u1_gauss_conserved(cl):
+    """A divergence-free electric field with the coupling off: the lattice Gauss law holds to
+    roundoff through Runge-Kutta (each stage adds a divergence-free increment)."""
+    N, L = 8, 6.0
+    m = O.make_model(N, L, nf=1, alpha=0.0, kappa=KAPPA, expansion=True, gauge=1, alphaL=0.0, ws2=WS2,
+                     m2=(M2, 0.0), lam=(LAM, 0.0))
+    st = random_state(m, 11)
+    # E = backward curl of a random vector field: div- E = 0 identically
+    v = inputs.rng(12).standard_normal((3, N, N, N)) * 0.3
+    dx = L / N
+    st.efield = np.stack([((v[(i + 2) % 3] - down(v[(i + 2) % 3], (i + 1) % 3))
+                           - (v[(i + 1) % 3] - down(v[(i + 1) % 3], (i + 2) % 3))) / dx for i in range(3)])
+    assert np.abs(O.u1_gauss(m, st)).max() < 1e-12
+    with cl.Lattice(N, L, 1, cl.CL_PREC_FP64, cl.CL_INT_RK4_5, gauge=cl.CL_GAUGE_U1_AXION, alpha=0.0,
+                    kappa=KAPPA, dt=0.01) as g:
+        g.cl_set_potential(cl.CL_POT_POLY, [M2, LAM, 0.0, 0.0, 0.0])
+        g.cl_set_gauge_coupling(0.0, WS2)
+        g.cl_set_state(cl.CL_FIELD_PHI0, st.phi[0])
+        g.cl_set_state(cl.CL_FIELD_PI0, st.pi[0])
+        for i in range(3):
+            g.cl_set_state(cl.CL_FIELD_THETA1 + i, st.links[i])
+            g.cl_set_state(cl.CL_FIELD_E1 + i, st.efield[i])
+        g.cl_set_scalars(1.0)  # a' from Eq. Friedmann2 with the electromagnetic energy
+        assert g.cl_energies()["gauss_violation"] < 1e-14
+        g.cl_step(40)
+        e = g.cl_energies()
+        assert e["gauss_violation"] < 1e-13
+        assert e["hubble_violation"] < 1e-3
+
+
+def test_u1_hubble_init_includes_em_energy(cl):
+    """cl_set_scalars(a, NaN) solves Eq. Friedmann2 with rho including E^2 and B^2."""
+    N, L = 8, 6.0
+    m = O.make_model(N, L, nf=1, alpha=1.0, kappa=KAPPA, expansion=True, gauge=1, alphaL=ALPHAL, ws2=WS2,
+                     m2=(M2, 0.0), lam=(LAM, 0.0))
+    st = random_state(m, 21)
+    st.abt[:] = (1.2, 0.0, 0.0)
+    rho = O.energies(m, st)["rho"]
+    with cl.Lattice(N, L, 1, cl.CL_PREC_FP64, cl.CL_INT_RK3_3, gauge=cl.CL_GAUGE_U1_AXION, alpha=1.0,
+                    kappa=KAPPA, dt=0.01) as g:
+        g.cl_set_potential(cl.CL_POT_POLY, [M2, LAM, 0.0, 0.0, 0.0])
+        g.cl_set_gauge_coupling(ALPHAL, WS2)
+        g.cl_set_state(cl.CL_FIELD_PHI0, st.phi[0])
+        g.cl_set_state(cl.CL_FIELD_PI0, st.pi[0])
+        for i in range(3):
+            g.cl_set_state(cl.CL_FIELD_THETA1 + i, st.links[i])
+            g.cl_set_state(cl.CL_FIELD_E1 + i, st.efield[i])
+        g.cl_set_scalars(1.2)
+        e = g.cl_energies()
+    assert e["rho"] == pytest.approx(rho, rel=1e-12)
+    assert e["adot"] == pytest.approx(1.2 ** 2 * math.sqrt(KAPPA * rho / 3.0), rel=1e-12)
+    assert e["hubble_violation"] < 1e-12
+
+
+def test_u1_invalid_configurations(cl):
+    with pytest.raises(cl.CLError):
+        cl.Lattice(8, 6.0, 1, cl.CL_PREC_FP64, cl.CL_INT_VV2, gauge=cl.CL_GAUGE_U1_AXION)
+    with pytest.raises(cl.CLError):
+        cl.Lattice(8, 6.0, 2, cl.CL_PREC_FP64, cl.CL_INT_RK3_3, gauge=cl.CL_GAUGE_U1_AXION)
+    with pytest.raises(cl.CLError):
+        cl.Lattice(8, 6.0, 1, cl.CL_PREC_FP32_KAHAN, cl.CL_INT_RK3_3, gauge=cl.CL_GAUGE_U1_AXION)
+    with cl.Lattice(8, 6.0, 1, cl.CL_PREC_FP64, cl.CL_INT_RK3_3) as g:
+        with pytest.raises(cl.CLError):
+            g.cl_set_gauge_coupling(1.0, 1.0)
+        with pytest.raises(cl.CLError):
+            g.cl_set_state(cl.CL_FIELD_THETA1, np.zeros((8, 8, 8)))
+    with cl.Lattice(8, 6.0, 1, cl.CL_PREC_FP64, cl.CL_INT_RK3_3, gauge=cl.CL_GAUGE_U1_AXION) as g:
+        with pytest.raises(cl.CLError):
+            g.cl_set_gauge_coupling(1.0, -1.0)
