@@ -87,6 +87,13 @@ enum {
     CL_FIELD_E1 = 7, CL_FIELD_E2 = 8, CL_FIELD_E3 = 9             /* electric field A_i' on the same links */
 };
 
+/* Batched ensembles (members > 1): B independent lattices of sizes member_N[m]
+ * (2..512 each) and boxes member_L[m], each with its own couplings, a, a', t and step
+ * count, advanced together by one launch per pass (N and L are then ignored).  They share
+ * nfields, precision, integrator (CL_INT_VV2 or CL_INT_YOSHIDA4), alpha, kappa and dt;
+ * gauge must be CL_GAUGE_NONE.  Every call that takes a member addresses one of them; the
+ * fields of member m hold member_N[m]^3 elements.  Errors at creation: CL_EINVAL (sizes),
+ * CL_EUNSUPPORTED (Runge-Kutta or gauge ensembles). */
 typedef struct {
     int32_t N;            /* sites per side, 2 <= N <= 1536 (single lattice)                */
     int32_t nfields;      /* scalar fields, 1 or 2 (1 when gauge = CL_GAUGE_U1_AXION)       */
@@ -94,7 +101,7 @@ typedef struct {
     int32_t integrator;   /* CL_INT_*                                                       */
     int32_t gauge;        /* CL_GAUGE_*                                                     */
     int32_t expansion;    /* 1: self-consistent expansion (Eq. Friedmann1); 0: a, a' frozen */
-    int32_t members;      /* ensemble size B; 0 or 1 = single lattice                       */
+    int32_t members;      /* ensemble size B; 0 or 1 = single lattice (see below)           */
     int32_t reserved;     /* must be 0                                                      */
     const int32_t* member_N; /* B per-member sizes (copied) when members > 1, else NULL     */
     const double* member_L;  /* B per-member box sides (copied), or NULL = L for all        */
@@ -140,12 +147,14 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p);
 /* Release every resource of the handle (waits for its queued work).  NULL is ignored. */
 void cl_free(cl_lattice* l);
 
-/* Set the potential (kind = CL_POT_*).  params holds nparams values per member; for an
- * ensemble, either one set (shared) or members sets back to back.  Errors: CL_EINVAL. */
+/* Set the potential (kind = CL_POT_*).  params holds the kind's values (LPHI4 {lam},
+ * M2 {m2}, M2_G2 {m2, g2}, LPHI4_G2 {lam, g2}, POLY {m2_0, lam_0, m2_1, lam_1, g2});
+ * for an ensemble either one set shared by every member or members sets back to back.
+ * Errors: CL_EINVAL (count, kind, non-finite value, two-field terms on one field). */
 cl_status cl_set_potential(cl_lattice* l, int32_t kind, const double* params, int32_t nparams);
 
-/* Copy one field of one member in (set) or out (get).  src/dst hold N^3 elements of the
- * lattice's element type, in host memory (on_device = 0) or device memory (on_device = 1).
+/* Copy one field of one member in (set) or out (get).  src/dst hold N^3 elements (the
+ * member's N for an ensemble; member -1 = 0 for a single lattice) of the lattice's element type, in host memory (on_device = 0) or device memory (on_device = 1).
  * cl_set_state leaves the handle at an integer time: the next cl_step first opens the
  * leapfrog with a half kick.  cl_get_state returns the values at the most recent
  * integer time (momenta are synchronised on the fly; the evolving state is not altered).
@@ -173,8 +182,9 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps);
 /* Wait for the handle's queued work; report device-side failures (CL_ENAN, CL_ECONSTRAINT). */
 cl_status cl_sync(cl_lattice* l);
 
-/* Copy the energies of `count` members (starting at member 0) to host memory `out`.
- * Synchronising.  Errors: CL_EINVAL, CL_ECUDA, CL_ENAN, CL_ECONSTRAINT. */
+/* Copy the energies of `count` members (starting at member 0; 1 <= count <= members, or
+ * count = 1 for a single lattice) to host memory `out`.
+ * Synchronising.  Errors: CL_EINVAL, CL_ECUDA, CL_ENAN, CL_ECONSTRAINT, CL_ETIMEOUT. */
 cl_status cl_energies(cl_lattice* l, cl_energy* out, int32_t count);
 
 /* Binned spectrum of one field (section "Arbitrary binning and unbinned spectra",

@@ -148,20 +148,35 @@ class Lattice:
     """Owns one cl_lattice handle.  Methods mirror the C calls."""
 
     def __init__(self, N, L, nfields=1, precision=CL_PREC_FP64, integrator=CL_INT_VV2, gauge=CL_GAUGE_NONE,
-                 expansion=True, alpha=1.0, kappa=0.1, dt=0.01, a0=1.0, stream=None):
+                 expansion=True, alpha=1.0, kappa=0.1, dt=0.01, a0=1.0, stream=None, member_N=None, member_L=None):
+        """A single N^3 lattice, or (member_N = list of sizes) a batched ensemble whose
+        member m has member_N[m]^3 sites and box side member_L[m] (default L)."""
         p = cl_lattice_params()
         p.N, p.nfields, p.precision, p.integrator = int(N), int(nfields), int(precision), int(integrator)
         p.gauge, p.expansion, p.members, p.reserved = int(gauge), int(bool(expansion)), 0, 0
         p.L, p.alpha, p.kappa, p.dt, p.a0 = float(L), float(alpha), float(kappa), float(dt), float(a0)
         p.stream = C.c_void_p(int(stream)) if stream else None
+        keep = []
+        if member_N is not None:
+            mn = (C.c_int32 * len(member_N))(*[int(x) for x in member_N])
+            keep.append(mn)
+            p.members = len(member_N)
+            p.member_N = C.cast(mn, C.POINTER(C.c_int32))
+            if member_L is not None:
+                ml = (C.c_double * len(member_L))(*[float(x) for x in member_L])
+                keep.append(ml)
+                p.member_L = C.cast(ml, C.POINTER(C.c_double))
         h = C.c_void_p()
         s = lib().cl_init_lattice(C.byref(h), C.byref(p))
         if s != CL_OK:
             raise CLError(s, "cl_init_lattice")
         self.h = h
-        self.N, self.nfields, self.precision = int(N), int(nfields), int(precision)
+        self.nfields, self.precision = int(nfields), int(precision)
+        self.member_N = [int(x) for x in member_N] if member_N is not None else [int(N)]
+        self.members = len(self.member_N)
+        self.N = int(N) if member_N is None else max(self.member_N)
         self.dtype = np.float64 if precision == CL_PREC_FP64 else np.float32
-        self.n = self.N ** 3
+        self.n = self.member_N[0] ** 3
 
     def close(self):
         if getattr(self, "h", None):
@@ -184,15 +199,20 @@ class Lattice:
         arr = (C.c_double * len(params))(*[float(x) for x in params])
         _check(self.h, lib().cl_set_potential(self.h, int(kind), arr, len(params)))
 
+    def _sites(self, member):
+        # sites of a member; an out-of-range member is left for the library to reject
+        return self.member_N[member if 0 <= member < self.members else 0] ** 3
+
     def cl_set_state(self, field, data, member=0):
-        ptr, dev, keep = _buffer(data, self.dtype, self.n)
+        ptr, dev, keep = _buffer(data, self.dtype, self._sites(member))
         _check(self.h, lib().cl_set_state(self.h, int(member), int(field), ptr, dev))
 
     def cl_get_state(self, field, out=None, member=0):
         """Return the field at the latest integer time (numpy), or fill `out` (tensor or array)."""
+        n = round(self._sites(member) ** (1.0 / 3.0))
         if out is None:
-            out = np.empty((self.N, self.N, self.N), dtype=self.dtype)
-        ptr, dev, keep = _buffer(out, self.dtype, self.n)
+            out = np.empty((n, n, n), dtype=self.dtype)
+        ptr, dev, keep = _buffer(out, self.dtype, n ** 3)
         _check(self.h, lib().cl_get_state(self.h, int(member), int(field), ptr, dev))
         return out
 
@@ -218,10 +238,12 @@ class Lattice:
     def cl_sync(self):
         _check(self.h, lib().cl_sync(self.h))
 
-    def cl_energies(self):
-        e = cl_energy()
-        _check(self.h, lib().cl_energies(self.h, C.byref(e), 1))
-        return e.as_dict()
+    def cl_energies(self, count=None):
+        """Energies of member 0 (a dict), or of members 0..count-1 (a list of dicts)."""
+        n = 1 if count is None else int(count)
+        e = (cl_energy * n)()
+        _check(self.h, lib().cl_energies(self.h, e, n))
+        return e[0].as_dict() if count is None else [x.as_dict() for x in e]
 
     def cl_spectrum(self, field, dn=1.0, type_=1, member=0):
         nb = C.c_int32()

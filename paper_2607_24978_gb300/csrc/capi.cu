@@ -17,6 +17,8 @@ using namespace clk;
 namespace {
 
 constexpr int kMaxN = 1536;
+constexpr int kMaxMembers = 1 << 16;  // ensemble members per handle
+constexpr int kEnsMaxN = 512;         // sites per side of one ensemble member
 
 // One pass of a kick-drift scheme in staggered form (see scalar_pass.cu):
 // drift by d, energies with pi + e F, kick by k.
@@ -63,6 +65,18 @@ struct cl_lattice {
     int opt_BY = 0, opt_DZ = 0, opt_stages = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t last_launches = 0;
+    // batched ensemble (members > 1): per-member sizes, boxes, arena offsets and couplings
+    int members = 1;
+    std::vector<int> mN;
+    std::vector<double> mL;
+    std::vector<long long> moff;
+    std::vector<double> mpot;       // 5 per member: m2_0, lam_0, m2_1, lam_1, g2
+    std::vector<EnsMember> hmem;
+    std::vector<EnsItem> hitems;
+    EnsMember* d_members = nullptr;
+    EnsItem* d_items = nullptr;
+    int nitems = 0, ens_grid = 0;
+    size_t ens_smem = 0;
     char err[512] = {0};
 };
 
@@ -87,6 +101,16 @@ cl_status fail(cl_lattice* l, cl_status s, const char* fmt, ...)
 
 bool is_fp64(const cl_lattice* l) { return l->p.precision == CL_PREC_FP64; }
 bool has_kahan(const cl_lattice* l) { return l->p.precision == CL_PREC_FP32_KAHAN; }
+bool is_ens(const cl_lattice* l) { return l->members > 1; }
+int mem_N(const cl_lattice* l, int m) { return is_ens(l) ? l->mN[m] : l->N; }
+int64_t mem_V(const cl_lattice* l, int m)
+{
+    const int64_t n = mem_N(l, m);
+    return n * n * n;
+}
+size_t mem_off_bytes(const cl_lattice* l, int m) { return is_ens(l) ? (size_t)l->moff[m] * l->es : 0; }
+double mem_L(const cl_lattice* l, int m) { return is_ens(l) ? l->mL[m] : l->p.L; }
+bool member_ok(const cl_lattice* l, int m) { return m >= 0 && m < l->members; }
 
 void invalidate_graphs(cl_lattice* l)
 {
@@ -99,8 +123,96 @@ void invalidate_graphs(cl_lattice* l)
 
 cl_status query_blocks_per_sm(cl_lattice* l, int* per_sm);
 
+cl_status grow_partials(cl_lattice* l, int nblocks)
+{
+    if (nblocks > l->partials_cap) {
+        if (l->partials) cudaFree(l->partials);
+        l->partials = nullptr;
+        if (cudaMalloc(&l->partials, sizeof(double) * kMaxQ * (size_t)nblocks) != cudaSuccess)
+            return fail(l, CL_ENOMEM, "cannot allocate %d reduction partials", nblocks);
+        l->partials_cap = nblocks;
+    }
+    return CL_OK;
+}
+
+// Copy the per-member couplings into the descriptor table and upload it.
+cl_status upload_members(cl_lattice* l)
+{
+    for (int m = 0; m < l->members; ++m) {
+        EnsMember& M = l->hmem[m];
+        const double* q = &l->mpot[5 * (size_t)m];
+        M.m2[0] = q[0]; M.lam[0] = q[1]; M.m2[1] = q[2]; M.lam[1] = q[3]; M.g2 = q[4];
+    }
+    CUDA_TRY(l, cudaMemcpy(l->d_members, l->hmem.data(), sizeof(EnsMember) * l->hmem.size(), cudaMemcpyHostToDevice));
+    return CL_OK;
+}
+
+// Ensemble work items.  Per member: BY full rows (as many as one block's threads cover)
+// by DZ planes (about 16K sites per item unless CL_OPT_TILE_DZ fixes DZ), both balanced
+// within the member; the items of a member are consecutive.  The persistent grid is one
+// wave of resident blocks.
+cl_status ens_tiles(cl_lattice* l)
+{
+    const int B = l->members, prec = l->p.precision;
+    l->hmem.assign(B, EnsMember{});
+    l->hitems.clear();
+    size_t smem = 0;
+    for (int m = 0; m < B; ++m) {
+        const int N = l->mN[m], TX = N / l->VW;
+        int BY = kEnsThreads / TX;
+        if (l->opt_BY > 0 && l->opt_BY < BY) BY = l->opt_BY;
+        if (BY > N) BY = N;
+        if (BY < 1) BY = 1;
+        const int nby = (N + BY - 1) / BY;
+        BY = (N + nby - 1) / nby;
+        int DZ = l->opt_DZ > 0 ? l->opt_DZ : (int)(16384 / ((int64_t)BY * N));
+        if (DZ > N) DZ = N;
+        if (DZ < 1) DZ = 1;
+        const int nbz = (N + DZ - 1) / DZ;
+        DZ = (N + nbz - 1) / nbz;
+        EnsMember& M = l->hmem[m];
+        M.off = l->moff[m];
+        M.N = N;
+        M.BY = BY;
+        M.DZ = DZ;
+        M.item0 = (int)l->hitems.size();
+        M.nitems = nby * nbz;
+        M.dx = l->mL[m] / N;
+        if ((nby - 1) * BY >= N || (nbz - 1) * DZ >= N) return fail(l, CL_EINVAL, "ensemble tiling error");
+        for (int bz = 0; bz < nbz; ++bz)
+            for (int by = 0; by < nby; ++by) l->hitems.push_back({m, by * BY, bz * DZ, 0});
+        const size_t sm = (size_t)l->nf * 3 * (BY + 2) * N * l->es;
+        if (sm > smem) smem = sm;
+    }
+    if (smem > (size_t)kPassMaxSmem) return fail(l, CL_EINVAL, "ensemble member too large for the pass tiling");
+    l->nitems = (int)l->hitems.size();
+    l->ens_smem = smem;
+    if (l->d_items) cudaFree(l->d_items);
+    l->d_items = nullptr;
+    if (!l->d_members && cudaMalloc(&l->d_members, sizeof(EnsMember) * B) != cudaSuccess)
+        return fail(l, CL_ENOMEM, "cannot allocate the member table");
+    if (cudaMalloc(&l->d_items, sizeof(EnsItem) * l->hitems.size()) != cudaSuccess)
+        return fail(l, CL_ENOMEM, "cannot allocate the item table");
+    CUDA_TRY(l, cudaMemcpy(l->d_items, l->hitems.data(), sizeof(EnsItem) * l->hitems.size(), cudaMemcpyHostToDevice));
+    cl_status s = upload_members(l);
+    if (s != CL_OK) return s;
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        return fail(l, CL_ECUDA, "cannot query the SM count");
+    CUDA_TRY(l, ensemble_pass_blocks_per_sm(prec, l->nf, l->VW, smem, &per_sm));
+    if (per_sm < 1) return fail(l, CL_EINVAL, "ensemble pass does not fit on an SM");
+    const int64_t wave = (int64_t)per_sm * nsm;
+    l->ens_grid = (int)(wave < l->nitems ? wave : l->nitems);
+    s = grow_partials(l, l->nitems);
+    if (s != CL_OK) return s;
+    invalidate_graphs(l);
+    return CL_OK;
+}
+
 cl_status choose_tiles(cl_lattice* l)
 {
+    if (is_ens(l)) return ens_tiles(l);
     const int N = l->N, prec = l->p.precision;
     l->VW = scalar_pass_vector_width(prec, N);
     const int TX = N / l->VW;
@@ -184,13 +296,8 @@ cl_status choose_tiles(cl_lattice* l)
         if (l->rk_nby * l->rk_nbz > nblocks) nblocks = l->rk_nby * l->rk_nbz;
     }
     if (l->gauge && u1_grid_blocks(N) > nblocks) nblocks = u1_grid_blocks(N);
-    if (nblocks > l->partials_cap) {
-        if (l->partials) cudaFree(l->partials);
-        l->partials = nullptr;
-        if (cudaMalloc(&l->partials, sizeof(double) * kMaxQ * (size_t)nblocks) != cudaSuccess)
-            return fail(l, CL_ENOMEM, "cannot allocate %d reduction partials", nblocks);
-        l->partials_cap = nblocks;
-    }
+    s = grow_partials(l, nblocks);
+    if (s != CL_OK) return s;
     invalidate_graphs(l);
     return CL_OK;
 }
@@ -283,8 +390,44 @@ cl_status run_rk_stage_t(cl_lattice* l, const PassCoef& pc, int in, int out)
 
 cl_status run_u1(cl_lattice* l, int what, double cA, double cB, int flags, int in, int out);
 
+// One ensemble pass over the members [m0, m1) reading buffer `in` and writing `out`.
+template <typename T>
+cl_status run_ens_pass_t(cl_lattice* l, const PassCoef& pc, int in, int out, int m0, int m1)
+{
+    EnsPassArgs<T> A{};
+    for (int f = 0; f < l->nf; ++f) {
+        A.phi_in[f] = (const T*)l->phi[f][in];
+        A.pi_in[f] = (const T*)l->pi[f][in];
+        A.c_in[f] = (const T*)l->cc[f][in];
+        A.phi_out[f] = (T*)l->phi[f][out];
+        A.pi_out[f] = (T*)l->pi[f][out];
+        A.c_out[f] = (T*)l->cc[f][out];
+    }
+    A.members = l->d_members;
+    A.items = l->d_items;
+    A.scal = l->scal;
+    A.partials = l->partials;
+    A.item_begin = l->hmem[m0].item0;
+    A.item_end = l->hmem[m1 - 1].item0 + l->hmem[m1 - 1].nitems;
+    A.alpha = l->p.alpha; A.kappa = l->p.kappa;
+    A.d = pc.d; A.e = pc.e; A.k = pc.k;
+    A.hubble_limit = l->hubble_limit;
+    A.flags = pc.flags | (l->p.expansion ? P_EXPANSION : 0);
+    const int n = A.item_end - A.item_begin;
+    const int grid = n < l->ens_grid ? n : l->ens_grid;
+    cudaError_t e = launch_ensemble_pass(l->p.precision, l->nf, &A, l->VW, grid, l->ens_smem, l->stream);
+    if (e != cudaSuccess) return fail(l, CL_ECUDA, "ensemble pass launch failed: %s", cudaGetErrorString(e));
+    return CL_OK;
+}
+
+cl_status run_ens_pass(cl_lattice* l, const PassCoef& pc, int in, int out, int m0, int m1)
+{
+    return is_fp64(l) ? run_ens_pass_t<double>(l, pc, in, out, m0, m1) : run_ens_pass_t<float>(l, pc, in, out, m0, m1);
+}
+
 cl_status run_pass(cl_lattice* l, const PassCoef& pc, int in, int out)
 {
+    if (is_ens(l)) return run_ens_pass(l, pc, in, out, 0, l->members);
     if (pc.rk == 2) return run_u1(l, 1, pc.A, pc.B, pc.flags, in, out);  // axion + U(1) stage
     if (pc.rk) return is_fp64(l) ? run_rk_stage_t<double>(l, pc, in, out) : run_rk_stage_t<float>(l, pc, in, out);
     return run_pass_impl(l, pc, in, out, nullptr);
@@ -434,6 +577,12 @@ cl_status run_u1(cl_lattice* l, int what, double cA, double cB, int flags, int i
                       : run_u1_t<float>(l, what, cA, cB, flags, in, out);
 }
 
+// Energies of members [m0, m1) of an ensemble only (a' from Eq. Friedmann2 with P_HUBBLE_INIT).
+cl_status energy_pass_members(cl_lattice* l, int flags, int m0, int m1)
+{
+    return run_ens_pass(l, {0.0, 0.0, 0.0, flags}, l->cur, l->cur ^ 1, m0, m1);
+}
+
 cl_status energy_pass(cl_lattice* l, int extra_flags)
 {
     cl_status s = l->gauge ? run_u1(l, 1, 0.0, 0.0, P_ENERGY_ONLY | (extra_flags & P_HUBBLE_INIT), l->cur, l->cur ^ 1)
@@ -443,14 +592,22 @@ cl_status energy_pass(cl_lattice* l, int extra_flags)
     return CL_OK;
 }
 
-cl_status read_status(cl_lattice* l, DevScal* host)
+// Copy the scalar state of every member to `host`; report and clear the device status.
+cl_status read_status(cl_lattice* l, std::vector<DevScal>& host)
 {
-    CUDA_TRY(l, cudaMemcpyAsync(host, l->scal, sizeof(DevScal), cudaMemcpyDeviceToHost, l->stream));
+    host.resize(l->members);
+    CUDA_TRY(l, cudaMemcpyAsync(host.data(), l->scal, sizeof(DevScal) * host.size(), cudaMemcpyDeviceToHost,
+                                l->stream));
     CUDA_TRY(l, cudaStreamSynchronize(l->stream));
-    if (host->status) {
-        const int st = host->status;
-        CUDA_TRY(l, cudaMemsetAsync(&l->scal->status, 0, sizeof(int), l->stream));
+    int st = 0;
+    for (int m = 0; m < l->members; ++m)
+        if (host[m].status) {
+            st |= host[m].status;
+            CUDA_TRY(l, cudaMemsetAsync(&l->scal[m].status, 0, sizeof(int), l->stream));
+        }
+    if (st) {
         CUDA_TRY(l, cudaStreamSynchronize(l->stream));
+        if (st & ST_TIMEOUT) return fail(l, CL_ETIMEOUT, "a bounded device wait gave up (copy pipeline)");
         if (st & ST_NAN) return fail(l, CL_ENAN, "a volume-averaged energy became non-finite");
         if (st & ST_CONSTRAINT) return fail(l, CL_ECONSTRAINT, "Hubble-constraint violation above %g", l->hubble_limit);
     }
@@ -538,6 +695,8 @@ void cl_free(cl_lattice* l)
         if (l->u1s[q]) cudaFree(l->u1s[q]);
     if (l->scal) cudaFree(l->scal);
     if (l->partials) cudaFree(l->partials);
+    if (l->d_members) cudaFree(l->d_members);
+    if (l->d_items) cudaFree(l->d_items);
     if (l->own_stream && l->stream) cudaStreamDestroy(l->stream);
     delete l;
 }
@@ -547,8 +706,18 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
     if (!out) return CL_EINVAL;
     *out = nullptr;
     if (!p) return CL_EINVAL;
-    if (p->members > 1) return CL_EUNSUPPORTED;
-    if (p->N < 2 || p->N > kMaxN || p->nfields < 1 || p->nfields > 2 || p->precision < 0 || p->precision > 2 ||
+    const bool ens = p->members > 1;
+    if (ens) {
+        // batched ensemble of independent lattices: leapfrog schemes, scalar fields only
+        if (p->members > kMaxMembers || !p->member_N) return CL_EINVAL;
+        if (p->gauge != CL_GAUGE_NONE || is_rk(p->integrator)) return CL_EUNSUPPORTED;
+        for (int m = 0; m < p->members; ++m) {
+            if (p->member_N[m] < 2 || p->member_N[m] > kEnsMaxN) return CL_EINVAL;
+            if (p->member_L && !(p->member_L[m] > 0)) return CL_EINVAL;
+        }
+    }
+    if (p->members < 0) return CL_EINVAL;
+    if ((!ens && (p->N < 2 || p->N > kMaxN)) || p->nfields < 1 || p->nfields > 2 || p->precision < 0 || p->precision > 2 ||
         p->integrator < 0 || p->integrator > 3 || p->gauge < 0 || p->gauge > 1 || !(p->L > 0) || !(p->dt > 0) ||
         !(p->a0 > 0) || p->reserved != 0)
         return CL_EINVAL;
@@ -563,11 +732,42 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
     l->p = *p;
     l->p.member_N = nullptr;
     l->p.member_L = nullptr;
-    l->N = p->N;
     l->nf = p->nfields;
     l->es = p->precision == CL_PREC_FP64 ? 8 : 4;
-    l->V = (int64_t)p->N * p->N * p->N;
-    l->dx = p->L / p->N;
+    if (ens) {
+        // members back to back in every arena, each on a 256-byte boundary; one vector
+        // width for all members (the widest that divides every size)
+        const int B = p->members;
+        l->members = B;
+        l->mN.assign(p->member_N, p->member_N + B);
+        l->mL.resize(B);
+        l->moff.resize(B);
+        l->mpot.assign(5 * (size_t)B, 0.0);
+        const int64_t align = 256 / l->es;
+        int64_t off = 0;
+        int vw = p->precision == CL_PREC_FP64 ? 2 : 4, nmax = 0;
+        for (int m = 0; m < B; ++m) {
+            const int n = l->mN[m];
+            l->mL[m] = p->member_L ? p->member_L[m] : p->L;
+            l->moff[m] = off;
+            off += ((int64_t)n * n * n + align - 1) / align * align;
+            while (n % vw) vw /= 2;
+            if (n > nmax) nmax = n;
+        }
+        for (int m = 0; m < B; ++m)
+            if (l->mN[m] / vw > kEnsThreads) {
+                delete l;
+                return CL_EINVAL;
+            }
+        l->VW = vw;
+        l->N = nmax;
+        l->V = off;
+        l->dx = l->mL[0] / l->mN[0];
+    } else {
+        l->N = p->N;
+        l->V = (int64_t)p->N * p->N * p->N;
+        l->dx = p->L / p->N;
+    }
     if (p->stream) {
         l->stream = (cudaStream_t)p->stream;
     } else {
@@ -611,16 +811,17 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
             return CL_ENOMEM;
         }
     }
-    if (cudaMalloc(&l->scal, sizeof(DevScal)) != cudaSuccess) {
+    if (cudaMalloc(&l->scal, sizeof(DevScal) * l->members) != cudaSuccess) {
         cl_free(l);
         return CL_ENOMEM;
     }
-    DevScal h{};
-    h.a = p->a0;
-    cudaMemcpyAsync(l->scal, &h, sizeof(DevScal), cudaMemcpyHostToDevice, l->stream);
-    if (choose_tiles(l) != CL_OK) {
+    std::vector<DevScal> h(l->members, DevScal{});
+    for (auto& x : h) x.a = p->a0;
+    cudaMemcpyAsync(l->scal, h.data(), sizeof(DevScal) * h.size(), cudaMemcpyHostToDevice, l->stream);
+    const cl_status ts = choose_tiles(l);
+    if (ts != CL_OK) {
         cl_free(l);
-        return CL_ENOMEM;
+        return ts == CL_EINVAL ? CL_EINVAL : CL_ENOMEM;
     }
     if (cudaStreamSynchronize(l->stream) != cudaSuccess) {
         cl_free(l);
@@ -634,36 +835,39 @@ cl_status cl_set_potential(cl_lattice* l, int32_t kind, const double* params, in
 {
     if (!l) return CL_EINVAL;
     if (!params) return fail(l, CL_EINVAL, "params is NULL");
-    double m2[2] = {0, 0}, lam[2] = {0, 0}, g2 = 0;
+    int per = 0;  // values per member
     switch (kind) {
-    case CL_POT_LPHI4:
-        if (nparams != 1) return fail(l, CL_EINVAL, "LPHI4 takes {lam}");
-        lam[0] = params[0];
-        break;
-    case CL_POT_M2:
-        if (nparams != 1) return fail(l, CL_EINVAL, "M2 takes {m2}");
-        m2[0] = params[0];
-        break;
-    case CL_POT_M2_G2:
-        if (nparams != 2 || l->nf != 2) return fail(l, CL_EINVAL, "M2_G2 takes {m2, g2} and two fields");
-        m2[0] = params[0];
-        g2 = params[1];
-        break;
-    case CL_POT_LPHI4_G2:
-        if (nparams != 2 || l->nf != 2) return fail(l, CL_EINVAL, "LPHI4_G2 takes {lam, g2} and two fields");
-        lam[0] = params[0];
-        g2 = params[1];
-        break;
-    case CL_POT_POLY:
-        if (nparams != 5) return fail(l, CL_EINVAL, "POLY takes {m2_0, lam_0, m2_1, lam_1, g2}");
-        m2[0] = params[0]; lam[0] = params[1]; m2[1] = params[2]; lam[1] = params[3]; g2 = params[4];
-        break;
+    case CL_POT_LPHI4: case CL_POT_M2: per = 1; break;
+    case CL_POT_M2_G2: case CL_POT_LPHI4_G2: per = 2; break;
+    case CL_POT_POLY: per = 5; break;
     default: return fail(l, CL_EINVAL, "unknown potential kind %d", kind);
     }
-    if (l->nf == 1 && (m2[1] != 0 || lam[1] != 0 || g2 != 0))
-        return fail(l, CL_EINVAL, "second-field couplings on a one-field lattice");
-    for (int f = 0; f < 2; ++f) { l->m2[f] = m2[f]; l->lam[f] = lam[f]; }
-    l->g2 = g2;
+    if (nparams != per && !(is_ens(l) && nparams == per * l->members))
+        return fail(l, CL_EINVAL, "potential kind %d takes %d values (per member for an ensemble)", kind, per);
+    if ((kind == CL_POT_M2_G2 || kind == CL_POT_LPHI4_G2) && l->nf != 2)
+        return fail(l, CL_EINVAL, "this potential needs two fields");
+    std::vector<double> pot(5 * (size_t)l->members, 0.0);
+    for (int m = 0; m < l->members; ++m) {
+        const double* q = params + (nparams == per ? 0 : (size_t)per * m);
+        double* c = &pot[5 * (size_t)m];  // m2_0, lam_0, m2_1, lam_1, g2
+        switch (kind) {
+        case CL_POT_LPHI4: c[1] = q[0]; break;
+        case CL_POT_M2: c[0] = q[0]; break;
+        case CL_POT_M2_G2: c[0] = q[0]; c[4] = q[1]; break;
+        case CL_POT_LPHI4_G2: c[1] = q[0]; c[4] = q[1]; break;
+        default: for (int i = 0; i < 5; ++i) c[i] = q[i]; break;
+        }
+        for (int i = 0; i < 5; ++i)
+            if (!isfinite(c[i])) return fail(l, CL_EINVAL, "non-finite coupling");
+        if (l->nf == 1 && (c[2] != 0 || c[3] != 0 || c[4] != 0))
+            return fail(l, CL_EINVAL, "second-field couplings on a one-field lattice");
+    }
+    l->m2[0] = pot[0]; l->lam[0] = pot[1]; l->m2[1] = pot[2]; l->lam[1] = pot[3]; l->g2 = pot[4];
+    if (is_ens(l)) {
+        l->mpot = pot;
+        cl_status s = upload_members(l);
+        if (s != CL_OK) return s;
+    }
     l->potential_set = true;
     l->diag_valid = false;
     invalidate_graphs(l);
@@ -673,18 +877,19 @@ cl_status cl_set_potential(cl_lattice* l, int32_t kind, const double* params, in
 cl_status cl_set_state(cl_lattice* l, int32_t member, int32_t field, const void* src, int32_t on_device)
 {
     if (!l) return CL_EINVAL;
-    if (member != 0 && member != -1) return fail(l, CL_EINVAL, "member %d out of range", member);
+    if (!is_ens(l) && member == -1) member = 0;
+    if (!member_ok(l, member)) return fail(l, CL_EINVAL, "member %d out of range", member);
     if (!src) return fail(l, CL_EINVAL, "src is NULL");
     int f = 0;
     const int kind = field_kind(l, field, &f);
     if (kind < 0) return fail(l, CL_EINVAL, "field %d not present", field);
     cl_status s = close_leapfrog(l, true);
     if (s != CL_OK) return s;
-    const size_t bytes = (size_t)l->V * l->es;
-    void* dst = field_buffer(l, kind, f, l->cur);
+    const size_t bytes = (size_t)mem_V(l, member) * l->es, off = mem_off_bytes(l, member);
+    void* dst = (char*)field_buffer(l, kind, f, l->cur) + off;
     CUDA_TRY(l, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                 l->stream));
-    if (kind == 0 && has_kahan(l)) CUDA_TRY(l, cudaMemsetAsync(l->cc[f][l->cur], 0, bytes, l->stream));
+    if (kind == 0 && has_kahan(l)) CUDA_TRY(l, cudaMemsetAsync((char*)l->cc[f][l->cur] + off, 0, bytes, l->stream));
     if (!on_device) CUDA_TRY(l, cudaStreamSynchronize(l->stream));
     l->diag_valid = false;
     return CL_OK;
@@ -693,7 +898,7 @@ cl_status cl_set_state(cl_lattice* l, int32_t member, int32_t field, const void*
 cl_status cl_get_state(cl_lattice* l, int32_t member, int32_t field, void* dst, int32_t on_device)
 {
     if (!l) return CL_EINVAL;
-    if (member != 0) return fail(l, CL_EINVAL, "member %d out of range", member);
+    if (!member_ok(l, member)) return fail(l, CL_EINVAL, "member %d out of range", member);
     if (!dst) return fail(l, CL_EINVAL, "dst is NULL");
     int f = 0;
     const int kind = field_kind(l, field, &f);
@@ -704,38 +909,44 @@ cl_status cl_get_state(cl_lattice* l, int32_t member, int32_t field, void* dst, 
         if (s != CL_OK) return s;
         buf = l->cur ^ 1;
     }
-    const size_t bytes = (size_t)l->V * l->es;
-    const void* srcp = field_buffer(l, kind, f, buf);
+    const size_t bytes = (size_t)mem_V(l, member) * l->es;
+    const void* srcp = (const char*)field_buffer(l, kind, f, buf) + mem_off_bytes(l, member);
     CUDA_TRY(l, cudaMemcpyAsync(dst, srcp, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                 l->stream));
-    DevScal h;
-    return read_status(l, &h);
+    std::vector<DevScal> h;
+    return read_status(l, h);
 }
 
 cl_status cl_set_scalars(cl_lattice* l, int32_t member, double a, double adot, double t)
 {
     if (!l) return CL_EINVAL;
-    if (member != 0 && member != -1) return fail(l, CL_EINVAL, "member %d out of range", member);
-    if (!(a > 0)) return fail(l, CL_EINVAL, "a must be positive");
+    if (member != -1 && !member_ok(l, member)) return fail(l, CL_EINVAL, "member %d out of range", member);
+    if (!(a > 0) || !isfinite(a)) return fail(l, CL_EINVAL, "a must be positive");
     cl_status s = close_leapfrog(l, true);
     if (s != CL_OK) return s;
-    DevScal h;
-    s = read_status(l, &h);
+    std::vector<DevScal> h;
+    s = read_status(l, h);
     if (s != CL_OK) return s;
-    h.a = a;
-    h.b = isnan(adot) ? 0.0 : adot;
-    h.t = t;
-    CUDA_TRY(l, cudaMemcpyAsync(l->scal, &h, sizeof(DevScal), cudaMemcpyHostToDevice, l->stream));
+    const int m0 = member < 0 ? 0 : member, m1 = member < 0 ? l->members : member + 1;
+    for (int m = m0; m < m1; ++m) {
+        h[m].a = a;
+        h[m].b = isnan(adot) ? 0.0 : adot;
+        h[m].t = t;
+    }
+    CUDA_TRY(l, cudaMemcpyAsync(l->scal, h.data(), sizeof(DevScal) * h.size(), cudaMemcpyHostToDevice, l->stream));
     CUDA_TRY(l, cudaStreamSynchronize(l->stream));
     l->diag_valid = false;
-    if (isnan(adot) && l->p.expansion) return energy_pass(l, P_HUBBLE_INIT | P_COMMIT);
+    if (isnan(adot) && l->p.expansion) {
+        if (is_ens(l) && member >= 0) return energy_pass_members(l, P_HUBBLE_INIT | P_COMMIT, m0, m1);
+        return energy_pass(l, P_HUBBLE_INIT | P_COMMIT);
+    }
     return CL_OK;
 }
 
 cl_status cl_get_scalars(cl_lattice* l, int32_t member, double* a, double* adot, double* t)
 {
     if (!l) return CL_EINVAL;
-    if (member != 0) return fail(l, CL_EINVAL, "member %d out of range", member);
+    if (!member_ok(l, member)) return fail(l, CL_EINVAL, "member %d out of range", member);
     if (l->open) {
         cl_status s = close_leapfrog(l, false);
         if (s != CL_OK) return s;
@@ -743,12 +954,12 @@ cl_status cl_get_scalars(cl_lattice* l, int32_t member, double* a, double* adot,
         cl_status s = energy_pass(l, 0);
         if (s != CL_OK) return s;
     }
-    DevScal h;
-    cl_status s = read_status(l, &h);
+    std::vector<DevScal> h;
+    cl_status s = read_status(l, h);
     if (s != CL_OK) return s;
-    if (a) *a = h.diag[D_A];
-    if (adot) *adot = h.diag[D_ADOT];
-    if (t) *t = h.diag[D_T];
+    if (a) *a = h[member].diag[D_A];
+    if (adot) *adot = h[member].diag[D_ADOT];
+    if (t) *t = h[member].diag[D_T];
     return CL_OK;
 }
 
@@ -786,6 +997,7 @@ cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value)
         l->opt_DZ = (int)value;
         return choose_tiles(l);
     case CL_OPT_STAGES:
+        if (is_ens(l)) return fail(l, CL_EINVAL, "ensembles use the direct loader");
         if (value < -1 || value == 1 || value > 6) return fail(l, CL_EINVAL, "stages must be -1, 0 or 2..6");
         l->opt_stages = (int)value;
         return choose_tiles(l);
@@ -848,14 +1060,14 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
 cl_status cl_sync(cl_lattice* l)
 {
     if (!l) return CL_EINVAL;
-    DevScal h;
-    return read_status(l, &h);
+    std::vector<DevScal> h;
+    return read_status(l, h);
 }
 
 cl_status cl_energies(cl_lattice* l, cl_energy* out, int32_t count)
 {
     if (!l) return CL_EINVAL;
-    if (!out || count < 1 || count > 1) return fail(l, CL_EINVAL, "energies: bad output or count");
+    if (!out || count < 1 || count > l->members) return fail(l, CL_EINVAL, "energies: bad output or count");
     if (!l->diag_valid) {
         cl_status s = energy_pass(l, 0);
         if (s != CL_OK) return s;
@@ -864,24 +1076,28 @@ cl_status cl_energies(cl_lattice* l, cl_energy* out, int32_t count)
         cl_status s = run_u1(l, 2, 0.0, 0.0, 0, l->cur, l->cur ^ 1);
         if (s != CL_OK) return s;
     }
-    DevScal h;
-    cl_status s = read_status(l, &h);
-    memset(out, 0, sizeof(cl_energy));
-    out->t = h.diag[D_T];
-    out->a = h.diag[D_A];
-    out->adot = h.diag[D_ADOT];
-    out->K[0] = h.diag[D_K0];
-    out->K[1] = h.diag[D_K1];
-    out->G[0] = h.diag[D_G0];
-    out->G[1] = h.diag[D_G1];
-    out->V = h.diag[D_V];
-    out->KE = h.diag[D_KE];
-    out->GB = h.diag[D_GB];
-    out->rho = h.diag[D_RHO];
-    out->p = h.diag[D_P];
-    out->hubble_violation = h.diag[D_HV];
-    out->gauss_violation = h.diag[D_GV];
-    out->step = h.step;
+    std::vector<DevScal> hv;
+    cl_status s = read_status(l, hv);
+    for (int m = 0; m < count; ++m) {
+        const DevScal& h = hv[m];
+        cl_energy* o = out + m;
+        memset(o, 0, sizeof(cl_energy));
+        o->t = h.diag[D_T];
+        o->a = h.diag[D_A];
+        o->adot = h.diag[D_ADOT];
+        o->K[0] = h.diag[D_K0];
+        o->K[1] = h.diag[D_K1];
+        o->G[0] = h.diag[D_G0];
+        o->G[1] = h.diag[D_G1];
+        o->V = h.diag[D_V];
+        o->KE = h.diag[D_KE];
+        o->GB = h.diag[D_GB];
+        o->rho = h.diag[D_RHO];
+        o->p = h.diag[D_P];
+        o->hubble_violation = h.diag[D_HV];
+        o->gauss_violation = h.diag[D_GV];
+        o->step = h.step;
+    }
     return s;
 }
 
@@ -889,54 +1105,81 @@ cl_status cl_init_vacuum(cl_lattice* l, int32_t member, const cl_vacuum_params* 
 {
     if (!l) return CL_EINVAL;
     if (!v) return fail(l, CL_EINVAL, "vacuum params NULL");
-    if (member != 0 && member != -1) return fail(l, CL_EINVAL, "member %d out of range", member);
+    if (member != -1 && !member_ok(l, member)) return fail(l, CL_EINVAL, "member %d out of range", member);
     if (!l->potential_set) return fail(l, CL_ESTATE, "cl_set_potential has not been called");
-    const int N = l->N, nf = l->nf;
+    const int m0 = member < 0 ? 0 : member, m1 = member < 0 ? l->members : member + 1;
+    const int nf = l->nf;
     const double a = l->p.a0, al = l->p.alpha;
-    // homogeneous energy and Hubble rate (Eq. Friedmann2) for the momentum modes
-    const double f0 = v->fbar[0], f1 = nf > 1 ? v->fbar[1] : 0.0;
-    double rho_h = 0.5 * l->m2[0] * f0 * f0 + 0.25 * l->lam[0] * f0 * f0 * f0 * f0 + 0.5 * l->m2[1] * f1 * f1 +
-                   0.25 * l->lam[1] * f1 * f1 * f1 * f1 + 0.5 * l->g2 * f0 * f0 * f1 * f1;
-    for (int f = 0; f < nf; ++f) rho_h += v->dfbar[f] * v->dfbar[f] / (2.0 * pow(a, 2.0 * al));
-    const double H = l->p.expansion ? sqrt(pow(a, 2.0 * al) * l->p.kappa * rho_h / 3.0) : 0.0;
-
-    const size_t nh = (size_t)N * N * (N / 2 + 1);
+    int nmax = 0;
+    for (int m = m0; m < m1; ++m) nmax = mem_N(l, m) > nmax ? mem_N(l, m) : nmax;
+    const size_t nh_max = (size_t)nmax * nmax * (nmax / 2 + 1);
     double2 *fk = nullptr, *pk = nullptr;
     double* real = nullptr;
     cufftHandle plan = 0;
+    int plan_N = 0;
     cl_status st = CL_OK;
-    if (cudaMalloc(&fk, nh * sizeof(double2)) != cudaSuccess || cudaMalloc(&pk, nh * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc(&real, (size_t)l->V * sizeof(double)) != cudaSuccess) {
+    if (cudaMalloc(&fk, nh_max * sizeof(double2)) != cudaSuccess || cudaMalloc(&pk, nh_max * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&real, (size_t)nmax * nmax * nmax * sizeof(double)) != cudaSuccess) {
         st = fail(l, CL_ENOMEM, "vacuum scratch allocation failed");
     }
-    if (st == CL_OK && cufftPlan3d(&plan, N, N, N, CUFFT_Z2D) != CUFFT_SUCCESS) st = fail(l, CL_ECUDA, "cufftPlan3d failed");
-    if (st == CL_OK && cufftSetStream(plan, l->stream) != CUFFT_SUCCESS) st = fail(l, CL_ECUDA, "cufftSetStream failed");
     if (st == CL_OK) st = close_leapfrog(l, true);
-    for (int f = 0; st == CL_OK && f < nf; ++f) {
-        VacuumModeArgs A{};
-        A.N = N; A.field = f; A.member = 0; A.seed = v->seed;
-        A.L = l->p.L; A.kcut = v->kcut; A.amp2 = v->amp2; A.a = a; A.alpha = al; A.H = H;
-        A.m2eff = f == 0 ? l->m2[0] + 3.0 * l->lam[0] * f0 * f0 + l->g2 * f1 * f1
-                         : l->m2[1] + 3.0 * l->lam[1] * f1 * f1 + l->g2 * f0 * f0;
-        cudaError_t e = launch_vacuum_modes(A, fk, pk, l->stream);
-        if (e != cudaSuccess) { st = fail(l, CL_ECUDA, "vacuum modes: %s", cudaGetErrorString(e)); break; }
-        const double inv = 1.0 / (double)l->V;  // f(n) = N^-3 sum_k e^{+ikn} f(k)
-        if (cufftExecZ2D(plan, (cufftDoubleComplex*)fk, real) != CUFFT_SUCCESS) { st = fail(l, CL_ECUDA, "Z2D failed"); break; }
-        e = launch_real_to_field(l->p.precision, real, l->phi[f][l->cur], v->fbar[f], inv, l->V, l->stream);
-        if (e != cudaSuccess) { st = fail(l, CL_ECUDA, "convert: %s", cudaGetErrorString(e)); break; }
-        if (cufftExecZ2D(plan, (cufftDoubleComplex*)pk, real) != CUFFT_SUCCESS) { st = fail(l, CL_ECUDA, "Z2D failed"); break; }
-        e = launch_real_to_field(l->p.precision, real, l->pi[f][l->cur], pow(a, 3.0 - al) * v->dfbar[f], inv, l->V,
-                                 l->stream);
-        if (e != cudaSuccess) { st = fail(l, CL_ECUDA, "convert: %s", cudaGetErrorString(e)); break; }
-        if (has_kahan(l)) cudaMemsetAsync(l->cc[f][l->cur], 0, (size_t)l->V * l->es, l->stream);
+    for (int m = m0; st == CL_OK && m < m1; ++m) {
+        const int N = mem_N(l, m);
+        const int64_t V = mem_V(l, m);
+        const size_t off = mem_off_bytes(l, m);
+        const double* c = is_ens(l) ? &l->mpot[5 * (size_t)m] : nullptr;
+        const double m2_0 = c ? c[0] : l->m2[0], lam_0 = c ? c[1] : l->lam[0];
+        const double m2_1 = c ? c[2] : l->m2[1], lam_1 = c ? c[3] : l->lam[1], g2 = c ? c[4] : l->g2;
+        // homogeneous energy and Hubble rate (Eq. Friedmann2) for the momentum modes
+        const double f0 = v->fbar[0], f1 = nf > 1 ? v->fbar[1] : 0.0;
+        double rho_h = 0.5 * m2_0 * f0 * f0 + 0.25 * lam_0 * f0 * f0 * f0 * f0 + 0.5 * m2_1 * f1 * f1 +
+                       0.25 * lam_1 * f1 * f1 * f1 * f1 + 0.5 * g2 * f0 * f0 * f1 * f1;
+        for (int f = 0; f < nf; ++f) rho_h += v->dfbar[f] * v->dfbar[f] / (2.0 * pow(a, 2.0 * al));
+        const double H = l->p.expansion ? sqrt(pow(a, 2.0 * al) * l->p.kappa * rho_h / 3.0) : 0.0;
+        if (plan_N != N) {
+            if (plan) cufftDestroy(plan);
+            plan = 0;
+            plan_N = 0;
+            if (cufftPlan3d(&plan, N, N, N, CUFFT_Z2D) != CUFFT_SUCCESS) { st = fail(l, CL_ECUDA, "cufftPlan3d failed"); break; }
+            if (cufftSetStream(plan, l->stream) != CUFFT_SUCCESS) { st = fail(l, CL_ECUDA, "cufftSetStream failed"); break; }
+            plan_N = N;
+        }
+        for (int f = 0; f < nf; ++f) {
+            VacuumModeArgs A{};
+            A.N = N; A.field = f; A.member = (uint32_t)m; A.seed = v->seed;
+            A.L = mem_L(l, m); A.kcut = v->kcut; A.amp2 = v->amp2; A.a = a; A.alpha = al; A.H = H;
+            A.m2eff = f == 0 ? m2_0 + 3.0 * lam_0 * f0 * f0 + g2 * f1 * f1 : m2_1 + 3.0 * lam_1 * f1 * f1 + g2 * f0 * f0;
+            cudaError_t e = launch_vacuum_modes(A, fk, pk, l->stream);
+            if (e != cudaSuccess) { st = fail(l, CL_ECUDA, "vacuum modes: %s", cudaGetErrorString(e)); break; }
+            const double inv = 1.0 / (double)V;  // f(n) = N^-3 sum_k e^{+ikn} f(k)
+            if (cufftExecZ2D(plan, (cufftDoubleComplex*)fk, real) != CUFFT_SUCCESS) { st = fail(l, CL_ECUDA, "Z2D failed"); break; }
+            e = launch_real_to_field(l->p.precision, real, (char*)l->phi[f][l->cur] + off, v->fbar[f], inv, V, l->stream);
+            if (e != cudaSuccess) { st = fail(l, CL_ECUDA, "convert: %s", cudaGetErrorString(e)); break; }
+            if (cufftExecZ2D(plan, (cufftDoubleComplex*)pk, real) != CUFFT_SUCCESS) { st = fail(l, CL_ECUDA, "Z2D failed"); break; }
+            e = launch_real_to_field(l->p.precision, real, (char*)l->pi[f][l->cur] + off, pow(a, 3.0 - al) * v->dfbar[f],
+                                     inv, V, l->stream);
+            if (e != cudaSuccess) { st = fail(l, CL_ECUDA, "convert: %s", cudaGetErrorString(e)); break; }
+            if (has_kahan(l)) cudaMemsetAsync((char*)l->cc[f][l->cur] + off, 0, (size_t)V * l->es, l->stream);
+        }
     }
     if (st == CL_OK) {
-        DevScal h{};
-        h.a = a;
-        cudaError_t e = cudaMemcpyAsync(l->scal, &h, sizeof(DevScal), cudaMemcpyHostToDevice, l->stream);
-        if (e != cudaSuccess) st = fail(l, CL_ECUDA, "scalar upload: %s", cudaGetErrorString(e));
+        std::vector<DevScal> h;
+        st = read_status(l, h);
+        if (st == CL_OK) {
+            for (int m = m0; m < m1; ++m) {
+                h[m] = DevScal{};
+                h[m].a = a;
+            }
+            cudaError_t e = cudaMemcpyAsync(l->scal, h.data(), sizeof(DevScal) * h.size(), cudaMemcpyHostToDevice, l->stream);
+            if (e != cudaSuccess) st = fail(l, CL_ECUDA, "scalar upload: %s", cudaGetErrorString(e));
+            if (st == CL_OK && cudaStreamSynchronize(l->stream) != cudaSuccess) st = fail(l, CL_ECUDA, "sync failed");
+        }
     }
-    if (st == CL_OK) st = energy_pass(l, P_HUBBLE_INIT | P_COMMIT);
+    if (st == CL_OK) {
+        l->diag_valid = false;
+        st = is_ens(l) ? energy_pass_members(l, P_HUBBLE_INIT | P_COMMIT, m0, m1) : energy_pass(l, P_HUBBLE_INIT | P_COMMIT);
+        if (st == CL_OK && !is_ens(l)) l->diag_valid = true;
+    }
     if (st == CL_OK && cudaStreamSynchronize(l->stream) != cudaSuccess) st = fail(l, CL_ECUDA, "sync failed");
     if (plan) cufftDestroy(plan);
     if (fk) cudaFree(fk);
@@ -950,13 +1193,14 @@ cl_status cl_spectrum(cl_lattice* l, int32_t member, int32_t field, double dn, i
                       double* delta_out, double* count_out, int32_t cap, int32_t* nbins)
 {
     if (!l) return CL_EINVAL;
-    if (member != 0) return fail(l, CL_EINVAL, "member %d out of range", member);
+    if (!member_ok(l, member)) return fail(l, CL_EINVAL, "member %d out of range", member);
     if (!(dn > 0) || (type != 1 && type != 2) || cap < 0 || (cap > 0 && (!k_out || !delta_out || !count_out)))
         return fail(l, CL_EINVAL, "spectrum: bad arguments");
     int f = 0;
     const int kind = field_kind(l, field, &f);
     if (kind < 0) return fail(l, CL_EINVAL, "field %d not present", field);
-    const int N = l->N;
+    const int N = mem_N(l, member);
+    const int64_t V = mem_V(l, member);
     const int nb = (int)floor(sqrt(3.0) * (N / 2) / dn + 0.5) + 1;
     if (nbins) *nbins = nb;
     if (cap == 0) return CL_OK;
@@ -966,19 +1210,19 @@ cl_status cl_spectrum(cl_lattice* l, int32_t member, int32_t field, double dn, i
         if (s != CL_OK) return s;
         buf = l->cur ^ 1;
     }
-    const void* src = kind == 0 ? l->phi[f][buf] : l->pi[f][buf];
+    const void* src = (const char*)(kind == 0 ? l->phi[f][buf] : l->pi[f][buf]) + mem_off_bytes(l, member);
     const size_t nh = (size_t)N * N * (N / 2 + 1);
     double* real = nullptr;
     double2* F = nullptr;
     double* bins = nullptr;  // S[nb], C[nb], k[nb], delta[nb]
     cufftHandle plan = 0;
     cl_status st = CL_OK;
-    if (cudaMalloc(&real, (size_t)l->V * sizeof(double)) != cudaSuccess ||
+    if (cudaMalloc(&real, (size_t)V * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&F, nh * sizeof(double2)) != cudaSuccess || cudaMalloc(&bins, 4 * (size_t)nb * sizeof(double)) != cudaSuccess)
         st = fail(l, CL_ENOMEM, "spectrum scratch allocation failed");
     if (st == CL_OK && cufftPlan3d(&plan, N, N, N, CUFFT_D2Z) != CUFFT_SUCCESS) st = fail(l, CL_ECUDA, "cufftPlan3d failed");
     if (st == CL_OK && cufftSetStream(plan, l->stream) != CUFFT_SUCCESS) st = fail(l, CL_ECUDA, "cufftSetStream failed");
-    if (st == CL_OK && launch_field_to_double(l->p.precision, src, real, l->V, l->stream) != cudaSuccess)
+    if (st == CL_OK && launch_field_to_double(l->p.precision, src, real, V, l->stream) != cudaSuccess)
         st = fail(l, CL_ECUDA, "field conversion failed");
     if (st == CL_OK && cufftExecD2Z(plan, real, (cufftDoubleComplex*)F) != CUFFT_SUCCESS) st = fail(l, CL_ECUDA, "D2Z failed");
     if (st == CL_OK && cudaMemsetAsync(bins, 0, 2 * (size_t)nb * sizeof(double), l->stream) != cudaSuccess)
@@ -986,7 +1230,7 @@ cl_status cl_spectrum(cl_lattice* l, int32_t member, int32_t field, double dn, i
     if (st == CL_OK && launch_spectrum_bins(F, N, dn, nb, bins, bins + nb, l->stream) != cudaSuccess)
         st = fail(l, CL_ECUDA, "binning failed");
     if (st == CL_OK &&
-        launch_spectrum_finish(bins, bins + nb, N, l->p.L, dn, type, nb, bins + 2 * nb, bins + 3 * nb, l->stream) != cudaSuccess)
+        launch_spectrum_finish(bins, bins + nb, N, mem_L(l, member), dn, type, nb, bins + 2 * nb, bins + 3 * nb, l->stream) != cudaSuccess)
         st = fail(l, CL_ECUDA, "spectrum finish failed");
     std::vector<double> h(4 * (size_t)nb);
     if (st == CL_OK && cudaMemcpyAsync(h.data(), bins, 4 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, l->stream) != cudaSuccess)

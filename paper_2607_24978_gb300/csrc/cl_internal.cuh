@@ -131,6 +131,44 @@ struct U1Args {
 cudaError_t launch_u1(int precision, const void* args, int what, cudaStream_t s);
 int u1_grid_blocks(int N);
 
+// Batched ensemble of independent lattices (ensemble_pass.cu).  Every array class (phi,
+// pi, compensation, per field and buffer) is one arena holding the members back to back,
+// each starting on a 256-byte boundary.  A work item is BY full x rows times DZ planes of
+// one member; items of a member are consecutive in the item table.
+constexpr int kEnsThreads = 256;
+struct EnsMember {
+    long long off;       // element offset of the member's arrays in every arena
+    int N, BY, DZ;       // sites per side and the tile of one work item
+    int item0, nitems;   // the member's work items [item0, item0 + nitems)
+    double dx;
+    double m2[2], lam[2], g2;
+};
+struct EnsItem {
+    int member, y0, z0, pad;
+};
+template <typename T>
+struct EnsPassArgs {
+    const T* phi_in[2];
+    const T* pi_in[2];
+    const T* c_in[2];
+    T* phi_out[2];
+    T* pi_out[2];
+    T* c_out[2];
+    const EnsMember* members;
+    const EnsItem* items;
+    DevScal* scal;        // one per member
+    double* partials;     // [items][kMaxQ]
+    int item_begin, item_end;
+    double alpha, kappa;
+    double d, e, k;       // pass coefficients (already x dt), as in ScalarPassArgs
+    double hubble_limit;
+    int flags;
+};
+// One pass over the items [item_begin, item_end) with `grid` persistent blocks.
+cudaError_t launch_ensemble_pass(int precision, int nf, const void* args, int vw, int grid, size_t smem,
+                                 cudaStream_t s);
+cudaError_t ensemble_pass_blocks_per_sm(int precision, int nf, int vw, size_t smem, int* blocks);
+
 // Vacuum initial conditions: fills the half spectrum (kx in [0, N/2]) of delta f and
 // delta pi for one field into two complex-double buffers of N*N*(N/2+1) entries.
 struct VacuumModeArgs {
