@@ -72,9 +72,14 @@ double orc_u1_magnetic_sum(int N, const double* th)
 {
     const int64_t V = (int64_t)N * N * N;
     double s = 0.0;
+    /* 1 - cos p written as 2 sin^2(p/2): the same function, without the cancellation
+     * that loses every digit when the plaquettes are small (gauge fields grown from zero) */
     for (int64_t n = 0; n < V; ++n)
         for (int i = 0; i < 3; ++i)
-            for (int j = i + 1; j < 3; ++j) s += 1.0 - cos(plaq(N, th, n, i, j));
+            for (int j = i + 1; j < 3; ++j) {
+                const double h = sin(0.5 * plaq(N, th, n, i, j));
+                s += 2.0 * h * h;
+            }
     return s;
 }
 
