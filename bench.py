@@ -16,6 +16,13 @@ Extra keys: roofline (dominant kernel = the fused scalar pass), cpu_baseline (th
 oracle on a bounded sample), e2e (the same metric through the C ABI with host
 buffers: state upload, step, energies download each step), fp64_plain (the same
 workload in FP64 without compensation), clocks (nvidia-smi during the timed region).
+
+Other workloads (--workload; one JSON line each, same keys where they apply):
+  u1        axion + compact U(1) links, 192^3, FP32, RK3-3, alpha_Lambda = 30,
+            V = phi^2/2, phi = 1 + noise, phi' = -0.5, A = 0, small divergence-free E.
+  ensemble  1024 independent lambda phi^4 lattices of sizes drawn from {32, 48, 64}^3,
+            per-member vacuum amplitude lambda log-uniform in [1e-6, 1e-3], VV-2,
+            FP32 + Kahan, one launch per pass for all members.
 """
 import argparse
 import json
@@ -222,6 +229,117 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ other workloads
+U1 = dict(N=192, L=2 * math.pi / 0.1, dt=0.01, alphaL=30.0, ws2=1e-4, kappa=1.0, alpha=0.0, m2=1.0, phi0=1.0,
+          dphi0=-0.5, e_amp=1e-6, seed=1234)
+U1_STAGES = 3
+# algorithmic bytes of one RK stage per site: phi, pi, theta_1..3, E_1..3 and their eight
+# Runge-Kutta auxiliaries, read + write, 4 B each
+U1_BYTES_PER_SITE_STAGE = 8 * 2 * 2 * 4
+ENS = dict(members=1024, sizes=(32, 48, 64), lam=(1e-6, 1e-3), L=8.0 * math.pi, dt=0.01, alpha=1.0, kappa=0.1,
+           seed=1234)
+# VV-2, one field, FP32 + Kahan: phi, pi, c read + write
+ENS_BYTES_PER_SITE = 3 * 2 * 4
+
+
+def timed_region(torch, g, stream, steps):
+    clk = Clocks(torch.cuda.current_device())
+    with clk:
+        el, launches = timed_steps(torch, g, stream, steps)
+    return el, launches, clk.summary()
+
+
+def run_u1_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src):
+    import numpy as np
+    from tests import inputs
+    c = U1
+    N = c["N"]
+    g = cl.Lattice(N, c["L"], 1, cl.CL_PREC_FP32, cl.CL_INT_RK3_3, gauge=cl.CL_GAUGE_U1_AXION, expansion=True,
+                   alpha=c["alpha"], kappa=c["kappa"], dt=c["dt"], stream=stream.cuda_stream)
+    g.cl_set_potential(cl.CL_POT_M2, [c["m2"]])
+    g.cl_set_gauge_coupling(c["alphaL"], c["ws2"])
+    phi, pi = inputs.scalar_state(N, 1, seed=c["seed"], fbar=(c["phi0"],), amp=1e-5, pamp=1e-5,
+                                  pbar=(c["dphi0"],))
+    E = inputs.solenoidal_field(N, seed=c["seed"] + 1, amp=c["e_amp"], dtype=np.float32)
+    g.cl_set_state(cl.CL_FIELD_PHI0, phi[0].astype(np.float32))
+    g.cl_set_state(cl.CL_FIELD_PI0, pi[0].astype(np.float32))
+    for i in range(3):
+        g.cl_set_state(cl.CL_FIELD_E1 + i, np.ascontiguousarray(E[i]))
+    del phi, pi, E
+    g.cl_set_scalars(1.0)
+    g.cl_step(args.warmup)
+    g.cl_sync()
+    barrier(world)
+    el, launches, clocks = timed_region(torch, g, stream, args.steps)
+    barrier(world)
+    el_max = max_over_ranks(el, world)
+    e = g.cl_energies()
+    g.close()
+    stage_s = el / (args.steps * U1_STAGES)
+    bytes_stage = N ** 3 * U1_BYTES_PER_SITE_STAGE
+    achieved = bytes_stage / stage_s / 1e9
+    return {"metric": "Gsite-updates/s, axion-U(1) 192^3 RK3-3", "value": world * N ** 3 * args.steps / el_max / 1e9,
+            "unit": "Gsite-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "axion-U(1) 192^3, RK3-3, FP32, alpha_Lambda=30, (omega*/f*)^2=1e-4, kappa=1, "
+                                   "V=phi^2/2, phi=1, phi'=-0.5, A=0, divergence-free E (rms 1e-6), dt=0.01",
+                       "lattice": N, "stages_per_step": U1_STAGES,
+                       "l2": "inputs (%.0f MB) larger than L2; no flush" % (N ** 3 * 16 * 2 * 4 / 1e6)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                         "kernel": "one RK stage: k_u1_helpers + k_u1_stage",
+                         "algorithmic_bytes_per_launch": bytes_stage},
+            "gpu_launches": launches, "clocks": clocks,
+            "energies_end": {"a": e["a"], "rho": e["rho"], "KE": e["KE"], "GB": e["GB"],
+                             "gauss_violation": e["gauss_violation"], "hubble_violation": e["hubble_violation"]}}
+
+
+def run_ensemble_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src):
+    import numpy as np
+    c = dict(ENS)
+    if args.members:  # smaller ensembles of the same mix (profiling runs)
+        c["members"] = args.members
+    rg = np.random.default_rng(c["seed"])
+    sizes = [int(x) for x in rg.choice(c["sizes"], c["members"])]
+    lam = 10.0 ** rg.uniform(math.log10(c["lam"][0]), math.log10(c["lam"][1]), c["members"])
+    g = cl.Lattice(sizes[0], c["L"], 1, cl.CL_PREC_FP32_KAHAN, cl.CL_INT_VV2, expansion=True, alpha=c["alpha"],
+                   kappa=c["kappa"], dt=c["dt"], stream=stream.cuda_stream, member_N=sizes)
+    g.cl_set_potential(cl.CL_POT_LPHI4, [1.0])
+    kcut = 16 * 2 * math.pi / c["L"]
+    for m in range(c["members"]):  # lambda phi^4 in program units: lambda sets the vacuum amplitude
+        g.cl_init_vacuum(c["seed"], kcut, float(lam[m]), (1.0,), (0.0,), member=m)
+    sites = sum(n ** 3 for n in sizes)
+    for opt, v in ((cl.CL_OPT_STAGES, args.stages), (cl.CL_OPT_TILE_BY, args.by), (cl.CL_OPT_TILE_DZ, args.dz)):
+        if v is not None:
+            g.cl_set_option(opt, v)
+    g.cl_step(args.warmup)
+    g.cl_sync()
+    barrier(world)
+    el, launches, clocks = timed_region(torch, g, stream, args.steps)
+    barrier(world)
+    el_max = max_over_ranks(el, world)
+    es = g.cl_energies(c["members"])
+    g.close()
+    pass_s = el / args.steps
+    bytes_pass = sites * ENS_BYTES_PER_SITE
+    achieved = bytes_pass / pass_s / 1e9
+    return {"metric": "Gsite-updates/s, ensemble of %d lattices" % c["members"], "value": world * sites * args.steps / el_max / 1e9,
+            "unit": "Gsite-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%d lambda phi^4 lattices, N from {32,48,64} (seeded), vacuum amplitude " % c["members"] +
+                                   "log-uniform in [1e-6,1e-3], L=8 pi, VV-2, FP32+Kahan, dt=0.01",
+                       "members": c["members"], "sites": sites,
+                       "l2": "inputs (%.0f MB) larger than L2; no flush" % (sites * 6 * 4 / 1e6)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                         "kernel": "k_ensemble_pass<float,1,kahan,4>", "algorithmic_bytes_per_launch": bytes_pass},
+            "gpu_launches": launches, "clocks": clocks,
+            "energies_end": {"members": len(es), "max_hubble_violation": max(x["hubble_violation"] for x in es),
+                             "steps": es[0]["step"]}}
+
+
 # ------------------------------------------------------------------ GPU arm
 def make_lattice(cl, precision, stream, args=None):
     g = cl.Lattice(N, L, 2, precision, cl.CL_INT_YOSHIDA4, expansion=True, alpha=ALPHA, kappa=KAPPA, dt=DT,
@@ -264,6 +382,12 @@ def run_gpu(args, world, rank, local):
     peaks = load_peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     peak_src = "of measured" if peaks else "of fallback"
+    if args.workload != "preheat":
+        fn = run_u1_workload if args.workload == "u1" else run_ensemble_workload
+        line = fn(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
 
     g = make_lattice(cl, cl.CL_PREC_FP32_KAHAN, stream.cuda_stream, args)
     g.cl_step(args.warmup)
@@ -349,6 +473,9 @@ def main():
     ap.add_argument("--stages", type=int, default=None, help="override CL_OPT_STAGES")
     ap.add_argument("--by", type=int, default=None, help="override CL_OPT_TILE_BY")
     ap.add_argument("--dz", type=int, default=None, help="override CL_OPT_TILE_DZ")
+    ap.add_argument("--workload", default="preheat", choices=["preheat", "u1", "ensemble"],
+                    help="preheat: the headline 256^3 two-field run; u1, ensemble: the other workloads")
+    ap.add_argument("--members", type=int, default=None, help="ensemble size (default 1024)")
     args = ap.parse_args()
     world, rank, local = dist_init(args)
     if args.impl == "reference":

@@ -116,9 +116,9 @@ struct U1Args {
     T* th_out[3];
     T* E_out[3];
     T* k_out[8];
-    T* Bbar[3];   // per-site scratch written by the helper launch
-    T* Bdot[3];
-    T* X[3];      // phi Ebar_k
+    T* sP[3];     // per-site plaquette fields written by the plaquette launch (normal k):
+    T* rP[3];     //   sin P_k, cos P_k * dP_k/dt, and cos P_k times the corner sum of phi Ebar_k
+    T* Z[3];
     DevScal* scal;
     double* partials;
     int N;
@@ -127,7 +127,9 @@ struct U1Args {
     double hubble_limit;
     int flags;    // P_EXPANSION, P_FIRST_STAGE, P_COUNT_STEP, P_ENERGY_ONLY, P_HUBBLE_INIT
 };
-// what: 0 = helper fields, 1 = stage (or energies with P_ENERGY_ONLY), 2 = Gauss diagnostic
+// what: 0 = plaquette fields, 1 = stage (or energies with P_ENERGY_ONLY), 2 = Gauss diagnostic.
+// The plaquette launch writes its magnetic-energy partials after the stage's, at
+// partials[u1_grid_blocks(N) * kMaxQ + block].
 cudaError_t launch_u1(int precision, const void* args, int what, cudaStream_t s);
 int u1_grid_blocks(int N);
 
@@ -156,6 +158,7 @@ struct EnsPassArgs {
     T* c_out[2];
     const EnsMember* members;
     const EnsItem* items;
+    const int* sched;     // processing order of all items (nullptr: items item_begin.. in order)
     DevScal* scal;        // one per member
     double* partials;     // [items][kMaxQ]
     int item_begin, item_end;
@@ -163,11 +166,15 @@ struct EnsPassArgs {
     double d, e, k;       // pass coefficients (already x dt), as in ScalarPassArgs
     double hubble_limit;
     int flags;
+    int stages;           // TMA stage buffers (2..4) or 0 for the direct loader
+    int stage_stride;     // elements of one stage buffer (largest member tile)
+    int ring_slot;        // elements of one ring slot of drifted fields (largest member tile)
 };
+constexpr int kEnsTmaThreads = kEnsThreads + 32;  // consumers + one producer warp
 // One pass over the items [item_begin, item_end) with `grid` persistent blocks.
 cudaError_t launch_ensemble_pass(int precision, int nf, const void* args, int vw, int grid, size_t smem,
                                  cudaStream_t s);
-cudaError_t ensemble_pass_blocks_per_sm(int precision, int nf, int vw, size_t smem, int* blocks);
+cudaError_t ensemble_pass_blocks_per_sm(int precision, int nf, int vw, int stages, size_t smem, int* blocks);
 
 // Vacuum initial conditions: fills the half spectrum (kx in [0, N/2]) of delta f and
 // delta pi for one field into two complex-double buffers of N*N*(N/2+1) entries.

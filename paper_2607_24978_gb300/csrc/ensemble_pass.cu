@@ -2,8 +2,8 @@
 //
 // Many small lattices (each with its own size, box, couplings, a and a') advance by one
 // pass of the staggered kick-drift scheme in a single persistent launch.  The work is a
-// table of items, each BY full x rows times DZ planes of one member; block b takes items
-// b, b + grid, b + 2 grid, ... and runs the same per-site arithmetic as the
+// table of items, each BY full x rows times DZ planes of one member; block b takes the
+// items b, b + grid, b + 2 grid, ... of a schedule (largest first) and runs the same per-site arithmetic as the
 // single-lattice direct loader on it (drift while loading, stencil kick, energies).
 // Reductions: every item writes its FP64 partial sums; the block that completes the last
 // item of a member (an arrival counter per member) sums that member's partials in a fixed
@@ -14,6 +14,7 @@
 #include "cl_internal.cuh"
 #include "kernel_common.cuh"
 #include "scalar_pass_common.cuh"
+#include "tma_pipeline.cuh"
 
 namespace clk {
 
@@ -29,13 +30,14 @@ __global__ void __launch_bounds__(kEnsThreads) k_ensemble_pass(const EnsPassArgs
     const bool do_drift = (A.flags & P_DRIFT) != 0;
     const bool expand = (A.flags & P_EXPANSION) != 0;
 
-    for (int it = A.item_begin + blockIdx.x; it < A.item_end; it += gridDim.x) {
+    for (int k = blockIdx.x; k < A.item_end - A.item_begin; k += gridDim.x) {
+        const int it = A.sched ? A.sched[k] : A.item_begin + k;
         const EnsItem I = A.items[it];
         const EnsMember& M = A.members[I.member];
         const int N = M.N, BY = M.BY;
         const double dx = M.dx;
         DevScal* S = A.scal + I.member;
-        if (tid == 0) pass_coefficients(S->a, S->b, A.d, A.alpha, dx, expand, s_coef);
+        pass_coefficients_warps(tid, S->a, S->b, A.d, A.alpha, dx, expand, s_coef);
         __syncthreads();
         const TileCoef<T> C{(T)s_coef[0], (T)s_coef[1], (T)s_coef[2], (T)A.e, (T)A.k};
         const PotCoef<T> P(M.m2, M.lam, M.g2);
@@ -86,61 +88,235 @@ __global__ void __launch_bounds__(kEnsThreads) k_ensemble_pass(const EnsPassArgs
     }
 }
 
+// TMA-staged variant (every member's rows a multiple of 16 bytes): one producer warp
+// streams the planes of the block's items, item after item, into a ring of S stage
+// buffers; kEnsThreads consumer threads drift and kick them with the register z-march of
+// the single-lattice kernel.  Stage buffers and ring slots have the size of the largest
+// member tile, so a change of member between items never moves a buffer that another
+// warp may still use; the full/empty mbarriers order the stages and the consumers'
+// named barriers order the ring, exactly as within one lattice.  Per item the consumers
+// evaluate the member's pass prefactors, reduce the item's partial sums on named barrier
+// 2 and, for a member's last item, run the member's epilogue.  All waits are bounded; a
+// timeout is reported through the status word of member 0.
+template <typename T, int NF, bool KAHAN, int VW, int S>
+__global__ void __launch_bounds__(kEnsTmaThreads, NF == 1 ? 2 : 1) k_ensemble_pass_tma(const EnsPassArgs<T> A)
+{
+    constexpr int RING = 3;
+    constexpr int KPF = KAHAN ? 3 : 2;
+    constexpr int NARR = NF * KPF;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_full[S];
+    __shared__ __align__(8) uint64_t s_empty[S];
+    __shared__ double s_coef[4];
+    __shared__ double s_red[32][kMaxQ];
+    __shared__ int s_last, s_timeout;
+    const int tid = threadIdx.x;
+    constexpr int CT = kEnsThreads, CW = CT / 32;
+    const bool producer = tid >= CT;
+    T* stage = reinterpret_cast<T*>(smem_raw);
+    T* ring = stage + S * A.stage_stride;
+    const bool do_drift = (A.flags & P_DRIFT) != 0;
+    const bool expand = (A.flags & P_EXPANSION) != 0;
+
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&s_full[s], 1);
+            mbar_init(&s_empty[s], CW);
+        }
+        mbar_fence_init();
+        s_timeout = 0;
+    }
+    __syncthreads();
+
+    if (producer) {
+        const int lane = tid - CT;
+        int st = 0;
+        uint32_t empty_phase = 0;
+        int issued = 0;
+        for (int k = blockIdx.x; k < A.item_end - A.item_begin; k += gridDim.x) {
+            const int it = A.sched ? A.sched[k] : A.item_begin + k;
+            const EnsItem I = A.items[it];
+            const EnsMember& M = A.members[I.member];
+            const int N = M.N, BY = M.BY, y0 = I.y0, z0 = I.z0;
+            const int R = min(BY, N - y0), NZ = min(M.DZ, N - z0);
+            const int ylo = y0 == 0 ? N - 1 : y0 - 1;
+            const int yhi = y0 + R == N ? 0 : y0 + R;
+            const int arr_stride = (BY + 2) * N;
+            const uint32_t plane_bytes = (uint32_t)(NARR * (R + 2) * N * sizeof(T));
+            const long long off = M.off;
+            FieldSet<T> F{};
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                F.phi_in[f] = A.phi_in[f] + off;
+                F.pi_in[f] = A.pi_in[f] + off;
+                F.c_in[f] = KAHAN ? A.c_in[f] + off : nullptr;
+            }
+            int zz = z0 == 0 ? N - 1 : z0 - 1;
+            for (int j = 0; j < NZ + 2; ++j) {
+                if (issued >= S) {
+                    if (!mbar_wait_bounded(&s_empty[st], (empty_phase >> st) & 1u,
+                                           s_timeout ? 1000000ull : 2000000000ull))
+                        s_timeout = 1;
+                    empty_phase ^= 1u << st;
+                }
+                if (lane == 0) mbar_arrive_expect_tx(&s_full[st], plane_bytes);
+                __syncwarp();
+                tma_issue_plane<T, NF, KAHAN>(lane, stage + st * A.stage_stride, arr_stride, F, N, zz, y0, R, ylo, yhi,
+                                              &s_full[st]);
+                __syncwarp();
+                ++issued;
+                st = st + 1 == S ? 0 : st + 1;
+                zz = zz + 1 == N ? 0 : zz + 1;
+            }
+        }
+    } else {
+        int st = 0;
+        uint32_t full_phase = 0;
+        int rnew = 0, rmid = RING - 1;
+        ZMarch<T, NF, VW> Z;
+        for (int k = blockIdx.x; k < A.item_end - A.item_begin; k += gridDim.x) {
+            const int it = A.sched ? A.sched[k] : A.item_begin + k;
+            const EnsItem I = A.items[it];
+            const EnsMember& M = A.members[I.member];
+            const int N = M.N, BY = M.BY, y0 = I.y0, z0 = I.z0;
+            const int R = min(BY, N - y0), NZ = min(M.DZ, N - z0);
+            const double dx = M.dx;
+            DevScal* Sm = A.scal + I.member;
+            pass_coefficients_warps(tid, Sm->a, Sm->b, A.d, A.alpha, dx, expand, s_coef);
+            named_barrier_sync(2, CT);
+            const TileCoef<T> C{(T)s_coef[0], (T)s_coef[1], (T)s_coef[2], (T)A.e, (T)A.k};
+            const PotCoef<T> P(M.m2, M.lam, M.g2);
+            const OutArrays<EnsPassArgs<T>> Out{A, M.off};
+            const TileGeom G(N, VW, BY, R, tid);
+            const size_t plane = (size_t)N * N;
+            const size_t row_off = (size_t)(y0 + G.r) * N + G.x0;
+            Acc<T> accK[NF], accG[NF], accV;
+            int zz = z0 == 0 ? N - 1 : z0 - 1;
+            for (int j = 0; j < NZ + 2; ++j) {
+                if (!mbar_wait_bounded(&s_full[st], (full_phase >> st) & 1u, s_timeout ? 1000000ull : 2000000000ull))
+                    s_timeout = 1;
+                full_phase ^= 1u << st;
+                tma_consume_plane<T, NF, KAHAN, VW>(G, stage + st * A.stage_stride, ring + rnew * A.ring_slot,
+                                                    ring + rmid * A.ring_slot, tid, CT, do_drift, j >= 1 && j <= NZ,
+                                                    j >= 2, (size_t)zz * plane + row_off,
+                                                    (size_t)(z0 + j - 2) * plane + row_off, Out, C, P, Z, accK,
+                                                    accG, accV, &s_empty[st]);
+                rmid = rnew;
+                rnew = rnew + 1 == RING ? 0 : rnew + 1;
+                st = st + 1 == S ? 0 : st + 1;
+                zz = zz + 1 == N ? 0 : zz + 1;
+            }
+            // item partials; the member's last item reduces them in a fixed order
+            double v[kMaxQ];
+            v[0] = accK[0].value();
+            v[1] = NF > 1 ? accK[NF - 1].value() : 0.0;
+            v[2] = accG[0].value();
+            v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
+            v[4] = accV.value();
+            group_reduce<kMaxQ>(v, s_red, tid, CT, 2);
+            if (tid == 0) {
+#pragma unroll
+                for (int q = 0; q < kMaxQ; ++q) A.partials[(size_t)it * kMaxQ + q] = v[q];
+                __threadfence();
+                const unsigned prev = atomicAdd(&Sm->counter, 1u);
+                s_last = (prev + 1u == (unsigned)M.nitems);
+            }
+            named_barrier_sync(2, CT);
+            if (s_last) {  // uniform over the consumers
+                __threadfence();
+                double w[kMaxQ];
+#pragma unroll
+                for (int q = 0; q < kMaxQ; ++q) w[q] = 0.0;
+                for (int b = tid; b < M.nitems; b += CT)
+#pragma unroll
+                    for (int q = 0; q < kMaxQ; ++q) w[q] += __ldcg(&A.partials[(size_t)(M.item0 + b) * kMaxQ + q]);
+                group_reduce<kMaxQ>(w, s_red, tid, CT, 2);
+                if (tid == 0)
+                    scalar_epilogue(Sm, w, (double)N * N * N, dx, s_coef[3], A.alpha, A.kappa, A.d, A.e, A.k, A.flags,
+                                    A.hubble_limit);
+            }
+            named_barrier_sync(2, CT);  // s_coef, s_red and s_last are rewritten by the next item
+        }
+    }
+    __syncthreads();  // producer and consumers meet; no copy is in flight past this point
+    if (tid == 0 && s_timeout) atomicOr(&A.scal[0].status, ST_TIMEOUT);
+}
+
 template <typename K>
 static cudaError_t ens_smem_attr(K kernel)
 {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPassMaxSmem);
 }
 
-template <typename T, int NF, bool KAHAN, int VW>
-static cudaError_t ens_one(const void* args, int grid, size_t smem, cudaStream_t s, int* occ)
+template <typename K, typename T>
+static cudaError_t ens_launch(K kernel, int threads, const void* args, int grid, size_t smem, cudaStream_t s,
+                              int* occ, bool& attr)
 {
-    auto kernel = k_ensemble_pass<T, NF, KAHAN, VW>;
-    static bool attr = false;
     if (!attr) {
         cudaError_t e = ens_smem_attr(kernel);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel, kEnsThreads, smem);
-    kernel<<<grid, kEnsThreads, smem, s>>>(*static_cast<const EnsPassArgs<T>*>(args));
+    if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel, threads, smem);
+    kernel<<<grid, threads, smem, s>>>(*static_cast<const EnsPassArgs<T>*>(args));
     return cudaGetLastError();
 }
 
-template <typename T, int NF, bool KAHAN>
-static cudaError_t ens_vw(const void* args, int vw, int grid, size_t smem, cudaStream_t s, int* occ)
+// stages: 0 = direct loader, 2..4 = TMA stage buffers
+template <typename T, int NF, bool KAHAN, int VW>
+static cudaError_t ens_one(const void* args, int stages, int grid, size_t smem, cudaStream_t s, int* occ)
 {
-    if (vw == 1) return ens_one<T, NF, KAHAN, 1>(args, grid, smem, s, occ);
-    if (vw == 2) return ens_one<T, NF, KAHAN, 2>(args, grid, smem, s, occ);
-    if constexpr (sizeof(T) == 4) {
-        if (vw == 4) return ens_one<T, NF, KAHAN, 4>(args, grid, smem, s, occ);
+    static bool attr[5] = {false, false, false, false, false};
+    if (stages <= 0) return ens_launch<decltype(&k_ensemble_pass<T, NF, KAHAN, VW>), T>(
+        k_ensemble_pass<T, NF, KAHAN, VW>, kEnsThreads, args, grid, smem, s, occ, attr[0]);
+    if constexpr (VW * sizeof(T) == 16) {  // 16-byte vectors: every member row is a 16-byte multiple
+        if (stages == 2) return ens_launch<decltype(&k_ensemble_pass_tma<T, NF, KAHAN, VW, 2>), T>(
+            k_ensemble_pass_tma<T, NF, KAHAN, VW, 2>, kEnsTmaThreads, args, grid, smem, s, occ, attr[2]);
+        if (stages == 3) return ens_launch<decltype(&k_ensemble_pass_tma<T, NF, KAHAN, VW, 3>), T>(
+            k_ensemble_pass_tma<T, NF, KAHAN, VW, 3>, kEnsTmaThreads, args, grid, smem, s, occ, attr[3]);
+        if (stages == 4) return ens_launch<decltype(&k_ensemble_pass_tma<T, NF, KAHAN, VW, 4>), T>(
+            k_ensemble_pass_tma<T, NF, KAHAN, VW, 4>, kEnsTmaThreads, args, grid, smem, s, occ, attr[4]);
     }
     return cudaErrorInvalidValue;
 }
 
-static cudaError_t ens_dispatch(int precision, int nf, const void* args, int vw, int grid, size_t smem,
+template <typename T, int NF, bool KAHAN>
+static cudaError_t ens_vw(const void* args, int vw, int stages, int grid, size_t smem, cudaStream_t s, int* occ)
+{
+    if (vw == 1) return ens_one<T, NF, KAHAN, 1>(args, stages, grid, smem, s, occ);
+    if (vw == 2) return ens_one<T, NF, KAHAN, 2>(args, stages, grid, smem, s, occ);
+    if constexpr (sizeof(T) == 4) {
+        if (vw == 4) return ens_one<T, NF, KAHAN, 4>(args, stages, grid, smem, s, occ);
+    }
+    return cudaErrorInvalidValue;
+}
+
+static cudaError_t ens_dispatch(int precision, int nf, const void* args, int vw, int stages, int grid, size_t smem,
                                 cudaStream_t s, int* occ)
 {
     if (precision == CL_PREC_FP64)
-        return nf == 1 ? ens_vw<double, 1, false>(args, vw, grid, smem, s, occ)
-                       : ens_vw<double, 2, false>(args, vw, grid, smem, s, occ);
+        return nf == 1 ? ens_vw<double, 1, false>(args, vw, stages, grid, smem, s, occ)
+                       : ens_vw<double, 2, false>(args, vw, stages, grid, smem, s, occ);
     if (precision == CL_PREC_FP32_KAHAN)
-        return nf == 1 ? ens_vw<float, 1, true>(args, vw, grid, smem, s, occ)
-                       : ens_vw<float, 2, true>(args, vw, grid, smem, s, occ);
-    return nf == 1 ? ens_vw<float, 1, false>(args, vw, grid, smem, s, occ)
-                   : ens_vw<float, 2, false>(args, vw, grid, smem, s, occ);
+        return nf == 1 ? ens_vw<float, 1, true>(args, vw, stages, grid, smem, s, occ)
+                       : ens_vw<float, 2, true>(args, vw, stages, grid, smem, s, occ);
+    return nf == 1 ? ens_vw<float, 1, false>(args, vw, stages, grid, smem, s, occ)
+                   : ens_vw<float, 2, false>(args, vw, stages, grid, smem, s, occ);
 }
 
 cudaError_t launch_ensemble_pass(int precision, int nf, const void* args, int vw, int grid, size_t smem,
                                  cudaStream_t s)
 {
     if (grid < 1) return cudaSuccess;
-    return ens_dispatch(precision, nf, args, vw, grid, smem, s, nullptr);
+    const int stages = precision == CL_PREC_FP64 ? static_cast<const EnsPassArgs<double>*>(args)->stages
+                                                 : static_cast<const EnsPassArgs<float>*>(args)->stages;
+    return ens_dispatch(precision, nf, args, vw, stages, grid, smem, s, nullptr);
 }
 
-cudaError_t ensemble_pass_blocks_per_sm(int precision, int nf, int vw, size_t smem, int* blocks)
+cudaError_t ensemble_pass_blocks_per_sm(int precision, int nf, int vw, int stages, size_t smem, int* blocks)
 {
-    return ens_dispatch(precision, nf, nullptr, vw, 0, smem, nullptr, blocks);
+    return ens_dispatch(precision, nf, nullptr, vw, stages, 0, smem, nullptr, blocks);
 }
 
 }  // namespace clk

@@ -113,6 +113,30 @@ __device__ __forceinline__ void block_reduce(double (&v)[Q], double (*s_red)[kMa
     __syncthreads();
 }
 
+// block_reduce over the first nthr threads only (a multiple of 32), synchronising on the
+// named barrier `bar` instead of the whole block.
+template <int Q>
+__device__ __forceinline__ void group_reduce(double (&v)[Q], double (*s_red)[kMaxQ], int tid, int nthr, int bar)
+{
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+        for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) s_red[warp][q] = v[q];
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthr) : "memory");
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            double x = lane < nw ? s_red[lane][q] : 0.0;
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            v[q] = x;
+        }
+    }
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthr) : "memory");
+}
+
 // ---------------------------------------------------------------- lattice tiling and potential
 
 // Work units are (y tile, z plane) pairs in tile-major order, U = nby * N of them.

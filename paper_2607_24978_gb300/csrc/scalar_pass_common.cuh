@@ -24,6 +24,24 @@ __device__ __forceinline__ void pass_coefficients(const double a_old, const doub
     s_coef[3] = a_new;
 }
 
+// The same prefactors computed by lanes 0 of warps 0, 1 and 2 at once (one pow each):
+// for kernels that evaluate them once per work item.  Needs at least 65 threads.
+__device__ __forceinline__ void pass_coefficients_warps(int tid, const double a_old, const double b_old,
+                                                        const double d, const double alpha, const double dx,
+                                                        const bool expand, double* s_coef)
+{
+    if (tid != 0 && tid != 32 && tid != 64) return;
+    const double a_new = expand ? a_old + d * b_old : a_old;
+    if (tid == 0) {
+        s_coef[0] = d * pow(0.5 * (a_old + a_new), alpha - 3.0);
+        s_coef[3] = a_new;
+    } else if (tid == 32) {
+        s_coef[1] = pow(a_new, 1.0 + alpha) / (dx * dx);
+    } else {
+        s_coef[2] = pow(a_new, 3.0 + alpha);
+    }
+}
+
 // Kick of one own-row vector of a plane.  S*[f] point at row (r+1) of the centre
 // (Sc), lower (Szm) and upper (Szp) planes of field f; rows r and r+2 of the
 // centre plane are Sc -/+ N.  Writes pi_out and accumulates K, G, V.

@@ -16,7 +16,9 @@
 // neighbour vectors from the ring.  With three ring slots the drift of plane j+1 never
 // touches the slot the kick of plane j-1 reads, so one consumer barrier per plane
 // suffices.  Halo-row drift work is spread evenly over the consumer threads.  All
-// mbarrier waits are bounded.
+// mbarrier waits are bounded.  (The ensemble kernel runs the same protocol through the
+// shared steps of tma_pipeline.cuh; this kernel keeps its own inline copy, which measured
+// about 2% faster on the 256^3 two-field pass than the version built on those steps.)
 
 template <typename T, int NF, bool KAHAN, int VW, int S>
 __global__ void __launch_bounds__(512, 1) k_scalar_pass_tma(const ScalarPassArgs<T> A)

@@ -19,12 +19,23 @@
 //                k the direction normal to P (the link derivative of sum phi Ebar.Bbar)
 //     W_i(n)   = (phi(n) Bbar_i(n) + phi(n+i) Bbar_i(n+i)) / 2
 //
-// Two launches per stage.  k_u1_helpers stores, per site, Bbar_k, its rate and
-// X_k = phi Ebar_k; k_u1_stage gathers the forces from them, performs
-// k <- A k + h F(y), y <- y + B k for all eight degrees of freedom per site, and
-// reduces the energies of the old state (FP64 across threads and blocks, fixed
-// order); the last block advances a, a' and their auxiliaries.  k_u1_gauss reduces
-// the lattice Gauss charge div-[a^(1-alpha) E + g W] for the diagnostics.
+// Two launches per stage.  k_u1_plaquettes evaluates every plaquette once: for the
+// plaquette P_k(n) with normal k (spanned by k1 = k+1, k2 = k+2, lower corner n) it
+// stores sin P_k, cos P_k * dP_k/dt and Z_k = cos P_k * (sum of X_k = phi Ebar_k over
+// the plaquette's four corners), and reduces the magnetic energy 2 sin^2(P_k / 2)
+// (= 1 - cos P_k without cancellation at small angles).  k_u1_stage gathers the forces
+// from those fields inside the 3x3x3 neighbourhood of each site (clover averages, the
+// magnetic curl, the Chern-Simons sums), performs k <- A k + h F(y), y <- y + B k for
+// the eight degrees of freedom of the site, and reduces the other energies of the old
+// state (FP64 across threads and blocks, fixed order); its last block advances a, a' and
+// their auxiliaries.  k_u1_gauss reduces the lattice Gauss charge
+// div-[a^(1-alpha) E + g W] for the diagnostics.
+//
+// Work decomposition (all three kernels): block b owns a 32 x 8 tile in (x, y) of the
+// planes [bz DZ, bz DZ + DZ); thread (lane, warp) owns column x = 32 bx + lane of row
+// y = 8 by + warp and marches up the planes, so most y and z neighbours it gathers were
+// loaded by its own block shortly before (L1 hits).  Linear indices fit 32 bits for
+// N <= 1536; coordinates and their periodic neighbours are formed once per site.
 #include <math.h>
 
 #include "cl_internal.cuh"
@@ -32,89 +43,123 @@
 
 namespace clk {
 
-struct Site {
-    int x, y, z, N;
-    __device__ __forceinline__ Site(int64_t n, int N_) : N(N_)
+constexpr int kU1DZ = 8;  // planes per block
+
+// The tile of this block and this thread's column and row in it.
+struct U1Tile {
+    uint32_t x, y, z0, z1;
+    bool active;
+    __device__ __forceinline__ explicit U1Tile(uint32_t N)
     {
-        x = (int)(n % N_);
-        y = (int)((n / N_) % N_);
-        z = (int)(n / ((int64_t)N_ * N_));
+        const uint32_t ntx = (N + 31) / 32, nty = (N + 7) / 8;
+        uint32_t b = blockIdx.x;
+        const uint32_t bx = b % ntx;
+        b /= ntx;
+        const uint32_t by = b % nty, bz = b / nty;
+        x = bx * 32 + (threadIdx.x & 31);
+        y = by * 8 + (threadIdx.x >> 5);
+        z0 = bz * kU1DZ;
+        z1 = z0 + kU1DZ < N ? z0 + kU1DZ : N;
+        active = x < N && y < N;
     }
-    __device__ __forceinline__ int64_t at(int dx_, int dy_, int dz_) const
+};
+
+// A site and its periodic neighbours at offsets -1, 0, +1 along each axis.
+struct Nbhd {
+    uint32_t N, cx[3], cy[3], cz[3];
+    __device__ __forceinline__ Nbhd(uint32_t x, uint32_t y, uint32_t z, uint32_t N_) : N(N_)
     {
-        int xx = x + dx_, yy = y + dy_, zz = z + dz_;
-        xx = xx < 0 ? xx + N : (xx >= N ? xx - N : xx);
-        yy = yy < 0 ? yy + N : (yy >= N ? yy - N : yy);
-        zz = zz < 0 ? zz + N : (zz >= N ? zz - N : zz);
-        return ((int64_t)zz * N + yy) * N + xx;
+        cx[0] = x == 0 ? N_ - 1 : x - 1; cx[1] = x; cx[2] = x + 1 == N_ ? 0 : x + 1;
+        cy[0] = y == 0 ? N_ - 1 : y - 1; cy[1] = y; cy[2] = y + 1 == N_ ? 0 : y + 1;
+        cz[0] = z == 0 ? N_ - 1 : z - 1; cz[1] = z; cz[2] = z + 1 == N_ ? 0 : z + 1;
     }
-    // site shifted by s along direction d, then by t along e
-    __device__ __forceinline__ int64_t sh(int d, int s, int e = 0, int t = 0) const
+    // site at offset o (each component -1, 0 or +1)
+    __device__ __forceinline__ uint32_t at(const int (&o)[3]) const
     {
-        int o[3] = {0, 0, 0};
-        o[d] += s;
-        o[e] += t;
-        return at(o[0], o[1], o[2]);
+        return (cz[o[2] + 1] * N + cy[o[1] + 1]) * N + cx[o[0] + 1];
+    }
+};
+
+// Offset vector: sa e_da + sb e_db + sc e_dc (direction indices 0..2, signs -1, 0, +1).
+struct Off {
+    int o[3];
+    __device__ __forceinline__ Off(int da = 0, int sa = 0, int db = 0, int sb = 0, int dc = 0, int sc = 0)
+    {
+        o[0] = o[1] = o[2] = 0;
+        o[da] += sa;
+        o[db] += sb;
+        o[dc] += sc;
     }
 };
 
 template <typename T>
-__device__ __forceinline__ T plaq(const U1Args<T>& A, const Site& s, int64_t q, int i, int j)
+__global__ void __launch_bounds__(256) k_u1_plaquettes(const U1Args<T> A)
 {
-    const Site sq(q, s.N);
-    return A.th_in[i][q] + A.th_in[j][sq.sh(i, 1)] - A.th_in[i][sq.sh(j, 1)] - A.th_in[j][q];
-}
-
-template <typename T>
-__device__ __forceinline__ T plaq_rate(const U1Args<T>& A, const Site& s, int64_t q, int i, int j)
-{
-    const Site sq(q, s.N);
-    return (T)A.dx * (A.E_in[i][q] + A.E_in[j][sq.sh(i, 1)] - A.E_in[i][sq.sh(j, 1)] - A.E_in[j][q]);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_u1_helpers(const U1Args<T> A)
-{
-    const int N = A.N;
-    const int64_t V = (int64_t)N * N * N;
-    const T inv4dx2 = (T)(0.25 / (A.dx * A.dx));
-    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < V; m += (int64_t)gridDim.x * blockDim.x) {
-        const Site s(m, N);
-        const T ph = A.phi_in[m];
+    __shared__ double s_red[32][kMaxQ];
+    const uint32_t N = (uint32_t)A.N;
+    const T dx = (T)A.dx;
+    Acc<T> accGB;
+    const U1Tile tile(N);
+    for (uint32_t z = tile.z0; z < tile.z1; ++z) {
+        if (!tile.active) break;
+        const uint32_t n = (z * N + tile.y) * N + tile.x;
+        const Nbhd s(tile.x, tile.y, z, N);
+        // every load of the site precedes its stores (outputs may not be assumed disjoint
+        // from inputs by the compiler, so an early store would serialise the loads)
+        T o_s[3], o_r[3], o_z[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
-            const int64_t q[4] = {m, s.sh(k1, -1), s.sh(k2, -1), s.sh(k1, -1, k2, -1)};
-            T b = (T)0, bd = (T)0;
+            const uint32_t n1 = s.at(Off(k1, 1).o), n2 = s.at(Off(k2, 1).o), n12 = s.at(Off(k1, 1, k2, 1).o);
+            const T P = A.th_in[k1][n] + A.th_in[k2][n1] - A.th_in[k1][n2] - A.th_in[k2][n];
+            const T R = dx * (A.E_in[k1][n] + A.E_in[k2][n1] - A.E_in[k1][n2] - A.E_in[k2][n]);
+            T sp, cp;
+            if constexpr (sizeof(T) == 4) sincosf(P, &sp, &cp);
+            else sincos(P, &sp, &cp);
+            // X_k = phi Ebar_k at the four corners; Ebar_k(q) = (E_k(q) + E_k(q - e_k)) / 2
+            const uint32_t m0 = s.at(Off(k, -1).o), m1 = s.at(Off(k1, 1, k, -1).o), m2 = s.at(Off(k2, 1, k, -1).o),
+                           m12 = s.at(Off(k1, 1, k2, 1, k, -1).o);
+            const T q = A.phi_in[n] * (A.E_in[k][n] + A.E_in[k][m0]) + A.phi_in[n1] * (A.E_in[k][n1] + A.E_in[k][m1]) +
+                        A.phi_in[n2] * (A.E_in[k][n2] + A.E_in[k][m2]) +
+                        A.phi_in[n12] * (A.E_in[k][n12] + A.E_in[k][m12]);
+            o_s[k] = sp;
+            o_r[k] = cp * R;
+            o_z[k] = cp * ((T)0.5 * q);
+            const T sh = sin((T)0.5 * P);
+            accGB.add((T)2 * sh * sh);
+        }
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const T p = plaq(A, s, q[c], k1, k2);
-                b += sin(p);
-                bd += cos(p) * plaq_rate(A, s, q[c], k1, k2);
-            }
-            A.Bbar[k][m] = b * inv4dx2;
-            A.Bdot[k][m] = bd * inv4dx2;
-            A.X[k][m] = ph * (T)0.5 * (A.E_in[k][m] + A.E_in[k][s.sh(k, -1)]);
+        for (int k = 0; k < 3; ++k) {
+            A.sP[k][n] = o_s[k];
+            A.rP[k][n] = o_r[k];
+            A.Z[k][n] = o_z[k];
         }
     }
+    double v[1] = {accGB.value()};
+    block_reduce<1>(v, s_red, threadIdx.x, blockDim.x);
+    if (threadIdx.x == 0) A.partials[(size_t)gridDim.x * kMaxQ + blockIdx.x] = v[0];
 }
 
-// Sum of X_k over the four corners q, q+e_k1, q+e_k2, q+e_k1+e_k2 of the plaquette at q.
+// Clover sum of f_k over the four plaquettes with normal k around site q (offset oq).
 template <typename T>
-__device__ __forceinline__ T corner_sum(const U1Args<T>& A, int64_t q, int k, int k1, int k2)
+__device__ __forceinline__ T clover(const T* const f, const Nbhd& s, const Off& oq, int k)
 {
-    const Site sq(q, A.N);
-    return A.X[k][q] + A.X[k][sq.sh(k1, 1)] + A.X[k][sq.sh(k2, 1)] + A.X[k][sq.sh(k1, 1, k2, 1)];
+    const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+    Off b = oq, c = oq;
+    b.o[k1] -= 1;
+    c.o[k2] -= 1;
+    Off d = b;
+    d.o[k2] -= 1;
+    return (f[s.at(oq.o)] + f[s.at(b.o)]) + (f[s.at(c.o)] + f[s.at(d.o)]);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_u1_stage(const U1Args<T> A)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_u1_stage(const U1Args<T> A)
 {
     __shared__ double s_coef[6];
     __shared__ double s_red[32][kMaxQ];
     __shared__ int s_last;
-    const int N = A.N;
-    const int64_t V = (int64_t)N * N * N;
+    const uint32_t N = (uint32_t)A.N, V = N * N * N;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const bool first = (A.flags & P_FIRST_STAGE) != 0;
     const bool update = (A.flags & P_ENERGY_ONLY) == 0;
@@ -131,75 +176,75 @@ __global__ void __launch_bounds__(256) k_u1_stage(const U1Args<T> A)
     __syncthreads();
     const T c_dphi = (T)s_coef[0], cL = (T)s_coef[1], cV = (T)s_coef[2], cE = (T)s_coef[3], cfr = (T)s_coef[4];
     const T g = (T)A.g, ws2 = (T)A.ws2, dx = (T)A.dx, m2 = (T)A.m2, lam = (T)A.lam;
-    const T inv_dx3 = (T)(1.0 / (A.dx * A.dx * A.dx)), inv4dx = (T)(0.25 / A.dx);
+    const T inv_dx3 = (T)(1.0 / (A.dx * A.dx * A.dx)), inv4dx = (T)(0.25 / A.dx), inv4dx2 = (T)(0.25 / (A.dx * A.dx));
     const T h = (T)A.h, cA = (T)A.A, cB = (T)A.B;
-    Acc<T> accK, accG, accV, accKE, accGB;
+    Acc<T> accK, accG, accV, accKE;
 
-    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + tid; n < V; n += (int64_t)gridDim.x * blockDim.x) {
-        const Site s(n, N);
+    const U1Tile tile(N);
+    for (uint32_t z = tile.z0; z < tile.z1; ++z) {
+        if (!tile.active) break;
+        const uint32_t n = (z * N + tile.y) * N + tile.x;
+        const Nbhd s(tile.x, tile.y, z, N);
         const T ph = A.phi_in[n], pv = A.pi_in[n];
         // scalar sector
-        const T pxp = A.phi_in[s.sh(0, 1)], pxm = A.phi_in[s.sh(0, -1)];
-        const T pyp = A.phi_in[s.sh(1, 1)], pym = A.phi_in[s.sh(1, -1)];
-        const T pzp = A.phi_in[s.sh(2, 1)], pzm = A.phi_in[s.sh(2, -1)];
+        const T pxp = A.phi_in[s.at(Off(0, 1).o)], pxm = A.phi_in[s.at(Off(0, -1).o)];
+        const T pyp = A.phi_in[s.at(Off(1, 1).o)], pym = A.phi_in[s.at(Off(1, -1).o)];
+        const T pzp = A.phi_in[s.at(Off(2, 1).o)], pzm = A.phi_in[s.at(Off(2, -1).o)];
         const T lap = ((pxp + pxm) + (pyp + pym) + (pzp + pzm)) - (T)6 * ph;
         const T dV = ph * (m2 + lam * ph * ph);
         T eb = (T)0, e2 = (T)0;
-        T Ecur[3];
+        T Ecur[3], Bn[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             Ecur[k] = A.E_in[k][n];
-            eb += (T)0.5 * (Ecur[k] + A.E_in[k][s.sh(k, -1)]) * A.Bbar[k][n];
+            Bn[k] = inv4dx2 * clover(A.sP[k], s, Off(), k);
+            eb += (T)0.5 * (Ecur[k] + A.E_in[k][s.at(Off(k, -1).o)]) * Bn[k];
             e2 += Ecur[k] * Ecur[k];
         }
         const T F_phi = c_dphi * pv;
         const T F_pi = cL * lap - cV * dV + ws2 * g * eb;
-        T gb = (T)0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = i + 1; j < 3; ++j) gb += (T)1 - cos(plaq(A, s, n, i, j));
         accK.add(pv * pv);
         accG.add((pxp - ph) * (pxp - ph) + (pyp - ph) * (pyp - ph) + (pzp - ph) * (pzp - ph));
         accV.add(ph * ph * ((T)0.5 * m2 + (T)0.25 * lam * ph * ph));
         accKE.add(e2);
-        accGB.add(gb);
         if (!update) continue;
 
         // link forces
-        T F_th[3], F_E[3];
+        T F_E[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const int ip = (i + 1) % 3, im = (i + 2) % 3;
-            // magnetic: sum_{j != i} sin theta_ij(n) - sin theta_ij(n - j), theta_ji = -theta_ij
-            T mag = sin(plaq(A, s, n, i, ip)) - sin(plaq(A, s, s.sh(ip, -1), i, ip)) -
-                    sin(plaq(A, s, n, im, i)) + sin(plaq(A, s, s.sh(im, -1), im, i));
-            // Chern-Simons: plaquettes (i, i+1) normal to i+2 and (i+2, i) normal to i+1
-            const int64_t qa = s.sh(ip, -1), qb = s.sh(im, -1);
-            const T cs = cos(plaq(A, s, n, i, ip)) * corner_sum(A, n, im, i, ip) -
-                         cos(plaq(A, s, qa, i, ip)) * corner_sum(A, qa, im, i, ip) +
-                         cos(plaq(A, s, qb, im, i)) * corner_sum(A, qb, ip, im, i) -
-                         cos(plaq(A, s, n, im, i)) * corner_sum(A, n, ip, im, i);
-            const int64_t ni = s.sh(i, 1);
-            const T wdot = (T)0.5 * (F_phi * A.Bbar[i][n] + ph * A.Bdot[i][n] +
-                                     c_dphi * A.pi_in[ni] * A.Bbar[i][ni] + A.phi_in[ni] * A.Bdot[i][ni]);
+            // magnetic: sum_{j != i} sin theta_ij(n) - sin theta_ij(n - j); theta_{i,ip} has normal im,
+            // theta_{im,i} normal ip
+            const T mag = (A.sP[im][n] - A.sP[im][s.at(Off(ip, -1).o)]) - (A.sP[ip][n] - A.sP[ip][s.at(Off(im, -1).o)]);
+            // Chern-Simons: the four plaquettes through the link
+            const T cs = (A.Z[im][n] - A.Z[im][s.at(Off(ip, -1).o)]) + (A.Z[ip][s.at(Off(im, -1).o)] - A.Z[ip][n]);
+            // W_i' from the clover fields at n and n + i
+            const Off oi(i, 1);
+            const uint32_t ni = s.at(oi.o);
+            const T Bdn = inv4dx2 * clover(A.rP[i], s, Off(), i);
+            const T Bni = inv4dx2 * clover(A.sP[i], s, oi, i);
+            const T Bdni = inv4dx2 * clover(A.rP[i], s, oi, i);
+            const T wdot = (T)0.5 * (F_phi * Bn[i] + ph * Bdn + c_dphi * A.pi_in[ni] * Bni + A.phi_in[ni] * Bdni);
             F_E[i] = cE * (-cE * mag * inv_dx3 + g * (cs * inv4dx - wdot)) - cfr * Ecur[i];
-            F_th[i] = dx * Ecur[i];
         }
-        // 2N Runge-Kutta update of the eight degrees of freedom of this site
-        const T F[8] = {F_phi, F_pi, F_th[0], F_th[1], F_th[2], F_E[0], F_E[1], F_E[2]};
+        // 2N Runge-Kutta update of the eight degrees of freedom of this site (all loads
+        // first, then the stores)
+        const T F[8] = {F_phi, F_pi, dx * Ecur[0], dx * Ecur[1], dx * Ecur[2], F_E[0], F_E[1], F_E[2]};
         const T y[8] = {ph, pv, A.th_in[0][n], A.th_in[1][n], A.th_in[2][n], Ecur[0], Ecur[1], Ecur[2]};
+        T kq[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) kq[q] = first ? h * F[q] : cA * A.k_in[q][n] + h * F[q];
         T* out[8] = {A.phi_out, A.pi_out, A.th_out[0], A.th_out[1], A.th_out[2], A.E_out[0], A.E_out[1], A.E_out[2]};
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const T kq = first ? h * F[q] : cA * A.k_in[q][n] + h * F[q];
-            A.k_out[q][n] = kq;
-            out[q][n] = y[q] + cB * kq;
+            A.k_out[q][n] = kq[q];
+            out[q][n] = y[q] + cB * kq[q];
         }
     }
 
     // ---- block partials; last block: energies of the old state and the (a, a') stage ----
-    double v[kMaxQ] = {accK.value(), accG.value(), accV.value(), accKE.value(), accGB.value()};
+    double v[kMaxQ] = {accK.value(), accG.value(), accV.value(), accKE.value(), 0.0};
     block_reduce<kMaxQ>(v, s_red, tid, nthr);
     if (tid == 0) {
 #pragma unroll
@@ -212,9 +257,11 @@ __global__ void __launch_bounds__(256) k_u1_stage(const U1Args<T> A)
     if (!s_last) return;
     __threadfence();
     double w[kMaxQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int b = tid; b < (int)gridDim.x; b += nthr)
+    for (int b = tid; b < (int)gridDim.x; b += nthr) {
 #pragma unroll
-        for (int q = 0; q < kMaxQ; ++q) w[q] += __ldcg(&A.partials[(size_t)b * kMaxQ + q]);
+        for (int q = 0; q < kMaxQ - 1; ++q) w[q] += __ldcg(&A.partials[(size_t)b * kMaxQ + q]);
+        w[kMaxQ - 1] += __ldcg(&A.partials[(size_t)gridDim.x * kMaxQ + b]);  // plaquette launch, same grid
+    }
     block_reduce<kMaxQ>(w, s_red, tid, nthr);
     if (tid == 0) {
         DevScal* S = A.scal;
@@ -276,20 +323,26 @@ __global__ void __launch_bounds__(256) k_u1_gauss(const U1Args<T> A)
 {
     __shared__ double s_red[32][kMaxQ];
     __shared__ int s_last;
-    const int N = A.N;
-    const int64_t V = (int64_t)N * N * N;
+    const uint32_t N = (uint32_t)A.N;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const double ca = pow(A.scal->a, 1.0 - A.alpha);
+    const double b4 = 0.25 / (A.dx * A.dx);
     double gmax = 0.0, smax = 0.0;
-    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + tid; n < V; n += (int64_t)gridDim.x * blockDim.x) {
-        const Site s(n, N);
+    const U1Tile tile(N);
+    for (uint32_t z = tile.z0; z < tile.z1; ++z) {
+        if (!tile.active) break;
+        const uint32_t n = (z * N + tile.y) * N + tile.x;
+        const Nbhd s(tile.x, tile.y, z, N);
         double G = 0.0, sc = 0.0;
+#pragma unroll
         for (int i = 0; i < 3; ++i) {
-            const int64_t np = s.sh(i, 1), nm = s.sh(i, -1);
-            const double Pn = ca * (double)A.E_in[i][n] +
-                              A.g * 0.5 * ((double)A.phi_in[n] * A.Bbar[i][n] + (double)A.phi_in[np] * A.Bbar[i][np]);
-            const double Pm = ca * (double)A.E_in[i][nm] +
-                              A.g * 0.5 * ((double)A.phi_in[nm] * A.Bbar[i][nm] + (double)A.phi_in[n] * A.Bbar[i][n]);
+            const Off op(i, 1), om(i, -1);
+            const uint32_t np = s.at(op.o), nm = s.at(om.o);
+            const double Bn = b4 * (double)clover(A.sP[i], s, Off(), i);
+            const double Bp = b4 * (double)clover(A.sP[i], s, op, i);
+            const double Bm = b4 * (double)clover(A.sP[i], s, om, i);
+            const double Pn = ca * (double)A.E_in[i][n] + A.g * 0.5 * ((double)A.phi_in[n] * Bn + (double)A.phi_in[np] * Bp);
+            const double Pm = ca * (double)A.E_in[i][nm] + A.g * 0.5 * ((double)A.phi_in[nm] * Bm + (double)A.phi_in[n] * Bn);
             G += Pn - Pm;
             sc += fabs(Pn) + fabs(Pm);
         }
@@ -330,18 +383,18 @@ __global__ void __launch_bounds__(256) k_u1_gauss(const U1Args<T> A)
     A.scal->counter = 0u;
 }
 
+// Grid of all three kernels (the stage kernel reads the plaquette kernel's partials by
+// block index, so both use this grid).
 static int u1_grid(int N)
 {
-    const int64_t V = (int64_t)N * N * N;
-    int64_t b = (V + 255) / 256;
-    return (int)(b < 152 * 16 ? b : 152 * 16);
+    return ((N + 31) / 32) * ((N + 7) / 8) * ((N + kU1DZ - 1) / kU1DZ);
 }
 
 template <typename T>
 static cudaError_t launch_u1_t(const U1Args<T>& A, int what, cudaStream_t s)
 {
     const int grid = u1_grid(A.N);
-    if (what == 0) k_u1_helpers<T><<<grid, 256, 0, s>>>(A);
+    if (what == 0) k_u1_plaquettes<T><<<grid, 256, 0, s>>>(A);
     else if (what == 1) k_u1_stage<T><<<grid, 256, 0, s>>>(A);
     else k_u1_gauss<T><<<grid, 256, 0, s>>>(A);
     return cudaGetLastError();

@@ -34,3 +34,16 @@ def gauge_state(N, seed=0, theta_amp=1e-1, e_amp=1e-1):
     """Random link angles theta_i and electric fields E_i, shape (3, N, N, N)."""
     g = rng(seed)
     return theta_amp * g.standard_normal((3, N, N, N)), e_amp * g.standard_normal((3, N, N, N))
+
+
+def solenoidal_field(N, seed=0, amp=1e-1, dtype=np.float64):
+    """Random link field E_i(n) with zero backward-difference divergence on the periodic
+    lattice: E = curl- v (E_i = [v_k(n) - v_k(n - e_j)] - [v_j(n) - v_j(n - e_k)], (i, j, k)
+    cyclic, direction 0 the fastest index) of a white-noise v, scaled to rms amp."""
+    v = rng(seed).standard_normal((3, N, N, N)).astype(dtype)
+
+    def back(f, d):  # f(n) - f(n - e_d)
+        return f - np.roll(f, 1, axis=2 - d)
+
+    E = np.stack([back(v[(i + 2) % 3], (i + 1) % 3) - back(v[(i + 1) % 3], (i + 2) % 3) for i in range(3)])
+    return (amp / max(float(np.sqrt(np.mean(E * E))), 1e-300)) * E

@@ -205,8 +205,23 @@ def test_ensemble_per_member_calls(cl):
         k, d, c = g.cl_spectrum(cl.CL_FIELD_PHI0, member=1)
         assert len(k) == int(math.floor(math.sqrt(3.0) * 6 + 0.5)) + 1
         with pytest.raises(cl.CLError):
-            g.cl_set_option(cl.CL_OPT_STAGES, 3)
+            g.cl_set_option(cl.CL_OPT_STAGES, 5)  # ensembles take 2..4 TMA stages
     with pytest.raises(cl.CLError):
         cl.Lattice(8, 1.0, 1, cl.CL_PREC_FP64, cl.CL_INT_RK3_3, member_N=[8, 8])
     with pytest.raises(cl.CLError):
         cl.Lattice(8, 1.0, 1, cl.CL_PREC_FP64, cl.CL_INT_VV2, member_N=[8, 1024])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ensemble_tma_and_direct_loaders_agree(cl, prec):
+    """The TMA-staged ensemble kernel (16-byte rows) and the direct loader do the same
+    per-site arithmetic on the same work items."""
+    params = member_params([16, 24, 12, 32], 1, seed=23)
+    a = run_ensemble(cl, params, 1, prec, 1, 0.02, 8)
+    b = run_ensemble(cl, params, 1, prec, 1, 0.02, 8, opts=((cl.CL_OPT_STAGES, -1),))
+    c = run_ensemble(cl, params, 1, prec, 1, 0.02, 8, opts=((cl.CL_OPT_STAGES, 2),))
+    for m in range(4):
+        for other in (b, c):
+            assert rel_l2(a[0][m], other[0][m]) < 1e-14
+            assert rel_l2(a[1][m], other[1][m]) < 1e-14
+            assert a[2][m]["rho"] == pytest.approx(other[2][m]["rho"], rel=1e-13)
