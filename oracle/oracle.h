@@ -103,6 +103,17 @@ void orc_vacuum(const orc_model* m, uint64_t seed, uint32_t member, double kcut,
 int  orc_spectrum(int N, double L, const double* f, double dn, int type,
                   double* k_out, double* delta_out, double* count_out, int cap);
 
+/* ---- convolutional surrogate layers (surrogate.c): periodic 3x3x3 convolutions ----
+ * x[n*C + c] site-major; W[(t*cout + co)*cin + ci], tap t = (tz*3 + ty)*3 + tx at offset
+ * (tx-1, ty-1, tz-1). */
+void orc_conv3d_fwd(int N, int cin, int cout, const double* x, const double* W, const double* b, double* y);
+void orc_conv3d_bwd_data(int N, int cin, int cout, const double* dy, const double* W, double* dx);
+void orc_conv3d_bwd_weight(int N, int cin, int cout, const double* x, const double* dy, double* dW, double* db);
+double orc_act(int act, double u);       /* 0 = ReLU, 1 = GELU (tanh form) */
+double orc_act_grad(int act, double u);
+void orc_act_array(int act, int64_t n, const double* u, double* h);
+void orc_act_bwd_array(int act, int64_t n, const double* u, const double* dh, double* du);
+
 #ifdef __cplusplus
 }
 #endif

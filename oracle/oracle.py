@@ -53,6 +53,15 @@ def lib():
                                  dp, dp, dp]
         L.orc_spectrum.restype = C.c_int
         L.orc_spectrum.argtypes = [C.c_int, C.c_double, dp, C.c_double, C.c_int, dp, dp, dp, C.c_int]
+        L.orc_conv3d_fwd.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, C.c_void_p, dp]
+        L.orc_conv3d_bwd_data.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp]
+        L.orc_conv3d_bwd_weight.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_void_p]
+        L.orc_act.restype = C.c_double
+        L.orc_act.argtypes = [C.c_int, C.c_double]
+        L.orc_act_grad.restype = C.c_double
+        L.orc_act_grad.argtypes = [C.c_int, C.c_double]
+        L.orc_act_array.argtypes = [C.c_int, C.c_int64, dp, dp]
+        L.orc_act_bwd_array.argtypes = [C.c_int, C.c_int64, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -191,3 +200,78 @@ def u1_rhs(model, st):
     out = [np.zeros((1, N, N, N)), np.zeros((1, N, N, N)), np.zeros((3, N, N, N)), np.zeros((3, N, N, N))]
     lib().orc_u1_rhs(C.byref(model), _c(st.phi), _c(st.pi), _c(st.links), _c(st.efield), _c(st.abt), *out)
     return out
+
+
+# ------------------------------------------------------------------ convolutional surrogate
+# Activations are arrays of shape (N, N, N, C) (site-major, channels last); weights
+# W[27, cout, cin] with tap t = (tz*3 + ty)*3 + tx at offset (tx-1, ty-1, tz-1), bias b[cout].
+RELU, GELU = 0, 1
+
+
+def conv3d_fwd(x, W, b=None):
+    N, cin = x.shape[0], x.shape[3]
+    cout = W.shape[1]
+    y = np.zeros((N, N, N, cout))
+    bb = None if b is None else _c(b)
+    lib().orc_conv3d_fwd(N, cin, cout, _c(x), _c(W), _ptr(bb), y)
+    return y
+
+
+def conv3d_bwd_data(dy, W):
+    N, cout = dy.shape[0], dy.shape[3]
+    cin = W.shape[2]
+    dx = np.zeros((N, N, N, cin))
+    lib().orc_conv3d_bwd_data(N, cin, cout, _c(dy), _c(W), dx)
+    return dx
+
+
+def conv3d_bwd_weight(x, dy):
+    N, cin, cout = x.shape[0], x.shape[3], dy.shape[3]
+    dW = np.zeros((27, cout, cin))
+    db = np.zeros(cout)
+    lib().orc_conv3d_bwd_weight(N, cin, cout, _c(x), _c(dy), dW, db.ctypes.data_as(C.c_void_p))
+    return dW, db
+
+
+def activation(act, u):
+    u = _c(u)
+    h = np.empty_like(u)
+    lib().orc_act_array(int(act), u.size, u, h)
+    return h
+
+
+def activation_bwd(act, u, dh):
+    u, dh = _c(u), _c(dh)
+    du = np.empty_like(u)
+    lib().orc_act_bwd_array(int(act), u.size, u, dh, du)
+    return du
+
+
+def surrogate_forward(x, layers, act=RELU):
+    """Network of periodic 3x3x3 convolutions: h_0 = x, h_{l+1} = act(conv_l(h_l)) for all but
+    the last layer, out = x[..., :cout_last] + conv_last(h_last) (the residual jump).
+    layers: list of (W, b).  Returns (out, cache) with cache = (inputs h_l, pre-activations u_l)."""
+    h, us, hs = _c(x), [], []
+    for i, (W, b) in enumerate(layers):
+        hs.append(h)
+        u = conv3d_fwd(h, W, b)
+        us.append(u)
+        h = activation(act, u) if i + 1 < len(layers) else u
+    cout = layers[-1][0].shape[1]
+    out = x[..., :cout] + h
+    return out, (hs, us)
+
+
+def surrogate_backward(cache, layers, g, act=RELU):
+    """Gradients of sum(out * g): returns (dx, [(dW_l, db_l)])."""
+    hs, us = cache
+    grads = [None] * len(layers)
+    du = _c(g)
+    for i in range(len(layers) - 1, -1, -1):
+        W = layers[i][0]
+        grads[i] = conv3d_bwd_weight(hs[i], du)
+        dh = conv3d_bwd_data(du, W)
+        du = activation_bwd(act, us[i - 1], dh) if i > 0 else dh
+    dx = du.copy()
+    dx[..., :g.shape[3]] += g
+    return dx, grads
