@@ -23,6 +23,10 @@ Other workloads (--workload; one JSON line each, same keys where they apply):
   ensemble  1024 independent lambda phi^4 lattices of sizes drawn from {32, 48, 64}^3,
             per-member vacuum amplitude lambda log-uniform in [1e-6, 1e-3], VV-2,
             FP32 + Kahan, one launch per pass for all members.
+  surrogate the convolutional surrogate at 128^3: 6 periodic 3x3x3 layers
+            (3 -> 48, 4 x 48 -> 48, 48 -> 2), BF16 on the tensor cores; forward and
+            forward + backward throughput, and the time of the 16 leapfrog steps one
+            forward replaces.
 """
 import argparse
 import json
@@ -340,6 +344,86 @@ def run_ensemble_workload(args, world, rank, local, cl, torch, stream, hbm_peak,
                              "steps": es[0]["step"]}}
 
 
+SG = dict(N=128, cin=3, cout=2, hidden=48, layers=6, K=16, seed=1234)
+
+
+def surrogate_flops(N, cin, cout, hidden, layers):
+    """Multiply-adds x 2 of one forward: 27 taps per input-output channel pair and site."""
+    pairs = cin * hidden + (layers - 2) * hidden * hidden + hidden * cout
+    return 2 * 27 * pairs * N ** 3
+
+
+def run_surrogate_workload(args, world, rank, local, cl, torch, stream, peak_tf, peak_src):
+    import numpy as np
+    c = SG
+    N = c["N"]
+    rg = np.random.default_rng(c["seed"])
+
+    def build(layers):
+        s = cl.Surrogate(N, c["cin"], c["cout"], c["hidden"], layers, cl.CL_ACT_RELU, cl.CL_SG_BF16,
+                         stream=stream.cuda_stream)
+        for l, (ci, co) in enumerate(s.shapes):
+            s.set_weights(l, rg.standard_normal((27, co, ci)) * math.sqrt(2.0 / (27 * ci)), 0.01 * rg.standard_normal(co))
+        return s
+
+    x = torch.randn(N ** 3 * c["cin"], device="cuda", dtype=torch.float32)
+    y = torch.empty(N ** 3 * c["cout"], device="cuda", dtype=torch.float32)
+    g = torch.randn(N ** 3 * c["cout"], device="cuda", dtype=torch.float32)
+
+    def time_it(fn, n):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3 / n
+
+    s6 = build(c["layers"])
+    s2 = build(2)
+    clk = Clocks(local)
+    with clk:
+        t6 = time_it(lambda: s6.forward(x, y), args.steps)
+        t2 = time_it(lambda: s2.forward(x, y), args.steps)
+        tfb = time_it(lambda: (s6.forward(x, y), s6.backward(g)), max(2, args.steps // 10))
+    launches = s6.last_launch_count()
+    s6.close()
+    s2.close()
+    # the leapfrog steps one forward replaces: K VV-2 steps, one field, FP32 + Kahan, 128^3
+    lat = cl.Lattice(N, 8.0 * math.pi * N / 256, 1, cl.CL_PREC_FP32_KAHAN, cl.CL_INT_VV2, alpha=1.0, kappa=0.1,
+                     dt=0.01, stream=stream.cuda_stream)
+    lat.cl_set_potential(cl.CL_POT_LPHI4, [1.0])
+    lat.cl_init_vacuum(c["seed"], 1e30, 1e-4, (1.0,), (0.0,))
+    lat.cl_step(20)
+    lat.cl_sync()
+    tl, _ = timed_steps(torch, lat, stream, 10 * c["K"])
+    tl = tl / 10
+    lat.close()
+    flops = surrogate_flops(N, c["cin"], c["cout"], c["hidden"], c["layers"])
+    tc_flops = 2 * 27 * c["hidden"] ** 2 * N ** 3
+    tc_s = (t6 - t2) / (c["layers"] - 2)
+    achieved = tc_flops / tc_s / 1e12
+    return {"metric": "surrogate forward TFLOP/s at 128^3 (6 layers, 48 channels, BF16)", "value": flops / t6 / 1e12,
+            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t6 * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "periodic 3x3x3 conv surrogate 3->48->48x4->2, ReLU, residual jump, 128^3, "
+                                   "BF16 tensor cores (FP32 accumulation); random weights",
+                       "flops_per_forward": flops, "l2": "activations (201 MB per hidden layer) larger than L2"},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tf, "traffic": None, "peak_source": peak_src,
+                         "kernel": "k_conv_tc<48> (one hidden layer; time = (6-layer - 2-layer forward) / 4)",
+                         "algorithmic_flops_per_launch": tc_flops},
+            "forward_backward": {"ms": tfb * 1e3, "tflops": 3 * flops / tfb / 1e12},
+            "leapfrog": {"steps": c["K"], "ms": tl * 1e3,
+                         "forward_over_leapfrog": t6 / tl},
+            "gpu_launches": launches, "clocks": clk.summary()}
+
+
 # ------------------------------------------------------------------ GPU arm
 def make_lattice(cl, precision, stream, args=None):
     g = cl.Lattice(N, L, 2, precision, cl.CL_INT_YOSHIDA4, expansion=True, alpha=ALPHA, kappa=KAPPA, dt=DT,
@@ -382,6 +466,13 @@ def run_gpu(args, world, rank, local):
     peaks = load_peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     peak_src = "of measured" if peaks else "of fallback"
+    if args.workload == "surrogate":
+        tf = peaks["bf16_tflops"] if peaks else 1900.0
+        line = run_surrogate_workload(args, world, rank, local, cl, torch, stream, tf,
+                                      "of measured" if peaks else "of fallback")
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     if args.workload != "preheat":
         fn = run_u1_workload if args.workload == "u1" else run_ensemble_workload
         line = fn(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src)
@@ -473,7 +564,7 @@ def main():
     ap.add_argument("--stages", type=int, default=None, help="override CL_OPT_STAGES")
     ap.add_argument("--by", type=int, default=None, help="override CL_OPT_TILE_BY")
     ap.add_argument("--dz", type=int, default=None, help="override CL_OPT_TILE_DZ")
-    ap.add_argument("--workload", default="preheat", choices=["preheat", "u1", "ensemble"],
+    ap.add_argument("--workload", default="preheat", choices=["preheat", "u1", "ensemble", "surrogate"],
                     help="preheat: the headline 256^3 two-field run; u1, ensemble: the other workloads")
     ap.add_argument("--members", type=int, default=None, help="ensemble size (default 1024)")
     args = ap.parse_args()

@@ -278,6 +278,57 @@ int64_t cl_last_launch_count(const cl_lattice* l);
 const char* cl_strerror(cl_status s);
 const char* cl_last_error(const cl_lattice* l);
 
+/* ------------------------------------------------------------------------------------
+ * Convolutional surrogate: a learned jump of the lattice state by a fixed number of
+ * leapfrog steps (the neural operator of the build's scope; the paper defines no learned
+ * component).  A stack of `layers` periodic 3x3x3 convolutions on an N^3 lattice:
+ *     h_0 = x,   h_{l+1} = act(conv_l(h_l))  (l < layers-1),
+ *     y = x[:, :out_channels] + conv_{layers-1}(h_{layers-1})          (residual jump)
+ * with conv_l(h)[n][co] = b_l[co] + sum_t sum_ci W_l[t][co][ci] h[n + o(t)][ci], tap
+ * t = (tz*3 + ty)*3 + tx at offset o(t) = (tx-1, ty-1, tz-1), periodic boundaries.
+ * Arrays are site-major with channels contiguous: x[n * in_channels + c], site
+ * n = (z*N + y)*N + x.  Weights W_l are FP32 [27][cout][cin], biases FP32 [cout].
+ *
+ * Precision CL_SG_BF16: the hidden C -> C layers run on the tensor cores (tcgen05, BF16
+ * operands, FP32 accumulation, activations stored in BF16), the thin first and last layers
+ * on CUDA cores in FP32 from BF16 activations; N must be a multiple of 16.
+ * CL_SG_FP32: every layer on CUDA cores in FP32 (reference mode).
+ * The handle owns all device memory; calls are ordered on its stream and synchronise
+ * when they copy to or from host memory. */
+enum { CL_ACT_RELU = 1, CL_ACT_GELU = 2 };
+enum { CL_SG_BF16 = 0, CL_SG_FP32 = 1 };
+
+typedef struct cl_surrogate cl_surrogate;
+
+typedef struct {
+    int32_t N;             /* sites per side                                              */
+    int32_t in_channels;   /* 1..3, e.g. phi, pi and a constant channel carrying a         */
+    int32_t out_channels;  /* 1..in_channels; the residual adds the first ones             */
+    int32_t hidden;        /* hidden width: 16, 32 or 48                                   */
+    int32_t layers;        /* convolutions, >= 2                                           */
+    int32_t activation;    /* CL_ACT_RELU or CL_ACT_GELU (tanh form)                       */
+    int32_t precision;     /* CL_SG_BF16 or CL_SG_FP32                                     */
+    int32_t reserved;      /* must be 0                                                    */
+    void* stream;          /* cudaStream_t for all work of the handle; NULL = own stream    */
+} cl_surrogate_params;
+
+/* Errors: CL_EINVAL (sizes, enums), CL_ENOMEM, CL_ECUDA.  Weights start at zero. */
+cl_status cl_surrogate_create(cl_surrogate** out, const cl_surrogate_params* p);
+void cl_surrogate_free(cl_surrogate* s);
+/* Copy layer `layer`'s weights W [27][cout][cin] and bias b [cout] (host FP32) in or out. */
+cl_status cl_surrogate_set_weights(cl_surrogate* s, int32_t layer, const float* W, const float* b);
+cl_status cl_surrogate_get_weights(cl_surrogate* s, int32_t layer, float* W, float* b);
+/* y = network(x): x holds N^3 * in_channels FP32 values, y N^3 * out_channels, both in host
+ * memory (on_device = 0) or device memory (1).  Keeps the activations for a backward call. */
+cl_status cl_surrogate_forward(cl_surrogate* s, const float* x, float* y, int32_t on_device);
+/* Gradients of sum(y * g) for the last forward's input: g holds N^3 * out_channels FP32
+ * values; dx (N^3 * in_channels, may be NULL) receives d/dx.  Weight and bias gradients stay
+ * on the device (cl_surrogate_get_grads).  Errors: CL_ESTATE without a preceding forward. */
+cl_status cl_surrogate_backward(cl_surrogate* s, const float* g, float* dx, int32_t on_device);
+cl_status cl_surrogate_get_grads(cl_surrogate* s, int32_t layer, float* dW, float* db);
+/* Kernel launches queued by the most recent forward or backward call. */
+int64_t cl_surrogate_last_launch_count(const cl_surrogate* s);
+
 #ifdef __cplusplus
 }
 #endif

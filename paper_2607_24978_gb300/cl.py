@@ -29,7 +29,11 @@ CL_OPT_GRAPH, CL_OPT_TILE_BY, CL_OPT_TILE_DZ, CL_OPT_STAGES = 0, 1, 2, 3
 EXPORTS = ["cl_init_lattice", "cl_free", "cl_set_potential", "cl_set_state", "cl_get_state", "cl_set_scalars",
            "cl_get_scalars", "cl_init_vacuum", "cl_step", "cl_sync", "cl_energies", "cl_spectrum",
            "cl_set_gauge_coupling", "cl_set_hubble_limit", "cl_set_option", "cl_last_launch_count", "cl_strerror", "cl_last_error",
-           "cl_fused_pass_noalloc"]
+           "cl_fused_pass_noalloc", "cl_surrogate_create", "cl_surrogate_free", "cl_surrogate_set_weights",
+           "cl_surrogate_get_weights", "cl_surrogate_forward", "cl_surrogate_backward", "cl_surrogate_get_grads",
+           "cl_surrogate_last_launch_count"]
+CL_ACT_RELU, CL_ACT_GELU = 1, 2
+CL_SG_BF16, CL_SG_FP32 = 0, 1
 
 
 class cl_lattice_params(C.Structure):
@@ -67,6 +71,12 @@ class cl_pass_noalloc_desc(C.Structure):
                 ("phi_in", C.c_void_p * 2), ("pi_in", C.c_void_p * 2), ("c_in", C.c_void_p * 2),
                 ("phi_out", C.c_void_p * 2), ("pi_out", C.c_void_p * 2), ("c_out", C.c_void_p * 2),
                 ("scalars", C.c_void_p), ("energies", C.c_void_p), ("stream", C.c_void_p)]
+
+
+class cl_surrogate_params(C.Structure):
+    _fields_ = [("N", C.c_int32), ("in_channels", C.c_int32), ("out_channels", C.c_int32), ("hidden", C.c_int32),
+                ("layers", C.c_int32), ("activation", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32),
+                ("stream", C.c_void_p)]
 
 
 class CLError(RuntimeError):
@@ -110,8 +120,20 @@ def lib():
         L.cl_last_error.argtypes = [C.c_void_p]
         L.cl_last_error.restype = C.c_char_p
         L.cl_fused_pass_noalloc.argtypes = [P(cl_pass_noalloc_desc)]
+        fp = P(C.c_float)
+        L.cl_surrogate_create.argtypes = [P(C.c_void_p), P(cl_surrogate_params)]
+        L.cl_surrogate_free.argtypes = [C.c_void_p]
+        L.cl_surrogate_free.restype = None
+        L.cl_surrogate_set_weights.argtypes = [C.c_void_p, C.c_int32, fp, fp]
+        L.cl_surrogate_get_weights.argtypes = [C.c_void_p, C.c_int32, fp, fp]
+        L.cl_surrogate_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
+        L.cl_surrogate_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
+        L.cl_surrogate_get_grads.argtypes = [C.c_void_p, C.c_int32, fp, fp]
+        L.cl_surrogate_last_launch_count.argtypes = [C.c_void_p]
+        L.cl_surrogate_last_launch_count.restype = C.c_int64
         for name in EXPORTS:
-            if name not in ("cl_free", "cl_last_launch_count", "cl_strerror", "cl_last_error"):
+            if name not in ("cl_free", "cl_last_launch_count", "cl_strerror", "cl_last_error", "cl_surrogate_free",
+                            "cl_surrogate_last_launch_count"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -275,3 +297,92 @@ def cl_fused_pass_noalloc(desc):
     s = lib().cl_fused_pass_noalloc(C.byref(desc))
     if s != CL_OK:
         raise CLError(s, "cl_fused_pass_noalloc")
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class Surrogate:
+    """Owns one cl_surrogate handle (see cl_surrogate_* in cl.h).  Host arrays are float32
+    numpy arrays; x has shape (N, N, N, in_channels), weights (27, cout, cin)."""
+
+    def __init__(self, N, in_channels=3, out_channels=2, hidden=48, layers=6, activation=CL_ACT_RELU,
+                 precision=CL_SG_BF16, stream=None):
+        p = cl_surrogate_params()
+        p.N, p.in_channels, p.out_channels, p.hidden = int(N), int(in_channels), int(out_channels), int(hidden)
+        p.layers, p.activation, p.precision, p.reserved = int(layers), int(activation), int(precision), 0
+        p.stream = C.c_void_p(int(stream)) if stream else None
+        h = C.c_void_p()
+        st = lib().cl_surrogate_create(C.byref(h), C.byref(p))
+        if st != CL_OK:
+            raise CLError(st, "cl_surrogate_create")
+        self.h = h
+        self.N, self.cin, self.cout, self.hidden, self.layers = int(N), int(in_channels), int(out_channels), int(
+            hidden), int(layers)
+        self.shapes = [((hidden if l else in_channels), (out_channels if l == layers - 1 else hidden))
+                       for l in range(layers)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cl_surrogate_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _chk(self, st, what):
+        if st != CL_OK:
+            raise CLError(st, what)
+
+    def set_weights(self, layer, W, b):
+        W = np.ascontiguousarray(W, dtype=np.float32)
+        b = np.ascontiguousarray(b, dtype=np.float32)
+        ci, co = self.shapes[layer]
+        if W.size != 27 * co * ci or b.size != co:
+            raise ValueError("layer %d takes W (27, %d, %d) and b (%d,)" % (layer, co, ci, co))
+        self._chk(lib().cl_surrogate_set_weights(self.h, int(layer), _fptr(W), _fptr(b)), "set_weights")
+
+    def get_weights(self, layer):
+        ci, co = self.shapes[layer]
+        W = np.empty((27, co, ci), np.float32)
+        b = np.empty(co, np.float32)
+        self._chk(lib().cl_surrogate_get_weights(self.h, int(layer), _fptr(W), _fptr(b)), "get_weights")
+        return W, b
+
+    def forward(self, x, out=None):
+        """x: (N, N, N, in_channels) float32 numpy array or CUDA tensor; returns y."""
+        n = self.N ** 3
+        xp, xdev, xk = _buffer(x, np.float32, n * self.cin)
+        if out is None:
+            out = np.empty((self.N, self.N, self.N, self.cout), np.float32) if not xdev else None
+        yp, ydev, yk = _buffer(out, np.float32, n * self.cout)
+        self._chk(lib().cl_surrogate_forward(self.h, xp, yp, xdev), "forward")
+        return out
+
+    def backward(self, g, want_dx=False):
+        n = self.N ** 3
+        gp, gdev, gk = _buffer(g, np.float32, n * self.cout)
+        dx = np.empty((self.N, self.N, self.N, self.cin), np.float32) if want_dx else None
+        self._chk(lib().cl_surrogate_backward(self.h, gp, dx.ctypes.data_as(C.c_void_p) if want_dx else None, gdev),
+                  "backward")
+        return dx
+
+    def grads(self, layer):
+        ci, co = self.shapes[layer]
+        dW = np.empty((27, co, ci), np.float32)
+        db = np.empty(co, np.float32)
+        self._chk(lib().cl_surrogate_get_grads(self.h, int(layer), _fptr(dW), _fptr(db)), "get_grads")
+        return dW, db
+
+    def last_launch_count(self):
+        return int(lib().cl_surrogate_last_launch_count(self.h))

@@ -1,0 +1,377 @@
+// C ABI of the convolutional surrogate: parameters, activations and gradients on the
+// device, and the order of the layer launches (surrogate_tc.cu, surrogate_cc.cu).
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "cl_internal.cuh"
+#include "surrogate_common.cuh"
+
+using namespace clk;
+
+struct cl_surrogate {
+    cl_surrogate_params p{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int nsm = 152;
+    int64_t V = 0;
+    std::vector<int> cin, cout;        // per layer
+    std::vector<float*> W, b;          // FP32 weights [27][cout][cin] and biases
+    std::vector<float*> dW, db;        // their gradients
+    std::vector<__nv_bfloat16*> wf;    // tensor-core layout of the hidden layers (forward)
+    std::vector<__nv_bfloat16*> wb;    // tensor-core layout of the adjoint (data gradient)
+    float* x = nullptr;                // last forward input (FP32, N^3 x in)
+    float* y = nullptr;                // output (FP32, N^3 x out)
+    float* g = nullptr;                // output gradient (FP32)
+    float* dx = nullptr;               // input gradient (FP32)
+    std::vector<void*> u;              // pre-activations of layers 0 .. layers-2 (BF16 or FP32)
+    void* du[2] = {nullptr, nullptr};  // gradient ping-pong (BF16 or FP32)
+    float* partial = nullptr;          // weight-gradient partials
+    int chunks = 1;
+    int* status = nullptr;
+    bool have_forward = false;
+    int64_t launches = 0;
+};
+
+namespace {
+
+bool bf16_mode(const cl_surrogate* s) { return s->p.precision == CL_SG_BF16; }
+size_t act_bytes(const cl_surrogate* s) { return bf16_mode(s) ? 2 : 4; }
+
+// Tensor-core layout of weights Wk[t][co][ci] (C x C): [t][ci/8][co/8][co%8][ci%8], BF16.
+void format_tc(const std::vector<float>& Wk, int C, std::vector<__nv_bfloat16>& out)
+{
+    const int KG = C / 8, NG = C / 8;
+    out.assign((size_t)27 * C * C, __float2bfloat16(0.f));
+    for (int t = 0; t < 27; ++t)
+        for (int co = 0; co < C; ++co)
+            for (int ci = 0; ci < C; ++ci) {
+                const size_t i = ((((size_t)t * KG + ci / 8) * NG + co / 8) * 8 + co % 8) * 8 + ci % 8;
+                out[i] = __float2bfloat16(Wk[((size_t)t * C + co) * C + ci]);
+            }
+}
+
+cl_status check(cudaError_t e) { return e == cudaSuccess ? CL_OK : CL_ECUDA; }
+
+cl_status read_status(cl_surrogate* s)
+{
+    int st = 0;
+    if (cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return CL_ECUDA;
+    if (st) {
+        cudaMemsetAsync(s->status, 0, sizeof(int), s->stream);
+        if (st & ST_TIMEOUT) return CL_ETIMEOUT;
+    }
+    return CL_OK;
+}
+
+int tc_grid(const cl_surrogate* s, int DZ)
+{
+    const int N = s->p.N;
+    const int units = (N / kSgTileX) * (N / kSgTileY) * ((N + DZ - 1) / DZ);
+    return units < s->nsm ? units : s->nsm;
+}
+
+constexpr int kTcDZ = 16;
+
+// Convolution of layer l (forward): in -> out with the input activation in_act.
+cl_status conv_forward(cl_surrogate* s, int l, const void* in, int in_bf16, int in_act, void* out, int out_bf16,
+                       const float* resid)
+{
+    const int last = (int)s->cin.size() - 1;
+    const bool tc = bf16_mode(s) && l > 0 && l < last;
+    if (tc) {
+        ConvTCArgs A{};
+        A.in = (const __nv_bfloat16*)in;
+        A.wfmt = s->wf[l];
+        A.bias = s->b[l];
+        A.out = (__nv_bfloat16*)out;
+        A.status = s->status;
+        A.N = s->p.N;
+        A.DZ = kTcDZ < s->p.N ? kTcDZ : s->p.N;
+        A.in_act = in_act;
+        ++s->launches;
+        return check(launch_conv_tc(s->p.hidden, A, tc_grid(s, A.DZ), s->stream));
+    }
+    ConvCCArgs A{};
+    A.in = in;
+    A.in_bf16 = in_bf16;
+    A.in_act = in_act;
+    A.cin = s->cin[l];
+    A.cout = s->cout[l];
+    A.w = s->W[l];
+    A.bias = s->b[l];
+    A.resid = resid;
+    A.resid_c = resid ? s->p.out_channels : 0;
+    A.resid_stride = s->p.in_channels;
+    A.out = out;
+    A.out_bf16 = out_bf16;
+    A.N = s->p.N;
+    ++s->launches;
+    return check(launch_conv_cc(A, s->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+void cl_surrogate_free(cl_surrogate* s)
+{
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (auto* p : s->W) cudaFree(p);
+    for (auto* p : s->b) cudaFree(p);
+    for (auto* p : s->dW) cudaFree(p);
+    for (auto* p : s->db) cudaFree(p);
+    for (auto* p : s->wf) cudaFree(p);
+    for (auto* p : s->wb) cudaFree(p);
+    for (auto* p : s->u) cudaFree(p);
+    cudaFree(s->du[0]);
+    cudaFree(s->du[1]);
+    cudaFree(s->x);
+    cudaFree(s->y);
+    cudaFree(s->g);
+    cudaFree(s->dx);
+    cudaFree(s->partial);
+    cudaFree(s->status);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+cl_status cl_surrogate_create(cl_surrogate** out, const cl_surrogate_params* p)
+{
+    if (!out) return CL_EINVAL;
+    *out = nullptr;
+    if (!p || p->reserved != 0 || p->N < 2 || p->N > 512 || p->in_channels < 1 || p->in_channels > 3 ||
+        p->out_channels < 1 || p->out_channels > p->in_channels || p->layers < 2 ||
+        (p->hidden != 16 && p->hidden != 32 && p->hidden != 48) ||
+        (p->activation != CL_ACT_RELU && p->activation != CL_ACT_GELU) ||
+        (p->precision != CL_SG_BF16 && p->precision != CL_SG_FP32))
+        return CL_EINVAL;
+    if (p->precision == CL_SG_BF16 && p->N % 16 != 0) return CL_EINVAL;
+    cl_surrogate* s = new (std::nothrow) cl_surrogate();
+    if (!s) return CL_ENOMEM;
+    s->p = *p;
+    s->V = (int64_t)p->N * p->N * p->N;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (p->stream) {
+        s->stream = (cudaStream_t)p->stream;
+    } else {
+        if (cudaStreamCreate(&s->stream) != cudaSuccess) {
+            delete s;
+            return CL_ECUDA;
+        }
+        s->own_stream = true;
+    }
+    const int L = p->layers;
+    bool ok = true;
+    for (int l = 0; l < L; ++l) {
+        const int ci = l == 0 ? p->in_channels : p->hidden;
+        const int co = l == L - 1 ? p->out_channels : p->hidden;
+        s->cin.push_back(ci);
+        s->cout.push_back(co);
+        float *w = nullptr, *bb = nullptr, *gw = nullptr, *gb = nullptr;
+        const size_t nw = (size_t)27 * co * ci;
+        ok = ok && cudaMalloc(&w, nw * 4) == cudaSuccess && cudaMalloc(&bb, co * 4) == cudaSuccess &&
+             cudaMalloc(&gw, nw * 4) == cudaSuccess && cudaMalloc(&gb, co * 4) == cudaSuccess;
+        s->W.push_back(w);
+        s->b.push_back(bb);
+        s->dW.push_back(gw);
+        s->db.push_back(gb);
+        if (ok) {
+            cudaMemset(w, 0, nw * 4);
+            cudaMemset(bb, 0, co * 4);
+        }
+        __nv_bfloat16 *f = nullptr, *fb = nullptr;
+        if (ok && p->precision == CL_SG_BF16 && l > 0 && l < L - 1)
+            ok = cudaMalloc(&f, nw * 2) == cudaSuccess && cudaMalloc(&fb, nw * 2) == cudaSuccess &&
+                 cudaMemset(f, 0, nw * 2) == cudaSuccess && cudaMemset(fb, 0, nw * 2) == cudaSuccess;
+        s->wf.push_back(f);
+        s->wb.push_back(fb);
+        if (l < L - 1) {
+            void* uu = nullptr;
+            ok = ok && cudaMalloc(&uu, (size_t)s->V * p->hidden * act_bytes(s)) == cudaSuccess;
+            s->u.push_back(uu);
+        }
+    }
+    s->chunks = conv_dw_chunks(p->N);
+    const size_t part = (size_t)s->chunks * (27 * (size_t)p->hidden * p->hidden + p->hidden);
+    ok = ok && cudaMalloc(&s->du[0], (size_t)s->V * p->hidden * act_bytes(s)) == cudaSuccess &&
+         cudaMalloc(&s->du[1], (size_t)s->V * p->hidden * act_bytes(s)) == cudaSuccess &&
+         cudaMalloc(&s->x, (size_t)s->V * p->in_channels * 4) == cudaSuccess &&
+         cudaMalloc(&s->y, (size_t)s->V * p->out_channels * 4) == cudaSuccess &&
+         cudaMalloc(&s->g, (size_t)s->V * p->out_channels * 4) == cudaSuccess &&
+         cudaMalloc(&s->dx, (size_t)s->V * p->in_channels * 4) == cudaSuccess &&
+         cudaMalloc(&s->partial, part * 4) == cudaSuccess && cudaMalloc(&s->status, sizeof(int)) == cudaSuccess &&
+         cudaMemset(s->status, 0, sizeof(int)) == cudaSuccess;
+    if (!ok || cudaDeviceSynchronize() != cudaSuccess) {
+        cl_surrogate_free(s);
+        return CL_ENOMEM;
+    }
+    *out = s;
+    return CL_OK;
+}
+
+cl_status cl_surrogate_set_weights(cl_surrogate* s, int32_t layer, const float* W, const float* b)
+{
+    if (!s || layer < 0 || layer >= (int)s->cin.size() || !W || !b) return CL_EINVAL;
+    const int ci = s->cin[layer], co = s->cout[layer];
+    const size_t nw = (size_t)27 * co * ci;
+    for (size_t i = 0; i < nw; ++i)
+        if (!isfinite(W[i])) return CL_EINVAL;
+    if (cudaMemcpyAsync(s->W[layer], W, nw * 4, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->b[layer], b, co * 4, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+        return CL_ECUDA;
+    if (s->wf[layer]) {
+        // forward layout, and the adjoint's: Wk[t][a][b] = W[26 - t][b][a]
+        std::vector<float> Wt(W, W + nw), Wa(nw);
+        for (int t = 0; t < 27; ++t)
+            for (int a = 0; a < co; ++a)
+                for (int c = 0; c < ci; ++c) Wa[((size_t)t * co + a) * ci + c] = W[((size_t)(26 - t) * co + c) * ci + a];
+        std::vector<__nv_bfloat16> f, fb;
+        format_tc(Wt, co, f);
+        format_tc(Wa, co, fb);
+        if (cudaMemcpyAsync(s->wf[layer], f.data(), nw * 2, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+            cudaMemcpyAsync(s->wb[layer], fb.data(), nw * 2, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+            return CL_ECUDA;
+    }
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? CL_OK : CL_ECUDA;
+}
+
+cl_status cl_surrogate_get_weights(cl_surrogate* s, int32_t layer, float* W, float* b)
+{
+    if (!s || layer < 0 || layer >= (int)s->cin.size() || !W || !b) return CL_EINVAL;
+    const size_t nw = (size_t)27 * s->cout[layer] * s->cin[layer];
+    if (cudaMemcpyAsync(W, s->W[layer], nw * 4, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b, s->b[layer], s->cout[layer] * 4, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+        return CL_ECUDA;
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? CL_OK : CL_ECUDA;
+}
+
+cl_status cl_surrogate_forward(cl_surrogate* s, const float* x, float* y, int32_t on_device)
+{
+    if (!s || !x || !y) return CL_EINVAL;
+    s->launches = 0;
+    const size_t nx = (size_t)s->V * s->p.in_channels * 4, ny = (size_t)s->V * s->p.out_channels * 4;
+    if (cudaMemcpyAsync(s->x, x, nx, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream) !=
+        cudaSuccess)
+        return CL_ECUDA;
+    const int L = (int)s->cin.size(), act = s->p.activation;
+    const int ab = bf16_mode(s) ? 1 : 0;
+    cl_status st = conv_forward(s, 0, s->x, 0, 0, s->u[0], ab, nullptr);
+    for (int l = 1; st == CL_OK && l < L - 1; ++l) st = conv_forward(s, l, s->u[l - 1], ab, act, s->u[l], ab, nullptr);
+    if (st == CL_OK) st = conv_forward(s, L - 1, s->u[L - 2], ab, act, s->y, 0, s->x);
+    if (st != CL_OK) return st;
+    if (cudaMemcpyAsync(y, s->y, ny, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream) !=
+        cudaSuccess)
+        return CL_ECUDA;
+    s->have_forward = true;
+    if (!on_device) return read_status(s);
+    return CL_OK;
+}
+
+cl_status cl_surrogate_backward(cl_surrogate* s, const float* g, float* dx, int32_t on_device)
+{
+    if (!s || !g) return CL_EINVAL;
+    if (!s->have_forward) return CL_ESTATE;
+    s->launches = 0;
+    const int L = (int)s->cin.size(), act = s->p.activation, C = s->p.hidden;
+    const int ab = bf16_mode(s) ? 1 : 0;
+    const size_t ng = (size_t)s->V * s->p.out_channels * 4;
+    if (cudaMemcpyAsync(s->g, g, ng, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream) !=
+        cudaSuccess)
+        return CL_ECUDA;
+    auto wgrad = [&](int l, const void* h, int h_bf16, int h_act, const void* gg, int g_bf16) {
+        ConvDWArgs A{};
+        A.h = h;
+        A.h_bf16 = h_bf16;
+        A.h_act = h_act;
+        A.g = gg;
+        A.g_bf16 = g_bf16;
+        A.cin = s->cin[l];
+        A.cout = s->cout[l];
+        A.N = s->p.N;
+        A.partial = s->partial;
+        A.chunks = s->chunks;
+        A.dW = s->dW[l];
+        A.db = s->db[l];
+        s->launches += 2;
+        return check(launch_conv_dw(A, s->stream));
+    };
+    // adjoint of layer l: from the gradient of its output (gin, cin' = cout_l) to the gradient
+    // of its input's pre-activation (gated by act'(gate)) or of the network input
+    auto dgrad = [&](int l, const void* gin, int gin_bf16, void* gout, int gout_bf16, const void* gate, int gate_bf16,
+                     int gate_act, const float* resid) {
+        if (ab && l > 0 && l < L - 1) {
+            ConvTCArgs A{};
+            A.in = (const __nv_bfloat16*)gin;
+            A.wfmt = s->wb[l];
+            A.gate = (const __nv_bfloat16*)gate;
+            A.gate_act = gate_act;
+            A.out = (__nv_bfloat16*)gout;
+            A.status = s->status;
+            A.N = s->p.N;
+            A.DZ = kTcDZ < s->p.N ? kTcDZ : s->p.N;
+            ++s->launches;
+            return check(launch_conv_tc(C, A, tc_grid(s, A.DZ), s->stream));
+        }
+        ConvCCArgs A{};
+        A.in = gin;
+        A.in_bf16 = gin_bf16;
+        A.cin = s->cout[l];
+        A.cout = s->cin[l];
+        A.w = s->W[l];
+        A.flip = 1;
+        A.gate = gate;
+        A.gate_bf16 = gate_bf16;
+        A.gate_act = gate_act;
+        A.resid = resid;
+        A.resid_c = resid ? s->p.out_channels : 0;
+        A.resid_stride = s->p.out_channels;
+        A.out = gout;
+        A.out_bf16 = gout_bf16;
+        A.N = s->p.N;
+        ++s->launches;
+        return check(launch_conv_cc(A, s->stream));
+    };
+    // last layer: input act(u_{L-2}), output gradient g (FP32)
+    cl_status st = wgrad(L - 1, s->u[L - 2], ab, act, s->g, 0);
+    int cur = 0;
+    if (st == CL_OK) st = dgrad(L - 1, s->g, 0, s->du[cur], ab, s->u[L - 2], ab, act, nullptr);
+    for (int l = L - 2; st == CL_OK && l >= 1; --l) {
+        st = wgrad(l, s->u[l - 1], ab, act, s->du[cur], ab);
+        if (st == CL_OK) st = dgrad(l, s->du[cur], ab, s->du[cur ^ 1], ab, s->u[l - 1], ab, act, nullptr);
+        cur ^= 1;
+    }
+    if (st == CL_OK) st = wgrad(0, s->x, 0, 0, s->du[cur], ab);
+    if (st == CL_OK && dx) {
+        // d/dx: adjoint of layer 0 plus the residual path (g on the first out_channels)
+        st = dgrad(0, s->du[cur], ab, s->dx, 0, nullptr, 0, 0, s->g);
+        if (st == CL_OK &&
+            cudaMemcpyAsync(dx, s->dx, (size_t)s->V * s->p.in_channels * 4,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+            st = CL_ECUDA;
+    }
+    if (st != CL_OK) return st;
+    return read_status(s);
+}
+
+cl_status cl_surrogate_get_grads(cl_surrogate* s, int32_t layer, float* dW, float* db)
+{
+    if (!s || layer < 0 || layer >= (int)s->cin.size() || !dW || !db) return CL_EINVAL;
+    const size_t nw = (size_t)27 * s->cout[layer] * s->cin[layer];
+    if (cudaMemcpyAsync(dW, s->dW[layer], nw * 4, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(db, s->db[layer], s->cout[layer] * 4, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+        return CL_ECUDA;
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? CL_OK : CL_ECUDA;
+}
+
+int64_t cl_surrogate_last_launch_count(const cl_surrogate* s) { return s ? s->launches : 0; }
+
+}  // extern "C"
