@@ -21,13 +21,18 @@ struct cl_surrogate {
     std::vector<int> cin, cout;        // per layer
     std::vector<float*> W, b;          // FP32 weights [27][cout][cin] and biases
     std::vector<float*> dW, db;        // their gradients
-    std::vector<__nv_bfloat16*> wf;    // tensor-core layout of the hidden layers (forward)
-    std::vector<__nv_bfloat16*> wb;    // tensor-core layout of the adjoint (data gradient)
+    std::vector<__nv_bfloat16*> wf;    // tensor-core layout of each layer (forward), BF16 mode
+    std::vector<__nv_bfloat16*> wb;    // tensor-core layout of the adjoint (data gradient), layers >= 1
+    std::vector<float*> bpad;          // biases zero-padded to the tensor-core output width
     float* x = nullptr;                // last forward input (FP32, N^3 x in)
     float* y = nullptr;                // output (FP32, N^3 x out)
     float* g = nullptr;                // output gradient (FP32)
     float* dx = nullptr;               // input gradient (FP32)
-    std::vector<void*> u;              // pre-activations of layers 0 .. layers-2 (BF16 or FP32)
+    // outputs of layers 0 .. layers-2: FP32 mode stores the pre-activations u_l; BF16 mode
+    // stores the activations h_l = act(u_l) (the next layer's input as is) and, for GELU,
+    // the pre-activations in upre (ReLU's derivative follows from h: h > 0 iff u > 0)
+    std::vector<void*> u;
+    std::vector<void*> upre;
     void* du[2] = {nullptr, nullptr};  // gradient ping-pong (BF16 or FP32)
     float* partial = nullptr;          // weight-gradient partials
     int chunks = 1;
@@ -41,17 +46,24 @@ namespace {
 bool bf16_mode(const cl_surrogate* s) { return s->p.precision == CL_SG_BF16; }
 size_t act_bytes(const cl_surrogate* s) { return bf16_mode(s) ? 2 : 4; }
 
-// Tensor-core layout of weights Wk[t][co][ci] (C x C): [t][ci/8][co/8][co%8][ci%8], BF16.
-void format_tc(const std::vector<float>& Wk, int C, std::vector<__nv_bfloat16>& out)
+// Tensor-core width of a channel count: 16, 32 or 48 (thin layers are zero-padded).
+int tc_width(int c) { return c <= 16 ? 16 : (c <= 32 ? 32 : 48); }
+
+// Tensor-core layout of weights Wk[t][co][ci] (co < CO, ci < CI real channels), padded to
+// CIp x COp, tap t = oz * 9 + t9: [t9][ci/8][oz][co/8][co%8][ci%8], BF16, zeros in the
+// padding (one MMA covers the three z taps of an (x, y) tap with N = 3 COp).
+void format_tc(const float* Wk, int CO, int CI, int COp, int CIp, std::vector<__nv_bfloat16>& out)
 {
-    const int KG = C / 8, NG = C / 8;
-    out.assign((size_t)27 * C * C, __float2bfloat16(0.f));
-    for (int t = 0; t < 27; ++t)
-        for (int co = 0; co < C; ++co)
-            for (int ci = 0; ci < C; ++ci) {
-                const size_t i = ((((size_t)t * KG + ci / 8) * NG + co / 8) * 8 + co % 8) * 8 + ci % 8;
-                out[i] = __float2bfloat16(Wk[((size_t)t * C + co) * C + ci]);
+    const int KG = CIp / 8, NG = COp / 8;
+    out.assign((size_t)27 * COp * CIp, __float2bfloat16(0.f));
+    for (int t = 0; t < 27; ++t) {
+        const int oz = t / 9, t9 = t % 9;
+        for (int co = 0; co < CO; ++co)
+            for (int ci = 0; ci < CI; ++ci) {
+                const size_t i = (((((size_t)t9 * KG + ci / 8) * 3 + oz) * NG + co / 8) * 8 + co % 8) * 8 + ci % 8;
+                out[i] = __float2bfloat16(Wk[((size_t)t * CO + co) * CI + ci]);
             }
+    }
 }
 
 cl_status check(cudaError_t e) { return e == cudaSuccess ? CL_OK : CL_ECUDA; }
@@ -80,22 +92,28 @@ constexpr int kTcDZ = 16;
 
 // Convolution of layer l (forward): in -> out with the input activation in_act.
 cl_status conv_forward(cl_surrogate* s, int l, const void* in, int in_bf16, int in_act, void* out, int out_bf16,
-                       const float* resid)
+                       const float* resid, int out_act = 0, void* out_pre = nullptr)
 {
-    const int last = (int)s->cin.size() - 1;
-    const bool tc = bf16_mode(s) && l > 0 && l < last;
-    if (tc) {
+    if (bf16_mode(s)) {  // every forward layer on the tensor cores
         ConvTCArgs A{};
-        A.in = (const __nv_bfloat16*)in;
+        A.in = in;
+        A.in_f32 = in_bf16 ? 0 : 1;
+        A.in_c = s->cin[l];
         A.wfmt = s->wf[l];
-        A.bias = s->b[l];
-        A.out = (__nv_bfloat16*)out;
+        A.bias = s->bpad[l];
+        A.out = out;
+        A.out_f32 = out_bf16 ? 0 : 1;
+        A.out_c = s->cout[l];
+        A.resid = resid;
+        A.resid_stride = s->p.in_channels;
         A.status = s->status;
         A.N = s->p.N;
         A.DZ = kTcDZ < s->p.N ? kTcDZ : s->p.N;
         A.in_act = in_act;
+        A.out_act = out_act;
+        A.out_pre = (__nv_bfloat16*)out_pre;
         ++s->launches;
-        return check(launch_conv_tc(s->p.hidden, A, tc_grid(s, A.DZ), s->stream));
+        return check(launch_conv_tc(tc_width(s->cin[l]), tc_width(s->cout[l]), A, tc_grid(s, A.DZ), s->stream));
     }
     ConvCCArgs A{};
     A.in = in;
@@ -129,7 +147,9 @@ void cl_surrogate_free(cl_surrogate* s)
     for (auto* p : s->db) cudaFree(p);
     for (auto* p : s->wf) cudaFree(p);
     for (auto* p : s->wb) cudaFree(p);
+    for (auto* p : s->bpad) cudaFree(p);
     for (auto* p : s->u) cudaFree(p);
+    for (auto* p : s->upre) cudaFree(p);
     cudaFree(s->du[0]);
     cudaFree(s->du[1]);
     cudaFree(s->x);
@@ -189,15 +209,24 @@ cl_status cl_surrogate_create(cl_surrogate** out, const cl_surrogate_params* p)
             cudaMemset(bb, 0, co * 4);
         }
         __nv_bfloat16 *f = nullptr, *fb = nullptr;
-        if (ok && p->precision == CL_SG_BF16 && l > 0 && l < L - 1)
-            ok = cudaMalloc(&f, nw * 2) == cudaSuccess && cudaMalloc(&fb, nw * 2) == cudaSuccess &&
-                 cudaMemset(f, 0, nw * 2) == cudaSuccess && cudaMemset(fb, 0, nw * 2) == cudaSuccess;
+        float* bp = nullptr;
+        if (ok && p->precision == CL_SG_BF16) {
+            const size_t np = (size_t)27 * tc_width(co) * tc_width(ci);
+            ok = cudaMalloc(&f, np * 2) == cudaSuccess && cudaMemset(f, 0, np * 2) == cudaSuccess &&
+                 cudaMalloc(&bp, tc_width(co) * 4) == cudaSuccess && cudaMemset(bp, 0, tc_width(co) * 4) == cudaSuccess;
+            if (ok && l > 0)
+                ok = cudaMalloc(&fb, np * 2) == cudaSuccess && cudaMemset(fb, 0, np * 2) == cudaSuccess;
+        }
         s->wf.push_back(f);
         s->wb.push_back(fb);
+        s->bpad.push_back(bp);
         if (l < L - 1) {
-            void* uu = nullptr;
+            void *uu = nullptr, *up = nullptr;
             ok = ok && cudaMalloc(&uu, (size_t)s->V * p->hidden * act_bytes(s)) == cudaSuccess;
+            if (ok && p->precision == CL_SG_BF16 && p->activation == CL_ACT_GELU)
+                ok = cudaMalloc(&up, (size_t)s->V * p->hidden * 2) == cudaSuccess;
             s->u.push_back(uu);
+            s->upre.push_back(up);
         }
     }
     s->chunks = conv_dw_chunks(p->N);
@@ -229,17 +258,24 @@ cl_status cl_surrogate_set_weights(cl_surrogate* s, int32_t layer, const float* 
         cudaMemcpyAsync(s->b[layer], b, co * 4, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
         return CL_ECUDA;
     if (s->wf[layer]) {
-        // forward layout, and the adjoint's: Wk[t][a][b] = W[26 - t][b][a]
-        std::vector<float> Wt(W, W + nw), Wa(nw);
-        for (int t = 0; t < 27; ++t)
-            for (int a = 0; a < co; ++a)
-                for (int c = 0; c < ci; ++c) Wa[((size_t)t * co + a) * ci + c] = W[((size_t)(26 - t) * co + c) * ci + a];
+        // forward layout (CI -> CO), and the adjoint's (CO -> CI): Wk[t][a][c] = W[26 - t][c][a]
+        const int cip = tc_width(ci), cop = tc_width(co);
         std::vector<__nv_bfloat16> f, fb;
-        format_tc(Wt, co, f);
-        format_tc(Wa, co, fb);
-        if (cudaMemcpyAsync(s->wf[layer], f.data(), nw * 2, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
-            cudaMemcpyAsync(s->wb[layer], fb.data(), nw * 2, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+        format_tc(W, co, ci, cop, cip, f);
+        if (cudaMemcpyAsync(s->wf[layer], f.data(), f.size() * 2, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+            cudaMemcpyAsync(s->bpad[layer], b, co * 4, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
             return CL_ECUDA;
+        if (s->wb[layer]) {
+            std::vector<float> Wa(nw);
+            for (int t = 0; t < 27; ++t)
+                for (int a = 0; a < ci; ++a)
+                    for (int c = 0; c < co; ++c)
+                        Wa[((size_t)t * ci + a) * co + c] = W[((size_t)(26 - t) * co + c) * ci + a];
+            format_tc(Wa.data(), ci, co, cip, cop, fb);
+            if (cudaMemcpyAsync(s->wb[layer], fb.data(), fb.size() * 2, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+                return CL_ECUDA;
+        }
+        if (cudaStreamSynchronize(s->stream) != cudaSuccess) return CL_ECUDA;  // host staging vectors go out of scope
     }
     return cudaStreamSynchronize(s->stream) == cudaSuccess ? CL_OK : CL_ECUDA;
 }
@@ -263,10 +299,17 @@ cl_status cl_surrogate_forward(cl_surrogate* s, const float* x, float* y, int32_
         cudaSuccess)
         return CL_ECUDA;
     const int L = (int)s->cin.size(), act = s->p.activation;
-    const int ab = bf16_mode(s) ? 1 : 0;
-    cl_status st = conv_forward(s, 0, s->x, 0, 0, s->u[0], ab, nullptr);
-    for (int l = 1; st == CL_OK && l < L - 1; ++l) st = conv_forward(s, l, s->u[l - 1], ab, act, s->u[l], ab, nullptr);
-    if (st == CL_OK) st = conv_forward(s, L - 1, s->u[L - 2], ab, act, s->y, 0, s->x);
+    cl_status st = CL_OK;
+    if (bf16_mode(s)) {  // stored tensors are activations; GELU also keeps the pre-activations
+        st = conv_forward(s, 0, s->x, 0, 0, s->u[0], 1, nullptr, act, s->upre[0]);
+        for (int l = 1; st == CL_OK && l < L - 1; ++l)
+            st = conv_forward(s, l, s->u[l - 1], 1, 0, s->u[l], 1, nullptr, act, s->upre[l]);
+        if (st == CL_OK) st = conv_forward(s, L - 1, s->u[L - 2], 1, 0, s->y, 0, s->x);
+    } else {
+        st = conv_forward(s, 0, s->x, 0, 0, s->u[0], 0, nullptr);
+        for (int l = 1; st == CL_OK && l < L - 1; ++l) st = conv_forward(s, l, s->u[l - 1], 0, act, s->u[l], 0, nullptr);
+        if (st == CL_OK) st = conv_forward(s, L - 1, s->u[L - 2], 0, act, s->y, 0, s->x);
+    }
     if (st != CL_OK) return st;
     if (cudaMemcpyAsync(y, s->y, ny, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream) !=
         cudaSuccess)
@@ -281,7 +324,7 @@ cl_status cl_surrogate_backward(cl_surrogate* s, const float* g, float* dx, int3
     if (!s || !g) return CL_EINVAL;
     if (!s->have_forward) return CL_ESTATE;
     s->launches = 0;
-    const int L = (int)s->cin.size(), act = s->p.activation, C = s->p.hidden;
+    const int L = (int)s->cin.size(), act = s->p.activation;
     const int ab = bf16_mode(s) ? 1 : 0;
     const size_t ng = (size_t)s->V * s->p.out_channels * 4;
     if (cudaMemcpyAsync(s->g, g, ng, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream) !=
@@ -308,18 +351,22 @@ cl_status cl_surrogate_backward(cl_surrogate* s, const float* g, float* dx, int3
     // of its input's pre-activation (gated by act'(gate)) or of the network input
     auto dgrad = [&](int l, const void* gin, int gin_bf16, void* gout, int gout_bf16, const void* gate, int gate_bf16,
                      int gate_act, const float* resid) {
-        if (ab && l > 0 && l < L - 1) {
+        if (ab && l > 0) {  // adjoint of layer l on the tensor cores: cout_l -> cin_l channels
             ConvTCArgs A{};
-            A.in = (const __nv_bfloat16*)gin;
+            A.in = gin;
+            A.in_f32 = gin_bf16 ? 0 : 1;
+            A.in_c = s->cout[l];
             A.wfmt = s->wb[l];
             A.gate = (const __nv_bfloat16*)gate;
             A.gate_act = gate_act;
-            A.out = (__nv_bfloat16*)gout;
+            A.out = gout;
+            A.out_f32 = gout_bf16 ? 0 : 1;
+            A.out_c = s->cin[l];
             A.status = s->status;
             A.N = s->p.N;
             A.DZ = kTcDZ < s->p.N ? kTcDZ : s->p.N;
             ++s->launches;
-            return check(launch_conv_tc(C, A, tc_grid(s, A.DZ), s->stream));
+            return check(launch_conv_tc(tc_width(s->cout[l]), tc_width(s->cin[l]), A, tc_grid(s, A.DZ), s->stream));
         }
         ConvCCArgs A{};
         A.in = gin;
@@ -340,13 +387,17 @@ cl_status cl_surrogate_backward(cl_surrogate* s, const float* g, float* dx, int3
         ++s->launches;
         return check(launch_conv_cc(A, s->stream));
     };
-    // last layer: input act(u_{L-2}), output gradient g (FP32)
-    cl_status st = wgrad(L - 1, s->u[L - 2], ab, act, s->g, 0);
+    // layer inputs h_l = act(u_l): stored as is in BF16 mode, activated on load in FP32 mode;
+    // activation-derivative gates: h (ReLU) or the pre-activations (GELU) in BF16 mode
+    const int h_act = ab ? 0 : act;
+    auto gate_of = [&](int l) -> const void* { return ab && act == CL_ACT_GELU ? s->upre[l] : s->u[l]; };
+    // last layer: input h_{L-2}, output gradient g (FP32)
+    cl_status st = wgrad(L - 1, s->u[L - 2], ab, h_act, s->g, 0);
     int cur = 0;
-    if (st == CL_OK) st = dgrad(L - 1, s->g, 0, s->du[cur], ab, s->u[L - 2], ab, act, nullptr);
+    if (st == CL_OK) st = dgrad(L - 1, s->g, 0, s->du[cur], ab, gate_of(L - 2), ab, act, nullptr);
     for (int l = L - 2; st == CL_OK && l >= 1; --l) {
-        st = wgrad(l, s->u[l - 1], ab, act, s->du[cur], ab);
-        if (st == CL_OK) st = dgrad(l, s->du[cur], ab, s->du[cur ^ 1], ab, s->u[l - 1], ab, act, nullptr);
+        st = wgrad(l, s->u[l - 1], ab, h_act, s->du[cur], ab);
+        if (st == CL_OK) st = dgrad(l, s->du[cur], ab, s->du[cur ^ 1], ab, gate_of(l - 1), ab, act, nullptr);
         cur ^= 1;
     }
     if (st == CL_OK) st = wgrad(0, s->x, 0, 0, s->du[cur], ab);

@@ -64,22 +64,31 @@ __device__ __forceinline__ uint4 act_bf16x8(int act, const uint4 v)
     return pack_bf16x8(f);
 }
 
-// Tensor-core hidden layer: out = conv(act(in)) + bias (forward) or
-// out = conv(in) * act'(gate) (data gradient with the transposed, flipped weights).
+// Tensor-core convolution layer with CI input and CO output channels (16, 32 or 48;
+// thinner layers are zero-padded to 16):
+//   out = act_out(conv(act_in(in)) + bias) (+ resid)   (forward)
+//   out = conv(in) * act'(gate)                        (data gradient, adjoint weights)
 struct ConvTCArgs {
-    const __nv_bfloat16* in;    // N^3 x C
-    const __nv_bfloat16* wfmt;  // weights in the tensor-core layout [27][C/8][C/8][8][8]
-    const float* bias;          // C, or nullptr
-    const __nv_bfloat16* gate;  // N^3 x C pre-activations whose derivative multiplies out, or nullptr
-    __nv_bfloat16* out;         // N^3 x C
+    const void* in;             // BF16 [N^3][CI], or FP32 [N^3][in_c] when in_f32 (padded with zeros)
+    int in_f32, in_c;
+    const __nv_bfloat16* wfmt;  // weights in the tensor-core layout [27][CI/8][CO/8][8][8]
+    const float* bias;          // CO values, or nullptr
+    const __nv_bfloat16* gate;  // BF16 [N^3][CO] pre-activations whose derivative multiplies out, or nullptr
+    void* out;                  // BF16 [N^3][CO], or FP32 [N^3][out_c] (first out_c channels) when out_f32
+    int out_f32, out_c;
+    const float* resid;         // FP32 residual added to the out_c channels (stride resid_stride), or nullptr
+    int resid_stride;
     int* status;                // ST_TIMEOUT on a bounded wait that gave up
     int N;                      // multiple of 16
     int DZ;                     // planes per work unit
-    int in_act;                 // activation applied to `in` while staging
-    int gate_act;               // activation whose derivative gates the output (0: none)
+    int in_act;                 // activation applied to a BF16 `in` while staging
+    int gate_act;               // activation whose derivative gates the output (0: none);
+                                // ReLU gates may be post-activation values (h > 0 iff u > 0)
+    int out_act;                // activation applied before a BF16 store (forward hidden layers)
+    __nv_bfloat16* out_pre;     // BF16 [N^3][CO] pre-activation copy of out (GELU backward), or nullptr
 };
-size_t conv_tc_smem(int C);
-cudaError_t launch_conv_tc(int C, const ConvTCArgs& A, int grid, cudaStream_t s);
+size_t conv_tc_smem(int CI, int CO);
+cudaError_t launch_conv_tc(int CI, int CO, const ConvTCArgs& A, int grid, cudaStream_t s);
 
 // CUDA-core convolution for the thin layers (and the FP32 reference mode): each thread
 // computes all cout outputs of one site.

@@ -1,10 +1,12 @@
 """GPU parity of the convolutional surrogate (forward and backward) against the oracle.
 
-FP32 reference mode (every layer on CUDA cores): 1e-5 relative L2.  BF16 mode (hidden
-layers on the tcgen05 tensor cores, BF16 activations, FP32 accumulation): 1e-2 relative L2
-for outputs, and for gradients through the smooth GELU (BF16 keeps 8 significant bits; the
-rounding of each stored activation is ~2^-9 relative and adds up over the layers; measured
-about 5e-3 for 4 layers, 1.1e-2 for 6).  Through ReLU the gradient is discontinuous in the
+FP32 reference mode (every layer on CUDA cores): 1e-5 relative L2.  BF16 mode (every
+layer on the tcgen05 tensor cores, BF16 activations and input, FP32 accumulation): 1e-2
+relative L2 for outputs, 2e-2 for gradients through the smooth GELU (BF16 keeps 8
+significant bits; the rounding of the input and of each stored activation is ~2^-9
+relative and adds up over the layers, and bias gradients are sums over all sites whose
+cancellation raises their relative error: measured up to 1.2e-2 for 4 layers, 1.4e-2
+for 6).  Through ReLU the gradient is discontinuous in the
 pre-activation: where the BF16 pre-activation lies within its rounding noise of zero the
 gate differs from the FP64 one, and those entries carry the whole gradient or none (3-10%
 relative L2 measured); ReLU gradients are checked to 0.15 only, the forward to 1e-2.
@@ -89,7 +91,7 @@ def test_bf16_tensor_core_mode_matches_oracle(cl, act, hidden):
     dxo, go = O.surrogate_backward(cache, net, g, OACT[act])
     # the network part of y (the residual x is exact) carries the BF16 rounding
     assert rel_l2(y - x[..., :2], yo - x[..., :2]) < 1e-2
-    tol = 1e-2 if act == 2 else 0.15
+    tol = 2e-2 if act == 2 else 0.15
     assert rel_l2(dx, dxo) < tol
     for l in range(layers):
         assert rel_l2(grads[l][0], go[l][0]) < tol, l
@@ -108,10 +110,10 @@ def test_bf16_matches_fp32_mode_at_production_width(cl):
         yf, dxf, gf, _ = run(cl, N, net, act, cl.CL_SG_FP32, x, g)
         assert rel_l2(yb - x[..., :2], yf - x[..., :2]) < 1e-2
         if act == 2:
-            assert rel_l2(dxb, dxf) < 1.5e-2
+            assert rel_l2(dxb, dxf) < 2e-2
             for l in range(6):
-                assert rel_l2(gb[l][0], gf[l][0]) < 2e-2, l
-                assert rel_l2(gb[l][1], gf[l][1]) < 2e-2, l
+                assert rel_l2(gb[l][0], gf[l][0]) < 2.5e-2, l
+                assert rel_l2(gb[l][1], gf[l][1]) < 2.5e-2, l
 
 
 def test_shift_network_is_exact(cl):
