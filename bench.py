@@ -67,7 +67,8 @@ def config(extra=None):
 
 
 KERNEL_SOURCES = ["paper_2607_24978_gb300/csrc/scalar_pass.cu", "paper_2607_24978_gb300/csrc/scalar_pass_tma.cuh",
-                  "paper_2607_24978_gb300/csrc/kernel_common.cuh", "paper_2607_24978_gb300/csrc/cl_internal.cuh"]
+                  "paper_2607_24978_gb300/csrc/scalar_pass_common.cuh", "paper_2607_24978_gb300/csrc/kernel_common.cuh",
+                  "paper_2607_24978_gb300/csrc/cl_internal.cuh"]
 
 
 def profiled_traffic():
