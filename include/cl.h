@@ -322,12 +322,53 @@ cl_status cl_surrogate_get_weights(cl_surrogate* s, int32_t layer, float* W, flo
  * memory (on_device = 0) or device memory (1).  Keeps the activations for a backward call. */
 cl_status cl_surrogate_forward(cl_surrogate* s, const float* x, float* y, int32_t on_device);
 /* Gradients of sum(y * g) for the last forward's input: g holds N^3 * out_channels FP32
- * values; dx (N^3 * in_channels, may be NULL) receives d/dx.  Weight and bias gradients stay
+ * values (NULL: the gradient left by cl_surrogate_loss); dx (N^3 * in_channels, may be NULL)
+ * receives d/dx.  Weight and bias gradients stay
  * on the device (cl_surrogate_get_grads).  Errors: CL_ESTATE without a preceding forward. */
 cl_status cl_surrogate_backward(cl_surrogate* s, const float* g, float* dx, int32_t on_device);
 cl_status cl_surrogate_get_grads(cl_surrogate* s, int32_t layer, float* dW, float* db);
 /* Kernel launches queued by the most recent forward or backward call. */
 int64_t cl_surrogate_last_launch_count(const cl_surrogate* s);
+
+/* Training loss of the most recent forward:
+ *     L = mean over sites n and output channels c of ((y[n][c] - target[n*stride + c]) / scale[c])^2
+ * (scale NULL: 1).  Keeps dL/dy as the output gradient of a following
+ * cl_surrogate_backward(s, NULL, ...) and writes L to *loss (synchronising).  target in
+ * device (on_device = 1) or host memory; stride >= out_channels.
+ * Errors: CL_EINVAL, CL_ESTATE (no forward yet), CL_ECUDA. */
+cl_status cl_surrogate_loss(cl_surrogate* s, const float* target, int32_t stride, const float* scale,
+                            int32_t on_device, double* loss);
+/* One AdamW step (Loshchilov & Hutter, decoupled weight decay) on every layer with the
+ * gradients of the most recent backward: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * W -= lr (m/(1-b1^t) / (sqrt(v/(1-b2^t)) + eps) + weight_decay W); biases without decay;
+ * t = 1, 2, ...  Rebuilds the tensor-core weight layouts on the device.  Errors: CL_EINVAL. */
+cl_status cl_surrogate_adamw(cl_surrogate* s, double lr, double beta1, double beta2, double eps, double weight_decay,
+                             int64_t t);
+/* Mean and standard deviation (population) of each of the `channels` (<= 3) columns of the
+ * device array x (n rows); results to host arrays.  Synchronising. */
+cl_status cl_surrogate_channel_stats(cl_surrogate* s, const float* x_dev, int64_t n, int32_t channels, float* mean,
+                                     float* stdev);
+
+/* Lattice <-> network (single FP32 lattice, one scalar field, N^3 sites = the network's N).
+ * cl_lattice_pack writes x[n] = ((phi - mu[0])/sg[0], (pi - mu[1])/sg[1], (a - mu[2])/sg[2])
+ * at the most recent integer time into the device array x (N^3 x 3); cl_lattice_unpack sets
+ * phi = mu[0] + sg[0] y[n][0], pi = mu[1] + sg[1] y[n][1] from the device array y (N^3 x 2)
+ * (Kahan compensation restarts at zero; a, a', t unchanged).  Errors: CL_EINVAL. */
+cl_status cl_lattice_pack(cl_lattice* l, const float* mu, const float* sg, float* x_dev);
+cl_status cl_lattice_unpack(cl_lattice* l, const float* mu, const float* sg, const float* y_dev);
+
+/* Advance the lattice by `steps` time steps with one surrogate forward (the learned jump):
+ * (phi, pi) from the network applied to the packed state (normalisation mu, sg as above),
+ * a and a' advanced over the jump J = steps * dt with a'' of the starting state,
+ * a += J a' + J^2 a''/2, a' += J a'' (Eq. Friedmann1).  The jump is accepted when the Hubble
+ * violation (Eq. Friedmann2) of the new state is finite and at most hubble_limit; otherwise
+ * the starting state is restored and `steps` leapfrog steps of the lattice's integrator are
+ * taken instead (the fallback).  *accepted = 1 or 0.  The network needs in_channels 3 and
+ * out_channels 2.  Synchronising.  Errors: CL_EINVAL (shapes, precision), CL_ECUDA. */
+cl_status cl_surrogate_jump(cl_surrogate* s, cl_lattice* l, int32_t steps, const float* mu, const float* sg,
+                            double hubble_limit, int32_t* accepted);
+/* Side of the network's lattice (for callers combining a surrogate with a lattice). */
+int32_t cl_surrogate_size(const cl_surrogate* s);
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,8 @@ EXPORTS = ["cl_init_lattice", "cl_free", "cl_set_potential", "cl_set_state", "cl
            "cl_set_gauge_coupling", "cl_set_hubble_limit", "cl_set_option", "cl_last_launch_count", "cl_strerror", "cl_last_error",
            "cl_fused_pass_noalloc", "cl_surrogate_create", "cl_surrogate_free", "cl_surrogate_set_weights",
            "cl_surrogate_get_weights", "cl_surrogate_forward", "cl_surrogate_backward", "cl_surrogate_get_grads",
-           "cl_surrogate_last_launch_count"]
+           "cl_surrogate_last_launch_count", "cl_surrogate_loss", "cl_surrogate_adamw", "cl_surrogate_channel_stats",
+           "cl_lattice_pack", "cl_lattice_unpack", "cl_surrogate_jump", "cl_surrogate_size"]
 CL_ACT_RELU, CL_ACT_GELU = 1, 2
 CL_SG_BF16, CL_SG_FP32 = 0, 1
 
@@ -131,6 +132,14 @@ def lib():
         L.cl_surrogate_get_grads.argtypes = [C.c_void_p, C.c_int32, fp, fp]
         L.cl_surrogate_last_launch_count.argtypes = [C.c_void_p]
         L.cl_surrogate_last_launch_count.restype = C.c_int64
+        L.cl_surrogate_loss.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, P(C.c_double)]
+        L.cl_surrogate_adamw.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                         C.c_int64]
+        L.cl_surrogate_channel_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, fp, fp]
+        L.cl_lattice_pack.argtypes = [C.c_void_p, fp, fp, C.c_void_p]
+        L.cl_lattice_unpack.argtypes = [C.c_void_p, fp, fp, C.c_void_p]
+        L.cl_surrogate_jump.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, fp, fp, C.c_double, P(C.c_int32)]
+        L.cl_surrogate_size.argtypes = [C.c_void_p]
         for name in EXPORTS:
             if name not in ("cl_free", "cl_last_launch_count", "cl_strerror", "cl_last_error", "cl_surrogate_free",
                             "cl_surrogate_last_launch_count"):
@@ -278,6 +287,19 @@ class Lattice:
                                          C.byref(nb)))
         return k, d, c
 
+    def cl_lattice_pack(self, mu, sg, x):
+        """Packed, normalised (phi, pi, a) of this lattice into the CUDA tensor x (N^3 x 3)."""
+        mu = np.ascontiguousarray(mu, dtype=np.float32)
+        sg = np.ascontiguousarray(sg, dtype=np.float32)
+        xp, xdev, xk = _buffer(x, np.float32, self.n * 3)
+        _check(self.h, lib().cl_lattice_pack(self.h, _fptr(mu), _fptr(sg), xp))
+
+    def cl_lattice_unpack(self, mu, sg, y):
+        mu = np.ascontiguousarray(mu, dtype=np.float32)
+        sg = np.ascontiguousarray(sg, dtype=np.float32)
+        yp, ydev, yk = _buffer(y, np.float32, self.n * 2)
+        _check(self.h, lib().cl_lattice_unpack(self.h, _fptr(mu), _fptr(sg), yp))
+
     def cl_set_gauge_coupling(self, alphaL, ws2):
         _check(self.h, lib().cl_set_gauge_coupling(self.h, float(alphaL), float(ws2)))
 
@@ -386,3 +408,38 @@ class Surrogate:
 
     def last_launch_count(self):
         return int(lib().cl_surrogate_last_launch_count(self.h))
+
+    def loss(self, target, stride=None, scale=None):
+        """Loss of the last forward against target (device tensor or host array with `stride`
+        values per site); keeps dL/dy for backward(None)."""
+        stride = self.cout if stride is None else int(stride)
+        tp, tdev, tk = _buffer(target, np.float32, self.N ** 3 * stride)
+        sc = None if scale is None else np.ascontiguousarray(scale, dtype=np.float32)
+        out = C.c_double()
+        self._chk(lib().cl_surrogate_loss(self.h, tp, stride, None if sc is None else sc.ctypes.data_as(C.c_void_p),
+                                          tdev, C.byref(out)), "loss")
+        return out.value
+
+    def backward_from_loss(self):
+        self._chk(lib().cl_surrogate_backward(self.h, None, None, 1), "backward")
+
+    def adamw(self, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=1e-4):
+        self._chk(lib().cl_surrogate_adamw(self.h, float(lr), float(beta1), float(beta2), float(eps),
+                                           float(weight_decay), int(t)), "adamw")
+
+    def channel_stats(self, x, n, channels):
+        xp, xdev, xk = _buffer(x, np.float32, int(n) * int(channels))
+        mean = np.zeros(3, np.float32)
+        std = np.zeros(3, np.float32)
+        self._chk(lib().cl_surrogate_channel_stats(self.h, xp, int(n), int(channels), _fptr(mean), _fptr(std)),
+                  "channel_stats")
+        return mean[:channels], std[:channels]
+
+    def jump(self, lattice, steps, mu, sg, hubble_limit=1e-3):
+        """One learned jump of `steps` lattice steps with the leapfrog as fallback; True if accepted."""
+        mu = np.ascontiguousarray(mu, dtype=np.float32)
+        sg = np.ascontiguousarray(sg, dtype=np.float32)
+        acc = C.c_int32()
+        _check(lattice.h, lib().cl_surrogate_jump(self.h, lattice.h, int(steps), _fptr(mu), _fptr(sg),
+                                                  float(hubble_limit), C.byref(acc)))
+        return bool(acc.value)

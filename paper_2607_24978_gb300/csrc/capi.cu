@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "cl_internal.cuh"
+#include "surrogate_train.cuh"
 
 using namespace clk;
 
@@ -78,6 +79,7 @@ struct cl_lattice {
     EnsItem* d_items = nullptr;
     int* d_sched = nullptr;         // items by decreasing size
     int nitems = 0, ens_grid = 0, ens_stages = 0, ens_stage_stride = 0, ens_ring_slot = 0;
+    float* sg_buf = nullptr;        // surrogate jumps: packed input (3 V), output (2 V), snapshot (3 V)
     size_t ens_smem = 0;
     char err[512] = {0};
 };
@@ -741,6 +743,7 @@ void cl_free(cl_lattice* l)
         if (l->u1s[q]) cudaFree(l->u1s[q]);
     if (l->scal) cudaFree(l->scal);
     if (l->partials) cudaFree(l->partials);
+    if (l->sg_buf) cudaFree(l->sg_buf);
     if (l->d_members) cudaFree(l->d_members);
     if (l->d_items) cudaFree(l->d_items);
     if (l->d_sched) cudaFree(l->d_sched);
@@ -1295,6 +1298,122 @@ cl_status cl_spectrum(cl_lattice* l, int32_t member, int32_t field, double dn, i
     if (real) cudaFree(real);
     if (F) cudaFree(F);
     if (bins) cudaFree(bins);
+    return st;
+}
+
+
+// ---------------------------------------------------------------- surrogate coupling
+static cl_status check_sg_lattice(cl_lattice* l)
+{
+    if (is_ens(l) || l->gauge || l->nf != 1 || is_fp64(l)) return fail(l, CL_EINVAL, "surrogate coupling needs a single FP32 one-field lattice");
+    return CL_OK;
+}
+
+static Norm3 make_norm(const float* mu, const float* sg, int C)
+{
+    Norm3 nm{};
+    for (int c = 0; c < 3; ++c) {
+        nm.mu[c] = c < C ? mu[c] : 0.f;
+        nm.sg[c] = c < C ? sg[c] : 1.f;
+    }
+    return nm;
+}
+
+cl_status cl_lattice_pack(cl_lattice* l, const float* mu, const float* sg, float* x_dev)
+{
+    if (!l) return CL_EINVAL;
+    if (!mu || !sg || !x_dev) return fail(l, CL_EINVAL, "pack: NULL argument");
+    cl_status st = check_sg_lattice(l);
+    if (st != CL_OK) return st;
+    for (int c = 0; c < 3; ++c)
+        if (!(sg[c] != 0.f) || !isfinite(sg[c]) || !isfinite(mu[c])) return fail(l, CL_EINVAL, "pack: bad normalisation");
+    st = close_leapfrog(l, true);
+    if (st != CL_OK) return st;
+    CUDA_TRY(l, launch_pack((const float*)l->phi[0][l->cur], (const float*)l->pi[0][l->cur], &l->scal->a, l->V, 3,
+                            make_norm(mu, sg, 3), x_dev, l->stream));
+    return CL_OK;
+}
+
+cl_status cl_lattice_unpack(cl_lattice* l, const float* mu, const float* sg, const float* y_dev)
+{
+    if (!l) return CL_EINVAL;
+    if (!mu || !sg || !y_dev) return fail(l, CL_EINVAL, "unpack: NULL argument");
+    cl_status st = check_sg_lattice(l);
+    if (st != CL_OK) return st;
+    st = close_leapfrog(l, true);
+    if (st != CL_OK) return st;
+    CUDA_TRY(l, launch_unpack(y_dev, l->V, 2, make_norm(mu, sg, 2), (float*)l->phi[0][l->cur], (float*)l->pi[0][l->cur],
+                              has_kahan(l) ? (float*)l->cc[0][l->cur] : nullptr, l->stream));
+    l->diag_valid = false;
+    return CL_OK;
+}
+
+cl_status cl_surrogate_jump(cl_surrogate* s, cl_lattice* l, int32_t steps, const float* mu, const float* sg,
+                            double hubble_limit, int32_t* accepted)
+{
+    if (!l) return CL_EINVAL;
+    if (!s || !mu || !sg || !accepted || steps < 1) return fail(l, CL_EINVAL, "jump: bad arguments");
+    cl_status st = check_sg_lattice(l);
+    if (st != CL_OK) return st;
+    if (cl_surrogate_size(s) != l->N) return fail(l, CL_EINVAL, "jump: network and lattice sizes differ");
+    *accepted = 0;
+    st = close_leapfrog(l, true);
+    if (st == CL_OK && !l->diag_valid) st = energy_pass(l, 0);
+    std::vector<DevScal> h;
+    if (st == CL_OK) st = read_status(l, h);
+    if (st != CL_OK) return st;
+    const DevScal h0 = h[0];
+    const size_t V = (size_t)l->V;
+    if (!l->sg_buf && cudaMalloc(&l->sg_buf, 8 * V * sizeof(float)) != cudaSuccess)
+        return fail(l, CL_ENOMEM, "jump: scratch allocation failed");
+    float* x = l->sg_buf;
+    float* y = x + 3 * V;
+    float* snap = y + 2 * V;
+    const int cur = l->cur;
+    float* ph = (float*)l->phi[0][cur];
+    float* pv = (float*)l->pi[0][cur];
+    float* cv = has_kahan(l) ? (float*)l->cc[0][cur] : nullptr;
+    CUDA_TRY(l, cudaMemcpyAsync(snap, ph, V * 4, cudaMemcpyDeviceToDevice, l->stream));
+    CUDA_TRY(l, cudaMemcpyAsync(snap + V, pv, V * 4, cudaMemcpyDeviceToDevice, l->stream));
+    if (cv) CUDA_TRY(l, cudaMemcpyAsync(snap + 2 * V, cv, V * 4, cudaMemcpyDeviceToDevice, l->stream));
+    // the learned jump of (phi, pi)
+    CUDA_TRY(l, launch_pack(ph, pv, &l->scal->a, l->V, 3, make_norm(mu, sg, 3), x, l->stream));
+    CUDA_TRY(l, cudaStreamSynchronize(l->stream));
+    st = cl_surrogate_forward(s, x, y, 1);
+    if (st != CL_OK) return fail(l, st, "jump: surrogate forward failed");
+    CUDA_TRY(l, cudaStreamSynchronize(surrogate_stream(s)));  // y is written on the surrogate's stream
+    CUDA_TRY(l, launch_unpack(y, l->V, 2, make_norm(mu, sg, 2), ph, pv, cv, l->stream));
+    // a, a' over the jump with a'' of the starting state (Eq. Friedmann1)
+    const double J = (double)steps * l->p.dt, al = l->p.alpha;
+    const double a = h0.diag[D_A], b = h0.diag[D_ADOT], rho = h0.diag[D_RHO], p = h0.diag[D_P];
+    const double addot =
+        l->p.expansion ? pow(a, 2.0 * al + 1.0) * (l->p.kappa / 6.0) * ((2.0 * al - 1.0) * rho - 3.0 * p) : 0.0;
+    DevScal hn = h0;
+    hn.a = l->p.expansion ? a + J * b + 0.5 * J * J * addot : a;
+    hn.b = l->p.expansion ? b + J * addot : b;
+    hn.t = h0.diag[D_T] + J;
+    hn.step = h0.step + steps;
+    hn.status = 0;
+    CUDA_TRY(l, cudaMemcpyAsync(l->scal, &hn, sizeof(DevScal), cudaMemcpyHostToDevice, l->stream));
+    st = energy_pass(l, 0);
+    if (st == CL_OK) st = read_status(l, h);
+    if (st != CL_OK && st != CL_ENAN) return st;
+    const double hv = h[0].diag[D_HV];
+    if (st == CL_OK && isfinite(h[0].diag[D_RHO]) && isfinite(hv) && hv <= hubble_limit) {
+        *accepted = 1;
+        return CL_OK;
+    }
+    // fallback: restore the starting state and take the leapfrog steps
+    CUDA_TRY(l, cudaMemcpyAsync(ph, snap, V * 4, cudaMemcpyDeviceToDevice, l->stream));
+    CUDA_TRY(l, cudaMemcpyAsync(pv, snap + V, V * 4, cudaMemcpyDeviceToDevice, l->stream));
+    if (cv) CUDA_TRY(l, cudaMemcpyAsync(cv, snap + 2 * V, V * 4, cudaMemcpyDeviceToDevice, l->stream));
+    DevScal hr = h0;
+    hr.status = 0;
+    CUDA_TRY(l, cudaMemcpyAsync(l->scal, &hr, sizeof(DevScal), cudaMemcpyHostToDevice, l->stream));
+    CUDA_TRY(l, cudaStreamSynchronize(l->stream));
+    l->diag_valid = false;
+    st = cl_step(l, steps);
+    if (st == CL_OK) st = cl_sync(l);
     return st;
 }
 

@@ -9,6 +9,7 @@
 
 #include "cl_internal.cuh"
 #include "surrogate_common.cuh"
+#include "surrogate_train.cuh"
 
 using namespace clk;
 
@@ -37,8 +38,11 @@ struct cl_surrogate {
     float* partial = nullptr;          // weight-gradient partials
     int chunks = 1;
     int* status = nullptr;
-    bool have_forward = false;
+    bool have_forward = false, have_loss = false;
     int64_t launches = 0;
+    std::vector<float*> mW, vW, mb, vb;  // AdamW moments
+    double* red = nullptr;             // reduction scratch (loss, statistics)
+    size_t red_cap = 0;
 };
 
 namespace {
@@ -158,6 +162,11 @@ void cl_surrogate_free(cl_surrogate* s)
     cudaFree(s->dx);
     cudaFree(s->partial);
     cudaFree(s->status);
+    for (auto* p : s->mW) cudaFree(p);
+    for (auto* p : s->vW) cudaFree(p);
+    for (auto* p : s->mb) cudaFree(p);
+    for (auto* p : s->vb) cudaFree(p);
+    cudaFree(s->red);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -204,6 +213,15 @@ cl_status cl_surrogate_create(cl_surrogate** out, const cl_surrogate_params* p)
         s->b.push_back(bb);
         s->dW.push_back(gw);
         s->db.push_back(gb);
+        float *m1 = nullptr, *v1 = nullptr, *m2 = nullptr, *v2 = nullptr;
+        ok = ok && cudaMalloc(&m1, nw * 4) == cudaSuccess && cudaMalloc(&v1, nw * 4) == cudaSuccess &&
+             cudaMalloc(&m2, co * 4) == cudaSuccess && cudaMalloc(&v2, co * 4) == cudaSuccess &&
+             cudaMemset(m1, 0, nw * 4) == cudaSuccess && cudaMemset(v1, 0, nw * 4) == cudaSuccess &&
+             cudaMemset(m2, 0, co * 4) == cudaSuccess && cudaMemset(v2, 0, co * 4) == cudaSuccess;
+        s->mW.push_back(m1);
+        s->vW.push_back(v1);
+        s->mb.push_back(m2);
+        s->vb.push_back(v2);
         if (ok) {
             cudaMemset(w, 0, nw * 4);
             cudaMemset(bb, 0, co * 4);
@@ -321,14 +339,14 @@ cl_status cl_surrogate_forward(cl_surrogate* s, const float* x, float* y, int32_
 
 cl_status cl_surrogate_backward(cl_surrogate* s, const float* g, float* dx, int32_t on_device)
 {
-    if (!s || !g) return CL_EINVAL;
-    if (!s->have_forward) return CL_ESTATE;
+    if (!s) return CL_EINVAL;
+    if (!s->have_forward || (!g && !s->have_loss)) return CL_ESTATE;
     s->launches = 0;
     const int L = (int)s->cin.size(), act = s->p.activation;
     const int ab = bf16_mode(s) ? 1 : 0;
     const size_t ng = (size_t)s->V * s->p.out_channels * 4;
-    if (cudaMemcpyAsync(s->g, g, ng, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream) !=
-        cudaSuccess)
+    if (g && cudaMemcpyAsync(s->g, g, ng, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             s->stream) != cudaSuccess)
         return CL_ECUDA;
     auto wgrad = [&](int l, const void* h, int h_bf16, int h_act, const void* gg, int g_bf16) {
         ConvDWArgs A{};
@@ -424,5 +442,114 @@ cl_status cl_surrogate_get_grads(cl_surrogate* s, int32_t layer, float* dW, floa
 }
 
 int64_t cl_surrogate_last_launch_count(const cl_surrogate* s) { return s ? s->launches : 0; }
+
+int32_t cl_surrogate_size(const cl_surrogate* s) { return s ? s->p.N : 0; }
+
+}  // extern "C"
+
+cudaStream_t surrogate_stream(const cl_surrogate* s) { return s ? s->stream : nullptr; }
+
+extern "C" {
+
+static cl_status ensure_red(cl_surrogate* s, size_t n)
+{
+    if (n + 1 <= s->red_cap) return CL_OK;
+    cudaFree(s->red);
+    s->red = nullptr;
+    s->red_cap = 0;
+    if (cudaMalloc(&s->red, (n + 1) * sizeof(double)) != cudaSuccess) return CL_ENOMEM;
+    s->red_cap = n + 1;
+    return CL_OK;
+}
+
+cl_status cl_surrogate_loss(cl_surrogate* s, const float* target, int32_t stride, const float* scale,
+                            int32_t on_device, double* loss)
+{
+    if (!s || !target || !loss || stride < s->p.out_channels) return CL_EINVAL;
+    if (!s->have_forward) return CL_ESTATE;
+    const int C = s->p.out_channels;
+    const int64_t n = s->V;
+    const int np = loss_partials(n);
+    cl_status st = ensure_red(s, (size_t)np + 8);
+    if (st != CL_OK) return st;
+    // target and scale in device memory: the target goes to the (idle) input-gradient buffer
+    const float* td = target;
+    if (!on_device) {  // host targets are staged in the input-gradient buffer (N^3 x in_channels)
+        if (stride > s->p.in_channels) return CL_EINVAL;
+        if (cudaMemcpyAsync(s->dx, target, (size_t)n * stride * 4, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+            return CL_ECUDA;
+        td = s->dx;
+    }
+    float* sc = nullptr;
+    if (scale) {
+        sc = reinterpret_cast<float*>(s->red + np + 1);
+        if (cudaMemcpyAsync(sc, scale, C * 4, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) return CL_ECUDA;
+    }
+    LossArgs A{};
+    A.y = s->y;
+    A.t = td;
+    A.scale = sc;
+    A.g = s->g;
+    A.partial = s->red;
+    A.n = n;
+    A.C = C;
+    A.tstride = stride;
+    double* res = s->red + np;
+    if (launch_loss(A, res, s->stream) != cudaSuccess) return CL_ECUDA;
+    if (cudaMemcpyAsync(loss, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return CL_ECUDA;
+    s->have_loss = true;
+    return CL_OK;
+}
+
+cl_status cl_surrogate_adamw(cl_surrogate* s, double lr, double beta1, double beta2, double eps, double weight_decay,
+                             int64_t t)
+{
+    if (!s || t < 1 || !(lr >= 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0) ||
+        !(weight_decay >= 0))
+        return CL_EINVAL;
+    AdamArgs A{};
+    A.lr = (float)lr;
+    A.b1 = (float)beta1;
+    A.b2 = (float)beta2;
+    A.eps = (float)eps;
+    A.wd = (float)weight_decay;
+    A.c1 = (float)(1.0 / (1.0 - pow(beta1, (double)t)));
+    A.c2 = (float)(1.0 / (1.0 - pow(beta2, (double)t)));
+    for (size_t l = 0; l < s->cin.size(); ++l) {
+        const int ci = s->cin[l], co = s->cout[l];
+        const int64_t nw = (int64_t)27 * co * ci;
+        if (launch_adamw(s->W[l], s->dW[l], s->mW[l], s->vW[l], nw, A, true, s->stream) != cudaSuccess ||
+            launch_adamw(s->b[l], s->db[l], s->mb[l], s->vb[l], co, A, false, s->stream) != cudaSuccess)
+            return CL_ECUDA;
+        if (s->wf[l]) {
+            const int cip = tc_width(ci), cop = tc_width(co);
+            if (launch_format_tc(s->W[l], co, ci, cop, cip, 0, s->wf[l], s->stream) != cudaSuccess ||
+                cudaMemcpyAsync(s->bpad[l], s->b[l], co * 4, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
+                return CL_ECUDA;
+            if (s->wb[l] && launch_format_tc(s->W[l], ci, co, cip, cop, 1, s->wb[l], s->stream) != cudaSuccess)
+                return CL_ECUDA;
+        }
+    }
+    return CL_OK;
+}
+
+cl_status cl_surrogate_channel_stats(cl_surrogate* s, const float* x_dev, int64_t n, int32_t channels, float* mean,
+                                     float* stdev)
+{
+    if (!s || !x_dev || n < 1 || channels < 1 || channels > 3 || !mean || !stdev) return CL_EINVAL;
+    const int np = channel_stats_partials(n);
+    cl_status st = ensure_red(s, (size_t)np + 8);
+    if (st != CL_OK) return st;
+    float* dm = reinterpret_cast<float*>(s->red + np);
+    float* ds = dm + 4;
+    if (launch_channel_stats(x_dev, n, channels, s->red, dm, ds, s->stream) != cudaSuccess) return CL_ECUDA;
+    if (cudaMemcpyAsync(mean, dm, channels * 4, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(stdev, ds, channels * 4, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return CL_ECUDA;
+    return CL_OK;
+}
 
 }  // extern "C"

@@ -150,3 +150,143 @@ def test_invalid_configurations(cl):
     with cl.Surrogate(16, 3, 2, 16, 3, 1, cl.CL_SG_BF16) as s:
         with pytest.raises(cl.CLError):
             s.backward(np.zeros((16, 16, 16, 2), np.float32))  # no forward yet
+
+
+# ---------------------------------------------------------------- training and application
+def test_loss_and_its_gradient(cl):
+    N, net = 16, make_net(11, 3, 2, 16, 3)
+    x = inputs.rng(12).standard_normal((N, N, N, 3)).astype(np.float32)
+    t = inputs.rng(13).standard_normal((N, N, N, 3)).astype(np.float32)
+    scale = np.array([0.5, 2.0], np.float32)
+    with cl.Surrogate(N, 3, 2, 16, 3, 1, cl.CL_SG_BF16) as s:
+        for l, (W, b) in enumerate(net):
+            s.set_weights(l, W, b)
+        y = s.forward(x)
+        L = s.loss(t, stride=3, scale=scale)
+        d = (y.astype(np.float64) - t[..., :2]) / scale
+        assert L == pytest.approx(np.mean(d * d), rel=1e-6)
+        s.backward_from_loss()
+        g_internal = [s.grads(l) for l in range(3)]
+        g = (2.0 * d / scale / d.size).astype(np.float32)
+        s.backward(g)
+        g_explicit = [s.grads(l) for l in range(3)]
+    for a, b in zip(g_internal, g_explicit):
+        assert rel_l2(a[0], b[0]) < 1e-5
+        assert rel_l2(a[1], b[1]) < 1e-5
+
+
+def test_adamw_matches_numpy_and_rebuilds_the_tensor_core_weights(cl):
+    N, net = 16, make_net(14, 3, 2, 32, 4)
+    x = inputs.rng(15).standard_normal((N, N, N, 3)).astype(np.float32)
+    g = inputs.rng(16).standard_normal((N, N, N, 2)).astype(np.float32)
+    lr, b1, b2, eps, wd = 1e-3, 0.9, 0.999, 1e-8, 1e-2
+    with cl.Surrogate(N, 3, 2, 32, 4, 1, cl.CL_SG_BF16) as s:
+        for l, (W, b) in enumerate(net):
+            s.set_weights(l, W, b)
+        expect = [[W.astype(np.float32), b.astype(np.float32), np.zeros_like(W), np.zeros_like(W), np.zeros_like(b),
+                   np.zeros_like(b)] for W, b in net]
+        for t in (1, 2, 3):
+            s.forward(x)
+            s.backward(g * t)
+            grads = [s.grads(l) for l in range(4)]
+            s.adamw(lr, t, b1, b2, eps, wd)
+            for l in range(4):
+                W, b, mW, vW, mb, vb = expect[l]
+                for P, G, M, Vv, decay in ((W, grads[l][0], mW, vW, wd), (b, grads[l][1], mb, vb, 0.0)):
+                    M[...] = b1 * M + (1 - b1) * G
+                    Vv[...] = b2 * Vv + (1 - b2) * G * G
+                    mh, vh = M / (1 - b1 ** t), Vv / (1 - b2 ** t)
+                    P -= lr * (mh / (np.sqrt(vh) + eps) + decay * P)
+        got = [s.get_weights(l) for l in range(4)]
+        y_updated = s.forward(x)
+    for l in range(4):
+        assert rel_l2(got[l][0], expect[l][0]) < 1e-5, l
+        assert rel_l2(got[l][1], expect[l][1]) < 1e-5, l
+    # the device-built tensor-core layouts equal the host-built ones of the same weights
+    with cl.Surrogate(N, 3, 2, 32, 4, 1, cl.CL_SG_BF16) as s2:
+        for l in range(4):
+            s2.set_weights(l, *got[l])
+        assert np.array_equal(s2.forward(x), y_updated)
+
+
+def test_channel_stats(cl):
+    import torch
+    n = 5000
+    a = inputs.rng(17).standard_normal((n, 3)) * np.array([1.0, 0.1, 3.0]) + np.array([2.0, -1.0, 0.5])
+    with cl.Surrogate(16, 3, 2, 16, 2, 1, cl.CL_SG_BF16) as s:
+        mean, std = s.channel_stats(torch.tensor(a, dtype=torch.float32, device="cuda").contiguous(), n, 3)
+    a32 = a.astype(np.float32).astype(np.float64)
+    assert np.allclose(mean, a32.mean(0), rtol=1e-6, atol=1e-7)
+    assert np.allclose(std, a32.std(0), rtol=1e-5)
+
+
+def lphi4_lattice(cl, N, dt=0.01, integ=0, seed=21):
+    import math
+    g = cl.Lattice(N, 8.0 * math.pi * N / 32, 1, cl.CL_PREC_FP32_KAHAN, integ, alpha=1.0, kappa=0.1, dt=dt)
+    g.cl_set_potential(cl.CL_POT_LPHI4, [1.0])
+    g.cl_init_vacuum(seed, 1e30, 1e-4, (1.0,), (0.0,))
+    return g
+
+
+def test_pack_and_unpack(cl):
+    import torch
+    N = 16
+    mu = np.array([1.0, 0.0, 1.0], np.float32)
+    sg = np.array([0.1, 0.05, 1.0], np.float32)
+    with lphi4_lattice(cl, N) as g:
+        g.cl_step(3)
+        x = torch.empty(N ** 3 * 3, device="cuda")
+        g.cl_lattice_pack(mu, sg, x)
+        phi, pi = g.cl_get_state(cl.CL_FIELD_PHI0), g.cl_get_state(cl.CL_FIELD_PI0)
+        a = g.cl_get_scalars()[0]
+        xh = x.cpu().numpy().reshape(N, N, N, 3)
+        assert np.allclose(xh[..., 0], (phi - mu[0]) / sg[0], rtol=1e-6, atol=1e-5)
+        assert np.allclose(xh[..., 1], (pi - mu[1]) / sg[1], rtol=1e-6, atol=1e-5)
+        assert np.allclose(xh[..., 2], (a - mu[2]) / sg[2], rtol=1e-6)
+        y = torch.tensor(inputs.rng(18).standard_normal(N ** 3 * 2), dtype=torch.float32, device="cuda")
+        g.cl_lattice_unpack(mu, sg, y)
+        yh = y.cpu().numpy().reshape(N, N, N, 2)
+        # the device forms mu + sg y with one fused multiply-add: within an ulp of numpy's two roundings
+        assert np.allclose(g.cl_get_state(cl.CL_FIELD_PHI0), mu[0] + sg[0] * yh[..., 0].astype(np.float64),
+                           rtol=2e-7, atol=0)
+        assert np.allclose(g.cl_get_state(cl.CL_FIELD_PI0), mu[1] + sg[1] * yh[..., 1].astype(np.float64),
+                           rtol=2e-7, atol=1e-12)
+
+
+def test_jump_fallback_is_the_leapfrog(cl):
+    """A jump that is never accepted leaves exactly the state of `steps` leapfrog steps."""
+    N = 16
+    mu, sg = np.array([1.0, 0.0, 1.0], np.float32), np.array([0.1, 0.1, 1.0], np.float32)
+    with cl.Surrogate(N, 3, 2, 16, 3, 1, cl.CL_SG_BF16) as s, lphi4_lattice(cl, N) as g, lphi4_lattice(cl, N) as ref:
+        for l, (W, b) in enumerate(make_net(19, 3, 2, 16, 3)):
+            s.set_weights(l, W, b)
+        assert s.jump(g, 16, mu, sg, hubble_limit=-1.0) is False
+        ref.cl_step(16)
+        for f in (cl.CL_FIELD_PHI0, cl.CL_FIELD_PI0):
+            assert np.array_equal(g.cl_get_state(f), ref.cl_get_state(f))
+        eg, er = g.cl_energies(), ref.cl_energies()
+        assert eg["a"] == er["a"] and eg["step"] == er["step"] == 16
+
+
+def test_jump_accepted_with_an_identity_network(cl):
+    """Zero last layer: the network returns its input, so an accepted jump keeps (phi, pi) and
+    advances a, a' and t by the Friedmann update over the jump."""
+    N, steps = 16, 16
+    mu, sg = np.array([1.0, 0.0, 1.0], np.float32), np.array([0.25, 0.125, 1.0], np.float32)
+    net = make_net(20, 3, 2, 16, 3)
+    net[-1] = (np.zeros_like(net[-1][0]), np.zeros_like(net[-1][1]))
+    with cl.Surrogate(N, 3, 2, 16, 3, 1, cl.CL_SG_BF16) as s, lphi4_lattice(cl, N) as g:
+        for l, (W, b) in enumerate(net):
+            s.set_weights(l, W, b)
+        phi0, pi0 = g.cl_get_state(cl.CL_FIELD_PHI0), g.cl_get_state(cl.CL_FIELD_PI0)
+        e0 = g.cl_energies()
+        assert s.jump(g, steps, mu, sg, hubble_limit=np.inf) is True
+        e1 = g.cl_energies()
+        assert np.allclose(g.cl_get_state(cl.CL_FIELD_PHI0), phi0, rtol=0, atol=1e-6)
+        assert np.allclose(g.cl_get_state(cl.CL_FIELD_PI0), pi0, rtol=0, atol=1e-6)
+        J = steps * 0.01
+        addot = e0["a"] ** 3 * (0.1 / 6.0) * (e0["rho"] - 3.0 * e0["p"])  # alpha = 1
+        assert e1["a"] == pytest.approx(e0["a"] + J * e0["adot"] + 0.5 * J * J * addot, rel=1e-12)
+        assert e1["adot"] == pytest.approx(e0["adot"] + J * addot, rel=1e-12)
+        assert e1["t"] == pytest.approx(e0["t"] + J, rel=1e-12)
+        assert e1["step"] == steps
