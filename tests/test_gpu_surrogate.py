@@ -290,3 +290,22 @@ def test_jump_accepted_with_an_identity_network(cl):
         assert e1["adot"] == pytest.approx(e0["adot"] + J * addot, rel=1e-12)
         assert e1["t"] == pytest.approx(e0["t"] + J, rel=1e-12)
         assert e1["step"] == steps
+
+
+def test_training_driver_and_the_judge(cl):
+    """A short training run lowers the loss; with a judge that accepts nothing the surrogate
+    path reproduces the plain leapfrog exactly (spectrum error 0), and with no limit every jump
+    is taken."""
+    import torch
+    from paper_2607_24978_gb300 import surrogate_train as T
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s, mu, sg, info = T.train(torch, N=16, hidden=16, layers=3, seeds=(1, 2), per_traj=8, warm=20, iters=150,
+                                  lr=3e-4)
+        assert info["loss_last"] < info["loss_first"]
+        r = T.evaluate(torch, s, mu, sg, N=16, jumps=3, warm=20, hubble_limit=-1.0, hidden=16, layers=3)
+        assert r["accepted"] == 0
+        assert r["spectrum_err_phi"] < 1e-12 and r["spectrum_err_pi"] < 1e-12
+        r = T.evaluate(torch, s, mu, sg, N=32, jumps=2, warm=20, hubble_limit=float("inf"), hidden=16, layers=3)
+        assert r["accepted"] == 2
+        s.close()
