@@ -318,6 +318,10 @@ def run_ensemble_workload(args, world, rank, local, cl, torch, stream, hbm_peak,
     for m in range(c["members"]):  # lambda phi^4 in program units: lambda sets the vacuum amplitude
         g.cl_init_vacuum(c["seed"], kcut, float(lam[m]), (1.0,), (0.0,), member=m)
     sites = sum(n ** 3 for n in sizes)
+    tuned = None
+    if args.stages is None and args.by is None and args.dz is None and not args.no_autotune:
+        st_, by_, dz_, us_ = g.cl_autotune()  # timed trial passes; the state is unchanged
+        tuned = {"stages": st_, "tile_by": by_, "tile_dz": dz_, "us_per_trial_pass": us_}
     for opt, v in ((cl.CL_OPT_STAGES, args.stages), (cl.CL_OPT_TILE_BY, args.by), (cl.CL_OPT_TILE_DZ, args.dz)):
         if v is not None:
             g.cl_set_option(opt, v)
@@ -342,7 +346,8 @@ def run_ensemble_workload(args, world, rank, local, cl, torch, stream, hbm_peak,
                        "l2": "inputs (%.0f MB) larger than L2; no flush" % (sites * 6 * 4 / 1e6)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
-                         "kernel": "k_ensemble_pass<float,1,kahan,4>", "algorithmic_bytes_per_launch": bytes_pass},
+                         "kernel": "k_ensemble_pass_tma<float,1,kahan,4,S>", "algorithmic_bytes_per_launch": bytes_pass},
+            "autotune": tuned,
             "gpu_launches": launches, "clocks": clocks,
             "energies_end": {"members": len(es), "max_hubble_violation": max(x["hubble_violation"] for x in es),
                              "steps": es[0]["step"]}}
@@ -589,6 +594,7 @@ def main():
                     help="preheat: the headline 256^3 two-field run; u1, ensemble: the other workloads")
     ap.add_argument("--members", type=int, default=None, help="ensemble size (default 1024)")
     ap.add_argument("--no-train", action="store_true", help="surrogate workload: throughput only")
+    ap.add_argument("--no-autotune", action="store_true", help="ensemble workload: default tiling, no trial passes")
     args = ap.parse_args()
     world, rank, local = dist_init(args)
     if args.impl == "reference":

@@ -226,6 +226,18 @@ cl_status cl_set_hubble_limit(cl_lattice* l, double limit);
 enum { CL_OPT_GRAPH = 0, CL_OPT_TILE_BY = 1, CL_OPT_TILE_DZ = 2, CL_OPT_STAGES = 3 };
 cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value);
 
+/* Autotuner of the fused leapfrog pass (single lattices and ensembles, no gauge field):
+ * times trial passes of candidate tilings -- TMA stage buffers (CL_OPT_STAGES), rows per tile
+ * (CL_OPT_TILE_BY) and planes per work unit or z chunk (CL_OPT_TILE_DZ) -- and keeps the
+ * fastest.  A trial pass does the full work of a pass (drift while loading, stencil kick,
+ * energies) but writes into the spare buffers and commits nothing: the state, a, a' and t are
+ * unchanged.  cache_path (may be NULL): a text file of earlier choices, one JSON object per
+ * line, keyed by the lattice's shape, precision and field count; a hit applies the cached
+ * choice without trials, a miss appends the new one.  best (may be NULL) receives
+ * {stages, tile_by, tile_dz, microseconds per pass}.  Errors: CL_EINVAL (Runge-Kutta or
+ * gauge lattice), CL_ESTATE (no potential), CL_ECUDA. */
+cl_status cl_autotune(cl_lattice* l, const char* cache_path, double* best);
+
 /* ---- Allocation-free pass (the paper has no counterpart; this serves callers that cannot
  * allocate device memory when they step: code inside an application that owns a fixed memory
  * arena, hosts that forbid allocation after start-up, frameworks that hand over only

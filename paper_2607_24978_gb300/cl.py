@@ -32,7 +32,7 @@ EXPORTS = ["cl_init_lattice", "cl_free", "cl_set_potential", "cl_set_state", "cl
            "cl_fused_pass_noalloc", "cl_surrogate_create", "cl_surrogate_free", "cl_surrogate_set_weights",
            "cl_surrogate_get_weights", "cl_surrogate_forward", "cl_surrogate_backward", "cl_surrogate_get_grads",
            "cl_surrogate_last_launch_count", "cl_surrogate_loss", "cl_surrogate_adamw", "cl_surrogate_channel_stats",
-           "cl_lattice_pack", "cl_lattice_unpack", "cl_surrogate_jump", "cl_surrogate_size"]
+           "cl_lattice_pack", "cl_lattice_unpack", "cl_surrogate_jump", "cl_surrogate_size", "cl_autotune"]
 CL_ACT_RELU, CL_ACT_GELU = 1, 2
 CL_SG_BF16, CL_SG_FP32 = 0, 1
 
@@ -140,6 +140,7 @@ def lib():
         L.cl_lattice_unpack.argtypes = [C.c_void_p, fp, fp, C.c_void_p]
         L.cl_surrogate_jump.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, fp, fp, C.c_double, P(C.c_int32)]
         L.cl_surrogate_size.argtypes = [C.c_void_p]
+        L.cl_autotune.argtypes = [C.c_void_p, C.c_char_p, P(C.c_double)]
         for name in EXPORTS:
             if name not in ("cl_free", "cl_last_launch_count", "cl_strerror", "cl_last_error", "cl_surrogate_free",
                             "cl_surrogate_last_launch_count"):
@@ -311,6 +312,13 @@ class Lattice:
 
     def cl_last_launch_count(self):
         return int(lib().cl_last_launch_count(self.h))
+
+    def cl_autotune(self, cache_path=None):
+        """Pick the fastest tiling from timed trial passes (state unchanged); returns
+        (stages, tile_by, tile_dz, microseconds per pass)."""
+        best = (C.c_double * 4)()
+        _check(self.h, lib().cl_autotune(self.h, cache_path.encode() if cache_path else None, best))
+        return int(best[0]), int(best[1]), int(best[2]), float(best[3])
 
 
 def cl_fused_pass_noalloc(desc):

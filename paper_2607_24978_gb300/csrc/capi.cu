@@ -8,6 +8,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
+#include <string>
 #include <new>
 #include <vector>
 
@@ -1053,6 +1055,131 @@ cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value)
         return choose_tiles(l);
     }
     return fail(l, CL_EINVAL, "unknown option %d", option);
+}
+
+// ---------------------------------------------------------------- autotuner
+static std::string tune_key(const cl_lattice* l)
+{
+    char buf[256];
+    if (!is_ens(l)) {
+        snprintf(buf, sizeof(buf), "single N=%d nf=%d prec=%d", l->N, l->nf, l->p.precision);
+    } else {
+        uint64_t h = 1469598103934665603ull;  // FNV-1a over the member sizes
+        for (int n : l->mN) {
+            h ^= (uint64_t)n;
+            h *= 1099511628211ull;
+        }
+        snprintf(buf, sizeof(buf), "ensemble B=%d sizes=%016llx nf=%d prec=%d", l->members, (unsigned long long)h, l->nf,
+                 l->p.precision);
+    }
+    return buf;
+}
+
+static cl_status apply_tiles(cl_lattice* l, int stages, int by, int dz)
+{
+    l->opt_stages = stages;
+    l->opt_BY = by;
+    l->opt_DZ = dz;
+    return choose_tiles(l);
+}
+
+// Average duration (microseconds) of `n` trial passes after `warm` untimed ones.
+static cl_status time_trials(cl_lattice* l, int warm, int n, double* us)
+{
+    const PassCoef pc{l->p.dt, 0.5 * l->p.dt, l->p.dt, P_DRIFT};  // no P_COMMIT: the state is untouched
+    for (int i = 0; i < warm; ++i) {
+        cl_status s = run_pass(l, pc, l->cur, l->cur ^ 1);
+        if (s != CL_OK) return s;
+    }
+    cudaEvent_t a, b;
+    CUDA_TRY(l, cudaEventCreate(&a));
+    CUDA_TRY(l, cudaEventCreate(&b));
+    cudaEventRecord(a, l->stream);
+    cl_status s = CL_OK;
+    for (int i = 0; i < n && s == CL_OK; ++i) s = run_pass(l, pc, l->cur, l->cur ^ 1);
+    cudaEventRecord(b, l->stream);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *us = 1e3 * ms / n;
+    return s;
+}
+
+cl_status cl_autotune(cl_lattice* l, const char* cache_path, double* best)
+{
+    if (!l) return CL_EINVAL;
+    if (is_rk(l->p.integrator) || l->gauge) return fail(l, CL_EINVAL, "the autotuner covers the leapfrog pass only");
+    if (!l->potential_set) return fail(l, CL_ESTATE, "cl_set_potential has not been called");
+    const std::string key = tune_key(l);
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "r")) {
+            char line[512];
+            int hit = 0, st = 0, by = 0, dz = 0;
+            double us = 0.0;
+            while (fgets(line, sizeof(line), f)) {
+                const char* k = strstr(line, "\"key\": \"");
+                if (!k) continue;
+                k += 8;
+                const char* e = strchr(k, '"');
+                if (!e || std::string(k, e - k) != key) continue;
+                if (sscanf(e, "\", \"stages\": %d, \"by\": %d, \"dz\": %d, \"us\": %lf", &st, &by, &dz, &us) == 4) hit = 1;
+            }
+            fclose(f);
+            if (hit && apply_tiles(l, st, by, dz) == CL_OK) {
+                if (best) { best[0] = st; best[1] = by; best[2] = dz; best[3] = us; }
+                l->diag_valid = false;
+                return CL_OK;
+            }
+        }
+    }
+    // candidates
+    std::vector<std::array<int, 3>> cand;
+    if (is_ens(l)) {
+        const int st_list[] = {-1, 2, 3, 4};
+        const int dz_list[] = {0, 32, 16};
+        for (int st : st_list)
+            for (int dz : dz_list)
+                for (int by : {0, 8}) cand.push_back({st, by, dz});
+    } else {
+        cl_status s0 = apply_tiles(l, 0, 0, 0);
+        if (s0 != CL_OK) return s0;
+        const int by_auto = l->BY;
+        std::vector<int> st_list = {-1, 0};
+        if (scalar_pass_tma_ok(l->p.precision, l->N))
+            for (int st = 2; st <= 6; ++st) st_list.push_back(st);
+        for (int st : st_list)
+            for (int dz : {0, -1})
+                for (int by : {0, by_auto > 1 ? by_auto / 2 : 0}) {
+                    std::array<int, 3> c = {st, by, dz};
+                    if (std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
+                }
+    }
+    double best_us = 1e300;
+    std::array<int, 3> best_c = {0, 0, 0};
+    for (const auto& c : cand) {
+        if (apply_tiles(l, c[0], c[1], c[2]) != CL_OK) continue;
+        double us = 0.0;
+        if (time_trials(l, 2, 5, &us) != CL_OK) continue;
+        if (us < best_us) {
+            best_us = us;
+            best_c = c;
+        }
+    }
+    cl_status s = apply_tiles(l, best_c[0], best_c[1], best_c[2]);
+    if (s != CL_OK) return s;
+    CUDA_TRY(l, cudaStreamSynchronize(l->stream));
+    l->diag_valid = false;
+    if (cache_path && best_us < 1e300) {
+        if (FILE* f = fopen(cache_path, "a")) {
+            fprintf(f, "{\"key\": \"%s\", \"stages\": %d, \"by\": %d, \"dz\": %d, \"us\": %.3f}\n", key.c_str(),
+                    best_c[0], best_c[1], best_c[2], best_us);
+            fclose(f);
+        }
+    }
+    if (best) { best[0] = best_c[0]; best[1] = best_c[1]; best[2] = best_c[2]; best[3] = best_us; }
+    return CL_OK;
 }
 
 cl_status cl_step(cl_lattice* l, int32_t nsteps)

@@ -225,3 +225,57 @@ def test_ensemble_tma_and_direct_loaders_agree(cl, prec):
             assert rel_l2(a[0][m], other[0][m]) < 1e-14
             assert rel_l2(a[1][m], other[1][m]) < 1e-14
             assert a[2][m]["rho"] == pytest.approx(other[2][m]["rho"], rel=1e-13)
+
+
+def test_autotune_keeps_the_state_and_caches_its_choice(cl, tmp_path):
+    sizes = [16, 24, 32, 16]
+    params = member_params(sizes, 1, seed=29)
+    cache = str(tmp_path / "tune.jsonl")
+    with cl.Lattice(16, 1.0, 1, cl.CL_PREC_FP32_KAHAN, cl.CL_INT_VV2, alpha=ALPHA, kappa=KAPPA, dt=0.02,
+                    member_N=sizes, member_L=[P["L"] for P in params]) as g:
+        g.cl_set_potential(cl.CL_POT_POLY, [x for P in params for x in P["pot"]])
+        for m, P in enumerate(params):
+            g.cl_set_state(cl.CL_FIELD_PHI0, P["phi"][0].astype(np.float32), member=m)
+            g.cl_set_state(cl.CL_FIELD_PI0, P["pi"][0].astype(np.float32), member=m)
+            g.cl_set_scalars(P["a0"], math.nan, 0.0, member=m)
+        g.cl_step(3)
+        before = [(g.cl_get_state(cl.CL_FIELD_PHI0, member=m), g.cl_get_state(cl.CL_FIELD_PI0, member=m),
+                   g.cl_get_scalars(m)) for m in range(4)]
+        stages, by, dz, us = g.cl_autotune(cache)
+        assert us > 0 and stages in (-1, 2, 3, 4)
+        for m in range(4):
+            assert np.array_equal(g.cl_get_state(cl.CL_FIELD_PHI0, member=m), before[m][0])
+            assert np.array_equal(g.cl_get_state(cl.CL_FIELD_PI0, member=m), before[m][1])
+            # a' at the integer time is re-synchronised through a pass whose FP64 reduction order
+            # depends on the tiling: equal to rounding
+            assert g.cl_get_scalars(m) == pytest.approx(before[m][2], rel=1e-12)
+        again = g.cl_autotune(cache)  # cache hit: the same choice without trials
+        assert again == (stages, by, dz, pytest.approx(us, rel=1e-3))
+        g.cl_step(4)
+        phis = [g.cl_get_state(cl.CL_FIELD_PHI0, member=m) for m in range(4)]
+    lines = open(cache).read().strip().splitlines()
+    assert len(lines) == 1 and '"key": "ensemble B=4' in lines[0]
+    # the tuned run follows the same trajectory as the default tiling
+    ref = run_ensemble(cl, params, 1, 1, 0, 0.02, 7)
+    for m in range(4):
+        assert rel_l2(phis[m], ref[0][m][0]) < 1e-6
+
+
+def test_autotune_single_lattice(cl):
+    N = 64
+    phi, pi = inputs.scalar_state(N, 2, seed=31, fbar=(1.0, 0.0), amp=1e-3, pamp=1e-3)
+    with cl.Lattice(N, 20.0, 2, cl.CL_PREC_FP32_KAHAN, cl.CL_INT_YOSHIDA4, alpha=0.0, kappa=0.1, dt=0.005) as g:
+        g.cl_set_potential(cl.CL_POT_M2_G2, [1.0, 100.0])
+        for f in range(2):
+            g.cl_set_state(cl.CL_FIELD_PHI0 + f, phi[f].astype(np.float32))
+            g.cl_set_state(cl.CL_FIELD_PI0 + f, pi[f].astype(np.float32))
+        g.cl_set_scalars(1.0)
+        e0 = g.cl_energies()
+        stages, by, dz, us = g.cl_autotune()
+        assert us > 0
+        assert g.cl_energies()["rho"] == e0["rho"]
+        assert np.array_equal(g.cl_get_state(cl.CL_FIELD_PHI1), phi[1].astype(np.float32))
+    with cl.Lattice(8, 6.0, 1, cl.CL_PREC_FP64, cl.CL_INT_RK3_3) as g:
+        g.cl_set_potential(cl.CL_POT_M2, [1.0])
+        with pytest.raises(cl.CLError):
+            g.cl_autotune()
