@@ -70,6 +70,7 @@ def config(extra=None):
 
 
 KERNEL_SOURCES = ["paper_2607_24978_gb300/csrc/scalar_pass.cu", "paper_2607_24978_gb300/csrc/scalar_pass_tma.cuh",
+                  "paper_2607_24978_gb300/csrc/scalar_pass_tma_nr.cuh",
                   "paper_2607_24978_gb300/csrc/scalar_pass_common.cuh", "paper_2607_24978_gb300/csrc/kernel_common.cuh",
                   "paper_2607_24978_gb300/csrc/cl_internal.cuh"]
 
@@ -320,7 +321,7 @@ def run_ensemble_workload(args, world, rank, local, cl, torch, stream, hbm_peak,
     sites = sum(n ** 3 for n in sizes)
     tuned = None
     if args.stages is None and args.by is None and args.dz is None and not args.no_autotune:
-        st_, by_, dz_, us_ = g.cl_autotune()  # timed trial passes; the state is unchanged
+        st_, by_, dz_, us_, _ = g.cl_autotune()  # timed trial passes; the state is unchanged
         tuned = {"stages": st_, "tile_by": by_, "tile_dz": dz_, "us_per_trial_pass": us_}
     for opt, v in ((cl.CL_OPT_STAGES, args.stages), (cl.CL_OPT_TILE_BY, args.by), (cl.CL_OPT_TILE_DZ, args.dz)):
         if v is not None:
@@ -463,6 +464,8 @@ def make_lattice(cl, precision, stream, args=None):
             g.cl_set_option(cl.CL_OPT_TILE_BY, args.by)
         if args.dz is not None:
             g.cl_set_option(cl.CL_OPT_TILE_DZ, args.dz)
+        if args.variant is not None:
+            g.cl_set_option(cl.CL_OPT_PASS_VARIANT, args.variant)
     return g
 
 
@@ -523,8 +526,12 @@ def run_gpu(args, world, rank, local):
     bytes_launch = N ** 3 * BYTES_PER_SITE_PASS
     achieved = bytes_launch / pass_s / 1e9
     traffic = profiled_traffic()
+    tiles = {k: g.cl_get_option(o) for k, o in (("tile_by", cl.CL_OPT_TILE_BY), ("tile_dz", cl.CL_OPT_TILE_DZ),
+                                                ("stages", cl.CL_OPT_STAGES), ("variant", cl.CL_OPT_PASS_VARIANT))}
+    kname = ("k_scalar_pass_tma_nr" if tiles["variant"] == 1 else "k_scalar_pass_tma") if tiles["stages"] > 0 \
+        else "k_scalar_pass"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": traffic, "kernel": "k_scalar_pass_tma<float,2,kahan,4,3>",
+                "traffic": traffic, "kernel": "%s<float,2,kahan,4,%d>" % (kname, tiles["stages"]), "tiles": tiles,
                 "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_src}
 
     if args.profile:
@@ -590,6 +597,7 @@ def main():
     ap.add_argument("--stages", type=int, default=None, help="override CL_OPT_STAGES")
     ap.add_argument("--by", type=int, default=None, help="override CL_OPT_TILE_BY")
     ap.add_argument("--dz", type=int, default=None, help="override CL_OPT_TILE_DZ")
+    ap.add_argument("--variant", type=int, default=None, help="override CL_OPT_PASS_VARIANT (0 ring, 1 ringless)")
     ap.add_argument("--workload", default="preheat", choices=["preheat", "u1", "ensemble", "surrogate"],
                     help="preheat: the headline 256^3 two-field run; u1, ensemble: the other workloads")
     ap.add_argument("--members", type=int, default=None, help="ensemble size (default 1024)")

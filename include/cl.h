@@ -222,19 +222,30 @@ cl_status cl_set_hubble_limit(cl_lattice* l, double limit);
  * of one wave, each block a balanced contiguous range of planes).  CL_OPT_STAGES: TMA stage
  * buffers of the fused pass, 2..6, or -1 for the loader without TMA staging (0 = library
  * choice; rows that are not a multiple of 16 bytes always use the loader without TMA).
+ * CL_OPT_PASS_VARIANT: TMA-staged pass kernel, 1 = ringless (default: each warp drifts the
+ * neighbour rows it needs from the stage buffers, no consumer barrier; 16-byte vectors,
+ * 2..5 stages, other rows fall back to 0), 0 = drifted rows shared through a ring in shared
+ * memory with one consumer barrier per plane.  Both give bit-identical fields on the same
+ * tiles.
  * Errors: CL_EINVAL. */
-enum { CL_OPT_GRAPH = 0, CL_OPT_TILE_BY = 1, CL_OPT_TILE_DZ = 2, CL_OPT_STAGES = 3 };
+enum { CL_OPT_GRAPH = 0, CL_OPT_TILE_BY = 1, CL_OPT_TILE_DZ = 2, CL_OPT_STAGES = 3, CL_OPT_PASS_VARIANT = 4 };
 cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value);
+
+/* The value in effect for an option after the library's choices: rows per tile, planes per
+ * block (-1: persistent ranges), TMA stages (0: loader without TMA staging) and the pass
+ * variant that the fused pass runs with.  Ensembles report member 0's tile and the ring
+ * variant (0).  value: host pointer, written on success.  Errors: CL_EINVAL. */
+cl_status cl_get_option(cl_lattice* l, int32_t option, int64_t* value);
 
 /* Autotuner of the fused leapfrog pass (single lattices and ensembles, no gauge field):
  * times trial passes of candidate tilings -- TMA stage buffers (CL_OPT_STAGES), rows per tile
- * (CL_OPT_TILE_BY) and planes per work unit or z chunk (CL_OPT_TILE_DZ) -- and keeps the
- * fastest.  A trial pass does the full work of a pass (drift while loading, stencil kick,
+ * (CL_OPT_TILE_BY), planes per work unit or z chunk (CL_OPT_TILE_DZ) and, for single
+ * lattices, the pass kernel (CL_OPT_PASS_VARIANT) -- and keeps the fastest.  A trial pass does the full work of a pass (drift while loading, stencil kick,
  * energies) but writes into the spare buffers and commits nothing: the state, a, a' and t are
  * unchanged.  cache_path (may be NULL): a text file of earlier choices, one JSON object per
  * line, keyed by the lattice's shape, precision and field count; a hit applies the cached
- * choice without trials, a miss appends the new one.  best (may be NULL) receives
- * {stages, tile_by, tile_dz, microseconds per pass}.  Errors: CL_EINVAL (Runge-Kutta or
+ * choice without trials, a miss appends the new one.  best (may be NULL, else 5 doubles)
+ * receives {stages, tile_by, tile_dz, microseconds per pass, pass variant}.  Errors: CL_EINVAL (Runge-Kutta or
  * gauge lattice), CL_ESTATE (no potential), CL_ECUDA. */
 cl_status cl_autotune(cl_lattice* l, const char* cache_path, double* best);
 

@@ -23,12 +23,12 @@ CL_GAUGE_NONE, CL_GAUGE_U1_AXION = 0, 1
 CL_POT_LPHI4, CL_POT_M2, CL_POT_M2_G2, CL_POT_LPHI4_G2, CL_POT_POLY = 0, 1, 2, 3, 4
 CL_FIELD_PHI0, CL_FIELD_PHI1, CL_FIELD_PI0, CL_FIELD_PI1 = 0, 1, 2, 3
 CL_FIELD_THETA1, CL_FIELD_THETA2, CL_FIELD_THETA3, CL_FIELD_E1, CL_FIELD_E2, CL_FIELD_E3 = 4, 5, 6, 7, 8, 9
-CL_OPT_GRAPH, CL_OPT_TILE_BY, CL_OPT_TILE_DZ, CL_OPT_STAGES = 0, 1, 2, 3
+CL_OPT_GRAPH, CL_OPT_TILE_BY, CL_OPT_TILE_DZ, CL_OPT_STAGES, CL_OPT_PASS_VARIANT = 0, 1, 2, 3, 4
 
 # Every exported entry point of include/cl.h.
 EXPORTS = ["cl_init_lattice", "cl_free", "cl_set_potential", "cl_set_state", "cl_get_state", "cl_set_scalars",
            "cl_get_scalars", "cl_init_vacuum", "cl_step", "cl_sync", "cl_energies", "cl_spectrum",
-           "cl_set_gauge_coupling", "cl_set_hubble_limit", "cl_set_option", "cl_last_launch_count", "cl_strerror", "cl_last_error",
+           "cl_set_gauge_coupling", "cl_set_hubble_limit", "cl_set_option", "cl_get_option", "cl_last_launch_count", "cl_strerror", "cl_last_error",
            "cl_fused_pass_noalloc", "cl_surrogate_create", "cl_surrogate_free", "cl_surrogate_set_weights",
            "cl_surrogate_get_weights", "cl_surrogate_forward", "cl_surrogate_backward", "cl_surrogate_get_grads",
            "cl_surrogate_last_launch_count", "cl_surrogate_loss", "cl_surrogate_adamw", "cl_surrogate_channel_stats",
@@ -114,6 +114,7 @@ def lib():
         L.cl_set_gauge_coupling.argtypes = [C.c_void_p, C.c_double, C.c_double]
         L.cl_set_hubble_limit.argtypes = [C.c_void_p, C.c_double]
         L.cl_set_option.argtypes = [C.c_void_p, C.c_int32, C.c_int64]
+        L.cl_get_option.argtypes = [C.c_void_p, C.c_int32, P(C.c_int64)]
         L.cl_last_launch_count.argtypes = [C.c_void_p]
         L.cl_last_launch_count.restype = C.c_int64
         L.cl_strerror.argtypes = [C.c_int]
@@ -310,15 +311,20 @@ class Lattice:
     def cl_set_option(self, option, value):
         _check(self.h, lib().cl_set_option(self.h, int(option), int(value)))
 
+    def cl_get_option(self, option):
+        v = C.c_int64()
+        _check(self.h, lib().cl_get_option(self.h, int(option), C.byref(v)))
+        return v.value
+
     def cl_last_launch_count(self):
         return int(lib().cl_last_launch_count(self.h))
 
     def cl_autotune(self, cache_path=None):
         """Pick the fastest tiling from timed trial passes (state unchanged); returns
-        (stages, tile_by, tile_dz, microseconds per pass)."""
-        best = (C.c_double * 4)()
+        (stages, tile_by, tile_dz, microseconds per pass, pass variant)."""
+        best = (C.c_double * 5)()
         _check(self.h, lib().cl_autotune(self.h, cache_path.encode() if cache_path else None, best))
-        return int(best[0]), int(best[1]), int(best[2]), float(best[3])
+        return int(best[0]), int(best[1]), int(best[2]), float(best[3]), int(best[4])
 
 
 def cl_fused_pass_noalloc(desc):

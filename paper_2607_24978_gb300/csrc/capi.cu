@@ -50,6 +50,7 @@ struct cl_lattice {
     void* kphi[2][2] = {};  // Runge-Kutta auxiliaries (RK integrators only)
     void* kpi[2][2] = {};
     int rk_BY = 1, rk_DZ = 1, rk_nby = 1, rk_nbz = 1;
+    int variant = 0;          // TMA pass kernel in use (0 ring, 1 ringless)
     bool gauge = false;       // axion + compact U(1) links (one scalar field, Runge-Kutta)
     void* th[3][2] = {};      // link angles theta_i
     void* ef[3][2] = {};      // electric fields E_i
@@ -66,7 +67,7 @@ struct cl_lattice {
     bool diag_valid = false;
     double hubble_limit = 0.0;
     bool use_graph = true;
-    int opt_BY = 0, opt_DZ = 0, opt_stages = 0;
+    int opt_BY = 0, opt_DZ = 0, opt_stages = 0, opt_variant = 1;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t last_launches = 0;
     // batched ensemble (members > 1): per-member sizes, boxes, arena offsets and couplings
@@ -269,7 +270,9 @@ cl_status choose_tiles(cl_lattice* l)
     // direct loader, which measured faster for them.
     bool tma = l->opt_stages >= 0 && scalar_pass_tma_ok(prec, N) && scalar_pass_threads(prec, N, 1) <= 480 &&
                !(prec == CL_PREC_FP64 && l->opt_stages == 0);
-    const int max_consumers = tma ? 480 : 512;
+    // ringless variant (16-byte vectors): at most 448 consumers (blocks of <= 480 threads)
+    const bool want_nr = tma && l->opt_variant == 1 && l->VW * l->es == 16;
+    const int max_consumers = want_nr ? 448 : (tma ? 480 : 512);
     // Default tile: as many rows as the consumer threads allow (more warps per SM), with
     // three TMA stages; measured best on GB300 for 256^3 and 512^3 lattices.
     int BY = l->opt_BY > 0 ? l->opt_BY : (tma ? max_consumers / TX : (TX >= 256 ? 1 : 256 / TX));
@@ -277,17 +280,23 @@ cl_status choose_tiles(cl_lattice* l)
     if (BY < 1) BY = 1;
     while (BY > 1 && scalar_pass_threads(prec, N, BY) > max_consumers) --BY;
     int stages = 0;
+    // ringless TMA variant: 16-byte vectors only, 2..5 stages
+    const int var = want_nr ? 1 : 0;
     if (tma) {
-        stages = l->opt_stages > 0 ? l->opt_stages : 3;
+        const int smax = var ? 5 : 6;
+        stages = l->opt_stages > 0 ? (l->opt_stages > smax ? smax : l->opt_stages) : (var ? 4 : 3);
         if (l->opt_BY <= 0)
-            while (BY > 1 && scalar_pass_smem_bytes(prec, l->nf, N, BY, stages) > (size_t)kPassMaxSmem) --BY;
-        while (BY > 1 && scalar_pass_smem_bytes(prec, l->nf, N, BY, 2) > (size_t)kPassMaxSmem) BY /= 2;
-        while (stages > 2 && scalar_pass_smem_bytes(prec, l->nf, N, BY, stages) > (size_t)kPassMaxSmem) --stages;
-        if (scalar_pass_smem_bytes(prec, l->nf, N, BY, stages) > (size_t)kPassMaxSmem) stages = 0;
+            while (BY > 1 && scalar_pass_smem_bytes(prec, l->nf, N, BY, stages, var) > (size_t)kPassMaxSmem) --BY;
+        while (BY > 1 && scalar_pass_smem_bytes(prec, l->nf, N, BY, 2, var) > (size_t)kPassMaxSmem) BY /= 2;
+        while (stages > 2 && scalar_pass_smem_bytes(prec, l->nf, N, BY, stages, var) > (size_t)kPassMaxSmem) --stages;
+        if (scalar_pass_smem_bytes(prec, l->nf, N, BY, stages, var) > (size_t)kPassMaxSmem) stages = 0;
     }
-    while (BY > 1 && scalar_pass_smem_bytes(prec, l->nf, N, BY, stages) > (size_t)kPassMaxSmem) BY /= 2;
-    if (scalar_pass_threads(prec, N, BY) > 512 || scalar_pass_smem_bytes(prec, l->nf, N, BY, stages) > (size_t)kPassMaxSmem)
+    const int var_eff = stages > 0 ? var : 0;
+    while (BY > 1 && scalar_pass_smem_bytes(prec, l->nf, N, BY, stages, var_eff) > (size_t)kPassMaxSmem) BY /= 2;
+    if (scalar_pass_threads(prec, N, BY) > 512 ||
+        scalar_pass_smem_bytes(prec, l->nf, N, BY, stages, var_eff) > (size_t)kPassMaxSmem)
         return fail(l, CL_EINVAL, "lattice too large for the fused pass tiling (N=%d)", N);
+    l->variant = var_eff;
     const int nby = (N + BY - 1) / BY;
     l->BY = BY;
     l->stages = stages;
@@ -373,6 +382,7 @@ cl_status run_pass_impl(cl_lattice* l, const PassCoef& pc, int in, int out, int*
         A.flags = flags;
         A.stages = l->stages;
         A.grid = l->grid;
+        A.variant = l->variant;
         e = occ ? scalar_pass_blocks_per_sm(l->p.precision, l->nf, &A, l->VW, occ)
                 : launch_scalar_pass(l->p.precision, l->nf, &A, l->VW, l->stream);
     } else {
@@ -396,6 +406,7 @@ cl_status run_pass_impl(cl_lattice* l, const PassCoef& pc, int in, int out, int*
         A.flags = flags;
         A.stages = l->stages;
         A.grid = l->grid;
+        A.variant = l->variant;
         e = occ ? scalar_pass_blocks_per_sm(l->p.precision, l->nf, &A, l->VW, occ)
                 : launch_scalar_pass(l->p.precision, l->nf, &A, l->VW, l->stream);
     }
@@ -1035,6 +1046,20 @@ cl_status cl_set_hubble_limit(cl_lattice* l, double limit)
     return CL_OK;
 }
 
+cl_status cl_get_option(cl_lattice* l, int32_t option, int64_t* value)
+{
+    if (!l || !value) return CL_EINVAL;
+    const bool ens = is_ens(l);
+    switch (option) {
+    case CL_OPT_GRAPH: *value = l->use_graph ? 1 : 0; return CL_OK;
+    case CL_OPT_TILE_BY: *value = ens ? l->hmem[0].BY : l->BY; return CL_OK;
+    case CL_OPT_TILE_DZ: *value = ens ? l->hmem[0].DZ : l->DZ; return CL_OK;
+    case CL_OPT_STAGES: *value = ens ? l->ens_stages : l->stages; return CL_OK;
+    case CL_OPT_PASS_VARIANT: *value = ens ? 0 : l->variant; return CL_OK;
+    }
+    return fail(l, CL_EINVAL, "unknown option %d", option);
+}
+
 cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value)
 {
     if (!l) return CL_EINVAL;
@@ -1047,6 +1072,10 @@ cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value)
     case CL_OPT_TILE_DZ:
         if (value < -1 || value > l->N) return fail(l, CL_EINVAL, "tile DZ out of range");
         l->opt_DZ = (int)value;
+        return choose_tiles(l);
+    case CL_OPT_PASS_VARIANT:
+        if (value < 0 || value > 1) return fail(l, CL_EINVAL, "pass variant must be 0 or 1");
+        l->opt_variant = (int)value;
         return choose_tiles(l);
     case CL_OPT_STAGES:
         if (is_ens(l) && value > 4) return fail(l, CL_EINVAL, "ensembles take stages -1, 0 or 2..4");
@@ -1075,11 +1104,12 @@ static std::string tune_key(const cl_lattice* l)
     return buf;
 }
 
-static cl_status apply_tiles(cl_lattice* l, int stages, int by, int dz)
+static cl_status apply_tiles(cl_lattice* l, int stages, int by, int dz, int variant)
 {
     l->opt_stages = stages;
     l->opt_BY = by;
     l->opt_DZ = dz;
+    l->opt_variant = variant;
     return choose_tiles(l);
 }
 
@@ -1116,7 +1146,7 @@ cl_status cl_autotune(cl_lattice* l, const char* cache_path, double* best)
     if (cache_path) {
         if (FILE* f = fopen(cache_path, "r")) {
             char line[512];
-            int hit = 0, st = 0, by = 0, dz = 0;
+            int hit = 0, st = 0, by = 0, dz = 0, var = 1;
             double us = 0.0;
             while (fgets(line, sizeof(line), f)) {
                 const char* k = strstr(line, "\"key\": \"");
@@ -1124,42 +1154,49 @@ cl_status cl_autotune(cl_lattice* l, const char* cache_path, double* best)
                 k += 8;
                 const char* e = strchr(k, '"');
                 if (!e || std::string(k, e - k) != key) continue;
-                if (sscanf(e, "\", \"stages\": %d, \"by\": %d, \"dz\": %d, \"us\": %lf", &st, &by, &dz, &us) == 4) hit = 1;
+                if (sscanf(e, "\", \"stages\": %d, \"by\": %d, \"dz\": %d, \"variant\": %d, \"us\": %lf", &st, &by, &dz,
+                           &var, &us) == 5)
+                    hit = 1;
             }
             fclose(f);
-            if (hit && apply_tiles(l, st, by, dz) == CL_OK) {
-                if (best) { best[0] = st; best[1] = by; best[2] = dz; best[3] = us; }
+            if (hit && apply_tiles(l, st, by, dz, var) == CL_OK) {
+                if (best) { best[0] = st; best[1] = by; best[2] = dz; best[3] = us; best[4] = var; }
                 l->diag_valid = false;
                 return CL_OK;
             }
         }
     }
     // candidates
-    std::vector<std::array<int, 3>> cand;
+    // candidates {stages, BY, DZ, pass variant}
+    std::vector<std::array<int, 4>> cand;
     if (is_ens(l)) {
         const int st_list[] = {-1, 2, 3, 4};
         const int dz_list[] = {0, 32, 16};
         for (int st : st_list)
             for (int dz : dz_list)
-                for (int by : {0, 8}) cand.push_back({st, by, dz});
+                for (int by : {0, 8}) cand.push_back({st, by, dz, 1});
     } else {
-        cl_status s0 = apply_tiles(l, 0, 0, 0);
+        cl_status s0 = apply_tiles(l, 0, 0, 0, 1);
         if (s0 != CL_OK) return s0;
         const int by_auto = l->BY;
+        const bool nr_ok = l->VW * l->es == 16;  // the ringless kernel takes 16-byte vectors
         std::vector<int> st_list = {-1, 0};
         if (scalar_pass_tma_ok(l->p.precision, l->N))
             for (int st = 2; st <= 6; ++st) st_list.push_back(st);
         for (int st : st_list)
-            for (int dz : {0, -1})
-                for (int by : {0, by_auto > 1 ? by_auto / 2 : 0}) {
-                    std::array<int, 3> c = {st, by, dz};
-                    if (std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
-                }
+            for (int var : {0, 1}) {
+                if (var == 1 && (!nr_ok || st < 0 || st > 5)) continue;
+                for (int dz : {0, -1})
+                    for (int by : {0, by_auto > 1 ? by_auto / 2 : 0}) {
+                        std::array<int, 4> c = {st, by, dz, var};
+                        if (std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
+                    }
+            }
     }
     double best_us = 1e300;
-    std::array<int, 3> best_c = {0, 0, 0};
+    std::array<int, 4> best_c = {0, 0, 0, 1};
     for (const auto& c : cand) {
-        if (apply_tiles(l, c[0], c[1], c[2]) != CL_OK) continue;
+        if (apply_tiles(l, c[0], c[1], c[2], c[3]) != CL_OK) continue;
         double us = 0.0;
         if (time_trials(l, 2, 5, &us) != CL_OK) continue;
         if (us < best_us) {
@@ -1167,18 +1204,18 @@ cl_status cl_autotune(cl_lattice* l, const char* cache_path, double* best)
             best_c = c;
         }
     }
-    cl_status s = apply_tiles(l, best_c[0], best_c[1], best_c[2]);
+    cl_status s = apply_tiles(l, best_c[0], best_c[1], best_c[2], best_c[3]);
     if (s != CL_OK) return s;
     CUDA_TRY(l, cudaStreamSynchronize(l->stream));
     l->diag_valid = false;
     if (cache_path && best_us < 1e300) {
         if (FILE* f = fopen(cache_path, "a")) {
-            fprintf(f, "{\"key\": \"%s\", \"stages\": %d, \"by\": %d, \"dz\": %d, \"us\": %.3f}\n", key.c_str(),
-                    best_c[0], best_c[1], best_c[2], best_us);
+            fprintf(f, "{\"key\": \"%s\", \"stages\": %d, \"by\": %d, \"dz\": %d, \"variant\": %d, \"us\": %.3f}\n",
+                    key.c_str(), best_c[0], best_c[1], best_c[2], best_c[3], best_us);
             fclose(f);
         }
     }
-    if (best) { best[0] = best_c[0]; best[1] = best_c[1]; best[2] = best_c[2]; best[3] = best_us; }
+    if (best) { best[0] = best_c[0]; best[1] = best_c[1]; best[2] = best_c[2]; best[3] = best_us; best[4] = best_c[3]; }
     return CL_OK;
 }
 

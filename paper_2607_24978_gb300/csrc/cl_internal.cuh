@@ -65,6 +65,7 @@ struct ScalarPassArgs {
     int flags;
     int stages;         // TMA stage buffers (2..6), 0 = general loader
     int grid;           // persistent grid size (used when DZ < 0)
+    int variant;        // TMA kernel: 0 = shared ring of drifted rows, 1 = ringless
 };
 
 // Launch one fused scalar pass (drift -> stencil kick -> energies -> scale-factor update).
@@ -74,7 +75,7 @@ cudaError_t launch_scalar_pass(int precision, int nf, const void* args, int vw, 
 cudaError_t scalar_pass_blocks_per_sm(int precision, int nf, const void* args, int vw, int* blocks);
 int scalar_pass_vector_width(int precision, int N);
 size_t scalar_pass_smem(int precision, int nf, int N, int BY);
-size_t scalar_pass_smem_bytes(int precision, int nf, int N, int BY, int stages);
+size_t scalar_pass_smem_bytes(int precision, int nf, int N, int BY, int stages, int variant = 0);
 bool scalar_pass_tma_ok(int precision, int N);
 int scalar_pass_threads(int precision, int N, int BY);
 

@@ -118,15 +118,17 @@ __global__ void __launch_bounds__(512) k_scalar_pass(const ScalarPassArgs<T> A)
 }
 
 #include "scalar_pass_tma.cuh"
+#include "scalar_pass_tma_nr.cuh"
 
 // ------------------------------------------------------------------ launchers
-size_t scalar_pass_smem_bytes(int precision, int nf, int N, int BY, int stages)
+size_t scalar_pass_smem_bytes(int precision, int nf, int N, int BY, int stages, int variant)
 {
     const size_t es = precision == CL_PREC_FP64 ? 8 : 4;
     const size_t rows = (size_t)(BY + 2) * N * es;
     if (stages <= 0) return (size_t)nf * 3 * rows;  // direct loader: three-plane ring
-    // TMA loader: three-slot ring of drifted fields plus the stage buffers
     const size_t narr = (size_t)nf * (precision == CL_PREC_FP32_KAHAN ? 3 : 2);
+    if (variant == 1) return (size_t)stages * narr * rows;  // ringless: the stage buffers only
+    // TMA loader: three-slot ring of drifted fields plus the stage buffers
     return (size_t)nf * 3 * rows + (size_t)stages * narr * rows;
 }
 
@@ -137,6 +139,39 @@ static cudaError_t allow_smem(K kernel)
 }
 
 // Launch the pass, or (occ != nullptr) report how many blocks of it fit on one SM.
+// Ringless TMA kernel (16-byte vectors only), S = 2..5 stages.
+template <typename T, int NF, bool KAHAN, int VW>
+static cudaError_t launch_nr(const ScalarPassArgs<T>& A, dim3 grid, dim3 block, size_t smem, cudaStream_t s, int* occ)
+{
+    if constexpr (VW * sizeof(T) == 16) {
+        static bool attr[6] = {false, false, false, false, false, false};
+        const int S = A.stages;
+        if (S < 2 || S > 5) return cudaErrorInvalidValue;
+        cudaError_t e = cudaSuccess;
+#define CL_NR_CASE(SS)                                                                                             \
+    case SS:                                                                                                       \
+        if (!attr[SS]) {                                                                                           \
+            e = cudaFuncSetAttribute(k_scalar_pass_tma_nr<T, NF, KAHAN, VW, SS>,                                  \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kPassMaxSmem);                    \
+            if (e != cudaSuccess) return e;                                                                        \
+            attr[SS] = true;                                                                                       \
+        }                                                                                                          \
+        if (occ)                                                                                                   \
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_scalar_pass_tma_nr<T, NF, KAHAN, VW, SS>, \
+                                                                 block.x, smem);                                   \
+        k_scalar_pass_tma_nr<T, NF, KAHAN, VW, SS><<<grid, block, smem, s>>>(A);                                  \
+        return cudaGetLastError();
+        switch (S) {
+            CL_NR_CASE(2)
+            CL_NR_CASE(3)
+            CL_NR_CASE(4)
+            CL_NR_CASE(5)
+        }
+#undef CL_NR_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <typename T, int NF, bool KAHAN, int VW>
 static cudaError_t launch_one(const ScalarPassArgs<T>& A, cudaStream_t s, int* occ)
 {
@@ -144,7 +179,8 @@ static cudaError_t launch_one(const ScalarPassArgs<T>& A, cudaStream_t s, int* o
     const int TX = A.N / VW;
     dim3 block(((TX * A.BY + 31) / 32) * 32 + (A.stages > 0 ? 32 : 0));  // + producer warp
     dim3 grid(A.DZ > 0 ? A.nby * A.nbz : A.grid);  // DZ < 0: balanced persistent ranges
-    const size_t smem = scalar_pass_smem_bytes(prec, NF, A.N, A.BY, A.stages);
+    const size_t smem = scalar_pass_smem_bytes(prec, NF, A.N, A.BY, A.stages, A.variant);
+    if (A.variant == 1 && A.stages > 0) return launch_nr<T, NF, KAHAN, VW>(A, grid, block, smem, s, occ);
     static bool attr_set[8] = {false, false, false, false, false, false, false, false};
     const int si = A.stages < 0 ? 0 : (A.stages > 7 ? 7 : A.stages);
     cudaError_t e = cudaSuccess;

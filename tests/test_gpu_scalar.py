@@ -208,6 +208,82 @@ def test_tma_and_direct_loaders_identical(cl, N, nf, prec):
         assert np.array_equal(o[1], outs[0][1])
 
 
+@pytest.mark.parametrize("N,nf,prec,by,dz,stages",
+                         [(64, 2, 2, 3, 5, 4), (64, 1, 1, 0, 0, 0), (40, 2, 1, 7, 9, 2), (32, 1, 0, 3, 5, 3),
+                          (48, 2, 2, 16, 1, 5), (128, 2, 2, 0, 0, 0), (256, 2, 2, 0, 0, 0)])
+def test_ringless_and_ring_passes_identical(cl, N, nf, prec, by, dz, stages):
+    """The ringless TMA pass re-drifts the y-neighbour rows from the stage instead of sharing
+    drifted rows through a ring: the same arithmetic, so fields must agree bit for bit with the
+    ring pass, and energies and the scale factor too when both run the same tiles."""
+    phi, pi = inputs.scalar_state(N, nf, seed=17, fbar=(1.0, 0.1), amp=0.05, pamp=0.05)
+    dt = np.float64 if prec == 0 else np.float32
+    outs = []
+    for variant in (0, 1):
+        with gpu_lattice(cl, N, 9.0, nf, prec, cl.CL_INT_YOSHIDA4, expansion=True, alpha=1.0, kappa=0.2,
+                         dt=0.01) as g:
+            g.cl_set_potential(cl.CL_POT_POLY, [0.5, 1.0, 0.2 if nf == 2 else 0.0, 0.0, 3.0 if nf == 2 else 0.0])
+            if by:
+                g.cl_set_option(cl.CL_OPT_TILE_BY, by)
+                g.cl_set_option(cl.CL_OPT_TILE_DZ, dz)
+            if stages:
+                g.cl_set_option(cl.CL_OPT_STAGES, stages)
+            g.cl_set_option(cl.CL_OPT_PASS_VARIANT, variant)
+            for f in range(nf):
+                g.cl_set_state(cl.CL_FIELD_PHI0 + f, phi[f].astype(dt))
+                g.cl_set_state(cl.CL_FIELD_PI0 + f, pi[f].astype(dt))
+            g.cl_set_scalars(1.0)
+            g.cl_step(7)
+            e = g.cl_energies()
+            outs.append(download(g, cl, nf) + (e["a"], e["rho"], g.cl_get_scalars()))
+    for k in range(2):
+        assert np.array_equal(outs[1][k], outs[0][k])
+    if by:
+        assert outs[1][2:] == outs[0][2:]
+    else:  # default tiles differ (448 vs 480 consumer threads): the per-thread compensated FP32
+        # energy sums cover other sites, so energies agree to their rounding only
+        assert outs[1][2] == pytest.approx(outs[0][2], rel=1e-10)
+        assert outs[1][3] == pytest.approx(outs[0][3], rel=1e-10)
+        for u, v in zip(outs[1][4], outs[0][4]):
+            assert u == pytest.approx(v, rel=1e-10)
+
+
+def test_effective_options_reported(cl):
+    """cl_get_option reports the tiling the library chose: the ringless TMA pass where rows are
+    16-byte vectors, the ring variant otherwise; overrides are reflected."""
+    with gpu_lattice(cl, 256, 9.0, 2, 2, cl.CL_INT_YOSHIDA4, expansion=True, alpha=0.0, kappa=0.1, dt=0.005) as g:
+        assert g.cl_get_option(cl.CL_OPT_PASS_VARIANT) == 1
+        assert g.cl_get_option(cl.CL_OPT_STAGES) == 4
+        assert g.cl_get_option(cl.CL_OPT_TILE_BY) == 7
+        assert g.cl_get_option(cl.CL_OPT_TILE_DZ) == 64
+        assert g.cl_get_option(cl.CL_OPT_GRAPH) == 1
+        g.cl_set_option(cl.CL_OPT_PASS_VARIANT, 0)
+        assert g.cl_get_option(cl.CL_OPT_PASS_VARIANT) == 0
+        assert g.cl_get_option(cl.CL_OPT_STAGES) == 3
+        g.cl_set_option(cl.CL_OPT_STAGES, -1)
+        assert g.cl_get_option(cl.CL_OPT_STAGES) == 0
+        with pytest.raises(cl.CLError):
+            g.cl_get_option(99)
+    with gpu_lattice(cl, 34, 9.0, 1, 1, cl.CL_INT_VV2, expansion=True, alpha=0.0, kappa=0.1, dt=0.005) as g:
+        assert g.cl_get_option(cl.CL_OPT_PASS_VARIANT) == 0  # 8-byte vectors: no ringless kernel
+
+
+def test_ringless_pass_matches_oracle(cl):
+    """Yoshida-4 with Kahan drifts through the ringless pass against the FP64 oracle."""
+    N, L, dt, n = 40, 0.9 * 40, 0.02, 12
+    phi, pi = inputs.scalar_state(N, 2, seed=21, fbar=(0.8, 0.1), amp=0.05, pamp=0.05)
+    m = O.make_model(N, L, nf=2, alpha=1.0, kappa=0.5, expansion=True, m2=(0.3, 0.2), lam=(1.0, 0.5), g2=2.0)
+    st = O.State(phi.copy(), pi.copy(), np.array([1.0, 0.2, 0.0]))
+    with gpu_lattice(cl, N, L, 2, 2, cl.CL_INT_YOSHIDA4, expansion=True, alpha=1.0, kappa=0.5, dt=dt) as g:
+        g.cl_set_potential(cl.CL_POT_POLY, [0.3, 1.0, 0.2, 0.5, 2.0])
+        g.cl_set_option(cl.CL_OPT_PASS_VARIANT, 1)
+        upload(g, cl, st, 2)
+        g.cl_step(n)
+        gphi, gpi = download(g, cl, 2)
+    O.step(m, st, O.YOSHIDA4, dt, n)
+    assert rel_l2(gphi, st.phi) < 1e-5
+    assert rel_l2(gpi, st.pi) < 1e-5
+
+
 def test_tiles_do_not_change_results(cl):
     N = 32
     phi, pi = inputs.scalar_state(N, 1, seed=9, fbar=(1.0,), amp=0.1, pamp=0.1)
