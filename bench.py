@@ -110,12 +110,18 @@ class Clocks:
         self.p = None
 
     def __enter__(self):
+        self.first = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
+        if self.p:  # the sampler is live (its first line, before the timed region, is read) or gone
+            import select
+            r, _, _ = select.select([self.p.stdout], [], [], 5.0)
+            if r:
+                self.first = self.p.stdout.readline()
         return self
 
     def __exit__(self, *a):
@@ -128,6 +134,8 @@ class Clocks:
                 self.p.kill()
                 out = ""
             self.lines = [l for l in out.splitlines() if l.strip()]
+            if not self.lines and self.first:  # a region shorter than one sampling period
+                self.lines = [self.first]
 
     def summary(self):
         sm, smax, reasons = [], None, set()
@@ -588,7 +596,8 @@ def run_gpu(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 1000; 200 oracle steps of the reference arm)")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -604,6 +613,8 @@ def main():
     ap.add_argument("--no-train", action="store_true", help="surrogate workload: throughput only")
     ap.add_argument("--no-autotune", action="store_true", help="ensemble workload: default tiling, no trial passes")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 200 if args.impl == "reference" else 1000
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
