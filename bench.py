@@ -253,6 +253,10 @@ U1_STAGES = 3
 # algorithmic bytes of one RK stage per site: phi, pi, theta_1..3, E_1..3 and their eight
 # Runge-Kutta auxiliaries, read + write, 4 B each
 U1_BYTES_PER_SITE_STAGE = 8 * 2 * 2 * 4
+RK_STAGES = 5
+# algorithmic bytes of one RK4-5 step per site, two fields, FP32 + Kahan: phi, pi, k_phi, k_pi,
+# c read + write in four stages; the first stage (A = 0) reads no k
+RK_BYTES_PER_SITE_STEP = 2 * 4 * (4 * 5 * 2 + (5 * 2 - 2))
 ENS = dict(members=1024, sizes=(32, 48, 64), lam=(1e-6, 1e-3), L=8.0 * math.pi, dt=0.01, alpha=1.0, kappa=0.1,
            seed=1234)
 # VV-2, one field, FP32 + Kahan: phi, pi, c read + write
@@ -310,6 +314,39 @@ def run_u1_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_
             "gpu_launches": launches, "clocks": clocks,
             "energies_end": {"a": e["a"], "rho": e["rho"], "KE": e["KE"], "GB": e["GB"],
                              "gauss_violation": e["gauss_violation"], "hubble_violation": e["hubble_violation"]}}
+
+
+def run_rk_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src):
+    """The headline two-field lattice advanced by the low-storage RK4-5 stages instead of the
+    leapfrog (the non-symplectic evolver measured on the same 256^3 state)."""
+    g = cl.Lattice(N, L, 2, cl.CL_PREC_FP32_KAHAN, cl.CL_INT_RK4_5, expansion=True, alpha=ALPHA, kappa=KAPPA, dt=DT,
+                   stream=stream.cuda_stream)
+    g.cl_set_potential(cl.CL_POT_M2_G2, [1.0, G2])
+    g.cl_init_vacuum(SEED, 1e30, AMP2, (1.0, 0.0), (0.0, 0.0))
+    g.cl_step(args.warmup)
+    g.cl_sync()
+    barrier(world)
+    el, launches, clocks = timed_region(torch, g, stream, args.steps)
+    barrier(world)
+    el_max = max_over_ranks(el, world)
+    e = g.cl_energies()
+    g.close()
+    stage_s = el / (args.steps * RK_STAGES)
+    bytes_stage = N ** 3 * RK_BYTES_PER_SITE_STEP / RK_STAGES
+    achieved = bytes_stage / stage_s / 1e9
+    return {"metric": "Gsite-updates/s, 256^3 two fields, RK4-5", "value": world * N ** 3 * args.steps / el_max / 1e9,
+            "unit": "Gsite-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config({"workload": "two-field preheating m2phi2+g2phi2chi2, q=1e4, 256^3, RK4-5 (2N), "
+                                          "FP32+Kahan, FP64 reductions, dt=0.005, self-consistent expansion",
+                              "integrator": "rk4_5", "passes_per_step": RK_STAGES}),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                         "kernel": "k_rk_stage<float,2,kahan,4> (mean over the 5 stages)",
+                         "algorithmic_bytes_per_launch": bytes_stage},
+            "gpu_launches": launches, "clocks": clocks,
+            "energies_end": {"a": e["a"], "rho": e["rho"], "hubble_violation": e["hubble_violation"]}}
 
 
 def run_ensemble_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src):
@@ -511,7 +548,7 @@ def run_gpu(args, world, rank, local):
             print(json.dumps(line), flush=True)
         return
     if args.workload != "preheat":
-        fn = run_u1_workload if args.workload == "u1" else run_ensemble_workload
+        fn = {"u1": run_u1_workload, "rk": run_rk_workload}.get(args.workload, run_ensemble_workload)
         line = fn(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src)
         if rank == 0:
             print(json.dumps(line), flush=True)
@@ -607,7 +644,7 @@ def main():
     ap.add_argument("--by", type=int, default=None, help="override CL_OPT_TILE_BY")
     ap.add_argument("--dz", type=int, default=None, help="override CL_OPT_TILE_DZ")
     ap.add_argument("--variant", type=int, default=None, help="override CL_OPT_PASS_VARIANT (0 ring, 1 ringless)")
-    ap.add_argument("--workload", default="preheat", choices=["preheat", "u1", "ensemble", "surrogate"],
+    ap.add_argument("--workload", default="preheat", choices=["preheat", "u1", "ensemble", "surrogate", "rk"],
                     help="preheat: the headline 256^3 two-field run; u1, ensemble: the other workloads")
     ap.add_argument("--members", type=int, default=None, help="ensemble size (default 1024)")
     ap.add_argument("--no-train", action="store_true", help="surrogate workload: throughput only")

@@ -64,7 +64,12 @@ enum {
     CL_INT_VV2 = 0,      /* velocity Verlet, O(dt^2), one fused lattice pass per step           */
     CL_INT_YOSHIDA4 = 1, /* Yoshida composition of three VV steps, O(dt^4), three passes/step   */
     CL_INT_RK3_3 = 2,    /* low-storage 2N Runge-Kutta, 3rd order, 3 stages (Williamson 1980)   */
-    CL_INT_RK4_5 = 3     /* low-storage 2N Runge-Kutta, 4th order, 5 stages (Carpenter-Kennedy 1994) */
+    CL_INT_RK4_5 = 3,    /* low-storage 2N Runge-Kutta, 4th order, 5 stages (Carpenter-Kennedy 1994) */
+    /* Higher-order Yoshida compositions (section "Non-symplectic evolvers" lists orders up to
+     * 10): the symmetric triple jump applied recursively to VV-2, 3^((p-2)/2) passes/step   */
+    CL_INT_YOSHIDA6 = 4,  /* O(dt^6), 9 passes/step   */
+    CL_INT_YOSHIDA8 = 5,  /* O(dt^8), 27 passes/step  */
+    CL_INT_YOSHIDA10 = 6  /* O(dt^10), 81 passes/step */
 };
 
 enum { CL_GAUGE_NONE = 0, CL_GAUGE_U1_AXION = 1 };
@@ -90,7 +95,7 @@ enum {
 /* Batched ensembles (members > 1): B independent lattices of sizes member_N[m]
  * (2..512 each) and boxes member_L[m], each with its own couplings, a, a', t and step
  * count, advanced together by one launch per pass (N and L are then ignored).  They share
- * nfields, precision, integrator (CL_INT_VV2 or CL_INT_YOSHIDA4), alpha, kappa and dt;
+ * nfields, precision, integrator (VV-2 or a Yoshida composition), alpha, kappa and dt;
  * gauge must be CL_GAUGE_NONE.  Every call that takes a member addresses one of them; the
  * fields of member m hold member_N[m]^3 elements.  Errors at creation: CL_EINVAL (sizes),
  * CL_EUNSUPPORTED (Runge-Kutta or gauge ensembles). */

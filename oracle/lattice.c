@@ -272,15 +272,23 @@ static void rk_step(const orc_model* m, int scheme, double h, double* phi, doubl
     free(Fpi);
 }
 
-/* Yoshida (1990) fourth-order composition of three velocity-Verlet steps. */
-static void yoshida4_step(const orc_model* m, double h, double* phi, double* pi, double* abt, double* tmp)
+/* Symmetric composition of order p (Yoshida 1990, section 4): a method of order p-2 applied
+ * with steps x1 h, x0 h, x1 h, where x1 = 1/(2 - 2^(1/(p-1))) and x0 = 1 - 2 x1 cancel the
+ * leading error term; order 2 is one velocity-Verlet step.  Order 4 gives the three-step
+ * Yoshida scheme, orders 6, 8 and 10 take 9, 27 and 81 velocity-Verlet steps. */
+static void composed_step(const orc_model* m, int order, double h, double* phi, double* pi, double* abt,
+                          double* tmp)
 {
-    const double c = cbrt(2.0);
-    const double w1 = 1.0 / (2.0 - c);
-    const double w0 = -c / (2.0 - c);
-    vv_step(m, w1 * h, phi, pi, abt, tmp);
-    vv_step(m, w0 * h, phi, pi, abt, tmp);
-    vv_step(m, w1 * h, phi, pi, abt, tmp);
+    if (order <= 2) {
+        vv_step(m, h, phi, pi, abt, tmp);
+        return;
+    }
+    const double c = pow(2.0, 1.0 / (order - 1));
+    const double x1 = 1.0 / (2.0 - c);
+    const double x0 = -c / (2.0 - c);
+    composed_step(m, order - 2, x1 * h, phi, pi, abt, tmp);
+    composed_step(m, order - 2, x0 * h, phi, pi, abt, tmp);
+    composed_step(m, order - 2, x1 * h, phi, pi, abt, tmp);
 }
 
 void orc_step(const orc_model* m, int scheme, double h, int nsteps,
@@ -295,7 +303,10 @@ void orc_step(const orc_model* m, int scheme, double h, int nsteps,
     for (int s = 0; s < nsteps; ++s) {
         switch (scheme) {
         case ORC_VV2: vv_step(m, h, phi, pi, abt, tmp); break;
-        case ORC_YOSHIDA4: yoshida4_step(m, h, phi, pi, abt, tmp); break;
+        case ORC_YOSHIDA4: composed_step(m, 4, h, phi, pi, abt, tmp); break;
+        case ORC_YOSHIDA6: composed_step(m, 6, h, phi, pi, abt, tmp); break;
+        case ORC_YOSHIDA8: composed_step(m, 8, h, phi, pi, abt, tmp); break;
+        case ORC_YOSHIDA10: composed_step(m, 10, h, phi, pi, abt, tmp); break;
         default: rk_step(m, scheme, h, phi, pi, abt); break;
         }
     }

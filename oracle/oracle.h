@@ -63,7 +63,8 @@ enum {
 };
 
 /* Integrators (section "Non-symplectic evolvers" and the symplectic family it lists). */
-enum { ORC_VV2 = 0, ORC_YOSHIDA4 = 1, ORC_RK3_3 = 2, ORC_RK4_5 = 3 };
+enum { ORC_VV2 = 0, ORC_YOSHIDA4 = 1, ORC_RK3_3 = 2, ORC_RK4_5 = 3, ORC_YOSHIDA6 = 4, ORC_YOSHIDA8 = 5,
+       ORC_YOSHIDA10 = 6 };
 
 /* ---- potential and lattice operators ---- */
 double orc_V(const orc_model* m, double f0, double f1);

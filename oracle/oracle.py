@@ -12,7 +12,7 @@ import numpy as np
 
 from . import build_oracle
 
-VV2, YOSHIDA4, RK3_3, RK4_5 = 0, 1, 2, 3
+VV2, YOSHIDA4, RK3_3, RK4_5, YOSHIDA6, YOSHIDA8, YOSHIDA10 = 0, 1, 2, 3, 4, 5, 6
 E_NAMES = ["K0", "K1", "G0", "G1", "V", "KEM", "GEM", "rho", "p", "hubble_violation", "a", "b"]
 
 

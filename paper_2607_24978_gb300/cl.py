@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libcl.so")
 
 CL_OK, CL_EINVAL, CL_ENOMEM, CL_ECUDA, CL_ENAN, CL_ECONSTRAINT, CL_ETIMEOUT, CL_ESTATE, CL_EUNSUPPORTED = range(9)
 CL_PREC_FP64, CL_PREC_FP32_KAHAN, CL_PREC_FP32 = 0, 1, 2
-CL_INT_VV2, CL_INT_YOSHIDA4, CL_INT_RK3_3, CL_INT_RK4_5 = 0, 1, 2, 3
+CL_INT_VV2, CL_INT_YOSHIDA4, CL_INT_RK3_3, CL_INT_RK4_5, CL_INT_YOSHIDA6, CL_INT_YOSHIDA8, CL_INT_YOSHIDA10 = range(7)
 CL_GAUGE_NONE, CL_GAUGE_U1_AXION = 0, 1
 CL_POT_LPHI4, CL_POT_M2, CL_POT_M2_G2, CL_POT_LPHI4_G2, CL_POT_POLY = 0, 1, 2, 3, 4
 CL_FIELD_PHI0, CL_FIELD_PHI1, CL_FIELD_PI0, CL_FIELD_PI1 = 0, 1, 2, 3

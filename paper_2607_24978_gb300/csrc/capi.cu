@@ -517,11 +517,34 @@ cl_status query_blocks_per_sm(cl_lattice* l, int* per_sm)
 }
 
 // Yoshida (1990) fourth-order weights.
-void yoshida_weights(double& w1, double& w0)
+// Order of a leapfrog-family integrator (2 for VV-2, 4..10 for the Yoshida compositions).
+int leapfrog_order(int integrator)
 {
-    const double c = cbrt(2.0);
-    w1 = 1.0 / (2.0 - c);
-    w0 = -c / (2.0 - c);
+    switch (integrator) {
+    case CL_INT_YOSHIDA4: return 4;
+    case CL_INT_YOSHIDA6: return 6;
+    case CL_INT_YOSHIDA8: return 8;
+    case CL_INT_YOSHIDA10: return 10;
+    default: return 2;
+    }
+}
+
+// Time weights of the velocity-Verlet substeps of one step: Yoshida's symmetric triple
+// jump (Yoshida 1990, section 4) applied recursively, S_{p+2}(h) = S_p(x1 h) S_p(x0 h) S_p(x1 h)
+// with x1 = 1 / (2 - 2^(1/(p+1))) and x0 = 1 - 2 x1, starting from VV-2 (p = 2): 3^((p-2)/2)
+// substeps for order p.
+void composition_weights(int order, std::vector<double>& w)
+{
+    w.assign(1, 1.0);
+    for (int p = 2; p < order; p += 2) {
+        const double c = pow(2.0, 1.0 / (p + 1));
+        const double x1 = 1.0 / (2.0 - c), x0 = -c / (2.0 - c);
+        std::vector<double> n;
+        n.reserve(3 * w.size());
+        for (double x : {x1, x0, x1})
+            for (double v : w) n.push_back(x * v);
+        w.swap(n);
+    }
 }
 
 // Pass schedule of one time step in staggered form, and the opening half-kick.
@@ -539,24 +562,26 @@ std::vector<PassCoef> step_schedule(const cl_lattice* l)
             pc.B = B[i];
             s.push_back(pc);
         }
-    } else if (l->p.integrator == CL_INT_VV2) {
-        s.push_back({h, 0.5 * h, h, P_DRIFT | P_COMMIT | P_COUNT_STEP});
     } else {
-        double w1, w0;
-        yoshida_weights(w1, w0);
-        s.push_back({w1 * h, 0.5 * w1 * h, 0.5 * (w1 + w0) * h, P_DRIFT | P_COMMIT});
-        s.push_back({w0 * h, 0.5 * w0 * h, 0.5 * (w0 + w1) * h, P_DRIFT | P_COMMIT});
-        s.push_back({w1 * h, 0.5 * w1 * h, w1 * h, P_DRIFT | P_COMMIT | P_COUNT_STEP});
+        // substep i: drift w_i h; the closing half-kick of substep i merged with the opening
+        // half-kick of substep i+1 (of the next step's first substep after the last one)
+        std::vector<double> w;
+        composition_weights(leapfrog_order(l->p.integrator), w);
+        const size_t S = w.size();
+        for (size_t i = 0; i < S; ++i) {
+            const double wn = i + 1 < S ? w[i + 1] : w[0];
+            s.push_back({w[i] * h, 0.5 * w[i] * h, 0.5 * (w[i] + wn) * h,
+                         P_DRIFT | P_COMMIT | (i + 1 == S ? P_COUNT_STEP : 0)});
+        }
     }
     return s;
 }
 
 double open_kick(const cl_lattice* l)
 {
-    if (l->p.integrator == CL_INT_VV2) return 0.5 * l->p.dt;
-    double w1, w0;
-    yoshida_weights(w1, w0);
-    return 0.5 * w1 * l->p.dt;
+    std::vector<double> w;
+    composition_weights(leapfrog_order(l->p.integrator), w);
+    return 0.5 * w[0] * l->p.dt;
 }
 
 cl_status open_leapfrog(cl_lattice* l)
@@ -781,7 +806,7 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
     }
     if (p->members < 0) return CL_EINVAL;
     if ((!ens && (p->N < 2 || p->N > kMaxN)) || p->nfields < 1 || p->nfields > 2 || p->precision < 0 || p->precision > 2 ||
-        p->integrator < 0 || p->integrator > 3 || p->gauge < 0 || p->gauge > 1 || !(p->L > 0) || !(p->dt > 0) ||
+        p->integrator < 0 || p->integrator > CL_INT_YOSHIDA10 || p->gauge < 0 || p->gauge > 1 || !(p->L > 0) || !(p->dt > 0) ||
         !(p->a0 > 0) || p->reserved != 0)
         return CL_EINVAL;
     if (p->gauge == CL_GAUGE_U1_AXION) {

@@ -141,6 +141,29 @@ def test_two_field_yoshida4_parity(cl, prec, tol):
     assert e["a"] == pytest.approx(st.abt[0], rel=tol)
 
 
+@pytest.mark.parametrize("scheme,prec,n", [(4, 0, 6), (5, 0, 3), (6, 0, 1), (4, 1, 6), (5, 2, 3)])
+def test_higher_yoshida_parity(cl, scheme, prec, n):
+    """Yoshida-6/8/10 (9, 27, 81 fused passes per step) against the FP64 oracle, two fields,
+    self-consistent expansion."""
+    N, L, dt = 16, 6.0, 0.02
+    phi, pi = inputs.scalar_state(N, 2, seed=23, fbar=(0.8, 0.1), amp=0.05, pamp=0.05)
+    m = O.make_model(N, L, nf=2, alpha=1.0, kappa=0.5, expansion=True, m2=(0.3, 0.2), lam=(1.0, 0.5), g2=2.0)
+    st = O.State(phi.copy(), pi.copy(), np.array([1.0, 0.2, 0.0]))
+    with gpu_lattice(cl, N, L, 2, prec, scheme, expansion=True, alpha=1.0, kappa=0.5, dt=dt) as g:
+        g.cl_set_potential(cl.CL_POT_POLY, [0.3, 1.0, 0.2, 0.5, 2.0])
+        upload(g, cl, st, 2)
+        g.cl_step(n)
+        gphi, gpi = download(g, cl, 2)
+        e = g.cl_energies()
+        assert g.cl_last_launch_count() == {4: 9, 5: 27, 6: 81}[scheme] * n + 1  # + the opening half-kick
+    O.step(m, st, {4: O.YOSHIDA6, 5: O.YOSHIDA8, 6: O.YOSHIDA10}[scheme], dt, n)
+    tol = 1e-10 if prec == 0 else 1e-4
+    assert rel_l2(gphi, st.phi) < tol
+    assert rel_l2(gpi, st.pi) < tol
+    assert e["a"] == pytest.approx(st.abt[0], rel=tol)
+    assert e["t"] == pytest.approx(n * dt, rel=1e-12)
+
+
 @pytest.mark.parametrize("N,by,dz", [(6, 4, 4), (10, 3, 4), (34, 5, 7), (7, 2, 3), (5, 1, 2), (48, 0, 0)])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_ragged_sizes_and_tiles(cl, N, by, dz, prec):
