@@ -128,4 +128,25 @@ struct ConvDWArgs {
 int conv_dw_chunks(int N);
 cudaError_t launch_conv_dw(const ConvDWArgs& A, cudaStream_t s);
 
+// Weight and bias gradients of a hidden layer (C -> C, C = 16, 32 or 48) on the tensor
+// cores: dW[t][co][ci] = sum_n g[n][co] h[n + o(t)][ci] from BF16 g and (activated) h,
+// db[co] = sum_n g[n][co]; block partials, then fixed-order sums (deterministic).
+struct ConvDWTCArgs {
+    const __nv_bfloat16* h;     // layer input, BF16 [N^3][C] (activations)
+    const __nv_bfloat16* g;     // gradient of the layer output, BF16 [N^3][C]
+    int N;                      // multiple of 16
+    int nslot;                  // staging slots, 2 .. conv_dw_tc_slots(C, N)
+    int nb;                     // blocks per tap group (grid nb x 2)
+    int nbias;                  // blocks of the bias partials
+    float* part0;               // [nb][18][C][C]: taps of planes tz = 0, 1
+    float* part1;               // [nb][9][C][C]: taps of plane tz = 2
+    double* bpart;              // [nbias][C]
+    float* dW;                  // [27][C][C]
+    float* db;                  // [C]
+    int* status;                // ST_TIMEOUT on a bounded wait that gave up
+};
+int conv_dw_tc_slots(int C, int N);  // 0: shape not supported on the tensor cores
+size_t conv_dw_tc_smem(int C, int N, int nslot);
+cudaError_t launch_conv_dw_tc(int C, const ConvDWTCArgs& A, cudaStream_t s);
+
 }  // namespace clk

@@ -140,6 +140,38 @@ def test_shift_network_is_exact(cl):
     assert np.array_equal(y, x[..., :2] + shifted[..., :2])
 
 
+@pytest.mark.parametrize("N,C", [(16, 16), (32, 32), (32, 48)])
+def test_tensor_core_weight_gradients_are_exact(cl, N, C):
+    """Hidden-layer weight gradients on the tensor cores against the oracle, bit for bit.
+    Channel-copying layers (centre tap 3 -> C, +x tap with a channel rotation, +y tap summing
+    all channels, +z tap C -> 2) on positive inputs k/8 keep every ReLU gate open; with
+    gradients k/8 all products are multiples of 1/64 and every partial sum stays below
+    2^17, so any summation order is exact in FP32.  Layers 1 and 2 (the tensor-core weight
+    gradients: every output-channel row of layer 1, both z-tap block groups, the periodic
+    halos) and layer 0 must then equal the oracle exactly."""
+    taps = [13, 14, 16, 22]  # (0,0,0), (+1,0,0), (0,+1,0), (0,0,+1)
+    W0 = np.zeros((27, C, 3))
+    W0[taps[0], np.arange(C), np.arange(C) % 3] = 1.0
+    W1 = np.zeros((27, C, C))
+    W1[taps[1], np.arange(C), (np.arange(C) + 1) % C] = 1.0
+    W2 = np.zeros((27, C, C))
+    W2[taps[2]] = 1.0
+    W3 = np.zeros((27, 2, C))
+    W3[taps[3], [0, 1], [0, 1]] = 1.0
+    net = [(W, np.zeros(W.shape[1])) for W in (W0, W1, W2, W3)]
+    x = (inputs.rng(11).integers(4, 16, size=(N, N, N, 3)) / 8.0).astype(np.float64)
+    g = (inputs.rng(12).integers(-8, 9, size=(N, N, N, 2)) / 8.0).astype(np.float64)
+    y, dx, grads, nf = run(cl, N, net, 1, cl.CL_SG_BF16, x, g)
+    yo, cache = O.surrogate_forward(x, net, O.RELU)
+    dxo, go = O.surrogate_backward(cache, net, g, O.RELU)
+    for l in (0, 1, 2):
+        assert np.array_equal(grads[l][0], go[l][0]), l
+        assert np.array_equal(grads[l][1], go[l][1]), l
+    # layer 3 reads h2 (sums of C inputs) rounded to BF16
+    assert rel_l2(grads[3][0], go[3][0]) < 1e-2
+    assert np.array_equal(dx, dxo)
+
+
 def test_invalid_configurations(cl):
     with pytest.raises(cl.CLError):
         cl.Surrogate(24, 3, 2, 48, 6, 1, cl.CL_SG_BF16)   # BF16 needs N % 16 == 0
