@@ -37,11 +37,10 @@ struct cl_surrogate {
     void* du[2] = {nullptr, nullptr};  // gradient ping-pong (BF16 or FP32)
     float* partial = nullptr;          // weight-gradient partials
     int chunks = 1;
-    // tensor-core weight gradients of the hidden layers (BF16 mode): blocks per tap group,
-    // staging slots, bias-partial blocks and their partial buffers
-    int dw_nb = 0, dw_nslot = 0, dw_nbias = 0;
-    float *dw_part0 = nullptr, *dw_part1 = nullptr;
-    double* dw_bpart = nullptr;
+    // tensor-core weight gradients (BF16 mode): blocks per tap group and their partials
+    // (weights of the two tap groups, biases)
+    int dw_nb = 0;
+    float *dw_part0 = nullptr, *dw_part1 = nullptr, *dw_bpart = nullptr;
     int* status = nullptr;
     bool have_forward = false, have_loss = false;
     int64_t launches = 0;
@@ -265,21 +264,17 @@ cl_status cl_surrogate_create(cl_surrogate** out, const cl_surrogate_params* p)
          cudaMalloc(&s->dx, (size_t)s->V * p->in_channels * 4) == cudaSuccess &&
          cudaMalloc(&s->partial, part * 4) == cudaSuccess && cudaMalloc(&s->status, sizeof(int)) == cudaSuccess &&
          cudaMemset(s->status, 0, sizeof(int)) == cudaSuccess;
-    if (ok && p->precision == CL_SG_BF16 && L >= 3 && conv_dw_tc_slots(p->hidden, p->N) >= 2) {
-        // hidden-layer weight gradients on the tensor cores: about 64 or more rows per block,
-        // two tap groups sharing the SMs; bias partials of about 8192 sites each
+    if (ok && p->precision == CL_SG_BF16 && conv_dw_tc_slots(16, p->N) >= 2) {
+        // weight gradients on the tensor cores: about 64 or more rows per block, two tap
+        // groups sharing the SMs; partials sized for the widest layer (hidden x hidden)
         const int C = p->hidden;
         const int64_t rows = (int64_t)p->N * p->N;
         int64_t nb = rows / 64;
         nb = nb < 1 ? 1 : (nb > s->nsm / 2 ? s->nsm / 2 : nb);
-        int64_t nbias = s->V / 8192;
-        nbias = nbias < 1 ? 1 : (nbias > 1024 ? 1024 : nbias);
         s->dw_nb = (int)(nb < 1 ? 1 : nb);
-        s->dw_nslot = conv_dw_tc_slots(C, p->N);
-        s->dw_nbias = (int)nbias;
         ok = cudaMalloc(&s->dw_part0, (size_t)s->dw_nb * 18 * C * C * 4) == cudaSuccess &&
              cudaMalloc(&s->dw_part1, (size_t)s->dw_nb * 9 * C * C * 4) == cudaSuccess &&
-             cudaMalloc(&s->dw_bpart, (size_t)s->dw_nbias * C * 8) == cudaSuccess;
+             cudaMalloc(&s->dw_bpart, (size_t)s->dw_nb * C * 4) == cudaSuccess;
     }
     if (!ok || cudaDeviceSynchronize() != cudaSuccess) {
         cl_surrogate_free(s);
@@ -373,22 +368,30 @@ cl_status cl_surrogate_backward(cl_surrogate* s, const float* g, float* dx, int3
                              s->stream) != cudaSuccess)
         return CL_ECUDA;
     auto wgrad = [&](int l, const void* h, int h_bf16, int h_act, const void* gg, int g_bf16) {
-        if (s->dw_nb > 0 && l >= 1 && l <= L - 2 && h_bf16 && g_bf16 && !h_act) {  // hidden layer: tensor cores
+        // BF16 mode: every layer's weight gradients on the tensor cores (the thin FP32 network
+        // input and loss gradient are rounded to BF16 while staged, as in the forward)
+        const int cip = tc_width(s->cin[l]), cop = tc_width(s->cout[l]);
+        if (s->dw_nb > 0 && !h_act && conv_dw_tc_slots(cip, s->p.N) >= 2) {
             ConvDWTCArgs A{};
-            A.h = (const __nv_bfloat16*)h;
-            A.g = (const __nv_bfloat16*)gg;
+            A.h = h;
+            A.h_f32 = h_bf16 ? 0 : 1;
+            A.h_c = s->cin[l];
+            A.g = gg;
+            A.g_f32 = g_bf16 ? 0 : 1;
+            A.g_c = s->cout[l];
+            A.CI = s->cin[l];
+            A.CO = s->cout[l];
             A.N = s->p.N;
-            A.nslot = s->dw_nslot;
+            A.nslot = conv_dw_tc_slots(cip, s->p.N);
             A.nb = s->dw_nb;
-            A.nbias = s->dw_nbias;
             A.part0 = s->dw_part0;
             A.part1 = s->dw_part1;
             A.bpart = s->dw_bpart;
             A.dW = s->dW[l];
             A.db = s->db[l];
             A.status = s->status;
-            s->launches += 3;
-            return check(launch_conv_dw_tc(s->p.hidden, A, s->stream));
+            s->launches += 2;
+            return check(launch_conv_dw_tc(cip, cop, A, s->stream));
         }
         ConvDWArgs A{};
         A.h = h;

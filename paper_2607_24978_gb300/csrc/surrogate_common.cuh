@@ -128,25 +128,27 @@ struct ConvDWArgs {
 int conv_dw_chunks(int N);
 cudaError_t launch_conv_dw(const ConvDWArgs& A, cudaStream_t s);
 
-// Weight and bias gradients of a hidden layer (C -> C, C = 16, 32 or 48) on the tensor
-// cores: dW[t][co][ci] = sum_n g[n][co] h[n + o(t)][ci] from BF16 g and (activated) h,
+// Weight and bias gradients of a layer on the tensor cores (channels padded to CIP, COP =
+// 16, 32 or 48; at most one of g and h FP32): dW[t][co][ci] = sum_n g[n][co] h[n + o(t)][ci],
 // db[co] = sum_n g[n][co]; block partials, then fixed-order sums (deterministic).
 struct ConvDWTCArgs {
-    const __nv_bfloat16* h;     // layer input, BF16 [N^3][C] (activations)
-    const __nv_bfloat16* g;     // gradient of the layer output, BF16 [N^3][C]
+    const void* h;              // layer input: BF16 [N^3][CIP] activations, or FP32 [N^3][h_c]
+    int h_f32, h_c;
+    const void* g;              // output gradient: BF16 [N^3][COP], or FP32 [N^3][g_c]
+    int g_f32, g_c;
+    int CI, CO;                 // real channels (the padded ones read as zeros)
     int N;                      // multiple of 16
-    int nslot;                  // staging slots, 2 .. conv_dw_tc_slots(C, N)
+    int nslot;                  // staging slots, 2 .. conv_dw_tc_slots(CIP, N)
     int nb;                     // blocks per tap group (grid nb x 2)
-    int nbias;                  // blocks of the bias partials
-    float* part0;               // [nb][18][C][C]: taps of planes tz = 0, 1
-    float* part1;               // [nb][9][C][C]: taps of plane tz = 2
-    double* bpart;              // [nbias][C]
-    float* dW;                  // [27][C][C]
-    float* db;                  // [C]
+    float* part0;               // [nb][18][COP][CIP]: taps of planes tz = 0, 1
+    float* part1;               // [nb][9][COP][CIP]: taps of plane tz = 2
+    float* bpart;               // [nb][COP]: bias partials
+    float* dW;                  // [27][CO][CI]
+    float* db;                  // [CO]
     int* status;                // ST_TIMEOUT on a bounded wait that gave up
 };
-int conv_dw_tc_slots(int C, int N);  // 0: shape not supported on the tensor cores
-size_t conv_dw_tc_smem(int C, int N, int nslot);
-cudaError_t launch_conv_dw_tc(int C, const ConvDWTCArgs& A, cudaStream_t s);
+int conv_dw_tc_slots(int CIP, int N);  // 0: shape not supported on the tensor cores
+size_t conv_dw_tc_smem(int CIP, int N, int nslot);
+cudaError_t launch_conv_dw_tc(int CIP, int COP, const ConvDWTCArgs& A, cudaStream_t s);
 
 }  // namespace clk
