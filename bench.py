@@ -279,6 +279,8 @@ def run_u1_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_
                    alpha=c["alpha"], kappa=c["kappa"], dt=c["dt"], stream=stream.cuda_stream)
     g.cl_set_potential(cl.CL_POT_M2, [c["m2"]])
     g.cl_set_gauge_coupling(c["alphaL"], c["ws2"])
+    if args.dz is not None:  # planes per block of the U(1) kernels (tuning runs)
+        g.cl_set_option(cl.CL_OPT_TILE_DZ, args.dz)
     phi, pi = inputs.scalar_state(N, 1, seed=c["seed"], fbar=(c["phi0"],), amp=1e-5, pamp=1e-5,
                                   pbar=(c["dphi0"],))
     E = inputs.solenoidal_field(N, seed=c["seed"] + 1, amp=c["e_amp"], dtype=np.float32)

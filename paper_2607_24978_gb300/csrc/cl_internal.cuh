@@ -127,12 +127,13 @@ struct U1Args {
     double A, B, h;
     double hubble_limit;
     int flags;    // P_EXPANSION, P_FIRST_STAGE, P_COUNT_STEP, P_ENERGY_ONLY, P_HUBBLE_INIT
+    int dz;       // planes per block (all three kernels)
 };
 // what: 0 = plaquette fields, 1 = stage (or energies with P_ENERGY_ONLY), 2 = Gauss diagnostic.
 // The plaquette launch writes its magnetic-energy partials after the stage's, at
-// partials[u1_grid_blocks(N) * kMaxQ + block].
+// partials[u1_grid_blocks(N, dz) * kMaxQ + block].
 cudaError_t launch_u1(int precision, const void* args, int what, cudaStream_t s);
-int u1_grid_blocks(int N);
+int u1_grid_blocks(int N, int dz);
 
 // Batched ensemble of independent lattices (ensemble_pass.cu).  Every array class (phi,
 // pi, compensation, per field and buffer) is one arena holding the members back to back,

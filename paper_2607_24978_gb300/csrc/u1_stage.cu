@@ -32,7 +32,7 @@
 // div-[a^(1-alpha) E + g W] for the diagnostics.
 //
 // Work decomposition (all three kernels): block b owns a 32 x 8 tile in (x, y) of the
-// planes [bz DZ, bz DZ + DZ); thread (lane, warp) owns column x = 32 bx + lane of row
+// planes [bz dz, bz dz + dz) (dz chosen by the library); thread (lane, warp) owns column x = 32 bx + lane of row
 // y = 8 by + warp and marches up the planes, so most y and z neighbours it gathers were
 // loaded by its own block shortly before (L1 hits).  Linear indices fit 32 bits for
 // N <= 1536; coordinates and their periodic neighbours are formed once per site.
@@ -43,13 +43,11 @@
 
 namespace clk {
 
-constexpr int kU1DZ = 8;  // planes per block
-
 // The tile of this block and this thread's column and row in it.
 struct U1Tile {
     uint32_t x, y, z0, z1;
     bool active;
-    __device__ __forceinline__ explicit U1Tile(uint32_t N)
+    __device__ __forceinline__ U1Tile(uint32_t N, uint32_t dz)
     {
         const uint32_t ntx = (N + 31) / 32, nty = (N + 7) / 8;
         uint32_t b = blockIdx.x;
@@ -58,8 +56,8 @@ struct U1Tile {
         const uint32_t by = b % nty, bz = b / nty;
         x = bx * 32 + (threadIdx.x & 31);
         y = by * 8 + (threadIdx.x >> 5);
-        z0 = bz * kU1DZ;
-        z1 = z0 + kU1DZ < N ? z0 + kU1DZ : N;
+        z0 = bz * dz;
+        z1 = z0 + dz < N ? z0 + dz : N;
         active = x < N && y < N;
     }
 };
@@ -99,7 +97,7 @@ __global__ void __launch_bounds__(256) k_u1_plaquettes(const U1Args<T> A)
     const uint32_t N = (uint32_t)A.N;
     const T dx = (T)A.dx;
     Acc<T> accGB;
-    const U1Tile tile(N);
+    const U1Tile tile(N, (uint32_t)A.dz);
     for (uint32_t z = tile.z0; z < tile.z1; ++z) {
         if (!tile.active) break;
         const uint32_t n = (z * N + tile.y) * N + tile.x;
@@ -154,7 +152,7 @@ __device__ __forceinline__ T clover(const T* const f, const Nbhd& s, const Off& 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_u1_stage(const U1Args<T> A)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_u1_stage(const U1Args<T> A)
 {
     __shared__ double s_coef[6];
     __shared__ double s_red[32][kMaxQ];
@@ -180,7 +178,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_u1_stage(const 
     const T h = (T)A.h, cA = (T)A.A, cB = (T)A.B;
     Acc<T> accK, accG, accV, accKE;
 
-    const U1Tile tile(N);
+    const U1Tile tile(N, (uint32_t)A.dz);
     for (uint32_t z = tile.z0; z < tile.z1; ++z) {
         if (!tile.active) break;
         const uint32_t n = (z * N + tile.y) * N + tile.x;
@@ -328,7 +326,7 @@ __global__ void __launch_bounds__(256) k_u1_gauss(const U1Args<T> A)
     const double ca = pow(A.scal->a, 1.0 - A.alpha);
     const double b4 = 0.25 / (A.dx * A.dx);
     double gmax = 0.0, smax = 0.0;
-    const U1Tile tile(N);
+    const U1Tile tile(N, (uint32_t)A.dz);
     for (uint32_t z = tile.z0; z < tile.z1; ++z) {
         if (!tile.active) break;
         const uint32_t n = (z * N + tile.y) * N + tile.x;
@@ -385,22 +383,23 @@ __global__ void __launch_bounds__(256) k_u1_gauss(const U1Args<T> A)
 
 // Grid of all three kernels (the stage kernel reads the plaquette kernel's partials by
 // block index, so both use this grid).
-static int u1_grid(int N)
+static int u1_grid(int N, int dz)
 {
-    return ((N + 31) / 32) * ((N + 7) / 8) * ((N + kU1DZ - 1) / kU1DZ);
+    return ((N + 31) / 32) * ((N + 7) / 8) * ((N + dz - 1) / dz);
 }
 
 template <typename T>
 static cudaError_t launch_u1_t(const U1Args<T>& A, int what, cudaStream_t s)
 {
-    const int grid = u1_grid(A.N);
+    if (A.dz < 1 || A.dz > A.N) return cudaErrorInvalidValue;
+    const int grid = u1_grid(A.N, A.dz);
     if (what == 0) k_u1_plaquettes<T><<<grid, 256, 0, s>>>(A);
     else if (what == 1) k_u1_stage<T><<<grid, 256, 0, s>>>(A);
     else k_u1_gauss<T><<<grid, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 
-int u1_grid_blocks(int N) { return u1_grid(N); }
+int u1_grid_blocks(int N, int dz) { return u1_grid(N, dz); }
 
 cudaError_t launch_u1(int precision, const void* args, int what, cudaStream_t s)
 {
