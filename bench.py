@@ -367,10 +367,11 @@ def run_ensemble_workload(args, world, rank, local, cl, torch, stream, hbm_peak,
         g.cl_init_vacuum(c["seed"], kcut, float(lam[m]), (1.0,), (0.0,), member=m)
     sites = sum(n ** 3 for n in sizes)
     tuned = None
-    if args.stages is None and args.by is None and args.dz is None and not args.no_autotune:
-        st_, by_, dz_, us_, _ = g.cl_autotune()  # timed trial passes; the state is unchanged
-        tuned = {"stages": st_, "tile_by": by_, "tile_dz": dz_, "us_per_trial_pass": us_}
-    for opt, v in ((cl.CL_OPT_STAGES, args.stages), (cl.CL_OPT_TILE_BY, args.by), (cl.CL_OPT_TILE_DZ, args.dz)):
+    if args.stages is None and args.by is None and args.dz is None and args.variant is None and not args.no_autotune:
+        st_, by_, dz_, us_, var_ = g.cl_autotune()  # timed trial passes; the state is unchanged
+        tuned = {"stages": st_, "tile_by": by_, "tile_dz": dz_, "variant": var_, "us_per_trial_pass": us_}
+    for opt, v in ((cl.CL_OPT_PASS_VARIANT, args.variant), (cl.CL_OPT_STAGES, args.stages), (cl.CL_OPT_TILE_BY, args.by),
+                   (cl.CL_OPT_TILE_DZ, args.dz)):
         if v is not None:
             g.cl_set_option(opt, v)
     g.cl_step(args.warmup)
@@ -380,7 +381,12 @@ def run_ensemble_workload(args, world, rank, local, cl, torch, stream, hbm_peak,
     barrier(world)
     el_max = max_over_ranks(el, world)
     es = g.cl_energies(c["members"])
+    tiles = {k: g.cl_get_option(o) for k, o in (("stages", cl.CL_OPT_STAGES), ("variant", cl.CL_OPT_PASS_VARIANT),
+                                                ("member0_tile_by", cl.CL_OPT_TILE_BY),
+                                                ("member0_tile_dz", cl.CL_OPT_TILE_DZ))}
     g.close()
+    kname = ("k_ensemble_pass_tma<float,1,kahan,4,%d,%s>" % (tiles["stages"], "ringless" if tiles["variant"] else "ring")
+             if tiles["stages"] > 0 else "k_ensemble_pass<float,1,kahan,4>")
     pass_s = el / args.steps
     bytes_pass = sites * ENS_BYTES_PER_SITE
     achieved = bytes_pass / pass_s / 1e9
@@ -394,7 +400,7 @@ def run_ensemble_workload(args, world, rank, local, cl, torch, stream, hbm_peak,
                        "l2": "inputs (%.0f MB) larger than L2; no flush" % (sites * 6 * 4 / 1e6)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
-                         "kernel": "k_ensemble_pass_tma<float,1,kahan,4,S>", "algorithmic_bytes_per_launch": bytes_pass},
+                         "kernel": kname, "tiles": tiles, "algorithmic_bytes_per_launch": bytes_pass},
             "autotune": tuned,
             "gpu_launches": launches, "clocks": clocks,
             "energies_end": {"members": len(es), "max_hubble_violation": max(x["hubble_violation"] for x in es),

@@ -224,14 +224,16 @@ cl_status cl_set_hubble_limit(cl_lattice* l, double limit);
  * launches.  CL_OPT_TILE_BY: rows per block of the fused scalar pass (0 = library
  * choice).  CL_OPT_TILE_DZ: planes per block (0 = library choice: the y tiles are cut into
  * the same z chunks so that one wave of blocks covers the lattice; -1 = a persistent grid
- * of one wave, each block a balanced contiguous range of planes).  CL_OPT_STAGES: TMA stage
- * buffers of the fused pass, 2..6, or -1 for the loader without TMA staging (0 = library
- * choice; rows that are not a multiple of 16 bytes always use the loader without TMA).
+ * of one wave, each block a balanced contiguous range of planes; for the axion-U(1)
+ * kernels, the planes each 32 x 8 tile marches through).  CL_OPT_STAGES: TMA stage buffers
+ * of the fused pass, 2..6, or -1 for the loader without TMA staging (0 = library choice;
+ * rows that are not a multiple of 16 bytes always use the loader without TMA; ensembles
+ * clamp to 2..4 with the ring kernel and 3..6 ringless).
  * CL_OPT_PASS_VARIANT: TMA-staged pass kernel, 1 = ringless (default: each warp drifts the
  * neighbour rows it needs from the stage buffers, no consumer barrier; 16-byte vectors,
- * 2..5 stages, other rows fall back to 0), 0 = drifted rows shared through a ring in shared
- * memory with one consumer barrier per plane.  Both give bit-identical fields on the same
- * tiles.
+ * 2..5 stages (ensembles 3..6), other rows fall back to 0), 0 = drifted rows shared through
+ * a ring in shared memory with one consumer barrier per plane.  Both give bit-identical
+ * fields on the same tiles.
  * Errors: CL_EINVAL. */
 enum { CL_OPT_GRAPH = 0, CL_OPT_TILE_BY = 1, CL_OPT_TILE_DZ = 2, CL_OPT_STAGES = 3, CL_OPT_PASS_VARIANT = 4 };
 cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value);

@@ -84,7 +84,7 @@ struct cl_lattice {
     EnsMember* d_members = nullptr;
     EnsItem* d_items = nullptr;
     int* d_sched = nullptr;         // items by decreasing size
-    int nitems = 0, ens_grid = 0, ens_stages = 0, ens_stage_stride = 0, ens_ring_slot = 0;
+    int nitems = 0, ens_grid = 0, ens_stages = 0, ens_stage_stride = 0, ens_ring_slot = 0, ens_variant = 0;
     float* sg_buf = nullptr;        // surrogate jumps: packed input (3 V), output (2 V), snapshot (3 V)
     size_t ens_smem = 0;
     char err[512] = {0};
@@ -202,20 +202,27 @@ cl_status ens_tiles(cl_lattice* l)
         if ((int64_t)l->nf * (BY + 2) * N > ring_max) ring_max = (int64_t)l->nf * (BY + 2) * N;
     }
     if (smem > (size_t)kPassMaxSmem) return fail(l, CL_EINVAL, "ensemble member too large for the pass tiling");
-    // TMA staging when every member row is a multiple of 16 bytes (16-byte vectors); by
-    // default as many stages (up to 4) as leave room for two blocks per SM
-    int stages = 0;
+    // TMA staging when every member row is a multiple of 16 bytes (16-byte vectors): the
+    // ringless kernel (default; 3..6 stages, no ring of drifted rows) or the ring kernel
+    // (2..4 stages); by default as many stages (up to 5 / 4) as leave room for two blocks
+    // per SM
+    int stages = 0, var = 0;
     if (l->opt_stages >= 0 && l->VW * l->es == 16) {
-        auto bytes = [&](int S) { return (size_t)(S * stage_max + 3 * ring_max) * l->es; };
+        var = l->opt_variant == 1 ? 1 : 0;
+        const int smin = var ? 3 : 2, smax = var ? 6 : 4;
+        auto bytes = [&](int S) { return (size_t)(S * stage_max + (var ? 0 : 3 * ring_max)) * l->es; };
         if (l->opt_stages >= 2) {
-            stages = bytes(l->opt_stages) <= (size_t)kPassMaxSmem ? l->opt_stages : 0;
+            const int S = l->opt_stages < smin ? smin : (l->opt_stages > smax ? smax : l->opt_stages);
+            stages = bytes(S) <= (size_t)kPassMaxSmem ? S : 0;
         } else {
-            for (int S = 4; S >= 2 && !stages; --S)
+            for (int S = var ? 5 : 4; S >= smin && !stages; --S)
                 if (bytes(S) <= (size_t)kPassMaxSmem / 2) stages = S;
         }
         if (stages) smem = bytes(stages);
     }
+    if (!stages) var = 0;
     l->ens_stages = stages;
+    l->ens_variant = var;
     l->ens_stage_stride = (int)stage_max;
     l->ens_ring_slot = (int)ring_max;
     l->nitems = (int)l->hitems.size();
@@ -250,7 +257,7 @@ cl_status ens_tiles(cl_lattice* l)
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
         return fail(l, CL_ECUDA, "cannot query the SM count");
-    CUDA_TRY(l, ensemble_pass_blocks_per_sm(prec, l->nf, l->VW, stages, smem, &per_sm));
+    CUDA_TRY(l, ensemble_pass_blocks_per_sm(prec, l->nf, l->VW, stages, var, smem, &per_sm));
     if (per_sm < 1) return fail(l, CL_EINVAL, "ensemble pass does not fit on an SM");
     const int64_t wave = (int64_t)per_sm * nsm;
     l->ens_grid = (int)(wave < l->nitems ? wave : l->nitems);
@@ -488,6 +495,7 @@ cl_status run_ens_pass_t(cl_lattice* l, const PassCoef& pc, int in, int out, int
     A.stages = l->ens_stages;
     A.stage_stride = l->ens_stage_stride;
     A.ring_slot = l->ens_ring_slot;
+    A.variant = l->ens_variant;
     const int n = A.item_end - A.item_begin;
     const int grid = n < l->ens_grid ? n : l->ens_grid;
     cudaError_t e = launch_ensemble_pass(l->p.precision, l->nf, &A, l->VW, grid, l->ens_smem, l->stream);
@@ -1095,7 +1103,7 @@ cl_status cl_get_option(cl_lattice* l, int32_t option, int64_t* value)
     case CL_OPT_TILE_BY: *value = ens ? l->hmem[0].BY : l->BY; return CL_OK;
     case CL_OPT_TILE_DZ: *value = ens ? l->hmem[0].DZ : (l->gauge ? l->u1_dz : l->DZ); return CL_OK;
     case CL_OPT_STAGES: *value = ens ? l->ens_stages : l->stages; return CL_OK;
-    case CL_OPT_PASS_VARIANT: *value = ens ? 0 : l->variant; return CL_OK;
+    case CL_OPT_PASS_VARIANT: *value = ens ? l->ens_variant : l->variant; return CL_OK;
     }
     return fail(l, CL_EINVAL, "unknown option %d", option);
 }
@@ -1118,7 +1126,6 @@ cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value)
         l->opt_variant = (int)value;
         return choose_tiles(l);
     case CL_OPT_STAGES:
-        if (is_ens(l) && value > 4) return fail(l, CL_EINVAL, "ensembles take stages -1, 0 or 2..4");
         if (value < -1 || value == 1 || value > 6) return fail(l, CL_EINVAL, "stages must be -1, 0 or 2..6");
         l->opt_stages = (int)value;
         return choose_tiles(l);
@@ -1210,11 +1217,12 @@ cl_status cl_autotune(cl_lattice* l, const char* cache_path, double* best)
     // candidates {stages, BY, DZ, pass variant}
     std::vector<std::array<int, 4>> cand;
     if (is_ens(l)) {
-        const int st_list[] = {-1, 2, 3, 4};
+        // {stages, variant}: the direct loader, the ring kernel and the ringless kernel
+        const int sv_list[][2] = {{-1, 1}, {2, 0}, {3, 0}, {4, 0}, {3, 1}, {4, 1}, {5, 1}, {6, 1}};
         const int dz_list[] = {0, 32, 16};
-        for (int st : st_list)
+        for (const auto& sv : sv_list)
             for (int dz : dz_list)
-                for (int by : {0, 8}) cand.push_back({st, by, dz, 1});
+                for (int by : {0, 8}) cand.push_back({sv[0], by, dz, sv[1]});
     } else {
         cl_status s0 = apply_tiles(l, 0, 0, 0, 1);
         if (s0 != CL_OK) return s0;

@@ -168,15 +168,17 @@ struct EnsPassArgs {
     double d, e, k;       // pass coefficients (already x dt), as in ScalarPassArgs
     double hubble_limit;
     int flags;
-    int stages;           // TMA stage buffers (2..4) or 0 for the direct loader
+    int stages;           // TMA stage buffers (ring 2..4, ringless 3..6) or 0 for the direct loader
     int stage_stride;     // elements of one stage buffer (largest member tile)
     int ring_slot;        // elements of one ring slot of drifted fields (largest member tile)
+    int variant;          // TMA kernel: 0 = ring of drifted rows, 1 = ringless
 };
 constexpr int kEnsTmaThreads = kEnsThreads + 32;  // consumers + one producer warp
 // One pass over the items [item_begin, item_end) with `grid` persistent blocks.
 cudaError_t launch_ensemble_pass(int precision, int nf, const void* args, int vw, int grid, size_t smem,
                                  cudaStream_t s);
-cudaError_t ensemble_pass_blocks_per_sm(int precision, int nf, int vw, int stages, size_t smem, int* blocks);
+cudaError_t ensemble_pass_blocks_per_sm(int precision, int nf, int vw, int stages, int variant, size_t smem,
+                                        int* blocks);
 
 // Vacuum initial conditions: fills the half spectrum (kx in [0, N/2]) of delta f and
 // delta pi for one field into two complex-double buffers of N*N*(N/2+1) entries.

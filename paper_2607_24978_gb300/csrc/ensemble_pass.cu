@@ -98,7 +98,10 @@ __global__ void __launch_bounds__(kEnsThreads) k_ensemble_pass(const EnsPassArgs
 // evaluate the member's pass prefactors, reduce the item's partial sums on named barrier
 // 2 and, for a member's last item, run the member's epilogue.  All waits are bounded; a
 // timeout is reported through the status word of member 0.
-template <typename T, int NF, bool KAHAN, int VW, int S>
+// NR (ringless): no ring and no per-plane barrier; each warp re-drifts the y-neighbour rows
+// it needs from the previous plane's stage, which it releases only after that plane's kick
+// (the producer then runs S - 2 planes ahead).
+template <typename T, int NF, bool KAHAN, int VW, int S, bool NR>
 __global__ void __launch_bounds__(kEnsTmaThreads, NF == 1 ? 2 : 1) k_ensemble_pass_tma(const EnsPassArgs<T> A)
 {
     constexpr int RING = 3;
@@ -171,9 +174,14 @@ __global__ void __launch_bounds__(kEnsTmaThreads, NF == 1 ? 2 : 1) k_ensemble_pa
             }
         }
     } else {
-        int st = 0;
+        int st = 0, st_prev = 0;
         uint32_t full_phase = 0;
         int rnew = 0, rmid = RING - 1;
+        const int lane = tid & 31;
+        auto release = [&](int s_idx) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_empty[s_idx]);
+        };
         ZMarch<T, NF, VW> Z;
         for (int k = blockIdx.x; k < A.item_end - A.item_begin; k += gridDim.x) {
             const int it = A.sched ? A.sched[k] : A.item_begin + k;
@@ -197,16 +205,27 @@ __global__ void __launch_bounds__(kEnsTmaThreads, NF == 1 ? 2 : 1) k_ensemble_pa
                 if (!mbar_wait_bounded(&s_full[st], (full_phase >> st) & 1u, s_timeout ? 1000000ull : 2000000000ull))
                     s_timeout = 1;
                 full_phase ^= 1u << st;
-                tma_consume_plane<T, NF, KAHAN, VW>(G, stage + st * A.stage_stride, ring + rnew * A.ring_slot,
-                                                    ring + rmid * A.ring_slot, tid, CT, do_drift, j >= 1 && j <= NZ,
-                                                    j >= 2, (size_t)zz * plane + row_off,
-                                                    (size_t)(z0 + j - 2) * plane + row_off, Out, C, P, Z, accK,
-                                                    accG, accV, &s_empty[st]);
-                rmid = rnew;
-                rnew = rnew + 1 == RING ? 0 : rnew + 1;
+                if constexpr (NR) {
+                    tma_consume_plane_nr<T, NF, KAHAN, VW>(G, stage + st * A.stage_stride,
+                                                           stage + st_prev * A.stage_stride, do_drift,
+                                                           j >= 1 && j <= NZ, j >= 2, (size_t)zz * plane + row_off,
+                                                           (size_t)(z0 + j - 2) * plane + row_off, Out, C, P, Z, accK,
+                                                           accG, accV);
+                    if (j >= 1) release(st_prev);  // plane j-1: kicked (or the lower z halo, never kicked)
+                } else {
+                    tma_consume_plane<T, NF, KAHAN, VW>(G, stage + st * A.stage_stride, ring + rnew * A.ring_slot,
+                                                        ring + rmid * A.ring_slot, tid, CT, do_drift,
+                                                        j >= 1 && j <= NZ, j >= 2, (size_t)zz * plane + row_off,
+                                                        (size_t)(z0 + j - 2) * plane + row_off, Out, C, P, Z, accK,
+                                                        accG, accV, &s_empty[st]);
+                    rmid = rnew;
+                    rnew = rnew + 1 == RING ? 0 : rnew + 1;
+                }
+                st_prev = st;
                 st = st + 1 == S ? 0 : st + 1;
                 zz = zz + 1 == N ? 0 : zz + 1;
             }
+            if constexpr (NR) release(st_prev);  // the upper z halo of the item is never kicked
             // item partials; the member's last item reduces them in a fixed order
             double v[kMaxQ];
             v[0] = accK[0].value();
@@ -263,60 +282,77 @@ static cudaError_t ens_launch(K kernel, int threads, const void* args, int grid,
     return cudaGetLastError();
 }
 
-// stages: 0 = direct loader, 2..4 = TMA stage buffers
+// stages: 0 = direct loader, 2..4 = TMA stage buffers with the ring, 3..6 ringless (variant 1)
 template <typename T, int NF, bool KAHAN, int VW>
-static cudaError_t ens_one(const void* args, int stages, int grid, size_t smem, cudaStream_t s, int* occ)
+static cudaError_t ens_one(const void* args, int stages, int variant, int grid, size_t smem, cudaStream_t s, int* occ)
 {
-    static bool attr[5] = {false, false, false, false, false};
+    static bool attr[2][7] = {};
     if (stages <= 0) return ens_launch<decltype(&k_ensemble_pass<T, NF, KAHAN, VW>), T>(
-        k_ensemble_pass<T, NF, KAHAN, VW>, kEnsThreads, args, grid, smem, s, occ, attr[0]);
+        k_ensemble_pass<T, NF, KAHAN, VW>, kEnsThreads, args, grid, smem, s, occ, attr[0][0]);
     if constexpr (VW * sizeof(T) == 16) {  // 16-byte vectors: every member row is a 16-byte multiple
-        if (stages == 2) return ens_launch<decltype(&k_ensemble_pass_tma<T, NF, KAHAN, VW, 2>), T>(
-            k_ensemble_pass_tma<T, NF, KAHAN, VW, 2>, kEnsTmaThreads, args, grid, smem, s, occ, attr[2]);
-        if (stages == 3) return ens_launch<decltype(&k_ensemble_pass_tma<T, NF, KAHAN, VW, 3>), T>(
-            k_ensemble_pass_tma<T, NF, KAHAN, VW, 3>, kEnsTmaThreads, args, grid, smem, s, occ, attr[3]);
-        if (stages == 4) return ens_launch<decltype(&k_ensemble_pass_tma<T, NF, KAHAN, VW, 4>), T>(
-            k_ensemble_pass_tma<T, NF, KAHAN, VW, 4>, kEnsTmaThreads, args, grid, smem, s, occ, attr[4]);
+#define CL_ENS_CASE(SS, NRV)                                                                                  \
+        if (stages == SS && variant == (NRV ? 1 : 0))                                                        \
+            return ens_launch<decltype(&k_ensemble_pass_tma<T, NF, KAHAN, VW, SS, NRV>), T>(                 \
+                k_ensemble_pass_tma<T, NF, KAHAN, VW, SS, NRV>, kEnsTmaThreads, args, grid, smem, s, occ,    \
+                attr[NRV ? 1 : 0][SS]);
+        CL_ENS_CASE(2, false)
+        CL_ENS_CASE(3, false)
+        CL_ENS_CASE(4, false)
+        CL_ENS_CASE(3, true)
+        CL_ENS_CASE(4, true)
+        CL_ENS_CASE(5, true)
+        CL_ENS_CASE(6, true)
+#undef CL_ENS_CASE
     }
     return cudaErrorInvalidValue;
 }
 
 template <typename T, int NF, bool KAHAN>
-static cudaError_t ens_vw(const void* args, int vw, int stages, int grid, size_t smem, cudaStream_t s, int* occ)
+static cudaError_t ens_vw(const void* args, int vw, int stages, int variant, int grid, size_t smem, cudaStream_t s,
+                          int* occ)
 {
-    if (vw == 1) return ens_one<T, NF, KAHAN, 1>(args, stages, grid, smem, s, occ);
-    if (vw == 2) return ens_one<T, NF, KAHAN, 2>(args, stages, grid, smem, s, occ);
+    if (vw == 1) return ens_one<T, NF, KAHAN, 1>(args, stages, variant, grid, smem, s, occ);
+    if (vw == 2) return ens_one<T, NF, KAHAN, 2>(args, stages, variant, grid, smem, s, occ);
     if constexpr (sizeof(T) == 4) {
-        if (vw == 4) return ens_one<T, NF, KAHAN, 4>(args, stages, grid, smem, s, occ);
+        if (vw == 4) return ens_one<T, NF, KAHAN, 4>(args, stages, variant, grid, smem, s, occ);
     }
     return cudaErrorInvalidValue;
 }
 
-static cudaError_t ens_dispatch(int precision, int nf, const void* args, int vw, int stages, int grid, size_t smem,
-                                cudaStream_t s, int* occ)
+static cudaError_t ens_dispatch(int precision, int nf, const void* args, int vw, int stages, int variant, int grid,
+                                size_t smem, cudaStream_t s, int* occ)
 {
     if (precision == CL_PREC_FP64)
-        return nf == 1 ? ens_vw<double, 1, false>(args, vw, stages, grid, smem, s, occ)
-                       : ens_vw<double, 2, false>(args, vw, stages, grid, smem, s, occ);
+        return nf == 1 ? ens_vw<double, 1, false>(args, vw, stages, variant, grid, smem, s, occ)
+                       : ens_vw<double, 2, false>(args, vw, stages, variant, grid, smem, s, occ);
     if (precision == CL_PREC_FP32_KAHAN)
-        return nf == 1 ? ens_vw<float, 1, true>(args, vw, stages, grid, smem, s, occ)
-                       : ens_vw<float, 2, true>(args, vw, stages, grid, smem, s, occ);
-    return nf == 1 ? ens_vw<float, 1, false>(args, vw, stages, grid, smem, s, occ)
-                   : ens_vw<float, 2, false>(args, vw, stages, grid, smem, s, occ);
+        return nf == 1 ? ens_vw<float, 1, true>(args, vw, stages, variant, grid, smem, s, occ)
+                       : ens_vw<float, 2, true>(args, vw, stages, variant, grid, smem, s, occ);
+    return nf == 1 ? ens_vw<float, 1, false>(args, vw, stages, variant, grid, smem, s, occ)
+                   : ens_vw<float, 2, false>(args, vw, stages, variant, grid, smem, s, occ);
 }
 
 cudaError_t launch_ensemble_pass(int precision, int nf, const void* args, int vw, int grid, size_t smem,
                                  cudaStream_t s)
 {
     if (grid < 1) return cudaSuccess;
-    const int stages = precision == CL_PREC_FP64 ? static_cast<const EnsPassArgs<double>*>(args)->stages
-                                                 : static_cast<const EnsPassArgs<float>*>(args)->stages;
-    return ens_dispatch(precision, nf, args, vw, stages, grid, smem, s, nullptr);
+    int stages, variant;
+    if (precision == CL_PREC_FP64) {
+        const auto* A = static_cast<const EnsPassArgs<double>*>(args);
+        stages = A->stages;
+        variant = A->variant;
+    } else {
+        const auto* A = static_cast<const EnsPassArgs<float>*>(args);
+        stages = A->stages;
+        variant = A->variant;
+    }
+    return ens_dispatch(precision, nf, args, vw, stages, variant, grid, smem, s, nullptr);
 }
 
-cudaError_t ensemble_pass_blocks_per_sm(int precision, int nf, int vw, int stages, size_t smem, int* blocks)
+cudaError_t ensemble_pass_blocks_per_sm(int precision, int nf, int vw, int stages, int variant, size_t smem,
+                                        int* blocks)
 {
-    return ens_dispatch(precision, nf, nullptr, vw, stages, 0, smem, nullptr, blocks);
+    return ens_dispatch(precision, nf, nullptr, vw, stages, variant, 0, smem, nullptr, blocks);
 }
 
 }  // namespace clk

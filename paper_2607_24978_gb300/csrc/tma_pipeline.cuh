@@ -1,7 +1,8 @@
 // Steps of the TMA-staged, warp-specialized scalar pass as used by the ensemble kernel
 // (ensemble_pass.cu): the producer's bulk copies of one plane and the consumers' drift /
-// kick of one plane.  Same protocol and register z-march as the single-lattice kernel
-// (scalar_pass_tma.cuh, which keeps an inline copy of these steps).
+// kick of one plane, with a ring of drifted rows or ringless.  Same protocol and register
+// z-march as the single-lattice kernels (scalar_pass_tma.cuh and scalar_pass_tma_nr.cuh,
+// which keep inline copies of these steps).
 #pragma once
 
 #include "cl_internal.cuh"
@@ -143,6 +144,135 @@ __device__ __forceinline__ void tma_consume_plane(const TileGeom& G, const T* sb
                 vload_smem<T, VW>(yp, Sc + N + x0);
                 const T xm_edge = G.xm_lane ? xm_s : Sc[G.xm_idx];
                 const T xp_edge = G.xp_lane ? xp_s : Sc[G.xp_idx];
+                T gsum = (T)0;
+#pragma unroll
+                for (int i = 0; i < VW; ++i) {
+                    const T c = Z.zmid[f][i];
+                    const T xm = i == 0 ? xm_edge : Z.zmid[f][i - 1];
+                    const T xp = i == VW - 1 ? xp_edge : Z.zmid[f][i + 1];
+                    lap[f][i] = ((xp + xm) + (yp[i] + ym[i]) + (Z.znew[f][i] + Z.zlo[f][i])) - (T)6 * c;
+                    const T gx = xp - c, gy = yp[i] - c, gz = Z.znew[f][i] - c;
+                    gsum += gx * gx + gy * gy + gz * gz;
+                    phc[f][i] = c;
+                }
+                accG[f].add(gsum);
+            }
+        }
+        if (r < R) {
+            T vsum = (T)0;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                T po[VW], ksum = (T)0;
+#pragma unroll
+                for (int i = 0; i < VW; ++i) {
+                    const T p0 = phc[0][i];
+                    const T p1 = NF > 1 ? phc[NF - 1][i] : (T)0;
+                    T dV;
+                    if (f == 0) dV = p0 * (P.m20 + P.l0 * p0 * p0 + (NF > 1 ? P.g2 * p1 * p1 : (T)0));
+                    else dV = p1 * (P.m21 + P.l1 * p1 * p1 + P.g2 * p0 * p0);
+                    const T Fk = C.cL * lap[f][i] - C.cV * dV;
+                    const T pe = Z.pcur[f][i] + C.ce * Fk;
+                    po[i] = Z.pcur[f][i] + C.ck * Fk;
+                    ksum += pe * pe;
+                    if (f == 0) {
+                        T v = p0 * p0 * (P.h_m20 + P.q_l0 * p0 * p0);
+                        if (NF > 1) v += p1 * p1 * (P.h_m21 + P.q_l1 * p1 * p1) + P.h_g2 * p0 * p0 * p1 * p1;
+                        vsum += v;
+                    }
+                }
+                accK[f].add(ksum);
+                vstore<T, VW>(F.pi(f) + base_kick, po);
+            }
+            accV.add(vsum);
+        }
+    }
+    // march the register window up one plane
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int i = 0; i < VW; ++i) {
+            Z.zlo[f][i] = Z.zmid[f][i];
+            Z.zmid[f][i] = Z.znew[f][i];
+            Z.pcur[f][i] = Z.pnext[f][i];
+        }
+}
+
+// Ringless consumer step j of a tile (no ring, no named barrier): drift this thread's own
+// row of the plane in stage sb into registers and write its phi (and c) at base_new when
+// write_out; then (kick) kick the previous plane, whose stage sp is still held, drifting the
+// y-neighbour rows again from sp with the same compensated arithmetic as their owners (so
+// the values agree bit for bit) and taking x neighbours from adjacent lanes or, at row and
+// warp ends, one drifted value from sp.  The caller releases sp after this step.
+template <typename T, int NF, bool KAHAN, int VW, class Out>
+__device__ __forceinline__ void tma_consume_plane_nr(const TileGeom& G, const T* sb, const T* sp, bool do_drift,
+                                                     bool write_out, bool kick, size_t base_new, size_t base_kick,
+                                                     const Out& F, const TileCoef<T>& C, const PotCoef<T>& P,
+                                                     ZMarch<T, NF, VW>& Z, Acc<T> (&accK)[NF], Acc<T> (&accG)[NF],
+                                                     Acc<T>& accV)
+{
+    constexpr int KPF = KAHAN ? 3 : 2;
+    const int N = G.N, r = G.r, R = G.R, x0 = G.x0, arr_stride = G.arr_stride;
+    // drifted value of field f at (stage row srow, column x) of stage buffer b
+    auto drifted1 = [&](const T* b, int f, int srow, int x) -> T {
+        const T* sa = b + f * KPF * arr_stride + srow * N + x;
+        T ph = sa[0];
+        if (do_drift) {
+            T cv = KAHAN ? sa[2 * arr_stride] : (T)0;
+            drift<T, KAHAN>(ph, cv, sa[arr_stride], C.cd);
+        }
+        return ph;
+    };
+    if (r < R) {  // own row of plane j: drift, write out, keep field and momenta in registers
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            T pv[VW], cv[VW];
+            const T* sa = sb + f * KPF * arr_stride + (r + 1) * N + x0;
+            vload_smem<T, VW>(Z.znew[f], sa);
+            vload_smem<T, VW>(pv, sa + arr_stride);
+            if (KAHAN) vload_smem<T, VW>(cv, sa + 2 * arr_stride);
+            if (do_drift) {
+#pragma unroll
+                for (int i = 0; i < VW; ++i) drift<T, KAHAN>(Z.znew[f][i], cv[i], pv[i], C.cd);
+            }
+            if (write_out) {
+                vstore<T, VW>(F.phi(f) + base_new, Z.znew[f]);
+                if (KAHAN) vstore<T, VW>(F.c(f) + base_new, cv);
+            }
+#pragma unroll
+            for (int i = 0; i < VW; ++i) Z.pnext[f][i] = pv[i];
+        }
+    }
+    if (kick) {
+        T phc[NF][VW], lap[NF][VW];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            // every consumer lane takes part in the shuffles (idle lanes pass junk)
+            T xm_s = __shfl_up_sync(0xffffffffu, Z.zmid[f][VW - 1], 1);
+            T xp_s = __shfl_down_sync(0xffffffffu, Z.zmid[f][0], 1);
+            if (r < R) {
+                T ym[VW], yp[VW];
+                {
+                    T pvm[VW], cvm[VW], pvp[VW], cvp[VW];
+                    const T* am = sp + f * KPF * arr_stride + r * N + x0;
+                    const T* ap = sp + f * KPF * arr_stride + (r + 2) * N + x0;
+                    vload_smem<T, VW>(ym, am);
+                    vload_smem<T, VW>(yp, ap);
+                    if (do_drift) {
+                        vload_smem<T, VW>(pvm, am + arr_stride);
+                        vload_smem<T, VW>(pvp, ap + arr_stride);
+                        if (KAHAN) {
+                            vload_smem<T, VW>(cvm, am + 2 * arr_stride);
+                            vload_smem<T, VW>(cvp, ap + 2 * arr_stride);
+                        }
+#pragma unroll
+                        for (int i = 0; i < VW; ++i) {
+                            drift<T, KAHAN>(ym[i], cvm[i], pvm[i], C.cd);
+                            drift<T, KAHAN>(yp[i], cvp[i], pvp[i], C.cd);
+                        }
+                    }
+                }
+                const T xm_edge = G.xm_lane ? xm_s : drifted1(sp, f, r + 1, G.xm_idx);
+                const T xp_edge = G.xp_lane ? xp_s : drifted1(sp, f, r + 1, G.xp_idx);
                 T gsum = (T)0;
 #pragma unroll
                 for (int i = 0; i < VW; ++i) {

@@ -205,7 +205,7 @@ def test_ensemble_per_member_calls(cl):
         k, d, c = g.cl_spectrum(cl.CL_FIELD_PHI0, member=1)
         assert len(k) == int(math.floor(math.sqrt(3.0) * 6 + 0.5)) + 1
         with pytest.raises(cl.CLError):
-            g.cl_set_option(cl.CL_OPT_STAGES, 5)  # ensembles take 2..4 TMA stages
+            g.cl_set_option(cl.CL_OPT_STAGES, 7)  # at most 6 TMA stages
     with pytest.raises(cl.CLError):
         cl.Lattice(8, 1.0, 1, cl.CL_PREC_FP64, cl.CL_INT_RK3_3, member_N=[8, 8])
     with pytest.raises(cl.CLError):
@@ -225,6 +225,24 @@ def test_ensemble_tma_and_direct_loaders_agree(cl, prec):
             assert rel_l2(a[0][m], other[0][m]) < 1e-14
             assert rel_l2(a[1][m], other[1][m]) < 1e-14
             assert a[2][m]["rho"] == pytest.approx(other[2][m]["rho"], rel=1e-13)
+
+
+@pytest.mark.parametrize("prec,nf", [(1, 1), (1, 2), (0, 1), (2, 2)])
+def test_ensemble_ringless_and_ring_kernels_identical(cl, prec, nf):
+    """The ringless TMA ensemble kernel re-drifts the y-neighbour rows from the stage instead
+    of sharing them through a ring: on the same items the fields, energies and scale factors
+    agree bit for bit with the ring kernel, for every stage count."""
+    params = member_params([16, 24, 12, 32, 8], nf, seed=41)
+    ref = run_ensemble(cl, params, nf, prec, 1, 0.02, 6,
+                       opts=((cl.CL_OPT_PASS_VARIANT, 0), (cl.CL_OPT_STAGES, 3)))
+    for stages in (3, 4, 6):
+        got = run_ensemble(cl, params, nf, prec, 1, 0.02, 6,
+                           opts=((cl.CL_OPT_PASS_VARIANT, 1), (cl.CL_OPT_STAGES, stages)))
+        for m in range(len(params)):
+            assert np.array_equal(got[0][m], ref[0][m]), (stages, m)
+            assert np.array_equal(got[1][m], ref[1][m]), (stages, m)
+            assert got[2][m]["rho"] == ref[2][m]["rho"]
+            assert got[2][m]["a"] == ref[2][m]["a"]
 
 
 def test_autotune_keeps_the_state_and_caches_its_choice(cl, tmp_path):
