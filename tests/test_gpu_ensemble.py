@@ -260,7 +260,7 @@ def test_autotune_keeps_the_state_and_caches_its_choice(cl, tmp_path):
         before = [(g.cl_get_state(cl.CL_FIELD_PHI0, member=m), g.cl_get_state(cl.CL_FIELD_PI0, member=m),
                    g.cl_get_scalars(m)) for m in range(4)]
         stages, by, dz, us, variant = g.cl_autotune(cache)
-        assert us > 0 and stages in (-1, 2, 3, 4) and variant == 1
+        assert us > 0 and stages in (-1, 2, 3, 4, 5, 6) and variant in (0, 1)
         for m in range(4):
             assert np.array_equal(g.cl_get_state(cl.CL_FIELD_PHI0, member=m), before[m][0])
             assert np.array_equal(g.cl_get_state(cl.CL_FIELD_PI0, member=m), before[m][1])
