@@ -229,11 +229,14 @@ cl_status cl_set_hubble_limit(cl_lattice* l, double limit);
  * of the fused pass, 2..6, or -1 for the loader without TMA staging (0 = library choice;
  * rows that are not a multiple of 16 bytes always use the loader without TMA; ensembles
  * clamp to 2..4 with the ring kernel and 3..6 ringless).
- * CL_OPT_PASS_VARIANT: TMA-staged pass kernel, 1 = ringless (default: each warp drifts the
- * neighbour rows it needs from the stage buffers, no consumer barrier; 16-byte vectors,
- * 2..5 stages (ensembles 3..6), other rows fall back to 0), 0 = drifted rows shared through
- * a ring in shared memory with one consumer barrier per plane.  Both give bit-identical
- * fields on the same tiles.
+ * CL_OPT_PASS_VARIANT (-1 = library choice, the default): TMA-staged pass kernel, 1 =
+ * ringless (the library's choice: each warp drifts the neighbour rows it needs from the
+ * stage buffers, no consumer barrier; 16-byte vectors, 2..5 stages (ensembles 3..6), other
+ * rows fall back to 0), 0 = drifted rows shared through a ring in shared memory with one
+ * consumer barrier per plane.  Both give bit-identical fields on the same tiles.  For an
+ * axion-U(1) lattice: 0 = the plaquette fields through global memory and a second launch
+ * per Runge-Kutta stage (the library's choice), 1 = one fused launch per stage with the
+ * plaquette fields in shared memory (N a multiple of 32; same results to rounding).
  * Errors: CL_EINVAL. */
 enum { CL_OPT_GRAPH = 0, CL_OPT_TILE_BY = 1, CL_OPT_TILE_DZ = 2, CL_OPT_STAGES = 3, CL_OPT_PASS_VARIANT = 4 };
 cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value);

@@ -69,8 +69,9 @@ struct cl_lattice {
     bool diag_valid = false;
     double hubble_limit = 0.0;
     bool use_graph = true;
-    int opt_BY = 0, opt_DZ = 0, opt_stages = 0, opt_variant = 1;
+    int opt_BY = 0, opt_DZ = 0, opt_stages = 0, opt_variant = -1;  // -1: library choice
     int u1_dz = 8;                  // planes per block of the U(1) kernels
+    bool u1_fused = false;          // U(1) stage as one fused launch (plaquettes in shared memory)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t last_launches = 0;
     // batched ensemble (members > 1): per-member sizes, boxes, arena offsets and couplings
@@ -208,7 +209,7 @@ cl_status ens_tiles(cl_lattice* l)
     // per SM
     int stages = 0, var = 0;
     if (l->opt_stages >= 0 && l->VW * l->es == 16) {
-        var = l->opt_variant == 1 ? 1 : 0;
+        var = l->opt_variant != 0 ? 1 : 0;
         const int smin = var ? 3 : 2, smax = var ? 6 : 4;
         auto bytes = [&](int S) { return (size_t)(S * stage_max + (var ? 0 : 3 * ring_max)) * l->es; };
         if (l->opt_stages >= 2) {
@@ -281,7 +282,7 @@ cl_status choose_tiles(cl_lattice* l)
     bool tma = l->opt_stages >= 0 && scalar_pass_tma_ok(prec, N) && scalar_pass_threads(prec, N, 1) <= 480 &&
                !(prec == CL_PREC_FP64 && l->opt_stages == 0);
     // ringless variant (16-byte vectors): at most 448 consumers (blocks of <= 480 threads)
-    const bool want_nr = tma && l->opt_variant == 1 && l->VW * l->es == 16;
+    const bool want_nr = tma && l->opt_variant != 0 && l->VW * l->es == 16;
     const int max_consumers = want_nr ? 448 : (tma ? 480 : 512);
     // Default tile: as many rows as the consumer threads allow (more warps per SM), with
     // three TMA stages; measured best on GB300 for 256^3 and 512^3 lattices.
@@ -366,7 +367,15 @@ cl_status choose_tiles(cl_lattice* l)
         // amortise each block's reduction; measured at 192^3 FP32: 0.29 of HBM with 48-plane
         // chunks in one wave of 4 blocks per SM, 0.21 with 8-plane chunks)
         const int tiles = ((N + 31) / 32) * ((N + 7) / 8);
-        int64_t nbz = (int64_t)(prec == CL_PREC_FP64 ? kU1BlocksPerSM64 : kU1BlocksPerSM32) * nsm / tiles;
+        // the fused stage only on request: measured slower than the two launches at 192^3
+        // (3.96 against 5.12 Gsite-updates/s; both latency-bound)
+        l->u1_fused = l->opt_variant == 1 && u1_fused_ok(N);
+        int bps = prec == CL_PREC_FP64 ? kU1BlocksPerSM64 : kU1BlocksPerSM32;
+        if (l->u1_fused) {
+            CUDA_TRY(l, u1_fused_blocks_per_sm(prec, &bps));
+            if (bps < 1) bps = 1;
+        }
+        int64_t nbz = (int64_t)bps * nsm / tiles;
         if (nbz < 1) nbz = 1;
         if (nbz > N) nbz = N;
         l->u1_dz = l->opt_DZ > 0 ? (l->opt_DZ > N ? N : l->opt_DZ) : (int)((N + nbz - 1) / nbz);
@@ -674,8 +683,13 @@ cl_status run_u1_t(cl_lattice* l, int what, double cA, double cB, int flags, int
     A.A = cA;
     A.B = cB;
     A.flags = flags | (l->p.expansion ? P_EXPANSION : 0);
-    cudaError_t e = launch_u1(l->p.precision, &A, 0, l->stream);  // plaquette fields first
-    if (e == cudaSuccess) e = launch_u1(l->p.precision, &A, what, l->stream);
+    cudaError_t e;
+    if (what == 1 && l->u1_fused) {
+        e = launch_u1_fused(l->p.precision, &A, l->stream);  // plaquettes and stage in one launch
+    } else {
+        e = launch_u1(l->p.precision, &A, 0, l->stream);  // plaquette fields first
+        if (e == cudaSuccess) e = launch_u1(l->p.precision, &A, what, l->stream);
+    }
     if (e != cudaSuccess) return fail(l, CL_ECUDA, "U(1) launch failed: %s", cudaGetErrorString(e));
     return CL_OK;
 }
@@ -1103,7 +1117,7 @@ cl_status cl_get_option(cl_lattice* l, int32_t option, int64_t* value)
     case CL_OPT_TILE_BY: *value = ens ? l->hmem[0].BY : l->BY; return CL_OK;
     case CL_OPT_TILE_DZ: *value = ens ? l->hmem[0].DZ : (l->gauge ? l->u1_dz : l->DZ); return CL_OK;
     case CL_OPT_STAGES: *value = ens ? l->ens_stages : l->stages; return CL_OK;
-    case CL_OPT_PASS_VARIANT: *value = ens ? l->ens_variant : l->variant; return CL_OK;
+    case CL_OPT_PASS_VARIANT: *value = ens ? l->ens_variant : (l->gauge ? (l->u1_fused ? 1 : 0) : l->variant); return CL_OK;
     }
     return fail(l, CL_EINVAL, "unknown option %d", option);
 }
@@ -1122,7 +1136,7 @@ cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value)
         l->opt_DZ = (int)value;
         return choose_tiles(l);
     case CL_OPT_PASS_VARIANT:
-        if (value < 0 || value > 1) return fail(l, CL_EINVAL, "pass variant must be 0 or 1");
+        if (value < -1 || value > 1) return fail(l, CL_EINVAL, "pass variant must be -1, 0 or 1");
         l->opt_variant = (int)value;
         return choose_tiles(l);
     case CL_OPT_STAGES:
@@ -1311,7 +1325,7 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
                 l->cur ^= 1;
             }
         }
-        l->last_launches += l->gauge ? 2 * pps : pps;  // gauge stages: helper + stage kernel
+        l->last_launches += l->gauge && !l->u1_fused ? 2 * pps : pps;  // two-launch gauge stages: helper + stage
     }
     // a leapfrog step ends with the energies of its integer time; a Runge-Kutta stage
     // reports those of the state it started from, so they are recomputed on demand

@@ -134,6 +134,11 @@ struct U1Args {
 // partials[u1_grid_blocks(N, dz) * kMaxQ + block].
 cudaError_t launch_u1(int precision, const void* args, int what, cudaStream_t s);
 int u1_grid_blocks(int N, int dz);
+// Fused stage (u1_fused.cu): plaquettes and stage in one launch, grid u1_grid_blocks(N, dz),
+// its partials (all five sums) at partials[block * kMaxQ]; needs u1_fused_ok(N).
+bool u1_fused_ok(int N);
+cudaError_t launch_u1_fused(int precision, const void* args, cudaStream_t s);
+cudaError_t u1_fused_blocks_per_sm(int precision, int* blocks);
 
 // Batched ensemble of independent lattices (ensemble_pass.cu).  Every array class (phi,
 // pi, compensation, per field and buffer) is one arena holding the members back to back,

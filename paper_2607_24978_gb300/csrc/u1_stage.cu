@@ -40,6 +40,7 @@
 
 #include "cl_internal.cuh"
 #include "kernel_common.cuh"
+#include "u1_common.cuh"
 
 namespace clk {
 
@@ -261,57 +262,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_u1_stage(const 
         w[kMaxQ - 1] += __ldcg(&A.partials[(size_t)gridDim.x * kMaxQ + b]);  // plaquette launch, same grid
     }
     block_reduce<kMaxQ>(w, s_red, tid, nthr);
-    if (tid == 0) {
-        DevScal* S = A.scal;
-        const double vol = (double)V;
-        const double a = s_coef[5], b = expand ? S->b : 0.0;
-        const double a2 = a * a, a4 = a2 * a2, a6 = a4 * a2;
-        const double K = w[0] / (2.0 * a6 * vol);
-        const double G = w[1] / (A.dx * A.dx * 2.0 * a2 * vol);
-        const double Vp = w[2] / vol;
-        const double KE = A.ws2 * w[3] / (2.0 * pow(a, 2.0 + 2.0 * A.alpha) * vol);
-        const double GB = A.ws2 * w[4] / (pow(A.dx, 4.0) * a4 * vol);
-        const double rho = K + G + Vp + KE + GB;
-        const double p = K - G / 3.0 - Vp + (KE + GB) / 3.0;
-        const double a2al = pow(a, 2.0 * A.alpha);
-        double bb = b;
-        if ((A.flags & P_HUBBLE_INIT) && expand) bb = a * sqrt(a2al * A.kappa * rho / 3.0);
-        const double H = bb / a;
-        const double hv = H != 0.0 ? fabs(H * H - a2al * A.kappa * rho / 3.0) / (H * H) : 0.0;
-        S->diag[D_T] = S->t;
-        S->diag[D_A] = a;
-        S->diag[D_ADOT] = bb;
-        S->diag[D_K0] = K;
-        S->diag[D_K1] = 0.0;
-        S->diag[D_G0] = G;
-        S->diag[D_G1] = 0.0;
-        S->diag[D_V] = Vp;
-        S->diag[D_KE] = KE;
-        S->diag[D_GB] = GB;
-        S->diag[D_RHO] = rho;
-        S->diag[D_P] = p;
-        S->diag[D_HV] = hv;
-        if (A.flags & P_HUBBLE_INIT) S->b = bb;
-        if (update && expand) {
-            const double Fa = b;
-            const double Fb = pow(a, 2.0 * A.alpha + 1.0) * (A.kappa / 6.0) * ((2.0 * A.alpha - 1.0) * rho - 3.0 * p);
-            const double ka = first ? A.h * Fa : A.A * S->rk[0] + A.h * Fa;
-            const double kb = first ? A.h * Fb : A.A * S->rk[1] + A.h * Fb;
-            S->rk[0] = ka;
-            S->rk[1] = kb;
-            S->a = a + A.B * ka;
-            S->b = b + A.B * kb;
-        }
-        if (update && (A.flags & P_COUNT_STEP)) {
-            S->t += A.h;
-            S->step += 1;
-        }
-        int st = 0;
-        if (!isfinite(rho) || !isfinite(p)) st |= ST_NAN;
-        if (first && A.hubble_limit > 0.0 && hv > A.hubble_limit) st |= ST_CONSTRAINT;
-        if (st) atomicOr(&S->status, st);
-        S->counter = 0u;
-    }
+    if (tid == 0) u1_epilogue(A, w, s_coef[5], first, update, expand, V);
 }
 
 // Lattice Gauss charge G(n) = sum_i [P_i(n) - P_i(n - i)] / dx, P = a^(1-alpha) E + g W.

@@ -73,11 +73,11 @@ def gauss_scale(model, st, g):
 
 
 def run_pair(cl, N, prec, integ, scheme, nsteps, dt=0.01, alpha=0.0, expansion=True, alphaL=ALPHAL, graph=1,
-             seed=5, L=None):
+             seed=5, L=None, th_amp=0.3, variant=None):
     L = 0.75 * N if L is None else L
     m = O.make_model(N, L, nf=1, alpha=alpha, kappa=KAPPA, expansion=expansion, gauge=1, alphaL=alphaL, ws2=WS2,
                      m2=(M2, 0.0), lam=(LAM, 0.0))
-    st = random_state(m, seed)
+    st = random_state(m, seed, th_amp=th_amp)
     st.abt[:] = (1.0, 0.0, 0.0)
     if expansion:
         st.abt[1] = math.sqrt(KAPPA * O.energies(m, st)["rho"] / 3.0)  # a = 1
@@ -88,6 +88,8 @@ def run_pair(cl, N, prec, integ, scheme, nsteps, dt=0.01, alpha=0.0, expansion=T
         g.cl_set_potential(cl.CL_POT_POLY, [M2, LAM, 0.0, 0.0, 0.0])
         g.cl_set_gauge_coupling(alphaL, WS2)
         g.cl_set_option(cl.CL_OPT_GRAPH, graph)
+        if variant is not None:
+            g.cl_set_option(cl.CL_OPT_PASS_VARIANT, variant)
         g.cl_set_state(cl.CL_FIELD_PHI0, st.phi[0].astype(dtype))
         g.cl_set_state(cl.CL_FIELD_PI0, st.pi[0].astype(dtype))
         for i in range(3):
@@ -129,6 +131,43 @@ def test_u1_parity(cl, integ, scheme, stages, prec, tol, alpha):
         assert e[k_gpu] == pytest.approx(eo[k_orc], rel=max(tol, 1e-9), abs=1e-14), k_gpu
     assert e["step"] == 20
     assert launches == 20 * stages * 2  # helper fields + stage kernel
+
+
+@pytest.mark.parametrize("integ,scheme,stages", CASES)
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-4)])
+@pytest.mark.parametrize("alpha", [0.0, 1.0])
+def test_u1_fused_stage_parity(cl, integ, scheme, stages, prec, tol, alpha):
+    """The fused stage (CL_OPT_PASS_VARIANT 1: plaquettes in shared memory, one launch per
+    stage) at N = 32 and 64 against the oracle, including the energies and the magnetic
+    energy each block counts for the plaquettes whose lower corner it owns."""
+    for N, n in ((32, 6), (64, 2)):
+        out, e0, e, st0, st, m, launches = run_pair(cl, N, prec, integ, scheme, n, alpha=alpha, th_amp=0.5,
+                                                    variant=1)
+        assert rel_l2(out["phi"], st.phi[0]) < tol
+        assert rel_l2(out["pi"], st.pi[0]) < tol
+        assert rel_l2(out["th"], st.links) < tol
+        assert rel_l2(out["E"], st.efield) < tol
+        eo = O.energies(m, st)
+        e0o = O.energies(m, st0)
+        assert e["a"] == pytest.approx(st.abt[0], rel=tol)
+        assert e["adot"] == pytest.approx(st.abt[1], rel=tol)
+        for k_gpu, k_orc in [("KE", "KEM"), ("GB", "GEM"), ("rho", "rho"), ("p", "p")]:
+            assert e[k_gpu] == pytest.approx(eo[k_orc], rel=max(tol, 1e-9)), k_gpu
+            assert e0[k_gpu] == pytest.approx(e0o[k_orc], rel=max(tol, 1e-9)), k_gpu
+        assert launches == n * stages  # one fused launch per stage
+
+
+def test_u1_fused_and_two_launch_forms_agree(cl):
+    """The fused stage and the plaquette + stage launches on the same 32^3 state."""
+    res = []
+    for variant in (1, 0):
+        out, e0, e, st0, st, m, launches = run_pair(cl, 32, 0, cl.CL_INT_RK3_3, O.RK3_3, 4, alpha=0.5,
+                                                    variant=variant)
+        res.append((out, e, launches))
+    for k in ("phi", "pi", "th", "E"):
+        assert rel_l2(res[0][0][k], res[1][0][k]) < 1e-13, k
+    assert res[0][1]["rho"] == pytest.approx(res[1][1]["rho"], rel=1e-12)
+    assert res[0][2] == 4 * 3 and res[1][2] == 4 * 3 * 2
 
 
 @pytest.mark.parametrize("N", [5, 7, 12])
