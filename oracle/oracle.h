@@ -92,6 +92,8 @@ void orc_step(const orc_model* m, int scheme, double h, int nsteps,
 void orc_u1_rhs(const orc_model* m, const double* phi, const double* pi, const double* links,
                 const double* efield, const double* abt,
                 double* dphi, double* dpi, double* dlinks, double* defield);
+int orc_gauge_spectrum(const orc_model* m, const double* links, const double* efield, int which, double dn,
+                       int type, double* k_out, double* delta_out, double* count_out, int cap);
 void orc_u1_gauss(const orc_model* m, const double* phi, const double* links,
                   const double* efield, double a, double* out_gauss /* N^3 */);
 

@@ -53,6 +53,8 @@ def lib():
                                  dp, dp, dp]
         L.orc_spectrum.restype = C.c_int
         L.orc_spectrum.argtypes = [C.c_int, C.c_double, dp, C.c_double, C.c_int, dp, dp, dp, C.c_int]
+        L.orc_gauge_spectrum.restype = C.c_int
+        L.orc_gauge_spectrum.argtypes = [mp, dp, dp, C.c_int, C.c_double, C.c_int, dp, dp, dp, C.c_int]
         L.orc_conv3d_fwd.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, C.c_void_p, dp]
         L.orc_conv3d_bwd_data.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp]
         L.orc_conv3d_bwd_weight.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_void_p]
@@ -191,6 +193,18 @@ def spectrum(N, L, f, dn=1.0, type_=1):
     d = np.zeros(cap)
     c = np.zeros(cap)
     nb = lib().orc_spectrum(int(N), float(L), _c(f), float(dn), int(type_), k, d, c, cap)
+    return k[:nb], d[:nb], c[:nb]
+
+
+def gauge_spectrum(model, st, which, dn=1.0, type_=1):
+    """which: 0 electric, 1 magnetic, 2 / 3 the + / - chirality of the gauge potential."""
+    N = model.N
+    cap = int(np.floor(np.sqrt(3.0) * (N // 2) / dn + 0.5)) + 2
+    k = np.zeros(cap)
+    d = np.zeros(cap)
+    c = np.zeros(cap)
+    nb = lib().orc_gauge_spectrum(C.byref(model), _c(st.links), _c(st.efield), int(which), float(dn), int(type_),
+                                  k, d, c, cap)
     return k[:nb], d[:nb], c[:nb]
 
 

@@ -44,6 +44,9 @@ static int64_t shift(int N, int64_t n, int d, int s)
     return ((int64_t)c[2] * N + c[1]) * N + c[0];
 }
 
+/* signed Fourier index: 0..N/2 and -(N/2-1)..-1 */
+static int signed_mode_u1(int i, int N) { return (i <= N / 2) ? i : i - N; }
+
 /* theta_ij(n) = theta_i(n) + theta_j(n+i) - theta_i(n+j) - theta_j(n) */
 static double plaq(int N, const double* th, int64_t n, int i, int j)
 {
@@ -230,4 +233,105 @@ void orc_u1_rk_step(const orc_model* m, int scheme, double h, double* phi, doubl
     abt[2] += h;
     free(k);
     free(F);
+}
+
+/* --------------------------------------------------------------- gauge spectra */
+
+/* Binned spectra of the U(1) sector (section "ALP-gauge interactions": the spectra of the
+ * two chiralities of the gauge field; reading, since the paper gives no definition):
+ *   which 0: electric field, sum over i of |E_i(k)|^2;
+ *   which 1: magnetic field B_k(n) = sin theta_{k1 k2}(n) / dx^2 (plaquette of normal k,
+ *            k1 = k+1, k2 = k+2 mod 3), sum over k of |B_k(k)|^2;
+ *   which 2, 3: the + and - chiralities of the gauge potential A_i = theta_i / dx.  A link
+ *            field lives at n + e_i/2, so its Fourier amplitude carries the phase
+ *            exp(-i k_i dx / 2): A^_i = exp(-i k_i dx/2) DFT(A_i).  The forward-difference
+ *            curl is then i kt x A^ with the real lattice momentum kt_l = (2/dx) sin(k_l dx/2).
+ *            With kh = kt/|kt| and u, v = kh x u orthonormal and transverse to kt, the
+ *            vectors e_s = (u + s i v)/sqrt(2) satisfy i kh x e_s = s e_s (s = +1, -1), and
+ *            A_s = conj(e_s) . A^ is the amplitude of chirality s (|A_s|^2 does not depend
+ *            on the choice of u).  The zero mode has none.
+ * Every mode of the full spectrum is visited; binning and normalisation as orc_spectrum. */
+int orc_gauge_spectrum(const orc_model* m, const double* links, const double* efield, int which, double dn,
+                       int type, double* k_out, double* delta_out, double* count_out, int cap)
+{
+    const int N = m->N;
+    const int64_t V = (int64_t)N * N * N;
+    const double dx = m->L / N;
+    const double pi_ = 3.14159265358979323846264338327950;
+    double* re[3];
+    double* im[3];
+    for (int c = 0; c < 3; ++c) {
+        re[c] = malloc(sizeof(double) * (size_t)V);
+        im[c] = calloc((size_t)V, sizeof(double));
+        for (int64_t n = 0; n < V; ++n) {
+            if (which == 0) re[c][n] = efield[c * V + n];
+            else if (which == 1) re[c][n] = sin(plaq(N, links, n, (c + 1) % 3, (c + 2) % 3)) / (dx * dx);
+            else re[c][n] = links[c * V + n] / dx;
+        }
+        orc_dft3(N, -1, re[c], im[c]);
+    }
+    const double nmax = sqrt(3.0) * (N / 2);
+    int nb = (int)floor(nmax / dn + 0.5) + 1;
+    if (nb > cap) nb = cap;
+    double* S = calloc((size_t)nb, sizeof(double));
+    double* C = calloc((size_t)nb, sizeof(double));
+    const double s_hel = which == 2 ? 1.0 : -1.0;
+    for (int k = 0; k < N; ++k)
+        for (int j = 0; j < N; ++j)
+            for (int i = 0; i < N; ++i) {
+                const int s[3] = {signed_mode_u1(i, N), signed_mode_u1(j, N), signed_mode_u1(k, N)};
+                const double nm = sqrt((double)s[0] * s[0] + (double)s[1] * s[1] + (double)s[2] * s[2]);
+                const int l = (int)floor(nm / dn + 0.5);
+                if (l >= nb) continue;
+                const int64_t n = ((int64_t)k * N + j) * N + i;
+                double p = 0.0;
+                if (which < 2) {
+                    for (int c = 0; c < 3; ++c) p += re[c][n] * re[c][n] + im[c][n] * im[c][n];
+                } else {
+                    double kt[3], ar[3], ai[3], nk = 0.0;
+                    for (int c = 0; c < 3; ++c) {
+                        const double half = pi_ * s[c] / N;  /* k_c dx / 2 */
+                        kt[c] = 2.0 / dx * sin(half);
+                        nk += kt[c] * kt[c];
+                        /* A^_c = exp(-i half) (re + i im) */
+                        ar[c] = cos(half) * re[c][n] + sin(half) * im[c][n];
+                        ai[c] = cos(half) * im[c][n] - sin(half) * re[c][n];
+                    }
+                    nk = sqrt(nk);
+                    if (nk > 0.0) {
+                        double kh[3] = {kt[0] / nk, kt[1] / nk, kt[2] / nk};
+                        int a = 0;  /* axis least aligned with kh */
+                        for (int c = 1; c < 3; ++c)
+                            if (fabs(kh[c]) < fabs(kh[a])) a = c;
+                        double u[3] = {-kh[a] * kh[0], -kh[a] * kh[1], -kh[a] * kh[2]};
+                        u[a] += 1.0;
+                        const double nu = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                        for (int c = 0; c < 3; ++c) u[c] /= nu;
+                        const double v[3] = {kh[1] * u[2] - kh[2] * u[1], kh[2] * u[0] - kh[0] * u[2],
+                                             kh[0] * u[1] - kh[1] * u[0]};
+                        /* A_s = sum_c conj(e_s,c) A^_c, conj(e_s,c) = (u_c - s i v_c) / sqrt(2) */
+                        double xr = 0.0, xi = 0.0;
+                        for (int c = 0; c < 3; ++c) {
+                            xr += u[c] * ar[c] + s_hel * v[c] * ai[c];
+                            xi += u[c] * ai[c] - s_hel * v[c] * ar[c];
+                        }
+                        p = 0.5 * (xr * xr + xi * xi);
+                    }
+                }
+                S[l] += p;
+                C[l] += 1.0;
+            }
+    const double kIR = 2.0 * pi_ / m->L;
+    const double N6 = (double)V * (double)V;
+    for (int l = 0; l < nb; ++l) {
+        const double nl = l * dn;
+        k_out[l] = kIR * nl;
+        count_out[l] = C[l];
+        if (l == 0 || C[l] == 0.0) { delta_out[l] = 0.0; continue; }
+        if (type == 1) delta_out[l] = nl * S[l] / (N6 * dn);
+        else delta_out[l] = 4.0 * pi_ * nl * nl * nl * (S[l] / C[l]) / N6;
+    }
+    for (int c = 0; c < 3; ++c) { free(re[c]); free(im[c]); }
+    free(S); free(C);
+    return nb;
 }

@@ -175,3 +175,109 @@ def test_hubble_constraint_with_gauge_fields_converges(scheme, order):
         viol.append(O.energies(model, st)["hubble_violation"])
     assert viol[0] < 1e-3
     assert np.log2(viol[0] / viol[1]) == pytest.approx(order, abs=0.3)
+
+
+# ---------------------------------------------------------------- gauge spectra
+def _bins_from_power(N, power, dn=1.0):
+    """Type-I binning of a per-mode power array (numpy FFT index order), as the oracle bins."""
+    s = np.fft.fftfreq(N, 1.0 / N)
+    s = np.where(s == -N // 2, N // 2, s)  # Nyquist counted positive, as the oracle does
+    sz, sy, sx = np.meshgrid(s, s, s, indexing="ij")
+    nm = np.sqrt(sx ** 2 + sy ** 2 + sz ** 2)
+    lbin = np.floor(nm / dn + 0.5).astype(int)
+    nb = int(np.floor(np.sqrt(3.0) * (N // 2) / dn + 0.5)) + 1
+    S = np.bincount(lbin.ravel(), weights=power.ravel(), minlength=nb)[:nb]
+    l = np.arange(nb)
+    d = np.zeros(nb)
+    d[1:] = l[1:] * dn * S[1:] / (float(N) ** 6 * dn)
+    return d, (sx, sy, sz)
+
+
+def _gauge_model(N, L=6.0):
+    return O.make_model(N, L, nf=1, gauge=1, alphaL=2.0, ws2=0.6)
+
+
+def test_gauge_spectra_parseval_electric():
+    """Sum over all modes of the electric spectrum = N^3 sum_n E^2 (unnormalised DFT)."""
+    N = 8
+    m = _gauge_model(N)
+    st = O.new_state(m)
+    st.links, st.efield = inputs.gauge_state(N, seed=4, theta_amp=0.3, e_amp=0.3)
+    k, d, c = O.gauge_spectrum(m, st, 0)
+    l = np.arange(len(d))
+    S = np.zeros(len(d))
+    S[1:] = d[1:] * float(N) ** 6 / l[1:]
+    zero = sum(float(np.sum(st.efield[i])) ** 2 for i in range(3))
+    assert S.sum() + zero == pytest.approx(N ** 3 * float(np.sum(st.efield ** 2)), rel=1e-12)
+    assert c.sum() == N ** 3
+
+
+def test_gauge_chiralities_sum_to_the_transverse_power():
+    """A+ and A- together carry the transverse part of A (numpy FFT with the half-link phase
+    and the lattice momentum), bin by bin."""
+    N, L = 8, 6.0
+    dx = L / N
+    m = _gauge_model(N, L)
+    st = O.new_state(m)
+    st.links, st.efield = inputs.gauge_state(N, seed=5, theta_amp=0.4, e_amp=0.1)
+    _, dp, _ = O.gauge_spectrum(m, st, 2)
+    _, dm, _ = O.gauge_spectrum(m, st, 3)
+    Ah = [np.fft.fftn(st.links[i] / dx) for i in range(3)]  # axes (z, y, x)
+    _, (sx, sy, sz) = _bins_from_power(N, np.zeros((N, N, N)))
+    kt = [2.0 / dx * np.sin(np.pi * s / N) for s in (sx, sy, sz)]
+    Ah = [np.exp(-1j * np.pi * s / N) * a for s, a in zip((sx, sy, sz), Ah)]
+    k2 = kt[0] ** 2 + kt[1] ** 2 + kt[2] ** 2
+    kdotA = kt[0] * Ah[0] + kt[1] * Ah[1] + kt[2] * Ah[2]
+    tot = sum(np.abs(a) ** 2 for a in Ah)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        trans = np.where(k2 > 0, tot - np.abs(kdotA) ** 2 / k2, 0.0)
+    dt, _ = _bins_from_power(N, trans)
+    np.testing.assert_allclose(dp + dm, dt, rtol=1e-11, atol=1e-14 * dt.max())
+    assert 0.2 < dp[1:].sum() / dm[1:].sum() < 5.0  # a random field populates both
+
+
+def test_gauge_chiralities_vanish_for_a_gradient():
+    """A = grad+ chi (theta_i = chi(n + e_i) - chi(n)) is longitudinal: no chirality."""
+    N = 8
+    m = _gauge_model(N)
+    st = O.new_state(m)
+    chi = inputs.rng(6).standard_normal((N, N, N))
+    st.links = np.stack([np.roll(chi, -1, axis=2 - i) - chi for i in range(3)])
+    st.efield = np.zeros_like(st.links)
+    for w in (2, 3):
+        _, d, _ = O.gauge_spectrum(m, st, w)
+        assert np.abs(d).max() < 1e-26
+
+
+@pytest.mark.parametrize("sign", [1, -1])
+def test_helical_wave_lands_in_its_chirality(sign):
+    """A circularly polarised plane wave built from numpy's eigenvector of i kh x with
+    eigenvalue `sign` puts all of its power into that chirality's bin; its magnetic
+    spectrum is |kt|^2 times it at small amplitude (B = curl A)."""
+    N, L = 8, 6.0
+    dx = L / N
+    s = np.array([1, 2, 0])
+    kt = 2.0 / dx * np.sin(np.pi * s / N)
+    kh = kt / np.linalg.norm(kt)
+    cross = np.array([[0, -kh[2], kh[1]], [kh[2], 0, -kh[0]], [-kh[1], kh[0], 0]])
+    w, vec = np.linalg.eig(1j * cross)
+    e = vec[:, int(np.argmin(np.abs(w - sign)))]
+    z, y, x = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    amp = 1e-5
+    links = []
+    for c in range(3):
+        pos = [x + 0.5 * (c == 0), y + 0.5 * (c == 1), z + 0.5 * (c == 2)]
+        phase = 2 * np.pi / N * (s[0] * pos[0] + s[1] * pos[1] + s[2] * pos[2])
+        links.append(dx * np.real(amp * e[c] * np.exp(1j * phase)))
+    m = _gauge_model(N, L)
+    st = O.new_state(m)
+    st.links = np.stack(links)
+    st.efield = np.zeros_like(st.links)
+    _, dp, _ = O.gauge_spectrum(m, st, 2)
+    _, dm, _ = O.gauge_spectrum(m, st, 3)
+    _, dB, _ = O.gauge_spectrum(m, st, 1)
+    mine, other = (dp, dm) if sign > 0 else (dm, dp)
+    lb = int(np.floor(np.linalg.norm(s) + 0.5))
+    assert mine[lb] > 0 and other.max() < 1e-24 * mine[lb]
+    assert np.count_nonzero(mine > 1e-20 * mine[lb]) == 1
+    assert dB[lb] == pytest.approx(np.dot(kt, kt) * mine[lb], rel=1e-8)
