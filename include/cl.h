@@ -202,6 +202,21 @@ cl_status cl_energies(cl_lattice* l, cl_energy* out, int32_t count);
 cl_status cl_spectrum(cl_lattice* l, int32_t member, int32_t field, double dn, int32_t type,
                       double* k_out, double* delta_out, double* count_out, int32_t cap, int32_t* nbins);
 
+/* Spectra of the U(1) sector of an axion-U(1) lattice (section "ALP-gauge interactions":
+ * the two chiralities of the gauge field are output separately).  which:
+ *   CL_GSPEC_E: electric field, sum over i of |E_i(k)|^2;
+ *   CL_GSPEC_B: magnetic field B_k(n) = sin P_k(n) / dx^2 (plaquette of normal k at lower corner n);
+ *   CL_GSPEC_APLUS / CL_GSPEC_AMINUS: the + / - chirality of the gauge potential
+ *     A_i = theta_i / dx: with the half-link phase exp(-i k_i dx / 2) of A^_i and the lattice
+ *     momentum kt_l = (2/dx) sin(k_l dx / 2), the power of conj(e_s) . A^ where
+ *     i (kt/|kt|) x e_s = s e_s, s = +1 / -1 (the forward-difference curl is i kt x A^).
+ * Binning, normalisation, type and outputs as cl_spectrum (state at the current integer time).
+ * Uses cuFFT; synchronising.  Errors: CL_EINVAL (no gauge field, bad arguments), CL_ECUDA,
+ * CL_ENOMEM. */
+enum { CL_GSPEC_E = 0, CL_GSPEC_B = 1, CL_GSPEC_APLUS = 2, CL_GSPEC_AMINUS = 3 };
+cl_status cl_gauge_spectrum(cl_lattice* l, int32_t which, double dn, int32_t type, double* k_out, double* delta_out,
+                            double* count_out, int32_t cap, int32_t* nbins);
+
 /* Axion-U(1) couplings (gauge = CL_GAUGE_U1_AXION; section "ALP-gauge interactions",
  * Eq. AxionInfEOM): alphaL is the dimensionless coupling alpha_Lambda of the
  * alpha_Lambda/(4 m_p) phi F Ftilde term, ws2 = (omega_star/f_star)^2 the weight of the

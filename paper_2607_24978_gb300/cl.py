@@ -20,6 +20,7 @@ CL_OK, CL_EINVAL, CL_ENOMEM, CL_ECUDA, CL_ENAN, CL_ECONSTRAINT, CL_ETIMEOUT, CL_
 CL_PREC_FP64, CL_PREC_FP32_KAHAN, CL_PREC_FP32 = 0, 1, 2
 CL_INT_VV2, CL_INT_YOSHIDA4, CL_INT_RK3_3, CL_INT_RK4_5, CL_INT_YOSHIDA6, CL_INT_YOSHIDA8, CL_INT_YOSHIDA10 = range(7)
 CL_GAUGE_NONE, CL_GAUGE_U1_AXION = 0, 1
+CL_GSPEC_E, CL_GSPEC_B, CL_GSPEC_APLUS, CL_GSPEC_AMINUS = 0, 1, 2, 3
 CL_POT_LPHI4, CL_POT_M2, CL_POT_M2_G2, CL_POT_LPHI4_G2, CL_POT_POLY = 0, 1, 2, 3, 4
 CL_FIELD_PHI0, CL_FIELD_PHI1, CL_FIELD_PI0, CL_FIELD_PI1 = 0, 1, 2, 3
 CL_FIELD_THETA1, CL_FIELD_THETA2, CL_FIELD_THETA3, CL_FIELD_E1, CL_FIELD_E2, CL_FIELD_E3 = 4, 5, 6, 7, 8, 9
@@ -32,7 +33,7 @@ EXPORTS = ["cl_init_lattice", "cl_free", "cl_set_potential", "cl_set_state", "cl
            "cl_fused_pass_noalloc", "cl_surrogate_create", "cl_surrogate_free", "cl_surrogate_set_weights",
            "cl_surrogate_get_weights", "cl_surrogate_forward", "cl_surrogate_backward", "cl_surrogate_get_grads",
            "cl_surrogate_last_launch_count", "cl_surrogate_loss", "cl_surrogate_adamw", "cl_surrogate_channel_stats",
-           "cl_lattice_pack", "cl_lattice_unpack", "cl_surrogate_jump", "cl_surrogate_size", "cl_autotune"]
+           "cl_lattice_pack", "cl_lattice_unpack", "cl_surrogate_jump", "cl_surrogate_size", "cl_autotune", "cl_gauge_spectrum"]
 CL_ACT_RELU, CL_ACT_GELU = 1, 2
 CL_SG_BF16, CL_SG_FP32 = 0, 1
 
@@ -109,6 +110,8 @@ def lib():
         L.cl_step.argtypes = [C.c_void_p, C.c_int32]
         L.cl_sync.argtypes = [C.c_void_p]
         L.cl_energies.argtypes = [C.c_void_p, P(cl_energy), C.c_int32]
+        L.cl_gauge_spectrum.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_int32, P(C.c_double), P(C.c_double),
+                                        P(C.c_double), C.c_int32, P(C.c_int32)]
         L.cl_spectrum.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_int32, P(C.c_double),
                                   P(C.c_double), P(C.c_double), C.c_int32, P(C.c_int32)]
         L.cl_set_gauge_coupling.argtypes = [C.c_void_p, C.c_double, C.c_double]
@@ -287,6 +290,17 @@ class Lattice:
         _check(self.h, lib().cl_spectrum(self.h, int(member), int(field), float(dn), int(type_),
                                          k.ctypes.data_as(dp), d.ctypes.data_as(dp), c.ctypes.data_as(dp), n,
                                          C.byref(nb)))
+        return k, d, c
+
+    def cl_gauge_spectrum(self, which, dn=1.0, type_=1):
+        """Spectra of the U(1) sector: which = CL_GSPEC_E, _B, _APLUS or _AMINUS."""
+        nb = C.c_int32()
+        lib().cl_gauge_spectrum(self.h, int(which), float(dn), int(type_), None, None, None, 0, C.byref(nb))
+        n = nb.value
+        k, d, c = np.zeros(n), np.zeros(n), np.zeros(n)
+        dp = C.POINTER(C.c_double)
+        _check(self.h, lib().cl_gauge_spectrum(self.h, int(which), float(dn), int(type_), k.ctypes.data_as(dp),
+                                               d.ctypes.data_as(dp), c.ctypes.data_as(dp), n, C.byref(nb)))
         return k, d, c
 
     def cl_lattice_pack(self, mu, sg, x):

@@ -674,6 +674,21 @@ void u1_fill(cl_lattice* l, U1Args<T>& A, int in, int out)
     A.dz = l->u1_dz;
 }
 
+// Component fields of a gauge spectrum (current buffer) as doubles.
+template <typename T>
+cudaError_t gauge_fields_t(cl_lattice* l, int which, double* out)
+{
+    GaugeSpecArgs<T> A{};
+    for (int i = 0; i < 3; ++i) {
+        A.th[i] = (const T*)l->th[i][l->cur];
+        A.E[i] = (const T*)l->ef[i][l->cur];
+    }
+    A.N = l->N;
+    A.dx = l->dx;
+    A.which = which;
+    return launch_gauge_fields(l->p.precision, &A, out, l->stream);
+}
+
 // U(1) launches on buffer `in` (-> `out`): what = 1 stage (or energies), 2 Gauss diagnostic.
 template <typename T>
 cl_status run_u1_t(cl_lattice* l, int what, double cA, double cB, int flags, int in, int out)
@@ -1527,6 +1542,62 @@ cl_status cl_spectrum(cl_lattice* l, int32_t member, int32_t field, double dn, i
     return st;
 }
 
+cl_status cl_gauge_spectrum(cl_lattice* l, int32_t which, double dn, int32_t type, double* k_out, double* delta_out,
+                            double* count_out, int32_t cap, int32_t* nbins)
+{
+    if (!l) return CL_EINVAL;
+    if (!l->gauge) return fail(l, CL_EINVAL, "gauge spectra need an axion-U(1) lattice");
+    if (which < 0 || which > 3 || !(dn > 0) || (type != 1 && type != 2) || cap < 0 ||
+        (cap > 0 && (!k_out || !delta_out || !count_out)))
+        return fail(l, CL_EINVAL, "gauge spectrum: bad arguments");
+    const int N = l->N;
+    const int64_t V = (int64_t)N * N * N;
+    const int nb = (int)floor(sqrt(3.0) * (N / 2) / dn + 0.5) + 1;
+    if (nbins) *nbins = nb;
+    if (cap == 0) return CL_OK;
+    const size_t nh = (size_t)N * N * (N / 2 + 1);
+    double* real = nullptr;
+    double2* F = nullptr;
+    double* bins = nullptr;  // S[nb], C[nb], k[nb], delta[nb]
+    cufftHandle plan = 0;
+    cl_status st = CL_OK;
+    if (cudaMalloc(&real, 3 * (size_t)V * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&F, 3 * nh * sizeof(double2)) != cudaSuccess || cudaMalloc(&bins, 4 * (size_t)nb * sizeof(double)) != cudaSuccess)
+        st = fail(l, CL_ENOMEM, "gauge spectrum scratch allocation failed");
+    if (st == CL_OK && cufftPlan3d(&plan, N, N, N, CUFFT_D2Z) != CUFFT_SUCCESS) st = fail(l, CL_ECUDA, "cufftPlan3d failed");
+    if (st == CL_OK && cufftSetStream(plan, l->stream) != CUFFT_SUCCESS) st = fail(l, CL_ECUDA, "cufftSetStream failed");
+    if (st == CL_OK) {
+        const cudaError_t e = is_fp64(l) ? gauge_fields_t<double>(l, which, real) : gauge_fields_t<float>(l, which, real);
+        if (e != cudaSuccess) st = fail(l, CL_ECUDA, "gauge field conversion failed");
+    }
+    for (int c = 0; c < 3 && st == CL_OK; ++c)
+        if (cufftExecD2Z(plan, real + c * V, (cufftDoubleComplex*)(F + c * nh)) != CUFFT_SUCCESS)
+            st = fail(l, CL_ECUDA, "D2Z failed");
+    if (st == CL_OK && cudaMemsetAsync(bins, 0, 2 * (size_t)nb * sizeof(double), l->stream) != cudaSuccess)
+        st = fail(l, CL_ECUDA, "memset failed");
+    if (st == CL_OK && launch_gauge_bins(F, N, l->dx, which, dn, nb, bins, bins + nb, l->stream) != cudaSuccess)
+        st = fail(l, CL_ECUDA, "binning failed");
+    if (st == CL_OK &&
+        launch_spectrum_finish(bins, bins + nb, N, l->p.L, dn, type, nb, bins + 2 * nb, bins + 3 * nb, l->stream) != cudaSuccess)
+        st = fail(l, CL_ECUDA, "spectrum finish failed");
+    std::vector<double> h(4 * (size_t)nb);
+    if (st == CL_OK && cudaMemcpyAsync(h.data(), bins, 4 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, l->stream) != cudaSuccess)
+        st = fail(l, CL_ECUDA, "copy failed");
+    if (st == CL_OK && cudaStreamSynchronize(l->stream) != cudaSuccess) st = fail(l, CL_ECUDA, "sync failed");
+    if (st == CL_OK) {
+        const int n = cap < nb ? cap : nb;
+        for (int i = 0; i < n; ++i) {
+            count_out[i] = h[nb + i];
+            k_out[i] = h[2 * nb + i];
+            delta_out[i] = h[3 * nb + i];
+        }
+    }
+    if (plan) cufftDestroy(plan);
+    if (real) cudaFree(real);
+    if (F) cudaFree(F);
+    if (bins) cudaFree(bins);
+    return st;
+}
 
 // ---------------------------------------------------------------- surrogate coupling
 static cl_status check_sg_lattice(cl_lattice* l)

@@ -198,6 +198,21 @@ cudaError_t launch_vacuum_modes(const VacuumModeArgs& a, double2* fk, double2* p
 cudaError_t launch_real_to_field(int precision, const double* in, void* out, double base, double scale,
                                  int64_t n, cudaStream_t s);
 cudaError_t launch_field_to_double(int precision, const void* in, double* out, int64_t n, cudaStream_t s);
+
+// Spectra of the U(1) sector (gauge_spectrum.cu): the three component fields of `which`
+// (0 electric, 1 magnetic, 2 / 3 the gauge potential for the + / - chirality) as doubles
+// [3][N^3], and the shell binning of their D2Z transforms F[3][N][N][N/2+1].
+template <typename T>
+struct GaugeSpecArgs {
+    const T* th[3];
+    const T* E[3];
+    int N;
+    double dx;
+    int which;
+};
+cudaError_t launch_gauge_fields(int precision, const void* args, double* out, cudaStream_t s);
+cudaError_t launch_gauge_bins(const double2* F, int N, double dx, int which, double dn, int nbins, double* S,
+                              double* C, cudaStream_t s);
 // Shell binning of |F|^2 over a real-to-complex half spectrum: S[l], C[l] (zeroed by the caller).
 cudaError_t launch_spectrum_bins(const double2* F, int N, double dn, int nbins, double* S, double* C,
                                  cudaStream_t s);

@@ -282,3 +282,39 @@ def test_u1_invalid_configurations(cl):
     with cl.Lattice(8, 6.0, 1, cl.CL_PREC_FP64, cl.CL_INT_RK3_3, gauge=cl.CL_GAUGE_U1_AXION) as g:
         with pytest.raises(cl.CLError):
             g.cl_set_gauge_coupling(1.0, -1.0)
+
+
+@pytest.mark.parametrize("N,prec", [(8, 0), (12, 2), (32, 0), (16, 2)])
+def test_gauge_spectra_match_oracle(cl, N, prec):
+    """Electric, magnetic and the two chirality spectra (cl_gauge_spectrum) against the
+    oracle on the same state (FP32 states are handed to the oracle as stored), both
+    binnings and types, N = 8 .. 32 (Nyquist planes and the conjugate partners of the half
+    spectrum)."""
+    L = 0.75 * N
+    m = O.make_model(N, L, nf=1, alpha=0.0, kappa=KAPPA, gauge=1, alphaL=ALPHAL, ws2=WS2, m2=(M2, 0.0),
+                     lam=(LAM, 0.0))
+    st = random_state(m, 9, th_amp=0.4, e_amp=0.3)
+    dtype = np.float64 if prec == 0 else np.float32
+    st.links = st.links.astype(dtype).astype(np.float64)
+    st.efield = st.efield.astype(dtype).astype(np.float64)
+    with cl.Lattice(N, L, 1, prec, cl.CL_INT_RK3_3, gauge=cl.CL_GAUGE_U1_AXION, alpha=0.0, kappa=KAPPA,
+                    dt=0.01) as g:
+        g.cl_set_potential(cl.CL_POT_POLY, [M2, LAM, 0.0, 0.0, 0.0])
+        g.cl_set_gauge_coupling(ALPHAL, WS2)
+        g.cl_set_state(cl.CL_FIELD_PHI0, st.phi[0].astype(dtype))
+        g.cl_set_state(cl.CL_FIELD_PI0, st.pi[0].astype(dtype))
+        for i in range(3):
+            g.cl_set_state(cl.CL_FIELD_THETA1 + i, st.links[i].astype(dtype))
+            g.cl_set_state(cl.CL_FIELD_E1 + i, st.efield[i].astype(dtype))
+        g.cl_set_scalars(1.0)
+        for which in (cl.CL_GSPEC_E, cl.CL_GSPEC_B, cl.CL_GSPEC_APLUS, cl.CL_GSPEC_AMINUS):
+            for dn, type_ in ((1.0, 1), (0.5, 2)):
+                k, d, c = g.cl_gauge_spectrum(which, dn, type_)
+                ko, do, co = O.gauge_spectrum(m, st, which, dn, type_)
+                assert np.array_equal(c, co), (which, dn)
+                np.testing.assert_allclose(k, ko, rtol=1e-14)
+                np.testing.assert_allclose(d, do, rtol=1e-10, atol=1e-12 * do.max()), (which, dn)
+    with cl.Lattice(8, 6.0, 1, 0, cl.CL_INT_VV2) as g:
+        g.cl_set_potential(cl.CL_POT_LPHI4, [1.0])
+        with pytest.raises(cl.CLError):
+            g.cl_gauge_spectrum(cl.CL_GSPEC_E)  # no gauge field
