@@ -228,9 +228,29 @@ int orc_rk_coeffs(int scheme, const double** A, const double** B)
     return 0;
 }
 
+double orc_nmc_ricci(const orc_model* m, const double* phi, const double* pi, const double* abt)
+{
+    const int N = m->N;
+    const int64_t V = (int64_t)N * N * N;
+    double e[ORC_NE];
+    orc_energies(m, phi, pi, NULL, NULL, abt, e);
+    double phidv = 0.0, phi2 = 0.0;
+    for (int64_t n = 0; n < V; ++n) {
+        phidv += phi[n] * orc_dV(m, 0, phi[n], 0.0);
+        phi2 += phi[n] * phi[n];
+    }
+    phidv /= (double)V;
+    phi2 /= (double)V;
+    const double dphi2 = 2.0 * e[ORC_E_G0] - 2.0 * e[ORC_E_K0];  /* g^{mu nu} d_mu phi d_nu phi */
+    const double F = 1.0 / (1.0 + (6.0 * m->xi - 1.0) * m->xi * m->kappa * phi2);
+    return m->kappa * F * ((1.0 - 6.0 * m->xi) * dphi2 + 4.0 * e[ORC_E_V] - 6.0 * m->xi * phidv);
+}
+
 /* One 2N-storage RK step of the scalar system y = (phi, pi, a, a'), with
  *   F(y) = (a^(alpha-3) pi, a^(1+alpha) Lap phi - a^(3+alpha) V', a', a''(a, rho(y), p(y))).
- * Per stage s:  k <- A_s k + h F(y);  y <- y + B_s k   (one auxiliary copy per dof). */
+ * Per stage s:  k <- A_s k + h F(y);  y <- y + B_s k   (one auxiliary copy per dof).
+ * NMC models (Eq. eomNMC, Eq. piadot): the kick of field 0 gains -a^(3+alpha) xi R phi and
+ *   a'' = a [a^(2 alpha) R / 6 - (1 - alpha) (a'/a)^2], with R = orc_nmc_ricci(y). */
 static void rk_step(const orc_model* m, int scheme, double h, double* phi, double* pi, double* abt)
 {
     const int N = m->N;
@@ -246,12 +266,18 @@ static void rk_step(const orc_model* m, int scheme, double h, double* phi, doubl
         const double a = abt[0], b = abt[1];
         double e[ORC_NE];
         double Fa = 0.0, Fb = 0.0;
+        const double R = m->nmc ? orc_nmc_ricci(m, phi, pi, abt) : 0.0;
         if (m->expansion) {
             orc_energies(m, phi, pi, NULL, NULL, abt, e);
             Fa = b;
-            Fb = orc_addot(m, a, e[ORC_E_RHO], e[ORC_E_P]);
+            Fb = m->nmc ? a * (pow(a, 2.0 * m->alpha) * R / 6.0 - (1.0 - m->alpha) * (b / a) * (b / a))
+                        : orc_addot(m, a, e[ORC_E_RHO], e[ORC_E_P]);
         }
         for (int f = 0; f < m->nf; ++f) orc_kick_force(m, f, phi, a, Fpi + (int64_t)f * V);
+        if (m->nmc) {
+            const double c = pow(a, 3.0 + m->alpha) * m->xi * R;
+            for (int64_t n = 0; n < V; ++n) Fpi[n] -= c * phi[n];
+        }
         const double cd = pow(a, m->alpha - 3.0);
         for (int64_t n = 0; n < nd; ++n) {
             kphi[n] = A[s] * kphi[n] + h * cd * pi[n];

@@ -51,6 +51,10 @@ typedef struct {
      * (omega_star / f_star)^2 that multiplies E.B in the axion equation.             */
     double alphaL;
     double ws2;
+    /* non-minimal coupling xi phi^2 R of field 0 (section "Scalar fields non-minimally
+     * coupled to gravity"); Runge-Kutta schemes only, one field, no gauge sector        */
+    int32_t nmc;        /* 1: on                                                         */
+    double xi;
 } orc_model;
 
 /* Indices into the energies vector returned by orc_energies(). */
@@ -80,6 +84,10 @@ void   orc_energies(const orc_model* m, const double* phi, const double* pi,
                     const double* links, const double* efield,
                     const double* abt, double* out);
 double orc_addot(const orc_model* m, double a, double rho, double p);
+/* Background Ricci scalar of an NMC model at the state (phi, pi, abt): Eq. eomR in program
+ * units, R = kappa F [(1 - 6 xi) <d phi . d phi> + 4 <V> - 6 xi <phi V'>],
+ * F = 1 / (1 + (6 xi - 1) xi kappa <phi^2>), <d phi . d phi> = 2 G - 2 K. */
+double orc_nmc_ricci(const orc_model* m, const double* phi, const double* pi, const double* abt);
 
 /* ---- time integration ----
  * Scalar models: links = efield = NULL.

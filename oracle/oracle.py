@@ -20,7 +20,7 @@ class Model(C.Structure):
     _fields_ = [("N", C.c_int32), ("nf", C.c_int32), ("expansion", C.c_int32), ("gauge", C.c_int32),
                 ("L", C.c_double), ("alpha", C.c_double), ("kappa", C.c_double),
                 ("m2", C.c_double * 2), ("lam", C.c_double * 2), ("g2", C.c_double),
-                ("alphaL", C.c_double), ("ws2", C.c_double)]
+                ("alphaL", C.c_double), ("ws2", C.c_double), ("nmc", C.c_int32), ("xi", C.c_double)]
 
 
 _lib = None
@@ -53,6 +53,8 @@ def lib():
                                  dp, dp, dp]
         L.orc_spectrum.restype = C.c_int
         L.orc_spectrum.argtypes = [C.c_int, C.c_double, dp, C.c_double, C.c_int, dp, dp, dp, C.c_int]
+        L.orc_nmc_ricci.restype = C.c_double
+        L.orc_nmc_ricci.argtypes = [mp, dp, dp, dp]
         L.orc_gauge_spectrum.restype = C.c_int
         L.orc_gauge_spectrum.argtypes = [mp, dp, dp, C.c_int, C.c_double, C.c_int, dp, dp, dp, C.c_int]
         L.orc_conv3d_fwd.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, C.c_void_p, dp]
@@ -69,8 +71,10 @@ def lib():
 
 
 def make_model(N, L, nf=1, alpha=1.0, kappa=0.0, expansion=False, m2=(0.0, 0.0), lam=(0.0, 0.0),
-               g2=0.0, gauge=0, alphaL=0.0, ws2=0.0):
+               g2=0.0, gauge=0, alphaL=0.0, ws2=0.0, xi=None):
+    """xi: non-minimal coupling of field 0 (None: minimally coupled)."""
     m = Model()
+    m.nmc, m.xi = (0, 0.0) if xi is None else (1, float(xi))
     m.N, m.nf, m.expansion, m.gauge = int(N), int(nf), int(bool(expansion)), int(gauge)
     m.L, m.alpha, m.kappa = float(L), float(alpha), float(kappa)
     m.m2[0], m.m2[1] = float(m2[0]), float(m2[1])
@@ -126,6 +130,10 @@ def energies(model, st):
                        _ptr(None if st.links is None else _c(st.links)),
                        _ptr(None if st.efield is None else _c(st.efield)), _c(st.abt), out)
     return dict(zip(E_NAMES, out))
+
+
+def nmc_ricci(model, st):
+    return lib().orc_nmc_ricci(C.byref(model), _c(st.phi), _c(st.pi), _c(st.abt))
 
 
 def addot(model, a, rho, p):
