@@ -142,6 +142,8 @@ typedef struct {
     double hubble_violation;  /* |H^2 - a^(2 alpha) kappa rho/3| / H^2, H = a'/a (0 if H = 0) */
     double gauss_violation;   /* U(1): max_n |Gauss(n)| / mean_n |div E(n)|; 0 without gauge */
     int64_t step;             /* time steps taken since the state was set                */
+    double ricci;             /* background Ricci scalar R (Eq. eomR) of a non-minimally coupled
+                                 lattice (cl_set_nonminimal); 0 otherwise                  */
 } cl_energy;
 
 /* Create a lattice.  Allocates all device memory (fields, their ping-pong copies,
@@ -230,6 +232,17 @@ cl_status cl_gauge_spectrum(cl_lattice* l, int32_t which, double dn, int32_t typ
  * CL_INT_RK3_3 / CL_INT_RK4_5 (as the paper does for this module), one axion field,
  * CL_PREC_FP64 or CL_PREC_FP32.  Errors: CL_EINVAL (no gauge field, bad values). */
 cl_status cl_set_gauge_coupling(cl_lattice* l, double alphaL, double ws2);
+
+/* Non-minimal coupling xi phi^2 R of the scalar field (section "Scalar fields non-minimally
+ * coupled to gravity", Eq. eomNMC, Eq. eomR, Eq. piadot) for a single lattice with one field
+ * and a Runge-Kutta integrator (the paper integrates this system with them).  Each stage then
+ * first reduces the background Ricci scalar of its state,
+ *   R = kappa F [(1 - 6 xi) (2 G - 2 K) + 4 <V> - 6 xi <phi V'>],  F = 1/(1 + (6 xi - 1) xi kappa <phi^2>)
+ * (program units, K = <pi^2>/(2 a^6), G = <(grad+ phi)^2>/(2 a^2)); the kick gains
+ * -a^(3+alpha) xi R phi and a'' = a [a^(2 alpha) R/6 - (1 - alpha)(a'/a)^2].  The energies keep
+ * their minimally coupled form (hubble_violation is then not a constraint of the system; set
+ * a' explicitly).  Errors: CL_EINVAL, CL_EUNSUPPORTED. */
+cl_status cl_set_nonminimal(cl_lattice* l, double xi);
 
 /* When limit > 0, a Hubble violation above it sets the device status CL_ECONSTRAINT
  * (reported by the next synchronising call).  limit <= 0 disables the check (default). */

@@ -33,7 +33,7 @@ EXPORTS = ["cl_init_lattice", "cl_free", "cl_set_potential", "cl_set_state", "cl
            "cl_fused_pass_noalloc", "cl_surrogate_create", "cl_surrogate_free", "cl_surrogate_set_weights",
            "cl_surrogate_get_weights", "cl_surrogate_forward", "cl_surrogate_backward", "cl_surrogate_get_grads",
            "cl_surrogate_last_launch_count", "cl_surrogate_loss", "cl_surrogate_adamw", "cl_surrogate_channel_stats",
-           "cl_lattice_pack", "cl_lattice_unpack", "cl_surrogate_jump", "cl_surrogate_size", "cl_autotune", "cl_gauge_spectrum"]
+           "cl_lattice_pack", "cl_lattice_unpack", "cl_surrogate_jump", "cl_surrogate_size", "cl_autotune", "cl_gauge_spectrum", "cl_set_nonminimal"]
 CL_ACT_RELU, CL_ACT_GELU = 1, 2
 CL_SG_BF16, CL_SG_FP32 = 0, 1
 
@@ -55,13 +55,13 @@ class cl_energy(C.Structure):
     _fields_ = [("t", C.c_double), ("a", C.c_double), ("adot", C.c_double), ("K", C.c_double * 2),
                 ("G", C.c_double * 2), ("V", C.c_double), ("KE", C.c_double), ("GB", C.c_double),
                 ("rho", C.c_double), ("p", C.c_double), ("hubble_violation", C.c_double),
-                ("gauss_violation", C.c_double), ("step", C.c_int64)]
+                ("gauss_violation", C.c_double), ("step", C.c_int64), ("ricci", C.c_double)]
 
     def as_dict(self):
         return {"t": self.t, "a": self.a, "adot": self.adot, "K0": self.K[0], "K1": self.K[1], "G0": self.G[0],
                 "G1": self.G[1], "V": self.V, "KE": self.KE, "GB": self.GB, "rho": self.rho, "p": self.p,
                 "hubble_violation": self.hubble_violation, "gauss_violation": self.gauss_violation,
-                "step": self.step}
+                "step": self.step, "ricci": self.ricci}
 
 
 class cl_pass_noalloc_desc(C.Structure):
@@ -116,6 +116,7 @@ def lib():
                                   P(C.c_double), P(C.c_double), C.c_int32, P(C.c_int32)]
         L.cl_set_gauge_coupling.argtypes = [C.c_void_p, C.c_double, C.c_double]
         L.cl_set_hubble_limit.argtypes = [C.c_void_p, C.c_double]
+        L.cl_set_nonminimal.argtypes = [C.c_void_p, C.c_double]
         L.cl_set_option.argtypes = [C.c_void_p, C.c_int32, C.c_int64]
         L.cl_get_option.argtypes = [C.c_void_p, C.c_int32, P(C.c_int64)]
         L.cl_last_launch_count.argtypes = [C.c_void_p]
@@ -318,6 +319,9 @@ class Lattice:
 
     def cl_set_gauge_coupling(self, alphaL, ws2):
         _check(self.h, lib().cl_set_gauge_coupling(self.h, float(alphaL), float(ws2)))
+
+    def cl_set_nonminimal(self, xi):
+        _check(self.h, lib().cl_set_nonminimal(self.h, float(xi)))
 
     def cl_set_hubble_limit(self, limit):
         _check(self.h, lib().cl_set_hubble_limit(self.h, float(limit)))

@@ -72,6 +72,8 @@ struct cl_lattice {
     int opt_BY = 0, opt_DZ = 0, opt_stages = 0, opt_variant = -1;  // -1: library choice
     int u1_dz = 8;                  // planes per block of the U(1) kernels
     bool u1_fused = false;          // U(1) stage as one fused launch (plaquettes in shared memory)
+    bool nmc = false;               // non-minimal coupling xi phi^2 R of field 0 (Runge-Kutta)
+    double xi = 0.0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t last_launches = 0;
     // batched ensemble (members > 1): per-member sizes, boxes, arena offsets and couplings
@@ -470,12 +472,37 @@ cl_status run_rk_stage_t(cl_lattice* l, const PassCoef& pc, int in, int out)
     A.g2 = l->g2;
     A.hubble_limit = l->hubble_limit;
     A.flags = pc.flags | (l->p.expansion ? P_EXPANSION : 0);
+    A.nmc = l->nmc ? 1 : 0;
+    A.xi = l->xi;
+    if (l->nmc) {  // the Ricci scalar of the stage's state first
+        cudaError_t e = launch_nmc_ricci(l->p.precision, &A, l->rk_nby * l->rk_nbz, l->stream);
+        if (e != cudaSuccess) return fail(l, CL_ECUDA, "Ricci reduction launch failed: %s", cudaGetErrorString(e));
+    }
     cudaError_t e = launch_rk_stage(l->p.precision, l->nf, &A, l->VW, l->stream);
     if (e != cudaSuccess) return fail(l, CL_ECUDA, "Runge-Kutta stage launch failed: %s", cudaGetErrorString(e));
     return CL_OK;
 }
 
 cl_status run_u1(cl_lattice* l, int what, double cA, double cB, int flags, int in, int out);
+
+// Background Ricci scalar of the current state of a non-minimally coupled lattice into scal->rbar.
+template <typename T>
+cl_status nmc_ricci_t(cl_lattice* l)
+{
+    RkStageArgs<T> A{};
+    A.phi_in[0] = (const T*)l->phi[0][l->cur];
+    A.pi_in[0] = (const T*)l->pi[0][l->cur];
+    A.scal = l->scal;
+    A.partials = l->partials;
+    A.N = l->N;
+    A.dx = l->dx; A.alpha = l->p.alpha; A.kappa = l->p.kappa;
+    A.m2[0] = l->m2[0]; A.lam[0] = l->lam[0];
+    A.nmc = 1;
+    A.xi = l->xi;
+    cudaError_t e = launch_nmc_ricci(l->p.precision, &A, l->rk_nby * l->rk_nbz, l->stream);
+    if (e != cudaSuccess) return fail(l, CL_ECUDA, "Ricci reduction launch failed: %s", cudaGetErrorString(e));
+    return CL_OK;
+}
 
 // One ensemble pass over the members [m0, m1) reading buffer `in` and writing `out`.
 template <typename T>
@@ -726,6 +753,10 @@ cl_status energy_pass(cl_lattice* l, int extra_flags)
     cl_status s = l->gauge ? run_u1(l, 1, 0.0, 0.0, P_ENERGY_ONLY | (extra_flags & P_HUBBLE_INIT), l->cur, l->cur ^ 1)
                            : run_pass(l, {0.0, 0.0, 0.0, extra_flags}, l->cur, l->cur ^ 1);
     if (s != CL_OK) return s;
+    if (l->nmc) {  // the background Ricci scalar of the same state
+        s = is_fp64(l) ? nmc_ricci_t<double>(l) : nmc_ricci_t<float>(l);
+        if (s != CL_OK) return s;
+    }
     l->diag_valid = true;
     return CL_OK;
 }
@@ -1115,6 +1146,19 @@ cl_status cl_set_gauge_coupling(cl_lattice* l, double alphaL, double ws2)
     return CL_OK;
 }
 
+cl_status cl_set_nonminimal(cl_lattice* l, double xi)
+{
+    if (!l) return CL_EINVAL;
+    if (is_ens(l) || l->gauge || l->nf != 1 || !is_rk(l->p.integrator))
+        return fail(l, CL_EUNSUPPORTED, "the non-minimal coupling needs one scalar field and a Runge-Kutta integrator");
+    if (!isfinite(xi)) return fail(l, CL_EINVAL, "xi must be finite");
+    l->nmc = true;
+    l->xi = xi;
+    l->diag_valid = false;
+    invalidate_graphs(l);
+    return CL_OK;
+}
+
 cl_status cl_set_hubble_limit(cl_lattice* l, double limit)
 {
     if (!l) return CL_EINVAL;
@@ -1340,7 +1384,8 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
                 l->cur ^= 1;
             }
         }
-        l->last_launches += l->gauge && !l->u1_fused ? 2 * pps : pps;  // two-launch gauge stages: helper + stage
+        // two-launch gauge stages (helper + stage) and non-minimally coupled stages (Ricci + stage)
+        l->last_launches += (l->gauge && !l->u1_fused) || l->nmc ? 2 * pps : pps;
     }
     // a leapfrog step ends with the energies of its integer time; a Runge-Kutta stage
     // reports those of the state it started from, so they are recomputed on demand
@@ -1388,6 +1433,7 @@ cl_status cl_energies(cl_lattice* l, cl_energy* out, int32_t count)
         o->hubble_violation = h.diag[D_HV];
         o->gauss_violation = h.diag[D_GV];
         o->step = h.step;
+        o->ricci = l->nmc ? h.rbar : 0.0;
     }
     return s;
 }

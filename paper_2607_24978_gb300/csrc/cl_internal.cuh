@@ -27,6 +27,7 @@ struct DevScal {
     unsigned int counter;  // last-block-done arrival counter; the last block resets it to 0
     int status;            // ST_* bits, sticky until read by the host
     double rk[2];          // 2N Runge-Kutta auxiliaries of a and a' (k_a, k_a')
+    double rbar;           // background Ricci scalar of the state (non-minimally coupled lattices)
 };
 
 // Flags of one fused scalar pass.
@@ -100,8 +101,13 @@ struct RkStageArgs {
     double m2[2], lam[2], g2;
     double hubble_limit;
     int flags;          // P_EXPANSION, P_FIRST_STAGE, P_COUNT_STEP
+    int nmc;            // non-minimal coupling xi phi^2 R of field 0 (one field): the kick and a''
+    double xi;          //   use scal->rbar, written by launch_nmc_ricci for the same state
 };
 cudaError_t launch_rk_stage(int precision, int nf, const void* args, int vw, cudaStream_t s);
+// Background Ricci scalar (Eq. eomR) of the state phi_in, pi_in (field 0) into scal->rbar:
+// `grid` blocks, partials[grid][kMaxQ].
+cudaError_t launch_nmc_ricci(int precision, const void* args, int grid, cudaStream_t s);
 
 // Axion + compact U(1) links, one 2N Runge-Kutta stage (u1_stage.cu).  Degrees of
 // freedom per site, in k order: phi, pi, theta_1..3, E_1..3.

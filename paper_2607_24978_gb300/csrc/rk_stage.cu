@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);  // [NF][3][BY+2][N] old field
-    __shared__ double s_coef[4];
+    __shared__ double s_coef[5];
     __shared__ double s_red[32][kMaxQ];
     __shared__ int s_last;
 
@@ -45,9 +45,10 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
         s_coef[1] = A.h * pow(a, 1.0 + A.alpha) / (A.dx * A.dx);
         s_coef[2] = A.h * pow(a, 3.0 + A.alpha);
         s_coef[3] = a;
+        s_coef[4] = A.nmc ? A.xi * A.scal->rbar : 0.0;  // xi R of the stage's state
     }
     __syncthreads();
-    const T cphi = (T)s_coef[0], cL = (T)s_coef[1], cV = (T)s_coef[2];
+    const T cphi = (T)s_coef[0], cL = (T)s_coef[1], cV = (T)s_coef[2], xiR = (T)s_coef[4];
     const T cA = (T)A.A, cB = (T)A.B;
     const PotCoef<T> P(A.m2, A.lam, A.g2);
     Acc<T> accK[NF], accG[NF], accV;
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
                         const T p0 = phc[0][i];
                         const T p1 = NF > 1 ? phc[NF - 1][i] : (T)0;
                         T dV;
-                        if (f == 0) dV = p0 * (P.m20 + P.l0 * p0 * p0 + (NF > 1 ? P.g2 * p1 * p1 : (T)0));
+                        if (f == 0) dV = p0 * (P.m20 + P.l0 * p0 * p0 + (NF > 1 ? P.g2 * p1 * p1 : (T)0)) + xiR * p0;
                         else dV = p1 * (P.m21 + P.l1 * p1 * p1 + P.g2 * p0 * p0);
                         ksum += pv[i] * pv[i];
                         const T fphi = cphi * pv[i];
@@ -219,7 +220,9 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
         S->diag[D_GV] = 0.0;
         if (expand) {
             const double Fa = b;
-            const double Fb = pow(a, 2.0 * A.alpha + 1.0) * (A.kappa / 6.0) * ((2.0 * A.alpha - 1.0) * rho - 3.0 * p);
+            // Eq. Friedmann1, or for a non-minimally coupled field Eq. piadot with R of the state
+            const double Fb = A.nmc ? a * (pow(a, 2.0 * A.alpha) * S->rbar / 6.0 - (1.0 - A.alpha) * (b / a) * (b / a))
+                                    : pow(a, 2.0 * A.alpha + 1.0) * (A.kappa / 6.0) * ((2.0 * A.alpha - 1.0) * rho - 3.0 * p);
             const double ka = first ? A.h * Fa : A.A * S->rk[0] + A.h * Fa;
             const double kb = first ? A.h * Fb : A.A * S->rk[1] + A.h * Fb;
             S->rk[0] = ka;
@@ -237,6 +240,75 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
         if (st) atomicOr(&S->status, st);
         S->counter = 0u;
     }
+}
+
+// Background Ricci scalar of a non-minimally coupled field (section "Scalar fields
+// non-minimally coupled to gravity", Eq. eomR in program units):
+//   R = kappa F [(1 - 6 xi) (2 G - 2 K) + 4 <V> - 6 xi <phi V'>],  F = 1 / (1 + (6 xi - 1) xi kappa <phi^2>),
+// with K = <pi^2> / (2 a^6) and G = <(grad+ phi)^2> / (2 a^2) of the state (field 0).  Per-thread
+// compensated sums, FP64 across threads and blocks in a fixed order; the last block writes R.
+template <typename T>
+__global__ void __launch_bounds__(256) k_nmc_ricci(const RkStageArgs<T> A)
+{
+    __shared__ double s_red[32][kMaxQ];
+    __shared__ int s_last;
+    const int N = A.N;
+    const long long V = (long long)N * N * N;
+    const T m2 = (T)A.m2[0], lam = (T)A.lam[0];
+    Acc<T> sK, sG, sV, sPV, sP2;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < V; n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % N), y = (int)((n / N) % N), z = (int)(n / ((long long)N * N));
+        const T ph = A.phi_in[0][n], pv = A.pi_in[0][n];
+        const T px = A.phi_in[0][n - x + (x + 1 == N ? 0 : x + 1)];
+        const T py = A.phi_in[0][n + (long long)((y + 1 == N ? 0 : y + 1) - y) * N];
+        const T pz = A.phi_in[0][n + (long long)((z + 1 == N ? 0 : z + 1) - z) * N * N];
+        sK.add(pv * pv);
+        sG.add((px - ph) * (px - ph) + (py - ph) * (py - ph) + (pz - ph) * (pz - ph));
+        sV.add(ph * ph * ((T)0.5 * m2 + (T)0.25 * lam * ph * ph));
+        sPV.add(ph * ph * (m2 + lam * ph * ph));
+        sP2.add(ph * ph);
+    }
+    double v[kMaxQ] = {sK.value(), sG.value(), sV.value(), sPV.value(), sP2.value()};
+    block_reduce<kMaxQ>(v, s_red, threadIdx.x, blockDim.x);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < kMaxQ; ++q) A.partials[(size_t)blockIdx.x * kMaxQ + q] = v[q];
+        __threadfence();
+        const unsigned prev = atomicAdd(&A.scal->counter, 1u);
+        s_last = (prev + 1u == gridDim.x);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double w[kMaxQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < kMaxQ; ++q) w[q] += __ldcg(&A.partials[(size_t)b * kMaxQ + q]);
+    block_reduce<kMaxQ>(w, s_red, threadIdx.x, blockDim.x);
+    if (threadIdx.x == 0) {
+        DevScal* S = A.scal;
+        const double vol = (double)V, a = S->a, a2 = a * a;
+        const double K = w[0] / (2.0 * a2 * a2 * a2 * vol);
+        const double G = w[1] / (2.0 * a2 * A.dx * A.dx * vol);
+        const double Vp = w[2] / vol, phidv = w[3] / vol, phi2 = w[4] / vol;
+        const double F = 1.0 / (1.0 + (6.0 * A.xi - 1.0) * A.xi * A.kappa * phi2);
+        S->rbar = A.kappa * F * ((1.0 - 6.0 * A.xi) * (2.0 * G - 2.0 * K) + 4.0 * Vp - 6.0 * A.xi * phidv);
+        S->counter = 0u;
+    }
+}
+
+template <typename T>
+static cudaError_t launch_nmc_ricci_t(const RkStageArgs<T>& A, int grid, cudaStream_t s)
+{
+    k_nmc_ricci<T><<<grid, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nmc_ricci(int precision, const void* args, int grid, cudaStream_t s)
+{
+    if (grid < 1) return cudaErrorInvalidValue;
+    if (precision == CL_PREC_FP64) return launch_nmc_ricci_t(*static_cast<const RkStageArgs<double>*>(args), grid, s);
+    return launch_nmc_ricci_t(*static_cast<const RkStageArgs<float>*>(args), grid, s);
 }
 
 template <typename T, int NF, bool KAHAN, int VW>

@@ -86,3 +86,65 @@ def test_rk_without_expansion(cl):
     gphi, gpi, e, st, eo, _ = run_pair(cl, 12, 1, 0, cl.CL_INT_RK4_5, O.RK4_5, 20, expansion=False)
     assert rel_l2(gphi, st.phi) < 1e-12
     assert e["a"] == 1.0
+
+
+def run_nmc(cl, N, prec, integ, scheme, nsteps, xi, alpha, dt=0.01, pot=(0.6, 1.0), seed=37, adot=0.3, fbar=0.9,
+            amp=0.05):
+    L = 0.8 * N
+    phi, pi = inputs.scalar_state(N, 1, seed=seed, fbar=(fbar,), amp=amp, pamp=amp)
+    m = O.make_model(N, L, nf=1, alpha=alpha, kappa=0.6, expansion=True, m2=(pot[0], 0.0), lam=(pot[1], 0.0),
+                     xi=xi)
+    st = O.State(phi.copy(), pi.copy(), np.array([1.0, adot, 0.0]))
+    dtype = np.float64 if prec == 0 else np.float32
+    with cl.Lattice(N, L, 1, prec, integ, expansion=True, alpha=alpha, kappa=0.6, dt=dt) as g:
+        g.cl_set_potential(cl.CL_POT_POLY, [pot[0], pot[1], 0.0, 0.0, 0.0])
+        g.cl_set_nonminimal(xi)
+        g.cl_set_state(cl.CL_FIELD_PHI0, st.phi[0].astype(dtype))
+        g.cl_set_state(cl.CL_FIELD_PI0, st.pi[0].astype(dtype))
+        g.cl_set_scalars(st.abt[0], st.abt[1], 0.0)
+        e0 = g.cl_energies()
+        r0 = O.nmc_ricci(m, st)
+        g.cl_step(nsteps)
+        launches = g.cl_last_launch_count()
+        gphi, gpi = g.cl_get_state(cl.CL_FIELD_PHI0), g.cl_get_state(cl.CL_FIELD_PI0)
+        e = g.cl_energies()
+    O.step(m, st, scheme, dt, nsteps)
+    return gphi, gpi, e0, r0, e, st, m, launches
+
+
+@pytest.mark.parametrize("integ,scheme,stages", [(2, O.RK3_3, 3), (3, O.RK4_5, 5)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4), (2, 1e-4)])
+@pytest.mark.parametrize("xi,alpha", [(0.25, 1.0), (-0.4, 0.0)])
+def test_nmc_parity(cl, integ, scheme, stages, prec, tol, xi, alpha):
+    """Non-minimally coupled field (cl_set_nonminimal): fields, a, a' and the background
+    Ricci scalar against the oracle; two launches per stage (Ricci reduction + stage)."""
+    N, n = 12, 20
+    gphi, gpi, e0, r0, e, st, m, launches = run_nmc(cl, N, prec, integ, scheme, n, xi, alpha)
+    assert rel_l2(gphi, st.phi[0]) < tol
+    assert rel_l2(gpi, st.pi[0]) < tol
+    assert e["a"] == pytest.approx(st.abt[0], rel=tol)
+    assert e["adot"] == pytest.approx(st.abt[1], rel=max(tol, 1e-9))
+    assert e0["ricci"] == pytest.approx(r0, rel=max(tol, 1e-9))
+    assert e["ricci"] == pytest.approx(O.nmc_ricci(m, st), rel=max(tol, 1e-9))
+    assert launches == 2 * n * stages
+
+
+def test_nmc_conformal_quartic_keeps_a_linear(cl):
+    """xi = 1/6 with a massless quartic potential: R = 0 and, in conformal time, a'' = 0."""
+    gphi, gpi, e0, r0, e, st, m, _ = run_nmc(cl, 16, 0, cl.CL_INT_RK4_5, O.RK4_5, 30, 1.0 / 6.0, 1.0, pot=(0.0, 1.0),
+                                             adot=0.3, fbar=1.2, amp=0.2)
+    assert abs(e["ricci"]) < 1e-13 and abs(e0["ricci"]) < 1e-13
+    assert e["a"] == pytest.approx(1.0 + 0.3 * 0.01 * 30, rel=1e-13)
+    assert e["adot"] == pytest.approx(0.3, rel=1e-13)
+
+
+def test_nmc_needs_one_field_and_runge_kutta(cl):
+    with cl.Lattice(8, 6.0, 1, 0, cl.CL_INT_VV2) as g:
+        with pytest.raises(cl.CLError):
+            g.cl_set_nonminimal(0.1)
+    with cl.Lattice(8, 6.0, 2, 0, cl.CL_INT_RK3_3) as g:
+        with pytest.raises(cl.CLError):
+            g.cl_set_nonminimal(0.1)
+    with cl.Lattice(8, 6.0, 1, 0, cl.CL_INT_RK3_3) as g:
+        with pytest.raises(cl.CLError):
+            g.cl_set_nonminimal(float("nan"))
