@@ -9,7 +9,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
-SOURCES = ["lattice.c", "vacuum.c", "u1.c", "surrogate.c"]
+SOURCES = ["lattice.c", "vacuum.c", "u1.c", "surrogate.c", "gw.c"]
 
 
 def _sources():

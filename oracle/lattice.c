@@ -167,12 +167,14 @@ void orc_u1_rk_step(const orc_model* m, int scheme, double h,
  *   a'  half-kick with rho(t), p(t);   pi half-kick with a(t);
  *   a   drift by h a';                 phi drift with ((a(t)+a(t+h))/2)^(alpha-3);
  *   pi  half-kick with a(t+h);         a' half-kick with rho(t+h), p(t+h).       */
-static void vv_step(const orc_model* m, double h, double* phi, double* pi, double* abt, double* tmp)
+static void vv_step(const orc_model* m, double h, double* phi, double* pi, double* abt, double* tmp, double* gv,
+                    double* gp)
 {
     const int N = m->N;
     const int64_t V = (int64_t)N * N * N;
     double e[ORC_NE];
     double a = abt[0], b = abt[1];
+    double* gtmp = gv ? malloc(sizeof(double) * (size_t)(5 * V)) : NULL;
 
     if (m->expansion) {
         orc_energies(m, phi, pi, NULL, NULL, abt, e);
@@ -181,18 +183,28 @@ static void vv_step(const orc_model* m, double h, double* phi, double* pi, doubl
     for (int f = 0; f < m->nf; ++f) {
         orc_kick_force(m, f, phi, a, tmp + (int64_t)f * V);
     }
+    if (gv) orc_gw_force(m, phi, gv, a, gtmp);  /* GW half-kick with the fields at t */
     for (int f = 0; f < m->nf; ++f)
         for (int64_t n = 0; n < V; ++n) pi[(int64_t)f * V + n] += 0.5 * h * tmp[(int64_t)f * V + n];
+    if (gv)
+        for (int64_t n = 0; n < 5 * V; ++n) gp[n] += 0.5 * h * gtmp[n];
 
     const double a1 = m->expansion ? a + h * b : a;
     const double ahalf = 0.5 * (a + a1);
     const double cd = h * pow(ahalf, m->alpha - 3.0);
     for (int64_t n = 0; n < (int64_t)m->nf * V; ++n) phi[n] += cd * pi[n];
+    if (gv)
+        for (int64_t n = 0; n < 5 * V; ++n) gv[n] += cd * gp[n];
     a = a1;
 
     for (int f = 0; f < m->nf; ++f) orc_kick_force(m, f, phi, a, tmp + (int64_t)f * V);
+    if (gv) orc_gw_force(m, phi, gv, a, gtmp);  /* and with the fields at t + h */
     for (int f = 0; f < m->nf; ++f)
         for (int64_t n = 0; n < V; ++n) pi[(int64_t)f * V + n] += 0.5 * h * tmp[(int64_t)f * V + n];
+    if (gv) {
+        for (int64_t n = 0; n < 5 * V; ++n) gp[n] += 0.5 * h * gtmp[n];
+        free(gtmp);
+    }
 
     if (m->expansion) {
         double abt1[3] = {a, b, abt[2]};
@@ -303,18 +315,18 @@ static void rk_step(const orc_model* m, int scheme, double h, double* phi, doubl
  * leading error term; order 2 is one velocity-Verlet step.  Order 4 gives the three-step
  * Yoshida scheme, orders 6, 8 and 10 take 9, 27 and 81 velocity-Verlet steps. */
 static void composed_step(const orc_model* m, int order, double h, double* phi, double* pi, double* abt,
-                          double* tmp)
+                          double* tmp, double* gv, double* gp)
 {
     if (order <= 2) {
-        vv_step(m, h, phi, pi, abt, tmp);
+        vv_step(m, h, phi, pi, abt, tmp, gv, gp);
         return;
     }
     const double c = pow(2.0, 1.0 / (order - 1));
     const double x1 = 1.0 / (2.0 - c);
     const double x0 = -c / (2.0 - c);
-    composed_step(m, order - 2, x1 * h, phi, pi, abt, tmp);
-    composed_step(m, order - 2, x0 * h, phi, pi, abt, tmp);
-    composed_step(m, order - 2, x1 * h, phi, pi, abt, tmp);
+    composed_step(m, order - 2, x1 * h, phi, pi, abt, tmp, gv, gp);
+    composed_step(m, order - 2, x0 * h, phi, pi, abt, tmp, gv, gp);
+    composed_step(m, order - 2, x1 * h, phi, pi, abt, tmp, gv, gp);
 }
 
 void orc_step(const orc_model* m, int scheme, double h, int nsteps,
@@ -328,13 +340,24 @@ void orc_step(const orc_model* m, int scheme, double h, int nsteps,
     double* tmp = malloc(sizeof(double) * (size_t)(m->nf * V));
     for (int s = 0; s < nsteps; ++s) {
         switch (scheme) {
-        case ORC_VV2: vv_step(m, h, phi, pi, abt, tmp); break;
-        case ORC_YOSHIDA4: composed_step(m, 4, h, phi, pi, abt, tmp); break;
-        case ORC_YOSHIDA6: composed_step(m, 6, h, phi, pi, abt, tmp); break;
-        case ORC_YOSHIDA8: composed_step(m, 8, h, phi, pi, abt, tmp); break;
-        case ORC_YOSHIDA10: composed_step(m, 10, h, phi, pi, abt, tmp); break;
+        case ORC_VV2: vv_step(m, h, phi, pi, abt, tmp, NULL, NULL); break;
+        case ORC_YOSHIDA4: composed_step(m, 4, h, phi, pi, abt, tmp, NULL, NULL); break;
+        case ORC_YOSHIDA6: composed_step(m, 6, h, phi, pi, abt, tmp, NULL, NULL); break;
+        case ORC_YOSHIDA8: composed_step(m, 8, h, phi, pi, abt, tmp, NULL, NULL); break;
+        case ORC_YOSHIDA10: composed_step(m, 10, h, phi, pi, abt, tmp, NULL, NULL); break;
         default: rk_step(m, scheme, h, phi, pi, abt); break;
         }
     }
+    free(tmp);
+}
+
+void orc_step_gw(const orc_model* m, int scheme, double h, int nsteps, double* phi, double* pi, double* gv,
+                 double* gp, double* abt)
+{
+    const int64_t V = (int64_t)m->N * m->N * m->N;
+    double* tmp = malloc(sizeof(double) * (size_t)(m->nf * V));
+    const int order = scheme == ORC_VV2 ? 2 : scheme == ORC_YOSHIDA4 ? 4 : scheme == ORC_YOSHIDA6 ? 6
+                    : scheme == ORC_YOSHIDA8 ? 8 : 10;
+    for (int s = 0; s < nsteps; ++s) composed_step(m, order, h, phi, pi, abt, tmp, gv, gp);
     free(tmp);
 }

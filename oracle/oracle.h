@@ -96,6 +96,21 @@ double orc_nmc_ricci(const orc_model* m, const double* phi, const double* pi, co
 void orc_step(const orc_model* m, int scheme, double h, int nsteps,
               double* phi, double* pi, double* links, double* efield, double* abt);
 
+/* ---- gravitational waves (gw.c; section "New algorithm for GWs") ----
+ * Five traceless auxiliaries v = {v11, v12, v13, v22, v23} (v33 = -v11 - v22), each N^3, and
+ * their momenta gp = a^(3-alpha) v' (same layout).  orc_gw_force: the kick
+ *   a^(1+alpha) Lap v_ab + 2 kappa a^(1+alpha) [Pi_ab - delta_ab Pi / 3],
+ *   Pi_ab = sum_f dbar_a phi_f dbar_b phi_f, dbar the central difference;
+ * orc_step_gw: the leapfrog schemes (VV2, Yoshida) of orc_step with the GW fields kicked and
+ * drifted alongside the scalars (no backreaction on a);
+ * orc_gw_spectrum: d rho_GW / d log k of the TT part of h' = a^(alpha-3) gp, binned as
+ * orc_spectrum with the factor 1 / (4 kappa a^(2 alpha)). */
+void orc_gw_force(const orc_model* m, const double* phi, const double* gv, double a, double* out);
+void orc_step_gw(const orc_model* m, int scheme, double h, int nsteps, double* phi, double* pi, double* gv,
+                 double* gp, double* abt);
+int orc_gw_spectrum(const orc_model* m, const double* gp, const double* abt, double dn, int type, double* k_out,
+                    double* delta_out, double* count_out, int cap);
+
 /* ---- U(1) + axion: right-hand side of the coupled system and the Gauss charge ---- */
 void orc_u1_rhs(const orc_model* m, const double* phi, const double* pi, const double* links,
                 const double* efield, const double* abt,

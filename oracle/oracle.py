@@ -53,6 +53,10 @@ def lib():
                                  dp, dp, dp]
         L.orc_spectrum.restype = C.c_int
         L.orc_spectrum.argtypes = [C.c_int, C.c_double, dp, C.c_double, C.c_int, dp, dp, dp, C.c_int]
+        L.orc_gw_force.argtypes = [mp, dp, dp, C.c_double, dp]
+        L.orc_step_gw.argtypes = [mp, C.c_int, C.c_double, C.c_int, dp, dp, dp, dp, dp]
+        L.orc_gw_spectrum.restype = C.c_int
+        L.orc_gw_spectrum.argtypes = [mp, dp, dp, C.c_double, C.c_int, dp, dp, dp, C.c_int]
         L.orc_nmc_ricci.restype = C.c_double
         L.orc_nmc_ricci.argtypes = [mp, dp, dp, dp]
         L.orc_gauge_spectrum.restype = C.c_int
@@ -130,6 +134,28 @@ def energies(model, st):
                        _ptr(None if st.links is None else _c(st.links)),
                        _ptr(None if st.efield is None else _c(st.efield)), _c(st.abt), out)
     return dict(zip(E_NAMES, out))
+
+
+def gw_force(model, phi, gv, a):
+    out = np.zeros_like(_c(gv))
+    lib().orc_gw_force(C.byref(model), _c(phi), _c(gv), float(a), out)
+    return out
+
+
+def step_gw(model, st, gv, gp, scheme, h, nsteps=1):
+    """Leapfrog steps of the scalars (st) and the five GW auxiliaries gv, gp (5, N, N, N), in place."""
+    st.phi, st.pi, st.abt = _c(st.phi), _c(st.pi), _c(st.abt)
+    assert gv.flags.c_contiguous and gp.flags.c_contiguous and gv.dtype == np.float64 and gp.dtype == np.float64
+    lib().orc_step_gw(C.byref(model), int(scheme), float(h), int(nsteps), st.phi, st.pi, gv, gp, st.abt)
+    return st
+
+
+def gw_spectrum(model, gp, abt, dn=1.0, type_=1):
+    N = model.N
+    cap = int(np.floor(np.sqrt(3.0) * (N // 2) / dn + 0.5)) + 2
+    k, d, c = np.zeros(cap), np.zeros(cap), np.zeros(cap)
+    nb = lib().orc_gw_spectrum(C.byref(model), _c(gp), _c(abt), float(dn), int(type_), k, d, c, cap)
+    return k[:nb], d[:nb], c[:nb]
 
 
 def nmc_ricci(model, st):
