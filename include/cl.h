@@ -89,7 +89,11 @@ enum {
     CL_FIELD_PHI0 = 0, CL_FIELD_PHI1 = 1, /* scalar fields                                  */
     CL_FIELD_PI0 = 2, CL_FIELD_PI1 = 3,   /* their momenta pi = a^(3-alpha) phi'            */
     CL_FIELD_THETA1 = 4, CL_FIELD_THETA2 = 5, CL_FIELD_THETA3 = 6, /* U(1) link angles dx*A_i on n -> n+i */
-    CL_FIELD_E1 = 7, CL_FIELD_E2 = 8, CL_FIELD_E3 = 9             /* electric field A_i' on the same links */
+    CL_FIELD_E1 = 7, CL_FIELD_E2 = 8, CL_FIELD_E3 = 9,            /* electric field A_i' on the same links */
+    /* gravitational-wave auxiliaries (cl_enable_gw): v11, v12, v13, v22, v23 (v33 = -v11 - v22)
+     * and their momenta a^(3-alpha) v' */
+    CL_FIELD_GW_V11 = 10, CL_FIELD_GW_V12 = 11, CL_FIELD_GW_V13 = 12, CL_FIELD_GW_V22 = 13, CL_FIELD_GW_V23 = 14,
+    CL_FIELD_GW_P11 = 15, CL_FIELD_GW_P12 = 16, CL_FIELD_GW_P13 = 17, CL_FIELD_GW_P22 = 18, CL_FIELD_GW_P23 = 19
 };
 
 /* Batched ensembles (members > 1): B independent lattices of sizes member_N[m]
@@ -243,6 +247,25 @@ cl_status cl_set_gauge_coupling(cl_lattice* l, double alphaL, double ws2);
  * their minimally coupled form (hubble_violation is then not a constraint of the system; set
  * a' explicitly).  Errors: CL_EINVAL, CL_EUNSUPPORTED. */
 cl_status cl_set_nonminimal(cl_lattice* l, double xi);
+
+/* Gravitational waves (section "New algorithm for GWs"): five traceless auxiliaries v_ij
+ * (v33 = -v11 - v22, fields CL_FIELD_GW_*, zero when enabled) evolved with the leapfrog
+ * alongside the scalars:
+ *   v' = a^(alpha-3) pi_v,  pi_v' = a^(1+alpha) Lap v + 2 kappa a^(1+alpha) [Pi_ij - delta_ij Pi / 3],
+ *   Pi_ij = sum_f dbar_i phi_f dbar_j phi_f  (central differences), no backreaction on a.
+ * A single scalar lattice with a leapfrog integrator (VV-2 or Yoshida); one GW launch joins
+ * every pass.  Errors: CL_EUNSUPPORTED (ensembles, gauge fields, Runge-Kutta), CL_ENOMEM. */
+cl_status cl_enable_gw(cl_lattice* l);
+
+/* Energy spectrum of the gravitational waves, d rho_GW / d log k in program units, of the TT
+ * part h_ij(k) = Lambda_ij,lm(kbar) v_lm(k) with kbar_i = sin(k_i dx)/dx:
+ *   type 1: n_l S_l / (N^6 dn) / (4 kappa a^(2 alpha)),  type 2: 4 pi n_l^3 (S_l/#_l) / N^6 / (4 kappa a^(2 alpha)),
+ * S_l the sum over bin l of sum_ij |(Lambda H')_ij|^2, H' the unnormalised DFT of h' = a^(alpha-3) pi_v
+ * (so that summing type 1 over the bins with weight dn/n_l gives rho_GW = <h'_ij h'_ij>_TT / (4 kappa a^(2 alpha))).
+ * Binning and outputs as cl_spectrum.  Uses cuFFT; synchronising.  Errors: CL_EINVAL (not
+ * enabled, bad arguments), CL_ECUDA, CL_ENOMEM. */
+cl_status cl_gw_spectrum(cl_lattice* l, double dn, int32_t type, double* k_out, double* delta_out, double* count_out,
+                         int32_t cap, int32_t* nbins);
 
 /* When limit > 0, a Hubble violation above it sets the device status CL_ECONSTRAINT
  * (reported by the next synchronising call).  limit <= 0 disables the check (default). */

@@ -24,6 +24,8 @@ CL_GSPEC_E, CL_GSPEC_B, CL_GSPEC_APLUS, CL_GSPEC_AMINUS = 0, 1, 2, 3
 CL_POT_LPHI4, CL_POT_M2, CL_POT_M2_G2, CL_POT_LPHI4_G2, CL_POT_POLY = 0, 1, 2, 3, 4
 CL_FIELD_PHI0, CL_FIELD_PHI1, CL_FIELD_PI0, CL_FIELD_PI1 = 0, 1, 2, 3
 CL_FIELD_THETA1, CL_FIELD_THETA2, CL_FIELD_THETA3, CL_FIELD_E1, CL_FIELD_E2, CL_FIELD_E3 = 4, 5, 6, 7, 8, 9
+CL_FIELD_GW_V11, CL_FIELD_GW_V12, CL_FIELD_GW_V13, CL_FIELD_GW_V22, CL_FIELD_GW_V23 = 10, 11, 12, 13, 14
+CL_FIELD_GW_P11, CL_FIELD_GW_P12, CL_FIELD_GW_P13, CL_FIELD_GW_P22, CL_FIELD_GW_P23 = 15, 16, 17, 18, 19
 CL_OPT_GRAPH, CL_OPT_TILE_BY, CL_OPT_TILE_DZ, CL_OPT_STAGES, CL_OPT_PASS_VARIANT = 0, 1, 2, 3, 4
 
 # Every exported entry point of include/cl.h.
@@ -33,7 +35,7 @@ EXPORTS = ["cl_init_lattice", "cl_free", "cl_set_potential", "cl_set_state", "cl
            "cl_fused_pass_noalloc", "cl_surrogate_create", "cl_surrogate_free", "cl_surrogate_set_weights",
            "cl_surrogate_get_weights", "cl_surrogate_forward", "cl_surrogate_backward", "cl_surrogate_get_grads",
            "cl_surrogate_last_launch_count", "cl_surrogate_loss", "cl_surrogate_adamw", "cl_surrogate_channel_stats",
-           "cl_lattice_pack", "cl_lattice_unpack", "cl_surrogate_jump", "cl_surrogate_size", "cl_autotune", "cl_gauge_spectrum", "cl_set_nonminimal"]
+           "cl_lattice_pack", "cl_lattice_unpack", "cl_surrogate_jump", "cl_surrogate_size", "cl_autotune", "cl_gauge_spectrum", "cl_set_nonminimal", "cl_enable_gw", "cl_gw_spectrum"]
 CL_ACT_RELU, CL_ACT_GELU = 1, 2
 CL_SG_BF16, CL_SG_FP32 = 0, 1
 
@@ -117,6 +119,9 @@ def lib():
         L.cl_set_gauge_coupling.argtypes = [C.c_void_p, C.c_double, C.c_double]
         L.cl_set_hubble_limit.argtypes = [C.c_void_p, C.c_double]
         L.cl_set_nonminimal.argtypes = [C.c_void_p, C.c_double]
+        L.cl_enable_gw.argtypes = [C.c_void_p]
+        L.cl_gw_spectrum.argtypes = [C.c_void_p, C.c_double, C.c_int32, P(C.c_double), P(C.c_double), P(C.c_double),
+                                     C.c_int32, P(C.c_int32)]
         L.cl_set_option.argtypes = [C.c_void_p, C.c_int32, C.c_int64]
         L.cl_get_option.argtypes = [C.c_void_p, C.c_int32, P(C.c_int64)]
         L.cl_last_launch_count.argtypes = [C.c_void_p]
@@ -322,6 +327,19 @@ class Lattice:
 
     def cl_set_nonminimal(self, xi):
         _check(self.h, lib().cl_set_nonminimal(self.h, float(xi)))
+
+    def cl_enable_gw(self):
+        _check(self.h, lib().cl_enable_gw(self.h))
+
+    def cl_gw_spectrum(self, dn=1.0, type_=1):
+        nb = C.c_int32()
+        lib().cl_gw_spectrum(self.h, float(dn), int(type_), None, None, None, 0, C.byref(nb))
+        n = nb.value
+        k, d, c = np.zeros(n), np.zeros(n), np.zeros(n)
+        dp = C.POINTER(C.c_double)
+        _check(self.h, lib().cl_gw_spectrum(self.h, float(dn), int(type_), k.ctypes.data_as(dp), d.ctypes.data_as(dp),
+                                            c.ctypes.data_as(dp), n, C.byref(nb)))
+        return k, d, c
 
     def cl_set_hubble_limit(self, limit):
         _check(self.h, lib().cl_set_hubble_limit(self.h, float(limit)))

@@ -74,6 +74,10 @@ struct cl_lattice {
     bool u1_fused = false;          // U(1) stage as one fused launch (plaquettes in shared memory)
     bool nmc = false;               // non-minimal coupling xi phi^2 R of field 0 (Runge-Kutta)
     double xi = 0.0;
+    bool gw = false;                // gravitational-wave auxiliaries evolved with the leapfrog
+    void* gv[5][2] = {};            // v11, v12, v13, v22, v23 (ping-pong)
+    void* gpv[5][2] = {};           // their momenta a^(3-alpha) v'
+    int gw_BY = 1, gw_DZ = 1, gw_nby = 1, gw_nbz = 1;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t last_launches = 0;
     // batched ensemble (members > 1): per-member sizes, boxes, arena offsets and couplings
@@ -347,6 +351,22 @@ cl_status choose_tiles(cl_lattice* l)
         nblocks = (int)(units < wave ? units : wave);
         l->grid = nblocks;
     }
+    if (l->gw) {
+        // GW pass (direct loads, as the Runge-Kutta stage kernel): about 256 threads per block,
+        // two blocks per SM, the y tiles cut into z chunks so that about one wave covers the lattice
+        int gby = TX >= 256 ? 1 : 256 / TX;
+        if (gby > N) gby = N;
+        while (gby > 1 && gw_pass_smem(l->nf, N, gby, l->es) > (size_t)kPassMaxSmem / 2) --gby;
+        if (gw_pass_smem(l->nf, N, gby, l->es) > (size_t)kPassMaxSmem)
+            return fail(l, CL_EINVAL, "lattice too large for the GW pass tiling (N=%d)", N);
+        l->gw_BY = gby;
+        l->gw_nby = (N + gby - 1) / gby;
+        int64_t nbz = (2 * (int64_t)nsm) / l->gw_nby;
+        if (nbz < 1) nbz = 1;
+        if (nbz > N) nbz = N;
+        l->gw_DZ = (int)((N + nbz - 1) / nbz);
+        l->gw_nbz = (N + l->gw_DZ - 1) / l->gw_DZ;
+    }
     if (is_rk(l->p.integrator)) {
         // Runge-Kutta stage kernel (direct loads): about 256 threads per block, two blocks per
         // SM, the y tiles cut into the same z chunks so that about one wave covers the lattice
@@ -485,6 +505,32 @@ cl_status run_rk_stage_t(cl_lattice* l, const PassCoef& pc, int in, int out)
 
 cl_status run_u1(cl_lattice* l, int what, double cA, double cB, int flags, int in, int out);
 
+// The GW pass of a leapfrog pass with coefficients pc, buffers in -> out.
+template <typename T>
+cl_status run_gw_pass_t(cl_lattice* l, const PassCoef& pc, int in, int out)
+{
+    GwPassArgs<T> A{};
+    for (int f = 0; f < l->nf; ++f) {
+        A.phi_in[f] = (const T*)l->phi[f][in];
+        A.pi_in[f] = (const T*)l->pi[f][in];
+        A.c_in[f] = (const T*)l->cc[f][in];
+    }
+    for (int c = 0; c < 5; ++c) {
+        A.v_in[c] = (const T*)l->gv[c][in];
+        A.pv_in[c] = (const T*)l->gpv[c][in];
+        A.v_out[c] = (T*)l->gv[c][out];
+        A.pv_out[c] = (T*)l->gpv[c][out];
+    }
+    A.scal = l->scal;
+    A.N = l->N; A.BY = l->gw_BY; A.DZ = l->gw_DZ; A.nby = l->gw_nby; A.nbz = l->gw_nbz;
+    A.dx = l->dx; A.alpha = l->p.alpha; A.kappa = l->p.kappa;
+    A.d = pc.d; A.k = pc.k;
+    A.flags = (pc.flags & P_DRIFT) | (l->p.expansion ? P_EXPANSION : 0);
+    cudaError_t e = launch_gw_pass(l->p.precision, l->nf, &A, l->VW, l->stream);
+    if (e != cudaSuccess) return fail(l, CL_ECUDA, "GW pass launch failed: %s", cudaGetErrorString(e));
+    return CL_OK;
+}
+
 // Background Ricci scalar of the current state of a non-minimally coupled lattice into scal->rbar.
 template <typename T>
 cl_status nmc_ricci_t(cl_lattice* l)
@@ -547,6 +593,10 @@ cl_status run_ens_pass(cl_lattice* l, const PassCoef& pc, int in, int out, int m
 cl_status run_pass(cl_lattice* l, const PassCoef& pc, int in, int out)
 {
     if (is_ens(l)) return run_ens_pass(l, pc, in, out, 0, l->members);
+    if (l->gw && !pc.rk) {  // the GW auxiliaries first, from the same scalar input buffers
+        cl_status s = is_fp64(l) ? run_gw_pass_t<double>(l, pc, in, out) : run_gw_pass_t<float>(l, pc, in, out);
+        if (s != CL_OK) return s;
+    }
     if (pc.rk == 2) return run_u1(l, 1, pc.A, pc.B, pc.flags, in, out);  // axion + U(1) stage
     if (pc.rk) return is_fp64(l) ? run_rk_stage_t<double>(l, pc, in, out) : run_rk_stage_t<float>(l, pc, in, out);
     return run_pass_impl(l, pc, in, out, nullptr);
@@ -786,6 +836,14 @@ cl_status read_status(cl_lattice* l, std::vector<DevScal>& host)
 // 0 = scalar field f, 1 = its momentum, 2 = link angle theta_f, 3 = electric field E_f.
 int field_kind(const cl_lattice* l, int field, int* f)
 {
+    if (l->gw && field >= CL_FIELD_GW_V11 && field <= CL_FIELD_GW_V23) {
+        *f = field - CL_FIELD_GW_V11;
+        return 4;
+    }
+    if (l->gw && field >= CL_FIELD_GW_P11 && field <= CL_FIELD_GW_P23) {
+        *f = field - CL_FIELD_GW_P11;
+        return 5;
+    }
     if (field == CL_FIELD_PHI0 || field == CL_FIELD_PHI1) {
         *f = field - CL_FIELD_PHI0;
         return *f < l->nf ? 0 : -1;
@@ -811,6 +869,8 @@ void* field_buffer(cl_lattice* l, int kind, int f, int buf)
     case 0: return l->phi[f][buf];
     case 1: return l->pi[f][buf];
     case 2: return l->th[f][buf];
+    case 4: return l->gv[f][buf];
+    case 5: return l->gpv[f][buf];
     default: return l->ef[f][buf];
     }
 }
@@ -859,6 +919,10 @@ void cl_free(cl_lattice* l)
         }
         for (int q = 0; q < 8; ++q)
             if (l->ku1[q][b]) cudaFree(l->ku1[q][b]);
+        for (int c = 0; c < 5; ++c) {
+            if (l->gv[c][b]) cudaFree(l->gv[c][b]);
+            if (l->gpv[c][b]) cudaFree(l->gpv[c][b]);
+        }
     }
     for (int q = 0; q < 9; ++q)
         if (l->u1s[q]) cudaFree(l->u1s[q]);
@@ -1075,7 +1139,7 @@ cl_status cl_get_state(cl_lattice* l, int32_t member, int32_t field, void* dst, 
     const int kind = field_kind(l, field, &f);
     if (kind < 0) return fail(l, CL_EINVAL, "field %d not present", field);
     int buf = l->cur;
-    if (l->open && kind == 1) {
+    if (l->open && (kind == 1 || kind == 5)) {
         cl_status s = close_leapfrog(l, false);  // integer-time momenta into the spare buffer
         if (s != CL_OK) return s;
         buf = l->cur ^ 1;
@@ -1157,6 +1221,97 @@ cl_status cl_set_nonminimal(cl_lattice* l, double xi)
     l->diag_valid = false;
     invalidate_graphs(l);
     return CL_OK;
+}
+
+cl_status cl_enable_gw(cl_lattice* l)
+{
+    if (!l) return CL_EINVAL;
+    if (is_ens(l) || l->gauge || is_rk(l->p.integrator))
+        return fail(l, CL_EUNSUPPORTED, "gravitational waves need a single scalar lattice with a leapfrog integrator");
+    if (l->gw) return CL_OK;
+    cl_status s = close_leapfrog(l, true);
+    if (s != CL_OK) return s;
+    const size_t bytes = (size_t)l->N * l->N * l->N * l->es;
+    for (int c = 0; c < 5; ++c)
+        for (int b = 0; b < 2; ++b) {
+            if (cudaMalloc(&l->gv[c][b], bytes) != cudaSuccess || cudaMalloc(&l->gpv[c][b], bytes) != cudaSuccess)
+                return fail(l, CL_ENOMEM, "GW field allocation failed");
+            CUDA_TRY(l, cudaMemsetAsync(l->gv[c][b], 0, bytes, l->stream));
+            CUDA_TRY(l, cudaMemsetAsync(l->gpv[c][b], 0, bytes, l->stream));
+        }
+    l->gw = true;
+    s = choose_tiles(l);
+    if (s != CL_OK) return s;
+    CUDA_TRY(l, cudaStreamSynchronize(l->stream));
+    invalidate_graphs(l);
+    return CL_OK;
+}
+
+cl_status cl_gw_spectrum(cl_lattice* l, double dn, int32_t type, double* k_out, double* delta_out, double* count_out,
+                         int32_t cap, int32_t* nbins)
+{
+    if (!l) return CL_EINVAL;
+    if (!l->gw) return fail(l, CL_EINVAL, "gravitational waves are not enabled (cl_enable_gw)");
+    if (!(dn > 0) || (type != 1 && type != 2) || cap < 0 || (cap > 0 && (!k_out || !delta_out || !count_out)))
+        return fail(l, CL_EINVAL, "GW spectrum: bad arguments");
+    const int N = l->N;
+    const int64_t V = (int64_t)N * N * N;
+    const int nb = (int)floor(sqrt(3.0) * (N / 2) / dn + 0.5) + 1;
+    if (nbins) *nbins = nb;
+    if (cap == 0) return CL_OK;
+    int buf = l->cur;
+    if (l->open) {  // integer-time momenta (and a) into the spare buffer / diagnostics
+        cl_status s = close_leapfrog(l, false);
+        if (s != CL_OK) return s;
+        buf = l->cur ^ 1;
+    }
+    std::vector<DevScal> hs;
+    cl_status st = read_status(l, hs);
+    if (st != CL_OK) return st;
+    const double a = hs[0].a;  // a at the integer time (the staggered form keeps a there)
+    const size_t nh = (size_t)N * N * (N / 2 + 1);
+    double* real = nullptr;
+    double2* F = nullptr;
+    double* bins = nullptr;  // S[nb], C[nb], k[nb], delta[nb]
+    cufftHandle plan = 0;
+    if (cudaMalloc(&real, (size_t)V * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&F, 5 * nh * sizeof(double2)) != cudaSuccess || cudaMalloc(&bins, 4 * (size_t)nb * sizeof(double)) != cudaSuccess)
+        st = fail(l, CL_ENOMEM, "GW spectrum scratch allocation failed");
+    if (st == CL_OK && cufftPlan3d(&plan, N, N, N, CUFFT_D2Z) != CUFFT_SUCCESS) st = fail(l, CL_ECUDA, "cufftPlan3d failed");
+    if (st == CL_OK && cufftSetStream(plan, l->stream) != CUFFT_SUCCESS) st = fail(l, CL_ECUDA, "cufftSetStream failed");
+    for (int c = 0; c < 5 && st == CL_OK; ++c) {
+        // h' = a^(alpha-3) pi_v: the factor is applied to the binned sums below
+        if (launch_field_to_double(l->p.precision, l->gpv[c][buf], real, V, l->stream) != cudaSuccess)
+            st = fail(l, CL_ECUDA, "field conversion failed");
+        else if (cufftExecD2Z(plan, real, (cufftDoubleComplex*)(F + c * nh)) != CUFFT_SUCCESS)
+            st = fail(l, CL_ECUDA, "D2Z failed");
+    }
+    if (st == CL_OK && cudaMemsetAsync(bins, 0, 2 * (size_t)nb * sizeof(double), l->stream) != cudaSuccess)
+        st = fail(l, CL_ECUDA, "memset failed");
+    if (st == CL_OK && launch_gw_bins(F, N, l->dx, dn, nb, bins, bins + nb, l->stream) != cudaSuccess)
+        st = fail(l, CL_ECUDA, "binning failed");
+    if (st == CL_OK &&
+        launch_spectrum_finish(bins, bins + nb, N, l->p.L, dn, type, nb, bins + 2 * nb, bins + 3 * nb, l->stream) != cudaSuccess)
+        st = fail(l, CL_ECUDA, "spectrum finish failed");
+    std::vector<double> h(4 * (size_t)nb);
+    if (st == CL_OK && cudaMemcpyAsync(h.data(), bins, 4 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, l->stream) != cudaSuccess)
+        st = fail(l, CL_ECUDA, "copy failed");
+    if (st == CL_OK && cudaStreamSynchronize(l->stream) != cudaSuccess) st = fail(l, CL_ECUDA, "sync failed");
+    if (st == CL_OK) {
+        // |h'|^2 = a^(2(alpha-3)) |pi_v|^2, times 1 / (4 kappa a^(2 alpha))
+        const double ca = pow(a, 2.0 * (l->p.alpha - 3.0)) / (4.0 * l->p.kappa * pow(a, 2.0 * l->p.alpha));
+        const int n = cap < nb ? cap : nb;
+        for (int i = 0; i < n; ++i) {
+            count_out[i] = h[nb + i];
+            k_out[i] = h[2 * nb + i];
+            delta_out[i] = ca * h[3 * nb + i];
+        }
+    }
+    if (plan) cufftDestroy(plan);
+    if (real) cudaFree(real);
+    if (F) cudaFree(F);
+    if (bins) cudaFree(bins);
+    return st;
 }
 
 cl_status cl_set_hubble_limit(cl_lattice* l, double limit)
@@ -1351,7 +1506,7 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
     if (!l->open && !rk) {
         cl_status s = open_leapfrog(l);
         if (s != CL_OK) return s;
-        l->last_launches += 1;
+        l->last_launches += l->gw ? 2 : 1;
     }
     const std::vector<PassCoef> sched = step_schedule(l);
     const int pps = (int)sched.size();
@@ -1384,8 +1539,9 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
                 l->cur ^= 1;
             }
         }
-        // two-launch gauge stages (helper + stage) and non-minimally coupled stages (Ricci + stage)
-        l->last_launches += (l->gauge && !l->u1_fused) || l->nmc ? 2 * pps : pps;
+        // two-launch gauge stages (helper + stage), non-minimally coupled stages (Ricci + stage)
+        // and leapfrog passes with gravitational waves (GW pass + scalar pass)
+        l->last_launches += (l->gauge && !l->u1_fused) || l->nmc || l->gw ? 2 * pps : pps;
     }
     // a leapfrog step ends with the energies of its integer time; a Runge-Kutta stage
     // reports those of the state it started from, so they are recomputed on demand

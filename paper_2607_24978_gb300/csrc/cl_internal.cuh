@@ -105,6 +105,30 @@ struct RkStageArgs {
     double xi;          //   use scal->rbar, written by launch_nmc_ricci for the same state
 };
 cudaError_t launch_rk_stage(int precision, int nf, const void* args, int vw, cudaStream_t s);
+// Gravitational waves (gw_pass.cu): five traceless auxiliaries v = {v11, v12, v13, v22,
+// v23} and their momenta, kicked and drifted by one pass before each fused scalar pass with
+// the same coefficients; the scalars' input buffers provide the source.
+template <typename T>
+struct GwPassArgs {
+    const T* phi_in[2];
+    const T* pi_in[2];
+    const T* c_in[2];
+    const T* v_in[5];
+    const T* pv_in[5];
+    T* v_out[5];
+    T* pv_out[5];
+    const DevScal* scal;
+    int N, BY, DZ, nby, nbz;
+    double dx, alpha, kappa;
+    double d, k;        // pass coefficients (already x dt), as in ScalarPassArgs
+    int flags;          // P_DRIFT, P_EXPANSION
+};
+cudaError_t launch_gw_pass(int precision, int nf, const void* args, int vw, cudaStream_t s);
+size_t gw_pass_smem(int nf, int N, int BY, int es);
+// TT energy spectrum sums of the five transformed momenta F[5][N][N][N/2+1] (h'_33 = -h'_11 - h'_22)
+cudaError_t launch_gw_bins(const double2* F, int N, double dx, double dn, int nbins, double* S, double* C,
+                           cudaStream_t s);
+
 // Background Ricci scalar (Eq. eomR) of the state phi_in, pi_in (field 0) into scal->rbar:
 // `grid` blocks, partials[grid][kMaxQ].
 cudaError_t launch_nmc_ricci(int precision, const void* args, int grid, cudaStream_t s);
