@@ -254,6 +254,14 @@ U1_STAGES = 3
 # Runge-Kutta auxiliaries, read + write, 4 B each
 U1_BYTES_PER_SITE_STAGE = 8 * 2 * 2 * 4
 RK_STAGES = 5
+# GW pass per site: the scalars' phi, pi, c of two fields read (24 B) and the five
+# auxiliaries and their momenta read and written (2 x 10 x 4 B), FP32
+GW_BYTES_PER_SITE_PASS = 2 * 3 * 4 + 2 * 10 * 4
+NMC_XI = 0.3
+# NMC stage per site, one field, FP32 + Kahan: the Ricci reduction reads phi, pi (8 B); the
+# stage reads phi, pi, k_phi, k_pi, c and writes them (40 B); averaged over 5 stages, the first
+# of which reads no k
+NMC_BYTES_PER_SITE_STAGE = 8 + (4 * 40 + (40 - 8)) / 5.0
 # algorithmic bytes of one RK4-5 step per site, two fields, FP32 + Kahan: phi, pi, k_phi, k_pi,
 # c read + write in four stages; the first stage (A = 0) reads no k
 RK_BYTES_PER_SITE_STEP = 2 * 4 * (4 * 5 * 2 + (5 * 2 - 2))
@@ -354,6 +362,79 @@ def run_rk_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_
                          "algorithmic_bytes_per_launch": bytes_stage},
             "gpu_launches": launches, "clocks": clocks,
             "energies_end": {"a": e["a"], "rho": e["rho"], "hubble_violation": e["hubble_violation"]}}
+
+
+def run_gw_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src):
+    """The headline two-field lattice with the gravitational-wave auxiliaries: every Yoshida-4
+    pass is a GW pass (k_gw_pass) and the fused scalar pass."""
+    g = make_lattice(cl, cl.CL_PREC_FP32_KAHAN, stream.cuda_stream)
+    g.cl_enable_gw()
+    g.cl_step(args.warmup)
+    g.cl_sync()
+    barrier(world)
+    el, launches, clocks = timed_region(torch, g, stream, args.steps)
+    barrier(world)
+    el_max = max_over_ranks(el, world)
+    # the GW pass alone, timed over the same number of passes with the scalar pass removed by
+    # difference: a second run of the scalar lattice without GW fields
+    k, d, c = g.cl_gw_spectrum()
+    g.close()
+    g2 = make_lattice(cl, cl.CL_PREC_FP32_KAHAN, stream.cuda_stream)
+    g2.cl_step(args.warmup)
+    g2.cl_sync()
+    el0, _, _ = timed_region(torch, g2, stream, args.steps)
+    g2.close()
+    gw_pass_s = max(el - el0, 1e-12) / (args.steps * PASSES_PER_STEP)
+    bytes_gw = N ** 3 * GW_BYTES_PER_SITE_PASS
+    achieved = bytes_gw / gw_pass_s / 1e9
+    return {"metric": "Gsite-updates/s at 256^3 with gravitational waves", "value": world * N ** 3 * args.steps / el_max / 1e9,
+            "unit": "Gsite-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config({"workload": "two-field preheating as the headline, plus the five traceless GW "
+                                          "auxiliaries (v, pi_v FP32) sourced by both fields, Yoshida-4",
+                              "gw_fields": 10}),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                         "kernel": "k_gw_pass<float,2,kahan,4> (time = with GW - without, per pass)",
+                         "algorithmic_bytes_per_launch": bytes_gw},
+            "scalar_only_ms_per_step": el0 / args.steps * 1e3,
+            "gw_spectrum_bins": int(len(d)), "gw_rho_max_bin": float(d.max()),
+            "gpu_launches": launches, "clocks": clocks}
+
+
+def run_nmc_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src):
+    """One non-minimally coupled lambda phi^4 field at 256^3 with RK4-5: every stage is the
+    Ricci reduction (k_nmc_ricci) and the stage kernel (k_rk_stage)."""
+    g = cl.Lattice(N, L, 1, cl.CL_PREC_FP32_KAHAN, cl.CL_INT_RK4_5, expansion=True, alpha=1.0, kappa=KAPPA, dt=DT,
+                   stream=stream.cuda_stream)
+    g.cl_set_potential(cl.CL_POT_LPHI4, [1.0])
+    g.cl_init_vacuum(SEED, 16 * 2 * math.pi / L, 1e-4, (1.0,), (0.0,))
+    g.cl_set_nonminimal(NMC_XI)
+    g.cl_step(args.warmup)
+    g.cl_sync()
+    barrier(world)
+    el, launches, clocks = timed_region(torch, g, stream, args.steps)
+    barrier(world)
+    el_max = max_over_ranks(el, world)
+    e = g.cl_energies()
+    g.close()
+    stage_s = el / (args.steps * RK_STAGES)
+    bytes_stage = N ** 3 * NMC_BYTES_PER_SITE_STAGE
+    achieved = bytes_stage / stage_s / 1e9
+    return {"metric": "Gsite-updates/s at 256^3, non-minimally coupled field, RK4-5",
+            "value": world * N ** 3 * args.steps / el_max / 1e9,
+            "unit": "Gsite-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config({"workload": "lambda phi^4 (program units), xi = %g, 256^3, RK4-5 (2N), FP32+Kahan, "
+                                          "alpha = 1, vacuum amplitude 1e-4, k_cut = 16 k_IR" % NMC_XI,
+                              "fields": 1, "integrator": "rk4_5", "passes_per_step": RK_STAGES}),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                         "kernel": "k_nmc_ricci + k_rk_stage<float,1,kahan,4> (mean per stage)",
+                         "algorithmic_bytes_per_launch": bytes_stage},
+            "ricci_end": e["ricci"], "gpu_launches": launches, "clocks": clocks}
 
 
 def run_ensemble_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src):
@@ -561,7 +642,8 @@ def run_gpu(args, world, rank, local):
             print(json.dumps(line), flush=True)
         return
     if args.workload != "preheat":
-        fn = {"u1": run_u1_workload, "rk": run_rk_workload}.get(args.workload, run_ensemble_workload)
+        fn = {"u1": run_u1_workload, "rk": run_rk_workload, "gw": run_gw_workload,
+              "nmc": run_nmc_workload}.get(args.workload, run_ensemble_workload)
         line = fn(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src)
         if rank == 0:
             print(json.dumps(line), flush=True)
@@ -657,7 +739,7 @@ def main():
     ap.add_argument("--by", type=int, default=None, help="override CL_OPT_TILE_BY")
     ap.add_argument("--dz", type=int, default=None, help="override CL_OPT_TILE_DZ")
     ap.add_argument("--variant", type=int, default=None, help="override CL_OPT_PASS_VARIANT (0 ring, 1 ringless)")
-    ap.add_argument("--workload", default="preheat", choices=["preheat", "u1", "ensemble", "surrogate", "rk"],
+    ap.add_argument("--workload", default="preheat", choices=["preheat", "u1", "ensemble", "surrogate", "rk", "gw", "nmc"],
                     help="preheat: the headline 256^3 two-field run; u1, ensemble: the other workloads")
     ap.add_argument("--members", type=int, default=None, help="ensemble size (default 1024)")
     ap.add_argument("--no-train", action="store_true", help="surrogate workload: throughput only")

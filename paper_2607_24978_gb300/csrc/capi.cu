@@ -467,6 +467,17 @@ cl_status run_pass_impl(cl_lattice* l, const PassCoef& pc, int in, int out, int*
 }
 
 // One 2N Runge-Kutta stage reading buffer `in` and writing buffer `out`.
+// Blocks of the Ricci reduction (whole x rows each): at most one per row, 8 per SM.
+int nmc_grid(const cl_lattice* l)
+{
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int64_t g = (int64_t)l->N * l->N;
+    if (g > 8 * (int64_t)nsm) g = 8 * (int64_t)nsm;
+    return (int)(g < 1 ? 1 : g);
+}
+
 template <typename T>
 cl_status run_rk_stage_t(cl_lattice* l, const PassCoef& pc, int in, int out)
 {
@@ -495,7 +506,7 @@ cl_status run_rk_stage_t(cl_lattice* l, const PassCoef& pc, int in, int out)
     A.nmc = l->nmc ? 1 : 0;
     A.xi = l->xi;
     if (l->nmc) {  // the Ricci scalar of the stage's state first
-        cudaError_t e = launch_nmc_ricci(l->p.precision, &A, l->rk_nby * l->rk_nbz, l->stream);
+        cudaError_t e = launch_nmc_ricci(l->p.precision, &A, nmc_grid(l), l->stream);
         if (e != cudaSuccess) return fail(l, CL_ECUDA, "Ricci reduction launch failed: %s", cudaGetErrorString(e));
     }
     cudaError_t e = launch_rk_stage(l->p.precision, l->nf, &A, l->VW, l->stream);
@@ -545,7 +556,7 @@ cl_status nmc_ricci_t(cl_lattice* l)
     A.m2[0] = l->m2[0]; A.lam[0] = l->lam[0];
     A.nmc = 1;
     A.xi = l->xi;
-    cudaError_t e = launch_nmc_ricci(l->p.precision, &A, l->rk_nby * l->rk_nbz, l->stream);
+    cudaError_t e = launch_nmc_ricci(l->p.precision, &A, nmc_grid(l), l->stream);
     if (e != cudaSuccess) return fail(l, CL_ECUDA, "Ricci reduction launch failed: %s", cudaGetErrorString(e));
     return CL_OK;
 }
@@ -1216,6 +1227,8 @@ cl_status cl_set_nonminimal(cl_lattice* l, double xi)
     if (is_ens(l) || l->gauge || l->nf != 1 || !is_rk(l->p.integrator))
         return fail(l, CL_EUNSUPPORTED, "the non-minimal coupling needs one scalar field and a Runge-Kutta integrator");
     if (!isfinite(xi)) return fail(l, CL_EINVAL, "xi must be finite");
+    cl_status s = grow_partials(l, nmc_grid(l));
+    if (s != CL_OK) return s;
     l->nmc = true;
     l->xi = xi;
     l->diag_valid = false;

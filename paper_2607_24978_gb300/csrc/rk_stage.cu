@@ -253,20 +253,25 @@ __global__ void __launch_bounds__(256) k_nmc_ricci(const RkStageArgs<T> A)
     __shared__ double s_red[32][kMaxQ];
     __shared__ int s_last;
     const int N = A.N;
-    const long long V = (long long)N * N * N;
     const T m2 = (T)A.m2[0], lam = (T)A.lam[0];
     Acc<T> sK, sG, sV, sPV, sP2;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < V; n += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(n % N), y = (int)((n / N) % N), z = (int)(n / ((long long)N * N));
-        const T ph = A.phi_in[0][n], pv = A.pi_in[0][n];
-        const T px = A.phi_in[0][n - x + (x + 1 == N ? 0 : x + 1)];
-        const T py = A.phi_in[0][n + (long long)((y + 1 == N ? 0 : y + 1) - y) * N];
-        const T pz = A.phi_in[0][n + (long long)((z + 1 == N ? 0 : z + 1) - z) * N * N];
-        sK.add(pv * pv);
-        sG.add((px - ph) * (px - ph) + (py - ph) * (py - ph) + (pz - ph) * (pz - ph));
-        sV.add(ph * ph * ((T)0.5 * m2 + (T)0.25 * lam * ph * ph));
-        sPV.add(ph * ph * (m2 + lam * ph * ph));
-        sP2.add(ph * ph);
+    // whole x rows per block: the +y and +z neighbour rows load coalesced, one division per row
+    for (int row = blockIdx.x; row < N * N; row += gridDim.x) {
+        const int z = row / N, y = row - z * N;
+        const size_t rb = (size_t)row * N;
+        const size_t ry = ((size_t)z * N + (y + 1 == N ? 0 : y + 1)) * N;
+        const size_t rz = ((size_t)(z + 1 == N ? 0 : z + 1) * N + y) * N;
+        for (int x = threadIdx.x; x < N; x += blockDim.x) {
+            const T ph = A.phi_in[0][rb + x], pv = A.pi_in[0][rb + x];
+            const T px = A.phi_in[0][rb + (x + 1 == N ? 0 : x + 1)];
+            const T py = A.phi_in[0][ry + x];
+            const T pz = A.phi_in[0][rz + x];
+            sK.add(pv * pv);
+            sG.add((px - ph) * (px - ph) + (py - ph) * (py - ph) + (pz - ph) * (pz - ph));
+            sV.add(ph * ph * ((T)0.5 * m2 + (T)0.25 * lam * ph * ph));
+            sPV.add(ph * ph * (m2 + lam * ph * ph));
+            sP2.add(ph * ph);
+        }
     }
     double v[kMaxQ] = {sK.value(), sG.value(), sV.value(), sPV.value(), sP2.value()};
     block_reduce<kMaxQ>(v, s_red, threadIdx.x, blockDim.x);
@@ -287,7 +292,7 @@ __global__ void __launch_bounds__(256) k_nmc_ricci(const RkStageArgs<T> A)
     block_reduce<kMaxQ>(w, s_red, threadIdx.x, blockDim.x);
     if (threadIdx.x == 0) {
         DevScal* S = A.scal;
-        const double vol = (double)V, a = S->a, a2 = a * a;
+        const double vol = (double)N * N * N, a = S->a, a2 = a * a;
         const double K = w[0] / (2.0 * a2 * a2 * a2 * vol);
         const double G = w[1] / (2.0 * a2 * A.dx * A.dx * vol);
         const double Vp = w[2] / vol, phidv = w[3] / vol, phi2 = w[4] / vol;
