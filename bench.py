@@ -287,7 +287,7 @@ def run_u1_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_
                    alpha=c["alpha"], kappa=c["kappa"], dt=c["dt"], stream=stream.cuda_stream)
     g.cl_set_potential(cl.CL_POT_M2, [c["m2"]])
     g.cl_set_gauge_coupling(c["alphaL"], c["ws2"])
-    if args.variant is not None:  # 1: fused stage (default), 0: plaquette + stage launches
+    if args.variant is not None:  # 2: staged launches (default), 0: gather launches, 1: fused stage
         g.cl_set_option(cl.CL_OPT_PASS_VARIANT, args.variant)
     if args.dz is not None:  # planes per block of the U(1) kernels (tuning runs)
         g.cl_set_option(cl.CL_OPT_TILE_DZ, args.dz)
@@ -307,7 +307,7 @@ def run_u1_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_
     barrier(world)
     el_max = max_over_ranks(el, world)
     e = g.cl_energies()
-    fused = g.cl_get_option(cl.CL_OPT_PASS_VARIANT) == 1
+    variant = g.cl_get_option(cl.CL_OPT_PASS_VARIANT)
     u1_dz = g.cl_get_option(cl.CL_OPT_TILE_DZ)
     g.close()
     stage_s = el / (args.steps * U1_STAGES)
@@ -323,8 +323,9 @@ def run_u1_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_
                        "l2": "inputs (%.0f MB) larger than L2; no flush" % (N ** 3 * 16 * 2 * 4 / 1e6)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
-                         "kernel": ("k_u1_fused<float> (one launch per RK stage)" if fused else
-                                    "one RK stage: k_u1_plaquettes + k_u1_stage"), "tile_dz": u1_dz,
+                         "kernel": {1: "k_u1_fused<float> (one launch per RK stage)",
+                                    2: "one RK stage: k_u1s_plaquettes + k_u1s_stage (staged neighbourhoods)"}.get(
+                                        variant, "one RK stage: k_u1_plaquettes + k_u1_stage"), "tile_dz": u1_dz,
                          "algorithmic_bytes_per_launch": bytes_stage},
             "gpu_launches": launches, "clocks": clocks,
             "energies_end": {"a": e["a"], "rho": e["rho"], "KE": e["KE"], "GB": e["GB"],

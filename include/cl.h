@@ -285,9 +285,11 @@ cl_status cl_set_hubble_limit(cl_lattice* l, double limit);
  * stage buffers, no consumer barrier; 16-byte vectors, 2..5 stages (ensembles 3..6), other
  * rows fall back to 0), 0 = drifted rows shared through a ring in shared memory with one
  * consumer barrier per plane.  Both give bit-identical fields on the same tiles.  For an
- * axion-U(1) lattice: 0 = the plaquette fields through global memory and a second launch
- * per Runge-Kutta stage (the library's choice), 1 = one fused launch per stage with the
- * plaquette fields in shared memory (N a multiple of 32; same results to rounding).
+ * axion-U(1) lattice, two launches per Runge-Kutta stage (plaquette fields through global
+ * memory, then the stage) unless 1: 0 = every neighbour gathered from L1/L2, 2 = the
+ * neighbourhoods of each plane staged in shared memory by asynchronous copies (the library's
+ * choice where N is a multiple of 32, else 0), 1 = one fused launch per stage with the
+ * plaquette fields in shared memory (N a multiple of 32).  All three agree to rounding.
  * Errors: CL_EINVAL. */
 enum { CL_OPT_GRAPH = 0, CL_OPT_TILE_BY = 1, CL_OPT_TILE_DZ = 2, CL_OPT_STAGES = 3, CL_OPT_PASS_VARIANT = 4 };
 cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value);

@@ -15,6 +15,7 @@
 
 #include "cl_internal.cuh"
 #include "surrogate_train.cuh"
+#include "u1_staged.cuh"
 
 using namespace clk;
 
@@ -72,6 +73,7 @@ struct cl_lattice {
     int opt_BY = 0, opt_DZ = 0, opt_stages = 0, opt_variant = -1;  // -1: library choice
     int u1_dz = 8;                  // planes per block of the U(1) kernels
     bool u1_fused = false;          // U(1) stage as one fused launch (plaquettes in shared memory)
+    bool u1_staged = false;         // U(1) launches with shared-memory staged neighbourhoods
     bool nmc = false;               // non-minimal coupling xi phi^2 R of field 0 (Runge-Kutta)
     double xi = 0.0;
     bool gw = false;                // gravitational-wave auxiliaries evolved with the leapfrog
@@ -392,6 +394,9 @@ cl_status choose_tiles(cl_lattice* l)
         // the fused stage only on request: measured slower than the two launches at 192^3
         // (3.96 against 5.12 Gsite-updates/s; both latency-bound)
         l->u1_fused = l->opt_variant == 1 && u1_fused_ok(N);
+        // the staged launches (neighbourhoods in shared memory) are the library's choice
+        // where the tiles divide N
+        l->u1_staged = (l->opt_variant == -1 || l->opt_variant == 2) && u1_staged_ok(N);
         int bps = prec == CL_PREC_FP64 ? kU1BlocksPerSM64 : kU1BlocksPerSM32;
         if (l->u1_fused) {
             CUDA_TRY(l, u1_fused_blocks_per_sm(prec, &bps));
@@ -400,8 +405,11 @@ cl_status choose_tiles(cl_lattice* l)
         int64_t nbz = (int64_t)bps * nsm / tiles;
         if (nbz < 1) nbz = 1;
         if (nbz > N) nbz = N;
-        l->u1_dz = l->opt_DZ > 0 ? (l->opt_DZ > N ? N : l->opt_DZ) : (int)((N + nbz - 1) / nbz);
+        const int auto_dz = l->u1_staged ? u1_staged_dz(prec, N, nsm) : (int)((N + nbz - 1) / nbz);
+        l->u1_dz = l->opt_DZ > 0 ? (l->opt_DZ > N ? N : l->opt_DZ) : auto_dz;
         if (2 * u1_grid_blocks(N, l->u1_dz) > nblocks) nblocks = 2 * u1_grid_blocks(N, l->u1_dz);  // stage + plaquette partials
+        if (l->u1_staged && 2 * u1_staged_blocks(prec, N, l->u1_dz) > nblocks)
+            nblocks = 2 * u1_staged_blocks(prec, N, l->u1_dz);
     }
     s = grow_partials(l, nblocks);
     if (s != CL_OK) return s;
@@ -789,6 +797,9 @@ cl_status run_u1_t(cl_lattice* l, int what, double cA, double cB, int flags, int
     cudaError_t e;
     if (what == 1 && l->u1_fused) {
         e = launch_u1_fused(l->p.precision, &A, l->stream);  // plaquettes and stage in one launch
+    } else if (what == 1 && l->u1_staged) {
+        e = launch_u1_staged(l->p.precision, &A, 0, l->stream);  // plaquette fields first
+        if (e == cudaSuccess) e = launch_u1_staged(l->p.precision, &A, 1, l->stream);
     } else {
         e = launch_u1(l->p.precision, &A, 0, l->stream);  // plaquette fields first
         if (e == cudaSuccess) e = launch_u1(l->p.precision, &A, what, l->stream);
@@ -1344,7 +1355,7 @@ cl_status cl_get_option(cl_lattice* l, int32_t option, int64_t* value)
     case CL_OPT_TILE_BY: *value = ens ? l->hmem[0].BY : l->BY; return CL_OK;
     case CL_OPT_TILE_DZ: *value = ens ? l->hmem[0].DZ : (l->gauge ? l->u1_dz : l->DZ); return CL_OK;
     case CL_OPT_STAGES: *value = ens ? l->ens_stages : l->stages; return CL_OK;
-    case CL_OPT_PASS_VARIANT: *value = ens ? l->ens_variant : (l->gauge ? (l->u1_fused ? 1 : 0) : l->variant); return CL_OK;
+    case CL_OPT_PASS_VARIANT: *value = ens ? l->ens_variant : (l->gauge ? (l->u1_fused ? 1 : (l->u1_staged ? 2 : 0)) : l->variant); return CL_OK;
     }
     return fail(l, CL_EINVAL, "unknown option %d", option);
 }
@@ -1363,7 +1374,8 @@ cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value)
         l->opt_DZ = (int)value;
         return choose_tiles(l);
     case CL_OPT_PASS_VARIANT:
-        if (value < -1 || value > 1) return fail(l, CL_EINVAL, "pass variant must be -1, 0 or 1");
+        if (value < -1 || value > (l->gauge ? 2 : 1))
+            return fail(l, CL_EINVAL, "pass variant must be -1, 0 or 1 (2 on an axion-U(1) lattice)");
         l->opt_variant = (int)value;
         return choose_tiles(l);
     case CL_OPT_STAGES:

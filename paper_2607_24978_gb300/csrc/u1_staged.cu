@@ -1,0 +1,526 @@
+// Shared-memory staged forms of the two axion-U(1) launches of a Runge-Kutta stage: the
+// plaquette fields, then the stage.  The equations, the lattice Chern-Simons discretisation,
+// the 2N-RK update and the energy sums are those of u1_stage.cu (section "ALP-gauge
+// interactions", Eq. AxionInfEOM), evaluated in the same order, except that the plaquette
+// launch takes sin P, cos P and sin^2(P/2) from one sincos of P/2 (sin P = 2 s c,
+// cos P = 1 - 2 s^2).
+//
+// The gather kernels of u1_stage.cu read 40 to 110 neighbour values per site from L1/L2
+// into registers; a thread can only keep as many loads in flight as it has registers, and
+// both kernels stall on memory latency at a fraction of the HBM bandwidth.  Here a block
+// owns a 32 x TY tile of (x, y) (TY = 16 in FP32, 8 in FP64; one site per consumer thread)
+// and marches up its z chunk with planes z-1, z, z+1 of every array that is read at a
+// neighbour in shared memory: rows y0-1 .. y0+TY and columns x0-VE .. x0+31+VE (VE elements
+// per 16 bytes, so that every row is whole 16-byte units; only the first and last columns
+// are read).  Warp roles, synchronised by mbarriers only:
+//  * six producer warps copy plane after plane into a ring of five slots with 16-byte
+//    asynchronous copies (cp.async; the source of every 16-byte unit of a plane, periodic
+//    wrap included, is tabulated in shared memory once per block), and each lane's copies
+//    arrive on the slot's "full" barrier when they have landed (measured at 192^3 FP32: one
+//    producer warp, 2.5 Gsite-updates/s; two, 4.3; four, 6.3; six, 6.7; eight, 6.4;
+//    single bulk copies of each staged row, 1.1: many small bulk copies are slow);
+//  * TY consumer warps (one row of the tile each) wait for the planes they need, compute the
+//    site, and release a slot once they have read it for the last time (its "empty" barrier
+//    counts one arrival per consumer warp), so no warp waits for another one's work.
+// Arrays read only at the site itself (theta and the Runge-Kutta auxiliaries) are loaded by
+// the consumers straight from global memory.  Every wait is bounded and reports through the
+// status word.  Needs N % 32 == 0; other sizes use the gather kernels.
+#include <math.h>
+
+#include "cl_internal.cuh"
+#include "kernel_common.cuh"
+#include "u1_common.cuh"
+#include "u1_staged.cuh"
+
+
+namespace clk {
+
+template <typename T>
+struct U1SGeom {
+    static constexpr int TX = 32;
+    static constexpr int TY = sizeof(T) == 4 ? 16 : 8;
+    static constexpr int CW = TY;              // consumer warps: one tile row each
+    static constexpr int PWARPS = 6;           // producer warps
+    static constexpr int PL = 32 * PWARPS;     // producer lanes
+    static constexpr int NT = 32 * (CW + PWARPS);  // threads of a block (consumers, then the producers)
+    static constexpr int VE = 16 / (int)sizeof(T);
+    static constexpr int PW = TX + 2 * VE;     // staged columns x0 - VE .. x0 + TX + VE - 1
+    static constexpr int PH = TY + 2;          // staged rows y0 - 1 .. y0 + TY
+    static constexpr int ARR = PH * PW;        // elements of one array plane
+    static constexpr int CPR = PW / VE;        // 16-byte units of a staged row
+    static constexpr int SLOTS = 5;
+};
+
+// arrays staged by the plaquette launch and by the stage launch, in slot order
+enum { PQ_PHI = 0, PQ_TH = 1, PQ_E = 4, PQ_NA = 7 };
+enum { SG_PHI = 0, SG_PI = 1, SG_E = 2, SG_SP = 5, SG_RP = 8, SG_Z = 11, SG_NA = 14 };
+
+// 16-byte units of one staged plane of NA arrays, and the producer lanes' share of them
+template <typename T, int NA>
+struct U1SUnits {
+    static constexpr int CH = NA * U1SGeom<T>::PH * U1SGeom<T>::CPR;
+    static constexpr int PER_LANE = (CH + U1SGeom<T>::PL - 1) / U1SGeom<T>::PL;
+};
+
+// dynamic shared memory: the ring of plane slots, then the unit table (two words a unit)
+template <typename T, int NA>
+constexpr size_t u1s_smem_bytes()
+{
+    return (size_t)U1SGeom<T>::SLOTS * NA * U1SGeom<T>::ARR * sizeof(T) +
+           (size_t)U1SGeom<T>::PL * U1SUnits<T, NA>::PER_LANE * 8;
+}
+
+// Tile and z chunk of this block.
+template <typename T>
+struct U1STile {
+    using G = U1SGeom<T>;
+    uint32_t N, x0, y0, z0, nz;
+    __device__ __forceinline__ U1STile(uint32_t N_, uint32_t dz) : N(N_)
+    {
+        const uint32_t ntx = N / G::TX, nty = N / G::TY;
+        uint32_t b = blockIdx.x;
+        const uint32_t bx = b % ntx;
+        b /= ntx;
+        const uint32_t by = b % nty, bz = b / nty;
+        x0 = bx * G::TX;
+        y0 = by * G::TY;
+        z0 = bz * dz;
+        nz = z0 + dz < N ? dz : N - z0;
+    }
+};
+
+// Unit table of the producer lanes: unit i of lane l (l + 32 i of the plane) is array a at
+// staged row r, 16-byte column unit u; its entry holds (a << 16 | element offset in the slot)
+// and the element offset of its source in a plane of the array (periodic wrap applied).
+template <typename T, int NA>
+__device__ __forceinline__ void u1s_build_units(uint2* table, const U1STile<T>& t, int tid, int nthr)
+{
+    using G = U1SGeom<T>;
+    using U = U1SUnits<T, NA>;
+    const int N = (int)t.N;
+    for (int e = tid; e < G::PL * U::PER_LANE; e += nthr) {
+        const int lane = e % G::PL, i = e / G::PL, c = lane + G::PL * i;
+        uint2 v = make_uint2(0xffffffffu, 0u);
+        if (c < U::CH) {
+            const int a = c / (G::PH * G::CPR), rem = c - a * (G::PH * G::CPR);
+            const int r = rem / G::CPR, u = rem - r * G::CPR;
+            int gy = (int)t.y0 - 1 + r, gx = (int)t.x0 - G::VE + u * G::VE;  // in [-1, N] and [-VE, N]
+            gy = gy < 0 ? gy + N : (gy >= N ? gy - N : gy);
+            gx = gx < 0 ? gx + N : (gx >= N ? gx - N : gx);
+            v.x = ((uint32_t)a << 16) | (uint32_t)(a * G::ARR + r * G::PW + u * G::VE);
+            v.y = (uint32_t)gy * (uint32_t)N + (uint32_t)gx;
+        }
+        table[i * G::PL + lane] = v;
+    }
+}
+
+__device__ __forceinline__ void cp_async16_cg(void* smem_dst, const void* gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+
+// This lane's cp.async copies, issued before, arrive on bar once they have landed (the
+// barrier's expected count includes the arrival).
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Producer lane: its units of plane z0 - 1 + q (periodic) of the arrays src[] into slot,
+// arriving on full when they have landed.
+template <typename T, int NA>
+__device__ __forceinline__ void u1s_copy_plane(int lane, T* slot, const T* const* src, const uint2* table,
+                                               const U1STile<T>& t, int q, uint64_t* full)
+{
+    const int N = (int)t.N;
+    int z = (int)t.z0 - 1 + q;
+    z = z < 0 ? z + N : (z >= N ? z - N : z);
+    const size_t zoff = (size_t)z * t.N * t.N;
+#pragma unroll 4
+    for (int i = 0; i < U1SUnits<T, NA>::PER_LANE; ++i) {
+        const uint2 v = table[i * U1SGeom<T>::PL + lane];
+        if (v.x != 0xffffffffu) cp_async16_cg(slot + (v.x & 0xffffu), src[v.x >> 16] + zoff + v.y);
+    }
+    cp_async_arrive_noinc(full);
+}
+
+// Neighbourhood of a consumer's site in the three staged planes (z-1, z, z+1).
+template <typename T>
+struct U1SNb {
+    using G = U1SGeom<T>;
+    const T* p[3];
+    __device__ __forceinline__ T operator()(int a, int ox, int oy, int oz) const
+    {
+        return p[oz + 1][a * G::ARR + oy * G::PW + ox];
+    }
+    __device__ __forceinline__ T at(int a, const int (&o)[3]) const { return (*this)(a, o[0], o[1], o[2]); }
+    // clover sum of array a (normal k) over the four plaquettes around the site at offset o
+    __device__ __forceinline__ T clover(int a, int k, int ox, int oy, int oz) const
+    {
+        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        const int o[3] = {ox, oy, oz};
+        int b[3] = {ox, oy, oz}, c[3] = {ox, oy, oz};
+        b[k1] -= 1;
+        c[k2] -= 1;
+        int d[3] = {b[0], b[1], b[2]};
+        d[k2] -= 1;
+        return (at(a, o) + at(a, b)) + (at(a, c) + at(a, d));
+    }
+};
+
+// Ring bookkeeping shared by both kernels: the producer loop and the consumers' waits and
+// releases.  Plane q of the chunk lives in slot q % SLOTS; consumers read planes j, j+1, j+2
+// for output plane j and release plane j afterwards (the last two planes after the loop).
+template <typename T, int NA>
+struct U1SRing {
+    using G = U1SGeom<T>;
+    static constexpr size_t SLOT = (size_t)NA * G::ARR;
+    T* sm;
+    const uint2* table;
+    uint64_t* full;
+    uint64_t* empty;
+    int* fail;
+    __device__ __forceinline__ bool wait(uint64_t* bar, uint32_t parity) const
+    {
+        if (mbar_wait_bounded(bar, parity, *fail ? 1000000ull : 2000000000ull)) return true;
+        *fail = 1;
+        return false;
+    }
+    // producer warp: every plane of the chunk
+    __device__ __forceinline__ void produce(int lane, const T* const* src, const U1STile<T>& t) const
+    {
+        const int nq = (int)t.nz + 2;
+        for (int q = 0; q < nq; ++q) {
+            const int st = q % G::SLOTS;
+            if (q >= G::SLOTS) wait(&empty[st], (uint32_t)((q / G::SLOTS - 1) & 1));
+            u1s_copy_plane<T, NA>(lane, sm + st * SLOT, src, table, t, q, &full[st]);
+        }
+        // copies still in flight (only after a timeout, when consumers stopped waiting)
+        if (*fail && lane == 0)
+            for (int q = max(0, nq - G::SLOTS); q < nq; ++q)
+                mbar_wait_bounded(&full[q % G::SLOTS], (uint32_t)((q / G::SLOTS) & 1), 1000000ull);
+    }
+    __device__ __forceinline__ void acquire(int q) const { wait(&full[q % G::SLOTS], (uint32_t)((q / G::SLOTS) & 1)); }
+    __device__ __forceinline__ void release(int q, int lane) const
+    {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[q % G::SLOTS]);
+    }
+    // the three planes of output plane j at the consumer's site (row ly, column lx)
+    __device__ __forceinline__ U1SNb<T> nb(int j, int lx, int ly) const
+    {
+        const int t0 = (ly + 1) * G::PW + lx + G::VE;
+        U1SNb<T> n;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) n.p[i] = sm + ((j + i) % G::SLOTS) * SLOT + t0;
+        return n;
+    }
+};
+
+// unit offset vector along axis d with sign s
+#define U1S_E(d, s) ((d) == 0 ? (s) : 0), ((d) == 1 ? (s) : 0), ((d) == 2 ? (s) : 0)
+
+template <typename T>
+__global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquettes(const U1Args<T> A)
+{
+    using G = U1SGeom<T>;
+    constexpr int NA = PQ_NA;
+    extern __shared__ __align__(128) unsigned char u1s_dyn[];
+    __shared__ const T* s_src[NA];
+    __shared__ __align__(8) uint64_t s_full[G::SLOTS], s_empty[G::SLOTS];
+    __shared__ double s_red[32][kMaxQ];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        s_src[PQ_PHI] = A.phi_in;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            s_src[PQ_TH + k] = A.th_in[k];
+            s_src[PQ_E + k] = A.E_in[k];
+        }
+        for (int k = 0; k < G::SLOTS; ++k) {
+            mbar_init(&s_full[k], G::PL);  // the producer lanes' copies
+            mbar_init(&s_empty[k], G::CW);
+        }
+        mbar_fence_init();
+        s_fail = 0;
+    }
+    __syncthreads();
+    const U1STile<T> t((uint32_t)A.N, (uint32_t)A.dz);
+    T* ring_sm = reinterpret_cast<T*>(u1s_dyn);
+    uint2* table = reinterpret_cast<uint2*>(ring_sm + G::SLOTS * NA * G::ARR);
+    u1s_build_units<T, NA>(table, t, tid, G::NT);
+    __syncthreads();
+    const U1SRing<T, NA> ring{ring_sm, table, s_full, s_empty, &s_fail};
+    Acc<T> accGB;
+    if (warp >= G::CW) {
+        ring.produce(tid - 32 * G::CW, s_src, t);
+    } else {
+        const uint32_t N = t.N;
+        const T dx = (T)A.dx;
+        ring.acquire(0);
+        ring.acquire(1);
+        for (int j = 0; j < (int)t.nz; ++j) {
+            ring.acquire(j + 2);
+            const U1SNb<T> S = ring.nb(j, lane, warp);
+            const uint32_t n = ((t.z0 + j) * N + t.y0 + warp) * N + t.x0 + lane;
+            T o_s[3], o_r[3], o_z[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+                const T P = S(PQ_TH + k1, 0, 0, 0) + S(PQ_TH + k2, U1S_E(k1, 1)) - S(PQ_TH + k1, U1S_E(k2, 1)) -
+                            S(PQ_TH + k2, 0, 0, 0);
+                const T R = dx * (S(PQ_E + k1, 0, 0, 0) + S(PQ_E + k2, U1S_E(k1, 1)) - S(PQ_E + k1, U1S_E(k2, 1)) -
+                                  S(PQ_E + k2, 0, 0, 0));
+                T sh, ch;  // sin, cos of P / 2
+                if constexpr (sizeof(T) == 4) sincosf((T)0.5 * P, &sh, &ch);
+                else sincos((T)0.5 * P, &sh, &ch);
+                const T sp = (T)2 * sh * ch, cp = (T)1 - (T)2 * sh * sh;
+                // X_k = phi Ebar_k at the corners n, n + e_k1, n + e_k2, n + e_k1 + e_k2
+                const int e1[3] = {U1S_E(k1, 1)}, e2[3] = {U1S_E(k2, 1)}, ek[3] = {U1S_E(k, 1)};
+                auto X = [&](int ox, int oy, int oz) {
+                    return S(PQ_PHI, ox, oy, oz) *
+                           (S(PQ_E + k, ox, oy, oz) + S(PQ_E + k, ox - ek[0], oy - ek[1], oz - ek[2]));
+                };
+                const T qs = X(0, 0, 0) + X(e1[0], e1[1], e1[2]) + X(e2[0], e2[1], e2[2]) +
+                             X(e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]);
+                o_s[k] = sp;
+                o_r[k] = cp * R;
+                o_z[k] = cp * ((T)0.5 * qs);
+                accGB.add((T)2 * sh * sh);
+            }
+            ring.release(j, lane);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                A.sP[k][n] = o_s[k];
+                A.rP[k][n] = o_r[k];
+                A.Z[k][n] = o_z[k];
+            }
+        }
+        ring.release((int)t.nz, lane);
+        ring.release((int)t.nz + 1, lane);
+    }
+    __syncthreads();  // producer and consumers meet; no copy is in flight past this point
+    double v[1] = {accGB.value()};
+    block_reduce<1>(v, s_red, tid, G::NT);
+    if (tid == 0) {
+        A.partials[(size_t)gridDim.x * kMaxQ + blockIdx.x] = v[0];
+        if (s_fail) atomicOr(&A.scal->status, ST_TIMEOUT);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T> A)
+{
+    using G = U1SGeom<T>;
+    constexpr int NA = SG_NA;
+    extern __shared__ __align__(128) unsigned char u1s_dyn[];
+    __shared__ const T* s_src[NA];
+    __shared__ __align__(8) uint64_t s_full[G::SLOTS], s_empty[G::SLOTS];
+    __shared__ double s_coef[6];
+    __shared__ double s_red[32][kMaxQ];
+    __shared__ int s_last, s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool first = (A.flags & P_FIRST_STAGE) != 0;
+    const bool update = (A.flags & P_ENERGY_ONLY) == 0;
+    const bool expand = (A.flags & P_EXPANSION) != 0;
+    if (tid == 0) {
+        const double a = A.scal->a, b = expand ? A.scal->b : 0.0;
+        s_coef[0] = pow(a, A.alpha - 3.0);                 // phi' = c0 pi
+        s_coef[1] = pow(a, 1.0 + A.alpha) / (A.dx * A.dx);  // Laplacian
+        s_coef[2] = pow(a, 3.0 + A.alpha);                 // potential
+        s_coef[3] = pow(a, A.alpha - 1.0);                 // E' prefactor
+        s_coef[4] = (1.0 - A.alpha) * b / a;               // electric friction
+        s_coef[5] = a;
+        s_src[SG_PHI] = A.phi_in;
+        s_src[SG_PI] = A.pi_in;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            s_src[SG_E + k] = A.E_in[k];
+            s_src[SG_SP + k] = A.sP[k];
+            s_src[SG_RP + k] = A.rP[k];
+            s_src[SG_Z + k] = A.Z[k];
+        }
+        for (int k = 0; k < G::SLOTS; ++k) {
+            mbar_init(&s_full[k], G::PL);  // the producer lanes' copies
+            mbar_init(&s_empty[k], G::CW);
+        }
+        mbar_fence_init();
+        s_fail = 0;
+    }
+    __syncthreads();
+    const U1STile<T> t((uint32_t)A.N, (uint32_t)A.dz);
+    T* ring_sm = reinterpret_cast<T*>(u1s_dyn);
+    uint2* table = reinterpret_cast<uint2*>(ring_sm + G::SLOTS * NA * G::ARR);
+    u1s_build_units<T, NA>(table, t, tid, G::NT);
+    __syncthreads();
+    const U1SRing<T, NA> ring{ring_sm, table, s_full, s_empty, &s_fail};
+    const uint32_t N = t.N, V = N * N * N;
+    Acc<T> accK, accG, accV, accKE;
+    if (warp >= G::CW) {
+        ring.produce(tid - 32 * G::CW, s_src, t);
+    } else {
+        const T c_dphi = (T)s_coef[0], cL = (T)s_coef[1], cV = (T)s_coef[2], cE = (T)s_coef[3], cfr = (T)s_coef[4];
+        const T g = (T)A.g, ws2 = (T)A.ws2, dx = (T)A.dx, m2 = (T)A.m2, lam = (T)A.lam;
+        const T inv_dx3 = (T)(1.0 / (A.dx * A.dx * A.dx)), inv4dx = (T)(0.25 / A.dx);
+        const T inv4dx2 = (T)(0.25 / (A.dx * A.dx));
+        const T h = (T)A.h, cA = (T)A.A, cB = (T)A.B;
+        ring.acquire(0);
+        ring.acquire(1);
+        for (int j = 0; j < (int)t.nz; ++j) {
+            ring.acquire(j + 2);
+            const U1SNb<T> S = ring.nb(j, lane, warp);
+            const uint32_t n = ((t.z0 + j) * N + t.y0 + warp) * N + t.x0 + lane;
+
+            // scalar sector
+            const T ph = S(SG_PHI, 0, 0, 0), pv = S(SG_PI, 0, 0, 0);
+            const T pxp = S(SG_PHI, 1, 0, 0), pxm = S(SG_PHI, -1, 0, 0);
+            const T pyp = S(SG_PHI, 0, 1, 0), pym = S(SG_PHI, 0, -1, 0);
+            const T pzp = S(SG_PHI, 0, 0, 1), pzm = S(SG_PHI, 0, 0, -1);
+            const T lap = ((pxp + pxm) + (pyp + pym) + (pzp + pzm)) - (T)6 * ph;
+            const T dV = ph * (m2 + lam * ph * ph);
+            T eb = (T)0, e2 = (T)0;
+            T Ecur[3], Bn[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                Ecur[k] = S(SG_E + k, 0, 0, 0);
+                Bn[k] = inv4dx2 * S.clover(SG_SP + k, k, 0, 0, 0);
+                eb += (T)0.5 * (Ecur[k] + S(SG_E + k, U1S_E(k, -1))) * Bn[k];
+                e2 += Ecur[k] * Ecur[k];
+            }
+            const T F_phi = c_dphi * pv;
+            const T F_pi = cL * lap - cV * dV + ws2 * g * eb;
+            accK.add(pv * pv);
+            accG.add((pxp - ph) * (pxp - ph) + (pyp - ph) * (pyp - ph) + (pzp - ph) * (pzp - ph));
+            accV.add(ph * ph * ((T)0.5 * m2 + (T)0.25 * lam * ph * ph));
+            accKE.add(e2);
+            if (update) {
+                // link forces
+                T F_E[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const int ip = (i + 1) % 3, im = (i + 2) % 3;
+                    const T mag = (S(SG_SP + im, 0, 0, 0) - S(SG_SP + im, U1S_E(ip, -1))) -
+                                  (S(SG_SP + ip, 0, 0, 0) - S(SG_SP + ip, U1S_E(im, -1)));
+                    const T cs = (S(SG_Z + im, 0, 0, 0) - S(SG_Z + im, U1S_E(ip, -1))) +
+                                 (S(SG_Z + ip, U1S_E(im, -1)) - S(SG_Z + ip, 0, 0, 0));
+                    const T Bdn = inv4dx2 * S.clover(SG_RP + i, i, 0, 0, 0);
+                    const T Bni = inv4dx2 * S.clover(SG_SP + i, i, U1S_E(i, 1));
+                    const T Bdni = inv4dx2 * S.clover(SG_RP + i, i, U1S_E(i, 1));
+                    const T wdot = (T)0.5 * (F_phi * Bn[i] + ph * Bdn + c_dphi * S(SG_PI, U1S_E(i, 1)) * Bni +
+                                             S(SG_PHI, U1S_E(i, 1)) * Bdni);
+                    F_E[i] = cE * (-cE * mag * inv_dx3 + g * (cs * inv4dx - wdot)) - cfr * Ecur[i];
+                }
+                ring.release(j, lane);
+                // 2N Runge-Kutta update of the eight degrees of freedom of this site
+                const T F[8] = {F_phi, F_pi, dx * Ecur[0], dx * Ecur[1], dx * Ecur[2], F_E[0], F_E[1], F_E[2]};
+                const T y[8] = {ph, pv, A.th_in[0][n], A.th_in[1][n], A.th_in[2][n], Ecur[0], Ecur[1], Ecur[2]};
+                T kq[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) kq[q] = first ? h * F[q] : cA * A.k_in[q][n] + h * F[q];
+                T* out[8] = {A.phi_out, A.pi_out, A.th_out[0], A.th_out[1], A.th_out[2], A.E_out[0], A.E_out[1],
+                             A.E_out[2]};
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    A.k_out[q][n] = kq[q];
+                    out[q][n] = y[q] + cB * kq[q];
+                }
+            } else {
+                ring.release(j, lane);
+            }
+        }
+        ring.release((int)t.nz, lane);
+        ring.release((int)t.nz + 1, lane);
+    }
+    __syncthreads();  // producer and consumers meet; no copy is in flight past this point
+
+    // ---- block partials; last block: energies of the old state and the (a, a') stage ----
+    double v[kMaxQ] = {accK.value(), accG.value(), accV.value(), accKE.value(), 0.0};
+    block_reduce<kMaxQ>(v, s_red, tid, G::NT);
+    if (tid == 0) {
+        if (s_fail) atomicOr(&A.scal->status, ST_TIMEOUT);
+#pragma unroll
+        for (int q = 0; q < kMaxQ; ++q) A.partials[(size_t)blockIdx.x * kMaxQ + q] = v[q];
+        __threadfence();
+        const unsigned prev = atomicAdd(&A.scal->counter, 1u);
+        s_last = (prev + 1u == gridDim.x);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double w[kMaxQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = tid; b < (int)gridDim.x; b += G::NT) {
+#pragma unroll
+        for (int q = 0; q < kMaxQ - 1; ++q) w[q] += __ldcg(&A.partials[(size_t)b * kMaxQ + q]);
+        w[kMaxQ - 1] += __ldcg(&A.partials[(size_t)gridDim.x * kMaxQ + b]);  // plaquette launch, same grid
+    }
+    block_reduce<kMaxQ>(w, s_red, tid, G::NT);
+    if (tid == 0) u1_epilogue(A, w, s_coef[5], first, update, expand, V);
+}
+
+#undef U1S_E
+
+bool u1_staged_ok(int N) { return N >= 32 && N % 32 == 0; }
+
+int u1_staged_blocks(int precision, int N, int dz)
+{
+    const int ty = precision == CL_PREC_FP64 ? U1SGeom<double>::TY : U1SGeom<float>::TY;
+    return (N / 32) * (N / ty) * ((N + dz - 1) / dz);
+}
+
+// z chunk of the staged launches: one block per SM at a time, so the chunk count minimises
+// waves x (planes + 2 halo planes) of the busiest SM.
+int u1_staged_dz(int precision, int N, int nsm)
+{
+    const int ty = precision == CL_PREC_FP64 ? U1SGeom<double>::TY : U1SGeom<float>::TY;
+    const long long tiles = (long long)(N / 32) * (N / ty);
+    long long best = -1;
+    int best_dz = N;
+    for (int nbz = 1; nbz <= N; ++nbz) {
+        const int dz = (N + nbz - 1) / nbz;
+        if ((N + dz - 1) / dz != nbz) continue;  // same chunks as a smaller count
+        const long long waves = (tiles * nbz + nsm - 1) / nsm;
+        const long long cost = waves * (dz + 2);
+        if (best < 0 || cost < best) {
+            best = cost;
+            best_dz = dz;
+        }
+    }
+    return best_dz;
+}
+
+template <typename T>
+static cudaError_t launch_u1s_t(const U1Args<T>& A, int what, cudaStream_t s)
+{
+    using G = U1SGeom<T>;
+    if (!u1_staged_ok(A.N) || A.dz < 1 || A.dz > A.N) return cudaErrorInvalidValue;
+    const int grid = u1_staged_blocks(sizeof(T) == 8 ? CL_PREC_FP64 : CL_PREC_FP32, A.N, A.dz);
+    static bool attr[2] = {false, false};
+    if (what == 0) {
+        constexpr size_t smem = u1s_smem_bytes<T, PQ_NA>();
+        if (!attr[0]) {
+            const cudaError_t e =
+                cudaFuncSetAttribute(k_u1s_plaquettes<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr[0] = true;
+        }
+        k_u1s_plaquettes<T><<<grid, G::NT, smem, s>>>(A);
+    } else {
+        constexpr size_t smem = u1s_smem_bytes<T, SG_NA>();
+        if (!attr[1]) {
+            const cudaError_t e = cudaFuncSetAttribute(k_u1s_stage<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr[1] = true;
+        }
+        k_u1s_stage<T><<<grid, G::NT, smem, s>>>(A);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_u1_staged(int precision, const void* args, int what, cudaStream_t s)
+{
+    if (precision == CL_PREC_FP64) return launch_u1s_t(*static_cast<const U1Args<double>*>(args), what, s);
+    return launch_u1s_t(*static_cast<const U1Args<float>*>(args), what, s);
+}
+
+}  // namespace clk

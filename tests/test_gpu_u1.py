@@ -170,6 +170,79 @@ def test_u1_fused_and_two_launch_forms_agree(cl):
     assert res[0][2] == 4 * 3 and res[1][2] == 4 * 3 * 2
 
 
+@pytest.mark.parametrize("integ,scheme,stages", CASES)
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-4)])
+@pytest.mark.parametrize("alpha", [0.0, 1.0])
+def test_u1_staged_parity(cl, integ, scheme, stages, prec, tol, alpha):
+    """The staged launches (CL_OPT_PASS_VARIANT 2, the default where N % 32 == 0: every
+    plane's neighbourhood in shared memory) at N = 32 and 64 against the oracle, with the
+    energies of the initial and final states."""
+    for N, n in ((32, 6), (64, 2)):
+        out, e0, e, st0, st, m, launches = run_pair(cl, N, prec, integ, scheme, n, alpha=alpha, th_amp=0.5,
+                                                    variant=2 if N == 32 else None)
+        assert rel_l2(out["phi"], st.phi[0]) < tol
+        assert rel_l2(out["pi"], st.pi[0]) < tol
+        assert rel_l2(out["th"], st.links) < tol
+        assert rel_l2(out["E"], st.efield) < tol
+        eo = O.energies(m, st)
+        e0o = O.energies(m, st0)
+        assert e["a"] == pytest.approx(st.abt[0], rel=tol)
+        assert e["adot"] == pytest.approx(st.abt[1], rel=tol)
+        for k_gpu, k_orc in [("KE", "KEM"), ("GB", "GEM"), ("rho", "rho"), ("p", "p"), ("V", "V"), ("K0", "K0"),
+                             ("G0", "G0")]:
+            assert e[k_gpu] == pytest.approx(eo[k_orc], rel=max(tol, 1e-9)), k_gpu
+            assert e0[k_gpu] == pytest.approx(e0o[k_orc], rel=max(tol, 1e-9)), k_gpu
+        assert launches == n * stages * 2
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (2, 2e-6)])
+@pytest.mark.parametrize("dz", [0, 1, 5, 31])
+def test_u1_staged_and_gather_forms_agree(cl, prec, tol, dz):
+    """Staged and gather launches on the same 32^3 state, with the library's z chunk and
+    with chunks of 1, 5 (ragged last chunk) and 31 planes (a last chunk of one plane)."""
+    res = []
+    for variant in (2, 0):
+        L = 24.0
+        m = O.make_model(32, L, nf=1, alpha=0.5, kappa=KAPPA, expansion=True, gauge=1, alphaL=ALPHAL, ws2=WS2,
+                         m2=(M2, 0.0), lam=(LAM, 0.0))
+        st = random_state(m, 11, th_amp=0.5)
+        dtype = np.float64 if prec == 0 else np.float32
+        with cl.Lattice(32, L, 1, prec, cl.CL_INT_RK3_3, gauge=cl.CL_GAUGE_U1_AXION, expansion=True, alpha=0.5,
+                        kappa=KAPPA, dt=0.01) as g:
+            g.cl_set_potential(cl.CL_POT_POLY, [M2, LAM, 0.0, 0.0, 0.0])
+            g.cl_set_gauge_coupling(ALPHAL, WS2)
+            g.cl_set_option(cl.CL_OPT_PASS_VARIANT, variant)
+            if dz:
+                g.cl_set_option(cl.CL_OPT_TILE_DZ, dz)
+            assert g.cl_get_option(cl.CL_OPT_PASS_VARIANT) == variant
+            g.cl_set_state(cl.CL_FIELD_PHI0, st.phi[0].astype(dtype))
+            g.cl_set_state(cl.CL_FIELD_PI0, st.pi[0].astype(dtype))
+            for i in range(3):
+                g.cl_set_state(cl.CL_FIELD_THETA1 + i, st.links[i].astype(dtype))
+                g.cl_set_state(cl.CL_FIELD_E1 + i, st.efield[i].astype(dtype))
+            g.cl_set_scalars(1.0, 0.3, 0.0)
+            g.cl_step(4)
+            out = {k: g.cl_get_state(f) for k, f in (("phi", cl.CL_FIELD_PHI0), ("pi", cl.CL_FIELD_PI0),
+                                                       ("E1", cl.CL_FIELD_E1), ("E3", cl.CL_FIELD_E3),
+                                                       ("th2", cl.CL_FIELD_THETA2))}
+            res.append((out, g.cl_energies()))
+    for k in res[0][0]:
+        assert rel_l2(res[0][0][k], res[1][0][k]) < tol, k
+    for k in ("rho", "KE", "GB", "a", "adot"):
+        assert res[0][1][k] == pytest.approx(res[1][1][k], rel=max(tol, 1e-12)), k
+
+
+def test_u1_variant_defaults(cl):
+    """The library picks the staged launches where N % 32 == 0 and the gather launches
+    elsewhere; variant 2 is accepted only on an axion-U(1) lattice."""
+    for N, want in ((32, 2), (24, 0)):
+        with cl.Lattice(N, 10.0, 1, 2, cl.CL_INT_RK3_3, gauge=cl.CL_GAUGE_U1_AXION, kappa=KAPPA, dt=0.01) as g:
+            assert g.cl_get_option(cl.CL_OPT_PASS_VARIANT) == want
+    with cl.Lattice(32, 10.0, 1, 2, cl.CL_INT_VV2) as g:
+        with pytest.raises(cl.CLError):
+            g.cl_set_option(cl.CL_OPT_PASS_VARIANT, 2)
+
+
 @pytest.mark.parametrize("N", [5, 7, 12])
 def test_u1_ragged_sizes(cl, N):
     out, *_, st, m, _ = run_pair(cl, N, 0, cl.CL_INT_RK4_5, O.RK4_5, 6, alpha=0.5)
