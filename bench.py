@@ -332,12 +332,23 @@ def run_u1_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_
                              "gauss_violation": e["gauss_violation"], "hubble_violation": e["hubble_violation"]}}
 
 
+def rk_tiling(g, args, cl):
+    """Apply --stages / --by / --dz to a Runge-Kutta lattice and return the tiling in effect
+    (stages -1: the direct-load stage kernel)."""
+    for opt, v in ((cl.CL_OPT_STAGES, args.stages), (cl.CL_OPT_TILE_BY, args.by), (cl.CL_OPT_TILE_DZ, args.dz)):
+        if v is not None:
+            g.cl_set_option(opt, v)
+    return {"stages": g.cl_get_option(cl.CL_OPT_STAGES), "tile_by": g.cl_get_option(cl.CL_OPT_TILE_BY),
+            "tile_dz": g.cl_get_option(cl.CL_OPT_TILE_DZ)}
+
+
 def run_rk_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src):
     """The headline two-field lattice advanced by the low-storage RK4-5 stages instead of the
     leapfrog (the non-symplectic evolver measured on the same 256^3 state)."""
     g = cl.Lattice(N, L, 2, cl.CL_PREC_FP32_KAHAN, cl.CL_INT_RK4_5, expansion=True, alpha=ALPHA, kappa=KAPPA, dt=DT,
                    stream=stream.cuda_stream)
     g.cl_set_potential(cl.CL_POT_M2_G2, [1.0, G2])
+    tiling = rk_tiling(g, args, cl)
     g.cl_init_vacuum(SEED, 1e30, AMP2, (1.0, 0.0), (0.0, 0.0))
     g.cl_step(args.warmup)
     g.cl_sync()
@@ -359,7 +370,9 @@ def run_rk_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_
                               "integrator": "rk4_5", "passes_per_step": RK_STAGES}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
-                         "kernel": "k_rk_stage<float,2,kahan,4> (mean over the 5 stages)",
+                         "kernel": ("k_rk_stage_tma<float,2,kahan,4,%d> (mean over the 5 stages)" % tiling["stages"]
+                                    if tiling["stages"] > 0 else "k_rk_stage<float,2,kahan,4> (mean over the 5 stages)"),
+                         "tiling": tiling,
                          "algorithmic_bytes_per_launch": bytes_stage},
             "gpu_launches": launches, "clocks": clocks,
             "energies_end": {"a": e["a"], "rho": e["rho"], "hubble_violation": e["hubble_violation"]}}
@@ -412,6 +425,7 @@ def run_nmc_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak
     g.cl_set_potential(cl.CL_POT_LPHI4, [1.0])
     g.cl_init_vacuum(SEED, 16 * 2 * math.pi / L, 1e-4, (1.0,), (0.0,))
     g.cl_set_nonminimal(NMC_XI)
+    tiling = rk_tiling(g, args, cl)
     g.cl_step(args.warmup)
     g.cl_sync()
     barrier(world)
@@ -433,7 +447,9 @@ def run_nmc_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak
                               "fields": 1, "integrator": "rk4_5", "passes_per_step": RK_STAGES}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
-                         "kernel": "k_nmc_ricci + k_rk_stage<float,1,kahan,4> (mean per stage)",
+                         "kernel": ("k_nmc_ricci + k_rk_stage_tma<float,1,kahan,4,%d> (mean per stage)" % tiling["stages"]
+                                    if tiling["stages"] > 0 else "k_nmc_ricci + k_rk_stage<float,1,kahan,4> (mean per stage)"),
+                         "tiling": tiling,
                          "algorithmic_bytes_per_launch": bytes_stage},
             "ricci_end": e["ricci"], "gpu_launches": launches, "clocks": clocks}
 

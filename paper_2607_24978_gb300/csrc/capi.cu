@@ -15,6 +15,7 @@
 
 #include "cl_internal.cuh"
 #include "surrogate_train.cuh"
+#include "rk_tma.cuh"
 #include "u1_staged.cuh"
 
 using namespace clk;
@@ -53,6 +54,7 @@ struct cl_lattice {
     void* kphi[2][2] = {};  // Runge-Kutta auxiliaries (RK integrators only)
     void* kpi[2][2] = {};
     int rk_BY = 1, rk_DZ = 1, rk_nby = 1, rk_nbz = 1;
+    int rk_stages = 0;              // TMA-staged Runge-Kutta kernel with this many stages (0: direct loads)
     int variant = 0;          // TMA pass kernel in use (0 ring, 1 ringless)
     bool gauge = false;       // axion + compact U(1) links (one scalar field, Runge-Kutta)
     void* th[3][2] = {};      // link angles theta_i
@@ -369,7 +371,53 @@ cl_status choose_tiles(cl_lattice* l)
         l->gw_DZ = (int)((N + nbz - 1) / nbz);
         l->gw_nbz = (N + l->gw_DZ - 1) / l->gw_DZ;
     }
-    if (is_rk(l->p.integrator)) {
+    l->rk_stages = 0;
+    if (is_rk(l->p.integrator) && l->VW * l->es == 16 && N % l->VW == 0 && l->opt_stages != -1) {
+        // TMA-staged Runge-Kutta kernel (the library's choice for 16-byte vectors): up to 448
+        // consumer threads, the tallest tile whose stage ring holds three or more stages (the
+        // deepest that fits), one block per SM over balanced persistent ranges of (tile,
+        // plane) units.  Measured at 256^3, two fields, FP32 + Kahan, RK4-5: 7 rows x 3
+        // stages 13.8 Gsite-updates/s, 5 x 4 13.5, 4 x 5 12.8; the direct-load kernel 9.7.
+        // CL_OPT_TILE_BY / CL_OPT_STAGES / CL_OPT_TILE_DZ override.
+        int by_max = 448 / TX < 1 ? 1 : 448 / TX;
+        if (by_max > N) by_max = N;
+        auto fits = [&](int by, int st) { return rk_stage_tma_smem(prec, l->nf, N, by, st) <= (size_t)kPassMaxSmem; };
+        auto most_stages = [&](int by) {  // the deepest ring (3..6) a tile of by rows allows, or 0
+            for (int st = 6; st >= 3; --st)
+                if (fits(by, st)) return st;
+            return 0;
+        };
+        int best_by = 0, best_s = 0;
+        if (l->opt_BY > 0) {  // the given rows (and stages, or the deepest ring)
+            const int by = l->opt_BY < by_max ? l->opt_BY : by_max;
+            const int want = l->opt_stages > 0 ? (l->opt_stages < 3 ? 3 : l->opt_stages) : 0;
+            const int st = want ? (fits(by, want) ? want : 0) : most_stages(by);
+            if (st) best_by = by, best_s = st;
+        } else if (l->opt_stages > 0) {  // the given stages (at least three), the tallest tile
+            const int want = l->opt_stages < 3 ? 3 : l->opt_stages;
+            for (int by = by_max; by >= 1 && !best_by; --by)
+                if (fits(by, want)) best_by = by, best_s = want;
+        } else {  // the tallest tile, with the deepest ring it allows
+            for (int by = by_max; by >= 1 && !best_by; --by)
+                if (most_stages(by)) best_by = by, best_s = most_stages(by);
+        }
+        if (best_by) {
+            l->rk_stages = best_s;
+            l->rk_BY = best_by;
+            l->rk_nby = (N + best_by - 1) / best_by;
+            if (l->opt_DZ > 0) {
+                l->rk_DZ = l->opt_DZ > N ? N : l->opt_DZ;
+                l->rk_nbz = (N + l->rk_DZ - 1) / l->rk_DZ;
+                if (l->rk_nby * l->rk_nbz > nblocks) nblocks = l->rk_nby * l->rk_nbz;
+            } else {
+                const int64_t units = (int64_t)l->rk_nby * N;
+                l->rk_DZ = -1;
+                l->rk_nbz = (int)(units < nsm ? units : nsm);  // the grid
+                if (l->rk_nbz > nblocks) nblocks = l->rk_nbz;
+            }
+        }
+    }
+    if (is_rk(l->p.integrator) && l->rk_stages == 0) {
         // Runge-Kutta stage kernel (direct loads): about 256 threads per block, two blocks per
         // SM, the y tiles cut into the same z chunks so that about one wave covers the lattice
         int rby = TX >= 256 ? 1 : 256 / TX;
@@ -517,7 +565,8 @@ cl_status run_rk_stage_t(cl_lattice* l, const PassCoef& pc, int in, int out)
         cudaError_t e = launch_nmc_ricci(l->p.precision, &A, nmc_grid(l), l->stream);
         if (e != cudaSuccess) return fail(l, CL_ECUDA, "Ricci reduction launch failed: %s", cudaGetErrorString(e));
     }
-    cudaError_t e = launch_rk_stage(l->p.precision, l->nf, &A, l->VW, l->stream);
+    cudaError_t e = l->rk_stages > 0 ? launch_rk_stage_tma(l->p.precision, l->nf, &A, l->VW, l->rk_stages, l->stream)
+                                     : launch_rk_stage(l->p.precision, l->nf, &A, l->VW, l->stream);
     if (e != cudaSuccess) return fail(l, CL_ECUDA, "Runge-Kutta stage launch failed: %s", cudaGetErrorString(e));
     return CL_OK;
 }
@@ -1352,9 +1401,13 @@ cl_status cl_get_option(cl_lattice* l, int32_t option, int64_t* value)
     const bool ens = is_ens(l);
     switch (option) {
     case CL_OPT_GRAPH: *value = l->use_graph ? 1 : 0; return CL_OK;
-    case CL_OPT_TILE_BY: *value = ens ? l->hmem[0].BY : l->BY; return CL_OK;
-    case CL_OPT_TILE_DZ: *value = ens ? l->hmem[0].DZ : (l->gauge ? l->u1_dz : l->DZ); return CL_OK;
-    case CL_OPT_STAGES: *value = ens ? l->ens_stages : l->stages; return CL_OK;
+    case CL_OPT_TILE_BY: *value = ens ? l->hmem[0].BY : (is_rk(l->p.integrator) && !l->gauge ? l->rk_BY : l->BY); return CL_OK;
+    case CL_OPT_TILE_DZ:
+        *value = ens ? l->hmem[0].DZ : (l->gauge ? l->u1_dz : (is_rk(l->p.integrator) ? l->rk_DZ : l->DZ));
+        return CL_OK;
+    case CL_OPT_STAGES:
+        *value = ens ? l->ens_stages : (is_rk(l->p.integrator) && !l->gauge ? (l->rk_stages > 0 ? l->rk_stages : -1) : l->stages);
+        return CL_OK;
     case CL_OPT_PASS_VARIANT: *value = ens ? l->ens_variant : (l->gauge ? (l->u1_fused ? 1 : (l->u1_staged ? 2 : 0)) : l->variant); return CL_OK;
     }
     return fail(l, CL_EINVAL, "unknown option %d", option);

@@ -17,13 +17,91 @@
 
 #include "cl_internal.cuh"
 #include "kernel_common.cuh"
+#include "rk_tma.cuh"
 
 namespace clk {
+
+// Block partials of the old state's energy sums v (K_0, K_1, G_0, G_1, V), then the last
+// block to arrive: volume averages, diagnostics, and the (a, a') part of the stage.
+template <typename T>
+__device__ __forceinline__ void rk_finish(const RkStageArgs<T>& A, double (&v)[kMaxQ], double a_old, bool first,
+                                          double (*s_red)[kMaxQ], int* s_last, int tid, int nthr)
+{
+    const int N = A.N;
+    block_reduce<kMaxQ>(v, s_red, tid, nthr);
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < kMaxQ; ++q) A.partials[(size_t)blockIdx.x * kMaxQ + q] = v[q];
+        __threadfence();
+        const unsigned prev = atomicAdd(&A.scal->counter, 1u);
+        *s_last = (prev + 1u == gridDim.x);
+    }
+    __syncthreads();
+    if (!*s_last) return;
+    __threadfence();
+    double w[kMaxQ];
+#pragma unroll
+    for (int q = 0; q < kMaxQ; ++q) w[q] = 0.0;
+    for (int b = tid; b < (int)gridDim.x; b += nthr)
+#pragma unroll
+        for (int q = 0; q < kMaxQ; ++q) w[q] += __ldcg(&A.partials[(size_t)b * kMaxQ + q]);
+    block_reduce<kMaxQ>(w, s_red, tid, nthr);
+    if (tid == 0) {
+        DevScal* S = A.scal;
+        const double vol = (double)N * N * N;
+        const double a = a_old, b = S->b;
+        const double a2 = a * a, a6 = a2 * a2 * a2;
+        const double K0 = w[0] / (2.0 * a6 * vol), K1 = w[1] / (2.0 * a6 * vol);
+        const double G0 = w[2] / (A.dx * A.dx * 2.0 * a2 * vol), G1 = w[3] / (A.dx * A.dx * 2.0 * a2 * vol);
+        const double Vp = w[4] / vol;
+        const double K = K0 + K1, G = G0 + G1;
+        const double rho = K + G + Vp, p = K - G / 3.0 - Vp;
+        const bool expand = (A.flags & P_EXPANSION) != 0;
+        const double a2al = pow(a, 2.0 * A.alpha);
+        const double H = b / a;
+        const double hv = H != 0.0 ? fabs(H * H - a2al * A.kappa * rho / 3.0) / (H * H) : 0.0;
+        S->diag[D_T] = S->t;
+        S->diag[D_A] = a;
+        S->diag[D_ADOT] = b;
+        S->diag[D_K0] = K0;
+        S->diag[D_K1] = K1;
+        S->diag[D_G0] = G0;
+        S->diag[D_G1] = G1;
+        S->diag[D_V] = Vp;
+        S->diag[D_KE] = 0.0;
+        S->diag[D_GB] = 0.0;
+        S->diag[D_RHO] = rho;
+        S->diag[D_P] = p;
+        S->diag[D_HV] = hv;
+        S->diag[D_GV] = 0.0;
+        if (expand) {
+            const double Fa = b;
+            // Eq. Friedmann1, or for a non-minimally coupled field Eq. piadot with R of the state
+            const double Fb = A.nmc ? a * (pow(a, 2.0 * A.alpha) * S->rbar / 6.0 - (1.0 - A.alpha) * (b / a) * (b / a))
+                                    : pow(a, 2.0 * A.alpha + 1.0) * (A.kappa / 6.0) * ((2.0 * A.alpha - 1.0) * rho - 3.0 * p);
+            const double ka = first ? A.h * Fa : A.A * S->rk[0] + A.h * Fa;
+            const double kb = first ? A.h * Fb : A.A * S->rk[1] + A.h * Fb;
+            S->rk[0] = ka;
+            S->rk[1] = kb;
+            S->a = a + A.B * ka;
+            S->b = b + A.B * kb;
+        }
+        if (A.flags & P_COUNT_STEP) {
+            S->t += A.h;
+            S->step += 1;
+        }
+        int st = 0;
+        if (!isfinite(rho) || !isfinite(p)) st |= ST_NAN;
+        if (first && A.hubble_limit > 0.0 && hv > A.hubble_limit) st |= ST_CONSTRAINT;
+        if (st) atomicOr(&S->status, st);
+        S->counter = 0u;
+    }
+}
 
 template <typename T, int NF, bool KAHAN, int VW>
 __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);  // [NF][3][BY+2][N] old field
     __shared__ double s_coef[5];
     __shared__ double s_red[32][kMaxQ];
@@ -172,105 +250,306 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
     v[2] = accG[0].value();
     v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
     v[4] = accV.value();
-    block_reduce<kMaxQ>(v, s_red, tid, nthr);
+    rk_finish(A, v, s_coef[3], first, s_red, &s_last, tid, nthr);
+}
+
+// TMA-staged form of the same stage.  One producer warp copies, plane after plane, the rows
+// a tile needs into a ring of S stage buffers with bulk asynchronous copies: the old field's
+// rows y0-1 .. y0+R (three copies: the halo rows and the R own rows) and the R own rows of
+// pi, the compensation and k_phi, k_pi (the z halo planes: the field only; the first stage:
+// no k).  Consumer warps own one x vector of one row each, keep the field of planes j-2,
+// j-1, j of their own vector in registers, and at plane j finish plane j-1: the z
+// neighbours from registers, the y neighbours and the other arrays from the stage of plane
+// j-1, the x neighbours from the adjacent lanes.  A stage is released once its plane was
+// finished (the z halos right away), so the producer stays S - 2 planes ahead; the warps
+// synchronise through the full / empty mbarriers only, every wait bounded.  The arithmetic
+// is that of k_rk_stage, operation for operation.
+template <typename T, int NF, bool KAHAN, int VW, int S>
+__global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
+{
+    constexpr int NOWN = KAHAN ? 4 : 3;  // own-row arrays per field: pi (, c), k_phi, k_pi
+    constexpr int OC = KAHAN ? 1 : -1, OKF = KAHAN ? 2 : 1, OKP = KAHAN ? 3 : 2;  // their slots
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_full[S];
+    __shared__ __align__(8) uint64_t s_empty[S];
+    __shared__ double s_coef[5];
+    __shared__ double s_red[32][kMaxQ];
+    __shared__ int s_last, s_timeout;
+
+    const int N = A.N, BY = A.BY;
+    const int TX = N / VW;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int CT = nthr - 32;  // consumer threads (whole warps)
+    const int CW = CT / 32;
+    const bool producer = tid >= CT;
+    const bool own = tid < BY * TX;
+    const int r = own ? tid / TX : BY, tx = own ? tid % TX : 0;
+    const int x0 = tx * VW;
+    const int phi_stride = (BY + 2) * N, own_stride = BY * N;
+    const int field_stride = phi_stride + NOWN * own_stride;
+    const int stage_stride = NF * field_stride;
+    T* stage = reinterpret_cast<T*>(smem_raw);
+    const bool first = (A.flags & P_FIRST_STAGE) != 0;
+    long long u0, u1;
+    block_units(N, A.nby, A.DZ, u0, u1);
+
     if (tid == 0) {
+        const double a = A.scal->a;
+        s_coef[0] = A.h * pow(a, A.alpha - 3.0);
+        s_coef[1] = A.h * pow(a, 1.0 + A.alpha) / (A.dx * A.dx);
+        s_coef[2] = A.h * pow(a, 3.0 + A.alpha);
+        s_coef[3] = a;
+        s_coef[4] = A.nmc ? A.xi * A.scal->rbar : 0.0;  // xi R of the stage's state
 #pragma unroll
-        for (int q = 0; q < kMaxQ; ++q) A.partials[(size_t)blockIdx.x * kMaxQ + q] = v[q];
-        __threadfence();
-        const unsigned prev = atomicAdd(&A.scal->counter, 1u);
-        s_last = (prev + 1u == gridDim.x);
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&s_full[k], 1);
+            mbar_init(&s_empty[k], CW);
+        }
+        mbar_fence_init();
+        s_timeout = 0;
     }
     __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    double w[kMaxQ];
-#pragma unroll
-    for (int q = 0; q < kMaxQ; ++q) w[q] = 0.0;
-    for (int b = tid; b < (int)gridDim.x; b += nthr)
-#pragma unroll
-        for (int q = 0; q < kMaxQ; ++q) w[q] += __ldcg(&A.partials[(size_t)b * kMaxQ + q]);
-    block_reduce<kMaxQ>(w, s_red, tid, nthr);
-    if (tid == 0) {
-        DevScal* S = A.scal;
-        const double vol = (double)N * N * N;
-        const double a = s_coef[3], b = S->b;
-        const double a2 = a * a, a6 = a2 * a2 * a2;
-        const double K0 = w[0] / (2.0 * a6 * vol), K1 = w[1] / (2.0 * a6 * vol);
-        const double G0 = w[2] / (A.dx * A.dx * 2.0 * a2 * vol), G1 = w[3] / (A.dx * A.dx * 2.0 * a2 * vol);
-        const double Vp = w[4] / vol;
-        const double K = K0 + K1, G = G0 + G1;
-        const double rho = K + G + Vp, p = K - G / 3.0 - Vp;
-        const bool expand = (A.flags & P_EXPANSION) != 0;
-        const double a2al = pow(a, 2.0 * A.alpha);
-        const double H = b / a;
-        const double hv = H != 0.0 ? fabs(H * H - a2al * A.kappa * rho / 3.0) / (H * H) : 0.0;
-        S->diag[D_T] = S->t;
-        S->diag[D_A] = a;
-        S->diag[D_ADOT] = b;
-        S->diag[D_K0] = K0;
-        S->diag[D_K1] = K1;
-        S->diag[D_G0] = G0;
-        S->diag[D_G1] = G1;
-        S->diag[D_V] = Vp;
-        S->diag[D_KE] = 0.0;
-        S->diag[D_GB] = 0.0;
-        S->diag[D_RHO] = rho;
-        S->diag[D_P] = p;
-        S->diag[D_HV] = hv;
-        S->diag[D_GV] = 0.0;
-        if (expand) {
-            const double Fa = b;
-            // Eq. Friedmann1, or for a non-minimally coupled field Eq. piadot with R of the state
-            const double Fb = A.nmc ? a * (pow(a, 2.0 * A.alpha) * S->rbar / 6.0 - (1.0 - A.alpha) * (b / a) * (b / a))
-                                    : pow(a, 2.0 * A.alpha + 1.0) * (A.kappa / 6.0) * ((2.0 * A.alpha - 1.0) * rho - 3.0 * p);
-            const double ka = first ? A.h * Fa : A.A * S->rk[0] + A.h * Fa;
-            const double kb = first ? A.h * Fb : A.A * S->rk[1] + A.h * Fb;
-            S->rk[0] = ka;
-            S->rk[1] = kb;
-            S->a = a + A.B * ka;
-            S->b = b + A.B * kb;
+    Acc<T> accK[NF], accG[NF], accV;
+    auto bounded = [&](uint64_t* bar, uint32_t parity) {
+        if (!mbar_wait_bounded(bar, parity, s_timeout ? 1000000ull : 2000000000ull)) s_timeout = 1;
+    };
+
+    if (producer) {
+        // ---------------------------------------------------------------- producer warp
+        const int lane = tid - CT;
+        int st = 0, issued = 0;
+        uint32_t empty_phase = 0;
+        const int nown_in = first ? (KAHAN ? 2 : 1) : NOWN;  // arrays of the own rows read this stage
+        for (long long u = u0; u < u1;) {
+            const int tile = (int)(u / N);
+            const int z0 = (int)(u - (long long)tile * N);
+            const int NZ = (int)min((long long)(N - z0), u1 - u);
+            const int y0 = tile * BY, R = min(BY, N - y0);
+            const int ylo = y0 == 0 ? N - 1 : y0 - 1;
+            const int yhi = y0 + R == N ? 0 : y0 + R;
+            u += NZ;
+            int zz = z0 == 0 ? N - 1 : z0 - 1;
+            for (int j = 0; j < NZ + 2; ++j) {
+                if (issued >= S) {
+                    bounded(&s_empty[st], (empty_phase >> st) & 1u);
+                    empty_phase ^= 1u << st;
+                }
+                const int nown = (j == 0 || j == NZ + 1) ? 0 : nown_in;  // z halos: the field only
+                const int per_field = 3 + nown;
+                if (lane == 0)
+                    mbar_arrive_expect_tx(&s_full[st], (uint32_t)(NF * (R + 2 + nown * R) * N * sizeof(T)));
+                __syncwarp();
+                if (lane < NF * per_field) {
+                    const int f = lane / per_field, part = lane - f * per_field;
+                    T* fb = stage + st * stage_stride + f * field_stride;
+                    const size_t plane = (size_t)zz * N;
+                    if (part < 3) {  // old field: halo row below, own rows, halo row above
+                        const T* src = f == 0 ? A.phi_in[0] : A.phi_in[NF - 1];
+                        const int y = part == 0 ? ylo : (part == 1 ? y0 : yhi);
+                        const int srow = part == 0 ? 0 : (part == 1 ? 1 : R + 1);
+                        const int nrows = part == 1 ? R : 1;
+                        tma_bulk_g2s(fb + srow * N, src + (plane + y) * N, (uint32_t)(nrows * N * sizeof(T)), &s_full[st]);
+                    } else {  // own rows of pi (, c), k_phi, k_pi
+                        const int k = part - 3;
+                        const T* src;
+                        if (k == 0) src = f == 0 ? A.pi_in[0] : A.pi_in[NF - 1];
+                        else if (k == OC) src = f == 0 ? A.c_in[0] : A.c_in[NF - 1];
+                        else if (k == OKF) src = f == 0 ? A.kphi_in[0] : A.kphi_in[NF - 1];
+                        else src = f == 0 ? A.kpi_in[0] : A.kpi_in[NF - 1];
+                        tma_bulk_g2s(fb + phi_stride + k * own_stride, src + (plane + y0) * N,
+                                     (uint32_t)(R * N * sizeof(T)), &s_full[st]);
+                    }
+                }
+                __syncwarp();
+                ++issued;
+                st = st + 1 == S ? 0 : st + 1;
+                zz = zz + 1 == N ? 0 : zz + 1;
+            }
         }
-        if (A.flags & P_COUNT_STEP) {
-            S->t += A.h;
-            S->step += 1;
+    } else {
+        // ---------------------------------------------------------------- consumer warps
+        const T cphi = (T)s_coef[0], cL = (T)s_coef[1], cV = (T)s_coef[2], xiR = (T)s_coef[4];
+        const T cA = (T)A.A, cB = (T)A.B;
+        const PotCoef<T> P(A.m2, A.lam, A.g2);
+        const int lane = tid & 31;
+        const bool xm_lane = own && lane > 0 && tx > 0;
+        const bool xp_lane = own && lane < 31 && tx < TX - 1;
+        const int xm_idx = x0 == 0 ? N - 1 : x0 - 1;
+        const int xp_idx = x0 + VW == N ? 0 : x0 + VW;
+        T zlo[NF][VW], zmid[NF][VW], znew[NF][VW];  // old field of planes j-2, j-1, j
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+#pragma unroll
+            for (int i = 0; i < VW; ++i) zlo[f][i] = zmid[f][i] = znew[f][i] = (T)0;
+        int st = 0, st_prev = 0;
+        uint32_t full_phase = 0;
+        auto release = [&](int s_idx) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_empty[s_idx]);
+        };
+        for (long long u = u0; u < u1;) {
+            const int tile = (int)(u / N);
+            const int z0 = (int)(u - (long long)tile * N);
+            const int NZ = (int)min((long long)(N - z0), u1 - u);
+            const int y0 = tile * BY, R = min(BY, N - y0);
+            u += NZ;
+            for (int j = 0; j < NZ + 2; ++j) {
+                bounded(&s_full[st], (full_phase >> st) & 1u);
+                full_phase ^= 1u << st;
+                const T* sb = stage + st * stage_stride;
+                if (r < R) {
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) vload_smem<T, VW>(znew[f], sb + f * field_stride + (r + 1) * N + x0);
+                }
+                if (j >= 2) {
+                    // finish plane j-1 from its stage (sp) and the registers
+                    const T* sp = stage + st_prev * stage_stride;
+                    T phc[NF][VW], lap[NF][VW];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        const T xm_s = __shfl_up_sync(0xffffffffu, zmid[f][VW - 1], 1);
+                        const T xp_s = __shfl_down_sync(0xffffffffu, zmid[f][0], 1);
+                        if (r < R) {
+                            const T* fp = sp + f * field_stride;
+                            T ym[VW], yp[VW];
+                            vload_smem<T, VW>(ym, fp + r * N + x0);
+                            vload_smem<T, VW>(yp, fp + (r + 2) * N + x0);
+                            const T xm_edge = xm_lane ? xm_s : fp[(r + 1) * N + xm_idx];
+                            const T xp_edge = xp_lane ? xp_s : fp[(r + 1) * N + xp_idx];
+                            T g = (T)0;
+#pragma unroll
+                            for (int i = 0; i < VW; ++i) {
+                                const T c = zmid[f][i];
+                                const T xm = i == 0 ? xm_edge : zmid[f][i - 1];
+                                const T xp = i == VW - 1 ? xp_edge : zmid[f][i + 1];
+                                lap[f][i] = ((xp + xm) + (yp[i] + ym[i]) + (znew[f][i] + zlo[f][i])) - (T)6 * c;
+                                const T gx = xp - c, gy = yp[i] - c, gz = znew[f][i] - c;
+                                g += gx * gx + gy * gy + gz * gz;
+                                phc[f][i] = c;
+                            }
+                            accG[f].add(g);
+                        }
+                    }
+                    if (r < R) {
+                        const size_t base = ((size_t)(z0 + j - 2) * N + (y0 + r)) * N + x0;
+                        T vsum = (T)0;
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) {
+                            const T* ob = sp + f * field_stride + phi_stride + r * N + x0;
+                            T pv[VW], kf[VW], kp[VW], cv[VW], ksum = (T)0;
+                            vload_smem<T, VW>(pv, ob);
+                            if (!first) {
+                                vload_smem<T, VW>(kf, ob + OKF * own_stride);
+                                vload_smem<T, VW>(kp, ob + OKP * own_stride);
+                            }
+                            if (KAHAN) vload_smem<T, VW>(cv, ob + (KAHAN ? OC : 0) * own_stride);
+                            T ph[VW], po[VW];
+#pragma unroll
+                            for (int i = 0; i < VW; ++i) {
+                                const T p0 = phc[0][i];
+                                const T p1 = NF > 1 ? phc[NF - 1][i] : (T)0;
+                                T dV;
+                                if (f == 0) dV = p0 * (P.m20 + P.l0 * p0 * p0 + (NF > 1 ? P.g2 * p1 * p1 : (T)0)) + xiR * p0;
+                                else dV = p1 * (P.m21 + P.l1 * p1 * p1 + P.g2 * p0 * p0);
+                                ksum += pv[i] * pv[i];
+                                const T fphi = cphi * pv[i];
+                                const T fpi = cL * lap[f][i] - cV * dV;
+                                kf[i] = first ? fphi : cA * kf[i] + fphi;
+                                kp[i] = first ? fpi : cA * kp[i] + fpi;
+                                ph[i] = phc[f][i];
+                                drift<T, KAHAN>(ph[i], cv[i], kf[i], cB);  // phi += B k_phi (compensated in FP32)
+                                po[i] = pv[i] + cB * kp[i];
+                                if (f == 0) {
+                                    T v = p0 * p0 * (P.h_m20 + P.q_l0 * p0 * p0);
+                                    if (NF > 1) v += p1 * p1 * (P.h_m21 + P.q_l1 * p1 * p1) + P.h_g2 * p0 * p0 * p1 * p1;
+                                    vsum += v;
+                                }
+                            }
+                            accK[f].add(ksum);
+                            vstore<T, VW>(A.phi_out[f] + base, ph);
+                            vstore<T, VW>(A.pi_out[f] + base, po);
+                            vstore<T, VW>(A.kphi_out[f] + base, kf);
+                            vstore<T, VW>(A.kpi_out[f] + base, kp);
+                            if (KAHAN) vstore<T, VW>(A.c_out[f] + base, cv);
+                        }
+                        accV.add(vsum);
+                    }
+                }
+                if (j >= 1) release(st_prev);  // plane j-1: finished (or the lower z halo)
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+#pragma unroll
+                    for (int i = 0; i < VW; ++i) {
+                        zlo[f][i] = zmid[f][i];
+                        zmid[f][i] = znew[f][i];
+                    }
+                st_prev = st;
+                st = st + 1 == S ? 0 : st + 1;
+            }
+            release(st_prev);  // the upper z halo of the segment is never finished
         }
-        int st = 0;
-        if (!isfinite(rho) || !isfinite(p)) st |= ST_NAN;
-        if (first && A.hubble_limit > 0.0 && hv > A.hubble_limit) st |= ST_CONSTRAINT;
-        if (st) atomicOr(&S->status, st);
-        S->counter = 0u;
     }
+    __syncthreads();  // producer and consumers meet; no copy is in flight past this point
+    if (tid == 0 && s_timeout) atomicOr(&A.scal->status, ST_TIMEOUT);
+    double v[kMaxQ];
+    v[0] = accK[0].value();
+    v[1] = NF > 1 ? accK[NF - 1].value() : 0.0;
+    v[2] = accG[0].value();
+    v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
+    v[4] = accV.value();
+    rk_finish(A, v, s_coef[3], first, s_red, &s_last, tid, nthr);
 }
 
 // Background Ricci scalar of a non-minimally coupled field (section "Scalar fields
 // non-minimally coupled to gravity", Eq. eomR in program units):
 //   R = kappa F [(1 - 6 xi) (2 G - 2 K) + 4 <V> - 6 xi <phi V'>],  F = 1 / (1 + (6 xi - 1) xi kappa <phi^2>),
 // with K = <pi^2> / (2 a^6) and G = <(grad+ phi)^2> / (2 a^2) of the state (field 0).  Per-thread
-// compensated sums, FP64 across threads and blocks in a fixed order; the last block writes R.
-template <typename T>
+// compensated sums of per-vector partial sums, FP64 across threads and blocks in a fixed order;
+// the last block writes R.
+template <typename T, int VW>
 __global__ void __launch_bounds__(256) k_nmc_ricci(const RkStageArgs<T> A)
 {
     __shared__ double s_red[32][kMaxQ];
     __shared__ int s_last;
-    const int N = A.N;
+    const int N = A.N, NV = N / VW;
     const T m2 = (T)A.m2[0], lam = (T)A.lam[0];
+    const T* __restrict__ phi = A.phi_in[0];
+    const T* __restrict__ pi = A.pi_in[0];
     Acc<T> sK, sG, sV, sPV, sP2;
-    // whole x rows per block: the +y and +z neighbour rows load coalesced, one division per row
-    for (int row = blockIdx.x; row < N * N; row += gridDim.x) {
-        const int z = row / N, y = row - z * N;
-        const size_t rb = (size_t)row * N;
-        const size_t ry = ((size_t)z * N + (y + 1 == N ? 0 : y + 1)) * N;
-        const size_t rz = ((size_t)(z + 1 == N ? 0 : z + 1) * N + y) * N;
-        for (int x = threadIdx.x; x < N; x += blockDim.x) {
-            const T ph = A.phi_in[0][rb + x], pv = A.pi_in[0][rb + x];
-            const T px = A.phi_in[0][rb + (x + 1 == N ? 0 : x + 1)];
-            const T py = A.phi_in[0][ry + x];
-            const T pz = A.phi_in[0][rz + x];
-            sK.add(pv * pv);
-            sG.add((px - ph) * (px - ph) + (py - ph) * (py - ph) + (pz - ph) * (pz - ph));
-            sV.add(ph * ph * ((T)0.5 * m2 + (T)0.25 * lam * ph * ph));
-            sPV.add(ph * ph * (m2 + lam * ph * ph));
-            sP2.add(ph * ph);
+    // Whole x rows of VW-vectors: tpr threads per row, rpi rows per block sweep; the +y and +z
+    // neighbour rows load coalesced, one division per row.
+    const int tpr = NV < (int)blockDim.x ? NV : (int)blockDim.x, rpi = (int)blockDim.x / tpr;
+    const int rr = (int)threadIdx.x / tpr, tx = (int)threadIdx.x - rr * tpr;
+    if (rr < rpi) {
+        for (int row = blockIdx.x * rpi + rr; row < N * N; row += gridDim.x * rpi) {
+            const int z = row / N, y = row - z * N;
+            const size_t rb = (size_t)row * N;
+            const size_t ry = ((size_t)z * N + (y + 1 == N ? 0 : y + 1)) * N;
+            const size_t rz = ((size_t)(z + 1 == N ? 0 : z + 1) * N + y) * N;
+            for (int xv = tx; xv < NV; xv += tpr) {
+                const int x0 = xv * VW;
+                T ph[VW], pv[VW], py[VW], pz[VW];
+                vload<T, VW>(ph, phi + rb + x0);
+                vload<T, VW>(pv, pi + rb + x0);
+                vload<T, VW>(py, phi + ry + x0);
+                vload<T, VW>(pz, phi + rz + x0);
+                const T pxe = __ldg(phi + rb + (x0 + VW == N ? 0 : x0 + VW));  // x neighbour of the last element
+                T k = (T)0, gsum = (T)0, v = (T)0, pvd = (T)0, p2 = (T)0;
+#pragma unroll
+                for (int i = 0; i < VW; ++i) {
+                    const T c = ph[i], px = i + 1 < VW ? ph[(i + 1) % VW] : pxe;
+                    k += pv[i] * pv[i];
+                    gsum += (px - c) * (px - c) + (py[i] - c) * (py[i] - c) + (pz[i] - c) * (pz[i] - c);
+                    v += c * c * ((T)0.5 * m2 + (T)0.25 * lam * c * c);
+                    pvd += c * c * (m2 + lam * c * c);
+                    p2 += c * c;
+                }
+                sK.add(k);
+                sG.add(gsum);
+                sV.add(v);
+                sPV.add(pvd);
+                sP2.add(p2);
+            }
         }
     }
     double v[kMaxQ] = {sK.value(), sG.value(), sV.value(), sPV.value(), sP2.value()};
@@ -305,7 +584,9 @@ __global__ void __launch_bounds__(256) k_nmc_ricci(const RkStageArgs<T> A)
 template <typename T>
 static cudaError_t launch_nmc_ricci_t(const RkStageArgs<T>& A, int grid, cudaStream_t s)
 {
-    k_nmc_ricci<T><<<grid, 256, 0, s>>>(A);
+    constexpr int VW = 16 / sizeof(T);  // 16-byte vectors where the rows allow them
+    if (A.N % VW == 0) k_nmc_ricci<T, VW><<<grid, 256, 0, s>>>(A);
+    else k_nmc_ricci<T, 1><<<grid, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -355,6 +636,60 @@ cudaError_t launch_rk_stage(int precision, int nf, const void* args, int vw, cud
     if (precision == CL_PREC_FP32_KAHAN)
         return nf == 1 ? rk_vw<float, 1, true>(A, vw, s) : rk_vw<float, 2, true>(A, vw, s);
     return nf == 1 ? rk_vw<float, 1, false>(A, vw, s) : rk_vw<float, 2, false>(A, vw, s);
+}
+
+size_t rk_stage_tma_smem(int precision, int nf, int N, int BY, int stages)
+{
+    const size_t es = precision == CL_PREC_FP64 ? 8 : 4;
+    const int nown = precision == CL_PREC_FP32_KAHAN ? 4 : 3;
+    return (size_t)stages * nf * ((size_t)(BY + 2) + (size_t)nown * BY) * N * es;
+}
+
+template <typename T, int NF, bool KAHAN, int VW>
+static cudaError_t launch_rk_tma(const RkStageArgs<T>& A, int stages, cudaStream_t s)
+{
+    if constexpr (VW * sizeof(T) == 16) {
+        const int prec = sizeof(T) == 8 ? CL_PREC_FP64 : (KAHAN ? CL_PREC_FP32_KAHAN : CL_PREC_FP32);
+        const int TX = A.N / VW;
+        const dim3 block(((TX * A.BY + 31) / 32) * 32 + 32);  // consumers + the producer warp
+        const dim3 grid(A.DZ > 0 ? A.nby * A.nbz : A.nbz);
+        const size_t smem = rk_stage_tma_smem(prec, NF, A.N, A.BY, stages);
+        if (block.x > 480 || smem > (size_t)kPassMaxSmem || A.N % VW != 0) return cudaErrorInvalidValue;
+        static bool attr[7] = {false, false, false, false, false, false, false};
+        cudaError_t e = cudaSuccess;
+#define CL_RKT_CASE(SS)                                                                                         \
+    case SS:                                                                                                    \
+        if (!attr[SS]) {                                                                                        \
+            e = cudaFuncSetAttribute(k_rk_stage_tma<T, NF, KAHAN, VW, SS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                     kPassMaxSmem);                                                             \
+            if (e != cudaSuccess) return e;                                                                     \
+            attr[SS] = true;                                                                                    \
+        }                                                                                                       \
+        k_rk_stage_tma<T, NF, KAHAN, VW, SS><<<grid, block, smem, s>>>(A);                                       \
+        return cudaGetLastError();
+        switch (stages) {
+            CL_RKT_CASE(3)
+            CL_RKT_CASE(4)
+            CL_RKT_CASE(5)
+            CL_RKT_CASE(6)
+        }
+#undef CL_RKT_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rk_stage_tma(int precision, int nf, const void* args, int vw, int stages, cudaStream_t s)
+{
+    if (precision == CL_PREC_FP64) {
+        const auto& A = *static_cast<const RkStageArgs<double>*>(args);
+        if (vw != 2) return cudaErrorInvalidValue;
+        return nf == 1 ? launch_rk_tma<double, 1, false, 2>(A, stages, s) : launch_rk_tma<double, 2, false, 2>(A, stages, s);
+    }
+    const auto& A = *static_cast<const RkStageArgs<float>*>(args);
+    if (vw != 4) return cudaErrorInvalidValue;
+    if (precision == CL_PREC_FP32_KAHAN)
+        return nf == 1 ? launch_rk_tma<float, 1, true, 4>(A, stages, s) : launch_rk_tma<float, 2, true, 4>(A, stages, s);
+    return nf == 1 ? launch_rk_tma<float, 1, false, 4>(A, stages, s) : launch_rk_tma<float, 2, false, 4>(A, stages, s);
 }
 
 }  // namespace clk

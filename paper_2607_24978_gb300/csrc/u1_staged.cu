@@ -23,7 +23,7 @@
 //    site, and release a slot once they have read it for the last time (its "empty" barrier
 //    counts one arrival per consumer warp), so no warp waits for another one's work.
 // Arrays read only at the site itself (theta and the Runge-Kutta auxiliaries) are loaded by
-// the consumers straight from global memory.  Every wait is bounded and reports through the
+// the consumers straight from global memory, one plane ahead.  Every wait is bounded and reports through the
 // status word.  Needs N % 32 == 0; other sizes use the gather kernels.
 #include <math.h>
 
@@ -365,12 +365,27 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
         const T inv_dx3 = (T)(1.0 / (A.dx * A.dx * A.dx)), inv4dx = (T)(0.25 / A.dx);
         const T inv4dx2 = (T)(0.25 / (A.dx * A.dx));
         const T h = (T)A.h, cA = (T)A.A, cB = (T)A.B;
+        // site-only arrays (theta, the RK auxiliaries), loaded one plane ahead
+        T thc[3] = {}, kc[8] = {};
+        auto load_site = [&](uint32_t m) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) thc[i] = A.th_in[i][m];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) kc[q] = first ? (T)0 : A.k_in[q][m];
+        };
+        if (update) load_site((t.z0 * N + t.y0 + warp) * N + t.x0 + lane);
         ring.acquire(0);
         ring.acquire(1);
         for (int j = 0; j < (int)t.nz; ++j) {
             ring.acquire(j + 2);
             const U1SNb<T> S = ring.nb(j, lane, warp);
             const uint32_t n = ((t.z0 + j) * N + t.y0 + warp) * N + t.x0 + lane;
+            T thv[3], kv[8];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) thv[i] = thc[i];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) kv[q] = kc[q];
+            if (update && j + 1 < (int)t.nz) load_site(n + N * N);
 
             // scalar sector
             const T ph = S(SG_PHI, 0, 0, 0), pv = S(SG_PI, 0, 0, 0);
@@ -414,10 +429,10 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
                 ring.release(j, lane);
                 // 2N Runge-Kutta update of the eight degrees of freedom of this site
                 const T F[8] = {F_phi, F_pi, dx * Ecur[0], dx * Ecur[1], dx * Ecur[2], F_E[0], F_E[1], F_E[2]};
-                const T y[8] = {ph, pv, A.th_in[0][n], A.th_in[1][n], A.th_in[2][n], Ecur[0], Ecur[1], Ecur[2]};
+                const T y[8] = {ph, pv, thv[0], thv[1], thv[2], Ecur[0], Ecur[1], Ecur[2]};
                 T kq[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) kq[q] = first ? h * F[q] : cA * A.k_in[q][n] + h * F[q];
+                for (int q = 0; q < 8; ++q) kq[q] = first ? h * F[q] : cA * kv[q] + h * F[q];
                 T* out[8] = {A.phi_out, A.pi_out, A.th_out[0], A.th_out[1], A.th_out[2], A.E_out[0], A.E_out[1],
                              A.E_out[2]};
 #pragma unroll

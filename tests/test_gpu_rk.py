@@ -27,7 +27,8 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def run_pair(cl, N, nf, prec, integ, scheme, nsteps, dt=0.01, graph=1, seed=31, expansion=True):
+def run_pair(cl, N, nf, prec, integ, scheme, nsteps, dt=0.01, graph=1, seed=31, expansion=True, opts=(),
+             effective=None):
     L = 0.8 * N
     pot = [0.6, 1.0, 0.3, 0.0, 2.5 if nf == 2 else 0.0]
     if nf == 1:
@@ -42,6 +43,10 @@ def run_pair(cl, N, nf, prec, integ, scheme, nsteps, dt=0.01, graph=1, seed=31, 
     with cl.Lattice(N, L, nf, prec, integ, expansion=expansion, alpha=0.5, kappa=0.4, dt=dt) as g:
         g.cl_set_potential(cl.CL_POT_POLY, pot)
         g.cl_set_option(cl.CL_OPT_GRAPH, graph)
+        for opt, val in opts:
+            g.cl_set_option(opt, val)
+        if effective is not None:
+            effective.update({k: g.cl_get_option(k) for k in (cl.CL_OPT_STAGES, cl.CL_OPT_TILE_BY, cl.CL_OPT_TILE_DZ)})
         for f in range(nf):
             g.cl_set_state(cl.CL_FIELD_PHI0 + f, st.phi[f].astype(dtype))
             g.cl_set_state(cl.CL_FIELD_PI0 + f, st.pi[f].astype(dtype))
@@ -67,6 +72,44 @@ def test_rk_parity(cl, integ, scheme, stages, prec, tol):
     assert e["rho"] == pytest.approx(eo["rho"], rel=max(tol, 1e-9))
     assert e["step"] == 30
     assert launches == 30 * stages  # no opening pass for Runge-Kutta
+
+
+@pytest.mark.parametrize("N,nf", [(32, 1), (32, 2), (48, 2)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 2e-6), (2, 2e-6)])
+def test_rk_tma_matches_direct_kernel(cl, N, nf, prec, tol):
+    """The TMA-staged stage kernel (the default for 16-byte vectors) and the direct-load
+    kernel (CL_OPT_STAGES -1) on the same state: same arithmetic per site, so the fields
+    agree to the rounding of a and a' (reduction order)."""
+    eff_t, eff_d = {}, {}
+    t = run_pair(cl, N, nf, prec, cl.CL_INT_RK4_5, O.RK4_5, 6, effective=eff_t)
+    d = run_pair(cl, N, nf, prec, cl.CL_INT_RK4_5, O.RK4_5, 6, opts=((cl.CL_OPT_STAGES, -1),), effective=eff_d)
+    assert eff_t[cl.CL_OPT_STAGES] >= 3 and eff_d[cl.CL_OPT_STAGES] == -1
+    assert rel_l2(t[0], d[0]) < tol
+    assert rel_l2(t[1], d[1]) < tol
+    assert t[2]["rho"] == pytest.approx(d[2]["rho"], rel=max(tol, 1e-12))
+    assert t[2]["a"] == pytest.approx(d[2]["a"], rel=max(tol, 1e-13))
+
+
+@pytest.mark.parametrize("by,stages,dz", [(1, 3, 0), (5, 4, 0), (7, 0, 0), (3, 6, 5), (0, 3, 31), (32, 0, 0)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-4)])
+def test_rk_tma_tilings(cl, by, stages, dz, prec, tol):
+    """TMA-staged stages against the oracle at 32^3 over tilings: one-row tiles, a ragged last
+    tile (5 and 7 rows), the whole box in one tile, 3 to 6 stages, persistent ranges and
+    fixed z chunks (5 planes; 31, leaving a chunk of one plane)."""
+    opts = [(cl.CL_OPT_TILE_BY, by)] if by else []
+    opts += [(cl.CL_OPT_STAGES, stages)] if stages else []
+    opts += [(cl.CL_OPT_TILE_DZ, dz)] if dz else []
+    eff = {}
+    gphi, gpi, e, st, eo, launches = run_pair(cl, 32, 2, prec, cl.CL_INT_RK4_5, O.RK4_5, 4, opts=tuple(opts),
+                                              effective=eff)
+    assert eff[cl.CL_OPT_STAGES] >= 3
+    if by:
+        assert eff[cl.CL_OPT_TILE_BY] == min(by, 448 // (32 // (4 if prec else 2)))
+    assert rel_l2(gphi, st.phi) < tol
+    assert rel_l2(gpi, st.pi) < tol
+    assert e["a"] == pytest.approx(st.abt[0], rel=tol)
+    assert e["rho"] == pytest.approx(eo["rho"], rel=max(tol, 1e-9))
+    assert launches == 4 * 5
 
 
 @pytest.mark.parametrize("N", [7, 10, 24])
