@@ -120,6 +120,7 @@ cl_status conv_forward(cl_surrogate* s, int l, const void* in, int in_bf16, int 
         A.in_act = in_act;
         A.out_act = out_act;
         A.out_pre = (__nv_bfloat16*)out_pre;
+        conv_tc_encode_input(A, tc_width(s->cin[l]));
         ++s->launches;
         return check(launch_conv_tc(tc_width(s->cin[l]), tc_width(s->cout[l]), A, tc_grid(s, A.DZ), s->stream));
     }
@@ -427,6 +428,7 @@ cl_status cl_surrogate_backward(cl_surrogate* s, const float* g, float* dx, int3
             A.status = s->status;
             A.N = s->p.N;
             A.DZ = kTcDZ < s->p.N ? kTcDZ : s->p.N;
+            conv_tc_encode_input(A, tc_width(s->cout[l]));
             ++s->launches;
             return check(launch_conv_tc(tc_width(s->cout[l]), tc_width(s->cin[l]), A, tc_grid(s, A.DZ), s->stream));
         }

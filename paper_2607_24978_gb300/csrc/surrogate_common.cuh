@@ -5,6 +5,7 @@
 // the consumer of u applies the activation (ReLU or the tanh form of GELU) as it loads.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -69,6 +70,8 @@ __device__ __forceinline__ uint4 act_bf16x8(int act, const uint4 v)
 //   out = act_out(conv(act_in(in)) + bias) (+ resid)   (forward)
 //   out = conv(in) * act'(gate)                        (data gradient, adjoint weights)
 struct ConvTCArgs {
+    CUtensorMap in_map;         // when in_tma: BF16 `in` viewed as (8 channels, x, y, channel group, z), so that
+    int in_tma;                 //   one box lands a staged plane in the [group][y][x] layout of the MMA operand
     const void* in;             // BF16 [N^3][CI], or FP32 [N^3][in_c] when in_f32 (padded with zeros)
     int in_f32, in_c;
     const __nv_bfloat16* wfmt;  // weights in the tensor-core layout [27][CI/8][CO/8][8][8]
@@ -89,6 +92,9 @@ struct ConvTCArgs {
 };
 size_t conv_tc_smem(int CI, int CO);
 cudaError_t launch_conv_tc(int CI, int CO, const ConvTCArgs& A, int grid, cudaStream_t s);
+// Encode A.in_map for a BF16 input of CI channels on an N^3 lattice (sets A.in_tma; leaves it
+// 0 when the driver's encoder is unavailable or refuses the view).
+void conv_tc_encode_input(ConvTCArgs& A, int CI);
 
 // CUDA-core convolution for the thin layers (and the FP32 reference mode): each thread
 // computes all cout outputs of one site.

@@ -20,9 +20,12 @@
 //    accumulators once the three input planes are staged and the accumulator was read
 //    back, and commits them to the accumulator's "done" barrier and to the "free" barrier
 //    of every ring slot whose plane they read last;
-//  * warps 1-3 copy input planes into free slots with cp.async (two planes in flight),
-//    apply the input activation in place once a plane landed, and arrive on its "full"
-//    barrier;
+//  * warps 1-3 stage input planes into free slots, two planes in flight: a BF16 input with
+//    one 5-D tensor copy per plane (the view (8 channels, x, y, channel group, z) lands the
+//    box directly in the [group][y][x] layout; zeros outside the lattice, after which the
+//    periodic halo entries of boundary tiles are patched with plain loads), the thin FP32
+//    input with converting loads; they apply the input activation in place once a plane
+//    landed, and arrive on its "full" barrier;
 //  * warps 4-7 (one per TMEM lane quarter) read an accumulator back (tcgen05.ld), release
 //    it, and finish the plane (bias / residual or activation derivative) into global memory.
 // Every barrier is waited for once per phase in order, so no waiter can miss a phase.  All
@@ -34,6 +37,8 @@
 #include "kernel_common.cuh"
 #include "surrogate_common.cuh"
 #include "tcgen05_ops.cuh"
+
+#include <cudaTypedefs.h>
 
 namespace clk {
 
@@ -53,7 +58,7 @@ struct ConvTCShape {
 };
 
 template <int CI, int CO>
-__global__ void __launch_bounds__(256, 1) k_conv_tc(const ConvTCArgs A)
+__global__ void __launch_bounds__(256, 1) k_conv_tc(const __grid_constant__ ConvTCArgs A)
 {
     using S = ConvTCShape<CI, CO>;
     constexpr int KG = S::KG, KC = S::KC, NG = S::NG, HX = S::HX, HY = S::HY, PLANE = S::PLANE, NSLOT = S::NSLOT;
@@ -64,6 +69,7 @@ __global__ void __launch_bounds__(256, 1) k_conv_tc(const ConvTCArgs A)
     uint4* sA = smem;                  // [NSLOT][KG][HY][HX]
     uint4* sB = smem + NSLOT * PLANE;  // [9 (oy, ox)][KG][3 (oz)][NG][8]
     __shared__ __align__(8) uint64_t s_full[NSLOT];   // plane staged in the slot (96 arrivals)
+    __shared__ __align__(8) uint64_t s_tma[NSLOT];    // tensor copy of the plane landed (bytes)
     __shared__ __align__(8) uint64_t s_freeb[NSLOT];  // slot's plane read by its last MMA (commit)
     __shared__ __align__(8) uint64_t s_done[S::NACC];     // accumulator complete (commit)
     __shared__ __align__(8) uint64_t s_accfree[S::NACC];  // accumulator read back (4 epilogue warps)
@@ -81,6 +87,7 @@ __global__ void __launch_bounds__(256, 1) k_conv_tc(const ConvTCArgs A)
         for (int k = 0; k < NSLOT; ++k) {
             mbar_init(&s_full[k], NSTAGE);
             mbar_init(&s_freeb[k], 1);
+            mbar_init(&s_tma[k], 1);
         }
         for (int k = 0; k < S::NACC; ++k) {
             mbar_init(&s_done[k], 1);
@@ -183,13 +190,43 @@ __global__ void __launch_bounds__(256, 1) k_conv_tc(const ConvTCArgs A)
     } else if (warp < 4) {
         // ------------------------------------------------------------ staging warps
         const int st = tid - 32;
-        uint32_t free_ph = 0;
+        uint32_t free_ph = 0, tma_ph = 0;
         uint32_t seq = 0;
-        int pend_slot = -1;  // slot of the plane whose copies are still landing
-        // this thread's entries of one plane: e = st, st + 96, ...
-        auto land = [&](int slot) {  // the plane in `slot` has landed: activation, then publish
+        int pend_slot = -1, pend_x0 = 0, pend_y0 = 0, pend_z = 0;  // the plane whose copies are still landing
+        const bool tma = A.in_tma && !A.in_f32;
+        // The plane in `slot` (tile x0, y0, plane z) has landed: periodic halo entries the
+        // tensor copy filled with zeros, the input activation, then publish.
+        auto land = [&](int slot, int x0, int y0, int z) {
+            uint4* dst = sA + slot * PLANE;
+            if (tma) {
+                wait(&s_tma[slot], tma_ph, slot);
+                const int lx = x0 == 0, rx = x0 + kSgTileX == N, ly = y0 == 0, ry = y0 + kSgTileY == N;
+                const int ncol = lx + rx, nrow = ly + ry;
+                const int nent = (ncol * HY + nrow * HX) * KG;
+                const __nv_bfloat16* in = reinterpret_cast<const __nv_bfloat16*>(A.in);
+                for (int e = st; e < nent; e += NSTAGE) {
+                    int hx, hy, kg;
+                    if (e < ncol * HY * KG) {  // a halo column, every row
+                        const int c = e / (HY * KG), rem = e - c * (HY * KG);
+                        hx = (c == 0 && lx) ? 0 : HX - 1;
+                        hy = rem / KG;
+                        kg = rem - hy * KG;
+                    } else {  // a halo row, every column
+                        const int e2 = e - ncol * HY * KG;
+                        const int c = e2 / (HX * KG), rem = e2 - c * (HX * KG);
+                        hy = (c == 0 && ly) ? 0 : HY - 1;
+                        hx = rem / KG;
+                        kg = rem - hx * KG;
+                    }
+                    int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+                    gx = gx < 0 ? gx + N : (gx >= N ? gx - N : gx);
+                    gy = gy < 0 ? gy + N : (gy >= N ? gy - N : gy);
+                    const size_t site = ((size_t)z * N + gy) * N + gx;
+                    dst[(kg * HY + hy) * HX + hx] = __ldg(reinterpret_cast<const uint4*>(in + site * CI + kg * 8));
+                }
+            }
             if (!A.in_f32 && A.in_act) {
-                uint4* dst = sA + slot * PLANE;
+                if (tma) named_barrier_sync(1, NSTAGE);  // every patch is in place
                 for (int e = st; e < PLANE; e += NSTAGE) {
                     const int kg = e % KG, s2 = e / KG;
                     uint4* d = dst + (kg * HY + s2 / HX) * HX + s2 % HX;
@@ -203,7 +240,8 @@ __global__ void __launch_bounds__(256, 1) k_conv_tc(const ConvTCArgs A)
         for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
             int x0, y0, z0, nz;
             unit_geom(unit, x0, y0, z0, nz);
-            // this thread's entries of a plane: shared-memory entry and site within the plane
+            // this thread's entries of a plane (copies without the tensor map): shared-memory
+            // entry and site within the plane
             int soff[EMAX], goff[EMAX];
 #pragma unroll
             for (int q = 0; q < EMAX; ++q) {
@@ -220,37 +258,53 @@ __global__ void __launch_bounds__(256, 1) k_conv_tc(const ConvTCArgs A)
                 const int slot = (int)(seq % NSLOT);
                 if (seq >= NSLOT) wait(&s_freeb[slot], free_ph, slot);
                 const int p = z0 - 1 + i;
-                const size_t zbase = (size_t)(((p % N) + N) % N) * N * N;
+                const int pz = ((p % N) + N) % N;
+                const size_t zbase = (size_t)pz * N * N;
                 uint4* dst = sA + slot * PLANE;
-#pragma unroll
-                for (int q = 0; q < EMAX; ++q) {
-                    const int e = st + q * NSTAGE;
-                    if (e >= PLANE) break;
-                    const int kg = e % KG;
-                    const size_t site = zbase + goff[q];
-                    if (!A.in_f32) {
-                        cp_async16(dst + soff[q], reinterpret_cast<const __nv_bfloat16*>(A.in) + site * CI + kg * 8);
-                    } else {  // thin FP32 input: convert and zero-pad to CI channels
-                        float f[8];
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            const int ch = kg * 8 + c;
-                            f[c] = ch < A.in_c ? __ldg(reinterpret_cast<const float*>(A.in) + site * A.in_c + ch) : 0.f;
-                        }
-                        dst[soff[q]] = pack_bf16x8(f);
+                if (tma) {
+                    if (st == 0) {  // one tensor copy: the plane with its halo (zeros outside the box)
+                        mbar_arrive_expect_tx(&s_tma[slot], (uint32_t)(PLANE * 16));
+                        asm volatile(
+                            "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                            " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+                            "l"(reinterpret_cast<uint64_t>(&A.in_map)), "r"(0), "r"(x0 - 1), "r"(y0 - 1), "r"(0), "r"(pz),
+                            "r"(smem_u32(&s_tma[slot]))
+                            : "memory");
                     }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < EMAX; ++q) {
+                        const int e = st + q * NSTAGE;
+                        if (e >= PLANE) break;
+                        const int kg = e % KG;
+                        const size_t site = zbase + goff[q];
+                        if (!A.in_f32) {
+                            cp_async16(dst + soff[q], reinterpret_cast<const __nv_bfloat16*>(A.in) + site * CI + kg * 8);
+                        } else {  // thin FP32 input: convert and zero-pad to CI channels
+                            float f[8];
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                const int ch = kg * 8 + c;
+                                f[c] = ch < A.in_c ? __ldg(reinterpret_cast<const float*>(A.in) + site * A.in_c + ch) : 0.f;
+                            }
+                            dst[soff[q]] = pack_bf16x8(f);
+                        }
+                    }
+                    cp_async_commit();
                 }
-                cp_async_commit();
-                if (pend_slot >= 0) {  // the previous plane's copies: landed once one group is left
-                    cp_async_wait1();
-                    land(pend_slot);
+                if (pend_slot >= 0) {  // the previous plane: landed once one group is left
+                    if (!tma) cp_async_wait1();
+                    land(pend_slot, pend_x0, pend_y0, pend_z);
                 }
                 pend_slot = slot;
+                pend_x0 = x0;
+                pend_y0 = y0;
+                pend_z = pz;
             }
         }
         if (pend_slot >= 0) {
-            cp_async_wait0();
-            land(pend_slot);
+            if (!tma) cp_async_wait0();
+            land(pend_slot, pend_x0, pend_y0, pend_z);
         }
     } else {
         // ------------------------------------------------------------ epilogue warps
@@ -328,6 +382,32 @@ static cudaError_t launch_conv_tc_t(const ConvTCArgs& A, int grid, cudaStream_t 
     }
     k_conv_tc<CI, CO><<<grid, 256, ConvTCShape<CI, CO>::SMEM, s>>>(A);
     return cudaGetLastError();
+}
+
+void conv_tc_encode_input(ConvTCArgs& A, int CI)
+{
+    A.in_tma = 0;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    if (!encode || A.in_f32 || !A.in || ((uintptr_t)A.in & 15u)) return;
+    const cuuint64_t N = (cuuint64_t)A.N, es = 2;
+    // dimensions: 8 channels (contiguous), x, y, channel group, z; strides of dims 1..4 in bytes
+    const cuuint64_t dims[5] = {8, N, N, (cuuint64_t)(CI / 8), N};
+    const cuuint64_t strides[4] = {CI * es, N * CI * es, 8 * es, N * N * CI * es};
+    const cuuint32_t box[5] = {8, (cuuint32_t)(kSgTileX + 2), (cuuint32_t)(kSgTileY + 2), (cuuint32_t)(CI / 8), 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    if (encode(&A.in_map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(A.in), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+        A.in_tma = 1;
 }
 
 #define CL_TC_SHAPES(X) X(16, 16) X(32, 32) X(48, 48) X(16, 32) X(16, 48) X(32, 16) X(48, 16)
