@@ -516,39 +516,51 @@ __global__ void __launch_bounds__(256) k_nmc_ricci(const RkStageArgs<T> A)
     const T* __restrict__ phi = A.phi_in[0];
     const T* __restrict__ pi = A.pi_in[0];
     Acc<T> sK, sG, sV, sPV, sP2;
-    // Whole x rows of VW-vectors: tpr threads per row, rpi rows per block sweep; the +y and +z
-    // neighbour rows load coalesced, one division per row.
-    const int tpr = NV < (int)blockDim.x ? NV : (int)blockDim.x, rpi = (int)blockDim.x / tpr;
+    // Whole x rows of VW-vectors: tpr threads per row, two vectors each (both loaded before
+    // either is summed), rpi rows per block sweep; the +y and +z neighbour rows load
+    // coalesced, one division per row.
+    int tpr = (NV + 1) / 2;
+    tpr = tpr < (int)blockDim.x ? tpr : (int)blockDim.x;
+    const int rpi = (int)blockDim.x / tpr;
     const int rr = (int)threadIdx.x / tpr, tx = (int)threadIdx.x - rr * tpr;
+    struct Vec { T ph[VW], pv[VW], py[VW], pz[VW], pxe; };
+    auto load = [&](Vec& q, size_t rb, size_t ry, size_t rz, int x0) {
+        vload<T, VW>(q.ph, phi + rb + x0);
+        vload<T, VW>(q.pv, pi + rb + x0);
+        vload<T, VW>(q.py, phi + ry + x0);
+        vload<T, VW>(q.pz, phi + rz + x0);
+        q.pxe = __ldg(phi + rb + (x0 + VW == N ? 0 : x0 + VW));  // x neighbour of the last element
+    };
+    auto sum = [&](const Vec& q) {
+        T k = (T)0, gsum = (T)0, v = (T)0, pvd = (T)0, p2 = (T)0;
+#pragma unroll
+        for (int i = 0; i < VW; ++i) {
+            const T c = q.ph[i], px = i + 1 < VW ? q.ph[(i + 1) % VW] : q.pxe;
+            k += q.pv[i] * q.pv[i];
+            gsum += (px - c) * (px - c) + (q.py[i] - c) * (q.py[i] - c) + (q.pz[i] - c) * (q.pz[i] - c);
+            v += c * c * ((T)0.5 * m2 + (T)0.25 * lam * c * c);
+            pvd += c * c * (m2 + lam * c * c);
+            p2 += c * c;
+        }
+        sK.add(k);
+        sG.add(gsum);
+        sV.add(v);
+        sPV.add(pvd);
+        sP2.add(p2);
+    };
     if (rr < rpi) {
         for (int row = blockIdx.x * rpi + rr; row < N * N; row += gridDim.x * rpi) {
             const int z = row / N, y = row - z * N;
             const size_t rb = (size_t)row * N;
             const size_t ry = ((size_t)z * N + (y + 1 == N ? 0 : y + 1)) * N;
             const size_t rz = ((size_t)(z + 1 == N ? 0 : z + 1) * N + y) * N;
-            for (int xv = tx; xv < NV; xv += tpr) {
-                const int x0 = xv * VW;
-                T ph[VW], pv[VW], py[VW], pz[VW];
-                vload<T, VW>(ph, phi + rb + x0);
-                vload<T, VW>(pv, pi + rb + x0);
-                vload<T, VW>(py, phi + ry + x0);
-                vload<T, VW>(pz, phi + rz + x0);
-                const T pxe = __ldg(phi + rb + (x0 + VW == N ? 0 : x0 + VW));  // x neighbour of the last element
-                T k = (T)0, gsum = (T)0, v = (T)0, pvd = (T)0, p2 = (T)0;
-#pragma unroll
-                for (int i = 0; i < VW; ++i) {
-                    const T c = ph[i], px = i + 1 < VW ? ph[(i + 1) % VW] : pxe;
-                    k += pv[i] * pv[i];
-                    gsum += (px - c) * (px - c) + (py[i] - c) * (py[i] - c) + (pz[i] - c) * (pz[i] - c);
-                    v += c * c * ((T)0.5 * m2 + (T)0.25 * lam * c * c);
-                    pvd += c * c * (m2 + lam * c * c);
-                    p2 += c * c;
-                }
-                sK.add(k);
-                sG.add(gsum);
-                sV.add(v);
-                sPV.add(pvd);
-                sP2.add(p2);
+            for (int xv = tx; xv < NV; xv += 2 * tpr) {
+                const bool two = xv + tpr < NV;
+                Vec a, b;
+                load(a, rb, ry, rz, xv * VW);
+                if (two) load(b, rb, ry, rz, (xv + tpr) * VW);
+                sum(a);
+                if (two) sum(b);
             }
         }
     }
@@ -585,7 +597,20 @@ template <typename T>
 static cudaError_t launch_nmc_ricci_t(const RkStageArgs<T>& A, int grid, cudaStream_t s)
 {
     constexpr int VW = 16 / sizeof(T);  // 16-byte vectors where the rows allow them
-    if (A.N % VW == 0) k_nmc_ricci<T, VW><<<grid, 256, 0, s>>>(A);
+    // one wave of resident blocks (a partial second wave would run at a fraction of the rate)
+    static int wave[2] = {0, 0};
+    const int vi = A.N % VW == 0 ? 0 : 1;
+    if (!wave[vi]) {
+        int dev = 0, nsm = 0, occ = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const cudaError_t e = vi == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_nmc_ricci<T, VW>, 256, 0)
+                                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_nmc_ricci<T, 1>, 256, 0);
+        if (e != cudaSuccess) return e;
+        wave[vi] = (occ > 0 ? occ : 1) * (nsm > 0 ? nsm : 1);
+    }
+    if (grid > wave[vi]) grid = wave[vi];
+    if (vi == 0) k_nmc_ricci<T, VW><<<grid, 256, 0, s>>>(A);
     else k_nmc_ricci<T, 1><<<grid, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
