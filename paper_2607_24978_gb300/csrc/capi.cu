@@ -77,6 +77,7 @@ struct cl_lattice {
     bool u1_fused = false;          // U(1) stage as one fused launch (plaquettes in shared memory)
     bool u1_staged = false;         // U(1) launches with shared-memory staged neighbourhoods
     bool nmc = false;               // non-minimal coupling xi phi^2 R of field 0 (Runge-Kutta)
+    bool rbar_valid = false;        // scal->rbar holds the Ricci scalar of the current state
     double xi = 0.0;
     bool gw = false;                // gravitational-wave auxiliaries evolved with the leapfrog
     void* gv[5][2] = {};            // v11, v12, v13, v22, v23 (ping-pong)
@@ -381,7 +382,8 @@ cl_status choose_tiles(cl_lattice* l)
         // CL_OPT_TILE_BY / CL_OPT_STAGES / CL_OPT_TILE_DZ override.
         int by_max = 448 / TX < 1 ? 1 : 448 / TX;
         if (by_max > N) by_max = N;
-        auto fits = [&](int by, int st) { return rk_stage_tma_smem(prec, l->nf, N, by, st) <= (size_t)kPassMaxSmem; };
+        const bool ricci = l->nmc && l->nf == 1;  // the stage also sums the Ricci terms of its output
+        auto fits = [&](int by, int st) { return rk_stage_tma_smem(prec, l->nf, N, by, st, ricci) <= (size_t)kPassMaxSmem; };
         auto most_stages = [&](int by) {  // the deepest ring (3..6) a tile of by rows allows, or 0
             for (int st = 6; st >= 3; --st)
                 if (fits(by, st)) return st;
@@ -408,12 +410,13 @@ cl_status choose_tiles(cl_lattice* l)
             if (l->opt_DZ > 0) {
                 l->rk_DZ = l->opt_DZ > N ? N : l->opt_DZ;
                 l->rk_nbz = (N + l->rk_DZ - 1) / l->rk_DZ;
-                if (l->rk_nby * l->rk_nbz > nblocks) nblocks = l->rk_nby * l->rk_nbz;
+                const int grid = l->rk_nby * l->rk_nbz * (ricci ? 2 : 1);  // two partial sets with the Ricci terms
+                if (grid > nblocks) nblocks = grid;
             } else {
                 const int64_t units = (int64_t)l->rk_nby * N;
                 l->rk_DZ = -1;
                 l->rk_nbz = (int)(units < nsm ? units : nsm);  // the grid
-                if (l->rk_nbz > nblocks) nblocks = l->rk_nbz;
+                if (l->rk_nbz * (ricci ? 2 : 1) > nblocks) nblocks = l->rk_nbz * (ricci ? 2 : 1);
             }
         }
     }
@@ -534,6 +537,9 @@ int nmc_grid(const cl_lattice* l)
     return (int)(g < 1 ? 1 : g);
 }
 
+// Non-minimal stages that carry the Ricci scalar themselves (TMA-staged stage kernel, one field).
+bool nmc_fused(const cl_lattice* l) { return l->nmc && l->nf == 1 && l->rk_stages > 0; }
+
 template <typename T>
 cl_status run_rk_stage_t(cl_lattice* l, const PassCoef& pc, int in, int out)
 {
@@ -559,9 +565,12 @@ cl_status run_rk_stage_t(cl_lattice* l, const PassCoef& pc, int in, int out)
     A.g2 = l->g2;
     A.hubble_limit = l->hubble_limit;
     A.flags = pc.flags | (l->p.expansion ? P_EXPANSION : 0);
-    A.nmc = l->nmc ? 1 : 0;
+    // with the TMA-staged kernel the stage itself leaves the Ricci scalar of its output state
+    // (the next stage's input) in scal->rbar; otherwise a reduction launch precedes each stage
+    const bool fused = nmc_fused(l);
+    A.nmc = l->nmc ? (fused ? 2 : 1) : 0;
     A.xi = l->xi;
-    if (l->nmc) {  // the Ricci scalar of the stage's state first
+    if (l->nmc && !fused) {  // the Ricci scalar of the stage's state first
         cudaError_t e = launch_nmc_ricci(l->p.precision, &A, nmc_grid(l), l->stream);
         if (e != cudaSuccess) return fail(l, CL_ECUDA, "Ricci reduction launch failed: %s", cudaGetErrorString(e));
     }
@@ -877,6 +886,7 @@ cl_status energy_pass(cl_lattice* l, int extra_flags)
     if (l->nmc) {  // the background Ricci scalar of the same state
         s = is_fp64(l) ? nmc_ricci_t<double>(l) : nmc_ricci_t<float>(l);
         if (s != CL_OK) return s;
+        l->rbar_valid = true;
     }
     l->diag_valid = true;
     return CL_OK;
@@ -1176,6 +1186,7 @@ cl_status cl_set_potential(cl_lattice* l, int32_t kind, const double* params, in
     }
     l->potential_set = true;
     l->diag_valid = false;
+    l->rbar_valid = false;
     invalidate_graphs(l);
     return CL_OK;
 }
@@ -1198,6 +1209,7 @@ cl_status cl_set_state(cl_lattice* l, int32_t member, int32_t field, const void*
     if (kind == 0 && has_kahan(l)) CUDA_TRY(l, cudaMemsetAsync((char*)l->cc[f][l->cur] + off, 0, bytes, l->stream));
     if (!on_device) CUDA_TRY(l, cudaStreamSynchronize(l->stream));
     l->diag_valid = false;
+    l->rbar_valid = false;
     return CL_OK;
 }
 
@@ -1242,6 +1254,7 @@ cl_status cl_set_scalars(cl_lattice* l, int32_t member, double a, double adot, d
     CUDA_TRY(l, cudaMemcpyAsync(l->scal, h.data(), sizeof(DevScal) * h.size(), cudaMemcpyHostToDevice, l->stream));
     CUDA_TRY(l, cudaStreamSynchronize(l->stream));
     l->diag_valid = false;
+    l->rbar_valid = false;
     if (isnan(adot) && l->p.expansion) {
         if (is_ens(l) && member >= 0) return energy_pass_members(l, P_HUBBLE_INIT | P_COMMIT, m0, m1);
         return energy_pass(l, P_HUBBLE_INIT | P_COMMIT);
@@ -1277,6 +1290,7 @@ cl_status cl_set_gauge_coupling(cl_lattice* l, double alphaL, double ws2)
     l->alphaL = alphaL;
     l->ws2 = ws2;
     l->diag_valid = false;
+    l->rbar_valid = false;
     invalidate_graphs(l);
     return CL_OK;
 }
@@ -1292,8 +1306,9 @@ cl_status cl_set_nonminimal(cl_lattice* l, double xi)
     l->nmc = true;
     l->xi = xi;
     l->diag_valid = false;
+    l->rbar_valid = false;
     invalidate_graphs(l);
-    return CL_OK;
+    return choose_tiles(l);  // the stage kernel's buffers grow by the rows of the Ricci terms
 }
 
 cl_status cl_enable_gw(cl_lattice* l)
@@ -1515,6 +1530,7 @@ cl_status cl_autotune(cl_lattice* l, const char* cache_path, double* best)
             if (hit && apply_tiles(l, st, by, dz, var) == CL_OK) {
                 if (best) { best[0] = st; best[1] = by; best[2] = dz; best[3] = us; best[4] = var; }
                 l->diag_valid = false;
+                l->rbar_valid = false;
                 return CL_OK;
             }
         }
@@ -1562,6 +1578,7 @@ cl_status cl_autotune(cl_lattice* l, const char* cache_path, double* best)
     if (s != CL_OK) return s;
     CUDA_TRY(l, cudaStreamSynchronize(l->stream));
     l->diag_valid = false;
+    l->rbar_valid = false;
     if (cache_path && best_us < 1e300) {
         if (FILE* f = fopen(cache_path, "a")) {
             fprintf(f, "{\"key\": \"%s\", \"stages\": %d, \"by\": %d, \"dz\": %d, \"variant\": %d, \"us\": %.3f}\n",
@@ -1588,6 +1605,13 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
     }
     const std::vector<PassCoef> sched = step_schedule(l);
     const int pps = (int)sched.size();
+    const bool nmc_f = nmc_fused(l);
+    if (nmc_f && !l->rbar_valid) {  // the fused stages carry the Ricci scalar from stage to stage
+        cl_status s = is_fp64(l) ? nmc_ricci_t<double>(l) : nmc_ricci_t<float>(l);
+        if (s != CL_OK) return s;
+        l->last_launches += 1;
+    }
+    if (nmc_f) l->rbar_valid = true;
     for (int i = 0; i < nsteps; ++i) {
         if (l->use_graph) {
             const int par = l->cur;
@@ -1619,7 +1643,7 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
         }
         // two-launch gauge stages (helper + stage), non-minimally coupled stages (Ricci + stage)
         // and leapfrog passes with gravitational waves (GW pass + scalar pass)
-        l->last_launches += (l->gauge && !l->u1_fused) || l->nmc || l->gw ? 2 * pps : pps;
+        l->last_launches += (l->gauge && !l->u1_fused) || (l->nmc && !nmc_f) || l->gw ? 2 * pps : pps;
     }
     // a leapfrog step ends with the energies of its integer time; a Runge-Kutta stage
     // reports those of the state it started from, so they are recomputed on demand
@@ -1747,6 +1771,7 @@ cl_status cl_init_vacuum(cl_lattice* l, int32_t member, const cl_vacuum_params* 
     }
     if (st == CL_OK) {
         l->diag_valid = false;
+        l->rbar_valid = false;
         st = is_ens(l) ? energy_pass_members(l, P_HUBBLE_INIT | P_COMMIT, m0, m1) : energy_pass(l, P_HUBBLE_INIT | P_COMMIT);
         if (st == CL_OK && !is_ens(l)) l->diag_valid = true;
     }
@@ -1922,6 +1947,7 @@ cl_status cl_lattice_unpack(cl_lattice* l, const float* mu, const float* sg, con
     CUDA_TRY(l, launch_unpack(y_dev, l->V, 2, make_norm(mu, sg, 2), (float*)l->phi[0][l->cur], (float*)l->pi[0][l->cur],
                               has_kahan(l) ? (float*)l->cc[0][l->cur] : nullptr, l->stream));
     l->diag_valid = false;
+    l->rbar_valid = false;
     return CL_OK;
 }
 
@@ -1989,6 +2015,7 @@ cl_status cl_surrogate_jump(cl_surrogate* s, cl_lattice* l, int32_t steps, const
     CUDA_TRY(l, cudaMemcpyAsync(l->scal, &hr, sizeof(DevScal), cudaMemcpyHostToDevice, l->stream));
     CUDA_TRY(l, cudaStreamSynchronize(l->stream));
     l->diag_valid = false;
+    l->rbar_valid = false;
     st = cl_step(l, steps);
     if (st == CL_OK) st = cl_sync(l);
     return st;

@@ -23,15 +23,23 @@ namespace clk {
 
 // Block partials of the old state's energy sums v (K_0, K_1, G_0, G_1, V), then the last
 // block to arrive: volume averages, diagnostics, and the (a, a') part of the stage.
+// With v2 (sums of pi^2, (grad+ phi)^2, V, phi V', phi^2 of the stage's output state, field 0),
+// the last block also writes the background Ricci scalar of that state to scal->rbar, after
+// the stage used the one of its input state (partials of v2 after those of v).
 template <typename T>
 __device__ __forceinline__ void rk_finish(const RkStageArgs<T>& A, double (&v)[kMaxQ], double a_old, bool first,
-                                          double (*s_red)[kMaxQ], int* s_last, int tid, int nthr)
+                                          double (*s_red)[kMaxQ], int* s_last, int tid, int nthr,
+                                          double (*v2)[kMaxQ] = nullptr)
 {
     const int N = A.N;
     block_reduce<kMaxQ>(v, s_red, tid, nthr);
+    if (v2) block_reduce<kMaxQ>(*v2, s_red, tid, nthr);
     if (tid == 0) {
 #pragma unroll
         for (int q = 0; q < kMaxQ; ++q) A.partials[(size_t)blockIdx.x * kMaxQ + q] = v[q];
+        if (v2)
+#pragma unroll
+            for (int q = 0; q < kMaxQ; ++q) A.partials[((size_t)gridDim.x + blockIdx.x) * kMaxQ + q] = (*v2)[q];
         __threadfence();
         const unsigned prev = atomicAdd(&A.scal->counter, 1u);
         *s_last = (prev + 1u == gridDim.x);
@@ -46,6 +54,13 @@ __device__ __forceinline__ void rk_finish(const RkStageArgs<T>& A, double (&v)[k
 #pragma unroll
         for (int q = 0; q < kMaxQ; ++q) w[q] += __ldcg(&A.partials[(size_t)b * kMaxQ + q]);
     block_reduce<kMaxQ>(w, s_red, tid, nthr);
+    double w2[kMaxQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (v2) {
+        for (int b = tid; b < (int)gridDim.x; b += nthr)
+#pragma unroll
+            for (int q = 0; q < kMaxQ; ++q) w2[q] += __ldcg(&A.partials[((size_t)gridDim.x + b) * kMaxQ + q]);
+        block_reduce<kMaxQ>(w2, s_red, tid, nthr);
+    }
     if (tid == 0) {
         DevScal* S = A.scal;
         const double vol = (double)N * N * N;
@@ -89,6 +104,13 @@ __device__ __forceinline__ void rk_finish(const RkStageArgs<T>& A, double (&v)[k
         if (A.flags & P_COUNT_STEP) {
             S->t += A.h;
             S->step += 1;
+        }
+        if (v2) {  // Eq. eomR for the output state, with its scale factor
+            const double an = S->a, an2 = an * an;
+            const double Kn = w2[0] / (2.0 * an2 * an2 * an2 * vol), Gn = w2[1] / (2.0 * an2 * A.dx * A.dx * vol);
+            const double Vn = w2[2] / vol, phidvn = w2[3] / vol, phi2n = w2[4] / vol;
+            const double F = 1.0 / (1.0 + (6.0 * A.xi - 1.0) * A.xi * A.kappa * phi2n);
+            S->rbar = A.kappa * F * ((1.0 - 6.0 * A.xi) * (2.0 * Gn - 2.0 * Kn) + 4.0 * Vn - 6.0 * A.xi * phidvn);
         }
         int st = 0;
         if (!isfinite(rho) || !isfinite(p)) st |= ST_NAN;
@@ -285,7 +307,11 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
     const bool own = tid < BY * TX;
     const int r = own ? tid / TX : BY, tx = own ? tid % TX : 0;
     const int x0 = tx * VW;
-    const int phi_stride = (BY + 2) * N, own_stride = BY * N;
+    // A.nmc == 2: the stage also sums the Ricci-scalar terms of its output state, which needs
+    // the new field one row beyond the tile (the own arrays carry the halo row y0+R as row R)
+    // and one plane beyond the z chunk (the upper halo plane carries pi, c, k_phi too)
+    const bool fuse_r = NF == 1 && A.nmc == 2;
+    const int phi_stride = (BY + 2) * N, own_stride = (BY + (fuse_r ? 1 : 0)) * N;
     const int field_stride = phi_stride + NOWN * own_stride;
     const int stage_stride = NF * field_stride;
     T* stage = reinterpret_cast<T*>(smem_raw);
@@ -310,6 +336,7 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
     }
     __syncthreads();
     Acc<T> accK[NF], accG[NF], accV;
+    Acc<T> nK, nG, nV, nPV, nP2;  // Ricci terms of the output state (fuse_r)
     auto bounded = [&](uint64_t* bar, uint32_t parity) {
         if (!mbar_wait_bounded(bar, parity, s_timeout ? 1000000ull : 2000000000ull)) s_timeout = 1;
     };
@@ -334,10 +361,15 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
                     bounded(&s_empty[st], (empty_phase >> st) & 1u);
                     empty_phase ^= 1u << st;
                 }
-                const int nown = (j == 0 || j == NZ + 1) ? 0 : nown_in;  // z halos: the field only
-                const int per_field = 3 + nown;
+                // own-row arrays this plane: none for the lower z halo, and for the upper one
+                // only what the new field needs when the Ricci terms are fused
+                const int nnew = first ? (KAHAN ? 2 : 1) : (KAHAN ? 3 : 2);  // pi (, c) (, k_phi)
+                const int nown = j == 0 ? 0 : (j == NZ + 1 ? (fuse_r ? nnew : 0) : nown_in);
+                const int nhalo = fuse_r && j > 0 ? nnew : 0;  // the row y0+R of the same arrays
+                const int per_field = 3 + nown + nhalo;
                 if (lane == 0)
-                    mbar_arrive_expect_tx(&s_full[st], (uint32_t)(NF * (R + 2 + nown * R) * N * sizeof(T)));
+                    mbar_arrive_expect_tx(&s_full[st],
+                                          (uint32_t)(NF * (R + 2 + nown * R + nhalo) * N * sizeof(T)));
                 __syncwarp();
                 if (lane < NF * per_field) {
                     const int f = lane / per_field, part = lane - f * per_field;
@@ -349,15 +381,20 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
                         const int srow = part == 0 ? 0 : (part == 1 ? 1 : R + 1);
                         const int nrows = part == 1 ? R : 1;
                         tma_bulk_g2s(fb + srow * N, src + (plane + y) * N, (uint32_t)(nrows * N * sizeof(T)), &s_full[st]);
-                    } else {  // own rows of pi (, c), k_phi, k_pi
-                        const int k = part - 3;
+                    } else {  // own rows (or the halo row y0+R) of pi (, c), k_phi, k_pi
+                        const bool halo = part - 3 >= nown;
+                        const int k = halo ? part - 3 - nown : part - 3;
                         const T* src;
                         if (k == 0) src = f == 0 ? A.pi_in[0] : A.pi_in[NF - 1];
                         else if (k == OC) src = f == 0 ? A.c_in[0] : A.c_in[NF - 1];
                         else if (k == OKF) src = f == 0 ? A.kphi_in[0] : A.kphi_in[NF - 1];
                         else src = f == 0 ? A.kpi_in[0] : A.kpi_in[NF - 1];
-                        tma_bulk_g2s(fb + phi_stride + k * own_stride, src + (plane + y0) * N,
-                                     (uint32_t)(R * N * sizeof(T)), &s_full[st]);
+                        if (halo)
+                            tma_bulk_g2s(fb + phi_stride + k * own_stride + R * N, src + (plane + yhi) * N,
+                                         (uint32_t)(N * sizeof(T)), &s_full[st]);
+                        else
+                            tma_bulk_g2s(fb + phi_stride + k * own_stride, src + (plane + y0) * N,
+                                         (uint32_t)(R * N * sizeof(T)), &s_full[st]);
                     }
                 }
                 __syncwarp();
@@ -381,6 +418,34 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
         for (int f = 0; f < NF; ++f)
 #pragma unroll
             for (int i = 0; i < VW; ++i) zlo[f][i] = zmid[f][i] = znew[f][i] = (T)0;
+        // new field 0 of VW elements at phi row rphi, own row rown, column col of stage sbuf: the
+        // same operations as the site that owns them (used for the forward differences of the
+        // output state across tile rows, vector edges and the z chunk's end)
+        auto phi_new = [&](const T* sbuf, int rphi, int rown, int col, T (&out)[VW]) {
+            const T* ob = sbuf + phi_stride + rown * N + col;
+            T pv[VW], cv[VW], kf[VW];
+            vload_smem<T, VW>(out, sbuf + rphi * N + col);
+            vload_smem<T, VW>(pv, ob);
+            if (KAHAN) vload_smem<T, VW>(cv, ob + (KAHAN ? OC : 0) * own_stride);
+            if (!first) vload_smem<T, VW>(kf, ob + OKF * own_stride);
+#pragma unroll
+            for (int i = 0; i < VW; ++i) {
+                const T fphi = cphi * pv[i];
+                kf[i] = first ? fphi : cA * kf[i] + fphi;
+                drift<T, KAHAN>(out[i], cv[i], kf[i], cB);
+            }
+        };
+        auto phi_new1 = [&](const T* sbuf, int rphi, int rown, int col) {
+            const T* ob = sbuf + phi_stride + rown * N + col;
+            T ph = sbuf[rphi * N + col], cv = KAHAN ? ob[(KAHAN ? OC : 0) * own_stride] : (T)0;
+            const T fphi = cphi * ob[0];
+            const T kf = first ? fphi : cA * ob[OKF * own_stride] + fphi;
+            drift<T, KAHAN>(ph, cv, kf, cB);
+            return ph;
+        };
+        T nzprev[VW];  // new field of the plane finished before (own vector), for the z differences
+#pragma unroll
+        for (int i = 0; i < VW; ++i) nzprev[i] = (T)0;
         int st = 0, st_prev = 0;
         uint32_t full_phase = 0;
         auto release = [&](int s_idx) {
@@ -466,6 +531,32 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
                                 }
                             }
                             accK[f].add(ksum);
+                            if (fuse_r && f == 0) {
+                                // Ricci terms of the output state at this vector: local ones, and the
+                                // forward differences in x and y (z: with the previous plane)
+                                const unsigned act = __activemask();
+                                const T xs = __shfl_down_sync(act, ph[0], 1);
+                                const T xe = xp_lane ? xs : phi_new1(sp, r + 1, r, xp_idx);
+                                T yn[VW];
+                                phi_new(sp, r + 2, r + 1, x0, yn);
+                                T kn = (T)0, gn = (T)0, vn = (T)0, pvn = (T)0, p2n = (T)0;
+#pragma unroll
+                                for (int i = 0; i < VW; ++i) {
+                                    const T c = ph[i], xn = i + 1 < VW ? ph[(i + 1) % VW] : xe;
+                                    kn += po[i] * po[i];
+                                    gn += (xn - c) * (xn - c) + (yn[i] - c) * (yn[i] - c);
+                                    if (j >= 3) gn += (c - nzprev[i]) * (c - nzprev[i]);  // plane below
+                                    vn += c * c * (P.h_m20 + P.q_l0 * c * c);
+                                    pvn += c * c * (P.m20 + P.l0 * c * c);
+                                    p2n += c * c;
+                                    nzprev[i] = c;
+                                }
+                                nK.add(kn);
+                                nG.add(gn);
+                                nV.add(vn);
+                                nPV.add(pvn);
+                                nP2.add(p2n);
+                            }
                             vstore<T, VW>(A.phi_out[f] + base, ph);
                             vstore<T, VW>(A.pi_out[f] + base, po);
                             vstore<T, VW>(A.kphi_out[f] + base, kf);
@@ -474,6 +565,15 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
                         }
                         accV.add(vsum);
                     }
+                }
+                if (fuse_r && j == NZ + 1 && r < R) {
+                    // the chunk's last plane: its z difference with the new field above it
+                    T up[VW];
+                    phi_new(sb, r + 1, r, x0, up);
+                    T gn = (T)0;
+#pragma unroll
+                    for (int i = 0; i < VW; ++i) gn += (up[i] - nzprev[i]) * (up[i] - nzprev[i]);
+                    nG.add(gn);
                 }
                 if (j >= 1) release(st_prev);  // plane j-1: finished (or the lower z halo)
 #pragma unroll
@@ -497,7 +597,8 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
     v[2] = accG[0].value();
     v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
     v[4] = accV.value();
-    rk_finish(A, v, s_coef[3], first, s_red, &s_last, tid, nthr);
+    double v2[kMaxQ] = {nK.value(), nG.value(), nV.value(), nPV.value(), nP2.value()};
+    rk_finish(A, v, s_coef[3], first, s_red, &s_last, tid, nthr, fuse_r ? &v2 : nullptr);
 }
 
 // Background Ricci scalar of a non-minimally coupled field (section "Scalar fields
@@ -663,11 +764,11 @@ cudaError_t launch_rk_stage(int precision, int nf, const void* args, int vw, cud
     return nf == 1 ? rk_vw<float, 1, false>(A, vw, s) : rk_vw<float, 2, false>(A, vw, s);
 }
 
-size_t rk_stage_tma_smem(int precision, int nf, int N, int BY, int stages)
+size_t rk_stage_tma_smem(int precision, int nf, int N, int BY, int stages, bool ricci)
 {
     const size_t es = precision == CL_PREC_FP64 ? 8 : 4;
     const int nown = precision == CL_PREC_FP32_KAHAN ? 4 : 3;
-    return (size_t)stages * nf * ((size_t)(BY + 2) + (size_t)nown * BY) * N * es;
+    return (size_t)stages * nf * ((size_t)(BY + 2) + (size_t)nown * (BY + (ricci ? 1 : 0))) * N * es;
 }
 
 template <typename T, int NF, bool KAHAN, int VW>
@@ -678,8 +779,9 @@ static cudaError_t launch_rk_tma(const RkStageArgs<T>& A, int stages, cudaStream
         const int TX = A.N / VW;
         const dim3 block(((TX * A.BY + 31) / 32) * 32 + 32);  // consumers + the producer warp
         const dim3 grid(A.DZ > 0 ? A.nby * A.nbz : A.nbz);
-        const size_t smem = rk_stage_tma_smem(prec, NF, A.N, A.BY, stages);
-        if (block.x > 480 || smem > (size_t)kPassMaxSmem || A.N % VW != 0) return cudaErrorInvalidValue;
+        const size_t smem = rk_stage_tma_smem(prec, NF, A.N, A.BY, stages, A.nmc == 2);
+        if (block.x > 480 || smem > (size_t)kPassMaxSmem || A.N % VW != 0 || (A.nmc == 2 && NF != 1))
+            return cudaErrorInvalidValue;
         static bool attr[7] = {false, false, false, false, false, false, false};
         cudaError_t e = cudaSuccess;
 #define CL_RKT_CASE(SS)                                                                                         \

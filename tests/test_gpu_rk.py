@@ -132,7 +132,7 @@ def test_rk_without_expansion(cl):
 
 
 def run_nmc(cl, N, prec, integ, scheme, nsteps, xi, alpha, dt=0.01, pot=(0.6, 1.0), seed=37, adot=0.3, fbar=0.9,
-            amp=0.05):
+            amp=0.05, opts=(), effective=None, energies_first=True):
     L = 0.8 * N
     phi, pi = inputs.scalar_state(N, 1, seed=seed, fbar=(fbar,), amp=amp, pamp=amp)
     m = O.make_model(N, L, nf=1, alpha=alpha, kappa=0.6, expansion=True, m2=(pot[0], 0.0), lam=(pot[1], 0.0),
@@ -142,10 +142,14 @@ def run_nmc(cl, N, prec, integ, scheme, nsteps, xi, alpha, dt=0.01, pot=(0.6, 1.
     with cl.Lattice(N, L, 1, prec, integ, expansion=True, alpha=alpha, kappa=0.6, dt=dt) as g:
         g.cl_set_potential(cl.CL_POT_POLY, [pot[0], pot[1], 0.0, 0.0, 0.0])
         g.cl_set_nonminimal(xi)
+        for opt, val in opts:
+            g.cl_set_option(opt, val)
+        if effective is not None:
+            effective["stages"] = g.cl_get_option(cl.CL_OPT_STAGES)
         g.cl_set_state(cl.CL_FIELD_PHI0, st.phi[0].astype(dtype))
         g.cl_set_state(cl.CL_FIELD_PI0, st.pi[0].astype(dtype))
         g.cl_set_scalars(st.abt[0], st.abt[1], 0.0)
-        e0 = g.cl_energies()
+        e0 = g.cl_energies() if energies_first else None
         r0 = O.nmc_ricci(m, st)
         g.cl_step(nsteps)
         launches = g.cl_last_launch_count()
@@ -162,14 +166,37 @@ def test_nmc_parity(cl, integ, scheme, stages, prec, tol, xi, alpha):
     """Non-minimally coupled field (cl_set_nonminimal): fields, a, a' and the background
     Ricci scalar against the oracle; two launches per stage (Ricci reduction + stage)."""
     N, n = 12, 20
-    gphi, gpi, e0, r0, e, st, m, launches = run_nmc(cl, N, prec, integ, scheme, n, xi, alpha)
+    eff = {}
+    gphi, gpi, e0, r0, e, st, m, launches = run_nmc(cl, N, prec, integ, scheme, n, xi, alpha, effective=eff)
     assert rel_l2(gphi, st.phi[0]) < tol
     assert rel_l2(gpi, st.pi[0]) < tol
     assert e["a"] == pytest.approx(st.abt[0], rel=tol)
     assert e["adot"] == pytest.approx(st.abt[1], rel=max(tol, 1e-9))
     assert e0["ricci"] == pytest.approx(r0, rel=max(tol, 1e-9))
     assert e["ricci"] == pytest.approx(O.nmc_ricci(m, st), rel=max(tol, 1e-9))
-    assert launches == 2 * n * stages
+    # TMA-staged stages carry the Ricci scalar of their output (the energies computed it for
+    # the initial state); the direct-load kernel needs a reduction launch per stage
+    assert launches == (n * stages if eff["stages"] > 0 else 2 * n * stages)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (2, 1e-5)])
+@pytest.mark.parametrize("N", [32, 48])
+def test_nmc_fused_ricci_matches_separate_reduction(cl, prec, tol, N):
+    """The Ricci scalar summed by the stage kernel for its output state (the default with the
+    TMA-staged kernel) against a reduction launch before every stage (CL_OPT_STAGES -1), with
+    no energies before the first step (so the first step starts with one reduction launch)."""
+    res = []
+    for opts in ((), ((cl.CL_OPT_STAGES, -1),)):
+        eff = {}
+        gphi, gpi, e0, r0, e, st, m, launches = run_nmc(cl, N, prec, cl.CL_INT_RK4_5, O.RK4_5, 6, 0.3, 1.0,
+                                                        opts=opts, effective=eff, energies_first=False)
+        res.append((gphi, gpi, e, launches, eff["stages"]))
+    (fa, pa, ea, la, sa), (fb, pb, eb, lb, sb) = res
+    assert sa > 0 and sb == -1
+    assert la == 6 * 5 + 1 and lb == 2 * 6 * 5
+    assert rel_l2(fa, fb) < tol and rel_l2(pa, pb) < tol
+    for k in ("ricci", "a", "adot", "rho"):
+        assert ea[k] == pytest.approx(eb[k], rel=max(tol, 1e-12)), k
 
 
 def test_nmc_conformal_quartic_keeps_a_linear(cl):
