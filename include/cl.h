@@ -282,8 +282,8 @@ cl_status cl_set_hubble_limit(cl_lattice* l, double limit);
  * clamp to 2..4 with the ring kernel and 3..6 ringless).  On a Runge-Kutta scalar lattice
  * the three options tile the stage kernel instead: CL_OPT_STAGES 3..6 stage buffers of the
  * TMA-staged stage kernel (2 counts as 3; -1 = the direct-load kernel), CL_OPT_TILE_BY its
- * rows per tile, CL_OPT_TILE_DZ fixed z chunks (0 = balanced persistent ranges, reported
- * as -1).
+ * rows per tile, CL_OPT_TILE_DZ its z chunks (0 = the library's: every y tile cut into the
+ * same chunks, one wave of blocks; -1 = balanced persistent ranges).
  * CL_OPT_PASS_VARIANT (-1 = library choice, the default): TMA-staged pass kernel, 1 =
  * ringless (the library's choice: each warp drifts the neighbour rows it needs from the
  * stage buffers, no consumer barrier; 16-byte vectors, 2..5 stages (ensembles 3..6), other

@@ -90,12 +90,14 @@ def test_rk_tma_matches_direct_kernel(cl, N, nf, prec, tol):
     assert t[2]["a"] == pytest.approx(d[2]["a"], rel=max(tol, 1e-13))
 
 
-@pytest.mark.parametrize("by,stages,dz", [(1, 3, 0), (5, 4, 0), (7, 0, 0), (3, 6, 5), (0, 3, 31), (32, 0, 0)])
+@pytest.mark.parametrize("by,stages,dz", [(1, 3, 0), (5, 4, 0), (7, 0, 0), (3, 6, 5), (0, 3, 31), (32, 0, 0),
+                                          (5, 4, -1), (1, 0, -1)])
 @pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-4)])
 def test_rk_tma_tilings(cl, by, stages, dz, prec, tol):
     """TMA-staged stages against the oracle at 32^3 over tilings: one-row tiles, a ragged last
-    tile (5 and 7 rows), the whole box in one tile, 3 to 6 stages, persistent ranges and
-    fixed z chunks (5 planes; 31, leaving a chunk of one plane)."""
+    tile (5 and 7 rows), the whole box in one tile, 3 to 6 stages, the library's z chunks,
+    fixed chunks (5 planes; 31, leaving a chunk of one plane) and balanced persistent ranges
+    (-1)."""
     opts = [(cl.CL_OPT_TILE_BY, by)] if by else []
     opts += [(cl.CL_OPT_STAGES, stages)] if stages else []
     opts += [(cl.CL_OPT_TILE_DZ, dz)] if dz else []
