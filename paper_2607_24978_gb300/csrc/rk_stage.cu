@@ -286,6 +286,12 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
 // finished (the z halos right away), so the producer stays S - 2 planes ahead; the warps
 // synchronise through the full / empty mbarriers only, every wait bounded.  The arithmetic
 // is that of k_rk_stage, operation for operation.
+// For a non-minimally coupled field (A.nmc == 2) the stage also sums the terms of the Ricci
+// scalar (Eq. eomR) of its output state, which the next stage needs: pi^2, V, phi V', phi^2
+// of the new values at each site and the forward differences of the new field.  Those cross
+// the tile's last row, the vector edges and the chunk's last plane, so the stage buffers
+// then also hold pi (, c), k_phi of the row y0+R and of the upper halo plane, from which a
+// consumer recomputes the new field there with the owner's operations.
 template <typename T, int NF, bool KAHAN, int VW, int S>
 __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
 {

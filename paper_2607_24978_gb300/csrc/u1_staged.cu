@@ -23,15 +23,14 @@
 //    site, and release a slot once they have read it for the last time (its "empty" barrier
 //    counts one arrival per consumer warp), so no warp waits for another one's work.
 // Arrays read only at the site itself (theta and the Runge-Kutta auxiliaries) are loaded by
-// the consumers straight from global memory, one plane ahead.  Every wait is bounded and reports through the
-// status word.  Needs N % 32 == 0; other sizes use the gather kernels.
+// the consumers straight from global memory, one plane ahead.  Every wait is bounded and
+// reports through the status word.  Needs N % 32 == 0; other sizes use the gather kernels.
 #include <math.h>
 
 #include "cl_internal.cuh"
 #include "kernel_common.cuh"
 #include "u1_common.cuh"
 #include "u1_staged.cuh"
-
 
 namespace clk {
 
