@@ -8,7 +8,9 @@
  * "Non-symplectic evolvers": velocity Verlet (order 2), the order-4 Yoshida
  * composition of it, and the low-storage 2N Runge-Kutta schemes RK3-3 and RK4-5.
  * Everything is plain triple loops in double precision, in the order the
- * equations are written; no blocking, fusion or reordering.
+ * equations are written; no blocking, fusion or reordering.  Reduced (d+1)-dimensional
+ * lattices (section "Scalar dynamics in 1+1 and 2+1 dimensions", model dims = 1 or 2) are
+ * boxes of extent 1 along the missing directions, whose terms the operators leave out.
  */
 #include "oracle.h"
 
@@ -16,7 +18,6 @@
 #include <stdlib.h>
 #include <string.h>
 
-static int64_t I3(int N, int x, int y, int z) { return ((int64_t)z * N + y) * N + x; }
 static int wrap(int i, int N) { return ((i % N) + N) % N; }
 
 /* ------------------------------------------------------------------ potential */
@@ -51,46 +52,78 @@ double orc_d2V(const orc_model* m, int f, double f0, double f1)
 
 /* ------------------------------------------------------------ lattice operators */
 
-void orc_laplacian(int N, double dx, const double* f, double* out)
+int64_t orc_volume(const orc_model* m)
 {
-    for (int z = 0; z < N; ++z)
-        for (int y = 0; y < N; ++y)
-            for (int x = 0; x < N; ++x) {
-                double c = f[I3(N, x, y, z)];
-                double s = f[I3(N, wrap(x + 1, N), y, z)] + f[I3(N, wrap(x - 1, N), y, z)] - 2.0 * c
-                         + f[I3(N, x, wrap(y + 1, N), z)] + f[I3(N, x, wrap(y - 1, N), z)] - 2.0 * c
-                         + f[I3(N, x, y, wrap(z + 1, N))] + f[I3(N, x, y, wrap(z - 1, N))] - 2.0 * c;
-                out[I3(N, x, y, z)] = s / (dx * dx);
+    int nx, ny, nz;
+    orc_extents(m, &nx, &ny, &nz);
+    return (int64_t)nx * ny * nz;
+}
+
+void orc_extents(const orc_model* m, int* nx, int* ny, int* nz)
+{
+    const int d = (m->dims == 1 || m->dims == 2) ? m->dims : 3;
+    *nx = m->N;
+    *ny = d >= 2 ? m->N : 1;
+    *nz = d >= 3 ? m->N : 1;
+}
+
+/* index of (x, y, z) in a box of extents nx, ny (x fastest) */
+static int64_t IB(int nx, int ny, int x, int y, int z) { return ((int64_t)z * ny + y) * nx + x; }
+
+/* 7-point Laplacian over the directions of extent > 1 of an nx x ny x nz box */
+static void laplacian_box(int nx, int ny, int nz, double dx, const double* f, double* out)
+{
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const double c = f[IB(nx, ny, x, y, z)];
+                double s = f[IB(nx, ny, wrap(x + 1, nx), y, z)] + f[IB(nx, ny, wrap(x - 1, nx), y, z)] - 2.0 * c;
+                if (ny > 1) s += f[IB(nx, ny, x, wrap(y + 1, ny), z)] + f[IB(nx, ny, x, wrap(y - 1, ny), z)] - 2.0 * c;
+                if (nz > 1) s += f[IB(nx, ny, x, y, wrap(z + 1, nz))] + f[IB(nx, ny, x, y, wrap(z - 1, nz))] - 2.0 * c;
+                out[IB(nx, ny, x, y, z)] = s / (dx * dx);
             }
 }
 
-/* sum_n sum_i [f(n+i) - f(n)]^2  (no 1/dx^2) */
-double orc_grad2_sum(int N, const double* f)
+/* sum_n sum_i [f(n+i) - f(n)]^2 over the directions of extent > 1  (no 1/dx^2) */
+static double grad2_box(int nx, int ny, int nz, const double* f)
 {
     double s = 0.0;
-    for (int z = 0; z < N; ++z)
-        for (int y = 0; y < N; ++y)
-            for (int x = 0; x < N; ++x) {
-                double c = f[I3(N, x, y, z)];
-                double gx = f[I3(N, wrap(x + 1, N), y, z)] - c;
-                double gy = f[I3(N, x, wrap(y + 1, N), z)] - c;
-                double gz = f[I3(N, x, y, wrap(z + 1, N))] - c;
-                s += gx * gx + gy * gy + gz * gz;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const double c = f[IB(nx, ny, x, y, z)];
+                const double gx = f[IB(nx, ny, wrap(x + 1, nx), y, z)] - c;
+                s += gx * gx;
+                if (ny > 1) {
+                    const double gy = f[IB(nx, ny, x, wrap(y + 1, ny), z)] - c;
+                    s += gy * gy;
+                }
+                if (nz > 1) {
+                    const double gz = f[IB(nx, ny, x, y, wrap(z + 1, nz))] - c;
+                    s += gz * gz;
+                }
             }
     return s;
 }
+
+void orc_laplacian(int N, double dx, const double* f, double* out) { laplacian_box(N, N, N, dx, f, out); }
+
+/* sum_n sum_i [f(n+i) - f(n)]^2  (no 1/dx^2) */
+double orc_grad2_sum(int N, const double* f) { return grad2_box(N, N, N, f); }
 
 /* Kick of Eq. singletEOM with pi = a^(3-alpha) phi':
  *   pi' = a^(1+alpha) Lap phi - a^(3+alpha) dV/dphi_f                     */
 void orc_kick_force(const orc_model* m, int f, const double* phi, double a, double* out)
 {
     const int N = m->N;
-    const int64_t V = (int64_t)N * N * N;
+    const int64_t V = orc_volume(m);
     const double dx = m->L / N;
     const double* pf = phi + (int64_t)f * V;
     const double* p0 = phi;
     const double* p1 = (m->nf > 1) ? phi + V : NULL;
-    orc_laplacian(N, dx, pf, out);
+    int nx, ny, nz;
+    orc_extents(m, &nx, &ny, &nz);
+    laplacian_box(nx, ny, nz, dx, pf, out);
     const double ca = pow(a, 1.0 + m->alpha), cv = pow(a, 3.0 + m->alpha);
     for (int64_t n = 0; n < V; ++n)
         out[n] = ca * out[n] - cv * orc_dV(m, f, p0[n], p1 ? p1[n] : 0.0);
@@ -111,9 +144,11 @@ void orc_energies(const orc_model* m, const double* phi, const double* pi,
                   const double* links, const double* efield, const double* abt, double* out)
 {
     const int N = m->N;
-    const int64_t V = (int64_t)N * N * N;
+    const int64_t V = orc_volume(m);
     const double dx = m->L / N;
     const double a = abt[0], b = abt[1];
+    int nx, ny, nz;
+    orc_extents(m, &nx, &ny, &nz);
     memset(out, 0, sizeof(double) * ORC_NE);
 
     for (int f = 0; f < m->nf; ++f) {
@@ -123,7 +158,7 @@ void orc_energies(const orc_model* m, const double* phi, const double* pi,
         /* K = phi'^2 / (2 a^(2 alpha)) with phi' = a^(alpha-3) pi  ->  pi^2 / (2 a^6) */
         out[ORC_E_K0 + f] = s / (2.0 * pow(a, 6.0) * (double)V);
         /* G = sum_i (grad+_i phi)^2 / (2 a^2) */
-        out[ORC_E_G0 + f] = orc_grad2_sum(N, phi + (int64_t)f * V) / (dx * dx) / (2.0 * a * a * (double)V);
+        out[ORC_E_G0 + f] = grad2_box(nx, ny, nz, phi + (int64_t)f * V) / (dx * dx) / (2.0 * a * a * (double)V);
     }
     {
         double s = 0.0;
@@ -170,8 +205,7 @@ void orc_u1_rk_step(const orc_model* m, int scheme, double h,
 static void vv_step(const orc_model* m, double h, double* phi, double* pi, double* abt, double* tmp, double* gv,
                     double* gp)
 {
-    const int N = m->N;
-    const int64_t V = (int64_t)N * N * N;
+    const int64_t V = orc_volume(m);
     double e[ORC_NE];
     double a = abt[0], b = abt[1];
     double* gtmp = gv ? malloc(sizeof(double) * (size_t)(5 * V)) : NULL;
@@ -242,8 +276,7 @@ int orc_rk_coeffs(int scheme, const double** A, const double** B)
 
 double orc_nmc_ricci(const orc_model* m, const double* phi, const double* pi, const double* abt)
 {
-    const int N = m->N;
-    const int64_t V = (int64_t)N * N * N;
+    const int64_t V = orc_volume(m);
     double e[ORC_NE];
     orc_energies(m, phi, pi, NULL, NULL, abt, e);
     double phidv = 0.0, phi2 = 0.0;
@@ -265,8 +298,7 @@ double orc_nmc_ricci(const orc_model* m, const double* phi, const double* pi, co
  *   a'' = a [a^(2 alpha) R / 6 - (1 - alpha) (a'/a)^2], with R = orc_nmc_ricci(y). */
 static void rk_step(const orc_model* m, int scheme, double h, double* phi, double* pi, double* abt)
 {
-    const int N = m->N;
-    const int64_t V = (int64_t)N * N * N;
+    const int64_t V = orc_volume(m);
     const int64_t nd = (int64_t)m->nf * V;
     const double *A, *B;
     const int S = orc_rk_coeffs(scheme, &A, &B);
@@ -332,7 +364,7 @@ static void composed_step(const orc_model* m, int order, double h, double* phi, 
 void orc_step(const orc_model* m, int scheme, double h, int nsteps,
               double* phi, double* pi, double* links, double* efield, double* abt)
 {
-    const int64_t V = (int64_t)m->N * m->N * m->N;
+    const int64_t V = orc_volume(m);
     if (m->gauge == 1) {
         for (int s = 0; s < nsteps; ++s) orc_u1_rk_step(m, scheme, h, phi, pi, links, efield, abt);
         return;

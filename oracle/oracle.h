@@ -55,7 +55,15 @@ typedef struct {
      * coupled to gravity"); Runge-Kutta schemes only, one field, no gauge sector        */
     int32_t nmc;        /* 1: on                                                         */
     double xi;
+    /* spatial dimensions of the lattice (section "Scalar dynamics in 1+1 and 2+1 dimensions"):
+     * 0 or 3 = N^3 sites; 2 = N^2 and 1 = N sites, the Laplacian and the gradient energy
+     * summed over those directions only, everything else unchanged.  Scalar fields only.   */
+    int32_t dims;
 } orc_model;
+
+/* Sites of the model's lattice, and its extents along x, y, z (1 beyond dims). */
+int64_t orc_volume(const orc_model* m);
+void orc_extents(const orc_model* m, int* nx, int* ny, int* nz);
 
 /* Indices into the energies vector returned by orc_energies(). */
 enum {

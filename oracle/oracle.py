@@ -20,7 +20,8 @@ class Model(C.Structure):
     _fields_ = [("N", C.c_int32), ("nf", C.c_int32), ("expansion", C.c_int32), ("gauge", C.c_int32),
                 ("L", C.c_double), ("alpha", C.c_double), ("kappa", C.c_double),
                 ("m2", C.c_double * 2), ("lam", C.c_double * 2), ("g2", C.c_double),
-                ("alphaL", C.c_double), ("ws2", C.c_double), ("nmc", C.c_int32), ("xi", C.c_double)]
+                ("alphaL", C.c_double), ("ws2", C.c_double), ("nmc", C.c_int32), ("xi", C.c_double),
+                ("dims", C.c_int32)]
 
 
 _lib = None
@@ -75,9 +76,11 @@ def lib():
 
 
 def make_model(N, L, nf=1, alpha=1.0, kappa=0.0, expansion=False, m2=(0.0, 0.0), lam=(0.0, 0.0),
-               g2=0.0, gauge=0, alphaL=0.0, ws2=0.0, xi=None):
-    """xi: non-minimal coupling of field 0 (None: minimally coupled)."""
+               g2=0.0, gauge=0, alphaL=0.0, ws2=0.0, xi=None, dims=3):
+    """xi: non-minimal coupling of field 0 (None: minimally coupled).  dims: 3, or 2 / 1 for
+    the reduced (2+1) / (1+1)-dimensional lattice of N^2 / N sites."""
     m = Model()
+    m.dims = int(dims)
     m.nmc, m.xi = (0, 0.0) if xi is None else (1, float(xi))
     m.N, m.nf, m.expansion, m.gauge = int(N), int(nf), int(bool(expansion)), int(gauge)
     m.L, m.alpha, m.kappa = float(L), float(alpha), float(kappa)
@@ -109,10 +112,19 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
 
 
+def extents(model):
+    """(nz, ny, nx) of the model's lattice: 1 along the directions a reduced lattice lacks."""
+    d = model.dims if model.dims in (1, 2) else 3
+    N = model.N
+    return (N if d >= 3 else 1, N if d >= 2 else 1, N)
+
+
 def new_state(model, a=1.0, b=0.0, t=0.0):
-    N, nf = model.N, model.nf
-    st = State(np.zeros((nf, N, N, N)), np.zeros((nf, N, N, N)), np.array([a, b, t], dtype=np.float64))
+    nf = model.nf
+    shape = (nf,) + extents(model)
+    st = State(np.zeros(shape), np.zeros(shape), np.array([a, b, t], dtype=np.float64))
     if model.gauge == 1:
+        N = model.N
         st.links = np.zeros((3, N, N, N))
         st.efield = np.zeros((3, N, N, N))
     return st
