@@ -111,7 +111,14 @@ typedef struct {
     int32_t gauge;        /* CL_GAUGE_*                                                     */
     int32_t expansion;    /* 1: self-consistent expansion (Eq. Friedmann1); 0: a, a' frozen */
     int32_t members;      /* ensemble size B; 0 or 1 = single lattice (see below)           */
-    int32_t reserved;     /* must be 0                                                      */
+    int32_t dims;         /* spatial dimensions: 0 or 3 = N^3 sites; 2 / 1 = the reduced     */
+                          /* (2+1) / (1+1)-dimensional lattice of N^2 / N sites (section     */
+                          /* "Scalar dynamics in 1+1 and 2+1 dimensions"): Laplacian and     */
+                          /* gradient energy over those directions, the rest unchanged;     */
+                          /* single lattices of scalar fields only (CL_EUNSUPPORTED with     */
+                          /* ensembles or gauge fields; vacuum initial conditions, spectra, */
+                          /* GW, non-minimal coupling, autotuner and surrogate refuse them). */
+                          /* Field arrays hold N^dims elements, x fastest.                  */
     const int32_t* member_N; /* B per-member sizes (copied) when members > 1, else NULL     */
     const double* member_L;  /* B per-member box sides (copied), or NULL = L for all        */
     double L;             /* box side in program units                                      */

@@ -42,7 +42,7 @@ CL_SG_BF16, CL_SG_FP32 = 0, 1
 
 class cl_lattice_params(C.Structure):
     _fields_ = [("N", C.c_int32), ("nfields", C.c_int32), ("precision", C.c_int32), ("integrator", C.c_int32),
-                ("gauge", C.c_int32), ("expansion", C.c_int32), ("members", C.c_int32), ("reserved", C.c_int32),
+                ("gauge", C.c_int32), ("expansion", C.c_int32), ("members", C.c_int32), ("dims", C.c_int32),
                 ("member_N", C.POINTER(C.c_int32)), ("member_L", C.POINTER(C.c_double)),
                 ("L", C.c_double), ("alpha", C.c_double), ("kappa", C.c_double), ("dt", C.c_double),
                 ("a0", C.c_double), ("stream", C.c_void_p)]
@@ -190,12 +190,14 @@ class Lattice:
     """Owns one cl_lattice handle.  Methods mirror the C calls."""
 
     def __init__(self, N, L, nfields=1, precision=CL_PREC_FP64, integrator=CL_INT_VV2, gauge=CL_GAUGE_NONE,
-                 expansion=True, alpha=1.0, kappa=0.1, dt=0.01, a0=1.0, stream=None, member_N=None, member_L=None):
-        """A single N^3 lattice, or (member_N = list of sizes) a batched ensemble whose
-        member m has member_N[m]^3 sites and box side member_L[m] (default L)."""
+                 expansion=True, alpha=1.0, kappa=0.1, dt=0.01, a0=1.0, stream=None, member_N=None, member_L=None,
+                 dims=3):
+        """A single N^3 lattice (dims 2 / 1: the reduced lattice of N^2 / N sites), or
+        (member_N = list of sizes) a batched ensemble whose member m has member_N[m]^3 sites
+        and box side member_L[m] (default L)."""
         p = cl_lattice_params()
         p.N, p.nfields, p.precision, p.integrator = int(N), int(nfields), int(precision), int(integrator)
-        p.gauge, p.expansion, p.members, p.reserved = int(gauge), int(bool(expansion)), 0, 0
+        p.gauge, p.expansion, p.members, p.dims = int(gauge), int(bool(expansion)), 0, int(dims)
         p.L, p.alpha, p.kappa, p.dt, p.a0 = float(L), float(alpha), float(kappa), float(dt), float(a0)
         p.stream = C.c_void_p(int(stream)) if stream else None
         keep = []
@@ -218,7 +220,8 @@ class Lattice:
         self.members = len(self.member_N)
         self.N = int(N) if member_N is None else max(self.member_N)
         self.dtype = np.float64 if precision == CL_PREC_FP64 else np.float32
-        self.n = self.member_N[0] ** 3
+        self.dims = int(dims) if dims in (1, 2) else 3
+        self.n = self._sites(0)
 
     def close(self):
         if getattr(self, "h", None):
@@ -241,9 +244,15 @@ class Lattice:
         arr = (C.c_double * len(params))(*[float(x) for x in params])
         _check(self.h, lib().cl_set_potential(self.h, int(kind), arr, len(params)))
 
+    def _shape(self, member):
+        # lattice shape of a member (z, y, x); an out-of-range member is left for the library to reject
+        n = self.member_N[member if 0 <= member < self.members else 0]
+        d = self.dims if self.dims in (1, 2) else 3
+        return (n if d >= 3 else 1, n if d >= 2 else 1, n)
+
     def _sites(self, member):
-        # sites of a member; an out-of-range member is left for the library to reject
-        return self.member_N[member if 0 <= member < self.members else 0] ** 3
+        z, y, x = self._shape(member)
+        return z * y * x
 
     def cl_set_state(self, field, data, member=0):
         ptr, dev, keep = _buffer(data, self.dtype, self._sites(member))
@@ -251,10 +260,9 @@ class Lattice:
 
     def cl_get_state(self, field, out=None, member=0):
         """Return the field at the latest integer time (numpy), or fill `out` (tensor or array)."""
-        n = round(self._sites(member) ** (1.0 / 3.0))
         if out is None:
-            out = np.empty((n, n, n), dtype=self.dtype)
-        ptr, dev, keep = _buffer(out, self.dtype, n ** 3)
+            out = np.empty(self._shape(member), dtype=self.dtype)
+        ptr, dev, keep = _buffer(out, self.dtype, self._sites(member))
         _check(self.h, lib().cl_get_state(self.h, int(member), int(field), ptr, dev))
         return out
 

@@ -76,6 +76,8 @@ struct cl_lattice {
     int u1_dz = 8;                  // planes per block of the U(1) kernels
     bool u1_fused = false;          // U(1) stage as one fused launch (plaquettes in shared memory)
     bool u1_staged = false;         // U(1) launches with shared-memory staged neighbourhoods
+    int dims = 3;                   // spatial dimensions (1, 2: reduced lattice of N^dims sites)
+    int red_grid = 1;               // blocks of the reduced-lattice kernels
     bool nmc = false;               // non-minimal coupling xi phi^2 R of field 0 (Runge-Kutta)
     bool rbar_valid = false;        // scal->rbar holds the Ricci scalar of the current state
     double xi = 0.0;
@@ -128,6 +130,7 @@ int mem_N(const cl_lattice* l, int m) { return is_ens(l) ? l->mN[m] : l->N; }
 int64_t mem_V(const cl_lattice* l, int m)
 {
     const int64_t n = mem_N(l, m);
+    if (!is_ens(l) && l->dims < 3) return l->dims == 1 ? n : n * n;  // reduced lattice
     return n * n * n;
 }
 size_t mem_off_bytes(const cl_lattice* l, int m) { return is_ens(l) ? (size_t)l->moff[m] * l->es : 0; }
@@ -282,6 +285,20 @@ cl_status ens_tiles(cl_lattice* l)
 cl_status choose_tiles(cl_lattice* l)
 {
     if (is_ens(l)) return ens_tiles(l);
+    if (l->dims < 3) {
+        // reduced lattice: one thread per site, at most eight blocks per SM
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+            return fail(l, CL_ECUDA, "cannot query the SM count");
+        const int64_t blocks = (l->V + 255) / 256;
+        l->red_grid = (int)(blocks < 8 * (int64_t)nsm ? blocks : 8 * (int64_t)nsm);
+        l->VW = 1;
+        cl_status s = grow_partials(l, l->red_grid);
+        if (s != CL_OK) return s;
+        invalidate_graphs(l);
+        return CL_OK;
+    }
     const int N = l->N, prec = l->p.precision;
     l->VW = scalar_pass_vector_width(prec, N);
     const int TX = N / l->VW;
@@ -504,8 +521,9 @@ cl_status run_pass_impl(cl_lattice* l, const PassCoef& pc, int in, int out, int*
         A.stages = l->stages;
         A.grid = l->grid;
         A.variant = l->variant;
-        e = occ ? scalar_pass_blocks_per_sm(l->p.precision, l->nf, &A, l->VW, occ)
-                : launch_scalar_pass(l->p.precision, l->nf, &A, l->VW, l->stream);
+        e = l->dims < 3 ? (occ ? (*occ = 1, cudaSuccess) : launch_reduced_pass(l->p.precision, l->nf, &A, l->dims, l->red_grid, l->stream))
+            : occ ? scalar_pass_blocks_per_sm(l->p.precision, l->nf, &A, l->VW, occ)
+                  : launch_scalar_pass(l->p.precision, l->nf, &A, l->VW, l->stream);
     } else {
         ScalarPassArgs<float> A{};
         for (int f = 0; f < l->nf; ++f) {
@@ -528,8 +546,9 @@ cl_status run_pass_impl(cl_lattice* l, const PassCoef& pc, int in, int out, int*
         A.stages = l->stages;
         A.grid = l->grid;
         A.variant = l->variant;
-        e = occ ? scalar_pass_blocks_per_sm(l->p.precision, l->nf, &A, l->VW, occ)
-                : launch_scalar_pass(l->p.precision, l->nf, &A, l->VW, l->stream);
+        e = l->dims < 3 ? (occ ? (*occ = 1, cudaSuccess) : launch_reduced_pass(l->p.precision, l->nf, &A, l->dims, l->red_grid, l->stream))
+            : occ ? scalar_pass_blocks_per_sm(l->p.precision, l->nf, &A, l->VW, occ)
+                  : launch_scalar_pass(l->p.precision, l->nf, &A, l->VW, l->stream);
     }
     if (e != cudaSuccess) return fail(l, CL_ECUDA, "scalar pass launch failed: %s", cudaGetErrorString(e));
     return CL_OK;
@@ -584,8 +603,9 @@ cl_status run_rk_stage_t(cl_lattice* l, const PassCoef& pc, int in, int out)
         cudaError_t e = launch_nmc_ricci(l->p.precision, &A, nmc_grid(l), l->stream);
         if (e != cudaSuccess) return fail(l, CL_ECUDA, "Ricci reduction launch failed: %s", cudaGetErrorString(e));
     }
-    cudaError_t e = l->rk_stages > 0 ? launch_rk_stage_tma(l->p.precision, l->nf, &A, l->VW, l->rk_stages, l->stream)
-                                     : launch_rk_stage(l->p.precision, l->nf, &A, l->VW, l->stream);
+    cudaError_t e = l->dims < 3 ? launch_reduced_rk_stage(l->p.precision, l->nf, &A, l->dims, l->red_grid, l->stream)
+                    : l->rk_stages > 0 ? launch_rk_stage_tma(l->p.precision, l->nf, &A, l->VW, l->rk_stages, l->stream)
+                                       : launch_rk_stage(l->p.precision, l->nf, &A, l->VW, l->stream);
     if (e != cudaSuccess) return fail(l, CL_ECUDA, "Runge-Kutta stage launch failed: %s", cudaGetErrorString(e));
     return CL_OK;
 }
@@ -1045,8 +1065,12 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
     if (p->members < 0) return CL_EINVAL;
     if ((!ens && (p->N < 2 || p->N > kMaxN)) || p->nfields < 1 || p->nfields > 2 || p->precision < 0 || p->precision > 2 ||
         p->integrator < 0 || p->integrator > CL_INT_YOSHIDA10 || p->gauge < 0 || p->gauge > 1 || !(p->L > 0) || !(p->dt > 0) ||
-        !(p->a0 > 0) || p->reserved != 0)
+        !(p->a0 > 0) || p->dims < 0 || p->dims > 3)
         return CL_EINVAL;
+    // reduced (d+1)-dimensional lattices: single lattices of scalar fields
+    if (p->dims == 1 || p->dims == 2) {
+        if (ens || p->gauge != CL_GAUGE_NONE) return CL_EUNSUPPORTED;
+    }
     if (p->gauge == CL_GAUGE_U1_AXION) {
         // the paper integrates the axion-gauge module with Runge-Kutta; one axion field;
         // fields stored in FP64 or plain FP32
@@ -1060,6 +1084,7 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
     l->p.member_L = nullptr;
     l->nf = p->nfields;
     l->es = p->precision == CL_PREC_FP64 ? 8 : 4;
+    l->dims = (p->dims == 1 || p->dims == 2) ? p->dims : 3;
     if (ens) {
         // members back to back in every arena, each on a 256-byte boundary; one vector
         // width for all members (the widest that divides every size)
@@ -1091,7 +1116,7 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
         l->dx = l->mL[0] / l->mN[0];
     } else {
         l->N = p->N;
-        l->V = (int64_t)p->N * p->N * p->N;
+        l->V = l->dims == 1 ? (int64_t)p->N : (l->dims == 2 ? (int64_t)p->N * p->N : (int64_t)p->N * p->N * p->N);
         l->dx = p->L / p->N;
     }
     if (p->stream) {
@@ -1308,6 +1333,7 @@ cl_status cl_set_gauge_coupling(cl_lattice* l, double alphaL, double ws2)
 cl_status cl_set_nonminimal(cl_lattice* l, double xi)
 {
     if (!l) return CL_EINVAL;
+    if (l->dims < 3) return fail(l, CL_EUNSUPPORTED, "the non-minimal coupling is not available on a reduced (1+1)/(2+1) lattice");
     if (is_ens(l) || l->gauge || l->nf != 1 || !is_rk(l->p.integrator))
         return fail(l, CL_EUNSUPPORTED, "the non-minimal coupling needs one scalar field and a Runge-Kutta integrator");
     if (!isfinite(xi)) return fail(l, CL_EINVAL, "xi must be finite");
@@ -1324,6 +1350,7 @@ cl_status cl_set_nonminimal(cl_lattice* l, double xi)
 cl_status cl_enable_gw(cl_lattice* l)
 {
     if (!l) return CL_EINVAL;
+    if (l->dims < 3) return fail(l, CL_EUNSUPPORTED, "the GW sector is not available on a reduced (1+1)/(2+1) lattice");
     if (is_ens(l) || l->gauge || is_rk(l->p.integrator))
         return fail(l, CL_EUNSUPPORTED, "gravitational waves need a single scalar lattice with a leapfrog integrator");
     if (l->gw) return CL_OK;
@@ -1518,6 +1545,7 @@ static cl_status time_trials(cl_lattice* l, int warm, int n, double* us)
 cl_status cl_autotune(cl_lattice* l, const char* cache_path, double* best)
 {
     if (!l) return CL_EINVAL;
+    if (l->dims < 3) return fail(l, CL_EUNSUPPORTED, "the autotuner is not available on a reduced (1+1)/(2+1) lattice");
     if (is_rk(l->p.integrator) || l->gauge) return fail(l, CL_EINVAL, "the autotuner covers the leapfrog pass only");
     if (!l->potential_set) return fail(l, CL_ESTATE, "cl_set_potential has not been called");
     const std::string key = tune_key(l);
@@ -1709,6 +1737,7 @@ cl_status cl_energies(cl_lattice* l, cl_energy* out, int32_t count)
 cl_status cl_init_vacuum(cl_lattice* l, int32_t member, const cl_vacuum_params* v)
 {
     if (!l) return CL_EINVAL;
+    if (l->dims < 3) return fail(l, CL_EUNSUPPORTED, "the vacuum initial condition is not available on a reduced (1+1)/(2+1) lattice");
     if (!v) return fail(l, CL_EINVAL, "vacuum params NULL");
     if (member != -1 && !member_ok(l, member)) return fail(l, CL_EINVAL, "member %d out of range", member);
     if (!l->potential_set) return fail(l, CL_ESTATE, "cl_set_potential has not been called");
@@ -1799,6 +1828,7 @@ cl_status cl_spectrum(cl_lattice* l, int32_t member, int32_t field, double dn, i
                       double* delta_out, double* count_out, int32_t cap, int32_t* nbins)
 {
     if (!l) return CL_EINVAL;
+    if (l->dims < 3) return fail(l, CL_EUNSUPPORTED, "the spectrum is not available on a reduced (1+1)/(2+1) lattice");
     if (!member_ok(l, member)) return fail(l, CL_EINVAL, "member %d out of range", member);
     if (!(dn > 0) || (type != 1 && type != 2) || cap < 0 || (cap > 0 && (!k_out || !delta_out || !count_out)))
         return fail(l, CL_EINVAL, "spectrum: bad arguments");
@@ -1934,6 +1964,7 @@ static Norm3 make_norm(const float* mu, const float* sg, int C)
 cl_status cl_lattice_pack(cl_lattice* l, const float* mu, const float* sg, float* x_dev)
 {
     if (!l) return CL_EINVAL;
+    if (l->dims < 3) return fail(l, CL_EUNSUPPORTED, "the surrogate is not available on a reduced (1+1)/(2+1) lattice");
     if (!mu || !sg || !x_dev) return fail(l, CL_EINVAL, "pack: NULL argument");
     cl_status st = check_sg_lattice(l);
     if (st != CL_OK) return st;
@@ -1949,6 +1980,7 @@ cl_status cl_lattice_pack(cl_lattice* l, const float* mu, const float* sg, float
 cl_status cl_lattice_unpack(cl_lattice* l, const float* mu, const float* sg, const float* y_dev)
 {
     if (!l) return CL_EINVAL;
+    if (l->dims < 3) return fail(l, CL_EUNSUPPORTED, "the surrogate is not available on a reduced (1+1)/(2+1) lattice");
     if (!mu || !sg || !y_dev) return fail(l, CL_EINVAL, "unpack: NULL argument");
     cl_status st = check_sg_lattice(l);
     if (st != CL_OK) return st;
@@ -1965,6 +1997,7 @@ cl_status cl_surrogate_jump(cl_surrogate* s, cl_lattice* l, int32_t steps, const
                             double hubble_limit, int32_t* accepted)
 {
     if (!l) return CL_EINVAL;
+    if (l->dims < 3) return fail(l, CL_EUNSUPPORTED, "the surrogate jump is not available on a reduced (1+1)/(2+1) lattice");
     if (!s || !mu || !sg || !accepted || steps < 1) return fail(l, CL_EINVAL, "jump: bad arguments");
     cl_status st = check_sg_lattice(l);
     if (st != CL_OK) return st;

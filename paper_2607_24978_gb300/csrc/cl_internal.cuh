@@ -72,6 +72,9 @@ struct ScalarPassArgs {
 // Launch one fused scalar pass (drift -> stencil kick -> energies -> scale-factor update).
 // Returns the CUDA error of the launch.
 cudaError_t launch_scalar_pass(int precision, int nf, const void* args, int vw, cudaStream_t s);
+// The same pass on a reduced lattice of N^dims sites (dims = 1, 2), `grid` blocks of 256
+// threads (partials[grid][kMaxQ]).
+cudaError_t launch_reduced_pass(int precision, int nf, const void* args, int dims, int grid, cudaStream_t s);
 // Resident blocks per SM of the pass configured by args (tiles, stages).
 cudaError_t scalar_pass_blocks_per_sm(int precision, int nf, const void* args, int vw, int* blocks);
 int scalar_pass_vector_width(int precision, int N);

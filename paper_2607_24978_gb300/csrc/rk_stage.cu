@@ -29,7 +29,7 @@ namespace clk {
 template <typename T>
 __device__ __forceinline__ void rk_finish(const RkStageArgs<T>& A, double (&v)[kMaxQ], double a_old, bool first,
                                           double (*s_red)[kMaxQ], int* s_last, int tid, int nthr,
-                                          double (*v2)[kMaxQ] = nullptr)
+                                          double (*v2)[kMaxQ] = nullptr, int dims = 3)
 {
     const int N = A.N;
     block_reduce<kMaxQ>(v, s_red, tid, nthr);
@@ -63,7 +63,7 @@ __device__ __forceinline__ void rk_finish(const RkStageArgs<T>& A, double (&v)[k
     }
     if (tid == 0) {
         DevScal* S = A.scal;
-        const double vol = (double)N * N * N;
+        const double vol = dims == 1 ? (double)N : (dims == 2 ? (double)N * N : (double)N * N * N);
         const double a = a_old, b = S->b;
         const double a2 = a * a, a6 = a2 * a2 * a2;
         const double K0 = w[0] / (2.0 * a6 * vol), K1 = w[1] / (2.0 * a6 * vol);
@@ -607,6 +607,96 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
     rk_finish(A, v, s_coef[3], first, s_red, &s_last, tid, nthr, fuse_r ? &v2 : nullptr);
 }
 
+// The stage on a reduced (d+1)-dimensional lattice (section "Scalar dynamics in 1+1 and 2+1
+// dimensions"): N^d sites (d = 1, 2; x fastest), the Laplacian and the gradient energy over
+// the d directions; one thread per site, grid-stride, the per-site arithmetic of k_rk_stage.
+template <typename T, int NF, bool KAHAN>
+__global__ void __launch_bounds__(256) k_reduced_rk(const RkStageArgs<T> A, int dims)
+{
+    __shared__ double s_coef[5];
+    __shared__ double s_red[32][kMaxQ];
+    __shared__ int s_last;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const bool first = (A.flags & P_FIRST_STAGE) != 0;
+    if (tid == 0) {
+        const double a = A.scal->a;
+        s_coef[0] = A.h * pow(a, A.alpha - 3.0);
+        s_coef[1] = A.h * pow(a, 1.0 + A.alpha) / (A.dx * A.dx);
+        s_coef[2] = A.h * pow(a, 3.0 + A.alpha);
+        s_coef[3] = a;
+        s_coef[4] = 0.0;
+    }
+    __syncthreads();
+    const T cphi = (T)s_coef[0], cL = (T)s_coef[1], cV = (T)s_coef[2];
+    const T cA = (T)A.A, cB = (T)A.B;
+    const PotCoef<T> P(A.m2, A.lam, A.g2);
+    const long long N = A.N, V = dims == 1 ? N : N * N;
+    Acc<T> accK[NF], accG[NF], accV;
+    for (long long n = blockIdx.x * (long long)nthr + tid; n < V; n += (long long)gridDim.x * nthr) {
+        const long long x = n % N, row = n - x;
+        const long long xm = row + (x == 0 ? N - 1 : x - 1), xp = row + (x + 1 == N ? 0 : x + 1);
+        long long ym = 0, yp = 0;
+        if (dims == 2) {
+            const long long y = n / N;
+            ym = (y == 0 ? N - 1 : y - 1) * N + x;
+            yp = (y + 1 == N ? 0 : y + 1) * N + x;
+        }
+        T phc[NF], lap[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const T* ph = f == 0 ? A.phi_in[0] : A.phi_in[NF - 1];
+            const T c = ph[n], xpv = ph[xp], xmv = ph[xm];
+            T g = (xpv - c) * (xpv - c);
+            if (dims == 2) {
+                const T ypv = ph[yp], ymv = ph[ym];
+                lap[f] = ((xpv + xmv) + (ypv + ymv)) - (T)4 * c;
+                g += (ypv - c) * (ypv - c);
+            } else {
+                lap[f] = (xpv + xmv) - (T)2 * c;
+            }
+            accG[f].add(g);
+            phc[f] = c;
+        }
+        const T p0 = phc[0], p1 = NF > 1 ? phc[NF - 1] : (T)0;
+        T vsum = (T)0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const T pv = (f == 0 ? A.pi_in[0] : A.pi_in[NF - 1])[n];
+            T kf = first ? (T)0 : (f == 0 ? A.kphi_in[0] : A.kphi_in[NF - 1])[n];
+            T kp = first ? (T)0 : (f == 0 ? A.kpi_in[0] : A.kpi_in[NF - 1])[n];
+            T cv = KAHAN ? (f == 0 ? A.c_in[0] : A.c_in[NF - 1])[n] : (T)0;
+            T dV;
+            if (f == 0) dV = p0 * (P.m20 + P.l0 * p0 * p0 + (NF > 1 ? P.g2 * p1 * p1 : (T)0));
+            else dV = p1 * (P.m21 + P.l1 * p1 * p1 + P.g2 * p0 * p0);
+            const T fphi = cphi * pv;
+            const T fpi = cL * lap[f] - cV * dV;
+            kf = first ? fphi : cA * kf + fphi;
+            kp = first ? fpi : cA * kp + fpi;
+            T phn = phc[f];
+            drift<T, KAHAN>(phn, cv, kf, cB);  // phi += B k_phi (compensated in FP32)
+            accK[f].add(pv * pv);
+            (f == 0 ? A.phi_out[0] : A.phi_out[NF - 1])[n] = phn;
+            (f == 0 ? A.pi_out[0] : A.pi_out[NF - 1])[n] = pv + cB * kp;
+            (f == 0 ? A.kphi_out[0] : A.kphi_out[NF - 1])[n] = kf;
+            (f == 0 ? A.kpi_out[0] : A.kpi_out[NF - 1])[n] = kp;
+            if (KAHAN) (f == 0 ? A.c_out[0] : A.c_out[NF - 1])[n] = cv;
+            if (f == 0) {
+                T v = p0 * p0 * (P.h_m20 + P.q_l0 * p0 * p0);
+                if (NF > 1) v += p1 * p1 * (P.h_m21 + P.q_l1 * p1 * p1) + P.h_g2 * p0 * p0 * p1 * p1;
+                vsum += v;
+            }
+        }
+        accV.add(vsum);
+    }
+    double v[kMaxQ];
+    v[0] = accK[0].value();
+    v[1] = NF > 1 ? accK[NF - 1].value() : 0.0;
+    v[2] = accG[0].value();
+    v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
+    v[4] = accV.value();
+    rk_finish(A, v, s_coef[3], first, s_red, &s_last, tid, nthr, nullptr, dims);
+}
+
 // Background Ricci scalar of a non-minimally coupled field (section "Scalar fields
 // non-minimally coupled to gravity", Eq. eomR in program units):
 //   R = kappa F [(1 - 6 xi) (2 G - 2 K) + 4 <V> - 6 xi <phi V'>],  F = 1 / (1 + (6 xi - 1) xi kappa <phi^2>),
@@ -823,6 +913,31 @@ cudaError_t launch_rk_stage_tma(int precision, int nf, const void* args, int vw,
     if (precision == CL_PREC_FP32_KAHAN)
         return nf == 1 ? launch_rk_tma<float, 1, true, 4>(A, stages, s) : launch_rk_tma<float, 2, true, 4>(A, stages, s);
     return nf == 1 ? launch_rk_tma<float, 1, false, 4>(A, stages, s) : launch_rk_tma<float, 2, false, 4>(A, stages, s);
+}
+
+template <typename T, int NF, bool KAHAN>
+static cudaError_t launch_reduced_rk_t(const RkStageArgs<T>& A, int dims, int grid, cudaStream_t s)
+{
+    k_reduced_rk<T, NF, KAHAN><<<grid, 256, 0, s>>>(A, dims);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduced_rk_stage(int precision, int nf, const void* args, int dims, int grid, cudaStream_t s)
+{
+    if ((dims != 1 && dims != 2) || grid < 1) return cudaErrorInvalidValue;
+    if (precision == CL_PREC_FP64) {
+        const auto& A = *static_cast<const RkStageArgs<double>*>(args);
+        if (A.nmc) return cudaErrorInvalidValue;
+        return nf == 1 ? launch_reduced_rk_t<double, 1, false>(A, dims, grid, s)
+                       : launch_reduced_rk_t<double, 2, false>(A, dims, grid, s);
+    }
+    const auto& A = *static_cast<const RkStageArgs<float>*>(args);
+    if (A.nmc) return cudaErrorInvalidValue;
+    if (precision == CL_PREC_FP32_KAHAN)
+        return nf == 1 ? launch_reduced_rk_t<float, 1, true>(A, dims, grid, s)
+                       : launch_reduced_rk_t<float, 2, true>(A, dims, grid, s);
+    return nf == 1 ? launch_reduced_rk_t<float, 1, false>(A, dims, grid, s)
+                   : launch_reduced_rk_t<float, 2, false>(A, dims, grid, s);
 }
 
 }  // namespace clk

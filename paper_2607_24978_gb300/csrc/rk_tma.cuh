@@ -15,5 +15,8 @@ size_t rk_stage_tma_smem(int precision, int nf, int N, int BY, int stages, bool 
 // writes the background Ricci scalar of its output state to scal->rbar (partials: two sets of
 // kMaxQ per block).
 cudaError_t launch_rk_stage_tma(int precision, int nf, const void* args, int vw, int stages, cudaStream_t s);
+// One stage on a reduced lattice of N^dims sites (dims = 1, 2; no non-minimal coupling),
+// `grid` blocks of 256 threads (partials[grid][kMaxQ]).
+cudaError_t launch_reduced_rk_stage(int precision, int nf, const void* args, int dims, int grid, cudaStream_t s);
 
 }  // namespace clk

@@ -41,11 +41,12 @@
 
 namespace clk {
 
-// Block partials, last-block-done fixed-order reduction and the scalar update.
+// Block partials, last-block-done fixed-order reduction and the scalar update (vol: the
+// lattice's sites).
 template <typename T, int NF>
-__device__ __forceinline__ void finish_pass(const ScalarPassArgs<T>& A, Acc<T> (&accK)[NF], Acc<T> (&accG)[NF],
-                                            Acc<T>& accV, const double* s_coef, double (*s_red)[kMaxQ],
-                                            int* s_last, int tid, int nthr, int timeout)
+__device__ __forceinline__ void finish_pass_vol(const ScalarPassArgs<T>& A, Acc<T> (&accK)[NF], Acc<T> (&accG)[NF],
+                                                Acc<T>& accV, const double* s_coef, double (*s_red)[kMaxQ],
+                                                int* s_last, int tid, int nthr, int timeout, double vol)
 {
     double v[kMaxQ];
     v[0] = accK[0].value();
@@ -74,8 +75,16 @@ __device__ __forceinline__ void finish_pass(const ScalarPassArgs<T>& A, Acc<T> (
         for (int q = 0; q < kMaxQ; ++q) w[q] += __ldcg(&A.partials[(size_t)b * kMaxQ + q]);
     block_reduce<kMaxQ>(w, s_red, tid, nthr);
     if (tid == 0)
-        scalar_epilogue(A.scal, w, (double)A.N * A.N * A.N, A.dx, s_coef[3], A.alpha, A.kappa, A.d, A.e, A.k, A.flags,
-                        A.hubble_limit);
+        scalar_epilogue(A.scal, w, vol, A.dx, s_coef[3], A.alpha, A.kappa, A.d, A.e, A.k, A.flags, A.hubble_limit);
+}
+
+// The same for an N^3 lattice.
+template <typename T, int NF>
+__device__ __forceinline__ void finish_pass(const ScalarPassArgs<T>& A, Acc<T> (&accK)[NF], Acc<T> (&accG)[NF],
+                                            Acc<T>& accV, const double* s_coef, double (*s_red)[kMaxQ],
+                                            int* s_last, int tid, int nthr, int timeout)
+{
+    finish_pass_vol<T, NF>(A, accK, accG, accV, s_coef, s_red, s_last, tid, nthr, timeout, (double)A.N * A.N * A.N);
 }
 
 // ------------------------------------------------------------------ general loader
@@ -119,6 +128,104 @@ __global__ void __launch_bounds__(512) k_scalar_pass(const ScalarPassArgs<T> A)
 
 #include "scalar_pass_tma.cuh"
 #include "scalar_pass_tma_nr.cuh"
+
+// ------------------------------------------------------------------ reduced lattices
+// The fused pass on a reduced (d+1)-dimensional lattice (section "Scalar dynamics in 1+1 and
+// 2+1 dimensions"): N^d sites (d = 1, 2; x fastest), the Laplacian and the gradient energy
+// summed over the d directions, everything else as on N^3 sites.  One thread per site,
+// grid-stride: the old field is drifted at the site and again at each of its 2d neighbours
+// (the same compensated operations as the owning thread), then kicked.
+template <typename T, int NF, bool KAHAN>
+__global__ void __launch_bounds__(256) k_reduced_pass(const ScalarPassArgs<T> A, int dims)
+{
+    __shared__ double s_coef[4];
+    __shared__ double s_red[32][kMaxQ];
+    __shared__ int s_last;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    if (tid == 0) pass_coefficients(A.scal->a, A.scal->b, A.d, A.alpha, A.dx, (A.flags & P_EXPANSION) != 0, s_coef);
+    __syncthreads();
+    const T cd = (T)s_coef[0], cL = (T)s_coef[1], cV = (T)s_coef[2], ce = (T)A.e, ck = (T)A.k;
+    const bool do_drift = (A.flags & P_DRIFT) != 0;
+    const PotCoef<T> P(A.m2, A.lam, A.g2);
+    const long long N = A.N, V = dims == 1 ? N : N * N;
+    Acc<T> accK[NF], accG[NF], accV;
+    // field f (constant-index selects of the argument arrays) drifted at site m
+    auto drifted = [&](int f, long long m, T& cv, T& pv) {
+        const T* ph_in = f == 0 ? A.phi_in[0] : A.phi_in[NF - 1];
+        const T* pi_in = f == 0 ? A.pi_in[0] : A.pi_in[NF - 1];
+        const T* c_in = f == 0 ? A.c_in[0] : A.c_in[NF - 1];
+        T ph = ph_in[m];
+        pv = pi_in[m];
+        cv = KAHAN ? c_in[m] : (T)0;
+        if (do_drift) drift<T, KAHAN>(ph, cv, pv, cd);
+        return ph;
+    };
+    for (long long n = blockIdx.x * (long long)nthr + tid; n < V; n += (long long)gridDim.x * nthr) {
+        const long long x = n % N, row = n - x;
+        const long long xm = row + (x == 0 ? N - 1 : x - 1), xp = row + (x + 1 == N ? 0 : x + 1);
+        long long ym = 0, yp = 0;
+        if (dims == 2) {
+            const long long y = n / N;
+            ym = (y == 0 ? N - 1 : y - 1) * N + x;
+            yp = (y + 1 == N ? 0 : y + 1) * N + x;
+        }
+        T phc[NF], lap[NF], pin[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            T cv, pv, c2, p2;
+            const T c = drifted(f, n, cv, pv);
+            const T xpv = drifted(f, xp, c2, p2), xmv = drifted(f, xm, c2, p2);
+            T g = (xpv - c) * (xpv - c);
+            if (dims == 2) {
+                const T ypv = drifted(f, yp, c2, p2), ymv = drifted(f, ym, c2, p2);
+                lap[f] = ((xpv + xmv) + (ypv + ymv)) - (T)4 * c;
+                g += (ypv - c) * (ypv - c);
+            } else {
+                lap[f] = (xpv + xmv) - (T)2 * c;
+            }
+            accG[f].add(g);
+            phc[f] = c;
+            pin[f] = pv;
+            (f == 0 ? A.phi_out[0] : A.phi_out[NF - 1])[n] = c;
+            if (KAHAN) (f == 0 ? A.c_out[0] : A.c_out[NF - 1])[n] = cv;
+        }
+        const T p0 = phc[0], p1 = NF > 1 ? phc[NF - 1] : (T)0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            T dV;
+            if (f == 0) dV = p0 * (P.m20 + P.l0 * p0 * p0 + (NF > 1 ? P.g2 * p1 * p1 : (T)0));
+            else dV = p1 * (P.m21 + P.l1 * p1 * p1 + P.g2 * p0 * p0);
+            const T F = cL * lap[f] - cV * dV;
+            const T pe = pin[f] + ce * F;
+            accK[f].add(pe * pe);
+            (f == 0 ? A.pi_out[0] : A.pi_out[NF - 1])[n] = pin[f] + ck * F;
+        }
+        T v = p0 * p0 * (P.h_m20 + P.q_l0 * p0 * p0);
+        if (NF > 1) v += p1 * p1 * (P.h_m21 + P.q_l1 * p1 * p1) + P.h_g2 * p0 * p0 * p1 * p1;
+        accV.add(v);
+    }
+    finish_pass_vol<T, NF>(A, accK, accG, accV, s_coef, s_red, &s_last, tid, nthr, 0, (double)V);
+}
+
+template <typename T, int NF, bool KAHAN>
+static cudaError_t launch_reduced_t(const ScalarPassArgs<T>& A, int dims, int grid, cudaStream_t s)
+{
+    k_reduced_pass<T, NF, KAHAN><<<grid, 256, 0, s>>>(A, dims);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduced_pass(int precision, int nf, const void* args, int dims, int grid, cudaStream_t s)
+{
+    if ((dims != 1 && dims != 2) || grid < 1) return cudaErrorInvalidValue;
+    if (precision == CL_PREC_FP64) {
+        const auto& A = *static_cast<const ScalarPassArgs<double>*>(args);
+        return nf == 1 ? launch_reduced_t<double, 1, false>(A, dims, grid, s) : launch_reduced_t<double, 2, false>(A, dims, grid, s);
+    }
+    const auto& A = *static_cast<const ScalarPassArgs<float>*>(args);
+    if (precision == CL_PREC_FP32_KAHAN)
+        return nf == 1 ? launch_reduced_t<float, 1, true>(A, dims, grid, s) : launch_reduced_t<float, 2, true>(A, dims, grid, s);
+    return nf == 1 ? launch_reduced_t<float, 1, false>(A, dims, grid, s) : launch_reduced_t<float, 2, false>(A, dims, grid, s);
+}
 
 // ------------------------------------------------------------------ launchers
 size_t scalar_pass_smem_bytes(int precision, int nf, int N, int BY, int stages, int variant)

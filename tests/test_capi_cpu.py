@@ -46,11 +46,21 @@ def _params(cl, **kw):
 
 
 @pytest.mark.parametrize("kw", [dict(N=1), dict(N=100000), dict(nfields=3), dict(precision=7), dict(integrator=9),
-                                dict(L=0.0), dict(dt=-1.0), dict(a0=0.0), dict(reserved=1), dict(gauge=5)])
+                                dict(L=0.0), dict(dt=-1.0), dict(a0=0.0), dict(dims=4), dict(dims=-1),
+                                dict(gauge=5)])
 def test_init_rejects_bad_params(cl, kw):
     h = C.c_void_p(123)
     s = cl.lib().cl_init_lattice(C.byref(h), C.byref(_params(cl, **kw)))
     assert s == cl.CL_EINVAL
+    assert not h.value
+
+
+@pytest.mark.parametrize("kw", [dict(dims=2, gauge=1, integrator=2), dict(dims=1, gauge=1, integrator=3)])
+def test_reduced_lattices_refuse_gauge_fields(cl, kw):
+    """The (1+1) / (2+1)-dimensional lattices carry scalar fields only."""
+    h = C.c_void_p(123)
+    s = cl.lib().cl_init_lattice(C.byref(h), C.byref(_params(cl, **kw)))
+    assert s == cl.CL_EUNSUPPORTED
     assert not h.value
 
 
