@@ -30,6 +30,10 @@ Other workloads (--workload; one JSON line each, same keys where they apply):
             (32^3) and the judged jumps on a fresh lattice: acceptance under the 1e-3
             Hubble limit, binned-spectrum error against the plain leapfrog, wall time
             (the surrogate speed-up at 1 % error, when reached).
+  rk        the headline lattice advanced by RK4-5 (2N) stages.
+  gw        the headline plus the five traceless GW auxiliaries, Yoshida-4.
+  nmc       one non-minimally coupled lambda phi^4 field (xi = 0.3), 256^3, RK4-5.
+  reduced   the headline's model on a (2+1)-dimensional 4096^2 lattice, Yoshida-4.
 """
 import argparse
 import json
@@ -379,6 +383,52 @@ def run_rk_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_
             "energies_end": {"a": e["a"], "rho": e["rho"], "hubble_violation": e["hubble_violation"]}}
 
 
+def run_reduced_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src):
+    """The headline's two-field model on a reduced (2+1)-dimensional lattice of 4096^2 sites
+    (as many as 256^3), Yoshida-4, FP32 + Kahan: one launch of the reduced-lattice pass per
+    pass.  The reduced lattices take no vacuum initial condition, so the state is the
+    homogeneous phi = 1 plus seeded Gaussian noise of rms 1e-4 (phi, chi, their momenta)."""
+    import numpy as np
+    N2 = 4096
+    L2 = 2048.0 * math.pi  # the headline's lattice spacing, pi / 32
+    g = cl.Lattice(N2, L2, 2, cl.CL_PREC_FP32_KAHAN, cl.CL_INT_YOSHIDA4, expansion=True, alpha=ALPHA, kappa=KAPPA,
+                   dt=DT, stream=stream.cuda_stream, dims=2)
+    g.cl_set_potential(cl.CL_POT_M2_G2, [1.0, G2])
+    rng = np.random.default_rng(SEED)
+    for f, (field, mom) in enumerate(((cl.CL_FIELD_PHI0, cl.CL_FIELD_PI0), (cl.CL_FIELD_PHI1, cl.CL_FIELD_PI1))):
+        g.cl_set_state(field, ((1.0 if f == 0 else 0.0) + 1e-4 * rng.standard_normal((1, N2, N2))).astype(np.float32))
+        g.cl_set_state(mom, (1e-4 * rng.standard_normal((1, N2, N2))).astype(np.float32))
+    g.cl_set_scalars(1.0)
+    g.cl_step(args.warmup)
+    g.cl_sync()
+    barrier(world)
+    el, launches, clocks = timed_region(torch, g, stream, args.steps)
+    barrier(world)
+    el_max = max_over_ranks(el, world)
+    e = g.cl_energies()
+    g.close()
+    sites = N2 * N2
+    pass_s = el / (args.steps * PASSES_PER_STEP)
+    bytes_pass = sites * BYTES_PER_SITE_PASS
+    achieved = bytes_pass / pass_s / 1e9
+    return {"metric": "Gsite-updates/s, (2+1)-dimensional 4096^2 two fields, Yoshida-4",
+            "value": world * sites * args.steps / el_max / 1e9,
+            "unit": "Gsite-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config({"workload": "two-field m2phi2+g2phi2chi2, q=1e4, reduced (2+1)-dimensional lattice "
+                                          "4096^2, dx = pi/32, Yoshida-4, FP32+Kahan, FP64 reductions, dt=0.005, "
+                                          "homogeneous phi=1 + noise 1e-4, self-consistent expansion",
+                              "lattice": N2, "dims": 2, "integrator": "yoshida4", "passes_per_step": PASSES_PER_STEP,
+                              "l2": "inputs (%.0f MB) larger than L2; no flush" % (sites * 24 / 1e6)}),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                         "kernel": "k_reduced_pass<float,2,kahan> (mean per pass)",
+                         "algorithmic_bytes_per_launch": bytes_pass},
+            "gpu_launches": launches, "clocks": clocks,
+            "energies_end": {"a": e["a"], "rho": e["rho"], "hubble_violation": e["hubble_violation"]}}
+
+
 def run_gw_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src):
     """The headline two-field lattice with the gravitational-wave auxiliaries: every Yoshida-4
     pass is a GW pass (k_gw_pass) and the fused scalar pass."""
@@ -663,7 +713,7 @@ def run_gpu(args, world, rank, local):
         return
     if args.workload != "preheat":
         fn = {"u1": run_u1_workload, "rk": run_rk_workload, "gw": run_gw_workload,
-              "nmc": run_nmc_workload}.get(args.workload, run_ensemble_workload)
+              "nmc": run_nmc_workload, "reduced": run_reduced_workload}.get(args.workload, run_ensemble_workload)
         line = fn(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src)
         if rank == 0:
             print(json.dumps(line), flush=True)
@@ -759,7 +809,7 @@ def main():
     ap.add_argument("--by", type=int, default=None, help="override CL_OPT_TILE_BY")
     ap.add_argument("--dz", type=int, default=None, help="override CL_OPT_TILE_DZ")
     ap.add_argument("--variant", type=int, default=None, help="override CL_OPT_PASS_VARIANT (0 ring, 1 ringless)")
-    ap.add_argument("--workload", default="preheat", choices=["preheat", "u1", "ensemble", "surrogate", "rk", "gw", "nmc"],
+    ap.add_argument("--workload", default="preheat", choices=["preheat", "u1", "ensemble", "surrogate", "rk", "gw", "nmc", "reduced"],
                     help="preheat: the headline 256^3 two-field run; u1, ensemble: the other workloads")
     ap.add_argument("--members", type=int, default=None, help="ensemble size (default 1024)")
     ap.add_argument("--no-train", action="store_true", help="surrogate workload: throughput only")

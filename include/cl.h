@@ -104,7 +104,8 @@ enum {
  * fields of member m hold member_N[m]^3 elements.  Errors at creation: CL_EINVAL (sizes),
  * CL_EUNSUPPORTED (Runge-Kutta or gauge ensembles). */
 typedef struct {
-    int32_t N;            /* sites per side, 2 <= N <= 1536 (single lattice)                */
+    int32_t N;            /* sites per side, 2 <= N <= 1536 (single lattice; reduced      */
+                          /* lattices: N <= 46340 for dims 2, N <= 2^30 for dims 1)          */
     int32_t nfields;      /* scalar fields, 1 or 2 (1 when gauge = CL_GAUGE_U1_AXION)       */
     int32_t precision;    /* CL_PREC_*                                                      */
     int32_t integrator;   /* CL_INT_*                                                       */

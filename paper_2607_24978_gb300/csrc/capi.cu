@@ -1063,7 +1063,10 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
         }
     }
     if (p->members < 0) return CL_EINVAL;
-    if ((!ens && (p->N < 2 || p->N > kMaxN)) || p->nfields < 1 || p->nfields > 2 || p->precision < 0 || p->precision > 2 ||
+    // largest N: 32-bit site indices for N^3 lattices; N^2 < 2^31 on the (2+1) lattice
+    const int dims_in = (p->dims == 1 || p->dims == 2) ? p->dims : 3;
+    const long long max_n = dims_in == 3 ? kMaxN : (dims_in == 2 ? 46340 : (1ll << 30));
+    if ((!ens && (p->N < 2 || p->N > max_n)) || p->nfields < 1 || p->nfields > 2 || p->precision < 0 || p->precision > 2 ||
         p->integrator < 0 || p->integrator > CL_INT_YOSHIDA10 || p->gauge < 0 || p->gauge > 1 || !(p->L > 0) || !(p->dt > 0) ||
         !(p->a0 > 0) || p->dims < 0 || p->dims > 3)
         return CL_EINVAL;
