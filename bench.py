@@ -808,7 +808,8 @@ def main():
     ap.add_argument("--stages", type=int, default=None, help="override CL_OPT_STAGES")
     ap.add_argument("--by", type=int, default=None, help="override CL_OPT_TILE_BY")
     ap.add_argument("--dz", type=int, default=None, help="override CL_OPT_TILE_DZ")
-    ap.add_argument("--variant", type=int, default=None, help="override CL_OPT_PASS_VARIANT (0 ring, 1 ringless)")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="override CL_OPT_PASS_VARIANT (scalar pass: 0 ring, 1 ringless; U(1): 0 gather, 1 fused, 2 staged)")
     ap.add_argument("--workload", default="preheat", choices=["preheat", "u1", "ensemble", "surrogate", "rk", "gw", "nmc", "reduced"],
                     help="preheat: the headline 256^3 two-field run; u1, ensemble: the other workloads")
     ap.add_argument("--members", type=int, default=None, help="ensemble size (default 1024)")
