@@ -1652,7 +1652,9 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
         if (s != CL_OK) return s;
         l->last_launches += 1;
     }
-    if (nmc_f) l->rbar_valid = true;
+    // the fused stages leave R of the final state behind; stages with a reduction launch leave
+    // that of their last input state
+    l->rbar_valid = nmc_f;
     for (int i = 0; i < nsteps; ++i) {
         if (l->use_graph) {
             const int par = l->cur;
