@@ -393,8 +393,9 @@ cl_status choose_tiles(cl_lattice* l)
     if (is_rk(l->p.integrator) && l->VW * l->es == 16 && N % l->VW == 0 && l->opt_stages != -1) {
         // TMA-staged Runge-Kutta kernel (the library's choice for 16-byte vectors): up to 448
         // consumer threads, the tallest tile whose stage ring holds three or more stages (the
-        // deepest that fits), one block per SM.  Measured at 256^3, two fields, FP32 + Kahan, RK4-5: 7 rows x 3
-        // stages 13.8 Gsite-updates/s, 5 x 4 13.5, 4 x 5 12.8; the direct-load kernel 9.7.
+        // deepest that fits), one block per SM.  Measured at 256^3, two fields, FP32 + Kahan,
+        // RK4-5 (persistent ranges): 7 rows x 3 stages 13.8 Gsite-updates/s, 5 x 4 13.5, 4 x 5
+        // 12.8; the direct-load kernel 9.7.
         // CL_OPT_TILE_BY / CL_OPT_STAGES / CL_OPT_TILE_DZ override.
         int by_max = 448 / TX < 1 ? 1 : 448 / TX;
         if (by_max > N) by_max = N;
