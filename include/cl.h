@@ -339,8 +339,10 @@ cl_status cl_autotune(cl_lattice* l, const char* cache_path, double* best);
  * Scratch (block partials of the energy reduction, the arrival counter, the working copy of
  * a, a', t) lives in one fixed array of static device memory inside the library, 327,936
  * bytes (320 KiB), which every GPU that loads the library holds until the process exits.  It limits a
- * pass to 8192 blocks of the direct-load kernel, which covers every N the library accepts;
- * a request it cannot serve returns CL_EINVAL.  The first call on a device looks up that
+ * pass to 8192 blocks of the direct-load kernel (larger lattices march more planes per block).
+ * A row of the lattice must fit one 512-thread block, as for cl_step: odd N up to 511, even N
+ * up to 1024, and in FP32 multiples of 4 up to 1536; other sizes return CL_EINVAL before any
+ * work is queued.  The first call on a device looks up that
  * array's device address (with the device current); make that first call before any stream
  * capture.  All calls share the array and each clears what must start at zero: calls whose
  * GPU work overlaps (other streams, other host threads) race and must be serialised by the
@@ -351,7 +353,12 @@ cl_status cl_autotune(cl_lattice* l, const char* cache_path, double* best);
  * Kahan compensations) are used with CL_PREC_FP32_KAHAN only.  scalars: device, 3 doubles
  * {a, a', t}, read and then overwritten with the values after the pass.  energies: device,
  * 14 doubles {t, a, a', K0, K1, G0, G1, V, KE, GB, rho, p, hubble_violation, gauss_violation}
- * at the pass's integer time, or NULL.  Errors: CL_EINVAL (bad descriptor), CL_ECUDA. */
+ * at the pass's integer time, or NULL.  status: device, one int32 or NULL; receives the pass's
+ * status bits (1: a non-finite energy, as CL_ENAN reports for cl_step).  The call queues work
+ * and returns before it runs, so it cannot report that condition itself: read status (or check
+ * that energies[rho] is finite) after the stream has run.  Every array must be device (or
+ * managed) memory of the current device; no output may overlap an input or another output.
+ * Errors: CL_EINVAL (bad descriptor, host pointer, overlapping arrays), CL_ECUDA. */
 typedef struct {
     int32_t N, nfields, precision, expansion;
     double L, alpha, kappa;
@@ -366,6 +373,7 @@ typedef struct {
     double* scalars;
     double* energies;
     void* stream;                       /* cudaStream_t, NULL = legacy default stream */
+    int32_t* status;                    /* device, optional: status bits of the pass */
 } cl_pass_noalloc_desc;
 cl_status cl_fused_pass_noalloc(const cl_pass_noalloc_desc* d);
 

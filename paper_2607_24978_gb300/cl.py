@@ -74,7 +74,7 @@ class cl_pass_noalloc_desc(C.Structure):
                 ("drift", C.c_double), ("energy_kick", C.c_double), ("kick", C.c_double),
                 ("phi_in", C.c_void_p * 2), ("pi_in", C.c_void_p * 2), ("c_in", C.c_void_p * 2),
                 ("phi_out", C.c_void_p * 2), ("pi_out", C.c_void_p * 2), ("c_out", C.c_void_p * 2),
-                ("scalars", C.c_void_p), ("energies", C.c_void_p), ("stream", C.c_void_p)]
+                ("scalars", C.c_void_p), ("energies", C.c_void_p), ("stream", C.c_void_p), ("status", C.c_void_p)]
 
 
 class cl_surrogate_params(C.Structure):

@@ -4,9 +4,38 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/cl.h"
 
 namespace clk {
+
+// A set-once flag kept per CUDA device, for kernel attributes (a function attribute
+// set with one device current does not carry over to another device).  Reading and
+// setting it refer to the current device; devices numbered 64 and above always read
+// false, so their attribute is set again on every call.
+struct DevFlag {
+    std::atomic<unsigned long long> bits{0ull};
+    static int current()
+    {
+        int d = 0;
+        return cudaGetDevice(&d) == cudaSuccess ? d : 64;
+    }
+    operator bool() const
+    {
+        const int d = current();
+        return d < 64 && ((bits.load(std::memory_order_acquire) >> d) & 1ull);
+    }
+    DevFlag& operator=(bool v)
+    {
+        const int d = current();
+        if (d < 64) {
+            if (v) bits.fetch_or(1ull << d, std::memory_order_acq_rel);
+            else bits.fetch_and(~(1ull << d), std::memory_order_acq_rel);
+        }
+        return *this;
+    }
+};
 
 // Status bits of the device status word.
 enum : int { ST_NAN = 1, ST_CONSTRAINT = 2, ST_TIMEOUT = 4 };

@@ -270,7 +270,7 @@ static cudaError_t ens_smem_attr(K kernel)
 
 template <typename K, typename T>
 static cudaError_t ens_launch(K kernel, int threads, const void* args, int grid, size_t smem, cudaStream_t s,
-                              int* occ, bool& attr)
+                              int* occ, DevFlag& attr)
 {
     if (!attr) {
         cudaError_t e = ens_smem_attr(kernel);
@@ -286,7 +286,7 @@ static cudaError_t ens_launch(K kernel, int threads, const void* args, int grid,
 template <typename T, int NF, bool KAHAN, int VW>
 static cudaError_t ens_one(const void* args, int stages, int variant, int grid, size_t smem, cudaStream_t s, int* occ)
 {
-    static bool attr[2][7] = {};
+    static DevFlag attr[2][7];
     if (stages <= 0) return ens_launch<decltype(&k_ensemble_pass<T, NF, KAHAN, VW>), T>(
         k_ensemble_pass<T, NF, KAHAN, VW>, kEnsThreads, args, grid, smem, s, occ, attr[0][0]);
     if constexpr (VW * sizeof(T) == 16) {  // 16-byte vectors: every member row is a 16-byte multiple

@@ -176,7 +176,7 @@ template <typename T, int NF, bool KAHAN, int VW>
 static cudaError_t launch_gw_t(const GwPassArgs<T>& A, cudaStream_t s)
 {
     const size_t smem = (size_t)(NF + kGwC) * 3 * (A.BY + 2) * A.N * sizeof(T);
-    static bool attr = false;
+    static DevFlag attr;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_gw_pass<T, NF, KAHAN, VW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kPassMaxSmem);

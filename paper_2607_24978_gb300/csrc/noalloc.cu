@@ -65,8 +65,9 @@ __global__ void k_noalloc_load(DevScal* S, const double* __restrict__ abt)
     }
 }
 
-// Copy the updated a, a', t and the pass's energies back to the caller.
-__global__ void k_noalloc_store(const DevScal* S, double* __restrict__ abt, double* __restrict__ energies)
+// Copy the updated a, a', t, the pass's energies and its status bits back to the caller.
+__global__ void k_noalloc_store(const DevScal* S, double* __restrict__ abt, double* __restrict__ energies,
+                                int32_t* __restrict__ status)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         abt[0] = S->a;
@@ -74,7 +75,26 @@ __global__ void k_noalloc_store(const DevScal* S, double* __restrict__ abt, doub
         abt[2] = S->t;
         if (energies)
             for (int i = 0; i < D_NDIAG; ++i) energies[i] = S->diag[i];
+        if (status) *status = S->status;
     }
+}
+
+// True when p is device (or managed) memory that the current device can address.
+bool on_current_device(const void* p, int dev)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+bool overlap(const void* a, const void* b, size_t bytes)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + bytes && y < x + bytes;
 }
 
 template <typename T>
@@ -102,20 +122,52 @@ extern "C" cl_status cl_fused_pass_noalloc(const cl_pass_noalloc_desc* d)
     for (int f = 0; f < nf; ++f) {
         if (!d->phi_in[f] || !d->pi_in[f] || !d->phi_out[f] || !d->pi_out[f]) return CL_EINVAL;
         if (kahan && (!d->c_in[f] || !d->c_out[f])) return CL_EINVAL;
-        if (d->phi_in[f] == d->phi_out[f] || d->pi_in[f] == d->pi_out[f] || (kahan && d->c_in[f] == d->c_out[f]))
-            return CL_EINVAL;  // inputs are read while outputs are written
     }
     if (nf == 1 && (d->m2[1] != 0 || d->lam[1] != 0 || d->g2 != 0)) return CL_EINVAL;
 
     // Tiling of the direct-load kernel: full x rows, BY rows per block, DZ planes per block,
-    // with the grid kept within the scratch's block capacity.
+    // with the grid kept within the scratch's block capacity.  A row of N / VW threads must
+    // fit the kernel's 512-thread blocks (the same rule as cl_step's set-up): odd N up to
+    // 512, even N up to 1024, and in FP32 multiples of 4 up to 1536.
     const int VW = scalar_pass_vector_width(prec, N);
     const int TX = N / VW;
     int BY = TX >= 256 ? 1 : 256 / TX;
     if (BY > N) BY = N;
     while (BY > 1 && scalar_pass_threads(prec, N, BY) > 512) --BY;
     while (BY > 1 && scalar_pass_smem_bytes(prec, nf, N, BY, 0) > (size_t)kPassMaxSmem) --BY;
+    if (scalar_pass_threads(prec, N, BY) > 512) return CL_EINVAL;
     if (scalar_pass_smem_bytes(prec, nf, N, BY, 0) > (size_t)kPassMaxSmem) return CL_EINVAL;
+
+    // Every array must be memory of the current device, and no output may overlap an input
+    // or another output (inputs are read while outputs are written).
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CL_ECUDA;
+    const size_t bytes = (size_t)N * N * N * (prec == CL_PREC_FP64 ? sizeof(double) : sizeof(float));
+    const void* ins[6];
+    const void* outs[6];
+    int nin = 0, nout = 0;
+    for (int f = 0; f < nf; ++f) {
+        ins[nin++] = d->phi_in[f];
+        ins[nin++] = d->pi_in[f];
+        outs[nout++] = d->phi_out[f];
+        outs[nout++] = d->pi_out[f];
+        if (kahan) {
+            ins[nin++] = d->c_in[f];
+            outs[nout++] = d->c_out[f];
+        }
+    }
+    for (int i = 0; i < nin; ++i)
+        if (!on_current_device(ins[i], dev)) return CL_EINVAL;
+    for (int i = 0; i < nout; ++i) {
+        if (!on_current_device(outs[i], dev)) return CL_EINVAL;
+        for (int j = 0; j < nin; ++j)
+            if (overlap(outs[i], ins[j], bytes)) return CL_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (overlap(outs[i], outs[j], bytes)) return CL_EINVAL;
+    }
+    if (!on_current_device(d->scalars, dev)) return CL_EINVAL;
+    if (d->energies && !on_current_device(d->energies, dev)) return CL_EINVAL;
+    if (d->status && !on_current_device(d->status, dev)) return CL_EINVAL;
     const int nby = (N + BY - 1) / BY;
     if (nby > kNoAllocMaxBlocks) return CL_EINVAL;  // beyond the scratch capacity
     int nbz = (N + 15) / 16;
@@ -155,7 +207,7 @@ extern "C" cl_status cl_fused_pass_noalloc(const cl_pass_noalloc_desc* d)
         e = launch_scalar_pass(prec, nf, &A, VW, s);
     }
     if (e != cudaSuccess) return CL_ECUDA;
-    k_noalloc_store<<<1, 32, 0, s>>>(S, d->scalars, d->energies);
+    k_noalloc_store<<<1, 32, 0, s>>>(S, d->scalars, d->energies, d->status);
     if (cudaGetLastError() != cudaSuccess) return CL_ECUDA;
     return CL_OK;
 }

@@ -826,7 +826,7 @@ static cudaError_t launch_rk(const RkStageArgs<T>& A, cudaStream_t s)
     dim3 block(((TX * A.BY + 31) / 32) * 32);
     dim3 grid(A.nby * A.nbz);
     const size_t smem = (size_t)NF * 3 * (A.BY + 2) * A.N * sizeof(T);
-    static bool attr_set = false;
+    static DevFlag attr_set;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_rk_stage<T, NF, KAHAN, VW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kPassMaxSmem);
@@ -878,7 +878,7 @@ static cudaError_t launch_rk_tma(const RkStageArgs<T>& A, int stages, cudaStream
         const size_t smem = rk_stage_tma_smem(prec, NF, A.N, A.BY, stages, A.nmc == 2);
         if (block.x > 480 || smem > (size_t)kPassMaxSmem || A.N % VW != 0 || (A.nmc == 2 && NF != 1))
             return cudaErrorInvalidValue;
-        static bool attr[7] = {false, false, false, false, false, false, false};
+        static DevFlag attr[7];
         cudaError_t e = cudaSuccess;
 #define CL_RKT_CASE(SS)                                                                                         \
     case SS:                                                                                                    \

@@ -251,7 +251,7 @@ template <typename T, int NF, bool KAHAN, int VW>
 static cudaError_t launch_nr(const ScalarPassArgs<T>& A, dim3 grid, dim3 block, size_t smem, cudaStream_t s, int* occ)
 {
     if constexpr (VW * sizeof(T) == 16) {
-        static bool attr[6] = {false, false, false, false, false, false};
+        static DevFlag attr[6];
         const int S = A.stages;
         if (S < 2 || S > 5) return cudaErrorInvalidValue;
         cudaError_t e = cudaSuccess;
@@ -288,7 +288,7 @@ static cudaError_t launch_one(const ScalarPassArgs<T>& A, cudaStream_t s, int* o
     dim3 grid(A.DZ > 0 ? A.nby * A.nbz : A.grid);  // DZ < 0: balanced persistent ranges
     const size_t smem = scalar_pass_smem_bytes(prec, NF, A.N, A.BY, A.stages, A.variant);
     if (A.variant == 1 && A.stages > 0) return launch_nr<T, NF, KAHAN, VW>(A, grid, block, smem, s, occ);
-    static bool attr_set[8] = {false, false, false, false, false, false, false, false};
+    static DevFlag attr_set[8];
     const int si = A.stages < 0 ? 0 : (A.stages > 7 ? 7 : A.stages);
     cudaError_t e = cudaSuccess;
     if (!attr_set[si]) {

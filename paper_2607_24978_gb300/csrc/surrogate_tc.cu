@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(256, 1) k_conv_tc(const __grid_constant__ Conv
 template <int CI, int CO>
 static cudaError_t launch_conv_tc_t(const ConvTCArgs& A, int grid, cudaStream_t s)
 {
-    static bool attr = false;
+    static DevFlag attr;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_conv_tc<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)ConvTCShape<CI, CO>::SMEM);

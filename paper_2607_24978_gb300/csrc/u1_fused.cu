@@ -312,7 +312,7 @@ int u1_fused_grid(int N, int dz) { return (N / kFX) * (N / kFY) * ((N + dz - 1) 
 template <typename T>
 static cudaError_t u1_fused_attr()
 {
-    static bool done = false;
+    static DevFlag done;
     if (done) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_u1_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(U1FusedSmem<T>));

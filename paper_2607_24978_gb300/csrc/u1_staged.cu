@@ -509,7 +509,7 @@ static cudaError_t launch_u1s_t(const U1Args<T>& A, int what, cudaStream_t s)
     using G = U1SGeom<T>;
     if (!u1_staged_ok(A.N) || A.dz < 1 || A.dz > A.N) return cudaErrorInvalidValue;
     const int grid = u1_staged_blocks(sizeof(T) == 8 ? CL_PREC_FP64 : CL_PREC_FP32, A.N, A.dz);
-    static bool attr[2] = {false, false};
+    static DevFlag attr[2];
     if (what == 0) {
         constexpr size_t smem = u1s_smem_bytes<T, PQ_NA>();
         if (!attr[0]) {
