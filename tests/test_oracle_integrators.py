@@ -101,14 +101,15 @@ def _cn_error(scheme, h, T=2.0):
     return abs(st.phi.flat[0] - cn)
 
 
-@pytest.mark.parametrize("scheme,order,h,tol", [(O.VV2, 2, 0.02, 0.12), (O.YOSHIDA4, 4, 0.1, 0.12),
-                                                (O.RK3_3, 3, 0.05, 0.12), (O.RK4_5, 4, 0.025, 0.12),
-                                                (O.YOSHIDA6, 6, 0.1, 0.12), (O.YOSHIDA8, 8, 0.0625, 0.12),
+@pytest.mark.parametrize("scheme,order,h,tol", [(O.VV2, 2, 0.02, 0.05), (O.YOSHIDA4, 4, 0.1, 0.1),
+                                                (O.RK3_3, 3, 0.05, 0.1), (O.RK4_5, 4, 0.025, 0.1),
+                                                (O.YOSHIDA6, 6, 0.1, 0.1), (O.YOSHIDA8, 8, 0.0625, 0.1),
                                                 (O.YOSHIDA10, 10, 0.1, 0.2)])
 def test_cn_elliptic_convergence_order(scheme, order, h, tol):
     """The higher Yoshida compositions are pinned by their order alone: a wrong weight, sign or
     recursion depth leaves a lower-order error term.  h is chosen so that the errors stay well
-    above rounding (orders 8 and 10 reach 1e-12 quickly)."""
+    above rounding (orders 8 and 10 reach 1e-12 quickly).  Bounds: order 2.00 +- 0.05 for velocity
+    Verlet and +- 0.1 for the others; order 10 keeps +- 0.2, its finer error meets rounding."""
     e1, e2 = _cn_error(scheme, h), _cn_error(scheme, h / 2)
     assert e1 < 1e-2
     assert np.log2(e1 / e2) == pytest.approx(order, abs=tol)

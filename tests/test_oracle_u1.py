@@ -136,18 +136,29 @@ def test_free_wave_lattice_frequency():
     assert st.links[0, 0, 0, 0] == pytest.approx(expect, abs=1e-12)
 
 
-def test_chiral_instability_growth_rate():
+@pytest.mark.parametrize("kappa", [1.0, 0.3])
+def test_chiral_instability_growth_rate(kappa):
+    """Rolling axion, no expansion, no back-reaction: the E equation of the paper's
+    ALP-gauge system reads, in cosmic time and physical units,
+        A'' = curl curl A - (alpha_L / m_p) phi_dot curl A,
+    so a helical mode of wavenumber k grows at Gamma^2 = (alpha_L / m_p) phi_dot k - k^2.
+    In program units phi = f_star phi~ and x = x~ / omega_star, phi_dot = f_star omega_star v,
+    hence Gamma~^2 = alpha_L (f_star / m_p) v k~ - k~^2 with f_star / m_p = sqrt(kappa).  On the
+    lattice k -> sin(k dx)/dx in the clover curl and k^2 -> (2 sin(k dx/2)/dx)^2.  Run at
+    kappa = 0.3 too, where alpha_L kappa, alpha_L sqrt(kappa) and alpha_L differ."""
     N, L = 8, 8.0
     kB_fn = lambda k, dx: np.sin(k * dx) / dx
     kL_fn = lambda k, dx: 2 * np.sin(k * dx / 2) / dx
     k, dx = 2 * np.pi / L, L / N
     kB, kL = kB_fn(k, dx), kL_fn(k, dx)
-    gv = 2 * kL ** 2 / kB  # so that Gamma = kL
-    model = O.make_model(N, L, nf=1, alpha=0.0, kappa=1.0, gauge=1, alphaL=gv, ws2=0.0)  # g = alpha_L, v = 1
+    g_phys = 2 * kL ** 2 / kB  # alpha_L f_star / m_p, chosen so that Gamma = kL at v = 1
+    alphaL = g_phys / np.sqrt(kappa)
+    model = O.make_model(N, L, nf=1, alpha=0.0, kappa=kappa, gauge=1, alphaL=alphaL, ws2=0.0)
     st = O.new_state(model)
-    st.pi[:] = 1.0  # phi' = v = 1 (a = 1, alpha = 0), V = 0, no back-reaction
+    v = 1.0
+    st.pi[:] = v  # phi' = v (a = 1, alpha = 0), V = 0, no back-reaction
     st.links, _, _ = _z_wave(N, L, 1e-9)
-    gamma = np.sqrt(gv * kB - kL ** 2)
+    gamma = np.sqrt(alphaL * np.sqrt(kappa) * v * kB - kL ** 2)
     h, ts, amps = 0.05, [], []
     for _ in range(12):
         O.step(model, st, O.RK4_5, h, 20)
@@ -158,7 +169,7 @@ def test_chiral_instability_growth_rate():
     assert slope == pytest.approx(gamma, rel=2e-3)
     assert amps[-1] < 1e-4  # linear regime
     # and the continuum rate within the lattice corrections
-    assert slope == pytest.approx(np.sqrt(gv * k - k * k), rel=0.1)
+    assert slope == pytest.approx(np.sqrt(g_phys * k - k * k), rel=0.1)
 
 
 @pytest.mark.parametrize("scheme,order", [(O.RK3_3, 3)])
