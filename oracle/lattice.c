@@ -20,6 +20,13 @@
 
 static int wrap(int i, int N) { return ((i % N) + N) % N; }
 
+#ifdef _OPENMP
+#include <omp.h>
+int orc_threads(void) { return omp_get_max_threads(); }
+#else
+int orc_threads(void) { return 1; }
+#endif
+
 /* ------------------------------------------------------------------ potential */
 
 double orc_V(const orc_model* m, double f0, double f1)
@@ -73,6 +80,7 @@ static int64_t IB(int nx, int ny, int x, int y, int z) { return ((int64_t)z * ny
 /* 7-point Laplacian over the directions of extent > 1 of an nx x ny x nz box */
 static void laplacian_box(int nx, int ny, int nz, double dx, const double* f, double* out)
 {
+    ORC_PAR_FOR
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
@@ -88,6 +96,7 @@ static void laplacian_box(int nx, int ny, int nz, double dx, const double* f, do
 static double grad2_box(int nx, int ny, int nz, const double* f)
 {
     double s = 0.0;
+    ORC_PAR_SUM(s)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
@@ -125,6 +134,7 @@ void orc_kick_force(const orc_model* m, int f, const double* phi, double a, doub
     orc_extents(m, &nx, &ny, &nz);
     laplacian_box(nx, ny, nz, dx, pf, out);
     const double ca = pow(a, 1.0 + m->alpha), cv = pow(a, 3.0 + m->alpha);
+    ORC_PAR_FOR
     for (int64_t n = 0; n < V; ++n)
         out[n] = ca * out[n] - cv * orc_dV(m, f, p0[n], p1 ? p1[n] : 0.0);
 }
@@ -154,6 +164,7 @@ void orc_energies(const orc_model* m, const double* phi, const double* pi,
     for (int f = 0; f < m->nf; ++f) {
         const double* pf = pi + (int64_t)f * V;
         double s = 0.0;
+        ORC_PAR_SUM(s)
         for (int64_t n = 0; n < V; ++n) s += pf[n] * pf[n];
         /* K = phi'^2 / (2 a^(2 alpha)) with phi' = a^(alpha-3) pi  ->  pi^2 / (2 a^6) */
         out[ORC_E_K0 + f] = s / (2.0 * pow(a, 6.0) * (double)V);
@@ -162,6 +173,7 @@ void orc_energies(const orc_model* m, const double* phi, const double* pi,
     }
     {
         double s = 0.0;
+        ORC_PAR_SUM(s)
         for (int64_t n = 0; n < V; ++n) s += orc_V(m, phi[n], m->nf > 1 ? phi[V + n] : 0.0);
         out[ORC_E_V] = s / (double)V;
     }
@@ -218,14 +230,17 @@ static void vv_step(const orc_model* m, double h, double* phi, double* pi, doubl
         orc_kick_force(m, f, phi, a, tmp + (int64_t)f * V);
     }
     if (gv) orc_gw_force(m, phi, gv, a, gtmp);  /* GW half-kick with the fields at t */
-    for (int f = 0; f < m->nf; ++f)
+    for (int f = 0; f < m->nf; ++f) {
+        ORC_PAR_FOR
         for (int64_t n = 0; n < V; ++n) pi[(int64_t)f * V + n] += 0.5 * h * tmp[(int64_t)f * V + n];
+    }
     if (gv)
         for (int64_t n = 0; n < 5 * V; ++n) gp[n] += 0.5 * h * gtmp[n];
 
     const double a1 = m->expansion ? a + h * b : a;
     const double ahalf = 0.5 * (a + a1);
     const double cd = h * pow(ahalf, m->alpha - 3.0);
+    ORC_PAR_FOR
     for (int64_t n = 0; n < (int64_t)m->nf * V; ++n) phi[n] += cd * pi[n];
     if (gv)
         for (int64_t n = 0; n < 5 * V; ++n) gv[n] += cd * gp[n];
@@ -233,8 +248,10 @@ static void vv_step(const orc_model* m, double h, double* phi, double* pi, doubl
 
     for (int f = 0; f < m->nf; ++f) orc_kick_force(m, f, phi, a, tmp + (int64_t)f * V);
     if (gv) orc_gw_force(m, phi, gv, a, gtmp);  /* and with the fields at t + h */
-    for (int f = 0; f < m->nf; ++f)
+    for (int f = 0; f < m->nf; ++f) {
+        ORC_PAR_FOR
         for (int64_t n = 0; n < V; ++n) pi[(int64_t)f * V + n] += 0.5 * h * tmp[(int64_t)f * V + n];
+    }
     if (gv) {
         for (int64_t n = 0; n < 5 * V; ++n) gp[n] += 0.5 * h * gtmp[n];
         free(gtmp);
@@ -267,10 +284,24 @@ static const double RK45_B[5] = {1432997174477.0 / 9575080441755.0,
                                  3134564353537.0 / 4481467310338.0,
                                  2277821191437.0 / 14882151754819.0};
 
+/* RK3-4 (reading: the paper names a third-order four-stage low-storage scheme that admits
+ * adaptive time steps, and prints no coefficients).  This 2N scheme is fixed by the order
+ * conditions alone: the four third-order conditions on its Butcher weights; the state after
+ * the third stage being a second-order solution at t + h (its abscissa c_4 = 1 and
+ * sum_j a_4j c_j = 1/2), so that y_4 - y_3 = B_4 k estimates the local error with no extra
+ * storage; and the z^4 coefficient of the stability function b A^3 1 = 1/24, which makes
+ * R(z) the degree-4 Taylor polynomial of e^z (stable on the imaginary axis up to 2 sqrt 2).
+ * These seven equations have one real solution; its coefficients, to 25 digits:           */
+static const double RK34_A[4] = {0.0, -0.7825460361923582986318837, -2.042914325731224687686953,
+                                 -1.799337253940777102361562};
+static const double RK34_B[4] = {0.06688758201974096587947945, 2.876554598956718963241208,
+                                 0.553465736134398241034173, 0.3912730180961791493159418};
+
 int orc_rk_coeffs(int scheme, const double** A, const double** B)
 {
     if (scheme == ORC_RK3_3) { *A = RK33_A; *B = RK33_B; return 3; }
     if (scheme == ORC_RK4_5) { *A = RK45_A; *B = RK45_B; return 5; }
+    if (scheme == ORC_RK3_4) { *A = RK34_A; *B = RK34_B; return 4; }
     return 0;
 }
 
@@ -296,7 +327,7 @@ double orc_nmc_ricci(const orc_model* m, const double* phi, const double* pi, co
  * Per stage s:  k <- A_s k + h F(y);  y <- y + B_s k   (one auxiliary copy per dof).
  * NMC models (Eq. eomNMC, Eq. piadot): the kick of field 0 gains -a^(3+alpha) xi R phi and
  *   a'' = a [a^(2 alpha) R / 6 - (1 - alpha) (a'/a)^2], with R = orc_nmc_ricci(y). */
-static void rk_step(const orc_model* m, int scheme, double h, double* phi, double* pi, double* abt)
+static double rk_step(const orc_model* m, int scheme, double h, double* phi, double* pi, double* abt)
 {
     const int64_t V = orc_volume(m);
     const int64_t nd = (int64_t)m->nf * V;
@@ -337,9 +368,32 @@ static void rk_step(const orc_model* m, int scheme, double h, double* phi, doubl
         abt[1] += B[s] * kb;
     }
     abt[2] += h;
+    /* embedded error estimate of the last stage's increment: |y_S - y_(S-1)| / |y_S| */
+    double e2 = 0.0, y2 = 0.0;
+    for (int64_t n = 0; n < nd; ++n) {
+        const double dphi = B[S - 1] * kphi[n], dpi = B[S - 1] * kpi[n];
+        e2 += dphi * dphi + dpi * dpi;
+        y2 += phi[n] * phi[n] + pi[n] * pi[n];
+    }
     free(kphi);
     free(kpi);
     free(Fpi);
+    return y2 > 0.0 ? sqrt(e2 / y2) : 0.0;
+}
+
+void orc_step_adaptive(const orc_model* m, double* h, double tol, double hmin, double hmax, int nsteps,
+                       double* phi, double* pi, double* abt, double* h_used, double* eps_out)
+{
+    for (int s = 0; s < nsteps; ++s) {
+        const double eps = rk_step(m, ORC_RK3_4, *h, phi, pi, abt);
+        h_used[s] = *h;
+        eps_out[s] = eps;
+        double f = eps > 0.0 ? 0.9 * cbrt(tol / eps) : 2.0;
+        f = f > 2.0 ? 2.0 : (f < 0.2 ? 0.2 : f);
+        double hn = *h * f;
+        hn = hn > hmax ? hmax : (hn < hmin ? hmin : hn);
+        *h = hn;
+    }
 }
 
 /* Symmetric composition of order p (Yoshida 1990, section 4): a method of order p-2 applied

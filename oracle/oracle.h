@@ -29,6 +29,20 @@
 
 #include <stdint.h>
 
+/* Loop-parallel build.  liboracle_omp.so (compiled with -fopenmp) exists only to time
+ * the oracle on every host core for the CPU baseline: the site loops of the scalar step
+ * are split across threads and its sums become OpenMP reductions (so their summation
+ * order differs).  liboracle.so, which every test loads, is compiled without OpenMP;
+ * there these macros expand to nothing and every loop runs in the order written. */
+#ifdef _OPENMP
+#define ORC_PRAGMA(x) _Pragma(#x)
+#define ORC_PAR_FOR ORC_PRAGMA(omp parallel for schedule(static))
+#define ORC_PAR_SUM(v) ORC_PRAGMA(omp parallel for schedule(static) reduction(+ : v))
+#else
+#define ORC_PAR_FOR
+#define ORC_PAR_SUM(v)
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -76,7 +90,7 @@ enum {
 
 /* Integrators (section "Non-symplectic evolvers" and the symplectic family it lists). */
 enum { ORC_VV2 = 0, ORC_YOSHIDA4 = 1, ORC_RK3_3 = 2, ORC_RK4_5 = 3, ORC_YOSHIDA6 = 4, ORC_YOSHIDA8 = 5,
-       ORC_YOSHIDA10 = 6 };
+       ORC_YOSHIDA10 = 6, ORC_RK3_4 = 7 };
 
 /* ---- potential and lattice operators ---- */
 double orc_V(const orc_model* m, double f0, double f1);
@@ -147,6 +161,19 @@ double orc_act(int act, double u);       /* 0 = ReLU, 1 = GELU (tanh form) */
 double orc_act_grad(int act, double u);
 void orc_act_array(int act, int64_t n, const double* u, double* h);
 void orc_act_bwd_array(int act, int64_t n, const double* u, const double* dh, double* du);
+
+/* Adaptive RK3-4 steps (section "Non-symplectic evolvers": RK3-4 admits adaptive time
+ * stepping).  Each step is taken with the current h and always accepted; its embedded error
+ * estimate eps = |y_4 - y_3| / |y_4| (2-norms over phi and pi of every field and site; y_3,
+ * the state after the third stage, is a second-order solution at t + h) sets the next step,
+ *     h <- clamp(h * min(2, max(1/5, 0.9 (tol / eps)^(1/3))), hmin, hmax)   (h * 2 if eps = 0).
+ * h_used[s], eps_out[s] (nsteps each) receive the step sizes taken and their estimates;
+ * h is updated in place. */
+void orc_step_adaptive(const orc_model* m, double* h, double tol, double hmin, double hmax, int nsteps,
+                       double* phi, double* pi, double* abt, double* h_used, double* eps_out);
+
+/* Threads the loop-parallel build uses (1 in the serial build). */
+int orc_threads(void);
 
 #ifdef __cplusplus
 }

@@ -12,7 +12,7 @@ import numpy as np
 
 from . import build_oracle
 
-VV2, YOSHIDA4, RK3_3, RK4_5, YOSHIDA6, YOSHIDA8, YOSHIDA10 = 0, 1, 2, 3, 4, 5, 6
+VV2, YOSHIDA4, RK3_3, RK4_5, YOSHIDA6, YOSHIDA8, YOSHIDA10, RK3_4 = 0, 1, 2, 3, 4, 5, 6, 7
 E_NAMES = ["K0", "K1", "G0", "G1", "V", "KEM", "GEM", "rho", "p", "hubble_violation", "a", "b"]
 
 
@@ -25,12 +25,31 @@ class Model(C.Structure):
 
 
 _lib = None
+_libs = {}
+
+
+def use_threads(on):
+    """Select the loop-parallel build (liboracle_omp.so, all host cores) for the calls that
+    follow, or the serial one.  Only the CPU-baseline timing turns it on."""
+    global _lib
+    _lib = _load(bool(on))
+
+
+def threads():
+    """Threads the selected build runs its loops on."""
+    return int(lib().orc_threads())
 
 
 def lib():
     global _lib
     if _lib is None:
-        path = build_oracle.build()
+        _lib = _load(False)
+    return _lib
+
+
+def _load(omp):
+    if omp not in _libs:
+        path = build_oracle.build(omp=omp)
         L = C.CDLL(path)
         dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
         mp = C.POINTER(Model)
@@ -71,8 +90,12 @@ def lib():
         L.orc_act_grad.argtypes = [C.c_int, C.c_double]
         L.orc_act_array.argtypes = [C.c_int, C.c_int64, dp, dp]
         L.orc_act_bwd_array.argtypes = [C.c_int, C.c_int64, dp, dp, dp]
-        _lib = L
-    return _lib
+        L.orc_step_adaptive.argtypes = [mp, C.POINTER(C.c_double), C.c_double, C.c_double, C.c_double, C.c_int,
+                                         dp, dp, dp, dp, dp]
+        L.orc_threads.restype = C.c_int
+        L.orc_threads.argtypes = []
+        _libs[omp] = L
+    return _libs[omp]
 
 
 def make_model(N, L, nf=1, alpha=1.0, kappa=0.0, expansion=False, m2=(0.0, 0.0), lam=(0.0, 0.0),
@@ -138,6 +161,17 @@ def step(model, st, scheme, h, nsteps=1):
     lib().orc_step(C.byref(model), int(scheme), float(h), int(nsteps), st.phi, st.pi,
                    _ptr(st.links), _ptr(st.efield), st.abt)
     return st
+
+
+def step_adaptive(model, st, h, tol, nsteps, hmin=0.0, hmax=1e300):
+    """Adaptive RK3-4 steps (always accepted; the next h from the embedded error estimate).
+    Returns (h_next, h_used[nsteps], eps[nsteps])."""
+    st.phi, st.pi, st.abt = _c(st.phi), _c(st.pi), _c(st.abt)
+    hh = C.c_double(float(h))
+    hu, ep = np.zeros(nsteps), np.zeros(nsteps)
+    lib().orc_step_adaptive(C.byref(model), C.byref(hh), float(tol), float(hmin), float(hmax), int(nsteps),
+                            st.phi, st.pi, st.abt, hu, ep)
+    return hh.value, hu, ep
 
 
 def energies(model, st):

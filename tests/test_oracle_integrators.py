@@ -74,6 +74,96 @@ def test_rk33_stability_polynomial():
     np.testing.assert_allclose(st.pi[0], amp[1] * shape, atol=1e-12)
 
 
+def test_rk34_stability_polynomial():
+    """RK3-4 is built so that its stability function is the degree-4 Taylor polynomial of e^z:
+    on y' = A y one step is I + hA + (hA)^2/2 + (hA)^3/6 + (hA)^4/24 (third order, with the z^4
+    coefficient b A^3 1 = 1/24 fixed as the scheme's last condition)."""
+    model, st, w2 = _free_wave()
+    h, n = 0.05, 30
+    shape = st.phi[0].copy()
+    O.step(model, st, O.RK3_4, h, n)
+    Z = h * np.array([[0.0, 1.0], [-w2, 0.0]])
+    R = np.eye(2) + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+    amp = np.linalg.matrix_power(R, n) @ np.array([1.0, 0.0])
+    np.testing.assert_allclose(st.phi[0], amp[0] * shape, atol=1e-12)
+    np.testing.assert_allclose(st.pi[0], amp[1] * shape, atol=1e-12)
+
+
+def _butcher_2n(A, B):
+    """Butcher matrix and weights of a 2N-storage scheme k <- A_s k + h F, y <- y + B_s k."""
+    s = len(B)
+    a = np.zeros((s + 1, s))
+    for i in range(1, s + 1):
+        for j in range(1, i + 1):
+            a[i, j - 1] = sum(B[m - 1] * np.prod([A[q - 1] for q in range(j + 1, m + 1)]) for m in range(j, i + 1))
+    return a[:s], a[s]
+
+
+def test_rk34_embedded_estimate_is_second_order():
+    """The state after RK3-4's third stage is a second-order solution at t + h, so the estimate
+    |y_4 - y_3| of a step falls as h^3 (homogeneous lambda phi^4, against cn)."""
+    model = O.make_model(2, L=1.0, nf=1, alpha=1.0, lam=(1.0, 0.0))
+    eps = []
+    for h in (0.04, 0.02, 0.01):
+        st = O.new_state(model)
+        st.phi[:] = 1.0
+        st.pi[:] = 0.3
+        _, hu, ep = O.step_adaptive(model, st, h, 1e-6, 1, hmin=h, hmax=h)  # one step of fixed size
+        assert hu[0] == h
+        eps.append(ep[0])
+    assert np.log2(eps[0] / eps[1]) == pytest.approx(3.0, abs=0.1)
+    assert np.log2(eps[1] / eps[2]) == pytest.approx(3.0, abs=0.1)
+
+
+def test_rk34_adaptive_controller():
+    """The adaptive driver takes every step and sets the next one from its estimate,
+    h <- h min(2, max(1/5, 0.9 (tol/eps)^(1/3))) within [hmin, hmax]: the estimates settle near
+    tol, a tighter tolerance takes smaller steps (h ~ tol^(1/3)), and the end state converges
+    to the cn-elliptic solution as tol falls."""
+    model = O.make_model(2, L=1.0, nf=1, alpha=1.0, lam=(1.0, 0.0))
+    res = {}
+    for tol in (1e-6, 1e-8):
+        st = O.new_state(model)
+        st.phi[:] = 1.0
+        h, hu, ep = O.step_adaptive(model, st, 0.01, tol, 200)
+        for i in range(199):
+            f = min(2.0, max(0.2, 0.9 * (tol / ep[i]) ** (1.0 / 3.0)))
+            assert hu[i + 1] == pytest.approx(hu[i] * f, rel=1e-14)
+        assert np.all(ep[20:] < 10 * tol) and 0.2 * tol < np.median(ep[20:]) < 2 * tol
+        T = st.abt[2]
+        sn, cn, dn, ph = scipy.special.ellipj(T, 0.5)
+        res[tol] = (hu[2], abs(st.phi.flat[0] - cn))
+    # from the same state near t = 0 the estimate is C h^3, so h settles at 0.9 (tol / C)^(1/3)
+    assert res[1e-6][0] / res[1e-8][0] == pytest.approx(100.0 ** (1.0 / 3.0), rel=0.02)
+    assert res[1e-8][1] < res[1e-6][1]
+
+
+def test_rk34_coefficients_satisfy_their_conditions():
+    """The 2N table meets the conditions that define it: third order, c_4 = 1 with
+    sum_j a_4j c_j = 1/2 (the embedded second-order state), and b A^3 1 = 1/24."""
+    A = [0.0, -0.7825460361923582986318837, -2.042914325731224687686953, -1.799337253940777102361562]
+    B = [0.06688758201974096587947945, 2.876554598956718963241208, 0.553465736134398241034173,
+         0.3912730180961791493159418]
+    a, b = _butcher_2n(A, B)
+    c = a.sum(1)
+    for got, want in [(b.sum(), 1.0), (b @ c, 0.5), (b @ c ** 2, 1 / 3), (b @ a @ c, 1 / 6), (c[3], 1.0),
+                      (a[3] @ c, 0.5), (b @ a @ a @ c, 1 / 24)]:
+        assert got == pytest.approx(want, abs=1e-14)
+    # the oracle steps with exactly this table: one step of y' = lambda y against the Butcher form
+    model, st, w2 = _free_wave()
+    h = 0.07
+    shape = st.phi[0].copy()
+    O.step(model, st, O.RK3_4, h, 1)
+    Z = h * np.array([[0.0, 1.0], [-w2, 0.0]])
+    K = np.zeros((4, 2))
+    y0 = np.array([1.0, 0.0])
+    for i in range(4):
+        K[i] = Z @ (y0 + sum(a[i, j] * K[j] for j in range(i)))
+    y1 = y0 + b @ K
+    np.testing.assert_allclose(st.phi[0], y1[0] * shape, atol=1e-13)
+    np.testing.assert_allclose(st.pi[0], y1[1] * shape, atol=1e-13)
+
+
 def test_rk45_one_step_order():
     """RK4-5 one-step error against the exact matrix exponential scales as h^5."""
     model, st0, w2 = _free_wave()
@@ -103,6 +193,7 @@ def _cn_error(scheme, h, T=2.0):
 
 @pytest.mark.parametrize("scheme,order,h,tol", [(O.VV2, 2, 0.02, 0.05), (O.YOSHIDA4, 4, 0.1, 0.1),
                                                 (O.RK3_3, 3, 0.05, 0.1), (O.RK4_5, 4, 0.025, 0.1),
+                                                (O.RK3_4, 3, 0.05, 0.1),
                                                 (O.YOSHIDA6, 6, 0.1, 0.1), (O.YOSHIDA8, 8, 0.0625, 0.1),
                                                 (O.YOSHIDA10, 10, 0.1, 0.2)])
 def test_cn_elliptic_convergence_order(scheme, order, h, tol):
