@@ -69,7 +69,14 @@ enum {
      * 10): the symmetric triple jump applied recursively to VV-2, 3^((p-2)/2) passes/step   */
     CL_INT_YOSHIDA6 = 4,  /* O(dt^6), 9 passes/step   */
     CL_INT_YOSHIDA8 = 5,  /* O(dt^8), 27 passes/step  */
-    CL_INT_YOSHIDA10 = 6  /* O(dt^10), 81 passes/step */
+    CL_INT_YOSHIDA10 = 6, /* O(dt^10), 81 passes/step */
+    /* low-storage 2N Runge-Kutta, 3rd order, 4 stages, with an embedded second-order solution
+     * (the state after its third stage) for adaptive time steps (section "Non-symplectic
+     * evolvers" names RK3-4 and its adaptive stepping without printing coefficients; this
+     * table is fixed by the third-order conditions, c_4 = 1 with sum_j a_4j c_j = 1/2, and a
+     * stability function equal to the degree-4 Taylor polynomial of e^z): see
+     * cl_set_adaptive */
+    CL_INT_RK3_4 = 7
 };
 
 enum { CL_GAUGE_NONE = 0, CL_GAUGE_U1_AXION = 1 };
@@ -152,10 +159,22 @@ typedef struct {
     double KE, GB;            /* U(1) electric and magnetic energies (0 without gauge)   */
     double rho, p;            /* energy density and pressure                             */
     double hubble_violation;  /* |H^2 - a^(2 alpha) kappa rho/3| / H^2, H = a'/a (0 if H = 0) */
-    double gauss_violation;   /* U(1): max_n |Gauss(n)| / mean_n |div E(n)|; 0 without gauge */
+    double gauss_violation;   /* U(1): lattice Gauss charge G(n) = sum_i [P_i(n) - P_i(n-i)]/dx,
+                                 P = a^(1-alpha) E + g W (Eq. AxionInfEOM's Gauss law), of the
+                                 current state: max_n |G(n)| / max_n sum_i (|P_i(n)| + |P_i(n-i)|)/dx;
+                                 0 without gauge                                         */
     int64_t step;             /* time steps taken since the state was set                */
     double ricci;             /* background Ricci scalar R (Eq. eomR) of a non-minimally coupled
                                  lattice (cl_set_nonminimal); 0 otherwise                  */
+    double gauss_rms_step;    /* U(1), tracked every step: rms Gauss violation of the latest
+                                 cl_step step's starting state,
+                                 dx sqrt(sum_n G(n)^2) / (a^(1-alpha) sqrt(sum_n E(n)^2))   */
+    double gauss_rms_max;     /* U(1): the largest gauss_rms_step since the last
+                                 cl_set_scalars or cl_init_vacuum                         */
+    double dt;                /* the step size the next cl_step step takes (adaptive RK3-4:
+                                 set by the controller; otherwise the lattice's dt)       */
+    double rk_error;          /* adaptive RK3-4: embedded error estimate of the latest step,
+                                 |y_4 - y_3| / |y_4| over phi and pi; 0 otherwise           */
 } cl_energy;
 
 /* Create a lattice.  Allocates all device memory (fields, their ping-pong copies,
@@ -255,6 +274,19 @@ cl_status cl_set_gauge_coupling(cl_lattice* l, double alphaL, double ws2);
  * their minimally coupled form (hubble_violation is then not a constraint of the system; set
  * a' explicitly).  Errors: CL_EINVAL, CL_EUNSUPPORTED. */
 cl_status cl_set_nonminimal(cl_lattice* l, double xi);
+
+/* Adaptive time steps of CL_INT_RK3_4 (section "Non-symplectic evolvers": RK3-4 admits
+ * adaptive time stepping).  With tol > 0 every cl_step step is taken with the current step
+ * size h (starting from the lattice's dt) and always accepted; its last stage reduces the
+ * embedded error estimate eps = |y_4 - y_3| / |y_4| (2-norms over phi and pi of every field
+ * and site, y_3 the second-order state after the third stage) and sets, on the device,
+ *     h <- clamp(h min(2, max(1/5, 0.9 (tol / eps)^(1/3))), h_min, h_max)   (2 h if eps = 0)
+ * for the next step, so steps stay graph-replayed with no host round trip.  tol <= 0 returns
+ * to the fixed dt.  cl_energies reports the current h (dt) and the latest eps (rk_error).
+ * Single lattices of scalar fields (3-D or reduced) without non-minimal coupling.
+ * Errors: CL_EINVAL (h_min > h_max, non-positive h_max), CL_EUNSUPPORTED (another
+ * integrator, gauge fields, ensembles, non-minimal coupling). */
+cl_status cl_set_adaptive(cl_lattice* l, double tol, double h_min, double h_max);
 
 /* Gravitational waves (section "New algorithm for GWs"): five traceless auxiliaries v_ij
  * (v33 = -v11 - v22, fields CL_FIELD_GW_*, zero when enabled) evolved with the leapfrog

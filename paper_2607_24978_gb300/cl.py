@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libcl.so")
 
 CL_OK, CL_EINVAL, CL_ENOMEM, CL_ECUDA, CL_ENAN, CL_ECONSTRAINT, CL_ETIMEOUT, CL_ESTATE, CL_EUNSUPPORTED = range(9)
 CL_PREC_FP64, CL_PREC_FP32_KAHAN, CL_PREC_FP32 = 0, 1, 2
-CL_INT_VV2, CL_INT_YOSHIDA4, CL_INT_RK3_3, CL_INT_RK4_5, CL_INT_YOSHIDA6, CL_INT_YOSHIDA8, CL_INT_YOSHIDA10 = range(7)
+CL_INT_VV2, CL_INT_YOSHIDA4, CL_INT_RK3_3, CL_INT_RK4_5, CL_INT_YOSHIDA6, CL_INT_YOSHIDA8, CL_INT_YOSHIDA10, CL_INT_RK3_4 = \
+    range(8)
 CL_GAUGE_NONE, CL_GAUGE_U1_AXION = 0, 1
 CL_GSPEC_E, CL_GSPEC_B, CL_GSPEC_APLUS, CL_GSPEC_AMINUS = 0, 1, 2, 3
 CL_POT_LPHI4, CL_POT_M2, CL_POT_M2_G2, CL_POT_LPHI4_G2, CL_POT_POLY = 0, 1, 2, 3, 4
@@ -35,7 +36,8 @@ EXPORTS = ["cl_init_lattice", "cl_free", "cl_set_potential", "cl_set_state", "cl
            "cl_fused_pass_noalloc", "cl_surrogate_create", "cl_surrogate_free", "cl_surrogate_set_weights",
            "cl_surrogate_get_weights", "cl_surrogate_forward", "cl_surrogate_backward", "cl_surrogate_get_grads",
            "cl_surrogate_last_launch_count", "cl_surrogate_loss", "cl_surrogate_adamw", "cl_surrogate_channel_stats",
-           "cl_lattice_pack", "cl_lattice_unpack", "cl_surrogate_jump", "cl_surrogate_size", "cl_autotune", "cl_gauge_spectrum", "cl_set_nonminimal", "cl_enable_gw", "cl_gw_spectrum"]
+           "cl_lattice_pack", "cl_lattice_unpack", "cl_surrogate_jump", "cl_surrogate_size", "cl_autotune", "cl_gauge_spectrum", "cl_set_nonminimal", "cl_enable_gw", "cl_gw_spectrum",
+           "cl_set_adaptive"]
 CL_ACT_RELU, CL_ACT_GELU = 1, 2
 CL_SG_BF16, CL_SG_FP32 = 0, 1
 
@@ -57,13 +59,16 @@ class cl_energy(C.Structure):
     _fields_ = [("t", C.c_double), ("a", C.c_double), ("adot", C.c_double), ("K", C.c_double * 2),
                 ("G", C.c_double * 2), ("V", C.c_double), ("KE", C.c_double), ("GB", C.c_double),
                 ("rho", C.c_double), ("p", C.c_double), ("hubble_violation", C.c_double),
-                ("gauss_violation", C.c_double), ("step", C.c_int64), ("ricci", C.c_double)]
+                ("gauss_violation", C.c_double), ("step", C.c_int64), ("ricci", C.c_double),
+                ("gauss_rms_step", C.c_double), ("gauss_rms_max", C.c_double), ("dt", C.c_double),
+                ("rk_error", C.c_double)]
 
     def as_dict(self):
         return {"t": self.t, "a": self.a, "adot": self.adot, "K0": self.K[0], "K1": self.K[1], "G0": self.G[0],
                 "G1": self.G[1], "V": self.V, "KE": self.KE, "GB": self.GB, "rho": self.rho, "p": self.p,
                 "hubble_violation": self.hubble_violation, "gauss_violation": self.gauss_violation,
-                "step": self.step, "ricci": self.ricci}
+                "step": self.step, "ricci": self.ricci, "gauss_rms_step": self.gauss_rms_step,
+                "gauss_rms_max": self.gauss_rms_max, "dt": self.dt, "rk_error": self.rk_error}
 
 
 class cl_pass_noalloc_desc(C.Structure):
@@ -119,6 +124,7 @@ def lib():
         L.cl_set_gauge_coupling.argtypes = [C.c_void_p, C.c_double, C.c_double]
         L.cl_set_hubble_limit.argtypes = [C.c_void_p, C.c_double]
         L.cl_set_nonminimal.argtypes = [C.c_void_p, C.c_double]
+        L.cl_set_adaptive.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double]
         L.cl_enable_gw.argtypes = [C.c_void_p]
         L.cl_gw_spectrum.argtypes = [C.c_void_p, C.c_double, C.c_int32, P(C.c_double), P(C.c_double), P(C.c_double),
                                      C.c_int32, P(C.c_int32)]
@@ -335,6 +341,9 @@ class Lattice:
 
     def cl_set_nonminimal(self, xi):
         _check(self.h, lib().cl_set_nonminimal(self.h, float(xi)))
+
+    def cl_set_adaptive(self, tol, h_min=0.0, h_max=1e300):
+        _check(self.h, lib().cl_set_adaptive(self.h, float(tol), float(h_min), float(h_max)))
 
     def cl_enable_gw(self):
         _check(self.h, lib().cl_enable_gw(self.h))

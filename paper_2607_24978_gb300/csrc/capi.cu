@@ -37,7 +37,10 @@ struct PassCoef {
     double A = 0.0, B = 0.0;
 };
 
-bool is_rk(int integrator) { return integrator == CL_INT_RK3_3 || integrator == CL_INT_RK4_5; }
+bool is_rk(int integrator)
+{
+    return integrator == CL_INT_RK3_3 || integrator == CL_INT_RK4_5 || integrator == CL_INT_RK3_4;
+}
 
 }  // namespace
 
@@ -81,6 +84,8 @@ struct cl_lattice {
     bool nmc = false;               // non-minimal coupling xi phi^2 R of field 0 (Runge-Kutta)
     bool rbar_valid = false;        // scal->rbar holds the Ricci scalar of the current state
     double xi = 0.0;
+    double adapt_tol = 0.0;         // adaptive RK3-4 steps when > 0 (the step size lives in scal->h)
+    double adapt_hmin = 0.0, adapt_hmax = 0.0;
     bool gw = false;                // gravitational-wave auxiliaries evolved with the leapfrog
     void* gv[5][2] = {};            // v11, v12, v13, v22, v23 (ping-pong)
     void* gpv[5][2] = {};           // their momenta a^(3-alpha) v'
@@ -294,7 +299,8 @@ cl_status choose_tiles(cl_lattice* l)
         const int64_t blocks = (l->V + 255) / 256;
         l->red_grid = (int)(blocks < 8 * (int64_t)nsm ? blocks : 8 * (int64_t)nsm);
         l->VW = 1;
-        cl_status s = grow_partials(l, l->red_grid);
+        // adaptive RK3-4: a second set of partials for the error estimate
+        cl_status s = grow_partials(l, l->red_grid * (l->p.integrator == CL_INT_RK3_4 ? 2 : 1));
         if (s != CL_OK) return s;
         invalidate_graphs(l);
         return CL_OK;
@@ -355,8 +361,11 @@ cl_status choose_tiles(cl_lattice* l)
     int DZ;
     if (l->opt_DZ > 0) {
         DZ = l->opt_DZ > N ? N : l->opt_DZ;  // fixed chunks
-    } else if (l->opt_DZ < 0) {
-        DZ = -1;  // balanced persistent ranges over one wave
+    } else if (l->opt_DZ < 0 || (prec == CL_PREC_FP64 && stages == 0)) {
+        // balanced persistent ranges over one wave; the default for FP64 direct-load passes,
+        // which are bound by the FP64 rate: every SM gets the same share (at 256^3 the lockstep
+        // chunks left 48 of 152 SMs with one block instead of two)
+        DZ = -1;
     } else {
         // lockstep: every y tile split into the same z chunks, all in one wave, so the blocks
         // of neighbouring tiles march through the same planes together (halo rows hit L2)
@@ -400,6 +409,8 @@ cl_status choose_tiles(cl_lattice* l)
         int by_max = 448 / TX < 1 ? 1 : 448 / TX;
         if (by_max > N) by_max = N;
         const bool ricci = l->nmc && l->nf == 1;  // the stage also sums the Ricci terms of its output
+        // two sets of partials with the Ricci terms, and for the error estimate of adaptive RK3-4
+        const int psets = ricci || l->p.integrator == CL_INT_RK3_4 ? 2 : 1;
         auto fits = [&](int by, int st) { return rk_stage_tma_smem(prec, l->nf, N, by, st, ricci) <= (size_t)kPassMaxSmem; };
         auto most_stages = [&](int by) {  // the deepest ring (3..6) a tile of by rows allows, or 0
             for (int st = 6; st >= 3; --st)
@@ -438,13 +449,13 @@ cl_status choose_tiles(cl_lattice* l)
                 }
                 l->rk_DZ = dz > N ? N : dz;
                 l->rk_nbz = (N + l->rk_DZ - 1) / l->rk_DZ;
-                const int grid = l->rk_nby * l->rk_nbz * (ricci ? 2 : 1);  // two partial sets with the Ricci terms
+                const int grid = l->rk_nby * l->rk_nbz * psets;
                 if (grid > nblocks) nblocks = grid;
             } else {  // balanced persistent ranges over one wave
                 const int64_t units = (int64_t)l->rk_nby * N;
                 l->rk_DZ = -1;
                 l->rk_nbz = (int)(units < nsm ? units : nsm);  // the grid
-                if (l->rk_nbz * (ricci ? 2 : 1) > nblocks) nblocks = l->rk_nbz * (ricci ? 2 : 1);
+                if (l->rk_nbz * psets > nblocks) nblocks = l->rk_nbz * psets;
             }
         }
     }
@@ -462,7 +473,8 @@ cl_status choose_tiles(cl_lattice* l)
         if (nbz > N) nbz = N;
         l->rk_DZ = (int)((N + nbz - 1) / nbz);
         l->rk_nbz = (N + l->rk_DZ - 1) / l->rk_DZ;
-        if (l->rk_nby * l->rk_nbz > nblocks) nblocks = l->rk_nby * l->rk_nbz;
+        const int psets = l->p.integrator == CL_INT_RK3_4 ? 2 : 1;  // error estimate of adaptive RK3-4
+        if (l->rk_nby * l->rk_nbz * psets > nblocks) nblocks = l->rk_nby * l->rk_nbz * psets;
     }
     if (l->gauge) {
         // U(1) kernels: 32 x 8 tiles marching through u1_dz planes each; by default the z
@@ -594,6 +606,7 @@ cl_status run_rk_stage_t(cl_lattice* l, const PassCoef& pc, int in, int out)
     for (int f = 0; f < 2; ++f) { A.m2[f] = l->m2[f]; A.lam[f] = l->lam[f]; }
     A.g2 = l->g2;
     A.hubble_limit = l->hubble_limit;
+    A.tol = l->adapt_tol; A.hmin = l->adapt_hmin; A.hmax = l->adapt_hmax;
     A.flags = pc.flags | (l->p.expansion ? P_EXPANSION : 0);
     // with the TMA-staged kernel the stage itself leaves the Ricci scalar of its output state
     // (the next stage's input) in scal->rbar; otherwise a reduction launch precedes each stage
@@ -713,11 +726,19 @@ cl_status run_pass(cl_lattice* l, const PassCoef& pc, int in, int out)
 // Low-storage 2N Runge-Kutta coefficients (A_s, B_s), as published:
 // RK3-3: Williamson, J. Comput. Phys. 35 (1980) 48.
 // RK4-5: Carpenter & Kennedy, NASA TM-109112 (1994), the five-stage fourth-order scheme.
+// RK3-4: the four-stage third-order 2N scheme whose third-stage state is a second-order
+//   solution at t + h (c_4 = 1, sum_j a_4j c_j = 1/2) and whose stability function is the
+//   degree-4 Taylor polynomial of e^z (b A^3 1 = 1/24); the paper names the scheme without
+//   its coefficients, and these seven conditions fix them (one real solution).
 void rk_tables(int integrator, std::vector<double>& A, std::vector<double>& B)
 {
     if (integrator == CL_INT_RK3_3) {
         A = {0.0, -5.0 / 9.0, -153.0 / 128.0};
         B = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+    } else if (integrator == CL_INT_RK3_4) {
+        A = {0.0, -0.7825460361923582986318837, -2.042914325731224687686953, -1.799337253940777102361562};
+        B = {0.06688758201974096587947945, 2.876554598956718963241208, 0.553465736134398241034173,
+             0.3912730180961791493159418};
     } else {
         A = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
              -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
@@ -771,8 +792,11 @@ std::vector<PassCoef> step_schedule(const cl_lattice* l)
     if (is_rk(l->p.integrator)) {
         std::vector<double> A, B;
         rk_tables(l->p.integrator, A, B);
+        // adaptive RK3-4: every stage takes h from the device, the last one sets the next h
+        const int adapt = l->adapt_tol > 0.0 ? P_DEVICE_H : 0;
         for (size_t i = 0; i < A.size(); ++i) {
-            PassCoef pc{0.0, 0.0, 0.0, (i == 0 ? P_FIRST_STAGE : 0) | (i + 1 == A.size() ? P_COUNT_STEP : 0)};
+            PassCoef pc{0.0, 0.0, 0.0, (i == 0 ? P_FIRST_STAGE : 0) | (i + 1 == A.size() ? P_COUNT_STEP : 0) | adapt |
+                                           (adapt && i + 1 == A.size() ? P_RK_ERROR : 0)};
             pc.rk = l->gauge ? 2 : 1;
             pc.A = A[i];
             pc.B = B[i];
@@ -884,13 +908,23 @@ cl_status run_u1_t(cl_lattice* l, int what, double cA, double cB, int flags, int
     A.B = cB;
     A.flags = flags | (l->p.expansion ? P_EXPANSION : 0);
     cudaError_t e;
+    // Gauss tracking in the first stage of every step: the staged stage sums it itself; the
+    // other forms launch the rms Gauss reduction on the step's starting state (after the
+    // plaquette fields of that state, which the fused stage does not write)
+    const bool track = what == 1 && (flags & P_FIRST_STAGE) && !(flags & P_ENERGY_ONLY) && !l->u1_staged;
     if (what == 1 && l->u1_fused) {
-        e = launch_u1_fused(l->p.precision, &A, l->stream);  // plaquettes and stage in one launch
+        e = cudaSuccess;
+        if (track) {
+            e = launch_u1(l->p.precision, &A, 0, l->stream);
+            if (e == cudaSuccess) e = launch_u1(l->p.precision, &A, 3, l->stream);
+        }
+        if (e == cudaSuccess) e = launch_u1_fused(l->p.precision, &A, l->stream);  // plaquettes and stage in one launch
     } else if (what == 1 && l->u1_staged) {
         e = launch_u1_staged(l->p.precision, &A, 0, l->stream);  // plaquette fields first
         if (e == cudaSuccess) e = launch_u1_staged(l->p.precision, &A, 1, l->stream);
     } else {
         e = launch_u1(l->p.precision, &A, 0, l->stream);  // plaquette fields first
+        if (e == cudaSuccess && track) e = launch_u1(l->p.precision, &A, 3, l->stream);
         if (e == cudaSuccess) e = launch_u1(l->p.precision, &A, what, l->stream);
     }
     if (e != cudaSuccess) return fail(l, CL_ECUDA, "U(1) launch failed: %s", cudaGetErrorString(e));
@@ -1068,7 +1102,7 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
     const int dims_in = (p->dims == 1 || p->dims == 2) ? p->dims : 3;
     const long long max_n = dims_in == 3 ? kMaxN : (dims_in == 2 ? 46340 : (1ll << 30));
     if ((!ens && (p->N < 2 || p->N > max_n)) || p->nfields < 1 || p->nfields > 2 || p->precision < 0 || p->precision > 2 ||
-        p->integrator < 0 || p->integrator > CL_INT_YOSHIDA10 || p->gauge < 0 || p->gauge > 1 || !(p->L > 0) || !(p->dt > 0) ||
+        p->integrator < 0 || p->integrator > CL_INT_RK3_4 || p->gauge < 0 || p->gauge > 1 || !(p->L > 0) || !(p->dt > 0) ||
         !(p->a0 > 0) || p->dims < 0 || p->dims > 3)
         return CL_EINVAL;
     // reduced (d+1)-dimensional lattices: single lattices of scalar fields
@@ -1171,7 +1205,10 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
         return CL_ENOMEM;
     }
     std::vector<DevScal> h(l->members, DevScal{});
-    for (auto& x : h) x.a = p->a0;
+    for (auto& x : h) {
+        x.a = p->a0;
+        x.h = p->dt;
+    }
     cudaMemcpyAsync(l->scal, h.data(), sizeof(DevScal) * h.size(), cudaMemcpyHostToDevice, l->stream);
     const cl_status ts = choose_tiles(l);
     if (ts != CL_OK) {
@@ -1289,6 +1326,7 @@ cl_status cl_set_scalars(cl_lattice* l, int32_t member, double a, double adot, d
         h[m].a = a;
         h[m].b = isnan(adot) ? 0.0 : adot;
         h[m].t = t;
+        h[m].gauss[0] = h[m].gauss[1] = 0.0;  // Gauss tracking restarts with the new state
     }
     CUDA_TRY(l, cudaMemcpyAsync(l->scal, h.data(), sizeof(DevScal) * h.size(), cudaMemcpyHostToDevice, l->stream));
     CUDA_TRY(l, cudaStreamSynchronize(l->stream));
@@ -1340,6 +1378,8 @@ cl_status cl_set_nonminimal(cl_lattice* l, double xi)
     if (l->dims < 3) return fail(l, CL_EUNSUPPORTED, "the non-minimal coupling is not available on a reduced (1+1)/(2+1) lattice");
     if (is_ens(l) || l->gauge || l->nf != 1 || !is_rk(l->p.integrator))
         return fail(l, CL_EUNSUPPORTED, "the non-minimal coupling needs one scalar field and a Runge-Kutta integrator");
+    if (l->adapt_tol > 0.0)
+        return fail(l, CL_EUNSUPPORTED, "the non-minimal coupling is not available with adaptive steps");
     if (!isfinite(xi)) return fail(l, CL_EINVAL, "xi must be finite");
     cl_status s = grow_partials(l, nmc_grid(l));
     if (s != CL_OK) return s;
@@ -1349,6 +1389,35 @@ cl_status cl_set_nonminimal(cl_lattice* l, double xi)
     l->rbar_valid = false;
     invalidate_graphs(l);
     return choose_tiles(l);  // the stage kernel's buffers grow by the rows of the Ricci terms
+}
+
+cl_status cl_set_adaptive(cl_lattice* l, double tol, double h_min, double h_max)
+{
+    if (!l) return CL_EINVAL;
+    if (l->p.integrator != CL_INT_RK3_4 || is_ens(l) || l->gauge || l->nmc)
+        return fail(l, CL_EUNSUPPORTED, "adaptive steps need a single scalar lattice integrated with RK3-4 "
+                                        "(no gauge field, no non-minimal coupling)");
+    if (!isfinite(tol) || !isfinite(h_min) || !isfinite(h_max))
+        return fail(l, CL_EINVAL, "tolerance and step bounds must be finite");
+    const bool on = tol > 0.0;
+    if (on && (!(h_max > 0.0) || h_min < 0.0 || h_min > h_max))
+        return fail(l, CL_EINVAL, "need 0 <= h_min <= h_max and h_max > 0");
+    std::vector<DevScal> h;
+    cl_status s = read_status(l, h);
+    if (s != CL_OK) return s;
+    if (on && !(l->adapt_tol > 0.0)) {  // start from the lattice's dt (within the bounds)
+        double h0 = l->p.dt;
+        h0 = h0 > h_max ? h_max : (h0 < h_min ? h_min : h0);
+        h[0].h = h0;
+        h[0].rk_err = 0.0;
+        CUDA_TRY(l, cudaMemcpyAsync(l->scal, h.data(), sizeof(DevScal), cudaMemcpyHostToDevice, l->stream));
+        CUDA_TRY(l, cudaStreamSynchronize(l->stream));
+    }
+    l->adapt_tol = on ? tol : 0.0;
+    l->adapt_hmin = on ? h_min : 0.0;
+    l->adapt_hmax = on ? h_max : 0.0;
+    invalidate_graphs(l);  // the stage flags change
+    return CL_OK;
 }
 
 cl_status cl_enable_gw(cl_lattice* l)
@@ -1688,6 +1757,8 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
         // two-launch gauge stages (helper + stage), non-minimally coupled stages (Ricci + stage)
         // and leapfrog passes with gravitational waves (GW pass + scalar pass)
         l->last_launches += (l->gauge && !l->u1_fused) || (l->nmc && !nmc_f) || l->gw ? 2 * pps : pps;
+        // per-step Gauss tracking launches of the U(1) forms whose stage does not sum it itself
+        if (l->gauge && !l->u1_staged) l->last_launches += l->u1_fused ? 2 : 1;
     }
     // a leapfrog step ends with the energies of its integer time; a Runge-Kutta stage
     // reports those of the state it started from, so they are recomputed on demand
@@ -1734,6 +1805,10 @@ cl_status cl_energies(cl_lattice* l, cl_energy* out, int32_t count)
         o->p = h.diag[D_P];
         o->hubble_violation = h.diag[D_HV];
         o->gauss_violation = h.diag[D_GV];
+        o->gauss_rms_step = l->gauge ? h.gauss[0] : 0.0;
+        o->gauss_rms_max = l->gauge ? h.gauss[1] : 0.0;
+        o->dt = l->adapt_tol > 0.0 ? h.h : l->p.dt;
+        o->rk_error = l->adapt_tol > 0.0 ? h.rk_err : 0.0;
         o->step = h.step;
         o->ricci = l->nmc ? h.rbar : 0.0;
     }
@@ -1808,6 +1883,7 @@ cl_status cl_init_vacuum(cl_lattice* l, int32_t member, const cl_vacuum_params* 
             for (int m = m0; m < m1; ++m) {
                 h[m] = DevScal{};
                 h[m].a = a;
+                h[m].h = l->p.dt;
             }
             cudaError_t e = cudaMemcpyAsync(l->scal, h.data(), sizeof(DevScal) * h.size(), cudaMemcpyHostToDevice, l->stream);
             if (e != cudaSuccess) st = fail(l, CL_ECUDA, "scalar upload: %s", cudaGetErrorString(e));

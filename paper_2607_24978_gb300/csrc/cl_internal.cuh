@@ -57,6 +57,10 @@ struct DevScal {
     int status;            // ST_* bits, sticky until read by the host
     double rk[2];          // 2N Runge-Kutta auxiliaries of a and a' (k_a, k_a')
     double rbar;           // background Ricci scalar of the state (non-minimally coupled lattices)
+    double gauss[2];       // U(1): rms Gauss violation of the latest step's starting state, and
+                           // its maximum over the steps since the state was set
+    double h;              // adaptive RK3-4: the step size of the next step (P_DEVICE_H)
+    double rk_err;         // adaptive RK3-4: error estimate of the latest step
 };
 
 // Flags of one fused scalar pass.
@@ -68,6 +72,9 @@ enum : int {
     P_COUNT_STEP = 16,  // this pass ends a time step
     P_FIRST_STAGE = 32, // Runge-Kutta: first stage of a step (A = 0, k is not read)
     P_ENERGY_ONLY = 64, // reduce the energies of the state, update nothing else
+    P_DEVICE_H = 128,   // Runge-Kutta: take the step size from DevScal::h, not from the arguments
+    P_RK_ERROR = 256,   // Runge-Kutta, last stage: reduce the embedded error estimate
+                        //   |B k| / |y| and set DevScal::h of the next step (adaptive RK3-4)
 };
 
 // Largest dynamic shared memory a fused-pass block may use (227 KB per block on sm_103a,
@@ -132,7 +139,8 @@ struct RkStageArgs {
     double A, B, h;     // stage coefficients and the step size
     double m2[2], lam[2], g2;
     double hubble_limit;
-    int flags;          // P_EXPANSION, P_FIRST_STAGE, P_COUNT_STEP
+    double tol, hmin, hmax;  // adaptive step-size control (P_RK_ERROR)
+    int flags;          // P_EXPANSION, P_FIRST_STAGE, P_COUNT_STEP, P_DEVICE_H, P_RK_ERROR
     int nmc;            // non-minimal coupling xi phi^2 R of field 0 (one field): the kick and a''
     double xi;          //   use scal->rbar, written by launch_nmc_ricci for the same state
 };
@@ -191,7 +199,9 @@ struct U1Args {
     int flags;    // P_EXPANSION, P_FIRST_STAGE, P_COUNT_STEP, P_ENERGY_ONLY, P_HUBBLE_INIT
     int dz;       // planes per block (all three kernels)
 };
-// what: 0 = plaquette fields, 1 = stage (or energies with P_ENERGY_ONLY), 2 = Gauss diagnostic.
+// what: 0 = plaquette fields, 1 = stage (or energies with P_ENERGY_ONLY), 2 = Gauss diagnostic,
+// 3 = rms Gauss violation of the state into DevScal::gauss (the staged stage launch computes
+// it itself in the first stage of every step).
 // The plaquette launch writes its magnetic-energy partials after the stage's, at
 // partials[u1_grid_blocks(N, dz) * kMaxQ + block].
 cudaError_t launch_u1(int precision, const void* args, int what, cudaStream_t s);

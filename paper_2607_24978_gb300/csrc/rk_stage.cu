@@ -27,8 +27,11 @@ namespace clk {
 // the last block also writes the background Ricci scalar of that state to scal->rbar, after
 // the stage used the one of its input state (partials of v2 after those of v).
 template <typename T>
-__device__ __forceinline__ void rk_finish(const RkStageArgs<T>& A, double (&v)[kMaxQ], double a_old, bool first,
-                                          double (*s_red)[kMaxQ], int* s_last, int tid, int nthr,
+// With P_RK_ERROR, v2 instead carries the sums |B k|^2 and |y|^2 over the degrees of freedom of
+// the last stage (adaptive RK3-4): the last block sets the next step size from their ratio.
+// h: the step size of this stage.
+__device__ __forceinline__ void rk_finish(const RkStageArgs<T>& A, double (&v)[kMaxQ], double a_old, double h,
+                                          bool first, double (*s_red)[kMaxQ], int* s_last, int tid, int nthr,
                                           double (*v2)[kMaxQ] = nullptr, int dims = 3)
 {
     const int N = A.N;
@@ -94,18 +97,27 @@ __device__ __forceinline__ void rk_finish(const RkStageArgs<T>& A, double (&v)[k
             // Eq. Friedmann1, or for a non-minimally coupled field Eq. piadot with R of the state
             const double Fb = A.nmc ? a * (pow(a, 2.0 * A.alpha) * S->rbar / 6.0 - (1.0 - A.alpha) * (b / a) * (b / a))
                                     : pow(a, 2.0 * A.alpha + 1.0) * (A.kappa / 6.0) * ((2.0 * A.alpha - 1.0) * rho - 3.0 * p);
-            const double ka = first ? A.h * Fa : A.A * S->rk[0] + A.h * Fa;
-            const double kb = first ? A.h * Fb : A.A * S->rk[1] + A.h * Fb;
+            const double ka = first ? h * Fa : A.A * S->rk[0] + h * Fa;
+            const double kb = first ? h * Fb : A.A * S->rk[1] + h * Fb;
             S->rk[0] = ka;
             S->rk[1] = kb;
             S->a = a + A.B * ka;
             S->b = b + A.B * kb;
         }
         if (A.flags & P_COUNT_STEP) {
-            S->t += A.h;
+            S->t += h;
             S->step += 1;
         }
-        if (v2) {  // Eq. eomR for the output state, with its scale factor
+        if (v2 && (A.flags & P_RK_ERROR)) {
+            // embedded estimate |y_4 - y_3| / |y_4| and the step-size controller
+            const double eps = w2[1] > 0.0 ? sqrt(w2[0] / w2[1]) : 0.0;
+            double f = eps > 0.0 ? 0.9 * cbrt(A.tol / eps) : 2.0;
+            f = f > 2.0 ? 2.0 : (f < 0.2 ? 0.2 : f);
+            double hn = h * f;
+            hn = hn > A.hmax ? A.hmax : (hn < A.hmin ? A.hmin : hn);
+            S->rk_err = eps;
+            S->h = hn;
+        } else if (v2) {  // Eq. eomR for the output state, with its scale factor
             const double an = S->a, an2 = an * an;
             const double Kn = w2[0] / (2.0 * an2 * an2 * an2 * vol), Gn = w2[1] / (2.0 * an2 * A.dx * A.dx * vol);
             const double Vn = w2[2] / vol, phidvn = w2[3] / vol, phi2n = w2[4] / vol;
@@ -120,12 +132,14 @@ __device__ __forceinline__ void rk_finish(const RkStageArgs<T>& A, double (&v)[k
     }
 }
 
-template <typename T, int NF, bool KAHAN, int VW>
+// EST: the last stage of an adaptive RK3-4 step, which also sums the embedded error estimate
+// (a separate instance keeps that work and its registers out of the other stages).
+template <typename T, int NF, bool KAHAN, int VW, bool EST>
 __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);  // [NF][3][BY+2][N] old field
-    __shared__ double s_coef[5];
+    __shared__ double s_coef[6];
     __shared__ double s_red[32][kMaxQ];
     __shared__ int s_last;
 
@@ -141,10 +155,12 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
 
     if (tid == 0) {
         const double a = A.scal->a;
-        s_coef[0] = A.h * pow(a, A.alpha - 3.0);
-        s_coef[1] = A.h * pow(a, 1.0 + A.alpha) / (A.dx * A.dx);
-        s_coef[2] = A.h * pow(a, 3.0 + A.alpha);
+        const double h = (A.flags & P_DEVICE_H) ? A.scal->h : A.h;  // adaptive steps: the device's h
+        s_coef[0] = h * pow(a, A.alpha - 3.0);
+        s_coef[1] = h * pow(a, 1.0 + A.alpha) / (A.dx * A.dx);
+        s_coef[2] = h * pow(a, 3.0 + A.alpha);
         s_coef[3] = a;
+        s_coef[5] = h;
         s_coef[4] = A.nmc ? A.xi * A.scal->rbar : 0.0;  // xi R of the stage's state
     }
     __syncthreads();
@@ -152,6 +168,8 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
     const T cA = (T)A.A, cB = (T)A.B;
     const PotCoef<T> P(A.m2, A.lam, A.g2);
     Acc<T> accK[NF], accG[NF], accV;
+    Acc<T> accE, accY;  // adaptive RK3-4, last stage: |B k|^2 and |y|^2
+    constexpr bool est = EST;
 
     int y0 = 0, z0 = 0, R = 1;
     // Load plane z0 + zrel of own and halo rows of the old fields into ring slot `slot`.
@@ -230,7 +248,7 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
                         vload<T, VW>(kp, A.kpi_in[f] + base);
                     }
                     if (KAHAN) vload<T, VW>(cv, A.c_in[f] + base);
-                    T ph[VW], po[VW];
+                    T ph[VW], po[VW], ee = (T)0, ey = (T)0;
 #pragma unroll
                     for (int i = 0; i < VW; ++i) {
                         const T p0 = phc[0][i];
@@ -246,6 +264,11 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
                         ph[i] = phc[f][i];
                         drift<T, KAHAN>(ph[i], cv[i], kf[i], cB);  // phi += B k_phi (compensated in FP32)
                         po[i] = pv[i] + cB * kp[i];
+                        if (est) {
+                            const T dp = cB * kf[i], dq = cB * kp[i];
+                            ee += dp * dp + dq * dq;
+                            ey += ph[i] * ph[i] + po[i] * po[i];
+                        }
                         if (f == 0) {
                             T v = p0 * p0 * (P.h_m20 + P.q_l0 * p0 * p0);
                             if (NF > 1) v += p1 * p1 * (P.h_m21 + P.q_l1 * p1 * p1) + P.h_g2 * p0 * p0 * p1 * p1;
@@ -253,6 +276,10 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
                         }
                     }
                     accK[f].add(ksum);
+                    if (est) {
+                        accE.add(ee);
+                        accY.add(ey);
+                    }
                     vstore<T, VW>(A.phi_out[f] + base, ph);
                     vstore<T, VW>(A.pi_out[f] + base, po);
                     vstore<T, VW>(A.kphi_out[f] + base, kf);
@@ -272,7 +299,8 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
     v[2] = accG[0].value();
     v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
     v[4] = accV.value();
-    rk_finish(A, v, s_coef[3], first, s_red, &s_last, tid, nthr);
+    double ve[kMaxQ] = {accE.value(), accY.value(), 0.0, 0.0, 0.0};
+    rk_finish(A, v, s_coef[3], s_coef[5], first, s_red, &s_last, tid, nthr, est ? &ve : nullptr);
 }
 
 // TMA-staged form of the same stage.  One producer warp copies, plane after plane, the rows
@@ -292,7 +320,7 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
 // the tile's last row, the vector edges and the chunk's last plane, so the stage buffers
 // then also hold pi (, c), k_phi of the row y0+R and of the upper halo plane, from which a
 // consumer recomputes the new field there with the owner's operations.
-template <typename T, int NF, bool KAHAN, int VW, int S>
+template <typename T, int NF, bool KAHAN, int VW, int S, bool EST>
 __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
 {
     constexpr int NOWN = KAHAN ? 4 : 3;  // own-row arrays per field: pi (, c), k_phi, k_pi
@@ -300,7 +328,7 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_full[S];
     __shared__ __align__(8) uint64_t s_empty[S];
-    __shared__ double s_coef[5];
+    __shared__ double s_coef[6];
     __shared__ double s_red[32][kMaxQ];
     __shared__ int s_last, s_timeout;
 
@@ -327,10 +355,12 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
 
     if (tid == 0) {
         const double a = A.scal->a;
-        s_coef[0] = A.h * pow(a, A.alpha - 3.0);
-        s_coef[1] = A.h * pow(a, 1.0 + A.alpha) / (A.dx * A.dx);
-        s_coef[2] = A.h * pow(a, 3.0 + A.alpha);
+        const double h = (A.flags & P_DEVICE_H) ? A.scal->h : A.h;  // adaptive steps: the device's h
+        s_coef[0] = h * pow(a, A.alpha - 3.0);
+        s_coef[1] = h * pow(a, 1.0 + A.alpha) / (A.dx * A.dx);
+        s_coef[2] = h * pow(a, 3.0 + A.alpha);
         s_coef[3] = a;
+        s_coef[5] = h;
         s_coef[4] = A.nmc ? A.xi * A.scal->rbar : 0.0;  // xi R of the stage's state
 #pragma unroll
         for (int k = 0; k < S; ++k) {
@@ -342,6 +372,8 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
     }
     __syncthreads();
     Acc<T> accK[NF], accG[NF], accV;
+    Acc<T> accE, accY;  // adaptive RK3-4, last stage: |B k|^2 and |y|^2
+    constexpr bool est = EST;
     Acc<T> nK, nG, nV, nPV, nP2;  // Ricci terms of the output state (fuse_r)
     auto bounded = [&](uint64_t* bar, uint32_t parity) {
         if (!mbar_wait_bounded(bar, parity, s_timeout ? 1000000ull : 2000000000ull)) s_timeout = 1;
@@ -514,7 +546,7 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
                                 vload_smem<T, VW>(kp, ob + OKP * own_stride);
                             }
                             if (KAHAN) vload_smem<T, VW>(cv, ob + (KAHAN ? OC : 0) * own_stride);
-                            T ph[VW], po[VW];
+                            T ph[VW], po[VW], ee = (T)0, ey = (T)0;
 #pragma unroll
                             for (int i = 0; i < VW; ++i) {
                                 const T p0 = phc[0][i];
@@ -530,6 +562,11 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
                                 ph[i] = phc[f][i];
                                 drift<T, KAHAN>(ph[i], cv[i], kf[i], cB);  // phi += B k_phi (compensated in FP32)
                                 po[i] = pv[i] + cB * kp[i];
+                                if (est) {
+                                    const T dp = cB * kf[i], dq = cB * kp[i];
+                                    ee += dp * dp + dq * dq;
+                                    ey += ph[i] * ph[i] + po[i] * po[i];
+                                }
                                 if (f == 0) {
                                     T v = p0 * p0 * (P.h_m20 + P.q_l0 * p0 * p0);
                                     if (NF > 1) v += p1 * p1 * (P.h_m21 + P.q_l1 * p1 * p1) + P.h_g2 * p0 * p0 * p1 * p1;
@@ -537,6 +574,10 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
                                 }
                             }
                             accK[f].add(ksum);
+                            if (est) {
+                                accE.add(ee);
+                                accY.add(ey);
+                            }
                             if (fuse_r && f == 0) {
                                 // Ricci terms of the output state at this vector: local ones, and the
                                 // forward differences in x and y (z: with the previous plane)
@@ -604,7 +645,11 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
     v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
     v[4] = accV.value();
     double v2[kMaxQ] = {nK.value(), nG.value(), nV.value(), nPV.value(), nP2.value()};
-    rk_finish(A, v, s_coef[3], first, s_red, &s_last, tid, nthr, fuse_r ? &v2 : nullptr);
+    if (est) {  // adaptive RK3-4 (never with the Ricci terms)
+        v2[0] = accE.value();
+        v2[1] = accY.value();
+    }
+    rk_finish(A, v, s_coef[3], s_coef[5], first, s_red, &s_last, tid, nthr, fuse_r || est ? &v2 : nullptr);
 }
 
 // The stage on a reduced (d+1)-dimensional lattice (section "Scalar dynamics in 1+1 and 2+1
@@ -613,17 +658,19 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
 template <typename T, int NF, bool KAHAN>
 __global__ void __launch_bounds__(256) k_reduced_rk(const RkStageArgs<T> A, int dims)
 {
-    __shared__ double s_coef[5];
+    __shared__ double s_coef[6];
     __shared__ double s_red[32][kMaxQ];
     __shared__ int s_last;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const bool first = (A.flags & P_FIRST_STAGE) != 0;
     if (tid == 0) {
         const double a = A.scal->a;
-        s_coef[0] = A.h * pow(a, A.alpha - 3.0);
-        s_coef[1] = A.h * pow(a, 1.0 + A.alpha) / (A.dx * A.dx);
-        s_coef[2] = A.h * pow(a, 3.0 + A.alpha);
+        const double h = (A.flags & P_DEVICE_H) ? A.scal->h : A.h;  // adaptive steps: the device's h
+        s_coef[0] = h * pow(a, A.alpha - 3.0);
+        s_coef[1] = h * pow(a, 1.0 + A.alpha) / (A.dx * A.dx);
+        s_coef[2] = h * pow(a, 3.0 + A.alpha);
         s_coef[3] = a;
+        s_coef[5] = h;
         s_coef[4] = 0.0;
     }
     __syncthreads();
@@ -632,6 +679,8 @@ __global__ void __launch_bounds__(256) k_reduced_rk(const RkStageArgs<T> A, int 
     const PotCoef<T> P(A.m2, A.lam, A.g2);
     const long long N = A.N, V = dims == 1 ? N : N * N;
     Acc<T> accK[NF], accG[NF], accV;
+    Acc<T> accE, accY;  // adaptive RK3-4, last stage: |B k|^2 and |y|^2
+    const bool est = (A.flags & P_RK_ERROR) != 0;
     for (long long n = blockIdx.x * (long long)nthr + tid; n < V; n += (long long)gridDim.x * nthr) {
         const long long x = n % N, row = n - x;
         const long long xm = row + (x == 0 ? N - 1 : x - 1), xp = row + (x + 1 == N ? 0 : x + 1);
@@ -675,8 +724,13 @@ __global__ void __launch_bounds__(256) k_reduced_rk(const RkStageArgs<T> A, int 
             T phn = phc[f];
             drift<T, KAHAN>(phn, cv, kf, cB);  // phi += B k_phi (compensated in FP32)
             accK[f].add(pv * pv);
+            const T pn = pv + cB * kp;
+            if (est) {
+                accE.add(cB * kf * (cB * kf) + cB * kp * (cB * kp));
+                accY.add(phn * phn + pn * pn);
+            }
             (f == 0 ? A.phi_out[0] : A.phi_out[NF - 1])[n] = phn;
-            (f == 0 ? A.pi_out[0] : A.pi_out[NF - 1])[n] = pv + cB * kp;
+            (f == 0 ? A.pi_out[0] : A.pi_out[NF - 1])[n] = pn;
             (f == 0 ? A.kphi_out[0] : A.kphi_out[NF - 1])[n] = kf;
             (f == 0 ? A.kpi_out[0] : A.kpi_out[NF - 1])[n] = kp;
             if (KAHAN) (f == 0 ? A.c_out[0] : A.c_out[NF - 1])[n] = cv;
@@ -694,7 +748,8 @@ __global__ void __launch_bounds__(256) k_reduced_rk(const RkStageArgs<T> A, int 
     v[2] = accG[0].value();
     v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
     v[4] = accV.value();
-    rk_finish(A, v, s_coef[3], first, s_red, &s_last, tid, nthr, nullptr, dims);
+    double ve[kMaxQ] = {accE.value(), accY.value(), 0.0, 0.0, 0.0};
+    rk_finish(A, v, s_coef[3], s_coef[5], first, s_red, &s_last, tid, nthr, est ? &ve : nullptr, dims);
 }
 
 // Background Ricci scalar of a non-minimally coupled field (section "Scalar fields
@@ -826,14 +881,18 @@ static cudaError_t launch_rk(const RkStageArgs<T>& A, cudaStream_t s)
     dim3 block(((TX * A.BY + 31) / 32) * 32);
     dim3 grid(A.nby * A.nbz);
     const size_t smem = (size_t)NF * 3 * (A.BY + 2) * A.N * sizeof(T);
-    static DevFlag attr_set;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_rk_stage<T, NF, KAHAN, VW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kPassMaxSmem);
+    static DevFlag attr_set[2];
+    const bool est = (A.flags & P_RK_ERROR) != 0;
+    if (!attr_set[est]) {
+        cudaError_t e = est ? cudaFuncSetAttribute(k_rk_stage<T, NF, KAHAN, VW, true>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kPassMaxSmem)
+                            : cudaFuncSetAttribute(k_rk_stage<T, NF, KAHAN, VW, false>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kPassMaxSmem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set[est] = true;
     }
-    k_rk_stage<T, NF, KAHAN, VW><<<grid, block, smem, s>>>(A);
+    if (est) k_rk_stage<T, NF, KAHAN, VW, true><<<grid, block, smem, s>>>(A);
+    else k_rk_stage<T, NF, KAHAN, VW, false><<<grid, block, smem, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -878,17 +937,21 @@ static cudaError_t launch_rk_tma(const RkStageArgs<T>& A, int stages, cudaStream
         const size_t smem = rk_stage_tma_smem(prec, NF, A.N, A.BY, stages, A.nmc == 2);
         if (block.x > 480 || smem > (size_t)kPassMaxSmem || A.N % VW != 0 || (A.nmc == 2 && NF != 1))
             return cudaErrorInvalidValue;
-        static DevFlag attr[7];
+        static DevFlag attr[2][7];
+        const bool est = (A.flags & P_RK_ERROR) != 0;
         cudaError_t e = cudaSuccess;
 #define CL_RKT_CASE(SS)                                                                                         \
     case SS:                                                                                                    \
-        if (!attr[SS]) {                                                                                        \
-            e = cudaFuncSetAttribute(k_rk_stage_tma<T, NF, KAHAN, VW, SS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                     kPassMaxSmem);                                                             \
+        if (!attr[est][SS]) {                                                                                   \
+            e = est ? cudaFuncSetAttribute(k_rk_stage_tma<T, NF, KAHAN, VW, SS, true>,                          \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kPassMaxSmem)           \
+                    : cudaFuncSetAttribute(k_rk_stage_tma<T, NF, KAHAN, VW, SS, false>,                         \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kPassMaxSmem);          \
             if (e != cudaSuccess) return e;                                                                     \
-            attr[SS] = true;                                                                                    \
+            attr[est][SS] = true;                                                                               \
         }                                                                                                       \
-        k_rk_stage_tma<T, NF, KAHAN, VW, SS><<<grid, block, smem, s>>>(A);                                       \
+        if (est) k_rk_stage_tma<T, NF, KAHAN, VW, SS, true><<<grid, block, smem, s>>>(A);                       \
+        else k_rk_stage_tma<T, NF, KAHAN, VW, SS, false><<<grid, block, smem, s>>>(A);                          \
         return cudaGetLastError();
         switch (stages) {
             CL_RKT_CASE(3)

@@ -104,7 +104,20 @@ __global__ void __launch_bounds__(512) k_scalar_pass(const ScalarPassArgs<T> A)
     long long u0, u1;
     block_units(N, A.nby, A.DZ, u0, u1);
 
-    if (tid == 0) pass_coefficients(A.scal->a, A.scal->b, A.d, A.alpha, A.dx, (A.flags & P_EXPANSION) != 0, s_coef);
+    // FP64: the summation-by-parts gradient sum (see kick_vector) needs one constant per field
+    // that every block takes alike: the drifted field at site 0, computed here by each block
+    // with the drift's own operation.
+    constexpr bool SBP = sizeof(T) == 8 && !KAHAN;
+    __shared__ T s_gC[2];
+    if (tid == 0) {
+        pass_coefficients(A.scal->a, A.scal->b, A.d, A.alpha, A.dx, (A.flags & P_EXPANSION) != 0, s_coef);
+        if (SBP)
+            for (int f = 0; f < NF; ++f) {
+                T ph = A.phi_in[f][0], c0 = (T)0;
+                if (A.flags & P_DRIFT) drift<T, false>(ph, c0, A.pi_in[f][0], (T)s_coef[0]);
+                s_gC[f] = ph;
+            }
+    }
     __syncthreads();
     const TileCoef<T> C{(T)s_coef[0], (T)s_coef[1], (T)s_coef[2], (T)A.e, (T)A.k};
     const bool do_drift = (A.flags & P_DRIFT) != 0;
@@ -112,6 +125,9 @@ __global__ void __launch_bounds__(512) k_scalar_pass(const ScalarPassArgs<T> A)
     const FieldSet<T> F{{A.phi_in[0], A.phi_in[1]}, {A.pi_in[0], A.pi_in[1]}, {A.c_in[0], A.c_in[1]},
                         {A.phi_out[0], A.phi_out[1]}, {A.pi_out[0], A.pi_out[1]}, {A.c_out[0], A.c_out[1]}};
     Acc<T> accK[NF], accG[NF], accV;
+    T gC[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) gC[f] = SBP ? s_gC[f] : (T)0;
 
     // segments of this block's unit range: one y tile, consecutive z planes
     for (long long u = u0; u < u1;) {
@@ -121,7 +137,8 @@ __global__ void __launch_bounds__(512) k_scalar_pass(const ScalarPassArgs<T> A)
         const int y0 = tile * BY;
         const int R = min(BY, N - y0);
         u += NZ;
-        march_tile<T, NF, KAHAN, VW>(F, N, BY, y0, R, z0, NZ, sm, tid, nthr, do_drift, C, P, accK, accG, accV);
+        march_tile<T, NF, KAHAN, VW, SBP>(F, N, BY, y0, R, z0, NZ, sm, tid, nthr, do_drift, C, P, accK, accG, accV,
+                                          gC);
     }
     finish_pass<T, NF>(A, accK, accG, accV, s_coef, s_red, &s_last, tid, nthr, 0);
 }

@@ -45,14 +45,77 @@ __device__ __forceinline__ void pass_coefficients_warps(int tid, const double a_
 // Kick of one own-row vector of a plane.  S*[f] point at row (r+1) of the centre
 // (Sc), lower (Szm) and upper (Szp) planes of field f; rows r and r+2 of the
 // centre plane are Sc -/+ N.  Writes pi_out and accumulates K, G, V.
-template <typename T, int NF, int VW>
+//
+// SBP (used by the FP64 direct-load pass, whose speed is set by GB300's FP64 rate, not
+// by memory): fewer FP64 operations for the same quantities.  The gradient sum
+// sum_n sum_i (phi(n+i) - phi(n))^2 equals -sum_n phi(n) Lap phi(n) dx^2 on the periodic
+// lattice (summation by parts), and sum_n Lap phi(n) = 0, so it is accumulated as
+// sum_n (C - phi(n)) Lap phi(n) dx^2 with a constant C that every block of the lattice
+// takes the same (gC[f]: the drifted field at site 0); subtracting C keeps the products
+// small, so the rounding of Lap phi does not swamp the sum.  The potential and its
+// derivatives are evaluated in Horner form on phi^2.
+template <typename T, int NF, int VW, bool SBP = false>
 __device__ __forceinline__ void kick_vector(const T* const (&Sc)[NF], const T* const (&Szm)[NF],
                                             const T* const (&Szp)[NF], int N, int x0, const T (&pin)[NF][VW],
                                             const T cL, const T cV, const T ce, const T ck, const PotCoef<T>& P,
                                             T* const* pi_out, size_t base, Acc<T> (&accK)[NF],
-                                            Acc<T> (&accG)[NF], Acc<T>& accV)
+                                            Acc<T> (&accG)[NF], Acc<T>& accV, const T* gC = nullptr)
 {
     T phc[NF][VW], lap[NF][VW];
+    if constexpr (SBP) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            T c[VW], ym[VW], yp[VW], zm[VW], zp[VW];
+            vload_smem<T, VW>(c, Sc[f] + x0);
+            vload_smem<T, VW>(ym, Sc[f] - N + x0);
+            vload_smem<T, VW>(yp, Sc[f] + N + x0);
+            vload_smem<T, VW>(zm, Szm[f] + x0);
+            vload_smem<T, VW>(zp, Szp[f] + x0);
+            const T xm_edge = Sc[f][x0 == 0 ? N - 1 : x0 - 1];
+            const T xp_edge = Sc[f][x0 + VW == N ? 0 : x0 + VW];
+            const T Cf = gC[f];
+            T g = (T)0;
+#pragma unroll
+            for (int i = 0; i < VW; ++i) {
+                const T xm = i == 0 ? xm_edge : c[i - 1];
+                const T xp = i == VW - 1 ? xp_edge : c[i + 1];
+                lap[f][i] = ((xp + xm) + (yp[i] + ym[i]) + (zp[i] + zm[i])) - (T)6 * c[i];
+                g = fma_rn(Cf - c[i], lap[f][i], g);
+                phc[f][i] = c[i];
+            }
+            accG[f].add(g);
+        }
+        T vsum = (T)0;
+        T dV[NF][VW];
+#pragma unroll
+        for (int i = 0; i < VW; ++i) {
+            const T p0 = phc[0][i], P0 = p0 * p0;
+            if constexpr (NF > 1) {
+                const T p1 = phc[NF - 1][i], P1 = p1 * p1;
+                dV[0][i] = p0 * fma_rn(P.l0, P0, fma_rn(P.g2, P1, P.m20));
+                dV[NF - 1][i] = p1 * fma_rn(P.l1, P1, fma_rn(P.g2, P0, P.m21));
+                vsum += fma_rn(P0, fma_rn(P.q_l0, P0, P.h_m20), P1 * fma_rn(P.q_l1, P1, fma_rn(P.h_g2, P0, P.h_m21)));
+            } else {
+                dV[0][i] = p0 * fma_rn(P.l0, P0, P.m20);
+                vsum += P0 * fma_rn(P.q_l0, P0, P.h_m20);
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            T po[VW], ksum = (T)0;
+#pragma unroll
+            for (int i = 0; i < VW; ++i) {
+                const T F = cL * lap[f][i] - cV * dV[f][i];
+                const T pe = pin[f][i] + ce * F;
+                po[i] = pin[f][i] + ck * F;
+                ksum += pe * pe;
+            }
+            accK[f].add(ksum);
+            vstore<T, VW>(pi_out[f] + base, po);
+        }
+        accV.add(vsum);
+        return;
+    }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         T c[VW], ym[VW], yp[VW], zm[VW], zp[VW];
@@ -125,11 +188,11 @@ struct TileCoef {
 // the plane being kicked; thread tid < BY*(N/VW) owns one row vector.  Every output is
 // written once; loads of the halo rows (and planes) are the only re-reads.  Ends with a
 // block barrier, so the ring may be refilled at once.
-template <typename T, int NF, bool KAHAN, int VW>
+template <typename T, int NF, bool KAHAN, int VW, bool SBP = false>
 __device__ __forceinline__ void march_tile(const FieldSet<T>& F, int N, int BY, int y0, int R, int z0, int NZ,
                                            T* sm, int tid, int nthr, bool do_drift, const TileCoef<T>& C,
                                            const PotCoef<T>& P, Acc<T> (&accK)[NF], Acc<T> (&accG)[NF],
-                                           Acc<T>& accV)
+                                           Acc<T>& accV, const T* gC = nullptr)
 {
     const int TX = N / VW;
     const int r = tid < BY * TX ? tid / TX : BY, tx = tid < BY * TX ? tid % TX : 0;
@@ -199,8 +262,8 @@ __device__ __forceinline__ void march_tile(const FieldSet<T>& F, int N, int BY, 
                 Szp[f] = sm + f * field_stride + su * slot_stride + (r + 1) * N;
             }
             const size_t base = ((size_t)(z0 + zr) * N + (y0 + r)) * N + x0;
-            kick_vector<T, NF, VW>(Sc, Szm, Szp, N, x0, pcur, C.cL, C.cV, C.ce, C.ck, P, F.pi_out, base, accK, accG,
-                                   accV);
+            kick_vector<T, NF, VW, SBP>(Sc, Szm, Szp, N, x0, pcur, C.cL, C.cV, C.ce, C.ck, P, F.pi_out, base, accK,
+                                        accG, accV, gC);
         }
 #pragma unroll
         for (int f = 0; f < NF; ++f)

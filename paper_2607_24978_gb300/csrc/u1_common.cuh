@@ -12,6 +12,18 @@
 
 namespace clk {
 
+// Per-step Gauss tracking: from gsum = sum_n (dx G(n))^2, the squared lattice Gauss charge
+// of the step's starting state (G = sum_i [P_i(n) - P_i(n - i)] / dx, P = a^(1-alpha) E + g W),
+// and e2sum = sum_n sum_i E_i(n)^2, the rms violation relative to the electric term,
+//     r = sqrt(gsum) / (a^(1-alpha) sqrt(e2sum))      (0 when gsum = 0),
+// stored as the latest value and folded into the running maximum.  One thread.
+__device__ __forceinline__ void u1_gauss_track(DevScal* S, double gsum, double e2sum, double ca)
+{
+    const double r = gsum > 0.0 ? sqrt(gsum) / (ca * sqrt(e2sum)) : 0.0;
+    S->gauss[0] = r;
+    S->gauss[1] = fmax(S->gauss[1], r);
+}
+
 template <typename T>
 __device__ __forceinline__ void u1_epilogue(const U1Args<T>& A, const double (&w)[kMaxQ], double a_old, bool first,
                                             bool update, bool expand, uint32_t V)

@@ -266,9 +266,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_u1_stage(const 
 }
 
 // Lattice Gauss charge G(n) = sum_i [P_i(n) - P_i(n - i)] / dx, P = a^(1-alpha) E + g W.
-// Writes diag[D_GV] = max_n |G(n)| / max_n sum_i (|P_i(n)| + |P_i(n - i)|) / dx.
+// mode 0 writes diag[D_GV] = max_n |G(n)| / max_n sum_i (|P_i(n)| + |P_i(n - i)|) / dx;
+// mode 1 (per-step tracking, for the launch forms whose stage does not sum it itself) the
+// rms violation sqrt(sum_n (dx G)^2) / (a^(1-alpha) sqrt(sum_n E^2)) into DevScal::gauss.
 template <typename T>
-__global__ void __launch_bounds__(256) k_u1_gauss(const U1Args<T> A)
+__global__ void __launch_bounds__(256) k_u1_gauss(const U1Args<T> A, int mode)
 {
     __shared__ double s_red[32][kMaxQ];
     __shared__ int s_last;
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(256) k_u1_gauss(const U1Args<T> A)
     const int tid = threadIdx.x, nthr = blockDim.x;
     const double ca = pow(A.scal->a, 1.0 - A.alpha);
     const double b4 = 0.25 / (A.dx * A.dx);
-    double gmax = 0.0, smax = 0.0;
+    double gmax = 0.0, smax = 0.0, gsq = 0.0, e2 = 0.0;
     const U1Tile tile(N, (uint32_t)A.dz);
     for (uint32_t z = tile.z0; z < tile.z1; ++z) {
         if (!tile.active) break;
@@ -294,9 +296,36 @@ __global__ void __launch_bounds__(256) k_u1_gauss(const U1Args<T> A)
             const double Pm = ca * (double)A.E_in[i][nm] + A.g * 0.5 * ((double)A.phi_in[nm] * Bm + (double)A.phi_in[n] * Bn);
             G += Pn - Pm;
             sc += fabs(Pn) + fabs(Pm);
+            e2 += (double)A.E_in[i][n] * (double)A.E_in[i][n];
         }
         gmax = fmax(gmax, fabs(G) / A.dx);
         smax = fmax(smax, sc / A.dx);
+        gsq += G * G;
+    }
+    if (mode == 1) {  // sums in a fixed order, then the last block stores the tracked value
+        double v[2] = {gsq, e2};
+        block_reduce<2>(v, s_red, tid, nthr);
+        if (tid == 0) {
+            A.partials[(size_t)blockIdx.x * kMaxQ + 0] = v[0];
+            A.partials[(size_t)blockIdx.x * kMaxQ + 1] = v[1];
+            __threadfence();
+            const unsigned prev = atomicAdd(&A.scal->counter, 1u);
+            s_last = (prev + 1u == gridDim.x);
+        }
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        double w[2] = {0.0, 0.0};
+        for (int b = tid; b < (int)gridDim.x; b += nthr) {
+            w[0] += __ldcg(&A.partials[(size_t)b * kMaxQ + 0]);
+            w[1] += __ldcg(&A.partials[(size_t)b * kMaxQ + 1]);
+        }
+        block_reduce<2>(w, s_red, tid, nthr);
+        if (tid == 0) {
+            u1_gauss_track(A.scal, w[0], w[1], ca);
+            A.scal->counter = 0u;
+        }
+        return;
     }
     // block maxima (fixed order), then the last block combines them
     for (int off = 16; off > 0; off >>= 1) {
@@ -346,7 +375,7 @@ static cudaError_t launch_u1_t(const U1Args<T>& A, int what, cudaStream_t s)
     const int grid = u1_grid(A.N, A.dz);
     if (what == 0) k_u1_plaquettes<T><<<grid, 256, 0, s>>>(A);
     else if (what == 1) k_u1_stage<T><<<grid, 256, 0, s>>>(A);
-    else k_u1_gauss<T><<<grid, 256, 0, s>>>(A);
+    else k_u1_gauss<T><<<grid, 256, 0, s>>>(A, what == 3 ? 1 : 0);
     return cudaGetLastError();
 }
 

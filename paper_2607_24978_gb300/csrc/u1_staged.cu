@@ -308,7 +308,10 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquettes(const U1Ar
     }
 }
 
-template <typename T>
+// TRACK: the first stage of a step, which also sums the squared lattice Gauss charge of its
+// input state (the state at the step's start), so that the Gauss constraint is tracked each
+// step; a separate instance keeps that work, and its registers, out of the other stages.
+template <typename T, bool TRACK>
 __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T> A)
 {
     using G = U1SGeom<T>;
@@ -316,12 +319,13 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
     extern __shared__ __align__(128) unsigned char u1s_dyn[];
     __shared__ const T* s_src[NA];
     __shared__ __align__(8) uint64_t s_full[G::SLOTS], s_empty[G::SLOTS];
-    __shared__ double s_coef[6];
+    __shared__ double s_coef[7];
     __shared__ double s_red[32][kMaxQ];
     __shared__ int s_last, s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool first = (A.flags & P_FIRST_STAGE) != 0;
     const bool update = (A.flags & P_ENERGY_ONLY) == 0;
+    constexpr bool track = TRACK;
     const bool expand = (A.flags & P_EXPANSION) != 0;
     if (tid == 0) {
         const double a = A.scal->a, b = expand ? A.scal->b : 0.0;
@@ -331,6 +335,7 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
         s_coef[3] = pow(a, A.alpha - 1.0);                 // E' prefactor
         s_coef[4] = (1.0 - A.alpha) * b / a;               // electric friction
         s_coef[5] = a;
+        s_coef[6] = pow(a, 1.0 - A.alpha);                 // a^(1-alpha) E in the Gauss charge
         s_src[SG_PHI] = A.phi_in;
         s_src[SG_PI] = A.pi_in;
 #pragma unroll
@@ -355,11 +360,12 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
     __syncthreads();
     const U1SRing<T, NA> ring{ring_sm, table, s_full, s_empty, &s_fail};
     const uint32_t N = t.N, V = N * N * N;
-    Acc<T> accK, accG, accV, accKE;
+    Acc<T> accK, accG, accV, accKE, accGs;
     if (warp >= G::CW) {
         ring.produce(tid - 32 * G::CW, s_src, t);
     } else {
         const T c_dphi = (T)s_coef[0], cL = (T)s_coef[1], cV = (T)s_coef[2], cE = (T)s_coef[3], cfr = (T)s_coef[4];
+        const T ca = (T)s_coef[6];
         const T g = (T)A.g, ws2 = (T)A.ws2, dx = (T)A.dx, m2 = (T)A.m2, lam = (T)A.lam;
         const T inv_dx3 = (T)(1.0 / (A.dx * A.dx * A.dx)), inv4dx = (T)(0.25 / A.dx);
         const T inv4dx2 = (T)(0.25 / (A.dx * A.dx));
@@ -409,6 +415,19 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
             accV.add(ph * ph * ((T)0.5 * m2 + (T)0.25 * lam * ph * ph));
             accKE.add(e2);
             if (update) {
+                if constexpr (TRACK) {
+                    // dx times the lattice Gauss charge sum_i [P_i(n) - P_i(n - i)] of the input
+                    // state, P_i = a^(1-alpha) E_i + g W_i (the phi B terms at n cancel)
+                    T gd = (T)0;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const T Bpi = inv4dx2 * S.clover(SG_SP + i, i, U1S_E(i, 1));
+                        const T Bmi = inv4dx2 * S.clover(SG_SP + i, i, U1S_E(i, -1));
+                        gd += ca * (Ecur[i] - S(SG_E + i, U1S_E(i, -1))) +
+                              (T)0.5 * g * (S(SG_PHI, U1S_E(i, 1)) * Bpi - S(SG_PHI, U1S_E(i, -1)) * Bmi);
+                    }
+                    accGs.add(gd * gd);
+                }
                 // link forces
                 T F_E[3];
 #pragma unroll
@@ -449,7 +468,9 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
     __syncthreads();  // producer and consumers meet; no copy is in flight past this point
 
     // ---- block partials; last block: energies of the old state and the (a, a') stage ----
-    double v[kMaxQ] = {accK.value(), accG.value(), accV.value(), accKE.value(), 0.0};
+    // slot 4 of the stage's partials carries the Gauss sum (the magnetic energy's partials
+    // follow in the plaquette launch's region)
+    double v[kMaxQ] = {accK.value(), accG.value(), accV.value(), accKE.value(), accGs.value()};
     block_reduce<kMaxQ>(v, s_red, tid, G::NT);
     if (tid == 0) {
         if (s_fail) atomicOr(&A.scal->status, ST_TIMEOUT);
@@ -463,13 +484,19 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
     if (!s_last) return;
     __threadfence();
     double w[kMaxQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double wg[1] = {0.0};
     for (int b = tid; b < (int)gridDim.x; b += G::NT) {
 #pragma unroll
         for (int q = 0; q < kMaxQ - 1; ++q) w[q] += __ldcg(&A.partials[(size_t)b * kMaxQ + q]);
         w[kMaxQ - 1] += __ldcg(&A.partials[(size_t)gridDim.x * kMaxQ + b]);  // plaquette launch, same grid
+        wg[0] += __ldcg(&A.partials[(size_t)b * kMaxQ + kMaxQ - 1]);
     }
     block_reduce<kMaxQ>(w, s_red, tid, G::NT);
-    if (tid == 0) u1_epilogue(A, w, s_coef[5], first, update, expand, V);
+    if (track) block_reduce<1>(wg, s_red, tid, G::NT);
+    if (tid == 0) {
+        if (track) u1_gauss_track(A.scal, wg[0], w[3], s_coef[6]);
+        u1_epilogue(A, w, s_coef[5], first, update, expand, V);
+    }
 }
 
 #undef U1S_E
@@ -509,7 +536,7 @@ static cudaError_t launch_u1s_t(const U1Args<T>& A, int what, cudaStream_t s)
     using G = U1SGeom<T>;
     if (!u1_staged_ok(A.N) || A.dz < 1 || A.dz > A.N) return cudaErrorInvalidValue;
     const int grid = u1_staged_blocks(sizeof(T) == 8 ? CL_PREC_FP64 : CL_PREC_FP32, A.N, A.dz);
-    static DevFlag attr[2];
+    static DevFlag attr[3];
     if (what == 0) {
         constexpr size_t smem = u1s_smem_bytes<T, PQ_NA>();
         if (!attr[0]) {
@@ -521,12 +548,17 @@ static cudaError_t launch_u1s_t(const U1Args<T>& A, int what, cudaStream_t s)
         k_u1s_plaquettes<T><<<grid, G::NT, smem, s>>>(A);
     } else {
         constexpr size_t smem = u1s_smem_bytes<T, SG_NA>();
-        if (!attr[1]) {
-            const cudaError_t e = cudaFuncSetAttribute(k_u1s_stage<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const bool track = (A.flags & P_FIRST_STAGE) && !(A.flags & P_ENERGY_ONLY);
+        if (!attr[track ? 2 : 1]) {
+            const cudaError_t e = track ? cudaFuncSetAttribute(k_u1s_stage<T, true>,
+                                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                                        : cudaFuncSetAttribute(k_u1s_stage<T, false>,
+                                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            attr[1] = true;
+            attr[track ? 2 : 1] = true;
         }
-        k_u1s_stage<T><<<grid, G::NT, smem, s>>>(A);
+        if (track) k_u1s_stage<T, true><<<grid, G::NT, smem, s>>>(A);
+        else k_u1s_stage<T, false><<<grid, G::NT, smem, s>>>(A);
     }
     return cudaGetLastError();
 }

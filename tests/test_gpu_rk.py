@@ -60,7 +60,7 @@ def run_pair(cl, N, nf, prec, integ, scheme, nsteps, dt=0.01, graph=1, seed=31, 
     return gphi, gpi, e, st, O.energies(m, st), launches
 
 
-@pytest.mark.parametrize("integ,scheme,stages", [(2, O.RK3_3, 3), (3, O.RK4_5, 5)])
+@pytest.mark.parametrize("integ,scheme,stages", [(2, O.RK3_3, 3), (3, O.RK4_5, 5), (7, O.RK3_4, 4)])
 @pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4), (2, 1e-4)])
 def test_rk_parity(cl, integ, scheme, stages, prec, tol):
     gphi, gpi, e, st, eo, launches = run_pair(cl, 16, 2, prec, integ, scheme, 30)
@@ -220,3 +220,88 @@ def test_nmc_needs_one_field_and_runge_kutta(cl):
     with cl.Lattice(8, 6.0, 1, 0, cl.CL_INT_RK3_3) as g:
         with pytest.raises(cl.CLError):
             g.cl_set_nonminimal(float("nan"))
+
+
+@pytest.mark.parametrize("N,nf,stages_opt", [(16, 2, 0), (32, 1, 0), (32, 2, -1), (15, 1, 0)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4)])
+def test_rk34_adaptive_matches_oracle(cl, N, nf, stages_opt, prec, tol):
+    """Adaptive RK3-4 (cl_set_adaptive): every step is taken and its last stage sets the next
+    step size on the device from the embedded estimate |y_4 - y_3| / |y_4|.  The GPU's step
+    sizes, estimates, fields and scale factor follow the oracle's adaptive driver step by step
+    (the TMA-staged stage kernel, the direct-load one with CL_OPT_STAGES -1, and odd N)."""
+    L, tol_rk, nsteps = 0.8 * N, 1e-5, 12
+    pot = [0.6, 1.0, 0.3 if nf == 2 else 0.0, 0.0, 2.5 if nf == 2 else 0.0]
+    phi, pi = inputs.scalar_state(N, nf, seed=41, fbar=(0.9, 0.1), amp=0.05, pamp=0.05)
+    m = O.make_model(N, L, nf=nf, alpha=0.5, kappa=0.4, expansion=True, m2=(pot[0], pot[2]), lam=(pot[1], pot[3]),
+                     g2=pot[4])
+    st = O.State(phi.copy(), pi.copy(), np.array([1.0, 0.0, 0.0]))
+    st.abt[1] = math.sqrt(0.4 * O.energies(m, st)["rho"] / 3.0)
+    dtype = np.float64 if prec == 0 else np.float32
+    with cl.Lattice(N, L, nf, prec, cl.CL_INT_RK3_4, expansion=True, alpha=0.5, kappa=0.4, dt=0.02) as g:
+        g.cl_set_potential(cl.CL_POT_POLY, pot)
+        if stages_opt:
+            g.cl_set_option(cl.CL_OPT_STAGES, stages_opt)
+        for f in range(nf):
+            g.cl_set_state(cl.CL_FIELD_PHI0 + f, st.phi[f].astype(dtype))
+            g.cl_set_state(cl.CL_FIELD_PI0 + f, st.pi[f].astype(dtype))
+        g.cl_set_scalars(st.abt[0], st.abt[1], 0.0)
+        g.cl_set_adaptive(tol_rk, 1e-4, 0.05)
+        assert g.cl_energies()["dt"] == 0.02
+        h = 0.02
+        ts = []
+        for k in range(nsteps):
+            g.cl_step(1)
+            e = g.cl_energies()
+            h_next, hu, ep = O.step_adaptive(m, st, h, tol_rk, 1, hmin=1e-4, hmax=0.05)
+            # the estimate is a norm of small increments: in FP32 it carries ~1e-4 of rounding,
+            # of which the next step size takes a third (h ~ eps^(-1/3))
+            assert e["rk_error"] == pytest.approx(ep[0], rel=1e-8 if prec == 0 else 1e-3), k
+            assert e["dt"] == pytest.approx(h_next, rel=max(tol, 1e-8)), k
+            assert e["t"] == pytest.approx(st.abt[2], rel=1e-8)
+            h = h_next
+            ts.append(h)
+        gphi = np.stack([g.cl_get_state(cl.CL_FIELD_PHI0 + f) for f in range(nf)])
+        gpi = np.stack([g.cl_get_state(cl.CL_FIELD_PI0 + f) for f in range(nf)])
+        e = g.cl_energies()
+        assert e["step"] == nsteps
+    assert len(set(np.round(ts, 12))) > 3  # the step size really changes
+    assert rel_l2(gphi, st.phi) < tol and rel_l2(gpi, st.pi) < tol
+    assert e["a"] == pytest.approx(st.abt[0], rel=tol)
+
+
+def test_rk34_adaptive_graph_replay_and_switch_off(cl):
+    """Adaptive steps replay from the captured graph (cl_step(n) in one call equals n calls),
+    and cl_set_adaptive(0) returns to the fixed dt."""
+    N = 16
+    phi, pi = inputs.scalar_state(N, 1, seed=43, fbar=(0.9,), amp=0.05, pamp=0.05)
+    res = []
+    for chunks in ((8,), (1,) * 8):
+        with cl.Lattice(N, 12.0, 1, cl.CL_PREC_FP64, cl.CL_INT_RK3_4, expansion=True, alpha=1.0, kappa=0.3,
+                        dt=0.01) as g:
+            g.cl_set_potential(cl.CL_POT_LPHI4, [1.0])
+            g.cl_set_state(cl.CL_FIELD_PHI0, phi[0])
+            g.cl_set_state(cl.CL_FIELD_PI0, pi[0])
+            g.cl_set_scalars(1.0)
+            g.cl_set_adaptive(1e-6, 0.0, 1.0)
+            for c in chunks:
+                g.cl_step(c)
+            e = g.cl_energies()
+            res.append((g.cl_get_state(cl.CL_FIELD_PHI0), e["dt"], e["t"]))
+            g.cl_set_adaptive(0.0)
+            g.cl_step(2)
+            e2 = g.cl_energies()
+            assert e2["dt"] == 0.01 and e2["t"] == pytest.approx(e["t"] + 0.02, rel=1e-12)
+    assert np.array_equal(res[0][0], res[1][0]) and res[0][1] == res[1][1] and res[0][2] == res[1][2]
+
+
+def test_rk34_adaptive_rejects_unsupported(cl):
+    with cl.Lattice(8, 6.0, 1, cl.CL_PREC_FP64, cl.CL_INT_RK3_3, dt=0.01) as g:
+        g.cl_set_potential(cl.CL_POT_LPHI4, [1.0])
+        with pytest.raises(cl.CLError) as ei:
+            g.cl_set_adaptive(1e-6)
+        assert ei.value.status == cl.CL_EUNSUPPORTED
+    with cl.Lattice(8, 6.0, 1, cl.CL_PREC_FP64, cl.CL_INT_RK3_4, dt=0.01) as g:
+        g.cl_set_potential(cl.CL_POT_LPHI4, [1.0])
+        with pytest.raises(cl.CLError) as ei:
+            g.cl_set_adaptive(1e-6, 0.5, 0.1)
+        assert ei.value.status == cl.CL_EINVAL

@@ -208,8 +208,11 @@ def test_graph_and_plain_launches_identical(cl):
 
 @pytest.mark.parametrize("N,nf,prec", [(64, 2, 1), (32, 1, 0), (48, 2, 2), (40, 2, 0)])
 def test_tma_and_direct_loaders_identical(cl, N, nf, prec):
-    """The TMA-staged loader only changes how rows reach shared memory: fields must be
-    bit-identical to the direct loader with the same tiles."""
+    """The TMA-staged loader only changes how rows reach shared memory: FP32 fields must be
+    bit-identical to the direct loader with the same tiles.  In FP64 the direct loader sums
+    the gradient energy by parts and evaluates the potential in Horner form (fewer FP64
+    operations; the TMA loaders keep the forward differences), so a(t) and the fields agree
+    to rounding instead."""
     phi, pi = inputs.scalar_state(N, nf, seed=13, fbar=(1.0, 0.1), amp=0.05, pamp=0.05)
     dt = np.float64 if prec == 0 else np.float32
     outs = []
@@ -227,8 +230,11 @@ def test_tma_and_direct_loaders_identical(cl, N, nf, prec):
             g.cl_step(9)
             outs.append(download(g, cl, nf))
     for o in outs[1:]:
-        assert np.array_equal(o[0], outs[0][0])
-        assert np.array_equal(o[1], outs[0][1])
+        if prec == 0:
+            assert rel_l2(o[0], outs[0][0]) < 1e-13 and rel_l2(o[1], outs[0][1]) < 1e-13
+        else:
+            assert np.array_equal(o[0], outs[0][0])
+            assert np.array_equal(o[1], outs[0][1])
 
 
 @pytest.mark.parametrize("N,nf,prec,by,dz,stages",

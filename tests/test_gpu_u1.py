@@ -110,7 +110,7 @@ def run_pair(cl, N, prec, integ, scheme, nsteps, dt=0.01, alpha=0.0, expansion=T
     return out, e0, e, st0, st, m, launches
 
 
-CASES = [(2, O.RK3_3, 3), (3, O.RK4_5, 5)]
+CASES = [(2, O.RK3_3, 3), (3, O.RK4_5, 5), (7, O.RK3_4, 4)]
 
 
 @pytest.mark.parametrize("integ,scheme,stages", CASES)
@@ -130,7 +130,8 @@ def test_u1_parity(cl, integ, scheme, stages, prec, tol, alpha):
                          ("G0", "G0")]:
         assert e[k_gpu] == pytest.approx(eo[k_orc], rel=max(tol, 1e-9), abs=1e-14), k_gpu
     assert e["step"] == 20
-    assert launches == 20 * stages * 2  # helper fields + stage kernel
+    # helper fields + stage kernel, and one Gauss-tracking reduction per step (gather form)
+    assert launches == 20 * stages * 2 + 20
 
 
 @pytest.mark.parametrize("integ,scheme,stages", CASES)
@@ -154,7 +155,8 @@ def test_u1_fused_stage_parity(cl, integ, scheme, stages, prec, tol, alpha):
         for k_gpu, k_orc in [("KE", "KEM"), ("GB", "GEM"), ("rho", "rho"), ("p", "p")]:
             assert e[k_gpu] == pytest.approx(eo[k_orc], rel=max(tol, 1e-9)), k_gpu
             assert e0[k_gpu] == pytest.approx(e0o[k_orc], rel=max(tol, 1e-9)), k_gpu
-        assert launches == n * stages  # one fused launch per stage
+        # one fused launch per stage; per step the plaquette fields and the Gauss-tracking reduction
+        assert launches == n * stages + 2 * n
 
 
 def test_u1_fused_and_two_launch_forms_agree(cl):
@@ -167,7 +169,7 @@ def test_u1_fused_and_two_launch_forms_agree(cl):
     for k in ("phi", "pi", "th", "E"):
         assert rel_l2(res[0][0][k], res[1][0][k]) < 1e-13, k
     assert res[0][1]["rho"] == pytest.approx(res[1][1]["rho"], rel=1e-12)
-    assert res[0][2] == 4 * 3 and res[1][2] == 4 * 3 * 2
+    assert res[0][2] == 4 * 3 + 4 * 2 and res[1][2] == 4 * 3 * 2 + 4
 
 
 @pytest.mark.parametrize("integ,scheme,stages", CASES)
@@ -391,3 +393,75 @@ def test_gauge_spectra_match_oracle(cl, N, prec):
         g.cl_set_potential(cl.CL_POT_LPHI4, [1.0])
         with pytest.raises(cl.CLError):
             g.cl_gauge_spectrum(cl.CL_GSPEC_E)  # no gauge field
+
+
+@pytest.mark.parametrize("variant,N", [(2, 32), (0, 32), (1, 32), (None, 12)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-4)])
+def test_u1_gauss_tracked_each_step(cl, variant, N, prec, tol):
+    """cl_step tracks the Gauss law every step (config "Gauss constraint tracked each step"):
+    after each step, gauss_rms_step is the rms lattice Gauss charge of that step's starting
+    state, r = dx sqrt(sum_n G(n)^2) / (a^(1-alpha) sqrt(sum_n E(n)^2)) with G the oracle's
+    Gauss charge, and gauss_rms_max the largest value so far.  The staged launch form (2)
+    sums it in its first stage; the gather (0) and fused (1) forms, and N = 12 (gather by
+    default), launch a reduction for it.  Random links and fields: G is O(1)."""
+    L, dt, alpha = 0.75 * N, 0.01, 0.5
+    m = O.make_model(N, L, nf=1, alpha=alpha, kappa=KAPPA, expansion=True, gauge=1, alphaL=ALPHAL, ws2=WS2,
+                     m2=(M2, 0.0), lam=(LAM, 0.0))
+    st = random_state(m, 31)
+    st.abt[:] = (1.1, 0.0, 0.0)
+    st.abt[1] = 1.1 * math.sqrt(KAPPA * 1.1 ** (2 * alpha) * O.energies(m, st)["rho"] / 3.0)
+    dtype = np.float64 if prec == 0 else np.float32
+    dx = L / N
+    with cl.Lattice(N, L, 1, prec, cl.CL_INT_RK3_3, gauge=cl.CL_GAUGE_U1_AXION, expansion=True, alpha=alpha,
+                    kappa=KAPPA, dt=dt) as g:
+        g.cl_set_potential(cl.CL_POT_POLY, [M2, LAM, 0.0, 0.0, 0.0])
+        g.cl_set_gauge_coupling(ALPHAL, WS2)
+        if variant is not None:
+            g.cl_set_option(cl.CL_OPT_PASS_VARIANT, variant)
+        g.cl_set_state(cl.CL_FIELD_PHI0, st.phi[0].astype(dtype))
+        g.cl_set_state(cl.CL_FIELD_PI0, st.pi[0].astype(dtype))
+        for i in range(3):
+            g.cl_set_state(cl.CL_FIELD_THETA1 + i, st.links[i].astype(dtype))
+            g.cl_set_state(cl.CL_FIELD_E1 + i, st.efield[i].astype(dtype))
+        g.cl_set_scalars(st.abt[0], st.abt[1], 0.0)
+        assert g.cl_energies()["gauss_rms_max"] == 0.0
+        want = {2: 2, 0: 0, 1: 1}.get(variant, 0)
+        assert g.cl_get_option(cl.CL_OPT_PASS_VARIANT) == want
+        rmax = 0.0
+        for _ in range(3):
+            G = O.u1_gauss(m, st)
+            r = dx * math.sqrt(float(np.sum(G * G))) / (st.abt[0] ** (1 - alpha) *
+                                                        math.sqrt(float(np.sum(st.efield ** 2))))
+            rmax = max(rmax, r)
+            g.cl_step(1)
+            e = g.cl_energies()
+            assert r > 0.1
+            assert e["gauss_rms_step"] == pytest.approx(r, rel=tol)
+            assert e["gauss_rms_max"] == pytest.approx(rmax, rel=tol)
+            O.step(m, st, O.RK3_3, dt, 1)
+
+
+@pytest.mark.parametrize("prec,bound", [(0, 1e-13), (2, 1e-5)])
+def test_u1_gauss_tracking_of_a_gauss_state(cl, prec, bound):
+    """With the coupling off and a divergence-free E the tracked violation stays at rounding
+    level over many steps (staged form, N = 32)."""
+    N, L = 32, 24.0
+    m = O.make_model(N, L, nf=1, alpha=0.0, kappa=KAPPA, expansion=True, gauge=1, alphaL=0.0, ws2=WS2,
+                     m2=(M2, 0.0), lam=(LAM, 0.0))
+    st = random_state(m, 13, th_amp=0.2)
+    dtype = np.float64 if prec == 0 else np.float32
+    E = inputs.solenoidal_field(N, seed=14, amp=0.3)
+    with cl.Lattice(N, L, 1, prec, cl.CL_INT_RK3_3, gauge=cl.CL_GAUGE_U1_AXION, alpha=0.0, kappa=KAPPA,
+                    dt=0.01, expansion=True) as g:
+        g.cl_set_potential(cl.CL_POT_POLY, [M2, LAM, 0.0, 0.0, 0.0])
+        g.cl_set_gauge_coupling(0.0, WS2)
+        g.cl_set_state(cl.CL_FIELD_PHI0, st.phi[0].astype(dtype))
+        g.cl_set_state(cl.CL_FIELD_PI0, st.pi[0].astype(dtype))
+        for i in range(3):
+            g.cl_set_state(cl.CL_FIELD_THETA1 + i, st.links[i].astype(dtype))
+            g.cl_set_state(cl.CL_FIELD_E1 + i, E[i].astype(dtype))
+        g.cl_set_scalars(1.0)
+        g.cl_step(30)
+        e = g.cl_energies()
+        assert 0.0 <= e["gauss_rms_max"] < bound
+        assert e["gauss_rms_step"] <= e["gauss_rms_max"]
