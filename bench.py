@@ -64,10 +64,10 @@ BYTES_PER_SITE_PASS_FP64 = 2 * 2 * 2 * 8
 
 
 def config(extra=None):
-    c = {"workload": "two-field preheating m2phi2+g2phi2chi2, q=1e4, 256^3, Yoshida-4, FP32+Kahan, "
-                     "FP64 reductions, dt=0.005, self-consistent expansion",
+    c = {"workload": "two-field preheating m2phi2+g2phi2chi2, q=1e4, %d^3, Yoshida-4, FP32+Kahan, "
+                     "FP64 reductions, dt=0.005, self-consistent expansion" % N,
          "lattice": N, "fields": 2, "integrator": "yoshida4", "passes_per_step": PASSES_PER_STEP,
-         "l2": "inputs (805 MB) larger than L2; no flush"}
+         "l2": "inputs (%.0f MB) larger than L2; no flush" % (N ** 3 * 6 * 4 * 2 / 1e6)}
     if extra:
         c.update(extra)
     return c
@@ -80,18 +80,19 @@ KERNEL_SOURCES = ["paper_2607_24978_gb300/csrc/scalar_pass.cu", "paper_2607_2497
 
 
 def profiled_traffic():
-    """DRAM bytes per launch of the fused pass from the committed ncu summary, or None when
-    the kernel sources changed since those counters were taken."""
+    """DRAM bytes per launch of the fused pass from the ncu record committed beside its summary
+    (profiles/scalar_pass_256_yoshida4_fp32kahan.json), or None when the kernel sources changed
+    since those counters were taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "scalar_pass_256_yoshida4_fp32kahan.md")
+    path = os.path.join(ROOT, "profiles", "scalar_pass_256_yoshida4_fp32kahan.json")
     try:
-        fields = dict(l.split(":", 1) for l in open(path) if l.startswith(("traffic_bytes", "kernel_sources")))
+        rec = json.load(open(path))
         h = hashlib.sha256()
         for s in KERNEL_SOURCES:
             h.update(open(os.path.join(ROOT, s), "rb").read())
-        if h.hexdigest()[:16] != fields["kernel_sources_sha256_16"].strip():
+        if h.hexdigest()[:16] != rec["kernel_sources_sha256_16"]:
             return None
-        return int(fields["traffic_bytes_per_launch"])
+        return int(rec["traffic_bytes_per_launch"])
     except Exception:
         return None
 
@@ -197,39 +198,57 @@ def barrier(world):
 REF_N = 64  # per-step sample of the reference arm: same per-site arithmetic on 64^3 sites
 
 
-def oracle_model(n=N):
+def oracle_model(n=None):
+    n = N if n is None else n
     from oracle import oracle as O
-    return O.make_model(n, L * n / N, nf=2, alpha=ALPHA, kappa=KAPPA, expansion=True, m2=(1.0, 0.0), g2=G2)
+    return O.make_model(n, L * n / 256, nf=2, alpha=ALPHA, kappa=KAPPA, expansion=True, m2=(1.0, 0.0), g2=G2)
 
 
-def oracle_state(n=N):
+def oracle_state(n=None):
     """Seeded homogeneous-plus-noise state of the bench shape (the oracle's own vacuum state
     at 256^3 would take minutes of direct DFTs, so the CPU legs start from this input)."""
     import numpy as np
     from oracle import oracle as O
     from tests import inputs
+    n = N if n is None else n
     phi, pi = inputs.scalar_state(n, 2, seed=SEED, fbar=(1.0, 0.0), amp=1e-5, pamp=1e-5)
     st = O.State(phi, pi, np.array([1.0, 0.0, 0.0]))
     st.abt[1] = math.sqrt(KAPPA * O.energies(oracle_model(n), st)["rho"] / 3.0)
     return st
 
 
-def cpu_baseline(steps=2):
+def cpu_baseline(n=None):
+    """The oracle on a bounded sample of the workload: Yoshida-4 steps of the two-field lattice
+    (the headline's size, at most 256^3), once on every host core (the loop-parallel build,
+    the reported figure) and once on one thread."""
     from oracle import oracle as O
-    m = oracle_model()
-    st = oracle_state()
-    t0 = time.perf_counter()
-    O.step(m, st, O.YOSHIDA4, DT, steps)
-    dt = time.perf_counter() - t0
-    return {"value": N ** 3 * steps / dt / 1e9, "unit": "Gsite-updates/s", "cores": 1, "kind": "oracle",
-            "sample": "%d oracle Yoshida-4 steps of the full 256^3 two-field lattice, FP64, single thread "
-                      "(%.1f s)" % (steps, dt)}
+    n = min(N, 256) if n is None else n
+    out = {}
+    for omp, steps in ((True, 8), (False, 2)):
+        O.use_threads(omp)
+        cores = O.threads()
+        m = oracle_model(n)
+        st = oracle_state(n)
+        O.step(m, st, O.YOSHIDA4, DT, 1)  # first touch of the arrays outside the timing
+        t0 = time.perf_counter()
+        O.step(m, st, O.YOSHIDA4, DT, steps)
+        dt = time.perf_counter() - t0
+        out[omp] = {"value": n ** 3 * steps / dt / 1e9, "unit": "Gsite-updates/s", "cores": cores, "kind": "oracle",
+                    "sample": "%d oracle Yoshida-4 steps of the %d^3 two-field lattice, FP64, %d thread%s (%.1f s)"
+                              % (steps, n, cores, "" if cores == 1 else "s", dt)}
+    O.use_threads(False)
+    line = dict(out[True])
+    line["nproc"] = os.cpu_count()
+    line["single_thread"] = out[False]
+    return line
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
     from oracle import oracle as O
+    O.use_threads(True)  # every host core (the loop-parallel build of the oracle)
+    cores = O.threads()
     m = oracle_model(REF_N)
     st = oracle_state(REF_N)
     for _ in range(args.warmup):
@@ -242,10 +261,11 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gsite-updates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config({"impl": "FP64 CPU oracle, single thread"}),
-            "cpu_baseline": {"value": v, "unit": "Gsite-updates/s", "cores": 1, "kind": "oracle",
+            "data": "synthetic", "config": config({"impl": "FP64 CPU oracle, %d threads" % cores}),
+            "cpu_baseline": {"value": v, "unit": "Gsite-updates/s", "cores": cores, "kind": "oracle",
                              "sample": "per timed step one oracle Yoshida-4 step of the same two-field "
-                                       "workload on 64^3 sites (same per-site arithmetic as 256^3)"},
+                                       "workload on 64^3 sites (same per-site arithmetic as 256^3), "
+                                       "%d threads" % cores},
             "e2e": {"value": v, "unit": "Gsite-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -334,7 +354,10 @@ def run_u1_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_
                          "algorithmic_bytes_per_launch": bytes_stage},
             "gpu_launches": launches, "clocks": clocks,
             "energies_end": {"a": e["a"], "rho": e["rho"], "KE": e["KE"], "GB": e["GB"],
-                             "gauss_violation": e["gauss_violation"], "hubble_violation": e["hubble_violation"]}}
+                             "gauss_violation": e["gauss_violation"], "hubble_violation": e["hubble_violation"],
+                             "gauss_rms_last_step": e["gauss_rms_step"], "gauss_rms_max_over_steps": e["gauss_rms_max"]},
+            "gauss_tracking": "rms lattice Gauss charge of every step's starting state, summed in the first RK "
+                              "stage (staged form) inside the timed steps"}
 
 
 def rk_tiling(g, args, cl):
@@ -612,16 +635,30 @@ def run_surrogate_workload(args, world, rank, local, cl, torch, stream, peak_tf,
     launches = s6.last_launch_count()
     s6.close()
     s2.close()
-    # the leapfrog steps one forward replaces: K VV-2 steps, one field, FP32 + Kahan, 128^3
+    # the leapfrog steps one forward replaces: K VV-2 steps, one field, FP32 + Kahan, 128^3, each
+    # time K steps queued by one cl_step call (graph replays), timed on the device
     lat = cl.Lattice(N, 8.0 * math.pi * N / 256, 1, cl.CL_PREC_FP32_KAHAN, cl.CL_INT_VV2, alpha=1.0, kappa=0.1,
                      dt=0.01, stream=stream.cuda_stream)
     lat.cl_set_potential(cl.CL_POT_LPHI4, [1.0])
     lat.cl_init_vacuum(c["seed"], 1e30, 1e-4, (1.0,), (0.0,))
     lat.cl_step(20)
     lat.cl_sync()
-    tl, _ = timed_steps(torch, lat, stream, 10 * c["K"])
-    tl = tl / 10
+    tl = time_it(lambda: lat.cl_step(c["K"]), 20)
+    lf_tiles = {k: lat.cl_get_option(o) for k, o in (("tile_by", cl.CL_OPT_TILE_BY), ("tile_dz", cl.CL_OPT_TILE_DZ),
+                                                     ("stages", cl.CL_OPT_STAGES), ("variant", cl.CL_OPT_PASS_VARIANT))}
     lat.close()
+    # break-even: the forward time of each hidden width against the leapfrog step, i.e. the jump
+    # length K at which one forward costs as much as the K steps it replaces
+    breakeven = {}
+    for hid in (16, 32, 48):
+        sv = cl.Surrogate(N, c["cin"], c["cout"], hid, c["layers"], cl.CL_ACT_RELU, cl.CL_SG_BF16,
+                          stream=stream.cuda_stream)
+        for l, (ci, co) in enumerate(sv.shapes):
+            sv.set_weights(l, rg.standard_normal((27, co, ci)) * math.sqrt(2.0 / (27 * ci)), 0.01 * rg.standard_normal(co))
+        tf = time_it(lambda: sv.forward(x, y), max(5, args.steps))
+        sv.close()
+        breakeven[str(hid)] = {"forward_ms": tf * 1e3, "flops": surrogate_flops(N, c["cin"], c["cout"], hid, c["layers"]),
+                               "breakeven_K": tf / (tl / c["K"])}
     flops = surrogate_flops(N, c["cin"], c["cout"], c["hidden"], c["layers"])
     tc_flops = 2 * 27 * c["hidden"] ** 2 * N ** 3
     tc_s = (t6 - t2) / (c["layers"] - 2)
@@ -630,18 +667,21 @@ def run_surrogate_workload(args, world, rank, local, cl, torch, stream, peak_tf,
     from paper_2607_24978_gb300 import surrogate_train as T
     trained = {}
     if not args.no_train:
-        with torch.cuda.stream(stream):
-            st, mu, sg, info = T.train(torch, N=32, iters=2000, lr=1e-4)
-            ev = {n: T.evaluate(torch, st, mu, sg, N=n, jumps=8, hubble_limit=1e-3) for n in (64, 128)}
-            ev_free = T.evaluate(torch, st, mu, sg, N=128, jumps=8, hubble_limit=float("inf"))
-            st.close()
-        e128 = ev[128]
-        ok = e128["accepted"] == e128["jumps"] and max(e128["spectrum_err_phi"], e128["spectrum_err_pi"]) <= 0.01
-        trained = {"training": info, "judged_jumps": {str(k): v for k, v in ev.items()},
-                   "unjudged_jumps_128": ev_free,
-                   "surrogate_speedup_at_1pct_err": e128["speedup"] if ok else None,
-                   "note": "speed-up at 1 % spectrum error reported only when every jump is accepted and both "
-                           "binned spectra are within 1 % of the plain leapfrog"}
+        for hid, K in ((c["hidden"], c["K"]), (32, 32)):  # the configured network, a cheaper break-even variant
+            with torch.cuda.stream(stream):
+                st, mu, sg, info = T.train(torch, N=32, hidden=hid, K=K, iters=2000, lr=1e-4)
+                ev = {n: T.evaluate(torch, st, mu, sg, N=n, K=K, jumps=8, hubble_limit=1e-3, hidden=hid)
+                      for n in (64, 128)}
+                ev_free = T.evaluate(torch, st, mu, sg, N=128, K=K, jumps=8, hubble_limit=float("inf"), hidden=hid)
+                st.close()
+            e128 = ev[128]
+            ok = e128["accepted"] == e128["jumps"] and max(e128["spectrum_err_phi"], e128["spectrum_err_pi"]) <= 0.01
+            trained["hidden%d_K%d" % (hid, K)] = {
+                "training": info, "judged_jumps": {str(k): v for k, v in ev.items()},
+                "unjudged_jumps_128": ev_free,
+                "surrogate_speedup_at_1pct_err": e128["speedup"] if ok else None}
+        trained["note"] = ("speed-up at 1 % spectrum error reported only when every jump is accepted and both "
+                           "binned spectra are within 1 % of the plain leapfrog")
     return {"metric": "surrogate forward TFLOP/s at 128^3 (6 layers, 48 channels, BF16)", "value": flops / t6 / 1e12,
             "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t6 * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -654,16 +694,19 @@ def run_surrogate_workload(args, world, rank, local, cl, torch, stream, peak_tf,
                          "kernel": "k_conv_tc<48> (one hidden layer; time = (6-layer - 2-layer forward) / 4)",
                          "algorithmic_flops_per_launch": tc_flops},
             "forward_backward": {"ms": tfb * 1e3, "tflops": 3 * flops / tfb / 1e12},
-            "leapfrog": {"steps": c["K"], "ms": tl * 1e3,
+            "leapfrog": {"steps": c["K"], "ms": tl * 1e3, "ms_per_step": tl / c["K"] * 1e3,
+                         "GBps_per_pass": N ** 3 * ENS_BYTES_PER_SITE / (tl / c["K"]) / 1e9, "tiles": lf_tiles,
                          "forward_over_leapfrog": t6 / tl},
+            "breakeven_by_hidden_width": breakeven,
             "trained": trained,
             "gpu_launches": launches, "clocks": clk.summary()}
 
 
 # ------------------------------------------------------------------ GPU arm
-def make_lattice(cl, precision, stream, args=None):
-    g = cl.Lattice(N, L, 2, precision, cl.CL_INT_YOSHIDA4, expansion=True, alpha=ALPHA, kappa=KAPPA, dt=DT,
-                   stream=stream)
+def make_lattice(cl, precision, stream, args=None, n=None):
+    n = N if n is None else n  # other sizes keep the lattice spacing of the 256^3 box
+    g = cl.Lattice(n, L * n / 256, 2, precision, cl.CL_INT_YOSHIDA4, expansion=True, alpha=ALPHA, kappa=KAPPA,
+                   dt=DT, stream=stream)
     g.cl_set_potential(cl.CL_POT_M2_G2, [1.0, G2])
     g.cl_init_vacuum(SEED, 1e30, AMP2, (1.0, 0.0), (0.0, 0.0))
     if args is not None:  # tile overrides (profiling and tuning runs)
@@ -693,6 +736,86 @@ def timed_steps(torch, g, stream, steps):
     return start.elapsed_time(stop) / 1e3, launches
 
 
+def e2e_leg(args, world, cl, torch, g):
+    """The headline metric through the C ABI with host buffers, and the transfer rates it sees
+    beside plain pinned cudaMemcpyAsync copies (torch) of the same arrays."""
+    nsite = N ** 3
+    steps = max(3, min(args.steps, 10))
+    tdt = torch.float64 if args.precision == "fp64" else torch.float32
+    es = 8 if args.precision == "fp64" else 4
+    host_in = [torch.empty(nsite, dtype=tdt, pin_memory=True) for _ in range(4)]
+    host_out = [torch.empty(nsite, dtype=tdt, pin_memory=True) for _ in range(4)]
+    fields = [cl.CL_FIELD_PHI0, cl.CL_FIELD_PHI1, cl.CL_FIELD_PI0, cl.CL_FIELD_PI1]
+    for h, f in zip(host_in, fields):
+        g.cl_get_state(f, h.numpy())
+    a_in = [h.numpy() for h in host_in]
+    a_out = [h.numpy() for h in host_out]
+    g.cl_sync()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for a, f in zip(a_in, fields):
+            g.cl_set_state(f, a)
+        g.cl_step(1)
+        for a, f in zip(a_out, fields):
+            g.cl_get_state(f, a)
+        g.cl_energies()
+    el = max_over_ranks(time.perf_counter() - t0, world)
+    # the transfers alone through the same calls, and plain pinned copies of the same bytes
+    t0 = time.perf_counter()
+    for a, f in zip(a_in, fields):
+        g.cl_set_state(f, a)
+    g.cl_sync()
+    t_up = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for a, f in zip(a_out, fields):
+        g.cl_get_state(f, a)
+    t_down = time.perf_counter() - t0
+    dev = [torch.empty(nsite, dtype=tdt, device="cuda") for _ in range(4)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for d, h in zip(dev, host_in):
+        d.copy_(h, non_blocking=True)
+    torch.cuda.synchronize()
+    p_up = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for d, h in zip(dev, host_out):
+        h.copy_(d, non_blocking=True)
+    torch.cuda.synchronize()
+    p_down = time.perf_counter() - t0
+    del dev
+    nbytes = 4 * nsite * es
+    return {"value": world * nsite * steps / el / 1e9, "unit": "Gsite-updates/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 14 * 8, "steps": steps,
+            "ms_per_step": el / steps * 1e3,
+            "path": "cl_set_state x4 (pinned host) + cl_step(1) + cl_get_state x4 (pinned host) + cl_energies",
+            "h2d_GBps": nbytes / t_up / 1e9, "d2h_GBps": nbytes / t_down / 1e9,
+            "plain_pinned_copy_h2d_GBps": nbytes / p_up / 1e9, "plain_pinned_copy_d2h_GBps": nbytes / p_down / 1e9}
+
+
+def size_point(args, cl, torch, stream, n, hbm_peak, peak_src):
+    """The headline workload at n^3 (same model and spacing): throughput and the fused pass's
+    roofline fraction."""
+    g = make_lattice(cl, cl.CL_PREC_FP32_KAHAN, stream.cuda_stream, n=n)
+    g.cl_step(3)
+    g.cl_sync()
+    steps = max(args.steps, 20)
+    el, launches = timed_steps(torch, g, stream, steps)
+    e = g.cl_energies()
+    tiles = {k: g.cl_get_option(o) for k, o in (("tile_by", cl.CL_OPT_TILE_BY), ("tile_dz", cl.CL_OPT_TILE_DZ),
+                                                ("stages", cl.CL_OPT_STAGES), ("variant", cl.CL_OPT_PASS_VARIANT))}
+    g.close()
+    bytes_launch = n ** 3 * BYTES_PER_SITE_PASS
+    achieved = bytes_launch / (el / (steps * PASSES_PER_STEP)) / 1e9
+    return {"lattice": n, "value": n ** 3 * steps / el / 1e9, "unit": "Gsite-updates/s", "steps": steps,
+            "ms_per_step": el / steps * 1e3, "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "peak_source": peak_src, "tiles": tiles,
+                         "algorithmic_bytes_per_launch": bytes_launch},
+            "hubble_violation_end": e["hubble_violation"],
+            "l2": "inputs (%.1f GB) larger than L2; no flush" % (n ** 3 * 6 * 4 / 1e9)}
+
+
 def run_gpu(args, world, rank, local):
     import numpy as np
     import torch
@@ -719,7 +842,8 @@ def run_gpu(args, world, rank, local):
             print(json.dumps(line), flush=True)
         return
 
-    g = make_lattice(cl, cl.CL_PREC_FP32_KAHAN, stream.cuda_stream, args)
+    prec = {"fp32k": cl.CL_PREC_FP32_KAHAN, "fp64": cl.CL_PREC_FP64, "fp32": cl.CL_PREC_FP32}[args.precision]
+    g = make_lattice(cl, prec, stream.cuda_stream, args)
     g.cl_step(args.warmup)
     g.cl_sync()
     barrier(world)
@@ -733,15 +857,17 @@ def run_gpu(args, world, rank, local):
 
     # roofline of the dominant kernel: the fused scalar pass, PASSES_PER_STEP launches per step
     pass_s = el / (args.steps * PASSES_PER_STEP)
-    bytes_launch = N ** 3 * BYTES_PER_SITE_PASS
+    bytes_site = {"fp32k": BYTES_PER_SITE_PASS, "fp64": BYTES_PER_SITE_PASS_FP64, "fp32": 2 * 2 * 2 * 4}[args.precision]
+    bytes_launch = N ** 3 * bytes_site
     achieved = bytes_launch / pass_s / 1e9
-    traffic = profiled_traffic()
+    traffic = profiled_traffic() if args.precision == "fp32k" and N == 256 else None
     tiles = {k: g.cl_get_option(o) for k, o in (("tile_by", cl.CL_OPT_TILE_BY), ("tile_dz", cl.CL_OPT_TILE_DZ),
                                                 ("stages", cl.CL_OPT_STAGES), ("variant", cl.CL_OPT_PASS_VARIANT))}
     kname = ("k_scalar_pass_tma_nr" if tiles["variant"] == 1 else "k_scalar_pass_tma") if tiles["stages"] > 0 \
         else "k_scalar_pass"
+    tname = {"fp32k": "float,2,kahan,4", "fp64": "double,2,plain,2", "fp32": "float,2,plain,4"}[args.precision]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": traffic, "kernel": "%s<float,2,kahan,4,%d>" % (kname, tiles["stages"]), "tiles": tiles,
+                "traffic": traffic, "kernel": "%s<%s,%d>" % (kname, tname, tiles["stages"]), "tiles": tiles,
                 "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_src}
 
     if args.profile:
@@ -751,27 +877,15 @@ def run_gpu(args, world, rank, local):
         g.close()
         return
 
-    # end to end through the C ABI with host buffers
-    e2e_steps = max(2, min(args.steps, 5))
-    host = [torch.empty(N ** 3, dtype=torch.float32, pin_memory=True) for _ in range(4)]
-    for f in range(2):
-        g.cl_get_state(cl.CL_FIELD_PHI0 + f, host[f].numpy())
-        g.cl_get_state(cl.CL_FIELD_PI0 + f, host[2 + f].numpy())
-    arrs = [h.numpy() for h in host]
-    g.cl_sync()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        for f in range(2):
-            g.cl_set_state(cl.CL_FIELD_PHI0 + f, arrs[f])
-            g.cl_set_state(cl.CL_FIELD_PI0 + f, arrs[2 + f])
-        g.cl_step(1)
-        g.cl_energies()
-    e2e_el = max_over_ranks(time.perf_counter() - t0, world)
-    e2e = {"value": world * N ** 3 * e2e_steps / e2e_el / 1e9, "unit": "Gsite-updates/s",
-           "h2d_bytes_per_step": 4 * N ** 3 * 4, "d2h_bytes_per_step": 144,
-           "steps": e2e_steps, "path": "cl_set_state x4 (pinned host) + cl_step(1) + cl_energies"}
+    # end to end through the C ABI with host buffers: every step uploads phi and pi of both
+    # fields from pinned host memory, advances one step and reads phi, pi and the energies back
+    e2e = e2e_leg(args, world, cl, torch, g)
     g.close()
-    del host, arrs
+
+    # the config's 512^3 roofline point (same model and spacing, 8x the sites)
+    big = None
+    if N != 512 and not args.no_512:
+        big = size_point(args, cl, torch, stream, 512, hbm_peak, peak_src)
 
     # the same workload in FP64 without compensation ("FP64 plain")
     g64 = make_lattice(cl, cl.CL_PREC_FP64, stream.cuda_stream)
@@ -785,10 +899,13 @@ def run_gpu(args, world, rank, local):
 
     line = {"metric": METRIC, "value": value, "unit": "Gsite-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el_max / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config({"parallelism": "replicas" if world > 1 else "single"}),
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+            "data": "synthetic",
+            "config": config({"parallelism": "replicas" if world > 1 else "single", "precision": args.precision}),
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
             "fp64_plain": fp64, "energies_end": {"a": e["a"], "rho": e["rho"], "hubble_violation": e["hubble_violation"]}}
+    if big is not None:
+        line["lattice_512"] = big
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -815,7 +932,16 @@ def main():
     ap.add_argument("--members", type=int, default=None, help="ensemble size (default 1024)")
     ap.add_argument("--no-train", action="store_true", help="surrogate workload: throughput only")
     ap.add_argument("--no-autotune", action="store_true", help="ensemble workload: default tiling, no trial passes")
+    ap.add_argument("--lattice", type=int, default=256,
+                    help="preheat workload: sites per side (same model and lattice spacing as 256^3)")
+    ap.add_argument("--no-512", action="store_true", help="preheat workload: skip the 512^3 roofline point")
+    ap.add_argument("--precision", default="fp32k", choices=["fp32k", "fp64", "fp32"],
+                    help="preheat workload: FP32 + Kahan (default), FP64, or plain FP32")
     args = ap.parse_args()
+    global N, METRIC
+    if args.lattice != N:
+        N = args.lattice
+        METRIC = "Gsite-updates/s at %d^3" % N
     if args.steps is None:
         args.steps = 200 if args.impl == "reference" else 1000
     world, rank, local = dist_init(args)
