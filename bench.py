@@ -97,6 +97,20 @@ def profiled_traffic():
         return None
 
 
+def fp64_ops_record():
+    """FP64 operations per site and pass of the FP64 pass kernel, counted by ncu (committed
+    beside its summary), or None when the kernel sources changed since."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "scalar_pass_256_yoshida4_fp64.json")))
+        h = hashlib.sha256()
+        for s in rec["kernel_sources"]:
+            h.update(open(os.path.join(ROOT, s), "rb").read())
+        return rec if h.hexdigest()[:16] == rec["kernel_sources_sha256_16"] else None
+    except Exception:
+        return None
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -896,6 +910,15 @@ def run_gpu(args, world, rank, local):
     fp64 = {"value": N ** 3 * n64 / el64 / 1e9, "unit": "Gsite-updates/s", "steps": n64,
             "fp32_kahan_speedup": (N ** 3 * args.steps / el) / (N ** 3 * n64 / el64),
             "achieved_GBps": N ** 3 * BYTES_PER_SITE_PASS_FP64 / (el64 / (n64 * PASSES_PER_STEP)) / 1e9}
+    # the FP64 pass is bound by the FP64 pipe (2 FP64 operations per SM per cycle on GB300), not by HBM
+    rec = fp64_ops_record()
+    if rec is not None:
+        peak = rec["fp64_peak_ops_per_cycle_per_sm"] * rec["sm_count"] * rec["sm_max_mhz"] * 1e6
+        ach = rec["fp64_ops_per_site_pass"] * N ** 3 * PASSES_PER_STEP * n64 / el64
+        fp64["roofline"] = {"bound": "alu", "achieved": ach / 1e9, "peak": peak / 1e9, "unit": "G FP64 op/s",
+                            "frac": ach / peak, "kernel": rec["kernel"],
+                            "ops_per_site_pass": rec["fp64_ops_per_site_pass"],
+                            "peak_source": "2 FP64 ops per SM per cycle (ncu peak_sustained) x 152 SMs x 2070 MHz"}
 
     line = {"metric": METRIC, "value": value, "unit": "Gsite-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el_max / args.steps * 1e3, "higher_is_better": True,
