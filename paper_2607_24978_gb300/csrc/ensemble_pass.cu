@@ -57,12 +57,9 @@ __global__ void __launch_bounds__(kEnsThreads) k_ensemble_pass(const EnsPassArgs
         march_tile<T, NF, KAHAN, VW>(F, N, BY, I.y0, R, I.z0, NZ, sm, tid, nthr, do_drift, C, P, accK, accG, accV);
 
         double v[kMaxQ];
-        v[0] = accK[0].value();
-        v[1] = NF > 1 ? accK[NF - 1].value() : 0.0;
-        v[2] = accG[0].value();
-        v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
-        v[4] = accV.value();
-        block_reduce<kMaxQ>(v, s_red, tid, nthr);
+        const Acc<T>* av[kMaxQ] = {&accK[0], NF > 1 ? &accK[NF - 1] : nullptr, &accG[0],
+                                   NF > 1 ? &accG[NF - 1] : nullptr, &accV};
+        block_reduce_acc<T, kMaxQ>(av, v, s_red, tid, nthr);
         if (tid == 0) {
 #pragma unroll
             for (int q = 0; q < kMaxQ; ++q) A.partials[(size_t)it * kMaxQ + q] = v[q];
@@ -71,15 +68,10 @@ __global__ void __launch_bounds__(kEnsThreads) k_ensemble_pass(const EnsPassArgs
             s_last = (prev + 1u == (unsigned)M.nitems);
         }
         __syncthreads();
-        if (s_last) {  // block-uniform
+        if (s_last && tid < 32) {  // block-uniform; one warp sums the member's item partials
             __threadfence();
             double w[kMaxQ];
-#pragma unroll
-            for (int q = 0; q < kMaxQ; ++q) w[q] = 0.0;
-            for (int b = tid; b < M.nitems; b += nthr)
-#pragma unroll
-                for (int q = 0; q < kMaxQ; ++q) w[q] += __ldcg(&A.partials[(size_t)(M.item0 + b) * kMaxQ + q]);
-            block_reduce<kMaxQ>(w, s_red, tid, nthr);
+            warp_sum_partials<kMaxQ>(A.partials + (size_t)M.item0 * kMaxQ, M.nitems, tid, w);
             if (tid == 0)
                 scalar_epilogue(S, w, (double)N * N * N, dx, s_coef[3], A.alpha, A.kappa, A.d, A.e, A.k, A.flags,
                                 A.hubble_limit);
@@ -228,12 +220,9 @@ __global__ void __launch_bounds__(kEnsTmaThreads, NF == 1 ? 2 : 1) k_ensemble_pa
             if constexpr (NR) release(st_prev);  // the upper z halo of the item is never kicked
             // item partials; the member's last item reduces them in a fixed order
             double v[kMaxQ];
-            v[0] = accK[0].value();
-            v[1] = NF > 1 ? accK[NF - 1].value() : 0.0;
-            v[2] = accG[0].value();
-            v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
-            v[4] = accV.value();
-            group_reduce<kMaxQ>(v, s_red, tid, CT, 2);
+            const Acc<T>* av[kMaxQ] = {&accK[0], NF > 1 ? &accK[NF - 1] : nullptr, &accG[0],
+                                       NF > 1 ? &accG[NF - 1] : nullptr, &accV};
+            group_reduce_acc<T, kMaxQ>(av, v, s_red, tid, CT, 2);
             if (tid == 0) {
 #pragma unroll
                 for (int q = 0; q < kMaxQ; ++q) A.partials[(size_t)it * kMaxQ + q] = v[q];
@@ -242,15 +231,10 @@ __global__ void __launch_bounds__(kEnsTmaThreads, NF == 1 ? 2 : 1) k_ensemble_pa
                 s_last = (prev + 1u == (unsigned)M.nitems);
             }
             named_barrier_sync(2, CT);
-            if (s_last) {  // uniform over the consumers
+            if (s_last && tid < 32) {  // uniform over the consumers; one warp sums the item partials
                 __threadfence();
                 double w[kMaxQ];
-#pragma unroll
-                for (int q = 0; q < kMaxQ; ++q) w[q] = 0.0;
-                for (int b = tid; b < M.nitems; b += CT)
-#pragma unroll
-                    for (int q = 0; q < kMaxQ; ++q) w[q] += __ldcg(&A.partials[(size_t)(M.item0 + b) * kMaxQ + q]);
-                group_reduce<kMaxQ>(w, s_red, tid, CT, 2);
+                warp_sum_partials<kMaxQ>(A.partials + (size_t)M.item0 * kMaxQ, M.nitems, tid, w);
                 if (tid == 0)
                     scalar_epilogue(Sm, w, (double)N * N * N, dx, s_coef[3], A.alpha, A.kappa, A.d, A.e, A.k, A.flags,
                                     A.hubble_limit);

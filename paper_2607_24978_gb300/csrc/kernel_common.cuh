@@ -47,6 +47,29 @@ __device__ __forceinline__ void vstore(T* p, const T (&s)[VW])
     *reinterpret_cast<V*>(p) = v;
 }
 
+// a^e for the powers of the scale factor in the equations of motion (e = alpha + const).
+// Integer exponents -- alpha = 0 or 1, the usual choices -- by repeated multiplication, a
+// handful of FP64 operations; other exponents by pow.  On GB300's narrow FP64 pipe the
+// accurate pow routine takes microseconds on the single thread that evaluates a pass's
+// coefficients while the rest of its block waits, so each pass paid several of them.
+__device__ __forceinline__ double apow(double a, double e)
+{
+    const double r = rint(e);
+    if (r == e && fabs(r) <= 16.0) {
+        int n = (int)r;
+        const bool neg = n < 0;
+        if (neg) n = -n;
+        double p = 1.0, b = a;
+        while (n) {
+            if (n & 1) p *= b;
+            b *= b;
+            n >>= 1;
+        }
+        return neg ? 1.0 / p : p;
+    }
+    return pow(a, e);
+}
+
 // Explicitly rounded operations: the drift of a halo element must be bit-identical
 // to the owner's drift of the same element, so no contraction choice is left to
 // the compiler.
@@ -113,6 +136,90 @@ __device__ __forceinline__ void block_reduce(double (&v)[Q], double (*s_red)[kMa
     __syncthreads();
 }
 
+// Float-pair (hi + lo) addition with the two-sum error term, for the warp-level stage of the
+// FP32 passes' energy sums: about 44 significant bits on the FP32 pipe.  GB300 executes FP64
+// additions two lanes per SM and cycle, so a warp butterfly of doubles on every lane is slow
+// on the critical path of each block's reduction; in pairs the warp stage costs no FP64 work.
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+// Sum over the block of per-thread values hi[q] + lo[q] (e.g. a compensated FP32 sum s - c),
+// the result in FP64, valid in thread 0.  Each warp adds its lanes as float pairs, lane 0
+// converts once to FP64, warp 0 adds the warps in FP64.  Fixed reduction order.
+template <int Q>
+__device__ __forceinline__ void block_reduce_pairs(const float (&hi)[Q], const float (&lo)[Q], double (&v)[Q],
+                                                   double (*s_red)[kMaxQ], int tid, int nthr)
+{
+    const int warp = tid >> 5, lane = tid & 31, nw = (nthr + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        F2 x{hi[q], lo[q]};
+        for (int off = 16; off > 0; off >>= 1) {
+            const F2 o{__shfl_xor_sync(0xffffffffu, x.hi, off), __shfl_xor_sync(0xffffffffu, x.lo, off)};
+            x = f2_add(x, o);
+        }
+        if (lane == 0) s_red[warp][q] = (double)x.hi + (double)x.lo;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            double x = lane < nw ? s_red[lane][q] : 0.0;
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            v[q] = x;
+        }
+    }
+    __syncthreads();
+}
+
+// Sum of the grid's block partials partials[b * kMaxQ + q] (b < nb) by one warp, in FP64 and a
+// fixed order (each lane adds the blocks b = lane, lane + 32, ... in turn, then a butterfly);
+// call with all 32 lanes of the warp; the result is valid in every lane.
+template <int Q>
+__device__ __forceinline__ void warp_sum_partials(const double* partials, int nb, int lane, double (&w)[Q])
+{
+#pragma unroll
+    for (int q = 0; q < Q; ++q) w[q] = 0.0;
+    for (int b = lane; b < nb; b += 32)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) w[q] += __ldcg(&partials[(size_t)b * kMaxQ + q]);
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+        for (int off = 16; off > 0; off >>= 1) w[q] += __shfl_xor_sync(0xffffffffu, w[q], off);
+}
+
+// Block sum of per-thread accumulators acc[q] (nullptr: 0) into v[q], valid in thread 0:
+// compensated FP32 accumulators (their s - c) through the float-pair warp stage, FP64 ones
+// through block_reduce.
+template <typename T, int Q>
+__device__ __forceinline__ void block_reduce_acc(const Acc<T>* const (&acc)[Q], double (&v)[Q],
+                                                 double (*s_red)[kMaxQ], int tid, int nthr)
+{
+    if constexpr (sizeof(T) == 4) {
+        float hi[Q], lo[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            hi[q] = acc[q] ? acc[q]->s : 0.f;
+            lo[q] = acc[q] ? -acc[q]->c : 0.f;
+        }
+        block_reduce_pairs<Q>(hi, lo, v, s_red, tid, nthr);
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) v[q] = acc[q] ? acc[q]->value() : 0.0;
+        block_reduce<Q>(v, s_red, tid, nthr);
+    }
+}
+
 // block_reduce over the first nthr threads only (a multiple of 32), synchronising on the
 // named barrier `bar` instead of the whole block.
 template <int Q>
@@ -135,6 +242,40 @@ __device__ __forceinline__ void group_reduce(double (&v)[Q], double (*s_red)[kMa
         }
     }
     asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthr) : "memory");
+}
+
+// group_reduce of per-thread accumulators acc[q] (nullptr: 0): compensated FP32 ones through
+// a float-pair warp stage, FP64 ones as group_reduce does.  Valid in thread 0 of the group.
+template <typename T, int Q>
+__device__ __forceinline__ void group_reduce_acc(const Acc<T>* const (&acc)[Q], double (&v)[Q],
+                                                 double (*s_red)[kMaxQ], int tid, int nthr, int bar)
+{
+    if constexpr (sizeof(T) == 4) {
+        const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            F2 x{acc[q] ? acc[q]->s : 0.f, acc[q] ? -acc[q]->c : 0.f};
+            for (int off = 16; off > 0; off >>= 1) {
+                const F2 o{__shfl_xor_sync(0xffffffffu, x.hi, off), __shfl_xor_sync(0xffffffffu, x.lo, off)};
+                x = f2_add(x, o);
+            }
+            if (lane == 0) s_red[warp][q] = (double)x.hi + (double)x.lo;
+        }
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthr) : "memory");
+        if (warp == 0) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                double x = lane < nw ? s_red[lane][q] : 0.0;
+                for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+                v[q] = x;
+            }
+        }
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthr) : "memory");
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) v[q] = acc[q] ? acc[q]->value() : 0.0;
+        group_reduce<Q>(v, s_red, tid, nthr, bar);
+    }
 }
 
 // ---------------------------------------------------------------- lattice tiling and potential

@@ -30,13 +30,16 @@ template <typename T>
 // With P_RK_ERROR, v2 instead carries the sums |B k|^2 and |y|^2 over the degrees of freedom of
 // the last stage (adaptive RK3-4): the last block sets the next step size from their ratio.
 // h: the step size of this stage.
-__device__ __forceinline__ void rk_finish(const RkStageArgs<T>& A, double (&v)[kMaxQ], double a_old, double h,
-                                          bool first, double (*s_red)[kMaxQ], int* s_last, int tid, int nthr,
-                                          double (*v2)[kMaxQ] = nullptr, int dims = 3)
+// acc / acc2: the thread's accumulators of the sums (nullptr: none; acc2 nullptr: no v2).
+__device__ __forceinline__ void rk_finish(const RkStageArgs<T>& A, const Acc<T>* const (&acc)[kMaxQ], double a_old,
+                                          double h, bool first, double (*s_red)[kMaxQ], int* s_last, int tid, int nthr,
+                                          const Acc<T>* const (*acc2)[kMaxQ] = nullptr, int dims = 3)
 {
     const int N = A.N;
-    block_reduce<kMaxQ>(v, s_red, tid, nthr);
-    if (v2) block_reduce<kMaxQ>(*v2, s_red, tid, nthr);
+    double v[kMaxQ], v2b[kMaxQ];
+    double (*v2)[kMaxQ] = acc2 ? &v2b : nullptr;
+    block_reduce_acc<T, kMaxQ>(acc, v, s_red, tid, nthr);
+    if (acc2) block_reduce_acc<T, kMaxQ>(*acc2, v2b, s_red, tid, nthr);
     if (tid == 0) {
 #pragma unroll
         for (int q = 0; q < kMaxQ; ++q) A.partials[(size_t)blockIdx.x * kMaxQ + q] = v[q];
@@ -50,20 +53,11 @@ __device__ __forceinline__ void rk_finish(const RkStageArgs<T>& A, double (&v)[k
     __syncthreads();
     if (!*s_last) return;
     __threadfence();
+    if (tid >= 32) return;  // one warp sums the grid's partials, its lane 0 runs the epilogue
     double w[kMaxQ];
-#pragma unroll
-    for (int q = 0; q < kMaxQ; ++q) w[q] = 0.0;
-    for (int b = tid; b < (int)gridDim.x; b += nthr)
-#pragma unroll
-        for (int q = 0; q < kMaxQ; ++q) w[q] += __ldcg(&A.partials[(size_t)b * kMaxQ + q]);
-    block_reduce<kMaxQ>(w, s_red, tid, nthr);
+    warp_sum_partials<kMaxQ>(A.partials, (int)gridDim.x, tid, w);
     double w2[kMaxQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    if (v2) {
-        for (int b = tid; b < (int)gridDim.x; b += nthr)
-#pragma unroll
-            for (int q = 0; q < kMaxQ; ++q) w2[q] += __ldcg(&A.partials[((size_t)gridDim.x + b) * kMaxQ + q]);
-        block_reduce<kMaxQ>(w2, s_red, tid, nthr);
-    }
+    if (v2) warp_sum_partials<kMaxQ>(A.partials + (size_t)gridDim.x * kMaxQ, (int)gridDim.x, tid, w2);
     if (tid == 0) {
         DevScal* S = A.scal;
         const double vol = dims == 1 ? (double)N : (dims == 2 ? (double)N * N : (double)N * N * N);
@@ -75,7 +69,7 @@ __device__ __forceinline__ void rk_finish(const RkStageArgs<T>& A, double (&v)[k
         const double K = K0 + K1, G = G0 + G1;
         const double rho = K + G + Vp, p = K - G / 3.0 - Vp;
         const bool expand = (A.flags & P_EXPANSION) != 0;
-        const double a2al = pow(a, 2.0 * A.alpha);
+        const double a2al = apow(a, 2.0 * A.alpha);
         const double H = b / a;
         const double hv = H != 0.0 ? fabs(H * H - a2al * A.kappa * rho / 3.0) / (H * H) : 0.0;
         S->diag[D_T] = S->t;
@@ -95,8 +89,8 @@ __device__ __forceinline__ void rk_finish(const RkStageArgs<T>& A, double (&v)[k
         if (expand) {
             const double Fa = b;
             // Eq. Friedmann1, or for a non-minimally coupled field Eq. piadot with R of the state
-            const double Fb = A.nmc ? a * (pow(a, 2.0 * A.alpha) * S->rbar / 6.0 - (1.0 - A.alpha) * (b / a) * (b / a))
-                                    : pow(a, 2.0 * A.alpha + 1.0) * (A.kappa / 6.0) * ((2.0 * A.alpha - 1.0) * rho - 3.0 * p);
+            const double Fb = A.nmc ? a * (apow(a, 2.0 * A.alpha) * S->rbar / 6.0 - (1.0 - A.alpha) * (b / a) * (b / a))
+                                    : apow(a, 2.0 * A.alpha + 1.0) * (A.kappa / 6.0) * ((2.0 * A.alpha - 1.0) * rho - 3.0 * p);
             const double ka = first ? h * Fa : A.A * S->rk[0] + h * Fa;
             const double kb = first ? h * Fb : A.A * S->rk[1] + h * Fb;
             S->rk[0] = ka;
@@ -156,9 +150,9 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
     if (tid == 0) {
         const double a = A.scal->a;
         const double h = (A.flags & P_DEVICE_H) ? A.scal->h : A.h;  // adaptive steps: the device's h
-        s_coef[0] = h * pow(a, A.alpha - 3.0);
-        s_coef[1] = h * pow(a, 1.0 + A.alpha) / (A.dx * A.dx);
-        s_coef[2] = h * pow(a, 3.0 + A.alpha);
+        s_coef[0] = h * apow(a, A.alpha - 3.0);
+        s_coef[1] = h * apow(a, 1.0 + A.alpha) / (A.dx * A.dx);
+        s_coef[2] = h * apow(a, 3.0 + A.alpha);
         s_coef[3] = a;
         s_coef[5] = h;
         s_coef[4] = A.nmc ? A.xi * A.scal->rbar : 0.0;  // xi R of the stage's state
@@ -293,14 +287,10 @@ __global__ void __launch_bounds__(512) k_rk_stage(const RkStageArgs<T> A)
     }
 
     // ---- block partials, last block: energies of the old state and the (a, a') stage ----
-    double v[kMaxQ];
-    v[0] = accK[0].value();
-    v[1] = NF > 1 ? accK[NF - 1].value() : 0.0;
-    v[2] = accG[0].value();
-    v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
-    v[4] = accV.value();
-    double ve[kMaxQ] = {accE.value(), accY.value(), 0.0, 0.0, 0.0};
-    rk_finish(A, v, s_coef[3], s_coef[5], first, s_red, &s_last, tid, nthr, est ? &ve : nullptr);
+    const Acc<T>* av[kMaxQ] = {&accK[0], NF > 1 ? &accK[NF - 1] : nullptr, &accG[0], NF > 1 ? &accG[NF - 1] : nullptr,
+                               &accV};
+    const Acc<T>* ae[kMaxQ] = {&accE, &accY, nullptr, nullptr, nullptr};
+    rk_finish(A, av, s_coef[3], s_coef[5], first, s_red, &s_last, tid, nthr, est ? &ae : nullptr);
 }
 
 // TMA-staged form of the same stage.  One producer warp copies, plane after plane, the rows
@@ -356,9 +346,9 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
     if (tid == 0) {
         const double a = A.scal->a;
         const double h = (A.flags & P_DEVICE_H) ? A.scal->h : A.h;  // adaptive steps: the device's h
-        s_coef[0] = h * pow(a, A.alpha - 3.0);
-        s_coef[1] = h * pow(a, 1.0 + A.alpha) / (A.dx * A.dx);
-        s_coef[2] = h * pow(a, 3.0 + A.alpha);
+        s_coef[0] = h * apow(a, A.alpha - 3.0);
+        s_coef[1] = h * apow(a, 1.0 + A.alpha) / (A.dx * A.dx);
+        s_coef[2] = h * apow(a, 3.0 + A.alpha);
         s_coef[3] = a;
         s_coef[5] = h;
         s_coef[4] = A.nmc ? A.xi * A.scal->rbar : 0.0;  // xi R of the stage's state
@@ -638,18 +628,12 @@ __global__ void __launch_bounds__(480, 1) k_rk_stage_tma(const RkStageArgs<T> A)
     }
     __syncthreads();  // producer and consumers meet; no copy is in flight past this point
     if (tid == 0 && s_timeout) atomicOr(&A.scal->status, ST_TIMEOUT);
-    double v[kMaxQ];
-    v[0] = accK[0].value();
-    v[1] = NF > 1 ? accK[NF - 1].value() : 0.0;
-    v[2] = accG[0].value();
-    v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
-    v[4] = accV.value();
-    double v2[kMaxQ] = {nK.value(), nG.value(), nV.value(), nPV.value(), nP2.value()};
-    if (est) {  // adaptive RK3-4 (never with the Ricci terms)
-        v2[0] = accE.value();
-        v2[1] = accY.value();
-    }
-    rk_finish(A, v, s_coef[3], s_coef[5], first, s_red, &s_last, tid, nthr, fuse_r || est ? &v2 : nullptr);
+    const Acc<T>* av[kMaxQ] = {&accK[0], NF > 1 ? &accK[NF - 1] : nullptr, &accG[0], NF > 1 ? &accG[NF - 1] : nullptr,
+                               &accV};
+    // the Ricci terms of the output state, or for adaptive RK3-4 (never with them) the estimate
+    const Acc<T>* a2[kMaxQ] = {est ? &accE : &nK, est ? &accY : &nG, est ? nullptr : &nV, est ? nullptr : &nPV,
+                               est ? nullptr : &nP2};
+    rk_finish(A, av, s_coef[3], s_coef[5], first, s_red, &s_last, tid, nthr, fuse_r || est ? &a2 : nullptr);
 }
 
 // The stage on a reduced (d+1)-dimensional lattice (section "Scalar dynamics in 1+1 and 2+1
@@ -666,9 +650,9 @@ __global__ void __launch_bounds__(256) k_reduced_rk(const RkStageArgs<T> A, int 
     if (tid == 0) {
         const double a = A.scal->a;
         const double h = (A.flags & P_DEVICE_H) ? A.scal->h : A.h;  // adaptive steps: the device's h
-        s_coef[0] = h * pow(a, A.alpha - 3.0);
-        s_coef[1] = h * pow(a, 1.0 + A.alpha) / (A.dx * A.dx);
-        s_coef[2] = h * pow(a, 3.0 + A.alpha);
+        s_coef[0] = h * apow(a, A.alpha - 3.0);
+        s_coef[1] = h * apow(a, 1.0 + A.alpha) / (A.dx * A.dx);
+        s_coef[2] = h * apow(a, 3.0 + A.alpha);
         s_coef[3] = a;
         s_coef[5] = h;
         s_coef[4] = 0.0;
@@ -742,14 +726,10 @@ __global__ void __launch_bounds__(256) k_reduced_rk(const RkStageArgs<T> A, int 
         }
         accV.add(vsum);
     }
-    double v[kMaxQ];
-    v[0] = accK[0].value();
-    v[1] = NF > 1 ? accK[NF - 1].value() : 0.0;
-    v[2] = accG[0].value();
-    v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
-    v[4] = accV.value();
-    double ve[kMaxQ] = {accE.value(), accY.value(), 0.0, 0.0, 0.0};
-    rk_finish(A, v, s_coef[3], s_coef[5], first, s_red, &s_last, tid, nthr, est ? &ve : nullptr, dims);
+    const Acc<T>* av[kMaxQ] = {&accK[0], NF > 1 ? &accK[NF - 1] : nullptr, &accG[0], NF > 1 ? &accG[NF - 1] : nullptr,
+                               &accV};
+    const Acc<T>* ae[kMaxQ] = {&accE, &accY, nullptr, nullptr, nullptr};
+    rk_finish(A, av, s_coef[3], s_coef[5], first, s_red, &s_last, tid, nthr, est ? &ae : nullptr, dims);
 }
 
 // Background Ricci scalar of a non-minimally coupled field (section "Scalar fields

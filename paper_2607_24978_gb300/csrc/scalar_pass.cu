@@ -49,12 +49,20 @@ __device__ __forceinline__ void finish_pass_vol(const ScalarPassArgs<T>& A, Acc<
                                                 int* s_last, int tid, int nthr, int timeout, double vol)
 {
     double v[kMaxQ];
-    v[0] = accK[0].value();
-    v[1] = NF > 1 ? accK[NF - 1].value() : 0.0;
-    v[2] = accG[0].value();
-    v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
-    v[4] = accV.value();
-    block_reduce<kMaxQ>(v, s_red, tid, nthr);
+    if constexpr (sizeof(T) == 4) {  // compensated FP32 sums s - c: the warp stage in float pairs
+        const float hi[kMaxQ] = {accK[0].s, NF > 1 ? accK[NF - 1].s : 0.f, accG[0].s, NF > 1 ? accG[NF - 1].s : 0.f,
+                                 accV.s};
+        const float lo[kMaxQ] = {-accK[0].c, NF > 1 ? -accK[NF - 1].c : 0.f, -accG[0].c,
+                                 NF > 1 ? -accG[NF - 1].c : 0.f, -accV.c};
+        block_reduce_pairs<kMaxQ>(hi, lo, v, s_red, tid, nthr);
+    } else {
+        v[0] = accK[0].value();
+        v[1] = NF > 1 ? accK[NF - 1].value() : 0.0;
+        v[2] = accG[0].value();
+        v[3] = NF > 1 ? accG[NF - 1].value() : 0.0;
+        v[4] = accV.value();
+        block_reduce<kMaxQ>(v, s_red, tid, nthr);
+    }
     if (tid == 0) {
 #pragma unroll
         for (int q = 0; q < kMaxQ; ++q) A.partials[(size_t)blockIdx.x * kMaxQ + q] = v[q];
@@ -67,13 +75,9 @@ __device__ __forceinline__ void finish_pass_vol(const ScalarPassArgs<T>& A, Acc<
     if (!*s_last) return;
 
     __threadfence();
+    if (tid >= 32) return;  // one warp sums the grid's partials, its lane 0 runs the epilogue
     double w[kMaxQ];
-#pragma unroll
-    for (int q = 0; q < kMaxQ; ++q) w[q] = 0.0;
-    for (int b = tid; b < (int)gridDim.x; b += nthr)
-#pragma unroll
-        for (int q = 0; q < kMaxQ; ++q) w[q] += __ldcg(&A.partials[(size_t)b * kMaxQ + q]);
-    block_reduce<kMaxQ>(w, s_red, tid, nthr);
+    warp_sum_partials<kMaxQ>(A.partials, (int)gridDim.x, tid, w);
     if (tid == 0)
         scalar_epilogue(A.scal, w, vol, A.dx, s_coef[3], A.alpha, A.kappa, A.d, A.e, A.k, A.flags, A.hubble_limit);
 }

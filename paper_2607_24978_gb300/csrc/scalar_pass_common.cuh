@@ -18,9 +18,9 @@ __device__ __forceinline__ void pass_coefficients(const double a_old, const doub
 {
     const double a_new = expand ? a_old + d * b_old : a_old;
     const double ah = 0.5 * (a_old + a_new);
-    s_coef[0] = d * pow(ah, alpha - 3.0);
-    s_coef[1] = pow(a_new, 1.0 + alpha) / (dx * dx);
-    s_coef[2] = pow(a_new, 3.0 + alpha);
+    s_coef[0] = d * apow(ah, alpha - 3.0);
+    s_coef[1] = apow(a_new, 1.0 + alpha) / (dx * dx);
+    s_coef[2] = apow(a_new, 3.0 + alpha);
     s_coef[3] = a_new;
 }
 
@@ -33,12 +33,12 @@ __device__ __forceinline__ void pass_coefficients_warps(int tid, const double a_
     if (tid != 0 && tid != 32 && tid != 64) return;
     const double a_new = expand ? a_old + d * b_old : a_old;
     if (tid == 0) {
-        s_coef[0] = d * pow(0.5 * (a_old + a_new), alpha - 3.0);
+        s_coef[0] = d * apow(0.5 * (a_old + a_new), alpha - 3.0);
         s_coef[3] = a_new;
     } else if (tid == 32) {
-        s_coef[1] = pow(a_new, 1.0 + alpha) / (dx * dx);
+        s_coef[1] = apow(a_new, 1.0 + alpha) / (dx * dx);
     } else {
-        s_coef[2] = pow(a_new, 3.0 + alpha);
+        s_coef[2] = apow(a_new, 3.0 + alpha);
     }
 }
 
@@ -280,21 +280,25 @@ __device__ inline void scalar_epilogue(DevScal* S, const double (&w)[kMaxQ], dou
                                        double alpha, double kappa, double d, double e, double k, int flags,
                                        double hubble_limit)
 {
-    const double a2 = a * a, a6 = a2 * a2 * a2;
-    const double K0 = w[0] / (2.0 * a6 * vol), K1 = w[1] / (2.0 * a6 * vol);
-    const double G0 = w[2] / (dx * dx * 2.0 * a2 * vol), G1 = w[3] / (dx * dx * 2.0 * a2 * vol);
-    const double Vp = w[4] / vol;
+    // reciprocals once: FP64 divisions are long dependent chains on GB300's FP64 pipe, and this
+    // runs on one thread at the end of every pass
+    constexpr double third = 1.0 / 3.0, sixth = 1.0 / 6.0;
+    const double ivol = 1.0 / vol, ia = 1.0 / a, ia2 = ia * ia, ia6 = ia2 * ia2 * ia2;
+    const double ck = 0.5 * ia6 * ivol, cg = 0.5 * ia2 * ivol / (dx * dx);
+    const double K0 = w[0] * ck, K1 = w[1] * ck;
+    const double G0 = w[2] * cg, G1 = w[3] * cg;
+    const double Vp = w[4] * ivol;
     const double K = K0 + K1, G = G0 + G1;
     const double rho = K + G + Vp;
-    const double p = K - G / 3.0 - Vp;
+    const double p = K - G * third - Vp;
     const bool expand = (flags & P_EXPANSION) != 0;
-    const double a2al = pow(a, 2.0 * alpha);
+    const double a2al = apow(a, 2.0 * alpha);
     double b = S->b;
-    if ((flags & P_HUBBLE_INIT) && expand) b = a * sqrt(a2al * kappa * rho / 3.0);
-    const double addot = expand ? pow(a, 2.0 * alpha + 1.0) * (kappa / 6.0) * ((2.0 * alpha - 1.0) * rho - 3.0 * p) : 0.0;
+    if ((flags & P_HUBBLE_INIT) && expand) b = a * sqrt(a2al * kappa * rho * third);
+    const double addot = expand ? a2al * a * (kappa * sixth) * ((2.0 * alpha - 1.0) * rho - 3.0 * p) : 0.0;
     const double b_int = b + e * addot;
-    const double H = b_int / a;
-    const double hv = H != 0.0 ? fabs(H * H - a2al * kappa * rho / 3.0) / (H * H) : 0.0;
+    const double H = b_int * ia;
+    const double hv = H != 0.0 ? fabs(H * H - a2al * kappa * rho * third) / (H * H) : 0.0;
     const double t_int = S->t + d;
     if (flags & P_COMMIT) {
         S->a = a;

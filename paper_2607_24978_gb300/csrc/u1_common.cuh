@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include "cl_internal.cuh"
+#include "kernel_common.cuh"
 
 namespace clk {
 
@@ -36,11 +37,11 @@ __device__ __forceinline__ void u1_epilogue(const U1Args<T>& A, const double (&w
     const double K = w[0] / (2.0 * a6 * vol);
     const double G = w[1] / (A.dx * A.dx * 2.0 * a2 * vol);
     const double Vp = w[2] / vol;
-    const double KE = A.ws2 * w[3] / (2.0 * pow(a, 2.0 + 2.0 * A.alpha) * vol);
-    const double GB = A.ws2 * w[4] / (pow(A.dx, 4.0) * a4 * vol);
+    const double KE = A.ws2 * w[3] / (2.0 * apow(a, 2.0 + 2.0 * A.alpha) * vol);
+    const double GB = A.ws2 * w[4] / (apow(A.dx, 4.0) * a4 * vol);
     const double rho = K + G + Vp + KE + GB;
     const double p = K - G / 3.0 - Vp + (KE + GB) / 3.0;
-    const double a2al = pow(a, 2.0 * A.alpha);
+    const double a2al = apow(a, 2.0 * A.alpha);
     double bb = b;
     if ((A.flags & P_HUBBLE_INIT) && expand) bb = a * sqrt(a2al * A.kappa * rho / 3.0);
     const double H = bb / a;
@@ -61,7 +62,7 @@ __device__ __forceinline__ void u1_epilogue(const U1Args<T>& A, const double (&w
     if (A.flags & P_HUBBLE_INIT) S->b = bb;
     if (update && expand) {
         const double Fa = b;
-        const double Fb = pow(a, 2.0 * A.alpha + 1.0) * (A.kappa / 6.0) * ((2.0 * A.alpha - 1.0) * rho - 3.0 * p);
+        const double Fb = apow(a, 2.0 * A.alpha + 1.0) * (A.kappa / 6.0) * ((2.0 * A.alpha - 1.0) * rho - 3.0 * p);
         const double ka = first ? A.h * Fa : A.A * S->rk[0] + A.h * Fa;
         const double kb = first ? A.h * Fb : A.A * S->rk[1] + A.h * Fb;
         S->rk[0] = ka;

@@ -102,10 +102,10 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 ? 3 : 2) k_u1_fused(
     const uint32_t z0 = bz * (uint32_t)A.dz, z1 = min(z0 + (uint32_t)A.dz, N);
     if (tid == 0) {
         const double a = A.scal->a, b = expand ? A.scal->b : 0.0;
-        s_coef[0] = pow(a, A.alpha - 3.0);                     // phi' = c0 pi
-        s_coef[1] = pow(a, 1.0 + A.alpha) / (A.dx * A.dx);      // Laplacian
-        s_coef[2] = pow(a, 3.0 + A.alpha);                     // potential
-        s_coef[3] = pow(a, A.alpha - 1.0);                     // E' prefactor
+        s_coef[0] = apow(a, A.alpha - 3.0);                     // phi' = c0 pi
+        s_coef[1] = apow(a, 1.0 + A.alpha) / (A.dx * A.dx);      // Laplacian
+        s_coef[2] = apow(a, 3.0 + A.alpha);                     // potential
+        s_coef[3] = apow(a, A.alpha - 1.0);                     // E' prefactor
         s_coef[4] = (1.0 - A.alpha) * b / a;                   // electric friction
         s_coef[5] = a;
     }

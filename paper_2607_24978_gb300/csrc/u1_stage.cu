@@ -165,10 +165,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_u1_stage(const 
     const bool expand = (A.flags & P_EXPANSION) != 0;
     if (tid == 0) {
         const double a = A.scal->a, b = expand ? A.scal->b : 0.0;
-        s_coef[0] = pow(a, A.alpha - 3.0);                     // phi' = c0 pi
-        s_coef[1] = pow(a, 1.0 + A.alpha) / (A.dx * A.dx);      // Laplacian
-        s_coef[2] = pow(a, 3.0 + A.alpha);                     // potential
-        s_coef[3] = pow(a, A.alpha - 1.0);                     // E' prefactor
+        s_coef[0] = apow(a, A.alpha - 3.0);                     // phi' = c0 pi
+        s_coef[1] = apow(a, 1.0 + A.alpha) / (A.dx * A.dx);      // Laplacian
+        s_coef[2] = apow(a, 3.0 + A.alpha);                     // potential
+        s_coef[3] = apow(a, A.alpha - 1.0);                     // E' prefactor
         s_coef[4] = (1.0 - A.alpha) * b / a;                   // electric friction
         s_coef[5] = a;
     }
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(256) k_u1_gauss(const U1Args<T> A, int mode)
     __shared__ int s_last;
     const uint32_t N = (uint32_t)A.N;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const double ca = pow(A.scal->a, 1.0 - A.alpha);
+    const double ca = apow(A.scal->a, 1.0 - A.alpha);
     const double b4 = 0.25 / (A.dx * A.dx);
     double gmax = 0.0, smax = 0.0, gsq = 0.0, e2 = 0.0;
     const U1Tile tile(N, (uint32_t)A.dz);

@@ -300,8 +300,9 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquettes(const U1Ar
         ring.release((int)t.nz + 1, lane);
     }
     __syncthreads();  // producer and consumers meet; no copy is in flight past this point
-    double v[1] = {accGB.value()};
-    block_reduce<1>(v, s_red, tid, G::NT);
+    double v[1];
+    const Acc<T>* av[1] = {&accGB};
+    block_reduce_acc<T, 1>(av, v, s_red, tid, G::NT);
     if (tid == 0) {
         A.partials[(size_t)gridDim.x * kMaxQ + blockIdx.x] = v[0];
         if (s_fail) atomicOr(&A.scal->status, ST_TIMEOUT);
@@ -329,13 +330,13 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
     const bool expand = (A.flags & P_EXPANSION) != 0;
     if (tid == 0) {
         const double a = A.scal->a, b = expand ? A.scal->b : 0.0;
-        s_coef[0] = pow(a, A.alpha - 3.0);                 // phi' = c0 pi
-        s_coef[1] = pow(a, 1.0 + A.alpha) / (A.dx * A.dx);  // Laplacian
-        s_coef[2] = pow(a, 3.0 + A.alpha);                 // potential
-        s_coef[3] = pow(a, A.alpha - 1.0);                 // E' prefactor
+        s_coef[0] = apow(a, A.alpha - 3.0);                 // phi' = c0 pi
+        s_coef[1] = apow(a, 1.0 + A.alpha) / (A.dx * A.dx);  // Laplacian
+        s_coef[2] = apow(a, 3.0 + A.alpha);                 // potential
+        s_coef[3] = apow(a, A.alpha - 1.0);                 // E' prefactor
         s_coef[4] = (1.0 - A.alpha) * b / a;               // electric friction
         s_coef[5] = a;
-        s_coef[6] = pow(a, 1.0 - A.alpha);                 // a^(1-alpha) E in the Gauss charge
+        s_coef[6] = apow(a, 1.0 - A.alpha);                 // a^(1-alpha) E in the Gauss charge
         s_src[SG_PHI] = A.phi_in;
         s_src[SG_PI] = A.pi_in;
 #pragma unroll
@@ -470,8 +471,9 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
     // ---- block partials; last block: energies of the old state and the (a, a') stage ----
     // slot 4 of the stage's partials carries the Gauss sum (the magnetic energy's partials
     // follow in the plaquette launch's region)
-    double v[kMaxQ] = {accK.value(), accG.value(), accV.value(), accKE.value(), accGs.value()};
-    block_reduce<kMaxQ>(v, s_red, tid, G::NT);
+    double v[kMaxQ];
+    const Acc<T>* av[kMaxQ] = {&accK, &accG, &accV, &accKE, &accGs};
+    block_reduce_acc<T, kMaxQ>(av, v, s_red, tid, G::NT);
     if (tid == 0) {
         if (s_fail) atomicOr(&A.scal->status, ST_TIMEOUT);
 #pragma unroll
@@ -483,16 +485,14 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    double w[kMaxQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    double wg[1] = {0.0};
-    for (int b = tid; b < (int)gridDim.x; b += G::NT) {
-#pragma unroll
-        for (int q = 0; q < kMaxQ - 1; ++q) w[q] += __ldcg(&A.partials[(size_t)b * kMaxQ + q]);
-        w[kMaxQ - 1] += __ldcg(&A.partials[(size_t)gridDim.x * kMaxQ + b]);  // plaquette launch, same grid
-        wg[0] += __ldcg(&A.partials[(size_t)b * kMaxQ + kMaxQ - 1]);
-    }
-    block_reduce<kMaxQ>(w, s_red, tid, G::NT);
-    if (track) block_reduce<1>(wg, s_red, tid, G::NT);
+    if (tid >= 32) return;  // one warp sums the grid's partials, its lane 0 runs the epilogue
+    double ws[kMaxQ];  // the stage's sums; slot 4 is the Gauss sum
+    warp_sum_partials<kMaxQ>(A.partials, (int)gridDim.x, tid, ws);
+    double gb = 0.0;  // the magnetic energy from the plaquette launch (same grid, one value a block)
+    for (int b = tid; b < (int)gridDim.x; b += 32) gb += __ldcg(&A.partials[(size_t)gridDim.x * kMaxQ + b]);
+    for (int off = 16; off > 0; off >>= 1) gb += __shfl_xor_sync(0xffffffffu, gb, off);
+    double w[kMaxQ] = {ws[0], ws[1], ws[2], ws[3], gb};
+    double wg[1] = {ws[kMaxQ - 1]};
     if (tid == 0) {
         if (track) u1_gauss_track(A.scal, wg[0], w[3], s_coef[6]);
         u1_epilogue(A, w, s_coef[5], first, update, expand, V);

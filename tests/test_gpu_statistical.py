@@ -23,8 +23,13 @@ calls for):
   * in the chaotic phase, statistics that one 64^3 realisation determines to 1 %: rho at every
     record, 2000-step window means of each energy and of the Hubble-constraint violation, and
     the spectra averaged over the 21 snapshots of steps 8000-10000, compared as the field
-    variance in five equal k-bands, the total variance and the peak bin.  (A single bin of
-    one snapshot scatters by 2-50 % between two chaotic runs: its mode count is 7 to 12,000.)
+    variance in five k-bands of equal mode count, the total variance and the peak bin.  (A
+    single bin of one snapshot scatters by 2-50 % between two chaotic runs: its mode count
+    is 7 to 12,000.  The choice of statistics was calibrated on independent, equally valid
+    FP64 runs -- the oracle with its sums in another order and with 1e-13 perturbations of
+    the initial field -- and on GPU runs: across them the window means stay within 0.3 %, the
+    total variances within 0.3 % and the equal-mode bands within 0.5 % of the stored run, while
+    five bands of equal width in k reach 1.1 %, since the lowest of them holds few modes.)
 The Hubble-constraint violation (Eq. Friedmann2) stays below 1e-3 everywhere.
 """
 import json
@@ -146,7 +151,7 @@ def test_spectra_per_bin(golden, gpu64, gpu32, which):
 @pytest.mark.parametrize("which", ["fp64", "fp32k"])
 def test_spectra_in_the_chaotic_phase(golden, gpu64, gpu32, which):
     """Spectra averaged over the 21 snapshots of steps 8000-10000: field variance per k-band
-    (five equal bands of the bin index), the total variance and the peak bin."""
+    (five bands holding a fifth of the k > 0 modes each), the total variance and the peak bin."""
     gpu = gpu64 if which == "fp64" else gpu32
     steps = [s for s in golden["spectrum_steps"] if 8000 <= s <= 10000]
     assert len(steps) == 21
@@ -157,7 +162,9 @@ def test_spectra_in_the_chaotic_phase(golden, gpu64, gpu32, which):
         # Type I: Delta_l = n_l S_l / N^6 (bin width 1), so Delta_l / l is the bin's share of <f^2>
         va, vb = a[1:] / lidx[1:], b[1:] / lidx[1:]
         assert abs(va.sum() - vb.sum()) / vb.sum() < 1e-2
-        edges = np.linspace(0, len(vb), 6).astype(int)
+        cum = np.cumsum(np.asarray(golden["spectrum_counts"][f][1:], dtype=np.float64))
+        cum /= cum[-1]
+        edges = [0] + [int(np.searchsorted(cum, q / 5.0)) + 1 for q in range(1, 5)] + [len(vb)]
         for i in range(5):
             sa, sb = va[edges[i]:edges[i + 1]].sum(), vb[edges[i]:edges[i + 1]].sum()
             assert abs(sa - sb) / sb < 1e-2, (f, i, abs(sa - sb) / sb)
