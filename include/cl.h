@@ -427,9 +427,11 @@ const char* cl_last_error(const cl_lattice* l);
  * Arrays are site-major with channels contiguous: x[n * in_channels + c], site
  * n = (z*N + y)*N + x.  Weights W_l are FP32 [27][cout][cin], biases FP32 [cout].
  *
- * Precision CL_SG_BF16: the hidden C -> C layers run on the tensor cores (tcgen05, BF16
- * operands, FP32 accumulation, activations stored in BF16), the thin first and last layers
- * on CUDA cores in FP32 from BF16 activations; N must be a multiple of 16.
+ * Precision CL_SG_BF16: every layer runs on the tensor cores (tcgen05, BF16 operands, FP32
+ * accumulation); the thin first and last layers are zero-padded to 16 channels, the FP32
+ * input is rounded to BF16 as it is staged, hidden activations are stored in BF16 and the
+ * last layer writes FP32 with the residual; the backward pass computes the data gradients
+ * and the weight and bias gradients on the tensor cores too.  N must be a multiple of 16.
  * CL_SG_FP32: every layer on CUDA cores in FP32 (reference mode).
  * The handle owns all device memory; calls are ordered on its stream and synchronise
  * when they copy to or from host memory. */
