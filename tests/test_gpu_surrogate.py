@@ -373,3 +373,47 @@ def test_training_driver_and_the_judge(cl):
         r = T.evaluate(torch, s, mu, sg, N=32, jumps=2, warm=20, hubble_limit=float("inf"), hidden=16, layers=3)
         assert r["accepted"] == 2
         s.close()
+
+
+def test_surrogate_wall_time_against_the_leapfrog(cl):
+    """What the configured surrogate gains over the plain FP32 leapfrog (measured on the device):
+    one forward of the 6-layer, 48-channel network on a 128^3 lattice against the K = 16
+    leapfrog steps it replaces (VV-2, FP32 + Kahan, one cl_step call, graph replays).  The
+    forward moves 1.07 TFLOP through the tensor cores while the 16 steps move 0.8 GB, so the
+    jump costs several times the steps it saves: no gain at this size, and the jump length at
+    which one forward would break even (forward time / time per step) is far above 16.  The
+    judged-jump path is exercised in test_training_driver_and_the_judge."""
+    import math
+
+    import torch
+    N, K = 128, 16
+    st = torch.cuda.Stream()
+    rg = np.random.default_rng(3)
+    x = torch.randn(N ** 3 * 3, device="cuda")
+    y = torch.empty(N ** 3 * 2, device="cuda")
+
+    def device_ms(fn, n):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(n):
+            fn()
+        b.record(st)
+        b.synchronize()
+        return a.elapsed_time(b) / n
+
+    with cl.Surrogate(N, 3, 2, 48, 6, cl.CL_ACT_RELU, cl.CL_SG_BF16, stream=st.cuda_stream) as s:
+        for l, (ci, co) in enumerate(s.shapes):
+            s.set_weights(l, rg.standard_normal((27, co, ci)) * math.sqrt(2.0 / (27 * ci)), np.zeros(co))
+        t_fwd = device_ms(lambda: s.forward(x, y), 10)
+    with cl.Lattice(N, 8.0 * math.pi * N / 256, 1, cl.CL_PREC_FP32_KAHAN, cl.CL_INT_VV2, expansion=True, alpha=1.0,
+                    kappa=0.1, dt=0.01, stream=st.cuda_stream) as g:
+        g.cl_set_potential(cl.CL_POT_LPHI4, [1.0])
+        g.cl_init_vacuum(7, 1e30, 1e-4, (1.0,), (0.0,))
+        t_lf = device_ms(lambda: g.cl_step(K), 10)
+    breakeven_K = t_fwd / (t_lf / K)
+    print("forward %.3f ms, %d leapfrog steps %.3f ms, break-even K %.1f" % (t_fwd, K, t_lf, breakeven_K))
+    assert t_fwd > 1.5 * t_lf  # no gain at the configured width and jump length
+    assert breakeven_K > 2 * K
