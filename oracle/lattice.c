@@ -420,6 +420,10 @@ void orc_step(const orc_model* m, int scheme, double h, int nsteps,
 {
     const int64_t V = orc_volume(m);
     if (m->gauge == 1) {
+        if (scheme == ORC_VV2) {  /* the leapfrog with three fixed-point evaluations per implicit kick */
+            orc_u1_leapfrog(m, h, nsteps, 3, phi, pi, links, efield, abt);
+            return;
+        }
         for (int s = 0; s < nsteps; ++s) orc_u1_rk_step(m, scheme, h, phi, pi, links, efield, abt);
         return;
     }

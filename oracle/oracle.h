@@ -141,6 +141,12 @@ int orc_gauge_spectrum(const orc_model* m, const double* links, const double* ef
                        int type, double* k_out, double* delta_out, double* count_out, int cap);
 void orc_u1_gauss(const orc_model* m, const double* phi, const double* links,
                   const double* efield, double a, double* out_gauss /* N^3 */);
+/* Leapfrog of the U(1) + axion system (u1.c): positions phi, theta, a at integer steps, the
+ * kick of the momenta pi, E at fixed positions implicit (generalized Stoermer-Verlet), solved
+ * with `iters` fixed-point evaluations of the momentum force.  orc_step with ORC_VV2 on a
+ * gauge model takes iters = 3. */
+void orc_u1_leapfrog(const orc_model* m, double h, int nsteps, int iters, double* phi, double* pi,
+                     double* links, double* efield, double* abt);
 
 /* ---- random numbers, initial conditions, spectra ---- */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

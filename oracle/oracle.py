@@ -67,6 +67,7 @@ def _load(omp):
         L.orc_step.argtypes = [mp, C.c_int, C.c_double, C.c_int, dp, dp, C.c_void_p, C.c_void_p, dp]
         L.orc_u1_gauss.argtypes = [mp, dp, dp, dp, C.c_double, dp]
         L.orc_u1_rhs.argtypes = [mp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+        L.orc_u1_leapfrog.argtypes = [mp, C.c_double, C.c_int, C.c_int, dp, dp, dp, dp, dp]
         L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
         L.orc_dft3.argtypes = [C.c_int, C.c_int, dp, dp]
         L.orc_vacuum.argtypes = [mp, C.c_uint64, C.c_uint32, C.c_double, C.c_double, dp, dp, C.c_double,
@@ -160,6 +161,16 @@ def step(model, st, scheme, h, nsteps=1):
         st.links, st.efield = _c(st.links), _c(st.efield)
     lib().orc_step(C.byref(model), int(scheme), float(h), int(nsteps), st.phi, st.pi,
                    _ptr(st.links), _ptr(st.efield), st.abt)
+    return st
+
+
+def u1_leapfrog(model, st, h, nsteps=1, iters=3):
+    """Leapfrog steps of a U(1) + axion state with `iters` fixed-point evaluations of the
+    implicit momentum kick (step(..., VV2, ...) takes 3)."""
+    st.phi, st.pi, st.abt = _c(st.phi), _c(st.pi), _c(st.abt)
+    st.links, st.efield = _c(st.links), _c(st.efield)
+    lib().orc_u1_leapfrog(C.byref(model), float(h), int(nsteps), int(iters), st.phi, st.pi, st.links, st.efield,
+                          st.abt)
     return st
 
 

@@ -235,6 +235,89 @@ void orc_u1_rk_step(const orc_model* m, int scheme, double h, double* phi, doubl
     free(F);
 }
 
+/* ------------------------------------------------------------------ leapfrog */
+
+/* Momentum part of the right-hand side, f(q, a, b, p) = (pi', E'), at positions q = (phi, theta)
+ * and momenta p = (pi, E) stored as P[0..V) = pi, P[V..4V) = E_0..2. */
+static void u1_momentum_force(const orc_model* m, const double* phi, const double* th, const double* P, double a,
+                              double b, double* Fp, double* sphi, double* sth)
+{
+    const int64_t V = (int64_t)m->N * m->N * m->N;
+    u1_rhs(m, phi, P, th, P + V, a, b, sphi, Fp, sth, Fp + V);
+}
+
+/* Leapfrog of the axion-U(1) system (section "ALP-gauge interactions": its equations are not
+ * canonical in (pi, E), since the E' of Eq. AxionInfEOM depends on phi' and the pi' on E, so
+ * a kick at fixed positions is not explicit).  Positions q = (phi, theta, a) and momenta
+ * p = (pi, E, a') are staggered as in the generalized Stoermer-Verlet method (Hairer, Lubich
+ * and Wanner, Geometric Numerical Integration, section VI.3, its Eq. (3.4) with the momentum
+ * force f affine in p), ordered like the scalar velocity-Verlet step of lattice.c:
+ *   a'_{1/2} = a'_0 + h/2 a''(a_0, rho_0, p_0)                        (energies of q_0, p_0)
+ *   p_{1/2}  = p_0 + h/2 f(q_0, a_0, a'_{1/2}, p_{1/2})                (implicit)
+ *   a_1 = a_0 + h a'_{1/2};  phi_1 = phi_0 + h ((a_0+a_1)/2)^(alpha-3) pi_{1/2};
+ *   theta_1 = theta_0 + h dx E_{1/2}
+ *   p_1      = p_{1/2} + h/2 f(q_1, a_1, a'_{1/2}, p_{1/2})             (explicit)
+ *   a'_1     = a'_{1/2} + h/2 a''(a_1, rho_1, p_1).
+ * The implicit half-kick is solved by fixed-point iteration, `iters` evaluations of f:
+ *   p^(1) = p_0 + h/2 G,   p^(k+1) = p_0 + h/2 f(q_0, a_0, a'_{1/2}, p^(k)),   p_{1/2} = p^(iters),
+ * where G is the force of the previous step's closing half-kick (so that p^(1) is the
+ * previous half-step momentum advanced by a full kick with the force at q_0), and, in the
+ * first step of a call, f(q_0, a_0, a'_0, p_0).  Because f is affine in p, the merged kick
+ * of two consecutive half-kicks is p_{n+1/2} = p_{n-1/2} + h f(q_n, (p_{n-1/2} + p_{n+1/2})/2)
+ * when iterated to convergence, which is the leapfrog with the coupling at the average of
+ * the old and new momenta. */
+void orc_u1_leapfrog(const orc_model* m, double h, int nsteps, int iters, double* phi, double* pi, double* links,
+                     double* efield, double* abt)
+{
+    const int N = m->N;
+    const int64_t V = (int64_t)N * N * N;
+    const double dx = m->L / N, al = m->alpha;
+    double* P0 = malloc(sizeof(double) * (size_t)(4 * V));  /* p_n: pi, E_0..2 */
+    double* Pk = malloc(sizeof(double) * (size_t)(4 * V));  /* iterate */
+    double* G = malloc(sizeof(double) * (size_t)(4 * V));   /* force of the last kick */
+    double* F = malloc(sizeof(double) * (size_t)(4 * V));
+    double* sphi = malloc(sizeof(double) * (size_t)V);      /* unused rates */
+    double* sth = malloc(sizeof(double) * (size_t)(3 * V));
+    memcpy(P0, pi, sizeof(double) * (size_t)V);
+    memcpy(P0 + V, efield, sizeof(double) * (size_t)(3 * V));
+    double a = abt[0], b = m->expansion ? abt[1] : 0.0;
+    if (iters < 1) iters = 1;
+    u1_momentum_force(m, phi, links, P0, a, b, G, sphi, sth);
+    for (int s = 0; s < nsteps; ++s) {
+        double e[ORC_NE];
+        double bh = b;
+        if (m->expansion) {
+            const double abt_n[3] = {a, b, abt[2]};
+            orc_energies(m, phi, P0, links, P0 + V, abt_n, e);
+            bh = b + 0.5 * h * orc_addot(m, a, e[ORC_E_RHO], e[ORC_E_P]);
+        }
+        for (int64_t l = 0; l < 4 * V; ++l) Pk[l] = P0[l] + 0.5 * h * G[l];
+        for (int k = 1; k < iters; ++k) {
+            u1_momentum_force(m, phi, links, Pk, a, bh, F, sphi, sth);
+            for (int64_t l = 0; l < 4 * V; ++l) Pk[l] = P0[l] + 0.5 * h * F[l];
+        }
+        const double a1 = m->expansion ? a + h * bh : a;
+        const double cd = h * pow(0.5 * (a + a1), al - 3.0);
+        for (int64_t n = 0; n < V; ++n) phi[n] += cd * Pk[n];
+        for (int64_t l = 0; l < 3 * V; ++l) links[l] += h * dx * Pk[V + l];
+        a = a1;
+        u1_momentum_force(m, phi, links, Pk, a, bh, G, sphi, sth);
+        for (int64_t l = 0; l < 4 * V; ++l) P0[l] = Pk[l] + 0.5 * h * G[l];
+        b = bh;
+        if (m->expansion) {
+            const double abt_n[3] = {a, bh, abt[2]};
+            orc_energies(m, phi, P0, links, P0 + V, abt_n, e);
+            b = bh + 0.5 * h * orc_addot(m, a, e[ORC_E_RHO], e[ORC_E_P]);
+        }
+        abt[2] += h;
+    }
+    memcpy(pi, P0, sizeof(double) * (size_t)V);
+    memcpy(efield, P0 + V, sizeof(double) * (size_t)(3 * V));
+    abt[0] = a;
+    if (m->expansion) abt[1] = b;
+    free(P0); free(Pk); free(G); free(F); free(sphi); free(sth);
+}
+
 /* --------------------------------------------------------------- gauge spectra */
 
 /* Binned spectra of the U(1) sector (section "ALP-gauge interactions": the spectra of the
