@@ -20,6 +20,7 @@ workload in FP64 without compensation), clocks (nvidia-smi during the timed regi
 Other workloads (--workload; one JSON line each, same keys where they apply):
   u1        axion + compact U(1) links, 192^3, FP32, RK3-3, alpha_Lambda = 30,
             V = phi^2/2, phi = 1 + noise, phi' = -0.5, A = 0, small divergence-free E.
+  u1lf      the same with the leapfrog (implicit momentum kick, three passes a step).
   ensemble  1024 independent lambda phi^4 lattices of sizes drawn from {32, 48, 64}^3,
             per-member vacuum amplitude lambda log-uniform in [1e-6, 1e-3], VV-2,
             FP32 + Kahan, one launch per pass for all members.
@@ -291,6 +292,12 @@ U1_STAGES = 3
 # algorithmic bytes of one RK stage per site: phi, pi, theta_1..3, E_1..3 and their eight
 # Runge-Kutta auxiliaries, read + write, 4 B each
 U1_BYTES_PER_SITE_STAGE = 8 * 2 * 2 * 4
+# the leapfrog's step per site, 4 B each: pass 1 reads (phi, theta_1..3) and (pi, E_1..3) and
+# writes the integer-time momenta and the first iterate (16 arrays); pass 2 reads the
+# positions, the iterate and the integer-time momenta and writes the next iterate (16);
+# pass 3 the same and writes the positions too (20)
+U1_LF_PASSES = 3
+U1_LF_BYTES_PER_SITE_STEP = (16 + 16 + 20) * 4
 RK_STAGES = 5
 # GW pass per site: the scalars' phi, pi, c of two fields read (24 B) and the five
 # auxiliaries and their momenta read and written (2 x 10 x 4 B), FP32
@@ -317,13 +324,14 @@ def timed_region(torch, g, stream, steps):
     return el, launches, clk.summary()
 
 
-def run_u1_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src):
+def run_u1_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src, leapfrog=False):
     import numpy as np
     from tests import inputs
     c = U1
     N = c["N"]
-    g = cl.Lattice(N, c["L"], 1, cl.CL_PREC_FP32, cl.CL_INT_RK3_3, gauge=cl.CL_GAUGE_U1_AXION, expansion=True,
-                   alpha=c["alpha"], kappa=c["kappa"], dt=c["dt"], stream=stream.cuda_stream)
+    g = cl.Lattice(N, c["L"], 1, cl.CL_PREC_FP32, cl.CL_INT_VV2 if leapfrog else cl.CL_INT_RK3_3,
+                   gauge=cl.CL_GAUGE_U1_AXION, expansion=True, alpha=c["alpha"], kappa=c["kappa"], dt=c["dt"],
+                   stream=stream.cuda_stream)
     g.cl_set_potential(cl.CL_POT_M2, [c["m2"]])
     g.cl_set_gauge_coupling(c["alphaL"], c["ws2"])
     if args.variant is not None:  # 2: staged launches (default), 0: gather launches, 1: fused stage
@@ -349,6 +357,31 @@ def run_u1_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_
     variant = g.cl_get_option(cl.CL_OPT_PASS_VARIANT)
     u1_dz = g.cl_get_option(cl.CL_OPT_TILE_DZ)
     g.close()
+    energies_end = {"a": e["a"], "rho": e["rho"], "KE": e["KE"], "GB": e["GB"],
+                    "gauss_violation": e["gauss_violation"], "hubble_violation": e["hubble_violation"],
+                    "gauss_rms_last_step": e["gauss_rms_step"], "gauss_rms_max_over_steps": e["gauss_rms_max"]}
+    if leapfrog:
+        step_s = el / args.steps
+        bytes_step = N ** 3 * U1_LF_BYTES_PER_SITE_STEP
+        achieved = bytes_step / step_s / 1e9
+        kern = ("three passes of k_u1s_plaquettes + k_u1s_stage<float,false,true> (staged neighbourhoods)"
+                if variant == 2 else "three passes of k_u1_plaquettes + k_u1_stage<float>")
+        return {"metric": "Gsite-updates/s, axion-U(1) 192^3 leapfrog", "value": world * N ** 3 * args.steps / el_max / 1e9,
+                "unit": "Gsite-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": el_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "axion-U(1) 192^3, leapfrog (implicit momentum kick, three force evaluations "
+                                       "per step), FP32, alpha_Lambda=30, (omega*/f*)^2=1e-4, kappa=1, V=phi^2/2, "
+                                       "phi=1, phi'=-0.5, A=0, divergence-free E (rms 1e-6), dt=0.01",
+                           "lattice": N, "passes_per_step": U1_LF_PASSES,
+                           "l2": "inputs (%.0f MB) larger than L2; no flush" % (N ** 3 * 16 * 4 / 1e6)},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                             "kernel": kern + ", per step", "tile_dz": u1_dz,
+                             "algorithmic_bytes_per_step": bytes_step},
+                "gpu_launches": launches, "clocks": clocks, "energies_end": energies_end,
+                "gauss_tracking": "rms lattice Gauss charge of every step's integer-time starting state, summed by "
+                                  "the second pass of the step (staged form) inside the timed steps"}
     stage_s = el / (args.steps * U1_STAGES)
     bytes_stage = N ** 3 * U1_BYTES_PER_SITE_STAGE
     achieved = bytes_stage / stage_s / 1e9
@@ -366,10 +399,7 @@ def run_u1_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_
                                     2: "one RK stage: k_u1s_plaquettes + k_u1s_stage (staged neighbourhoods)"}.get(
                                         variant, "one RK stage: k_u1_plaquettes + k_u1_stage"), "tile_dz": u1_dz,
                          "algorithmic_bytes_per_launch": bytes_stage},
-            "gpu_launches": launches, "clocks": clocks,
-            "energies_end": {"a": e["a"], "rho": e["rho"], "KE": e["KE"], "GB": e["GB"],
-                             "gauss_violation": e["gauss_violation"], "hubble_violation": e["hubble_violation"],
-                             "gauss_rms_last_step": e["gauss_rms_step"], "gauss_rms_max_over_steps": e["gauss_rms_max"]},
+            "gpu_launches": launches, "clocks": clocks, "energies_end": energies_end,
             "gauss_tracking": "rms lattice Gauss charge of every step's starting state, summed in the first RK "
                               "stage (staged form) inside the timed steps"}
 
@@ -850,6 +880,7 @@ def run_gpu(args, world, rank, local):
         return
     if args.workload != "preheat":
         fn = {"u1": run_u1_workload, "rk": run_rk_workload, "gw": run_gw_workload,
+              "u1lf": lambda *a: run_u1_workload(*a, leapfrog=True),
               "nmc": run_nmc_workload, "reduced": run_reduced_workload}.get(args.workload, run_ensemble_workload)
         line = fn(args, world, rank, local, cl, torch, stream, hbm_peak, peak_src)
         if rank == 0:
@@ -950,7 +981,8 @@ def main():
     ap.add_argument("--dz", type=int, default=None, help="override CL_OPT_TILE_DZ")
     ap.add_argument("--variant", type=int, default=None,
                     help="override CL_OPT_PASS_VARIANT (scalar pass: 0 ring, 1 ringless; U(1): 0 gather, 1 fused, 2 staged)")
-    ap.add_argument("--workload", default="preheat", choices=["preheat", "u1", "ensemble", "surrogate", "rk", "gw", "nmc", "reduced"],
+    ap.add_argument("--workload", default="preheat", choices=["preheat", "u1", "u1lf", "ensemble", "surrogate", "rk", "gw", "nmc",
+                                                              "reduced"],
                     help="preheat: the headline 256^3 two-field run; u1, ensemble: the other workloads")
     ap.add_argument("--members", type=int, default=None, help="ensemble size (default 1024)")
     ap.add_argument("--no-train", action="store_true", help="surrogate workload: throughput only")

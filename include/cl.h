@@ -167,7 +167,8 @@ typedef struct {
     double ricci;             /* background Ricci scalar R (Eq. eomR) of a non-minimally coupled
                                  lattice (cl_set_nonminimal); 0 otherwise                  */
     double gauss_rms_step;    /* U(1), tracked every step: rms Gauss violation of the latest
-                                 cl_step step's starting state,
+                                 cl_step step's starting state (Runge-Kutta) or integer-time
+                                 end state (leapfrog),
                                  dx sqrt(sum_n G(n)^2) / (a^(1-alpha) sqrt(sum_n E(n)^2))   */
     double gauss_rms_max;     /* U(1): the largest gauss_rms_step since the last
                                  cl_set_scalars or cl_init_vacuum                         */
@@ -260,8 +261,23 @@ cl_status cl_gauge_spectrum(cl_lattice* l, int32_t which, double dn, int32_t typ
  * Ebar the two-link average and Bbar the clover average of sin(plaquette)/dx^2; the equations
  * are the Euler-Lagrange equations of the lattice action, so the lattice Gauss law is a
  * conserved charge of the continuous-time flow.  Gauge lattices integrate with
- * CL_INT_RK3_3 / CL_INT_RK4_5 (as the paper does for this module), one axion field,
- * CL_PREC_FP64 or CL_PREC_FP32.  Errors: CL_EINVAL (no gauge field, bad values). */
+ * CL_INT_RK3_3 / CL_INT_RK4_5 / CL_INT_RK3_4 (as the paper does for this module) or with
+ * CL_INT_VV2, a leapfrog with the kick of (pi, E) implicit at fixed positions, since the
+ * E' of Eq. AxionInfEOM depends on phi' and the pi' on E: positions (phi, theta, a) at
+ * integer steps, momenta (pi, E, a') at half steps in between, and
+ *   p_(n+1/2) = p_n + h/2 f(q_n, a_n, a'_(n+1/2), p_(n+1/2))   (implicit half-kick)
+ *   q_(n+1)   = q_n + h (drift with p_(n+1/2), a at the midpoint)
+ *   p_(n+1)   = p_(n+1/2) + h/2 f(q_(n+1), a_(n+1), a'_(n+1/2), p_(n+1/2))   (explicit)
+ * with a' half-kicked by Eq. Friedmann1 at the integer times (the generalized
+ * Stoermer-Verlet method: order 2, time-reversible when converged).  The implicit half-kick
+ * is solved by three evaluations of f: the first from the previous step's closing force (in
+ * the first step of a cl_step call from a written state, the force at that state), two
+ * fixed-point iterations after it.  Between calls the leapfrog stays open: the integer-time
+ * momenta are kept beside the staggered ones, so reading fields, energies or spectra does
+ * not change the trajectory; writing the state or the scalars closes it.  One step is three
+ * passes of two launches each plus the Gauss reduction (the rms Gauss violation of every
+ * step's integer-time end state is tracked in cl_energy::gauss_rms_step / _max).  One axion
+ * field, CL_PREC_FP64 or CL_PREC_FP32.  Errors: CL_EINVAL (no gauge field, bad values). */
 cl_status cl_set_gauge_coupling(cl_lattice* l, double alphaL, double ws2);
 
 /* Non-minimal coupling xi phi^2 R of the scalar field (section "Scalar fields non-minimally
@@ -333,8 +349,9 @@ cl_status cl_set_hubble_limit(cl_lattice* l, double limit);
  * memory, then the stage) unless 1: 0 = every neighbour gathered from L1/L2, 2 = the
  * neighbourhoods of each plane staged in shared memory by asynchronous copies (the library's
  * choice where N is a multiple of 32, else 0), 1 = one fused launch per stage with the
- * plaquette fields in shared memory (N a multiple of 32).  All three agree to rounding.
- * Errors: CL_EINVAL. */
+ * plaquette fields in shared memory (N a multiple of 32; Runge-Kutta only, CL_EUNSUPPORTED
+ * with the leapfrog).  All three agree to rounding.
+ * Errors: CL_EINVAL, CL_EUNSUPPORTED. */
 enum { CL_OPT_GRAPH = 0, CL_OPT_TILE_BY = 1, CL_OPT_TILE_DZ = 2, CL_OPT_STAGES = 3, CL_OPT_PASS_VARIANT = 4 };
 cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value);
 

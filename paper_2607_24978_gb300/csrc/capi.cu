@@ -35,6 +35,9 @@ struct PassCoef {
     int flags;
     int rk = 0;       // 1: a 2N Runge-Kutta stage with coefficients A, B instead
     double A = 0.0, B = 0.0;
+    int lf = 0;       // 1..3: a pass of the axion-U(1) leapfrog (U1Args::lf) with le, lk, lb
+    double le = 0.0, lk = 0.0, lb = 0.0;
+    bool flip = true;  // the pass leaves the state in the other buffer
 };
 
 bool is_rk(int integrator)
@@ -77,6 +80,7 @@ struct cl_lattice {
     bool use_graph = true;
     int opt_BY = 0, opt_DZ = 0, opt_stages = 0, opt_variant = -1;  // -1: library choice
     int u1_dz = 8;                  // planes per block of the U(1) kernels
+    int u1_gdz = 8;                 // planes per block of the gather kernels beside staged ones
     bool u1_fused = false;          // U(1) stage as one fused launch (plaquettes in shared memory)
     bool u1_staged = false;         // U(1) launches with shared-memory staged neighbourhoods
     int dims = 3;                   // spatial dimensions (1, 2: reduced lattice of N^dims sites)
@@ -131,6 +135,8 @@ cl_status fail(cl_lattice* l, cl_status s, const char* fmt, ...)
 bool is_fp64(const cl_lattice* l) { return l->p.precision == CL_PREC_FP64; }
 bool has_kahan(const cl_lattice* l) { return l->p.precision == CL_PREC_FP32_KAHAN; }
 bool is_ens(const cl_lattice* l) { return l->members > 1; }
+// axion-U(1) lattice integrated with the leapfrog (the only leapfrog a gauge lattice accepts)
+bool is_u1_lf(const cl_lattice* l) { return l->gauge && !is_rk(l->p.integrator); }
 int mem_N(const cl_lattice* l, int m) { return is_ens(l) ? l->mN[m] : l->N; }
 int64_t mem_V(const cl_lattice* l, int m)
 {
@@ -484,7 +490,7 @@ cl_status choose_tiles(cl_lattice* l)
         const int tiles = ((N + 31) / 32) * ((N + 7) / 8);
         // the fused stage only on request: measured slower than the two launches at 192^3
         // (3.96 against 5.12 Gsite-updates/s; both latency-bound)
-        l->u1_fused = l->opt_variant == 1 && u1_fused_ok(N);
+        l->u1_fused = l->opt_variant == 1 && u1_fused_ok(N) && !is_u1_lf(l);
         // the staged launches (neighbourhoods in shared memory) are the library's choice
         // where the tiles divide N
         l->u1_staged = (l->opt_variant == -1 || l->opt_variant == 2) && u1_staged_ok(N);
@@ -498,7 +504,11 @@ cl_status choose_tiles(cl_lattice* l)
         if (nbz > N) nbz = N;
         const int auto_dz = l->u1_staged ? u1_staged_dz(prec, N, nsm) : (int)((N + nbz - 1) / nbz);
         l->u1_dz = l->opt_DZ > 0 ? (l->opt_DZ > N ? N : l->opt_DZ) : auto_dz;
+        // the gather kernels that run beside the staged launches (the Gauss diagnostic and its
+        // plaquette fields) keep the gather form's one-wave chunks
+        l->u1_gdz = l->u1_staged ? (int)((N + nbz - 1) / nbz) : l->u1_dz;
         if (2 * u1_grid_blocks(N, l->u1_dz) > nblocks) nblocks = 2 * u1_grid_blocks(N, l->u1_dz);  // stage + plaquette partials
+        if (2 * u1_grid_blocks(N, l->u1_gdz) > nblocks) nblocks = 2 * u1_grid_blocks(N, l->u1_gdz);
         if (l->u1_staged && 2 * u1_staged_blocks(prec, N, l->u1_dz) > nblocks)
             nblocks = 2 * u1_staged_blocks(prec, N, l->u1_dz);
     }
@@ -625,6 +635,7 @@ cl_status run_rk_stage_t(cl_lattice* l, const PassCoef& pc, int in, int out)
 }
 
 cl_status run_u1(cl_lattice* l, int what, double cA, double cB, int flags, int in, int out);
+cl_status run_u1_lf(cl_lattice* l, const PassCoef& pc, int s);
 
 // The GW pass of a leapfrog pass with coefficients pc, buffers in -> out.
 template <typename T>
@@ -718,6 +729,7 @@ cl_status run_pass(cl_lattice* l, const PassCoef& pc, int in, int out)
         cl_status s = is_fp64(l) ? run_gw_pass_t<double>(l, pc, in, out) : run_gw_pass_t<float>(l, pc, in, out);
         if (s != CL_OK) return s;
     }
+    if (pc.lf) return run_u1_lf(l, pc, in);                              // axion + U(1) leapfrog pass
     if (pc.rk == 2) return run_u1(l, 1, pc.A, pc.B, pc.flags, in, out);  // axion + U(1) stage
     if (pc.rk) return is_fp64(l) ? run_rk_stage_t<double>(l, pc, in, out) : run_rk_stage_t<float>(l, pc, in, out);
     return run_pass_impl(l, pc, in, out, nullptr);
@@ -789,6 +801,17 @@ std::vector<PassCoef> step_schedule(const cl_lattice* l)
 {
     const double h = l->p.dt;
     std::vector<PassCoef> s;
+    if (is_u1_lf(l)) {
+        // axion-U(1) leapfrog: the second and third evaluations of the implicit kick (the
+        // third with the drift), then the closing half-kick of the step merged with the first
+        // evaluation of the next step's kick
+        PassCoef b{0.0, 0.0, 0.0, 0}, c{0.0, 0.0, 0.0, P_COUNT_STEP}, a{0.0, 0.0, 0.0, 0};
+        b.lf = 2; b.lk = 0.5 * h; b.flip = false;
+        c.lf = 3; c.lk = 0.5 * h;
+        a.lf = 1; a.le = 0.5 * h; a.lk = h; a.lb = h; a.flip = false;
+        s = {b, c, a};
+        return s;
+    }
     if (is_rk(l->p.integrator)) {
         std::vector<double> A, B;
         rk_tables(l->p.integrator, A, B);
@@ -827,6 +850,15 @@ double open_kick(const cl_lattice* l)
 cl_status open_leapfrog(cl_lattice* l)
 {
     if (l->open) return CL_OK;
+    if (is_u1_lf(l)) {  // integer-time momenta kept, the first evaluation of the implicit kick
+        PassCoef o{0.0, 0.0, 0.0, 0};
+        o.lf = 1; o.le = 0.0; o.lk = 0.5 * l->p.dt; o.lb = 0.5 * l->p.dt;
+        cl_status s = run_u1_lf(l, o, l->cur);
+        if (s != CL_OK) return s;
+        l->open = true;
+        l->diag_valid = true;
+        return CL_OK;
+    }
     const double hk = open_kick(l);
     cl_status s = run_pass(l, {0.0, 0.0, hk, P_COMMIT}, l->cur, l->cur ^ 1);
     if (s != CL_OK) return s;
@@ -840,6 +872,20 @@ cl_status open_leapfrog(cl_lattice* l)
 cl_status close_leapfrog(cl_lattice* l, bool commit)
 {
     if (!l->open) return CL_OK;
+    if (is_u1_lf(l)) {
+        // the open state keeps the integer-time momenta (ku1 slots 1, 5..7) and a' of the
+        // integer time in the diagnostics: committing copies them into the state
+        if (!commit) return CL_OK;
+        const size_t bytes = (size_t)l->V * l->es;
+        CUDA_TRY(l, cudaMemcpyAsync(l->pi[0][l->cur], l->ku1[1][l->cur], bytes, cudaMemcpyDeviceToDevice, l->stream));
+        for (int i = 0; i < 3; ++i)
+            CUDA_TRY(l, cudaMemcpyAsync(l->ef[i][l->cur], l->ku1[5 + i][l->cur], bytes, cudaMemcpyDeviceToDevice,
+                                        l->stream));
+        CUDA_TRY(l, cudaMemcpyAsync(&l->scal->b, &l->scal->diag[D_ADOT], sizeof(double), cudaMemcpyDeviceToDevice,
+                                    l->stream));
+        l->open = false;
+        return CL_OK;
+    }
     const double hk = open_kick(l);
     cl_status s = run_pass(l, {0.0, -hk, -hk, commit ? P_COMMIT : 0}, l->cur, l->cur ^ 1);
     if (s != CL_OK) return s;
@@ -890,7 +936,7 @@ cudaError_t gauge_fields_t(cl_lattice* l, int which, double* out)
     GaugeSpecArgs<T> A{};
     for (int i = 0; i < 3; ++i) {
         A.th[i] = (const T*)l->th[i][l->cur];
-        A.E[i] = (const T*)l->ef[i][l->cur];
+        A.E[i] = (const T*)(is_u1_lf(l) && l->open ? l->ku1[5 + i][l->cur] : l->ef[i][l->cur]);
     }
     A.N = l->N;
     A.dx = l->dx;
@@ -904,6 +950,10 @@ cl_status run_u1_t(cl_lattice* l, int what, double cA, double cB, int flags, int
 {
     U1Args<T> A{};
     u1_fill(l, A, in, out);
+    if (is_u1_lf(l) && l->open) {  // the integer-time momenta of the open leapfrog
+        A.pi_in = (const T*)l->ku1[1][in];
+        for (int i = 0; i < 3; ++i) A.E_in[i] = (const T*)l->ku1[5 + i][in];
+    }
     A.A = cA;
     A.B = cB;
     A.flags = flags | (l->p.expansion ? P_EXPANSION : 0);
@@ -923,6 +973,7 @@ cl_status run_u1_t(cl_lattice* l, int what, double cA, double cB, int flags, int
         e = launch_u1_staged(l->p.precision, &A, 0, l->stream);  // plaquette fields first
         if (e == cudaSuccess) e = launch_u1_staged(l->p.precision, &A, 1, l->stream);
     } else {
+        if (l->u1_staged) A.dz = l->u1_gdz;  // gather kernels beside the staged launches
         e = launch_u1(l->p.precision, &A, 0, l->stream);  // plaquette fields first
         if (e == cudaSuccess && track) e = launch_u1(l->p.precision, &A, 3, l->stream);
         if (e == cudaSuccess) e = launch_u1(l->p.precision, &A, what, l->stream);
@@ -937,6 +988,56 @@ cl_status run_u1(cl_lattice* l, int what, double cA, double cB, int flags, int i
                       : run_u1_t<float>(l, what, cA, cB, flags, in, out);
 }
 
+// One pass of the axion-U(1) leapfrog (U1Args::lf) on the state whose positions are in buffer s:
+//   lf 1: the force at the momenta of s; integer-time momenta into ku1[.][s] (slots 1, 5..7),
+//         the first iterate of the implicit kick into the momenta of s^1
+//   lf 2: the force at the iterate in the momenta of s^1, base ku1[.][s] -> momenta of s; and
+//         the rms Gauss violation of the integer-time state (positions of s, momenta ku1[.][s])
+//   lf 3: the force at the iterate in the momenta of s, base ku1[.][s] -> momenta of s^1, and
+//         the positions drifted with them into s^1
+template <typename T>
+cl_status run_u1_lf_t(cl_lattice* l, const PassCoef& pc, int s)
+{
+    U1Args<T> A{};
+    u1_fill(l, A, s, s ^ 1);
+    const int pin = pc.lf == 2 ? (s ^ 1) : s;
+    const int pout = pc.lf == 2 ? s : (s ^ 1);
+    A.pi_in = (const T*)l->pi[0][pin];
+    A.pi_out = (T*)l->pi[0][pout];
+    for (int i = 0; i < 3; ++i) {
+        A.E_in[i] = (const T*)l->ef[i][pin];
+        A.E_out[i] = (T*)l->ef[i][pout];
+    }
+    for (int q = 0; q < 8; ++q) {
+        A.k_in[q] = (const T*)l->ku1[q][s];
+        A.k_out[q] = (T*)l->ku1[q][s];
+    }
+    A.lf = pc.lf;
+    A.le = pc.le;
+    A.lk = pc.lk;
+    A.lb = pc.lb;
+    A.flags = pc.flags | (l->p.expansion ? P_EXPANSION : 0);
+    const int prec = l->p.precision;
+    cudaError_t e = l->u1_staged ? launch_u1_staged(prec, &A, 0, l->stream) : launch_u1(prec, &A, 0, l->stream);
+    if (e == cudaSuccess && pc.lf == 2 && !l->u1_staged) {
+        // Gauss tracking of the step's integer-time starting state (positions of s, the
+        // plaquette fields just computed from them, momenta ku1[.][s]); the staged second
+        // pass sums it itself
+        U1Args<T> G = A;
+        G.pi_in = (const T*)l->ku1[1][s];
+        for (int i = 0; i < 3; ++i) G.E_in[i] = (const T*)l->ku1[5 + i][s];
+        e = launch_u1(prec, &G, 3, l->stream);
+    }
+    if (e == cudaSuccess) e = l->u1_staged ? launch_u1_staged(prec, &A, 1, l->stream) : launch_u1(prec, &A, 1, l->stream);
+    if (e != cudaSuccess) return fail(l, CL_ECUDA, "U(1) leapfrog launch failed: %s", cudaGetErrorString(e));
+    return CL_OK;
+}
+
+cl_status run_u1_lf(cl_lattice* l, const PassCoef& pc, int s)
+{
+    return is_fp64(l) ? run_u1_lf_t<double>(l, pc, s) : run_u1_lf_t<float>(l, pc, s);
+}
+
 // Energies of members [m0, m1) of an ensemble only (a' from Eq. Friedmann2 with P_HUBBLE_INIT).
 cl_status energy_pass_members(cl_lattice* l, int flags, int m0, int m1)
 {
@@ -945,6 +1046,10 @@ cl_status energy_pass_members(cl_lattice* l, int flags, int m0, int m1)
 
 cl_status energy_pass(cl_lattice* l, int extra_flags)
 {
+    if (is_u1_lf(l) && l->open) {  // the energy launch reads a closed state
+        cl_status c = close_leapfrog(l, true);
+        if (c != CL_OK) return c;
+    }
     cl_status s = l->gauge ? run_u1(l, 1, 0.0, 0.0, P_ENERGY_ONLY | (extra_flags & P_HUBBLE_INIT), l->cur, l->cur ^ 1)
                            : run_pass(l, {0.0, 0.0, 0.0, extra_flags}, l->cur, l->cur ^ 1);
     if (s != CL_OK) return s;
@@ -1113,7 +1218,9 @@ cl_status cl_init_lattice(cl_lattice** out, const cl_lattice_params* p)
         // the paper integrates the axion-gauge module with Runge-Kutta; one axion field;
         // fields stored in FP64 or plain FP32
         if (p->nfields != 1) return CL_EINVAL;
-        if (!is_rk(p->integrator) || p->precision == CL_PREC_FP32_KAHAN) return CL_EUNSUPPORTED;
+        // the Runge-Kutta schemes, or the leapfrog with an implicit momentum kick (order 2)
+        if ((!is_rk(p->integrator) && p->integrator != CL_INT_VV2) || p->precision == CL_PREC_FP32_KAHAN)
+            return CL_EUNSUPPORTED;
     }
     cl_lattice* l = new (std::nothrow) cl_lattice();
     if (!l) return CL_ENOMEM;
@@ -1298,13 +1405,18 @@ cl_status cl_get_state(cl_lattice* l, int32_t member, int32_t field, void* dst, 
     const int kind = field_kind(l, field, &f);
     if (kind < 0) return fail(l, CL_EINVAL, "field %d not present", field);
     int buf = l->cur;
-    if (l->open && (kind == 1 || kind == 5)) {
+    const void* fb = nullptr;
+    if (l->open && is_u1_lf(l)) {  // the open axion-U(1) leapfrog keeps the integer-time momenta
+        if (kind == 1) fb = l->ku1[1][l->cur];
+        else if (kind == 3) fb = l->ku1[5 + f][l->cur];
+    } else if (l->open && (kind == 1 || kind == 5)) {
         cl_status s = close_leapfrog(l, false);  // integer-time momenta into the spare buffer
         if (s != CL_OK) return s;
         buf = l->cur ^ 1;
     }
+    if (!fb) fb = field_buffer(l, kind, f, buf);
     const size_t bytes = (size_t)mem_V(l, member) * l->es;
-    const void* srcp = (const char*)field_buffer(l, kind, f, buf) + mem_off_bytes(l, member);
+    const void* srcp = (const char*)fb + mem_off_bytes(l, member);
     CUDA_TRY(l, cudaMemcpyAsync(dst, srcp, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                 l->stream));
     std::vector<DevScal> h;
@@ -1343,7 +1455,7 @@ cl_status cl_get_scalars(cl_lattice* l, int32_t member, double* a, double* adot,
 {
     if (!l) return CL_EINVAL;
     if (!member_ok(l, member)) return fail(l, CL_EINVAL, "member %d out of range", member);
-    if (l->open) {
+    if (l->open && !is_u1_lf(l)) {
         cl_status s = close_leapfrog(l, false);
         if (s != CL_OK) return s;
     } else if (!l->diag_valid) {
@@ -1554,6 +1666,8 @@ cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value)
     case CL_OPT_PASS_VARIANT:
         if (value < -1 || value > (l->gauge ? 2 : 1))
             return fail(l, CL_EINVAL, "pass variant must be -1, 0 or 1 (2 on an axion-U(1) lattice)");
+        if (value == 1 && is_u1_lf(l))
+            return fail(l, CL_EUNSUPPORTED, "the axion-U(1) leapfrog has no fused pass form");
         l->opt_variant = (int)value;
         return choose_tiles(l);
     case CL_OPT_STAGES:
@@ -1712,10 +1826,12 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
     if (!l->open && !rk) {
         cl_status s = open_leapfrog(l);
         if (s != CL_OK) return s;
-        l->last_launches += l->gw ? 2 : 1;
+        l->last_launches += is_u1_lf(l) ? 2 : (l->gw ? 2 : 1);
     }
     const std::vector<PassCoef> sched = step_schedule(l);
     const int pps = (int)sched.size();
+    int flips = 0;  // buffer swaps of one step
+    for (const auto& pc : sched) flips += pc.flip ? 1 : 0;
     const bool nmc_f = nmc_fused(l);
     if (nmc_f && !l->rbar_valid) {  // the fused stages carry the Ricci scalar from stage to stage
         cl_status s = is_fp64(l) ? nmc_ricci_t<double>(l) : nmc_ricci_t<float>(l);
@@ -1736,7 +1852,7 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
                 for (const auto& pc : sched) {
                     s = run_pass(l, pc, c, c ^ 1);
                     if (s != CL_OK) break;
-                    c ^= 1;
+                    if (pc.flip) c ^= 1;
                 }
                 cudaError_t ee = cudaStreamEndCapture(l->stream, &g);
                 if (s != CL_OK) return s;
@@ -1746,19 +1862,20 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
                 if (ee != cudaSuccess) return fail(l, CL_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ee));
             }
             CUDA_TRY(l, cudaGraphLaunch(l->graph[par], l->stream));
-            l->cur = (pps & 1) ? par ^ 1 : par;
+            l->cur = (flips & 1) ? par ^ 1 : par;
         } else {
             for (const auto& pc : sched) {
                 cl_status s = run_pass(l, pc, l->cur, l->cur ^ 1);
                 if (s != CL_OK) return s;
-                l->cur ^= 1;
+                if (pc.flip) l->cur ^= 1;
             }
         }
         // two-launch gauge stages (helper + stage), non-minimally coupled stages (Ricci + stage)
         // and leapfrog passes with gravitational waves (GW pass + scalar pass)
         l->last_launches += (l->gauge && !l->u1_fused) || (l->nmc && !nmc_f) || l->gw ? 2 * pps : pps;
         // per-step Gauss tracking launches of the U(1) forms whose stage does not sum it itself
-        if (l->gauge && !l->u1_staged) l->last_launches += l->u1_fused ? 2 : 1;
+        if (is_u1_lf(l)) l->last_launches += l->u1_staged ? 0 : 1;
+        else if (l->gauge && !l->u1_staged) l->last_launches += l->u1_fused ? 2 : 1;
     }
     // a leapfrog step ends with the energies of its integer time; a Runge-Kutta stage
     // reports those of the state it started from, so they are recomputed on demand
@@ -1923,12 +2040,16 @@ cl_status cl_spectrum(cl_lattice* l, int32_t member, int32_t field, double dn, i
     if (nbins) *nbins = nb;
     if (cap == 0) return CL_OK;
     int buf = l->cur;
-    if (l->open && kind == 1) {
+    const void* fb = kind == 0 ? l->phi[f][buf] : l->pi[f][buf];
+    if (l->open && kind == 1 && is_u1_lf(l)) {
+        fb = l->ku1[1][l->cur];  // the open axion-U(1) leapfrog keeps the integer-time momenta
+    } else if (l->open && kind == 1) {
         cl_status s = close_leapfrog(l, false);
         if (s != CL_OK) return s;
         buf = l->cur ^ 1;
+        fb = l->pi[f][buf];
     }
-    const void* src = (const char*)(kind == 0 ? l->phi[f][buf] : l->pi[f][buf]) + mem_off_bytes(l, member);
+    const void* src = (const char*)fb + mem_off_bytes(l, member);
     const size_t nh = (size_t)N * N * (N / 2 + 1);
     double* real = nullptr;
     double2* F = nullptr;

@@ -198,6 +198,16 @@ struct U1Args {
     double hubble_limit;
     int flags;    // P_EXPANSION, P_FIRST_STAGE, P_COUNT_STEP, P_ENERGY_ONLY, P_HUBBLE_INIT
     int dz;       // planes per block (all three kernels)
+    // Leapfrog passes (lf != 0; the stage launch only, the plaquette launch is unchanged).
+    // The force f = (pi', E') is evaluated at positions (phi, theta, a) with the momenta of
+    // pi_in / E_in and a' = scal->b; p~ denotes those momenta, base those of k_in[1], k_in[5..7].
+    //   lf 1: k_out[1], k_out[5..7] = p~ + le f (the integer-time momenta, whose energies are
+    //         reduced), pi_out / E_out = p~ + lk f; a' += lb a''(rho), diag a' = a' + le a''
+    //   lf 2: pi_out / E_out = base + lk f
+    //   lf 3: as 2, then phi_out = phi + h ((a + a_1)/2)^(alpha-3) pi_out, theta_out = theta
+    //         + h dx E_out with a_1 = a + h a'; a = a_1, t += h, step += 1
+    int lf;
+    double le, lk, lb;
 };
 // what: 0 = plaquette fields, 1 = stage (or energies with P_ENERGY_ONLY), 2 = Gauss diagnostic,
 // 3 = rms Gauss violation of the state into DevScal::gauss (the staged stage launch computes

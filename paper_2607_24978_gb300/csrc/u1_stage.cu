@@ -155,7 +155,7 @@ __device__ __forceinline__ T clover(const T* const f, const Nbhd& s, const Off& 
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_u1_stage(const U1Args<T> A)
 {
-    __shared__ double s_coef[6];
+    __shared__ double s_coef[7];
     __shared__ double s_red[32][kMaxQ];
     __shared__ int s_last;
     const uint32_t N = (uint32_t)A.N, V = N * N * N;
@@ -171,9 +171,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_u1_stage(const 
         s_coef[3] = apow(a, A.alpha - 1.0);                     // E' prefactor
         s_coef[4] = (1.0 - A.alpha) * b / a;                   // electric friction
         s_coef[5] = a;
+        s_coef[6] = A.lf == 3 ? u1_lf_drift(a, b, A.h, A.alpha) : 0.0;  // leapfrog drift of phi
     }
     __syncthreads();
     const T c_dphi = (T)s_coef[0], cL = (T)s_coef[1], cV = (T)s_coef[2], cE = (T)s_coef[3], cfr = (T)s_coef[4];
+    const int lf = A.lf;
+    const T le = (T)A.le, lk = (T)A.lk, cdrift = (T)s_coef[6], hdx = (T)(A.h * A.dx);
     const T g = (T)A.g, ws2 = (T)A.ws2, dx = (T)A.dx, m2 = (T)A.m2, lam = (T)A.lam;
     const T inv_dx3 = (T)(1.0 / (A.dx * A.dx * A.dx)), inv4dx = (T)(0.25 / A.dx), inv4dx2 = (T)(0.25 / (A.dx * A.dx));
     const T h = (T)A.h, cA = (T)A.A, cB = (T)A.B;
@@ -202,10 +205,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_u1_stage(const 
         }
         const T F_phi = c_dphi * pv;
         const T F_pi = cL * lap - cV * dV + ws2 * g * eb;
-        accK.add(pv * pv);
+        if (lf == 0) {  // (leapfrog pass 1 sums the kinetic energies of its output momenta)
+            accK.add(pv * pv);
+            accKE.add(e2);
+        }
         accG.add((pxp - ph) * (pxp - ph) + (pyp - ph) * (pyp - ph) + (pzp - ph) * (pzp - ph));
         accV.add(ph * ph * ((T)0.5 * m2 + (T)0.25 * lam * ph * ph));
-        accKE.add(e2);
         if (!update) continue;
 
         // link forces
@@ -226,6 +231,43 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_u1_stage(const 
             const T Bdni = inv4dx2 * clover(A.rP[i], s, oi, i);
             const T wdot = (T)0.5 * (F_phi * Bn[i] + ph * Bdn + c_dphi * A.pi_in[ni] * Bni + A.phi_in[ni] * Bdni);
             F_E[i] = cE * (-cE * mag * inv_dx3 + g * (cs * inv4dx - wdot)) - cfr * Ecur[i];
+        }
+        if (lf == 1) {  // leapfrog: closing half-kick (integer-time momenta) and the first iterate
+            const T pn = pv + le * F_pi;
+            const T po = pv + lk * F_pi;
+            T En[3], Eo[3], en2 = (T)0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                En[i] = Ecur[i] + le * F_E[i];
+                Eo[i] = Ecur[i] + lk * F_E[i];
+                en2 += En[i] * En[i];
+            }
+            accK.add(pn * pn);
+            accKE.add(en2);
+            A.k_out[1][n] = pn;
+            A.pi_out[n] = po;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                A.k_out[5 + i][n] = En[i];
+                A.E_out[i][n] = Eo[i];
+            }
+            continue;
+        }
+        if (lf != 0) {  // leapfrog: an iterate of the implicit kick from the base momenta
+            const T po = A.k_in[1][n] + lk * F_pi;
+            T Eo[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) Eo[i] = A.k_in[5 + i][n] + lk * F_E[i];
+            if (lf == 3) {
+                const T th[3] = {A.th_in[0][n], A.th_in[1][n], A.th_in[2][n]};
+                A.phi_out[n] = ph + cdrift * po;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) A.th_out[i][n] = th[i] + hdx * Eo[i];
+            }
+            A.pi_out[n] = po;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) A.E_out[i][n] = Eo[i];
+            continue;
         }
         // 2N Runge-Kutta update of the eight degrees of freedom of this site (all loads
         // first, then the stores)
@@ -262,7 +304,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_u1_stage(const 
         w[kMaxQ - 1] += __ldcg(&A.partials[(size_t)gridDim.x * kMaxQ + b]);  // plaquette launch, same grid
     }
     block_reduce<kMaxQ>(w, s_red, tid, nthr);
-    if (tid == 0) u1_epilogue(A, w, s_coef[5], first, update, expand, V);
+    if (tid == 0) {
+        if (lf) u1_lf_epilogue(A, w, s_coef[5], expand, V);
+        else u1_epilogue(A, w, s_coef[5], first, update, expand, V);
+    }
 }
 
 // Lattice Gauss charge G(n) = sum_i [P_i(n) - P_i(n - i)] / dx, P = a^(1-alpha) E + g W.

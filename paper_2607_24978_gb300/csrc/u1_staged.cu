@@ -312,7 +312,8 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquettes(const U1Ar
 // TRACK: the first stage of a step, which also sums the squared lattice Gauss charge of its
 // input state (the state at the step's start), so that the Gauss constraint is tracked each
 // step; a separate instance keeps that work, and its registers, out of the other stages.
-template <typename T, bool TRACK>
+// LF: the passes of the leapfrog (U1Args::lf) instead of a Runge-Kutta stage.
+template <typename T, bool TRACK, bool LF>
 __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T> A)
 {
     using G = U1SGeom<T>;
@@ -320,11 +321,12 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
     extern __shared__ __align__(128) unsigned char u1s_dyn[];
     __shared__ const T* s_src[NA];
     __shared__ __align__(8) uint64_t s_full[G::SLOTS], s_empty[G::SLOTS];
-    __shared__ double s_coef[7];
+    __shared__ double s_coef[8];
     __shared__ double s_red[32][kMaxQ];
     __shared__ int s_last, s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool first = (A.flags & P_FIRST_STAGE) != 0;
+    const bool first = !LF && (A.flags & P_FIRST_STAGE) != 0;
+    const int lf = LF ? A.lf : 0;
     const bool update = (A.flags & P_ENERGY_ONLY) == 0;
     constexpr bool track = TRACK;
     const bool expand = (A.flags & P_EXPANSION) != 0;
@@ -337,6 +339,7 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
         s_coef[4] = (1.0 - A.alpha) * b / a;               // electric friction
         s_coef[5] = a;
         s_coef[6] = apow(a, 1.0 - A.alpha);                 // a^(1-alpha) E in the Gauss charge
+        s_coef[7] = LF && A.lf == 3 ? u1_lf_drift(a, b, A.h, A.alpha) : 0.0;  // leapfrog drift of phi
         s_src[SG_PHI] = A.phi_in;
         s_src[SG_PI] = A.pi_in;
 #pragma unroll
@@ -371,13 +374,27 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
         const T inv_dx3 = (T)(1.0 / (A.dx * A.dx * A.dx)), inv4dx = (T)(0.25 / A.dx);
         const T inv4dx2 = (T)(0.25 / (A.dx * A.dx));
         const T h = (T)A.h, cA = (T)A.A, cB = (T)A.B;
-        // site-only arrays (theta, the RK auxiliaries), loaded one plane ahead
+        const T le = (T)A.le, lk = (T)A.lk, cdrift = (T)s_coef[7], hdx = (T)(A.h * A.dx);
+        // site-only arrays (theta, the RK auxiliaries or the leapfrog's base momenta), loaded
+        // one plane ahead
         T thc[3] = {}, kc[8] = {};
         auto load_site = [&](uint32_t m) {
+            if constexpr (LF) {
+                if (lf == 3) {
 #pragma unroll
-            for (int i = 0; i < 3; ++i) thc[i] = A.th_in[i][m];
+                    for (int i = 0; i < 3; ++i) thc[i] = A.th_in[i][m];
+                }
+                if (lf >= 2) {
+                    kc[1] = A.k_in[1][m];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) kc[q] = first ? (T)0 : A.k_in[q][m];
+                    for (int i = 0; i < 3; ++i) kc[5 + i] = A.k_in[5 + i][m];
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) thc[i] = A.th_in[i][m];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) kc[q] = first ? (T)0 : A.k_in[q][m];
+            }
         };
         if (update) load_site((t.z0 * N + t.y0 + warp) * N + t.x0 + lane);
         ring.acquire(0);
@@ -411,20 +428,45 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
             }
             const T F_phi = c_dphi * pv;
             const T F_pi = cL * lap - cV * dV + ws2 * g * eb;
-            accK.add(pv * pv);
-            accG.add((pxp - ph) * (pxp - ph) + (pyp - ph) * (pyp - ph) + (pzp - ph) * (pzp - ph));
-            accV.add(ph * ph * ((T)0.5 * m2 + (T)0.25 * lam * ph * ph));
-            accKE.add(e2);
+            if (!LF) {  // (leapfrog pass 1 sums the kinetic energies of its output momenta)
+                accK.add(pv * pv);
+                accKE.add(e2);
+            }
+            if (!LF || lf == 1) {
+                accG.add((pxp - ph) * (pxp - ph) + (pyp - ph) * (pyp - ph) + (pzp - ph) * (pzp - ph));
+                accV.add(ph * ph * ((T)0.5 * m2 + (T)0.25 * lam * ph * ph));
+            }
             if (update) {
                 if constexpr (TRACK) {
                     // dx times the lattice Gauss charge sum_i [P_i(n) - P_i(n - i)] of the input
-                    // state, P_i = a^(1-alpha) E_i + g W_i (the phi B terms at n cancel)
+                    // state, P_i = a^(1-alpha) E_i + g W_i (the phi B terms at n cancel).  The
+                    // leapfrog's second pass tracks the integer-time state of the step's start:
+                    // its positions are staged, its electric field is the base (site and the
+                    // three lower neighbours, loaded here)
+                    T ec[3], em[3];
+                    if constexpr (LF) {
+                        const uint32_t x = t.x0 + lane, y = t.y0 + warp, z = t.z0 + j;
+                        const uint32_t nm[3] = {x == 0 ? n + N - 1 : n - 1, y == 0 ? n + (N - 1) * N : n - N,
+                                                z == 0 ? n + (N - 1) * N * N : n - N * N};
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            ec[i] = kv[5 + i];
+                            em[i] = A.k_in[5 + i][nm[i]];
+                        }
+                        accKE.add(ec[0] * ec[0] + ec[1] * ec[1] + ec[2] * ec[2]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            ec[i] = Ecur[i];
+                            em[i] = S(SG_E + i, U1S_E(i, -1));
+                        }
+                    }
                     T gd = (T)0;
 #pragma unroll
                     for (int i = 0; i < 3; ++i) {
                         const T Bpi = inv4dx2 * S.clover(SG_SP + i, i, U1S_E(i, 1));
                         const T Bmi = inv4dx2 * S.clover(SG_SP + i, i, U1S_E(i, -1));
-                        gd += ca * (Ecur[i] - S(SG_E + i, U1S_E(i, -1))) +
+                        gd += ca * (ec[i] - em[i]) +
                               (T)0.5 * g * (S(SG_PHI, U1S_E(i, 1)) * Bpi - S(SG_PHI, U1S_E(i, -1)) * Bmi);
                     }
                     accGs.add(gd * gd);
@@ -446,6 +488,41 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
                     F_E[i] = cE * (-cE * mag * inv_dx3 + g * (cs * inv4dx - wdot)) - cfr * Ecur[i];
                 }
                 ring.release(j, lane);
+                if constexpr (LF) {
+                    if (lf == 1) {  // closing half-kick (integer-time momenta) and the first iterate
+                        T En[3], Eo[3], en2 = (T)0;
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            En[i] = Ecur[i] + le * F_E[i];
+                            Eo[i] = Ecur[i] + lk * F_E[i];
+                            en2 += En[i] * En[i];
+                        }
+                        const T pn = pv + le * F_pi;
+                        accK.add(pn * pn);
+                        accKE.add(en2);
+                        A.k_out[1][n] = pn;
+                        A.pi_out[n] = pv + lk * F_pi;
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            A.k_out[5 + i][n] = En[i];
+                            A.E_out[i][n] = Eo[i];
+                        }
+                    } else {  // an iterate of the implicit kick from the base momenta
+                        const T po = kv[1] + lk * F_pi;
+                        T Eo[3];
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) Eo[i] = kv[5 + i] + lk * F_E[i];
+                        if (lf == 3) {
+                            A.phi_out[n] = ph + cdrift * po;
+#pragma unroll
+                            for (int i = 0; i < 3; ++i) A.th_out[i][n] = thv[i] + hdx * Eo[i];
+                        }
+                        A.pi_out[n] = po;
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) A.E_out[i][n] = Eo[i];
+                    }
+                    continue;
+                }
                 // 2N Runge-Kutta update of the eight degrees of freedom of this site
                 const T F[8] = {F_phi, F_pi, dx * Ecur[0], dx * Ecur[1], dx * Ecur[2], F_E[0], F_E[1], F_E[2]};
                 const T y[8] = {ph, pv, thv[0], thv[1], thv[2], Ecur[0], Ecur[1], Ecur[2]};
@@ -495,7 +572,8 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
     double wg[1] = {ws[kMaxQ - 1]};
     if (tid == 0) {
         if (track) u1_gauss_track(A.scal, wg[0], w[3], s_coef[6]);
-        u1_epilogue(A, w, s_coef[5], first, update, expand, V);
+        if (LF) u1_lf_epilogue(A, w, s_coef[5], expand, V);
+        else u1_epilogue(A, w, s_coef[5], first, update, expand, V);
     }
 }
 
@@ -536,7 +614,7 @@ static cudaError_t launch_u1s_t(const U1Args<T>& A, int what, cudaStream_t s)
     using G = U1SGeom<T>;
     if (!u1_staged_ok(A.N) || A.dz < 1 || A.dz > A.N) return cudaErrorInvalidValue;
     const int grid = u1_staged_blocks(sizeof(T) == 8 ? CL_PREC_FP64 : CL_PREC_FP32, A.N, A.dz);
-    static DevFlag attr[3];
+    static DevFlag attr[5];
     if (what == 0) {
         constexpr size_t smem = u1s_smem_bytes<T, PQ_NA>();
         if (!attr[0]) {
@@ -548,17 +626,23 @@ static cudaError_t launch_u1s_t(const U1Args<T>& A, int what, cudaStream_t s)
         k_u1s_plaquettes<T><<<grid, G::NT, smem, s>>>(A);
     } else {
         constexpr size_t smem = u1s_smem_bytes<T, SG_NA>();
-        const bool track = (A.flags & P_FIRST_STAGE) && !(A.flags & P_ENERGY_ONLY);
-        if (!attr[track ? 2 : 1]) {
-            const cudaError_t e = track ? cudaFuncSetAttribute(k_u1s_stage<T, true>,
-                                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                                        : cudaFuncSetAttribute(k_u1s_stage<T, false>,
-                                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // forms: 1 a Runge-Kutta stage, 2 the first stage of a step (Gauss tracking), 3 a
+        // leapfrog pass, 4 the leapfrog's second pass (Gauss tracking)
+        const int form = A.lf ? (A.lf == 2 ? 4 : 3) : ((A.flags & P_FIRST_STAGE) && !(A.flags & P_ENERGY_ONLY) ? 2 : 1);
+        if (!attr[form]) {
+            const int sm = (int)smem;
+            const cudaError_t e =
+                form == 4   ? cudaFuncSetAttribute(k_u1s_stage<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)
+                : form == 3 ? cudaFuncSetAttribute(k_u1s_stage<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)
+                : form == 2 ? cudaFuncSetAttribute(k_u1s_stage<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)
+                            : cudaFuncSetAttribute(k_u1s_stage<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             if (e != cudaSuccess) return e;
-            attr[track ? 2 : 1] = true;
+            attr[form] = true;
         }
-        if (track) k_u1s_stage<T, true><<<grid, G::NT, smem, s>>>(A);
-        else k_u1s_stage<T, false><<<grid, G::NT, smem, s>>>(A);
+        if (form == 4) k_u1s_stage<T, true, true><<<grid, G::NT, smem, s>>>(A);
+        else if (form == 3) k_u1s_stage<T, false, true><<<grid, G::NT, smem, s>>>(A);
+        else if (form == 2) k_u1s_stage<T, true, false><<<grid, G::NT, smem, s>>>(A);
+        else k_u1s_stage<T, false, false><<<grid, G::NT, smem, s>>>(A);
     }
     return cudaGetLastError();
 }

@@ -343,8 +343,8 @@ def test_u1_hubble_init_includes_em_energy(cl):
 
 
 def test_u1_invalid_configurations(cl):
-    with pytest.raises(cl.CLError):
-        cl.Lattice(8, 6.0, 1, cl.CL_PREC_FP64, cl.CL_INT_VV2, gauge=cl.CL_GAUGE_U1_AXION)
+    with pytest.raises(cl.CLError):  # the leapfrog of a gauge lattice is order 2 only
+        cl.Lattice(8, 6.0, 1, cl.CL_PREC_FP64, cl.CL_INT_YOSHIDA4, gauge=cl.CL_GAUGE_U1_AXION)
     with pytest.raises(cl.CLError):
         cl.Lattice(8, 6.0, 2, cl.CL_PREC_FP64, cl.CL_INT_RK3_3, gauge=cl.CL_GAUGE_U1_AXION)
     with pytest.raises(cl.CLError):
