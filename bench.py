@@ -461,6 +461,12 @@ def run_reduced_workload(args, world, rank, local, cl, torch, stream, hbm_peak, 
     g = cl.Lattice(N2, L2, 2, cl.CL_PREC_FP32_KAHAN, cl.CL_INT_YOSHIDA4, expansion=True, alpha=ALPHA, kappa=KAPPA,
                    dt=DT, stream=stream.cuda_stream, dims=2)
     g.cl_set_potential(cl.CL_POT_M2_G2, [1.0, G2])
+    if args.dz is not None:  # rows per chunk of the row-marching pass (tuning runs)
+        g.cl_set_option(cl.CL_OPT_TILE_DZ, args.dz)
+    if args.by is not None:  # rows ahead of its L2 prefetch (tuning runs)
+        g.cl_set_option(cl.CL_OPT_TILE_BY, args.by)
+    if args.variant is not None:  # 1: row marching (default), 0: one thread per site
+        g.cl_set_option(cl.CL_OPT_PASS_VARIANT, args.variant)
     rng = np.random.default_rng(SEED)
     for f, (field, mom) in enumerate(((cl.CL_FIELD_PHI0, cl.CL_FIELD_PI0), (cl.CL_FIELD_PHI1, cl.CL_FIELD_PI1))):
         g.cl_set_state(field, ((1.0 if f == 0 else 0.0) + 1e-4 * rng.standard_normal((1, N2, N2))).astype(np.float32))
@@ -473,6 +479,7 @@ def run_reduced_workload(args, world, rank, local, cl, torch, stream, hbm_peak, 
     barrier(world)
     el_max = max_over_ranks(el, world)
     e = g.cl_energies()
+    variant, rows = g.cl_get_option(cl.CL_OPT_PASS_VARIANT), g.cl_get_option(cl.CL_OPT_TILE_DZ)
     g.close()
     sites = N2 * N2
     pass_s = el / (args.steps * PASSES_PER_STEP)
@@ -490,7 +497,8 @@ def run_reduced_workload(args, world, rank, local, cl, torch, stream, hbm_peak, 
                               "l2": "inputs (%.0f MB) larger than L2; no flush" % (sites * 24 / 1e6)}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
-                         "kernel": "k_reduced_pass<float,2,kahan> (mean per pass)",
+                         "kernel": ("k_plane_pass<float,2,kahan,4> (row marching, %d rows a chunk; mean per pass)" % rows
+                                    if variant == 1 else "k_reduced_pass<float,2,kahan> (mean per pass)"),
                          "algorithmic_bytes_per_launch": bytes_pass},
             "gpu_launches": launches, "clocks": clocks,
             "energies_end": {"a": e["a"], "rho": e["rho"], "hubble_violation": e["hubble_violation"]}}

@@ -350,7 +350,12 @@ cl_status cl_set_hubble_limit(cl_lattice* l, double limit);
  * neighbourhoods of each plane staged in shared memory by asynchronous copies (the library's
  * choice where N is a multiple of 32, else 0), 1 = one fused launch per stage with the
  * plaquette fields in shared memory (N a multiple of 32; Runge-Kutta only, CL_EUNSUPPORTED
- * with the leapfrog).  All three agree to rounding.
+ * with the leapfrog).  All three agree to rounding.  On a (2+1)-dimensional lattice the
+ * leapfrog pass is 1 = row marching (the library's choice where N is a multiple of 128 in
+ * FP32, 64 in FP64: each warp owns a strip of columns and a chunk of rows and keeps three
+ * drifted rows in registers; CL_OPT_TILE_DZ its rows per chunk, CL_OPT_TILE_BY how many rows
+ * ahead it prefetches into L2, 0 = library choice) or 0 = one thread per site; both agree to
+ * rounding.
  * Errors: CL_EINVAL, CL_EUNSUPPORTED. */
 enum { CL_OPT_GRAPH = 0, CL_OPT_TILE_BY = 1, CL_OPT_TILE_DZ = 2, CL_OPT_STAGES = 3, CL_OPT_PASS_VARIANT = 4 };
 cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value);

@@ -85,6 +85,8 @@ struct cl_lattice {
     bool u1_staged = false;         // U(1) launches with shared-memory staged neighbourhoods
     int dims = 3;                   // spatial dimensions (1, 2: reduced lattice of N^dims sites)
     int red_grid = 1;               // blocks of the reduced-lattice kernels
+    int red_dy = 0, red_pgrid = 0;  // (2+1) row-marching pass: rows per chunk and blocks (0: not used)
+    int red_pd = 0;                 //   and the rows ahead of its L2 prefetch (0: none)
     bool nmc = false;               // non-minimal coupling xi phi^2 R of field 0 (Runge-Kutta)
     bool rbar_valid = false;        // scal->rbar holds the Ricci scalar of the current state
     double xi = 0.0;
@@ -305,8 +307,35 @@ cl_status choose_tiles(cl_lattice* l)
         const int64_t blocks = (l->V + 255) / 256;
         l->red_grid = (int)(blocks < 8 * (int64_t)nsm ? blocks : 8 * (int64_t)nsm);
         l->VW = 1;
+        // (2+1) leapfrog passes: the row-marching kernel where the strips divide N (the library's
+        // choice, pass variant 1), else one thread per site (variant 0).  By default one wave of
+        // warps (three 256-thread blocks per SM, its launch bounds): enough chunks of rows that
+        // strips x chunks fills it, at least 8 rows a chunk (the two halo rows of a chunk are
+        // loaded twice; measured at 4096^2: 36 rows, one wave, 0.70 of HBM; 18 rows, two waves,
+        // 0.65; 24 rows, 1.5 waves, 0.55); CL_OPT_TILE_DZ > 0 sets the rows per chunk
+        l->red_dy = 0;
+        l->red_pgrid = 0;
+        l->variant = 0;
+        if (l->dims == 2 && l->opt_variant != 0 && plane_pass_ok(l->p.precision, l->N)) {
+            const int64_t N = l->N, strips = N / (l->p.precision == CL_PREC_FP64 ? 64 : 128);
+            const int64_t target = 24 * (int64_t)nsm;
+            int64_t chunks = (target + strips - 1) / strips;
+            if (chunks > N) chunks = N;
+            int64_t dy = (N + chunks - 1) / chunks;
+            if (dy < 8) dy = N < 8 ? N : 8;
+            if (l->opt_DZ > 0) dy = l->opt_DZ > N ? N : l->opt_DZ;
+            // the next row but one prefetched into L2 while the next is loaded (measured at
+            // 4096^2 FP32 + Kahan, two fields: 0.70 of HBM without, 0.77 one row ahead, 0.61-0.68
+            // two to eight rows ahead); CL_OPT_TILE_BY > 0 sets the distance
+            l->red_pd = l->opt_BY > 0 ? l->opt_BY : 1;
+            chunks = (N + dy - 1) / dy;
+            l->red_dy = (int)dy;
+            l->red_pgrid = (int)((strips * chunks + 7) / 8);
+            l->variant = 1;
+        }
+        const int pblocks = l->red_pgrid > l->red_grid ? l->red_pgrid : l->red_grid;
         // adaptive RK3-4: a second set of partials for the error estimate
-        cl_status s = grow_partials(l, l->red_grid * (l->p.integrator == CL_INT_RK3_4 ? 2 : 1));
+        cl_status s = grow_partials(l, pblocks * (l->p.integrator == CL_INT_RK3_4 ? 2 : 1));
         if (s != CL_OK) return s;
         invalidate_graphs(l);
         return CL_OK;
@@ -544,7 +573,9 @@ cl_status run_pass_impl(cl_lattice* l, const PassCoef& pc, int in, int out, int*
         A.stages = l->stages;
         A.grid = l->grid;
         A.variant = l->variant;
-        e = l->dims < 3 ? (occ ? (*occ = 1, cudaSuccess) : launch_reduced_pass(l->p.precision, l->nf, &A, l->dims, l->red_grid, l->stream))
+        e = l->dims < 3 ? (occ ? (*occ = 1, cudaSuccess)
+                           : l->red_dy > 0 ? launch_plane_pass(l->p.precision, l->nf, &A, l->red_dy, l->red_pd, l->red_pgrid, l->stream)
+                                           : launch_reduced_pass(l->p.precision, l->nf, &A, l->dims, l->red_grid, l->stream))
             : occ ? scalar_pass_blocks_per_sm(l->p.precision, l->nf, &A, l->VW, occ)
                   : launch_scalar_pass(l->p.precision, l->nf, &A, l->VW, l->stream);
     } else {
@@ -569,7 +600,9 @@ cl_status run_pass_impl(cl_lattice* l, const PassCoef& pc, int in, int out, int*
         A.stages = l->stages;
         A.grid = l->grid;
         A.variant = l->variant;
-        e = l->dims < 3 ? (occ ? (*occ = 1, cudaSuccess) : launch_reduced_pass(l->p.precision, l->nf, &A, l->dims, l->red_grid, l->stream))
+        e = l->dims < 3 ? (occ ? (*occ = 1, cudaSuccess)
+                           : l->red_dy > 0 ? launch_plane_pass(l->p.precision, l->nf, &A, l->red_dy, l->red_pd, l->red_pgrid, l->stream)
+                                           : launch_reduced_pass(l->p.precision, l->nf, &A, l->dims, l->red_grid, l->stream))
             : occ ? scalar_pass_blocks_per_sm(l->p.precision, l->nf, &A, l->VW, occ)
                   : launch_scalar_pass(l->p.precision, l->nf, &A, l->VW, l->stream);
     }
@@ -1640,7 +1673,8 @@ cl_status cl_get_option(cl_lattice* l, int32_t option, int64_t* value)
     case CL_OPT_GRAPH: *value = l->use_graph ? 1 : 0; return CL_OK;
     case CL_OPT_TILE_BY: *value = ens ? l->hmem[0].BY : (is_rk(l->p.integrator) && !l->gauge ? l->rk_BY : l->BY); return CL_OK;
     case CL_OPT_TILE_DZ:
-        *value = ens ? l->hmem[0].DZ : (l->gauge ? l->u1_dz : (is_rk(l->p.integrator) ? l->rk_DZ : l->DZ));
+        *value = ens ? l->hmem[0].DZ
+                     : (l->gauge ? l->u1_dz : (l->dims < 3 ? l->red_dy : (is_rk(l->p.integrator) ? l->rk_DZ : l->DZ)));
         return CL_OK;
     case CL_OPT_STAGES:
         *value = ens ? l->ens_stages : (is_rk(l->p.integrator) && !l->gauge ? (l->rk_stages > 0 ? l->rk_stages : -1) : l->stages);

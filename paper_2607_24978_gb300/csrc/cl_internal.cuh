@@ -111,6 +111,12 @@ cudaError_t launch_scalar_pass(int precision, int nf, const void* args, int vw, 
 // The same pass on a reduced lattice of N^dims sites (dims = 1, 2), `grid` blocks of 256
 // threads (partials[grid][kMaxQ]).
 cudaError_t launch_reduced_pass(int precision, int nf, const void* args, int dims, int grid, cudaStream_t s);
+// (2+1)-dimensional pass with row marching (scalar_pass.cu): N a multiple of 32 x (16 bytes /
+// element size) (plane_pass_ok); dy rows per chunk; pd > 0 prefetches the row pd ahead into L2;
+// grid = ceil((N / (32 VW)) x ceil(N / dy) / 8) blocks of 256 threads (one warp per strip and
+// chunk).  Same results as launch_reduced_pass.
+bool plane_pass_ok(int precision, int N);
+cudaError_t launch_plane_pass(int precision, int nf, const void* args, int dy, int pd, int grid, cudaStream_t s);
 // Resident blocks per SM of the pass configured by args (tiles, stages).
 cudaError_t scalar_pass_blocks_per_sm(int precision, int nf, const void* args, int vw, int* blocks);
 int scalar_pass_vector_width(int precision, int N);

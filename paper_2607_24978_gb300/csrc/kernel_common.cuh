@@ -80,6 +80,12 @@ __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 
+// Fetch the 128-byte line holding p into L2 (no register result; a hint).
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // phi += cd * pi, with Kahan compensation c when KAHAN.
 template <typename T, bool KAHAN>
 __device__ __forceinline__ void drift(T& phi, T& c, T pi, T cd)

@@ -228,6 +228,175 @@ __global__ void __launch_bounds__(256) k_reduced_pass(const ScalarPassArgs<T> A,
     finish_pass_vol<T, NF>(A, accK, accG, accV, s_coef, s_red, &s_last, tid, nthr, 0, (double)V);
 }
 
+// The (2+1)-dimensional pass with row marching (N a multiple of 32 VW): warp w owns a strip of
+// 32 VW columns (lane l the VW columns from 32 VW s + VW l, loaded as one 16-byte vector) and
+// a chunk of rows [y0, y0 + dy), and marches up its rows keeping the drifted rows y - 1, y,
+// y + 1 of every field in registers.  Each input row is loaded and drifted once per strip
+// (the two halo rows of a chunk twice, by the neighbouring chunks), with the same compensated
+// operations as k_reduced_pass, and its own rows' drifted fields are stored at once; the
+// momenta of a row are read again for its kick one row later (L1 hits); the x neighbours of a lane's vector come from its own
+// registers, from the neighbouring lanes (shuffles) and, at the strip's ends, from one column
+// that the first and the last lane load and drift.  Lattice sums, stores and the epilogue as in
+// k_reduced_pass.  Units (strip, chunk) beyond the grid's warps are left to no one: the grid
+// is ceil(strips x chunks / 8) blocks of 8 warps.
+template <typename T, int NF, bool KAHAN, int VW>
+__global__ void __launch_bounds__(256, 3) k_plane_pass(const ScalarPassArgs<T> A, int dy, int pd)
+{
+    __shared__ double s_coef[4];
+    __shared__ double s_red[32][kMaxQ];
+    __shared__ int s_last;
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+    if (tid == 0) pass_coefficients(A.scal->a, A.scal->b, A.d, A.alpha, A.dx, (A.flags & P_EXPANSION) != 0, s_coef);
+    __syncthreads();
+    const T cd = (T)s_coef[0], cL = (T)s_coef[1], cV = (T)s_coef[2], ce = (T)A.e, ck = (T)A.k;
+    const bool do_drift = (A.flags & P_DRIFT) != 0;
+    const PotCoef<T> P(A.m2, A.lam, A.g2);
+    const int N = A.N, SW = 32 * VW, nstrips = N / SW, nchunks = (N + dy - 1) / dy;
+    const int unit = blockIdx.x * (nthr >> 5) + (tid >> 5);
+    Acc<T> accK[NF], accG[NF], accV;
+    if (unit < nstrips * nchunks) {  // warp-uniform
+        const int strip = unit % nstrips, chunk = unit / nstrips;
+        const int xs = strip * SW, x0 = xs + lane * VW;
+        const int xe = lane == 0 ? (xs == 0 ? N - 1 : xs - 1) : (xs + SW == N ? 0 : xs + SW);  // edge column
+        const bool edge_lane = lane == 0 || lane == 31;
+        const int y0 = chunk * dy, y1 = min(y0 + dy, N);
+        // row y of field f, drifted: the lane's vector (stored at once, with its compensation,
+        // when the row is one of the chunk's own) and, on the edge lanes, the edge column
+        auto load_row = [&](int f, int y, bool own, T (&ph)[VW], T& pe) {
+            const size_t row = (size_t)y * N;
+            const T* ph_in = f == 0 ? A.phi_in[0] : A.phi_in[NF - 1];
+            const T* pi_in = f == 0 ? A.pi_in[0] : A.pi_in[NF - 1];
+            const T* c_in = f == 0 ? A.c_in[0] : A.c_in[NF - 1];
+            T pv[VW], cv[VW];
+            vload<T, VW>(ph, ph_in + row + x0);
+            vload<T, VW>(pv, pi_in + row + x0);
+            if (KAHAN) vload<T, VW>(cv, c_in + row + x0);
+            else {
+#pragma unroll
+                for (int i = 0; i < VW; ++i) cv[i] = (T)0;
+            }
+            T eph = (T)0, epv = (T)0, ecv = (T)0;
+            if (edge_lane) {
+                eph = ph_in[row + xe];
+                epv = pi_in[row + xe];
+                ecv = KAHAN ? c_in[row + xe] : (T)0;
+            }
+            if (do_drift) {
+#pragma unroll
+                for (int i = 0; i < VW; ++i) drift<T, KAHAN>(ph[i], cv[i], pv[i], cd);
+                drift<T, KAHAN>(eph, ecv, epv, cd);
+            }
+            pe = eph;
+            if (own) {
+                vstore<T, VW>((f == 0 ? A.phi_out[0] : A.phi_out[NF - 1]) + row + x0, ph);
+                if (KAHAN) vstore<T, VW>((f == 0 ? A.c_out[0] : A.c_out[NF - 1]) + row + x0, cv);
+            }
+        };
+        T prv[NF][VW], cur[NF][VW], cedge[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            T e;
+            load_row(f, y0 == 0 ? N - 1 : y0 - 1, false, prv[f], e);
+            load_row(f, y0, true, cur[f], cedge[f]);
+        }
+        for (int y = y0; y < y1; ++y) {
+            const int yn = y + 1 == N ? 0 : y + 1;
+            if (pd > 0 && (lane & 7) == 0 && y + 1 + pd <= y1) {
+                // the row pd ahead into L2 (one 128-byte line a lane of eight), so that its
+                // loads wait on L2 rather than DRAM
+                int yq = y + 1 + pd;
+                yq = yq >= N ? yq - N : yq;
+                const size_t off = (size_t)yq * N + x0;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    prefetch_l2((f == 0 ? A.phi_in[0] : A.phi_in[NF - 1]) + off);
+                    prefetch_l2((f == 0 ? A.pi_in[0] : A.pi_in[NF - 1]) + off);
+                    if (KAHAN) prefetch_l2((f == 0 ? A.c_in[0] : A.c_in[NF - 1]) + off);
+                }
+            }
+            T nxt[NF][VW], nedge[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) load_row(f, yn, y + 1 < y1, nxt[f], nedge[f]);
+            T lap[NF][VW];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                // x neighbours of the lane's first and last columns
+                const T left_l = __shfl_up_sync(0xffffffffu, cur[f][VW - 1], 1);
+                const T right_l = __shfl_down_sync(0xffffffffu, cur[f][0], 1);
+                const T left = lane == 0 ? cedge[f] : left_l;
+                const T right = lane == 31 ? cedge[f] : right_l;
+#pragma unroll
+                for (int i = 0; i < VW; ++i) {
+                    const T c = cur[f][i];
+                    const T xm = i > 0 ? cur[f][i - 1] : left;
+                    const T xp = i + 1 < VW ? cur[f][i + 1] : right;
+                    const T yp = nxt[f][i], ym = prv[f][i];
+                    lap[f][i] = ((xp + xm) + (yp + ym)) - (T)4 * c;
+                    accG[f].add((xp - c) * (xp - c) + (yp - c) * (yp - c));
+                }
+            }
+            // the kick: pi of row y again (loaded with the row one step earlier, an L1 hit)
+            const size_t base = (size_t)y * N + x0;
+            T pin[NF][VW];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) vload<T, VW>(pin[f], (f == 0 ? A.pi_in[0] : A.pi_in[NF - 1]) + base);
+#pragma unroll
+            for (int i = 0; i < VW; ++i) {
+                const T p0 = cur[0][i], p1 = NF > 1 ? cur[NF - 1][i] : (T)0;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    T dV;
+                    if (f == 0) dV = p0 * (P.m20 + P.l0 * p0 * p0 + (NF > 1 ? P.g2 * p1 * p1 : (T)0));
+                    else dV = p1 * (P.m21 + P.l1 * p1 * p1 + P.g2 * p0 * p0);
+                    const T F = cL * lap[f][i] - cV * dV;
+                    const T pe = pin[f][i] + ce * F;
+                    accK[f].add(pe * pe);
+                    pin[f][i] = pin[f][i] + ck * F;
+                }
+                T v = p0 * p0 * (P.h_m20 + P.q_l0 * p0 * p0);
+                if (NF > 1) v += p1 * p1 * (P.h_m21 + P.q_l1 * p1 * p1) + P.h_g2 * p0 * p0 * p1 * p1;
+                accV.add(v);
+            }
+#pragma unroll
+            for (int f = 0; f < NF; ++f) vstore<T, VW>((f == 0 ? A.pi_out[0] : A.pi_out[NF - 1]) + base, pin[f]);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+#pragma unroll
+                for (int i = 0; i < VW; ++i) {
+                    prv[f][i] = cur[f][i];
+                    cur[f][i] = nxt[f][i];
+                }
+                cedge[f] = nedge[f];
+            }
+        }
+    }
+    finish_pass_vol<T, NF>(A, accK, accG, accV, s_coef, s_red, &s_last, tid, nthr, 0, (double)N * N);
+}
+
+template <typename T, int NF, bool KAHAN>
+static cudaError_t launch_plane_t(const ScalarPassArgs<T>& A, int dy, int pd, int grid, cudaStream_t s)
+{
+    constexpr int VW = 16 / (int)sizeof(T);
+    if (A.N % (32 * VW) != 0 || dy < 1 || pd < 0 || grid < 1) return cudaErrorInvalidValue;
+    k_plane_pass<T, NF, KAHAN, VW><<<grid, 256, 0, s>>>(A, dy, pd);
+    return cudaGetLastError();
+}
+
+bool plane_pass_ok(int precision, int N) { return N % (precision == CL_PREC_FP64 ? 64 : 128) == 0; }
+
+cudaError_t launch_plane_pass(int precision, int nf, const void* args, int dy, int pd, int grid, cudaStream_t s)
+{
+    if (precision == CL_PREC_FP64) {
+        const auto& A = *static_cast<const ScalarPassArgs<double>*>(args);
+        return nf == 1 ? launch_plane_t<double, 1, false>(A, dy, pd, grid, s)
+                       : launch_plane_t<double, 2, false>(A, dy, pd, grid, s);
+    }
+    const auto& A = *static_cast<const ScalarPassArgs<float>*>(args);
+    if (precision == CL_PREC_FP32_KAHAN)
+        return nf == 1 ? launch_plane_t<float, 1, true>(A, dy, pd, grid, s) : launch_plane_t<float, 2, true>(A, dy, pd, grid, s);
+    return nf == 1 ? launch_plane_t<float, 1, false>(A, dy, pd, grid, s) : launch_plane_t<float, 2, false>(A, dy, pd, grid, s);
+}
+
 template <typename T, int NF, bool KAHAN>
 static cudaError_t launch_reduced_t(const ScalarPassArgs<T>& A, int dims, int grid, cudaStream_t s)
 {

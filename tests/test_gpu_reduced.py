@@ -28,7 +28,7 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def run_pair(cl, dims, N, nf, prec, integ, scheme, nsteps, dt=0.01, seed=3, graph=1):
+def run_pair(cl, dims, N, nf, prec, integ, scheme, nsteps, dt=0.01, seed=3, graph=1, variant=None, oracle=True):
     L = 0.8 * N
     pot = [0.6, 1.0, 0.3, 0.5 if nf == 2 else 0.0, 2.5 if nf == 2 else 0.0]
     if nf == 1:
@@ -45,6 +45,8 @@ def run_pair(cl, dims, N, nf, prec, integ, scheme, nsteps, dt=0.01, seed=3, grap
     with cl.Lattice(N, L, nf, prec, integ, expansion=True, alpha=0.5, kappa=0.4, dt=dt, dims=dims) as g:
         g.cl_set_potential(cl.CL_POT_POLY, pot)
         g.cl_set_option(cl.CL_OPT_GRAPH, graph)
+        if variant is not None:
+            g.cl_set_option(cl.CL_OPT_PASS_VARIANT, variant)
         for f in range(nf):
             g.cl_set_state(cl.CL_FIELD_PHI0 + f, st.phi[f].astype(dtype))
             g.cl_set_state(cl.CL_FIELD_PI0 + f, st.pi[f].astype(dtype))
@@ -56,6 +58,8 @@ def run_pair(cl, dims, N, nf, prec, integ, scheme, nsteps, dt=0.01, seed=3, grap
         gphi = np.stack([g.cl_get_state(cl.CL_FIELD_PHI0 + f) for f in range(nf)])
         gpi = np.stack([g.cl_get_state(cl.CL_FIELD_PI0 + f) for f in range(nf)])
         e = g.cl_energies()
+    if not oracle:
+        return gphi, gpi, e0, None, e, None, None, launches
     O.step(m, st, scheme, dt, nsteps)
     return gphi, gpi, e0, eo0, e, st, O.energies(m, st), launches
 
@@ -110,3 +114,34 @@ def test_reduced_lattice_refusals(cl):
             g.cl_enable_gw()
         with pytest.raises(cl.CLError):
             g.cl_autotune()
+
+
+@pytest.mark.parametrize("N", [128, 256])
+@pytest.mark.parametrize("integ,scheme,passes", SCHEMES[:2])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-4)])
+@pytest.mark.parametrize("nf", [1, 2])
+def test_plane_pass_parity(cl, N, integ, scheme, passes, prec, tol, nf):
+    """The row-marching (2+1) pass (the library's choice where N is a multiple of 128 (FP32)
+    or 64 (FP64); N = 128 is one strip of columns in FP32) against the oracle."""
+    gphi, gpi, e0, eo0, e, st, eo, launches = run_pair(cl, 2, N, nf, prec, integ, scheme, 6)
+    assert rel_l2(gphi, st.phi) < tol
+    assert rel_l2(gpi, st.pi) < tol
+    assert e["a"] == pytest.approx(st.abt[0], rel=tol)
+    for k in ("rho", "p", "V", "G0", "K0"):
+        assert e[k] == pytest.approx(eo[k], rel=max(tol, 1e-9)), k
+    assert launches == 6 * passes + 1
+
+
+@pytest.mark.parametrize("N,prec,tol", [(4096, 2, 2e-6), (1024, 0, 1e-13), (640, 2, 2e-6)])
+def test_plane_pass_matches_the_site_kernel(cl, N, prec, tol):
+    """Row marching (variant 1, chunks of 18 rows at 4096^2: a ragged last chunk) against one
+    thread per site (variant 0) on the same state: the same compensated operations, so the
+    fields agree to rounding of the contracted multiply-adds."""
+    a = run_pair(cl, 2, N, 2, prec, cl.CL_INT_YOSHIDA4, O.YOSHIDA4, 2, variant=1, oracle=False)
+    b = run_pair(cl, 2, N, 2, prec, cl.CL_INT_YOSHIDA4, O.YOSHIDA4, 2, variant=0, oracle=False)
+    assert rel_l2(a[0], b[0]) < tol and rel_l2(a[1], b[1]) < tol
+    assert a[4]["rho"] == pytest.approx(b[4]["rho"], rel=1e-9)
+    with cl.Lattice(N, 0.8 * N, 2, prec, cl.CL_INT_YOSHIDA4, dims=2) as g:
+        assert g.cl_get_option(cl.CL_OPT_PASS_VARIANT) == 1
+        g.cl_set_option(cl.CL_OPT_PASS_VARIANT, 0)
+        assert g.cl_get_option(cl.CL_OPT_PASS_VARIANT) == 0
