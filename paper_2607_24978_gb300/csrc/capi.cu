@@ -83,6 +83,7 @@ struct cl_lattice {
     int u1_gdz = 8;                 // planes per block of the gather kernels beside staged ones
     bool u1_fused = false;          // U(1) stage as one fused launch (plaquettes in shared memory)
     bool u1_staged = false;         // U(1) launches with shared-memory staged neighbourhoods
+    bool u1_sfused = false;         //   as one launch, the plaquette fields in shared memory
     int dims = 3;                   // spatial dimensions (1, 2: reduced lattice of N^dims sites)
     int red_grid = 1;               // blocks of the reduced-lattice kernels
     int red_dy = 0, red_pgrid = 0;  // (2+1) row-marching pass: rows per chunk and blocks (0: not used)
@@ -522,7 +523,8 @@ cl_status choose_tiles(cl_lattice* l)
         l->u1_fused = l->opt_variant == 1 && u1_fused_ok(N) && !is_u1_lf(l);
         // the staged launches (neighbourhoods in shared memory) are the library's choice
         // where the tiles divide N
-        l->u1_staged = (l->opt_variant == -1 || l->opt_variant == 2) && u1_staged_ok(N);
+        l->u1_staged = (l->opt_variant == -1 || l->opt_variant == 2 || l->opt_variant == 3) && u1_staged_ok(N);
+        l->u1_sfused = l->u1_staged && l->opt_variant == 3;
         int bps = prec == CL_PREC_FP64 ? kU1BlocksPerSM64 : kU1BlocksPerSM32;
         if (l->u1_fused) {
             CUDA_TRY(l, u1_fused_blocks_per_sm(prec, &bps));
@@ -1002,6 +1004,8 @@ cl_status run_u1_t(cl_lattice* l, int what, double cA, double cB, int flags, int
             if (e == cudaSuccess) e = launch_u1(l->p.precision, &A, 3, l->stream);
         }
         if (e == cudaSuccess) e = launch_u1_fused(l->p.precision, &A, l->stream);  // plaquettes and stage in one launch
+    } else if (what == 1 && l->u1_sfused) {
+        e = launch_u1_staged(l->p.precision, &A, 2, l->stream);  // plaquette fields in shared memory
     } else if (what == 1 && l->u1_staged) {
         e = launch_u1_staged(l->p.precision, &A, 0, l->stream);  // plaquette fields first
         if (e == cudaSuccess) e = launch_u1_staged(l->p.precision, &A, 1, l->stream);
@@ -1051,6 +1055,11 @@ cl_status run_u1_lf_t(cl_lattice* l, const PassCoef& pc, int s)
     A.lb = pc.lb;
     A.flags = pc.flags | (l->p.expansion ? P_EXPANSION : 0);
     const int prec = l->p.precision;
+    if (l->u1_sfused) {  // one launch: plaquette fields in shared memory, Gauss summed in pass 2
+        const cudaError_t ef = launch_u1_staged(prec, &A, 2, l->stream);
+        if (ef != cudaSuccess) return fail(l, CL_ECUDA, "U(1) leapfrog launch failed: %s", cudaGetErrorString(ef));
+        return CL_OK;
+    }
     cudaError_t e = l->u1_staged ? launch_u1_staged(prec, &A, 0, l->stream) : launch_u1(prec, &A, 0, l->stream);
     if (e == cudaSuccess && pc.lf == 2 && !l->u1_staged) {
         // Gauss tracking of the step's integer-time starting state (positions of s, the
@@ -1679,7 +1688,9 @@ cl_status cl_get_option(cl_lattice* l, int32_t option, int64_t* value)
     case CL_OPT_STAGES:
         *value = ens ? l->ens_stages : (is_rk(l->p.integrator) && !l->gauge ? (l->rk_stages > 0 ? l->rk_stages : -1) : l->stages);
         return CL_OK;
-    case CL_OPT_PASS_VARIANT: *value = ens ? l->ens_variant : (l->gauge ? (l->u1_fused ? 1 : (l->u1_staged ? 2 : 0)) : l->variant); return CL_OK;
+    case CL_OPT_PASS_VARIANT:
+        *value = ens ? l->ens_variant : (l->gauge ? (l->u1_fused ? 1 : (l->u1_sfused ? 3 : (l->u1_staged ? 2 : 0))) : l->variant);
+        return CL_OK;
     }
     return fail(l, CL_EINVAL, "unknown option %d", option);
 }
@@ -1698,8 +1709,8 @@ cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value)
         l->opt_DZ = (int)value;
         return choose_tiles(l);
     case CL_OPT_PASS_VARIANT:
-        if (value < -1 || value > (l->gauge ? 2 : 1))
-            return fail(l, CL_EINVAL, "pass variant must be -1, 0 or 1 (2 on an axion-U(1) lattice)");
+        if (value < -1 || value > (l->gauge ? 3 : 1))
+            return fail(l, CL_EINVAL, "pass variant must be -1, 0 or 1 (2, 3 on an axion-U(1) lattice)");
         if (value == 1 && is_u1_lf(l))
             return fail(l, CL_EUNSUPPORTED, "the axion-U(1) leapfrog has no fused pass form");
         l->opt_variant = (int)value;
@@ -1860,7 +1871,7 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
     if (!l->open && !rk) {
         cl_status s = open_leapfrog(l);
         if (s != CL_OK) return s;
-        l->last_launches += is_u1_lf(l) ? 2 : (l->gw ? 2 : 1);
+        l->last_launches += is_u1_lf(l) ? (l->u1_sfused ? 1 : 2) : (l->gw ? 2 : 1);
     }
     const std::vector<PassCoef> sched = step_schedule(l);
     const int pps = (int)sched.size();
@@ -1906,7 +1917,7 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
         }
         // two-launch gauge stages (helper + stage), non-minimally coupled stages (Ricci + stage)
         // and leapfrog passes with gravitational waves (GW pass + scalar pass)
-        l->last_launches += (l->gauge && !l->u1_fused) || (l->nmc && !nmc_f) || l->gw ? 2 * pps : pps;
+        l->last_launches += (l->gauge && !l->u1_fused && !l->u1_sfused) || (l->nmc && !nmc_f) || l->gw ? 2 * pps : pps;
         // per-step Gauss tracking launches of the U(1) forms whose stage does not sum it itself
         if (is_u1_lf(l)) l->last_launches += l->u1_staged ? 0 : 1;
         else if (l->gauge && !l->u1_staged) l->last_launches += l->u1_fused ? 2 : 1;

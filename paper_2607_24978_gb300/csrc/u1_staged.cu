@@ -577,6 +577,399 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
     }
 }
 
+// ---------------------------------------------------------------- fused staged stage
+// One launch per stage (or leapfrog pass): the plaquette fields live in shared memory instead
+// of going through global memory.  The producer warps stage the eight raw arrays (phi, pi,
+// theta_1..3, E_1..3) plane by plane as above; the consumer warps, for output plane z, first
+// compute the plaquettes of normal x and y at plane z and of normal z at plane z + 1 over the
+// tile and the halo the stage reads (one consumer barrier per plane separates writers from
+// readers), then run the stage of plane z with every
+// plaquette field from shared memory and theta from the staged planes.  Ranges (relative to
+// the tile origin): normal x, columns -1..32, rows -1..TY-1; normal y, columns -1..31, rows
+// -1..TY; normal z, columns -1..31, rows -1..TY-1 (column -1 of normal x and row -1 of normal
+// y only for the Gauss charge, which needs the clover field at n - e_i; row -1 of normal y
+// has no Chern-Simons field, whose corner sum would reach row -2).  The magnetic energy of a
+// plaquette is counted by the block that owns its corner.  The plaquette planes rotate through
+// four slots: a warp that runs one plane ahead writes a slot that no warp still on the previous
+// plane reads (that plane's stage reads the slots of its planes z - 1 .. z + 1).
+template <typename T>
+struct U1FPq {
+    using G = U1SGeom<T>;
+    static constexpr int X = G::TX + 2;            // columns -1 .. TX
+    static constexpr int Y = G::TY + 2;            // rows -1 .. TY
+    static constexpr int PLANE = X * Y;            // one field of one orientation
+    static constexpr int SLOT = 9 * PLANE;         // three orientations x (sin P, cos P dP/dt, Z)
+    static constexpr int NSLOT = 4;
+};
+
+template <typename T>
+constexpr size_t u1f_smem_bytes()
+{
+    return u1s_smem_bytes<T, 8>() + (size_t)U1FPq<T>::NSLOT * U1FPq<T>::SLOT * sizeof(T);
+}
+
+enum { FR_PHI = 0, FR_PI = 1, FR_TH = 2, FR_E = 5, FR_NA = 8 };
+
+// Raw staged planes c - 1, c, c + 1 (chunk-relative plane indices) around the point at tile
+// offset (lx, ly) (lx in -VE .. TX + VE - 1, ly in -1 .. TY).
+template <typename T>
+__device__ __forceinline__ U1SNb<T> u1f_raw(const T* ring, int c, int lx, int ly)
+{
+    using G = U1SGeom<T>;
+    constexpr size_t SL = (size_t)FR_NA * G::ARR;
+    const int t0 = (ly + 1) * G::PW + lx + G::VE;
+    U1SNb<T> n;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) n.p[i] = ring + ((c - 1 + i + G::SLOTS) % G::SLOTS) * SL + t0;
+    return n;
+}
+
+// Plaquette fields around a site at tile offset (lx, ly) of the output plane whose
+// chunk-relative index is c (plaquette planes c - 1 .. c + 1 for the offsets oz = -1 .. 1).
+template <typename T>
+struct U1FQ {
+    const T* pq;
+    int c, lx, ly;
+    __device__ __forceinline__ T operator()(int k, int f, int ox, int oy, int oz) const
+    {
+        using P = U1FPq<T>;
+        return pq[((c + oz) % P::NSLOT) * P::SLOT + (k * 3 + f) * P::PLANE + (ly + oy + 1) * P::X + lx + ox + 1];
+    }
+    // clover sum of field f of normal k over the four plaquettes around offset o
+    __device__ __forceinline__ T clover(int f, int k, int ox, int oy, int oz) const
+    {
+        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        int b[3] = {ox, oy, oz}, d[3] = {ox, oy, oz}, e[3];
+        b[k1] -= 1;
+        d[k2] -= 1;
+        e[0] = b[0]; e[1] = b[1]; e[2] = b[2];
+        e[k2] -= 1;
+        return ((*this)(k, f, ox, oy, oz) + (*this)(k, f, b[0], b[1], b[2])) +
+               ((*this)(k, f, d[0], d[1], d[2]) + (*this)(k, f, e[0], e[1], e[2]));
+    }
+};
+
+// Plaquettes of normal K at plane c (chunk-relative), into slot c % 4; `count` adds the
+// magnetic energy of the corners this block owns; with_z: the Chern-Simons field too (normal
+// z needs raw plane c - 1 for it).  K is a template parameter so that every offset folds.
+template <typename T, int K>
+__device__ __forceinline__ void u1f_plaquettes(T* pq, const T* ring, int c, bool with_z, bool count, T dx, int ctid,
+                                               Acc<T>& accGB)
+{
+    using G = U1SGeom<T>;
+    using P = U1FPq<T>;
+    constexpr int NT = 32 * G::CW;
+    // corners: normal x columns -1..TX, rows -1..TY-1; normal y columns -1..TX-1, rows -1..TY;
+    // normal z columns -1..TX-1, rows -1..TY-1 (tile offsets; xo, yo count from -1)
+    constexpr int W = K == 0 ? G::TX + 2 : G::TX + 1;
+    constexpr int H = K == 1 ? G::TY + 2 : G::TY + 1;
+    constexpr int K1 = (K + 1) % 3, K2 = (K + 2) % 3;
+    constexpr int e1x = K1 == 0, e1y = K1 == 1, e1z = K1 == 2;
+    constexpr int e2x = K2 == 0, e2y = K2 == 1, e2z = K2 == 2;
+    constexpr int ekx = K == 0, eky = K == 1, ekz = K == 2;
+    T* slot = pq + (c % P::NSLOT) * P::SLOT + (K * 3) * P::PLANE;
+    for (int w = ctid; w < W * H; w += NT) {
+        const int xo = w % W, yo = w / W;
+        const U1SNb<T> S = u1f_raw<T>(ring, c, xo - 1, yo - 1);
+        const T Pl = S(FR_TH + K1, 0, 0, 0) + S(FR_TH + K2, e1x, e1y, e1z) - S(FR_TH + K1, e2x, e2y, e2z) -
+                     S(FR_TH + K2, 0, 0, 0);
+        const T R = dx * (S(FR_E + K1, 0, 0, 0) + S(FR_E + K2, e1x, e1y, e1z) - S(FR_E + K1, e2x, e2y, e2z) -
+                          S(FR_E + K2, 0, 0, 0));
+        T sh, ch;  // sin, cos of P / 2
+        if constexpr (sizeof(T) == 4) sincosf((T)0.5 * Pl, &sh, &ch);
+        else sincos((T)0.5 * Pl, &sh, &ch);
+        const T sp = (T)2 * sh * ch, cp = (T)1 - (T)2 * sh * sh;
+        // the corner sum of phi Ebar_k reaches one row / plane below the corner along k: not
+        // formed for row -1 of normal y (never read) nor when the plane below is not staged
+        T z = (T)0;
+        if ((K != 1 || yo > 0) && (K != 2 || with_z)) {
+            auto X = [&](int ox, int oy, int oz) {
+                return S(FR_PHI, ox, oy, oz) * (S(FR_E + K, ox, oy, oz) + S(FR_E + K, ox - ekx, oy - eky, oz - ekz));
+            };
+            const T qs = X(0, 0, 0) + X(e1x, e1y, e1z) + X(e2x, e2y, e2z) + X(e1x + e2x, e1y + e2y, e1z + e2z);
+            z = cp * ((T)0.5 * qs);
+        }
+        const int at = yo * P::X + xo;
+        slot[at] = sp;
+        slot[at + P::PLANE] = cp * R;
+        slot[at + 2 * P::PLANE] = z;
+        // owned corners: tile columns 0..TX-1, rows 0..TY-1
+        if (count && xo >= 1 && xo <= G::TX && yo >= 1 && yo <= G::TY) accGB.add((T)2 * sh * sh);
+    }
+}
+
+__device__ __forceinline__ void u1f_consumer_barrier(int nthreads)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+template <typename T, bool TRACK, bool LF>
+__global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1f_stage(const U1Args<T> A)
+{
+    using G = U1SGeom<T>;
+    constexpr int NA = FR_NA;
+    extern __shared__ __align__(128) unsigned char u1s_dyn[];
+    __shared__ const T* s_src[NA];
+    __shared__ __align__(8) uint64_t s_full[G::SLOTS], s_empty[G::SLOTS];
+    __shared__ double s_coef[8];
+    __shared__ double s_red[32][kMaxQ];
+    __shared__ int s_last, s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool first = !LF && (A.flags & P_FIRST_STAGE) != 0;
+    const int lf = LF ? A.lf : 0;
+    const bool update = (A.flags & P_ENERGY_ONLY) == 0;
+    constexpr bool track = TRACK;
+    const bool expand = (A.flags & P_EXPANSION) != 0;
+    if (tid == 0) {
+        const double a = A.scal->a, b = expand ? A.scal->b : 0.0;
+        s_coef[0] = apow(a, A.alpha - 3.0);                 // phi' = c0 pi
+        s_coef[1] = apow(a, 1.0 + A.alpha) / (A.dx * A.dx);  // Laplacian
+        s_coef[2] = apow(a, 3.0 + A.alpha);                 // potential
+        s_coef[3] = apow(a, A.alpha - 1.0);                 // E' prefactor
+        s_coef[4] = (1.0 - A.alpha) * b / a;               // electric friction
+        s_coef[5] = a;
+        s_coef[6] = apow(a, 1.0 - A.alpha);                 // a^(1-alpha) E in the Gauss charge
+        s_coef[7] = LF && A.lf == 3 ? u1_lf_drift(a, b, A.h, A.alpha) : 0.0;  // leapfrog drift of phi
+        s_src[FR_PHI] = A.phi_in;
+        s_src[FR_PI] = A.pi_in;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            s_src[FR_TH + k] = A.th_in[k];
+            s_src[FR_E + k] = A.E_in[k];
+        }
+        for (int k = 0; k < G::SLOTS; ++k) {
+            mbar_init(&s_full[k], G::PL);  // the producer lanes' copies
+            mbar_init(&s_empty[k], G::CW);
+        }
+        mbar_fence_init();
+        s_fail = 0;
+    }
+    __syncthreads();
+    const U1STile<T> t((uint32_t)A.N, (uint32_t)A.dz);
+    T* ring_sm = reinterpret_cast<T*>(u1s_dyn);
+    uint2* table = reinterpret_cast<uint2*>(ring_sm + G::SLOTS * NA * G::ARR);
+    T* pq = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(u1s_dyn) + u1s_smem_bytes<T, NA>());
+    u1s_build_units<T, NA>(table, t, tid, G::NT);
+    __syncthreads();
+    const U1SRing<T, NA> ring{ring_sm, table, s_full, s_empty, &s_fail};
+    const uint32_t N = t.N, V = N * N * N;
+    Acc<T> accK, accG, accV, accKE, accGs, accGB;
+    if (warp >= G::CW) {
+        ring.produce(tid - 32 * G::CW, s_src, t);
+    } else {
+        const T c_dphi = (T)s_coef[0], cL = (T)s_coef[1], cV = (T)s_coef[2], cE = (T)s_coef[3], cfr = (T)s_coef[4];
+        const T ca = (T)s_coef[6];
+        const T g = (T)A.g, ws2 = (T)A.ws2, dx = (T)A.dx, m2 = (T)A.m2, lam = (T)A.lam;
+        const T inv_dx3 = (T)(1.0 / (A.dx * A.dx * A.dx)), inv4dx = (T)(0.25 / A.dx);
+        const T inv4dx2 = (T)(0.25 / (A.dx * A.dx));
+        const T h = (T)A.h, cA = (T)A.A, cB = (T)A.B;
+        const T le = (T)A.le, lk = (T)A.lk, cdrift = (T)s_coef[7], hdx = (T)(A.h * A.dx);
+        const int nz = (int)t.nz;
+        // site-only arrays (the Runge-Kutta auxiliaries or the leapfrog's base momenta), loaded
+        // one plane ahead
+        T kc[8] = {};
+        auto load_site = [&](uint32_t m) {
+            if constexpr (LF) {
+                if (lf >= 2) {
+                    kc[1] = A.k_in[1][m];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) kc[5 + i] = A.k_in[5 + i][m];
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) kc[q] = first ? (T)0 : A.k_in[q][m];
+            }
+        };
+        if (update) load_site((t.z0 * N + t.y0 + warp) * N + t.x0 + lane);
+        // plaquette planes before the march: normal x and y at plane z0 - 1, normal z at z0
+        // (and, for the Gauss charge, its sin P at z0 - 1)
+        ring.acquire(0);
+        ring.acquire(1);
+        u1f_plaquettes<T, 0>(pq, ring_sm, 0, true, false, dx, tid, accGB);
+        u1f_plaquettes<T, 1>(pq, ring_sm, 0, true, false, dx, tid, accGB);
+        if (TRACK) u1f_plaquettes<T, 2>(pq, ring_sm, 0, false, false, dx, tid, accGB);
+        u1f_plaquettes<T, 2>(pq, ring_sm, 1, true, nz > 0, dx, tid, accGB);
+        for (int j = 0; j < nz; ++j) {
+            ring.acquire(j + 2);
+            // normal x, y at plane z0 + j (chunk-relative j + 1), normal z at plane z0 + j + 1
+            u1f_plaquettes<T, 0>(pq, ring_sm, j + 1, true, true, dx, tid, accGB);
+            u1f_plaquettes<T, 1>(pq, ring_sm, j + 1, true, true, dx, tid, accGB);
+            u1f_plaquettes<T, 2>(pq, ring_sm, j + 2, true, j + 1 < nz, dx, tid, accGB);
+            u1f_consumer_barrier(32 * G::CW);
+            const U1SNb<T> S = u1f_raw<T>(ring_sm, j + 1, lane, warp);
+            const U1FQ<T> Q{pq, j + 1, lane, warp};
+            const uint32_t n = ((t.z0 + j) * N + t.y0 + warp) * N + t.x0 + lane;
+            T kv[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) kv[q] = kc[q];
+            if (update && j + 1 < nz) load_site(n + N * N);
+
+            // scalar sector
+            const T ph = S(FR_PHI, 0, 0, 0), pv = S(FR_PI, 0, 0, 0);
+            const T pxp = S(FR_PHI, 1, 0, 0), pxm = S(FR_PHI, -1, 0, 0);
+            const T pyp = S(FR_PHI, 0, 1, 0), pym = S(FR_PHI, 0, -1, 0);
+            const T pzp = S(FR_PHI, 0, 0, 1), pzm = S(FR_PHI, 0, 0, -1);
+            const T lap = ((pxp + pxm) + (pyp + pym) + (pzp + pzm)) - (T)6 * ph;
+            const T dV = ph * (m2 + lam * ph * ph);
+            T eb = (T)0, e2 = (T)0;
+            T Ecur[3], Bn[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                Ecur[k] = S(FR_E + k, 0, 0, 0);
+                Bn[k] = inv4dx2 * Q.clover(0, k, 0, 0, 0);
+                eb += (T)0.5 * (Ecur[k] + S(FR_E + k, U1S_E(k, -1))) * Bn[k];
+                e2 += Ecur[k] * Ecur[k];
+            }
+            const T F_phi = c_dphi * pv;
+            const T F_pi = cL * lap - cV * dV + ws2 * g * eb;
+            if (!LF) {  // (leapfrog pass 1 sums the kinetic energies of its output momenta)
+                accK.add(pv * pv);
+                accKE.add(e2);
+            }
+            if (!LF || lf == 1) {
+                accG.add((pxp - ph) * (pxp - ph) + (pyp - ph) * (pyp - ph) + (pzp - ph) * (pzp - ph));
+                accV.add(ph * ph * ((T)0.5 * m2 + (T)0.25 * lam * ph * ph));
+            }
+            if (update) {
+                if constexpr (TRACK) {
+                    // dx times the lattice Gauss charge of the input state (the leapfrog's:
+                    // the integer-time state, its electric field the base momenta)
+                    T ec[3], em[3];
+                    if constexpr (LF) {
+                        const uint32_t x = t.x0 + lane, y = t.y0 + warp, z = t.z0 + j;
+                        const uint32_t nm[3] = {x == 0 ? n + N - 1 : n - 1, y == 0 ? n + (N - 1) * N : n - N,
+                                                z == 0 ? n + (N - 1) * N * N : n - N * N};
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            ec[i] = kv[5 + i];
+                            em[i] = A.k_in[5 + i][nm[i]];
+                        }
+                        accKE.add(ec[0] * ec[0] + ec[1] * ec[1] + ec[2] * ec[2]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            ec[i] = Ecur[i];
+                            em[i] = S(FR_E + i, U1S_E(i, -1));
+                        }
+                    }
+                    T gd = (T)0;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const T Bpi = inv4dx2 * Q.clover(0, i, U1S_E(i, 1));
+                        const T Bmi = inv4dx2 * Q.clover(0, i, U1S_E(i, -1));
+                        gd += ca * (ec[i] - em[i]) +
+                              (T)0.5 * g * (S(FR_PHI, U1S_E(i, 1)) * Bpi - S(FR_PHI, U1S_E(i, -1)) * Bmi);
+                    }
+                    accGs.add(gd * gd);
+                }
+                // link forces
+                T F_E[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const int ip = (i + 1) % 3, im = (i + 2) % 3;
+                    const T mag = (Q(im, 0, 0, 0, 0) - Q(im, 0, U1S_E(ip, -1))) - (Q(ip, 0, 0, 0, 0) - Q(ip, 0, U1S_E(im, -1)));
+                    const T cs = (Q(im, 2, 0, 0, 0) - Q(im, 2, U1S_E(ip, -1))) + (Q(ip, 2, U1S_E(im, -1)) - Q(ip, 2, 0, 0, 0));
+                    const T Bdn = inv4dx2 * Q.clover(1, i, 0, 0, 0);
+                    const T Bni = inv4dx2 * Q.clover(0, i, U1S_E(i, 1));
+                    const T Bdni = inv4dx2 * Q.clover(1, i, U1S_E(i, 1));
+                    const T wdot = (T)0.5 * (F_phi * Bn[i] + ph * Bdn + c_dphi * S(FR_PI, U1S_E(i, 1)) * Bni +
+                                             S(FR_PHI, U1S_E(i, 1)) * Bdni);
+                    F_E[i] = cE * (-cE * mag * inv_dx3 + g * (cs * inv4dx - wdot)) - cfr * Ecur[i];
+                }
+                const T thv[3] = {S(FR_TH + 0, 0, 0, 0), S(FR_TH + 1, 0, 0, 0), S(FR_TH + 2, 0, 0, 0)};
+                ring.release(j, lane);
+                if constexpr (LF) {
+                    if (lf == 1) {  // closing half-kick (integer-time momenta) and the first iterate
+                        T En[3], Eo[3], en2 = (T)0;
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            En[i] = Ecur[i] + le * F_E[i];
+                            Eo[i] = Ecur[i] + lk * F_E[i];
+                            en2 += En[i] * En[i];
+                        }
+                        const T pn = pv + le * F_pi;
+                        accK.add(pn * pn);
+                        accKE.add(en2);
+                        A.k_out[1][n] = pn;
+                        A.pi_out[n] = pv + lk * F_pi;
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            A.k_out[5 + i][n] = En[i];
+                            A.E_out[i][n] = Eo[i];
+                        }
+                    } else {  // an iterate of the implicit kick from the base momenta
+                        const T po = kv[1] + lk * F_pi;
+                        T Eo[3];
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) Eo[i] = kv[5 + i] + lk * F_E[i];
+                        if (lf == 3) {
+                            A.phi_out[n] = ph + cdrift * po;
+#pragma unroll
+                            for (int i = 0; i < 3; ++i) A.th_out[i][n] = thv[i] + hdx * Eo[i];
+                        }
+                        A.pi_out[n] = po;
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) A.E_out[i][n] = Eo[i];
+                    }
+                } else {
+                    // 2N Runge-Kutta update of the eight degrees of freedom of this site
+                    const T F[8] = {F_phi, F_pi, dx * Ecur[0], dx * Ecur[1], dx * Ecur[2], F_E[0], F_E[1], F_E[2]};
+                    const T y[8] = {ph, pv, thv[0], thv[1], thv[2], Ecur[0], Ecur[1], Ecur[2]};
+                    T kq[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) kq[q] = first ? h * F[q] : cA * kv[q] + h * F[q];
+                    T* out[8] = {A.phi_out, A.pi_out, A.th_out[0], A.th_out[1], A.th_out[2], A.E_out[0], A.E_out[1],
+                                 A.E_out[2]};
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        A.k_out[q][n] = kq[q];
+                        out[q][n] = y[q] + cB * kq[q];
+                    }
+                }
+            } else {
+                ring.release(j, lane);
+            }
+        }
+        ring.release(nz, lane);
+        ring.release(nz + 1, lane);
+    }
+    __syncthreads();  // producer and consumers meet; no copy is in flight past this point
+
+    // ---- block partials; last block: energies of the old state and the (a, a') stage ----
+    // the stage's five sums (slot 4 the Gauss sum), the magnetic energy after them (one value a
+    // block, as the plaquette launch of the two-launch form leaves it)
+    double v[kMaxQ];
+    const Acc<T>* av[kMaxQ] = {&accK, &accG, &accV, &accKE, &accGs};
+    block_reduce_acc<T, kMaxQ>(av, v, s_red, tid, G::NT);
+    double vb[1];
+    const Acc<T>* ab[1] = {&accGB};
+    block_reduce_acc<T, 1>(ab, vb, s_red, tid, G::NT);
+    if (tid == 0) {
+        if (s_fail) atomicOr(&A.scal->status, ST_TIMEOUT);
+#pragma unroll
+        for (int q = 0; q < kMaxQ; ++q) A.partials[(size_t)blockIdx.x * kMaxQ + q] = v[q];
+        A.partials[(size_t)gridDim.x * kMaxQ + blockIdx.x] = vb[0];
+        __threadfence();
+        const unsigned prev = atomicAdd(&A.scal->counter, 1u);
+        s_last = (prev + 1u == gridDim.x);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (tid >= 32) return;  // one warp sums the grid's partials, its lane 0 runs the epilogue
+    double ws[kMaxQ];
+    warp_sum_partials<kMaxQ>(A.partials, (int)gridDim.x, tid, ws);
+    double gb = 0.0;
+    for (int b = tid; b < (int)gridDim.x; b += 32) gb += __ldcg(&A.partials[(size_t)gridDim.x * kMaxQ + b]);
+    for (int off = 16; off > 0; off >>= 1) gb += __shfl_xor_sync(0xffffffffu, gb, off);
+    double w[kMaxQ] = {ws[0], ws[1], ws[2], ws[3], gb};
+    if (tid == 0) {
+        if (track) u1_gauss_track(A.scal, ws[kMaxQ - 1], w[3], s_coef[6]);
+        if (LF) u1_lf_epilogue(A, w, s_coef[5], expand, V);
+        else u1_epilogue(A, w, s_coef[5], first, update, expand, V);
+    }
+}
+
 #undef U1S_E
 
 bool u1_staged_ok(int N) { return N >= 32 && N % 32 == 0; }
@@ -624,6 +1017,24 @@ static cudaError_t launch_u1s_t(const U1Args<T>& A, int what, cudaStream_t s)
             attr[0] = true;
         }
         k_u1s_plaquettes<T><<<grid, G::NT, smem, s>>>(A);
+    } else if (what == 2) {
+        constexpr size_t smem = u1f_smem_bytes<T>();
+        const int form = A.lf ? (A.lf == 2 ? 4 : 3) : ((A.flags & P_FIRST_STAGE) && !(A.flags & P_ENERGY_ONLY) ? 2 : 1);
+        static DevFlag fattr[5];
+        if (!fattr[form]) {
+            const int sm = (int)smem;
+            const cudaError_t e =
+                form == 4   ? cudaFuncSetAttribute(k_u1f_stage<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)
+                : form == 3 ? cudaFuncSetAttribute(k_u1f_stage<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)
+                : form == 2 ? cudaFuncSetAttribute(k_u1f_stage<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)
+                            : cudaFuncSetAttribute(k_u1f_stage<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            if (e != cudaSuccess) return e;
+            fattr[form] = true;
+        }
+        if (form == 4) k_u1f_stage<T, true, true><<<grid, G::NT, smem, s>>>(A);
+        else if (form == 3) k_u1f_stage<T, false, true><<<grid, G::NT, smem, s>>>(A);
+        else if (form == 2) k_u1f_stage<T, true, false><<<grid, G::NT, smem, s>>>(A);
+        else k_u1f_stage<T, false, false><<<grid, G::NT, smem, s>>>(A);
     } else {
         constexpr size_t smem = u1s_smem_bytes<T, SG_NA>();
         // forms: 1 a Runge-Kutta stage, 2 the first stage of a step (Gauss tracking), 3 a

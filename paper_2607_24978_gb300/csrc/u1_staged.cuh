@@ -5,9 +5,10 @@
 
 namespace clk {
 
-// what 0 = plaquette fields, 1 = stage (or energies with P_ENERGY_ONLY), with the partial
-// layout of launch_u1, on u1_staged_blocks(precision, N, dz) blocks of 32 x 16 (FP32) or
-// 32 x 8 (FP64) tiles, each marching through dz planes; needs u1_staged_ok(N).
+// what 0 = plaquette fields, 1 = stage (or energies with P_ENERGY_ONLY), 2 = the fused stage
+// (plaquette fields in shared memory, no plaquette launch), with the partial layout of
+// launch_u1, on u1_staged_blocks(precision, N, dz) blocks of 32 x 16 (FP32) or 32 x 8 (FP64)
+// tiles, each marching through dz planes; needs u1_staged_ok(N).
 bool u1_staged_ok(int N);
 int u1_staged_blocks(int precision, int N, int dz);
 // The library's z chunk: one block per SM at a time, waves x (planes + 2) minimised.

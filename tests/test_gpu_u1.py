@@ -175,13 +175,15 @@ def test_u1_fused_and_two_launch_forms_agree(cl):
 @pytest.mark.parametrize("integ,scheme,stages", CASES)
 @pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-4)])
 @pytest.mark.parametrize("alpha", [0.0, 1.0])
-def test_u1_staged_parity(cl, integ, scheme, stages, prec, tol, alpha):
+@pytest.mark.parametrize("form", [2, 3])
+def test_u1_staged_parity(cl, integ, scheme, stages, prec, tol, alpha, form):
     """The staged launches (CL_OPT_PASS_VARIANT 2, the default where N % 32 == 0: every
-    plane's neighbourhood in shared memory) at N = 32 and 64 against the oracle, with the
-    energies of the initial and final states."""
+    plane's neighbourhood in shared memory; 3: the same in one launch per stage with the
+    plaquette fields in shared memory) at N = 32 and 64 against the oracle, with the energies
+    of the initial and final states."""
     for N, n in ((32, 6), (64, 2)):
         out, e0, e, st0, st, m, launches = run_pair(cl, N, prec, integ, scheme, n, alpha=alpha, th_amp=0.5,
-                                                    variant=2 if N == 32 else None)
+                                                    variant=form if (N == 32 or form == 3) else None)
         assert rel_l2(out["phi"], st.phi[0]) < tol
         assert rel_l2(out["pi"], st.pi[0]) < tol
         assert rel_l2(out["th"], st.links) < tol
@@ -194,16 +196,17 @@ def test_u1_staged_parity(cl, integ, scheme, stages, prec, tol, alpha):
                              ("G0", "G0")]:
             assert e[k_gpu] == pytest.approx(eo[k_orc], rel=max(tol, 1e-9)), k_gpu
             assert e0[k_gpu] == pytest.approx(e0o[k_orc], rel=max(tol, 1e-9)), k_gpu
-        assert launches == n * stages * 2
+        assert launches == n * stages * (2 if form == 2 else 1)
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-13), (2, 2e-6)])
 @pytest.mark.parametrize("dz", [0, 1, 5, 31])
-def test_u1_staged_and_gather_forms_agree(cl, prec, tol, dz):
+@pytest.mark.parametrize("form", [2, 3])
+def test_u1_staged_and_gather_forms_agree(cl, prec, tol, dz, form):
     """Staged and gather launches on the same 32^3 state, with the library's z chunk and
     with chunks of 1, 5 (ragged last chunk) and 31 planes (a last chunk of one plane)."""
     res = []
-    for variant in (2, 0):
+    for variant in (form, 0):
         L = 24.0
         m = O.make_model(32, L, nf=1, alpha=0.5, kappa=KAPPA, expansion=True, gauge=1, alphaL=ALPHAL, ws2=WS2,
                          m2=(M2, 0.0), lam=(LAM, 0.0))
@@ -395,7 +398,7 @@ def test_gauge_spectra_match_oracle(cl, N, prec):
             g.cl_gauge_spectrum(cl.CL_GSPEC_E)  # no gauge field
 
 
-@pytest.mark.parametrize("variant,N", [(2, 32), (0, 32), (1, 32), (None, 12)])
+@pytest.mark.parametrize("variant,N", [(2, 32), (0, 32), (1, 32), (3, 32), (None, 12)])
 @pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-4)])
 def test_u1_gauss_tracked_each_step(cl, variant, N, prec, tol):
     """cl_step tracks the Gauss law every step (config "Gauss constraint tracked each step"):
@@ -425,7 +428,7 @@ def test_u1_gauss_tracked_each_step(cl, variant, N, prec, tol):
             g.cl_set_state(cl.CL_FIELD_E1 + i, st.efield[i].astype(dtype))
         g.cl_set_scalars(st.abt[0], st.abt[1], 0.0)
         assert g.cl_energies()["gauss_rms_max"] == 0.0
-        want = {2: 2, 0: 0, 1: 1}.get(variant, 0)
+        want = {2: 2, 0: 0, 1: 1, 3: 3}.get(variant, 0)
         assert g.cl_get_option(cl.CL_OPT_PASS_VARIANT) == want
         rmax = 0.0
         for _ in range(3):

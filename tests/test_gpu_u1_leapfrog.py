@@ -80,7 +80,7 @@ def check_energies(e, m, st, tol):
     assert e["hubble_violation"] == pytest.approx(eo["hubble_violation"], abs=tol)
 
 
-@pytest.mark.parametrize("N,variant", [(8, None), (12, None), (32, None), (32, 0), (64, None)])
+@pytest.mark.parametrize("N,variant", [(8, None), (12, None), (32, None), (32, 0), (64, None), (32, 3), (64, 3)])
 @pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-4)])
 @pytest.mark.parametrize("alpha", [0.0, 0.5, 1.0])
 def test_leapfrog_parity(cl, N, variant, prec, tol, alpha):
@@ -95,7 +95,7 @@ def test_leapfrog_parity(cl, N, variant, prec, tol, alpha):
     st = start(m, 5, th_amp=0.5)
     dtype = np.float64 if prec == 0 else np.float32
     with lattice(cl, N, L, prec, alpha, variant=variant) as g:
-        assert g.cl_get_option(cl.CL_OPT_PASS_VARIANT) == (2 if N % 32 == 0 and variant is None else 0)
+        assert g.cl_get_option(cl.CL_OPT_PASS_VARIANT) == (2 if N % 32 == 0 and variant is None else (variant or 0))
         upload(cl, g, st, dtype)
         g.cl_step(n)
         launches = g.cl_last_launch_count()
@@ -105,8 +105,8 @@ def test_leapfrog_parity(cl, N, variant, prec, tol, alpha):
     check_state(out, st, tol)
     check_energies(e, m, st, tol)
     assert e["step"] == n
-    staged = N % 32 == 0 and variant is None
-    assert launches == 2 + (6 if staged else 7) * n
+    per_step = {None: 6 if N % 32 == 0 else 7, 0: 7, 3: 3}[variant]
+    assert launches == (1 if variant == 3 else 2) + per_step * n
 
 
 @pytest.mark.parametrize("prec", [0, 2])
