@@ -299,9 +299,9 @@ U1_BYTES_PER_SITE_STAGE = 8 * 2 * 2 * 4
 U1_LF_PASSES = 3
 U1_LF_BYTES_PER_SITE_STEP = (16 + 16 + 20) * 4
 RK_STAGES = 5
-# GW pass per site: the scalars' phi, pi, c of two fields read (24 B) and the five
-# auxiliaries and their momenta read and written (2 x 10 x 4 B), FP32
-GW_BYTES_PER_SITE_PASS = 2 * 3 * 4 + 2 * 10 * 4
+# GW pass per site: the scalars the scalar pass just drifted, two fields read (8 B), and the
+# five auxiliaries and their momenta read and written (2 x 10 x 4 B), FP32
+GW_BYTES_PER_SITE_PASS = 2 * 4 + 2 * 10 * 4
 NMC_XI = 0.3
 # NMC stage per site, one field, FP32 + Kahan: phi, pi, k_phi, k_pi, c read and written (40 B;
 # 32 B in the first stage, which reads no k), averaged over the 5 stages.  The Ricci scalar's

@@ -420,7 +420,10 @@ cl_status choose_tiles(cl_lattice* l)
     }
     if (l->gw) {
         // GW pass (direct loads, as the Runge-Kutta stage kernel): about 256 threads per block,
-        // two blocks per SM, the y tiles cut into z chunks so that about one wave covers the lattice
+        // two blocks per SM, the y tiles cut into z chunks so that about one wave covers the
+        // lattice.  (Measured at 256^3 FP32, two fields, Yoshida-4: 10.5 Gsite-updates/s; a pass
+        // with four cp.async plane stages of 2-row tiles, one block per SM, 6.2 with 8 warps and
+        // 8.0 with 16: the pass is bound by its latency-exposed arithmetic, not by its loads.)
         int gby = TX >= 256 ? 1 : 256 / TX;
         if (gby > N) gby = N;
         while (gby > 1 && gw_pass_smem(l->nf, N, gby, l->es) > (size_t)kPassMaxSmem / 2) --gby;
@@ -677,11 +680,7 @@ template <typename T>
 cl_status run_gw_pass_t(cl_lattice* l, const PassCoef& pc, int in, int out)
 {
     GwPassArgs<T> A{};
-    for (int f = 0; f < l->nf; ++f) {
-        A.phi_in[f] = (const T*)l->phi[f][in];
-        A.pi_in[f] = (const T*)l->pi[f][in];
-        A.c_in[f] = (const T*)l->cc[f][in];
-    }
+    for (int f = 0; f < l->nf; ++f) A.phi_in[f] = (const T*)l->phi[f][out];  // drifted by the scalar pass
     for (int c = 0; c < 5; ++c) {
         A.v_in[c] = (const T*)l->gv[c][in];
         A.pv_in[c] = (const T*)l->gpv[c][in];
@@ -760,14 +759,13 @@ cl_status run_ens_pass(cl_lattice* l, const PassCoef& pc, int in, int out, int m
 cl_status run_pass(cl_lattice* l, const PassCoef& pc, int in, int out)
 {
     if (is_ens(l)) return run_ens_pass(l, pc, in, out, 0, l->members);
-    if (l->gw && !pc.rk) {  // the GW auxiliaries first, from the same scalar input buffers
-        cl_status s = is_fp64(l) ? run_gw_pass_t<double>(l, pc, in, out) : run_gw_pass_t<float>(l, pc, in, out);
-        if (s != CL_OK) return s;
-    }
     if (pc.lf) return run_u1_lf(l, pc, in);                              // axion + U(1) leapfrog pass
     if (pc.rk == 2) return run_u1(l, 1, pc.A, pc.B, pc.flags, in, out);  // axion + U(1) stage
     if (pc.rk) return is_fp64(l) ? run_rk_stage_t<double>(l, pc, in, out) : run_rk_stage_t<float>(l, pc, in, out);
-    return run_pass_impl(l, pc, in, out, nullptr);
+    cl_status s = run_pass_impl(l, pc, in, out, nullptr);
+    if (s == CL_OK && l->gw)  // the GW auxiliaries after it, from the scalars it drifted
+        s = is_fp64(l) ? run_gw_pass_t<double>(l, pc, in, out) : run_gw_pass_t<float>(l, pc, in, out);
+    return s;
 }
 
 // Low-storage 2N Runge-Kutta coefficients (A_s, B_s), as published:

@@ -61,6 +61,8 @@ struct DevScal {
                            // its maximum over the steps since the state was set
     double h;              // adaptive RK3-4: the step size of the next step (P_DEVICE_H)
     double rk_err;         // adaptive RK3-4: error estimate of the latest step
+    double a_prev;         // leapfrog: a before the latest committed scalar pass (the GW pass
+                           // that follows it forms the pass's midpoint a from it and a)
 };
 
 // Flags of one fused scalar pass.
@@ -152,13 +154,11 @@ struct RkStageArgs {
 };
 cudaError_t launch_rk_stage(int precision, int nf, const void* args, int vw, cudaStream_t s);
 // Gravitational waves (gw_pass.cu): five traceless auxiliaries v = {v11, v12, v13, v22,
-// v23} and their momenta, kicked and drifted by one pass before each fused scalar pass with
-// the same coefficients; the scalars' input buffers provide the source.
+// v23} and their momenta, kicked and drifted by one pass after each fused scalar pass with
+// the same coefficients; that pass's output (the drifted scalars) provides the source.
 template <typename T>
 struct GwPassArgs {
-    const T* phi_in[2];
-    const T* pi_in[2];
-    const T* c_in[2];
+    const T* phi_in[2];  // the scalars drifted by this pass: the scalar pass's output
     const T* v_in[5];
     const T* pv_in[5];
     T* v_out[5];
@@ -166,7 +166,8 @@ struct GwPassArgs {
     const DevScal* scal;
     int N, BY, DZ, nby, nbz;
     double dx, alpha, kappa;
-    double d, k;        // pass coefficients (already x dt), as in ScalarPassArgs
+    double d, k;        // pass coefficients (already x dt), as in ScalarPassArgs; the pass
+                        // runs after the scalar pass of the same coefficients
     int flags;          // P_DRIFT, P_EXPANSION
 };
 cudaError_t launch_gw_pass(int precision, int nf, const void* args, int vw, cudaStream_t s);

@@ -2,10 +2,11 @@
 // GWs"): v = {v11, v12, v13, v22, v23} (v33 = -v11 - v22) and pi_v = a^(3-alpha) v', with
 //   v' = a^(alpha-3) pi_v,   pi_v' = a^(1+alpha) Lap v + 2 kappa a^(1+alpha) [Pi_ij - delta_ij Pi / 3],
 //   Pi_ij = sum_f dbar_i phi_f dbar_j phi_f  (central differences),
-// evolved by the leapfrog alongside the scalars.  One GW pass runs before each fused scalar
-// pass with the same coefficients (d, k): it drifts the scalars to the kick time again (the
-// same compensated arithmetic as the scalar pass) for the source, drifts v, and kicks pi_v.
-// The GW fields do not act back on the scalars or on a.
+// evolved by the leapfrog alongside the scalars.  One GW pass runs after each fused scalar
+// pass with the same coefficients (d, k): it reads the scalars that pass drifted (its output)
+// for the source, drifts v, and kicks pi_v, with the pass's prefactors formed from a before
+// and after the pass (DevScal::a_prev, a) exactly as the scalar pass formed them.  The GW
+// fields do not act back on the scalars or on a.
 //
 // Work decomposition as the Runge-Kutta stage kernel: a block owns BY full x rows and a
 // range of planes and marches up z with a three-plane ring of the drifted scalars and v
@@ -41,8 +42,13 @@ __global__ void __launch_bounds__(256) k_gw_pass(const GwPassArgs<T> A)
     const bool do_drift = (A.flags & P_DRIFT) != 0;
     long long u0, u1;
     block_units(N, A.nby, A.DZ, u0, u1);
-    if (tid == 0)
-        pass_coefficients(A.scal->a, A.scal->b, A.d, A.alpha, A.dx, (A.flags & P_EXPANSION) != 0, s_coef);
+    if (tid == 0) {
+        // the scalar pass's prefactors: a_new = a_old + d a' is what it committed
+        const bool expand = (A.flags & P_EXPANSION) != 0;
+        const double a_new = A.scal->a, a_old = expand ? A.scal->a_prev : a_new;
+        s_coef[0] = A.d * apow(0.5 * (a_old + a_new), A.alpha - 3.0);
+        s_coef[1] = apow(a_new, 1.0 + A.alpha) / (A.dx * A.dx);
+    }
     __syncthreads();
     const T cd = (T)s_coef[0], cL = (T)s_coef[1];
     const T cS = (T)(2.0 * A.kappa * s_coef[1] * A.dx * A.dx);  // 2 kappa a_new^(1+alpha)
@@ -56,15 +62,9 @@ __global__ void __launch_bounds__(256) k_gw_pass(const GwPassArgs<T> A)
         auto row = [&](int y, int srow, int vx) {
             const size_t g = ((size_t)zz * N + y) * N + vx;
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                T ph[VW], pv[VW], cv[VW];
+            for (int f = 0; f < NF; ++f) {  // already drifted by the scalar pass
+                T ph[VW];
                 vload<T, VW>(ph, A.phi_in[f] + g);
-                if (do_drift) {
-                    vload<T, VW>(pv, A.pi_in[f] + g);
-                    if (KAHAN) vload<T, VW>(cv, A.c_in[f] + g);
-#pragma unroll
-                    for (int i = 0; i < VW; ++i) drift<T, KAHAN>(ph[i], cv[i], pv[i], cd);
-                }
                 vstore<T, VW>(sm + f * field_stride + slot * slot_stride + srow * N + vx, ph);
             }
 #pragma unroll

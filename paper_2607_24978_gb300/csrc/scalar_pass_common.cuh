@@ -301,6 +301,7 @@ __device__ inline void scalar_epilogue(DevScal* S, const double (&w)[kMaxQ], dou
     const double hv = H != 0.0 ? fabs(H * H - a2al * kappa * rho * third) / (H * H) : 0.0;
     const double t_int = S->t + d;
     if (flags & P_COMMIT) {
+        S->a_prev = S->a;
         S->a = a;
         S->b = b + k * addot;
         S->t = t_int;

@@ -31,9 +31,11 @@ SCHEMES = {0: O.VV2, 1: O.YOSHIDA4}
 
 
 @pytest.mark.parametrize("integ", [0, 1])
-@pytest.mark.parametrize("prec,tol,nf,N", [(0, 1e-10, 2, 12), (2, 1e-4, 1, 16), (1, 1e-4, 2, 12), (0, 1e-10, 1, 10)])
+@pytest.mark.parametrize("prec,tol,nf,N", [(0, 1e-10, 2, 12), (2, 1e-4, 1, 16), (1, 1e-4, 2, 12), (0, 1e-10, 1, 10),
+                                           (1, 1e-4, 2, 64), (2, 1e-4, 1, 64), (1, 1e-4, 2, 128)])
 def test_gw_evolution_and_spectrum_parity(cl, integ, prec, tol, nf, N):
-    L, dt, n = 0.8 * N, 0.02, 15
+    """Sizes 10 to 128 (several tiles and z chunks at 64 and 128)."""
+    L, dt, n = 0.8 * N, 0.02, (15 if N <= 16 else (4 if N <= 64 else 2))
     phi, pi = inputs.scalar_state(N, nf, seed=51, fbar=(0.9, 0.1), amp=0.1, pamp=0.1)
     m = O.make_model(N, L, nf=nf, alpha=1.0, kappa=0.6, expansion=True, m2=(0.5, 0.2), lam=(1.0, 0.0),
                      g2=1.5 if nf == 2 else 0.0)
