@@ -206,3 +206,66 @@ def test_ensemble_1024_members_sampled(cl):
         assert rel_l2(end[mm][0], st.phi[0]) < 1e-6, mm
         assert rel_l2(end[mm][1], st.pi[0]) < 1e-4, mm
         assert es[mm]["a"] == pytest.approx(st.abt[0], rel=1e-7), mm
+
+
+def test_headline_512_cubed(cl):
+    """The headline model at 512^3 (the roofline size of the two-field workload; two-row
+    tiles), Yoshida-4, FP32 + Kahan; state periodic with period 32."""
+    N, P, dt = 512, 32, 0.005
+    L = 8.0 * math.pi * N / 256  # the headline's spacing
+    Ls = L * P / N
+    m = O.make_model(P, Ls, nf=2, alpha=0.0, kappa=0.1, expansion=True, m2=(1.0, 0.0), g2=4e4)
+    phi, pi = inputs.scalar_state(P, 2, seed=101, fbar=(1.0, 0.0), amp=1e-3, pamp=1e-3)
+    st = O.State(phi.astype(np.float32).astype(np.float64), pi.astype(np.float32).astype(np.float64),
+                 np.array([1.0, 0.0, 0.0]))
+    st.abt[1] = math.sqrt(0.1 * O.energies(m, st)["rho"] / 3.0)
+    reps = N // P
+    n = 2
+    with cl.Lattice(N, L, 2, cl.CL_PREC_FP32_KAHAN, cl.CL_INT_YOSHIDA4, expansion=True, alpha=0.0, kappa=0.1,
+                    dt=dt) as g:
+        g.cl_set_potential(cl.CL_POT_M2_G2, [1.0, 4e4])
+        for f in range(2):
+            g.cl_set_state(cl.CL_FIELD_PHI0 + f, tile3(st.phi[f], reps).astype(np.float32))
+            g.cl_set_state(cl.CL_FIELD_PI0 + f, tile3(st.pi[f], reps).astype(np.float32))
+        g.cl_set_scalars(st.abt[0], st.abt[1], 0.0)
+        g.cl_step(n)
+        out = [(g.cl_get_state(cl.CL_FIELD_PHI0 + f), g.cl_get_state(cl.CL_FIELD_PI0 + f)) for f in range(2)]
+        e = g.cl_energies()
+    O.step(m, st, O.YOSHIDA4, dt, n)
+    for f in range(2):
+        assert rel_l2(out[f][0], tile3(st.phi[f], reps)) < 1e-6
+        assert rel_l2(out[f][1], tile3(st.pi[f], reps)) < 1e-4
+    assert e["rho"] == pytest.approx(O.energies(m, st)["rho"], rel=1e-5)
+    assert e["a"] == pytest.approx(st.abt[0], rel=1e-7)
+
+
+def test_nonminimal_256_cubed(cl):
+    """bench.py --workload nmc: one lambda phi^4 field non-minimally coupled (xi = 0.3) at
+    256^3, RK4-5, FP32 + Kahan, the TMA-staged stage that carries the Ricci scalar; state
+    periodic with period 16."""
+    N, P, dt, xi = 256, 16, 0.005, 0.3
+    L = 8.0 * math.pi
+    Ls = L * P / N
+    m = O.make_model(P, Ls, nf=1, alpha=1.0, kappa=0.1, expansion=True, lam=(1.0, 0.0), xi=xi)
+    phi, pi = inputs.scalar_state(P, 1, seed=111, fbar=(1.0,), amp=1e-2, pamp=1e-2)
+    st = O.State(phi.astype(np.float32).astype(np.float64), pi.astype(np.float32).astype(np.float64),
+                 np.array([1.0, 0.0, 0.0]))
+    reps = N // P
+    n = 3
+    with cl.Lattice(N, L, 1, cl.CL_PREC_FP32_KAHAN, cl.CL_INT_RK4_5, expansion=True, alpha=1.0, kappa=0.1,
+                    dt=dt) as g:
+        g.cl_set_potential(cl.CL_POT_LPHI4, [1.0])
+        g.cl_set_nonminimal(xi)
+        g.cl_set_state(cl.CL_FIELD_PHI0, tile3(st.phi[0], reps).astype(np.float32))
+        g.cl_set_state(cl.CL_FIELD_PI0, tile3(st.pi[0], reps).astype(np.float32))
+        g.cl_set_scalars(1.0)  # a' from the constraint of the non-minimally coupled system
+        e0 = g.cl_energies()
+        st.abt[:] = (e0["a"], e0["adot"], 0.0)
+        g.cl_step(n)
+        gphi, gpi = g.cl_get_state(cl.CL_FIELD_PHI0), g.cl_get_state(cl.CL_FIELD_PI0)
+        e = g.cl_energies()
+    O.step(m, st, O.RK4_5, dt, n)
+    assert rel_l2(gphi, tile3(st.phi[0], reps)) < 1e-6
+    assert rel_l2(gpi, tile3(st.pi[0], reps)) < 1e-4
+    assert e["a"] == pytest.approx(st.abt[0], rel=1e-7)
+    assert e["adot"] == pytest.approx(st.abt[1], rel=1e-5)
