@@ -409,6 +409,20 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
 #pragma unroll
             for (int q = 0; q < 8; ++q) kv[q] = kc[q];
             if (update && j + 1 < (int)t.nz) load_site(n + N * N);
+            if (update && j + 2 < (int)t.nz) {
+                // the site-only arrays of the plane after next into L2 (one 128-byte row a
+                // lane), so that the loads one plane ahead wait on L2 rather than DRAM
+                const T* pf = nullptr;
+                if constexpr (LF) {
+                    if (lane < 3) pf = lf == 3 ? A.th_in[lane] : nullptr;
+                    else if (lane == 3) pf = lf >= 2 ? A.k_in[1] : nullptr;
+                    else if (lane < 7) pf = lf >= 2 ? A.k_in[1 + lane] : nullptr;
+                } else {
+                    if (lane < 3) pf = A.th_in[lane];
+                    else if (lane < 11 && !first) pf = A.k_in[lane - 3];
+                }
+                if (pf) prefetch_l2(pf + n + 2 * N * N);
+            }
 
             // scalar sector
             const T ph = S(SG_PHI, 0, 0, 0), pv = S(SG_PI, 0, 0, 0);
