@@ -88,6 +88,23 @@ __global__ void __launch_bounds__(256) k_gw_pass(const GwPassArgs<T> A)
         }
     };
 
+    // the own rows of plane z0 + zrel into L2 (one 128-byte line per lane that starts one), so
+    // that the fill one plane later waits on L2 rather than DRAM; the halo rows are other
+    // tiles' own rows
+    auto prefetch_plane = [&](int zrel) {
+        if (r >= R || ((x0 * (int)sizeof(T)) & 127) != 0) return;
+        int zz = z0 + zrel;
+        zz = zz < 0 ? zz + N : (zz >= N ? zz - N : zz);
+        const size_t g = ((size_t)zz * N + (y0 + r)) * N + x0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) prefetch_l2(A.phi_in[f] + g);
+#pragma unroll
+        for (int c = 0; c < kGwC; ++c) {
+            prefetch_l2(A.v_in[c] + g);
+            if (do_drift) prefetch_l2(A.pv_in[c] + g);
+        }
+    };
+
     for (long long u = u0; u < u1;) {
         const int tile = (int)(u / N);
         z0 = (int)(u - (long long)tile * N);
@@ -99,6 +116,7 @@ __global__ void __launch_bounds__(256) k_gw_pass(const GwPassArgs<T> A)
         fill(0, 1);
         for (int zr = 0; zr < NZ; ++zr) {
             const int sl = zr % 3, sc = (zr + 1) % 3, su = (zr + 2) % 3;
+            if (zr + 2 <= NZ) prefetch_plane(zr + 2);
             fill(zr + 1, su);
             __syncthreads();
             if (r < R) {
