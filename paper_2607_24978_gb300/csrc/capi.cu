@@ -371,6 +371,11 @@ cl_status choose_tiles(cl_lattice* l)
         while (BY > 1 && scalar_pass_smem_bytes(prec, l->nf, N, BY, 2, var) > (size_t)kPassMaxSmem) BY /= 2;
         while (stages > 2 && scalar_pass_smem_bytes(prec, l->nf, N, BY, stages, var) > (size_t)kPassMaxSmem) --stages;
         if (scalar_pass_smem_bytes(prec, l->nf, N, BY, stages, var) > (size_t)kPassMaxSmem) stages = 0;
+        // a fifth ringless stage where it fits beside the same tile (one field: measured at
+        // 256^3 FP32 + Kahan 0.70 -> 0.75 of HBM for VV-2; two fields at 256^3 do not fit it)
+        if (l->opt_stages <= 0 && var && stages == 4 &&
+            scalar_pass_smem_bytes(prec, l->nf, N, BY, 5, var) <= (size_t)kPassMaxSmem)
+            stages = 5;
     }
     const int var_eff = stages > 0 ? var : 0;
     while (BY > 1 && scalar_pass_smem_bytes(prec, l->nf, N, BY, stages, var_eff) > (size_t)kPassMaxSmem) BY /= 2;

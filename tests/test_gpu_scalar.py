@@ -279,9 +279,15 @@ def test_ringless_and_ring_passes_identical(cl, N, nf, prec, by, dz, stages):
 def test_effective_options_reported(cl):
     """cl_get_option reports the tiling the library chose: the ringless TMA pass where rows are
     16-byte vectors, the ring variant otherwise; overrides are reflected."""
-    with gpu_lattice(cl, 256, 9.0, 2, 2, cl.CL_INT_YOSHIDA4, expansion=True, alpha=0.0, kappa=0.1, dt=0.005) as g:
+    with gpu_lattice(cl, 256, 9.0, 2, 1, cl.CL_INT_YOSHIDA4, expansion=True, alpha=0.0, kappa=0.1, dt=0.005) as g:
+        # the headline tiling: two fields with Kahan compensation, six arrays a row, four stages
         assert g.cl_get_option(cl.CL_OPT_PASS_VARIANT) == 1
         assert g.cl_get_option(cl.CL_OPT_STAGES) == 4
+        assert g.cl_get_option(cl.CL_OPT_TILE_BY) == 7
+    with gpu_lattice(cl, 256, 9.0, 2, 2, cl.CL_INT_YOSHIDA4, expansion=True, alpha=0.0, kappa=0.1, dt=0.005) as g:
+        # plain FP32: four arrays a row leave room for a fifth stage beside the same tile
+        assert g.cl_get_option(cl.CL_OPT_PASS_VARIANT) == 1
+        assert g.cl_get_option(cl.CL_OPT_STAGES) == 5
         assert g.cl_get_option(cl.CL_OPT_TILE_BY) == 7
         assert g.cl_get_option(cl.CL_OPT_TILE_DZ) == 64
         assert g.cl_get_option(cl.CL_OPT_GRAPH) == 1
