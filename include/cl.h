@@ -375,7 +375,9 @@ cl_status cl_get_option(cl_lattice* l, int32_t option, int64_t* value);
  * unchanged.  cache_path (may be NULL): a text file of earlier choices, one JSON object per
  * line, keyed by the lattice's shape, precision and field count; a hit applies the cached
  * choice without trials, a miss appends the new one.  best (may be NULL, else 5 doubles)
- * receives {stages, tile_by, tile_dz, microseconds per pass, pass variant}.  Errors: CL_EINVAL (Runge-Kutta or
+ * receives the tiling then in effect (as cl_get_option reports it: stages, 0 for the loader
+ * without TMA staging; tile_by; tile_dz, -1 for persistent ranges), the microseconds per trial
+ * pass and the pass variant: {stages, tile_by, tile_dz, us, variant}.  Errors: CL_EINVAL (Runge-Kutta or
  * gauge lattice), CL_ESTATE (no potential), CL_ECUDA. */
 cl_status cl_autotune(cl_lattice* l, const char* cache_path, double* best);
 

@@ -1727,6 +1727,19 @@ cl_status cl_set_option(cl_lattice* l, int32_t option, int64_t value)
 }
 
 // ---------------------------------------------------------------- autotuner
+// The tiling in effect (after the library's own choices for the 0 = "library choice" values
+// a candidate may carry) and the time per trial pass, into best[5].
+static void report_tiles(const cl_lattice* l, double us, double* best)
+{
+    if (!best) return;
+    const bool ens = is_ens(l);
+    best[0] = ens ? l->ens_stages : l->stages;
+    best[1] = ens ? l->hmem[0].BY : l->BY;
+    best[2] = ens ? l->hmem[0].DZ : l->DZ;
+    best[3] = us;
+    best[4] = ens ? l->ens_variant : l->variant;
+}
+
 static std::string tune_key(const cl_lattice* l)
 {
     char buf[256];
@@ -1801,7 +1814,7 @@ cl_status cl_autotune(cl_lattice* l, const char* cache_path, double* best)
             }
             fclose(f);
             if (hit && apply_tiles(l, st, by, dz, var) == CL_OK) {
-                if (best) { best[0] = st; best[1] = by; best[2] = dz; best[3] = us; best[4] = var; }
+                report_tiles(l, us, best);
                 l->diag_valid = false;
                 l->rbar_valid = false;
                 return CL_OK;
@@ -1859,7 +1872,7 @@ cl_status cl_autotune(cl_lattice* l, const char* cache_path, double* best)
             fclose(f);
         }
     }
-    if (best) { best[0] = best_c[0]; best[1] = best_c[1]; best[2] = best_c[2]; best[3] = best_us; best[4] = best_c[3]; }
+    report_tiles(l, best_us, best);
     return CL_OK;
 }
 

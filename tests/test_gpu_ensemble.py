@@ -260,7 +260,10 @@ def test_autotune_keeps_the_state_and_caches_its_choice(cl, tmp_path):
         before = [(g.cl_get_state(cl.CL_FIELD_PHI0, member=m), g.cl_get_state(cl.CL_FIELD_PI0, member=m),
                    g.cl_get_scalars(m)) for m in range(4)]
         stages, by, dz, us, variant = g.cl_autotune(cache)
-        assert us > 0 and stages in (-1, 2, 3, 4, 5, 6) and variant in (0, 1)
+        # the tiling in effect, as cl_get_option reports it (0: the loader without TMA staging)
+        assert us > 0 and stages in (0, 2, 3, 4, 5, 6) and variant in (0, 1)
+        assert (stages, by, dz, variant) == tuple(g.cl_get_option(o) for o in (
+            cl.CL_OPT_STAGES, cl.CL_OPT_TILE_BY, cl.CL_OPT_TILE_DZ, cl.CL_OPT_PASS_VARIANT))
         for m in range(4):
             assert np.array_equal(g.cl_get_state(cl.CL_FIELD_PHI0, member=m), before[m][0])
             assert np.array_equal(g.cl_get_state(cl.CL_FIELD_PI0, member=m), before[m][1])
@@ -292,6 +295,8 @@ def test_autotune_single_lattice(cl):
         stages, by, dz, us, variant = g.cl_autotune()
         assert us > 0 and variant in (0, 1)
         assert variant == 0 or 2 <= stages <= 5
+        assert (stages, by, dz, variant) == tuple(g.cl_get_option(o) for o in (
+            cl.CL_OPT_STAGES, cl.CL_OPT_TILE_BY, cl.CL_OPT_TILE_DZ, cl.CL_OPT_PASS_VARIANT))
         # the energies of the unchanged state, summed over another tiling (per-thread FP32 sums
         # of other sites): equal to their rounding
         assert g.cl_energies()["rho"] == pytest.approx(e0["rho"], rel=1e-9)
