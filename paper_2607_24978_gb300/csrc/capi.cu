@@ -1063,7 +1063,19 @@ cl_status run_u1_lf_t(cl_lattice* l, const PassCoef& pc, int s)
         if (ef != cudaSuccess) return fail(l, CL_ECUDA, "U(1) leapfrog launch failed: %s", cudaGetErrorString(ef));
         return CL_OK;
     }
-    cudaError_t e = l->u1_staged ? launch_u1_staged(prec, &A, 0, l->stream) : launch_u1(prec, &A, 0, l->stream);
+    int pq = 0;  // plaquette launch: 0 full, 3 the E-dependent fields only (staged form)
+    if (l->u1_staged) {
+        // the three passes of a step evaluate the force at the positions of the previous
+        // pass 1: its plaquette launch keeps sin P and cos P in arrays of their own (free
+        // auxiliary slots, untouched by the diagnostic launches), so passes 2 and 3 form only
+        // cos P dP/dt and the Chern-Simons sums
+        for (int i = 0; i < 3; ++i) {
+            A.sP[i] = (T*)l->ku1[2 + i][1];
+            A.cP[i] = (T*)l->ku1[2 + i][0];
+        }
+        pq = pc.lf == 1 ? 0 : 3;
+    }
+    cudaError_t e = l->u1_staged ? launch_u1_staged(prec, &A, pq, l->stream) : launch_u1(prec, &A, 0, l->stream);
     if (e == cudaSuccess && pc.lf == 2 && !l->u1_staged) {
         // Gauss tracking of the step's integer-time starting state (positions of s, the
         // plaquette fields just computed from them, momenta ku1[.][s]); the staged second

@@ -215,6 +215,11 @@ struct U1Args {
     //         + h dx E_out with a_1 = a + h a'; a = a_1, t += h, step += 1
     int lf;
     double le, lk, lb;
+    // cos P of every plaquette (normal k, lower corner n), saved by a plaquette launch when
+    // non-null; the staged "rates" launch (launch_u1_staged what 3) reads it back and forms
+    // only the fields that depend on E (cos P dP/dt and the Chern-Simons corner sums) for
+    // the same link angles, keeping sin P from the launch that saved it
+    T* cP[3];
 };
 // what: 0 = plaquette fields, 1 = stage (or energies with P_ENERGY_ONLY), 2 = Gauss diagnostic,
 // 3 = rms Gauss violation of the state into DevScal::gauss (the staged stage launch computes

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquettes(const U1Ar
             ring.acquire(j + 2);
             const U1SNb<T> S = ring.nb(j, lane, warp);
             const uint32_t n = ((t.z0 + j) * N + t.y0 + warp) * N + t.x0 + lane;
-            T o_s[3], o_r[3], o_z[3];
+            T o_s[3], o_r[3], o_z[3], o_c[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
@@ -286,6 +286,7 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquettes(const U1Ar
                 o_s[k] = sp;
                 o_r[k] = cp * R;
                 o_z[k] = cp * ((T)0.5 * qs);
+                o_c[k] = cp;
                 accGB.add((T)2 * sh * sh);
             }
             ring.release(j, lane);
@@ -294,6 +295,10 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquettes(const U1Ar
                 A.sP[k][n] = o_s[k];
                 A.rP[k][n] = o_r[k];
                 A.Z[k][n] = o_z[k];
+            }
+            if (A.cP[0]) {  // cos P, for the rates launches of the same link angles
+#pragma unroll
+                for (int k = 0; k < 3; ++k) A.cP[k][n] = o_c[k];
             }
         }
         ring.release((int)t.nz, lane);
@@ -307,6 +312,91 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquettes(const U1Ar
         A.partials[(size_t)gridDim.x * kMaxQ + blockIdx.x] = v[0];
         if (s_fail) atomicOr(&A.scal->status, ST_TIMEOUT);
     }
+}
+
+// The E-dependent plaquette fields of link angles whose cos P a plaquette launch saved
+// (A.cP): cos P dP/dt and cos P times the corner sum of phi Ebar_k, from the staged phi and E
+// (four arrays instead of seven, no trigonometry); sin P and the magnetic energy stay from
+// that launch.  The leapfrog's second and third passes evaluate the force at the positions
+// of the previous pass 1, whose plaquette launch saved cos P.
+enum { RQ_PHI = 0, RQ_E = 1, RQ_NA = 4 };
+
+template <typename T>
+__global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquette_rates(const U1Args<T> A)
+{
+    using G = U1SGeom<T>;
+    constexpr int NA = RQ_NA;
+    extern __shared__ __align__(128) unsigned char u1s_dyn[];
+    __shared__ const T* s_src[NA];
+    __shared__ __align__(8) uint64_t s_full[G::SLOTS], s_empty[G::SLOTS];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        s_src[RQ_PHI] = A.phi_in;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s_src[RQ_E + k] = A.E_in[k];
+        for (int k = 0; k < G::SLOTS; ++k) {
+            mbar_init(&s_full[k], G::PL);  // the producer lanes' copies
+            mbar_init(&s_empty[k], G::CW);
+        }
+        mbar_fence_init();
+        s_fail = 0;
+    }
+    __syncthreads();
+    const U1STile<T> t((uint32_t)A.N, (uint32_t)A.dz);
+    T* ring_sm = reinterpret_cast<T*>(u1s_dyn);
+    uint2* table = reinterpret_cast<uint2*>(ring_sm + G::SLOTS * NA * G::ARR);
+    u1s_build_units<T, NA>(table, t, tid, G::NT);
+    __syncthreads();
+    const U1SRing<T, NA> ring{ring_sm, table, s_full, s_empty, &s_fail};
+    if (warp >= G::CW) {
+        ring.produce(tid - 32 * G::CW, s_src, t);
+    } else {
+        const uint32_t N = t.N;
+        const T dx = (T)A.dx;
+        // cos P of the site's three plaquettes, loaded one plane ahead
+        T cc[3];
+        auto load_c = [&](uint32_t m) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cc[k] = A.cP[k][m];
+        };
+        load_c((t.z0 * N + t.y0 + warp) * N + t.x0 + lane);
+        ring.acquire(0);
+        ring.acquire(1);
+        for (int j = 0; j < (int)t.nz; ++j) {
+            ring.acquire(j + 2);
+            const U1SNb<T> S = ring.nb(j, lane, warp);
+            const uint32_t n = ((t.z0 + j) * N + t.y0 + warp) * N + t.x0 + lane;
+            const T cp3[3] = {cc[0], cc[1], cc[2]};
+            if (j + 1 < (int)t.nz) load_c(n + N * N);
+            T o_r[3], o_z[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+                const T R = dx * (S(RQ_E + k1, 0, 0, 0) + S(RQ_E + k2, U1S_E(k1, 1)) - S(RQ_E + k1, U1S_E(k2, 1)) -
+                                  S(RQ_E + k2, 0, 0, 0));
+                const int e1[3] = {U1S_E(k1, 1)}, e2[3] = {U1S_E(k2, 1)}, ek[3] = {U1S_E(k, 1)};
+                auto X = [&](int ox, int oy, int oz) {
+                    return S(RQ_PHI, ox, oy, oz) *
+                           (S(RQ_E + k, ox, oy, oz) + S(RQ_E + k, ox - ek[0], oy - ek[1], oz - ek[2]));
+                };
+                const T qs = X(0, 0, 0) + X(e1[0], e1[1], e1[2]) + X(e2[0], e2[1], e2[2]) +
+                             X(e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]);
+                o_r[k] = cp3[k] * R;
+                o_z[k] = cp3[k] * ((T)0.5 * qs);
+            }
+            ring.release(j, lane);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                A.rP[k][n] = o_r[k];
+                A.Z[k][n] = o_z[k];
+            }
+        }
+        ring.release((int)t.nz, lane);
+        ring.release((int)t.nz + 1, lane);
+    }
+    __syncthreads();  // producer and consumers meet; no copy is in flight past this point
+    if (tid == 0 && s_fail) atomicOr(&A.scal->status, ST_TIMEOUT);
 }
 
 // TRACK: the first stage of a step, which also sums the squared lattice Gauss charge of its
@@ -1031,6 +1121,17 @@ static cudaError_t launch_u1s_t(const U1Args<T>& A, int what, cudaStream_t s)
             attr[0] = true;
         }
         k_u1s_plaquettes<T><<<grid, G::NT, smem, s>>>(A);
+    } else if (what == 3) {
+        constexpr size_t smem = u1s_smem_bytes<T, RQ_NA>();
+        if (!A.cP[0] || !A.cP[1] || !A.cP[2]) return cudaErrorInvalidValue;
+        static DevFlag rattr;
+        if (!rattr) {
+            const cudaError_t e =
+                cudaFuncSetAttribute(k_u1s_plaquette_rates<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            rattr = true;
+        }
+        k_u1s_plaquette_rates<T><<<grid, G::NT, smem, s>>>(A);
     } else if (what == 2) {
         constexpr size_t smem = u1f_smem_bytes<T>();
         const int form = A.lf ? (A.lf == 2 ? 4 : 3) : ((A.flags & P_FIRST_STAGE) && !(A.flags & P_ENERGY_ONLY) ? 2 : 1);
