@@ -321,31 +321,34 @@ __global__ void __launch_bounds__(256) k_u1_gauss(const U1Args<T> A, int mode)
     __shared__ int s_last;
     const uint32_t N = (uint32_t)A.N;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const double ca = apow(A.scal->a, 1.0 - A.alpha);
-    const double b4 = 0.25 / (A.dx * A.dx);
+    // per-site arithmetic in the field precision (GB300's FP64 rate would make this
+    // diagnostic cost a millisecond at 192^3 in double), the maxima and sums in double
+    const T ca = (T)apow(A.scal->a, 1.0 - A.alpha);
+    const T b4 = (T)(0.25 / (A.dx * A.dx)), gh = (T)(0.5 * A.g);
     double gmax = 0.0, smax = 0.0, gsq = 0.0, e2 = 0.0;
     const U1Tile tile(N, (uint32_t)A.dz);
     for (uint32_t z = tile.z0; z < tile.z1; ++z) {
         if (!tile.active) break;
         const uint32_t n = (z * N + tile.y) * N + tile.x;
         const Nbhd s(tile.x, tile.y, z, N);
-        double G = 0.0, sc = 0.0;
+        T G = (T)0, sc = (T)0, ee = (T)0;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const Off op(i, 1), om(i, -1);
             const uint32_t np = s.at(op.o), nm = s.at(om.o);
-            const double Bn = b4 * (double)clover(A.sP[i], s, Off(), i);
-            const double Bp = b4 * (double)clover(A.sP[i], s, op, i);
-            const double Bm = b4 * (double)clover(A.sP[i], s, om, i);
-            const double Pn = ca * (double)A.E_in[i][n] + A.g * 0.5 * ((double)A.phi_in[n] * Bn + (double)A.phi_in[np] * Bp);
-            const double Pm = ca * (double)A.E_in[i][nm] + A.g * 0.5 * ((double)A.phi_in[nm] * Bm + (double)A.phi_in[n] * Bn);
+            const T Bn = b4 * clover(A.sP[i], s, Off(), i);
+            const T Bp = b4 * clover(A.sP[i], s, op, i);
+            const T Bm = b4 * clover(A.sP[i], s, om, i);
+            const T Pn = ca * A.E_in[i][n] + gh * (A.phi_in[n] * Bn + A.phi_in[np] * Bp);
+            const T Pm = ca * A.E_in[i][nm] + gh * (A.phi_in[nm] * Bm + A.phi_in[n] * Bn);
             G += Pn - Pm;
             sc += fabs(Pn) + fabs(Pm);
-            e2 += (double)A.E_in[i][n] * (double)A.E_in[i][n];
+            ee += A.E_in[i][n] * A.E_in[i][n];
         }
-        gmax = fmax(gmax, fabs(G) / A.dx);
-        smax = fmax(smax, sc / A.dx);
-        gsq += G * G;
+        gmax = fmax(gmax, fabs((double)G) / A.dx);
+        smax = fmax(smax, (double)sc / A.dx);
+        gsq += (double)G * (double)G;
+        e2 += (double)ee;
     }
     if (mode == 1) {  // sums in a fixed order, then the last block stores the tracked value
         double v[2] = {gsq, e2};
