@@ -298,6 +298,12 @@ U1_BYTES_PER_SITE_STAGE = 8 * 2 * 2 * 4
 # pass 3 the same and writes the positions too (20)
 U1_LF_PASSES = 3
 U1_LF_BYTES_PER_SITE_STEP = (16 + 16 + 20) * 4
+# what the staged launches of a step move per site, 4 B each (halo rows from L2 not counted):
+# the full plaquette launch reads phi, theta, E (7) and writes sin P, cos P, the rate and the
+# Chern-Simons field (12); each of the two rates launches reads phi, E, cos P (7) and writes 6;
+# the stage launches read their 14 staged arrays, passes 2 and 3 also the 4 base momenta and
+# pass 3 the 3 link angles it drifts, and write 8 (pass 1), 4 (pass 2) and 8 (pass 3)
+U1_LF_DESIGN_BYTES_PER_SITE_STEP = (7 + 12 + 2 * (7 + 6) + (14 + 8) + (14 + 4 + 4) + (14 + 4 + 3 + 8)) * 4
 RK_STAGES = 5
 # GW pass per site: the scalars the scalar pass just drifted, two fields read (8 B), and the
 # five auxiliaries and their momenta read and written (2 x 10 x 4 B), FP32
@@ -378,7 +384,9 @@ def run_u1_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                              "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
                              "kernel": kern + ", per step", "tile_dz": u1_dz,
-                             "algorithmic_bytes_per_step": bytes_step},
+                             "algorithmic_bytes_per_step": bytes_step,
+                             "launch_bytes_per_step": N ** 3 * U1_LF_DESIGN_BYTES_PER_SITE_STEP,
+                             "launch_bytes_frac": N ** 3 * U1_LF_DESIGN_BYTES_PER_SITE_STEP / step_s / 1e9 / hbm_peak},
                 "gpu_launches": launches, "clocks": clocks, "energies_end": energies_end,
                 "gauss_tracking": "rms lattice Gauss charge of every step's integer-time starting state, summed by "
                                   "the second pass of the step (staged form) inside the timed steps"}
