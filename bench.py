@@ -296,6 +296,11 @@ U1_BYTES_PER_SITE_STAGE = 8 * 2 * 2 * 4
 # writes the integer-time momenta and the first iterate (16 arrays); pass 2 reads the
 # positions, the iterate and the integer-time momenta and writes the next iterate (16);
 # pass 3 the same and writes the positions too (20)
+# what the staged launches of one RK stage move per site, 4 B each: the plaquette launch reads
+# phi, theta, E (7) and writes sin P, the rate and the Chern-Simons field (9); the stage reads
+# its 14 staged arrays, theta and the 8 auxiliaries at the site (11; the first stage reads no
+# auxiliaries) and writes the 8 degrees of freedom and their 8 auxiliaries
+U1_RK_DESIGN_BYTES_PER_SITE_STAGE = (7 + 9 + 14 + 11 + 16) * 4
 U1_LF_PASSES = 3
 U1_LF_BYTES_PER_SITE_STEP = (16 + 16 + 20) * 4
 # what the staged launches of a step move per site, 4 B each (halo rows from L2 not counted):
@@ -406,7 +411,10 @@ def run_u1_workload(args, world, rank, local, cl, torch, stream, hbm_peak, peak_
                          "kernel": {1: "k_u1_fused<float> (one launch per RK stage)",
                                     2: "one RK stage: k_u1s_plaquettes + k_u1s_stage (staged neighbourhoods)"}.get(
                                         variant, "one RK stage: k_u1_plaquettes + k_u1_stage"), "tile_dz": u1_dz,
-                         "algorithmic_bytes_per_launch": bytes_stage},
+                         "algorithmic_bytes_per_launch": bytes_stage,
+                         "launch_bytes_per_step": N ** 3 * (U1_STAGES * U1_RK_DESIGN_BYTES_PER_SITE_STAGE - 8 * 4),
+                         "launch_bytes_frac": N ** 3 * (U1_STAGES * U1_RK_DESIGN_BYTES_PER_SITE_STAGE - 8 * 4) /
+                                              (stage_s * U1_STAGES) / 1e9 / hbm_peak},
             "gpu_launches": launches, "clocks": clocks, "energies_end": energies_end,
             "gauss_tracking": "rms lattice Gauss charge of every step's starting state, summed in the first RK "
                               "stage (staged form) inside the timed steps"}
