@@ -8,8 +8,9 @@
 // The gather kernels of u1_stage.cu read 40 to 110 neighbour values per site from L1/L2
 // into registers; a thread can only keep as many loads in flight as it has registers, and
 // both kernels stall on memory latency at a fraction of the HBM bandwidth.  Here a block
-// owns a 32 x TY tile of (x, y) (TY = 16 in FP32, 8 in FP64; one site per consumer thread)
-// and marches up its z chunk with planes z-1, z, z+1 of every array that is read at a
+// owns a 32 x TY tile of (x, y) (stage launches: TY = 16 in FP32, 8 in FP64; plaquette
+// launches, which stage fewer arrays: twice that, over half the z chunk, so that both
+// launch the same blocks; one site per consumer thread) and marches up its z chunk with planes z-1, z, z+1 of every array that is read at a
 // neighbour in shared memory: rows y0-1 .. y0+TY and columns x0-VE .. x0+31+VE (VE elements
 // per 16 bytes, so that every row is whole 16-byte units; only the first and last columns
 // are read).  Warp roles, synchronised by mbarriers only:
@@ -34,12 +35,18 @@
 
 namespace clk {
 
-template <typename T>
-struct U1SGeom {
+// Tile geometry: TX x TY sites a block, RW tile rows a consumer warp (rows w, w + CW, ...),
+// PWARPS producer warps; SPLIT z parts of every z chunk of the stage grid, so that a geometry
+// with SPLIT times taller tiles launches the same number of blocks over the same chunks.
+template <typename T_, int TY_, int PWARPS_, int SPLIT_, int RW_>
+struct U1SGeomT {
+    using T = T_;
     static constexpr int TX = 32;
-    static constexpr int TY = sizeof(T) == 4 ? 16 : 8;
-    static constexpr int CW = TY;              // consumer warps: one tile row each
-    static constexpr int PWARPS = 6;           // producer warps
+    static constexpr int TY = TY_;
+    static constexpr int RW = RW_;
+    static constexpr int CW = TY / RW;         // consumer warps
+    static constexpr int PWARPS = PWARPS_;     // producer warps
+    static constexpr int SPLIT = SPLIT_;
     static constexpr int PL = 32 * PWARPS;     // producer lanes
     static constexpr int NT = 32 * (CW + PWARPS);  // threads of a block (consumers, then the producers)
     static constexpr int VE = 16 / (int)sizeof(T);
@@ -48,31 +55,48 @@ struct U1SGeom {
     static constexpr int ARR = PH * PW;        // elements of one array plane
     static constexpr int CPR = PW / VE;        // 16-byte units of a staged row
     static constexpr int SLOTS = 5;
+    static_assert(TY % RW == 0 && NT <= 1024, "tile rows a warp; threads a block");
 };
+
+// the stage launches: 32 x 16 tiles in FP32, 32 x 8 in FP64, six producer warps
+template <typename T>
+using U1SGeom = U1SGeomT<T, sizeof(T) == 4 ? 16 : 8, 6, 1, 1>;
+// the plaquette launches, which stage half as many arrays: tiles twice as tall over half z
+// chunks, six producer warps, and in FP32 two sites a consumer thread (two independent
+// chains of shared-memory loads and trigonometry; measured at 192^3 FP32 with one site a
+// thread in 32 x 16 tiles: 113 us a launch, 61% of the issue slots active; two sites a
+// thread with four producer warps: 121 us, the consumers waiting on the copies)
+template <typename T>
+using U1PGeom = U1SGeomT<T, 2 * U1SGeom<T>::TY, 6, 2, sizeof(T) == 4 ? 2 : 1>;
 
 // arrays staged by the plaquette launch and by the stage launch, in slot order
 enum { PQ_PHI = 0, PQ_TH = 1, PQ_E = 4, PQ_NA = 7 };
 enum { SG_PHI = 0, SG_PI = 1, SG_E = 2, SG_SP = 5, SG_RP = 8, SG_Z = 11, SG_NA = 14 };
 
 // 16-byte units of one staged plane of NA arrays, and the producer lanes' share of them
-template <typename T, int NA>
+template <typename G, int NA>
 struct U1SUnits {
-    static constexpr int CH = NA * U1SGeom<T>::PH * U1SGeom<T>::CPR;
-    static constexpr int PER_LANE = (CH + U1SGeom<T>::PL - 1) / U1SGeom<T>::PL;
+    static constexpr int CH = NA * G::PH * G::CPR;
+    static constexpr int PER_LANE = (CH + G::PL - 1) / G::PL;
 };
 
 // dynamic shared memory: the ring of plane slots, then the unit table (two words a unit)
-template <typename T, int NA>
+template <typename G, int NA>
 constexpr size_t u1s_smem_bytes()
 {
-    return (size_t)U1SGeom<T>::SLOTS * NA * U1SGeom<T>::ARR * sizeof(T) +
-           (size_t)U1SGeom<T>::PL * U1SUnits<T, NA>::PER_LANE * 8;
+    return (size_t)G::SLOTS * NA * G::ARR * sizeof(typename G::T) + (size_t)G::PL * U1SUnits<G, NA>::PER_LANE * 8;
 }
+// (every launch's dynamic shared memory, with 2 KB for its static arrays, fits one block)
+static_assert(u1s_smem_bytes<U1PGeom<float>, PQ_NA>() + 2048 <= (size_t)kPassMaxSmem, "plaquette ring (FP32)");
+static_assert(u1s_smem_bytes<U1PGeom<double>, PQ_NA>() + 2048 <= (size_t)kPassMaxSmem, "plaquette ring (FP64)");
+static_assert(u1s_smem_bytes<U1SGeom<float>, SG_NA>() + 2048 <= (size_t)kPassMaxSmem, "stage ring (FP32)");
+static_assert(u1s_smem_bytes<U1SGeom<double>, SG_NA>() + 2048 <= (size_t)kPassMaxSmem, "stage ring (FP64)");
 
-// Tile and z chunk of this block.
-template <typename T>
+// Tile and z range of this block: part bz % SPLIT of the z chunk bz / SPLIT (dz planes; the
+// last chunk may be shorter).  A part may be empty (nz = 0) when its chunk has fewer planes
+// than SPLIT; its block stages the two halo planes and writes nothing.
+template <typename G>
 struct U1STile {
-    using G = U1SGeom<T>;
     uint32_t N, x0, y0, z0, nz;
     __device__ __forceinline__ U1STile(uint32_t N_, uint32_t dz) : N(N_)
     {
@@ -83,19 +107,21 @@ struct U1STile {
         const uint32_t by = b % nty, bz = b / nty;
         x0 = bx * G::TX;
         y0 = by * G::TY;
-        z0 = bz * dz;
-        nz = z0 + dz < N ? dz : N - z0;
+        const uint32_t c0 = (bz / G::SPLIT) * dz;
+        const uint32_t cn = c0 + dz < N ? dz : N - c0;
+        const uint32_t per = (cn + G::SPLIT - 1) / G::SPLIT, skip = (bz % G::SPLIT) * per;
+        z0 = c0 + skip;
+        nz = cn > skip ? (cn - skip < per ? cn - skip : per) : 0u;
     }
 };
 
 // Unit table of the producer lanes: unit i of lane l (l + 32 i of the plane) is array a at
 // staged row r, 16-byte column unit u; its entry holds (a << 16 | element offset in the slot)
 // and the element offset of its source in a plane of the array (periodic wrap applied).
-template <typename T, int NA>
-__device__ __forceinline__ void u1s_build_units(uint2* table, const U1STile<T>& t, int tid, int nthr)
+template <typename G, int NA>
+__device__ __forceinline__ void u1s_build_units(uint2* table, const U1STile<G>& t, int tid, int nthr)
 {
-    using G = U1SGeom<T>;
-    using U = U1SUnits<T, NA>;
+    using U = U1SUnits<G, NA>;
     const int N = (int)t.N;
     for (int e = tid; e < G::PL * U::PER_LANE; e += nthr) {
         const int lane = e % G::PL, i = e / G::PL, c = lane + G::PL * i;
@@ -127,26 +153,26 @@ __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar)
 
 // Producer lane: its units of plane z0 - 1 + q (periodic) of the arrays src[] into slot,
 // arriving on full when they have landed.
-template <typename T, int NA>
+template <typename G, int NA, typename T = typename G::T>
 __device__ __forceinline__ void u1s_copy_plane(int lane, T* slot, const T* const* src, const uint2* table,
-                                               const U1STile<T>& t, int q, uint64_t* full)
+                                               const U1STile<G>& t, int q, uint64_t* full)
 {
     const int N = (int)t.N;
     int z = (int)t.z0 - 1 + q;
     z = z < 0 ? z + N : (z >= N ? z - N : z);
     const size_t zoff = (size_t)z * t.N * t.N;
 #pragma unroll 4
-    for (int i = 0; i < U1SUnits<T, NA>::PER_LANE; ++i) {
-        const uint2 v = table[i * U1SGeom<T>::PL + lane];
+    for (int i = 0; i < U1SUnits<G, NA>::PER_LANE; ++i) {
+        const uint2 v = table[i * G::PL + lane];
         if (v.x != 0xffffffffu) cp_async16_cg(slot + (v.x & 0xffffu), src[v.x >> 16] + zoff + v.y);
     }
     cp_async_arrive_noinc(full);
 }
 
 // Neighbourhood of a consumer's site in the three staged planes (z-1, z, z+1).
-template <typename T>
+template <typename G>
 struct U1SNb {
-    using G = U1SGeom<T>;
+    using T = typename G::T;
     const T* p[3];
     __device__ __forceinline__ T operator()(int a, int ox, int oy, int oz) const
     {
@@ -170,9 +196,9 @@ struct U1SNb {
 // Ring bookkeeping shared by both kernels: the producer loop and the consumers' waits and
 // releases.  Plane q of the chunk lives in slot q % SLOTS; consumers read planes j, j+1, j+2
 // for output plane j and release plane j afterwards (the last two planes after the loop).
-template <typename T, int NA>
+template <typename G, int NA>
 struct U1SRing {
-    using G = U1SGeom<T>;
+    using T = typename G::T;
     static constexpr size_t SLOT = (size_t)NA * G::ARR;
     T* sm;
     const uint2* table;
@@ -186,13 +212,13 @@ struct U1SRing {
         return false;
     }
     // producer warp: every plane of the chunk
-    __device__ __forceinline__ void produce(int lane, const T* const* src, const U1STile<T>& t) const
+    __device__ __forceinline__ void produce(int lane, const T* const* src, const U1STile<G>& t) const
     {
         const int nq = (int)t.nz + 2;
         for (int q = 0; q < nq; ++q) {
             const int st = q % G::SLOTS;
             if (q >= G::SLOTS) wait(&empty[st], (uint32_t)((q / G::SLOTS - 1) & 1));
-            u1s_copy_plane<T, NA>(lane, sm + st * SLOT, src, table, t, q, &full[st]);
+            u1s_copy_plane<G, NA>(lane, sm + st * SLOT, src, table, t, q, &full[st]);
         }
         // copies still in flight (only after a timeout, when consumers stopped waiting)
         if (*fail && lane == 0)
@@ -206,10 +232,10 @@ struct U1SRing {
         if (lane == 0) mbar_arrive(&empty[q % G::SLOTS]);
     }
     // the three planes of output plane j at the consumer's site (row ly, column lx)
-    __device__ __forceinline__ U1SNb<T> nb(int j, int lx, int ly) const
+    __device__ __forceinline__ U1SNb<G> nb(int j, int lx, int ly) const
     {
         const int t0 = (ly + 1) * G::PW + lx + G::VE;
-        U1SNb<T> n;
+        U1SNb<G> n;
 #pragma unroll
         for (int i = 0; i < 3; ++i) n.p[i] = sm + ((j + i) % G::SLOTS) * SLOT + t0;
         return n;
@@ -220,14 +246,14 @@ struct U1SRing {
 #define U1S_E(d, s) ((d) == 0 ? (s) : 0), ((d) == 1 ? (s) : 0), ((d) == 2 ? (s) : 0)
 
 template <typename T>
-__global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquettes(const U1Args<T> A)
+__global__ void __launch_bounds__(U1PGeom<T>::NT, 1) k_u1s_plaquettes(const U1Args<T> A)
 {
-    using G = U1SGeom<T>;
+    using G = U1PGeom<T>;
     constexpr int NA = PQ_NA;
     extern __shared__ __align__(128) unsigned char u1s_dyn[];
     __shared__ const T* s_src[NA];
     __shared__ __align__(8) uint64_t s_full[G::SLOTS], s_empty[G::SLOTS];
-    __shared__ double s_red[32][kMaxQ];
+    __shared__ double s_red[G::NT / 32][kMaxQ];  // a row for every warp; the sum takes the consumers'
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -245,12 +271,12 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquettes(const U1Ar
         s_fail = 0;
     }
     __syncthreads();
-    const U1STile<T> t((uint32_t)A.N, (uint32_t)A.dz);
+    const U1STile<G> t((uint32_t)A.N, (uint32_t)A.dz);
     T* ring_sm = reinterpret_cast<T*>(u1s_dyn);
     uint2* table = reinterpret_cast<uint2*>(ring_sm + G::SLOTS * NA * G::ARR);
-    u1s_build_units<T, NA>(table, t, tid, G::NT);
+    u1s_build_units<G, NA>(table, t, tid, G::NT);
     __syncthreads();
-    const U1SRing<T, NA> ring{ring_sm, table, s_full, s_empty, &s_fail};
+    const U1SRing<G, NA> ring{ring_sm, table, s_full, s_empty, &s_fail};
     Acc<T> accGB;
     if (warp >= G::CW) {
         ring.produce(tid - 32 * G::CW, s_src, t);
@@ -261,11 +287,12 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquettes(const U1Ar
         ring.acquire(1);
         for (int j = 0; j < (int)t.nz; ++j) {
             ring.acquire(j + 2);
-            const U1SNb<T> S = ring.nb(j, lane, warp);
-            const uint32_t n = ((t.z0 + j) * N + t.y0 + warp) * N + t.x0 + lane;
-            T o_s[3], o_r[3], o_z[3], o_c[3];
+            T o_s[G::RW][3], o_r[G::RW][3], o_z[G::RW][3], o_c[G::RW][3];
+#pragma unroll
+            for (int r = 0; r < G::RW; ++r)
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
+                const U1SNb<G> S = ring.nb(j, lane, warp + r * G::CW);
                 const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
                 const T P = S(PQ_TH + k1, 0, 0, 0) + S(PQ_TH + k2, U1S_E(k1, 1)) - S(PQ_TH + k1, U1S_E(k2, 1)) -
                             S(PQ_TH + k2, 0, 0, 0);
@@ -283,22 +310,23 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquettes(const U1Ar
                 };
                 const T qs = X(0, 0, 0) + X(e1[0], e1[1], e1[2]) + X(e2[0], e2[1], e2[2]) +
                              X(e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]);
-                o_s[k] = sp;
-                o_r[k] = cp * R;
-                o_z[k] = cp * ((T)0.5 * qs);
-                o_c[k] = cp;
+                o_s[r][k] = sp;
+                o_r[r][k] = cp * R;
+                o_z[r][k] = cp * ((T)0.5 * qs);
+                o_c[r][k] = cp;
                 accGB.add((T)2 * sh * sh);
             }
             ring.release(j, lane);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                A.sP[k][n] = o_s[k];
-                A.rP[k][n] = o_r[k];
-                A.Z[k][n] = o_z[k];
-            }
-            if (A.cP[0]) {  // cos P, for the rates launches of the same link angles
+            for (int r = 0; r < G::RW; ++r) {
+                const uint32_t n = ((t.z0 + j) * N + t.y0 + warp + r * G::CW) * N + t.x0 + lane;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) A.cP[k][n] = o_c[k];
+                for (int k = 0; k < 3; ++k) {
+                    A.sP[k][n] = o_s[r][k];
+                    A.rP[k][n] = o_r[r][k];
+                    A.Z[k][n] = o_z[r][k];
+                    if (A.cP[0]) A.cP[k][n] = o_c[r][k];  // cos P, for the rates launches of the same link angles
+                }
             }
         }
         ring.release((int)t.nz, lane);
@@ -307,7 +335,7 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquettes(const U1Ar
     __syncthreads();  // producer and consumers meet; no copy is in flight past this point
     double v[1];
     const Acc<T>* av[1] = {&accGB};
-    block_reduce_acc<T, 1>(av, v, s_red, tid, G::NT);
+    block_reduce_acc<T, 1>(av, v, s_red, tid, 32 * G::CW);  // (the producers' sums are zero)
     if (tid == 0) {
         A.partials[(size_t)gridDim.x * kMaxQ + blockIdx.x] = v[0];
         if (s_fail) atomicOr(&A.scal->status, ST_TIMEOUT);
@@ -322,9 +350,9 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquettes(const U1Ar
 enum { RQ_PHI = 0, RQ_E = 1, RQ_NA = 4 };
 
 template <typename T>
-__global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquette_rates(const U1Args<T> A)
+__global__ void __launch_bounds__(U1PGeom<T>::NT, 1) k_u1s_plaquette_rates(const U1Args<T> A)
 {
-    using G = U1SGeom<T>;
+    using G = U1PGeom<T>;
     constexpr int NA = RQ_NA;
     extern __shared__ __align__(128) unsigned char u1s_dyn[];
     __shared__ const T* s_src[NA];
@@ -343,35 +371,43 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquette_rates(const
         s_fail = 0;
     }
     __syncthreads();
-    const U1STile<T> t((uint32_t)A.N, (uint32_t)A.dz);
+    const U1STile<G> t((uint32_t)A.N, (uint32_t)A.dz);
     T* ring_sm = reinterpret_cast<T*>(u1s_dyn);
     uint2* table = reinterpret_cast<uint2*>(ring_sm + G::SLOTS * NA * G::ARR);
-    u1s_build_units<T, NA>(table, t, tid, G::NT);
+    u1s_build_units<G, NA>(table, t, tid, G::NT);
     __syncthreads();
-    const U1SRing<T, NA> ring{ring_sm, table, s_full, s_empty, &s_fail};
+    const U1SRing<G, NA> ring{ring_sm, table, s_full, s_empty, &s_fail};
     if (warp >= G::CW) {
         ring.produce(tid - 32 * G::CW, s_src, t);
     } else {
         const uint32_t N = t.N;
         const T dx = (T)A.dx;
-        // cos P of the site's three plaquettes, loaded one plane ahead
-        T cc[3];
+        // cos P of the sites' three plaquettes, loaded one plane ahead
+        T cc[G::RW][3];
         auto load_c = [&](uint32_t m) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) cc[k] = A.cP[k][m];
+            for (int r = 0; r < G::RW; ++r)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) cc[r][k] = A.cP[k][m + (uint32_t)(r * G::CW) * N];
         };
-        load_c((t.z0 * N + t.y0 + warp) * N + t.x0 + lane);
+        if (t.nz > 0) load_c((t.z0 * N + t.y0 + warp) * N + t.x0 + lane);
         ring.acquire(0);
         ring.acquire(1);
         for (int j = 0; j < (int)t.nz; ++j) {
             ring.acquire(j + 2);
-            const U1SNb<T> S = ring.nb(j, lane, warp);
-            const uint32_t n = ((t.z0 + j) * N + t.y0 + warp) * N + t.x0 + lane;
-            const T cp3[3] = {cc[0], cc[1], cc[2]};
+            const uint32_t n = ((t.z0 + j) * N + t.y0 + warp) * N + t.x0 + lane;  // row warp; row warp + r CW at + r CW N
+            T cp3[G::RW][3];
+#pragma unroll
+            for (int r = 0; r < G::RW; ++r)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) cp3[r][k] = cc[r][k];
             if (j + 1 < (int)t.nz) load_c(n + N * N);
-            T o_r[3], o_z[3];
+            T o_r[G::RW][3], o_z[G::RW][3];
+#pragma unroll
+            for (int r = 0; r < G::RW; ++r)
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
+                const U1SNb<G> S = ring.nb(j, lane, warp + r * G::CW);
                 const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
                 const T R = dx * (S(RQ_E + k1, 0, 0, 0) + S(RQ_E + k2, U1S_E(k1, 1)) - S(RQ_E + k1, U1S_E(k2, 1)) -
                                   S(RQ_E + k2, 0, 0, 0));
@@ -382,15 +418,17 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_plaquette_rates(const
                 };
                 const T qs = X(0, 0, 0) + X(e1[0], e1[1], e1[2]) + X(e2[0], e2[1], e2[2]) +
                              X(e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]);
-                o_r[k] = cp3[k] * R;
-                o_z[k] = cp3[k] * ((T)0.5 * qs);
+                o_r[r][k] = cp3[r][k] * R;
+                o_z[r][k] = cp3[r][k] * ((T)0.5 * qs);
             }
             ring.release(j, lane);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                A.rP[k][n] = o_r[k];
-                A.Z[k][n] = o_z[k];
-            }
+            for (int r = 0; r < G::RW; ++r)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    A.rP[k][n + (uint32_t)(r * G::CW) * N] = o_r[r][k];
+                    A.Z[k][n + (uint32_t)(r * G::CW) * N] = o_z[r][k];
+                }
         }
         ring.release((int)t.nz, lane);
         ring.release((int)t.nz + 1, lane);
@@ -447,12 +485,12 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
         s_fail = 0;
     }
     __syncthreads();
-    const U1STile<T> t((uint32_t)A.N, (uint32_t)A.dz);
+    const U1STile<G> t((uint32_t)A.N, (uint32_t)A.dz);
     T* ring_sm = reinterpret_cast<T*>(u1s_dyn);
     uint2* table = reinterpret_cast<uint2*>(ring_sm + G::SLOTS * NA * G::ARR);
-    u1s_build_units<T, NA>(table, t, tid, G::NT);
+    u1s_build_units<G, NA>(table, t, tid, G::NT);
     __syncthreads();
-    const U1SRing<T, NA> ring{ring_sm, table, s_full, s_empty, &s_fail};
+    const U1SRing<G, NA> ring{ring_sm, table, s_full, s_empty, &s_fail};
     const uint32_t N = t.N, V = N * N * N;
     Acc<T> accK, accG, accV, accKE, accGs;
     if (warp >= G::CW) {
@@ -491,7 +529,7 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1s_stage(const U1Args<T>
         ring.acquire(1);
         for (int j = 0; j < (int)t.nz; ++j) {
             ring.acquire(j + 2);
-            const U1SNb<T> S = ring.nb(j, lane, warp);
+            const U1SNb<G> S = ring.nb(j, lane, warp);
             const uint32_t n = ((t.z0 + j) * N + t.y0 + warp) * N + t.x0 + lane;
             T thv[3], kv[8];
 #pragma unroll
@@ -709,7 +747,7 @@ struct U1FPq {
 template <typename T>
 constexpr size_t u1f_smem_bytes()
 {
-    return u1s_smem_bytes<T, 8>() + (size_t)U1FPq<T>::NSLOT * U1FPq<T>::SLOT * sizeof(T);
+    return u1s_smem_bytes<U1SGeom<T>, 8>() + (size_t)U1FPq<T>::NSLOT * U1FPq<T>::SLOT * sizeof(T);
 }
 
 enum { FR_PHI = 0, FR_PI = 1, FR_TH = 2, FR_E = 5, FR_NA = 8 };
@@ -717,12 +755,12 @@ enum { FR_PHI = 0, FR_PI = 1, FR_TH = 2, FR_E = 5, FR_NA = 8 };
 // Raw staged planes c - 1, c, c + 1 (chunk-relative plane indices) around the point at tile
 // offset (lx, ly) (lx in -VE .. TX + VE - 1, ly in -1 .. TY).
 template <typename T>
-__device__ __forceinline__ U1SNb<T> u1f_raw(const T* ring, int c, int lx, int ly)
+__device__ __forceinline__ U1SNb<U1SGeom<T>> u1f_raw(const T* ring, int c, int lx, int ly)
 {
     using G = U1SGeom<T>;
     constexpr size_t SL = (size_t)FR_NA * G::ARR;
     const int t0 = (ly + 1) * G::PW + lx + G::VE;
-    U1SNb<T> n;
+    U1SNb<U1SGeom<T>> n;
 #pragma unroll
     for (int i = 0; i < 3; ++i) n.p[i] = ring + ((c - 1 + i + G::SLOTS) % G::SLOTS) * SL + t0;
     return n;
@@ -774,7 +812,7 @@ __device__ __forceinline__ void u1f_plaquettes(T* pq, const T* ring, int c, bool
     T* slot = pq + (c % P::NSLOT) * P::SLOT + (K * 3) * P::PLANE;
     for (int w = ctid; w < W * H; w += NT) {
         const int xo = w % W, yo = w / W;
-        const U1SNb<T> S = u1f_raw<T>(ring, c, xo - 1, yo - 1);
+        const U1SNb<U1SGeom<T>> S = u1f_raw<T>(ring, c, xo - 1, yo - 1);
         const T Pl = S(FR_TH + K1, 0, 0, 0) + S(FR_TH + K2, e1x, e1y, e1z) - S(FR_TH + K1, e2x, e2y, e2z) -
                      S(FR_TH + K2, 0, 0, 0);
         const T R = dx * (S(FR_E + K1, 0, 0, 0) + S(FR_E + K2, e1x, e1y, e1z) - S(FR_E + K1, e2x, e2y, e2z) -
@@ -849,13 +887,13 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1f_stage(const U1Args<T>
         s_fail = 0;
     }
     __syncthreads();
-    const U1STile<T> t((uint32_t)A.N, (uint32_t)A.dz);
+    const U1STile<G> t((uint32_t)A.N, (uint32_t)A.dz);
     T* ring_sm = reinterpret_cast<T*>(u1s_dyn);
     uint2* table = reinterpret_cast<uint2*>(ring_sm + G::SLOTS * NA * G::ARR);
-    T* pq = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(u1s_dyn) + u1s_smem_bytes<T, NA>());
-    u1s_build_units<T, NA>(table, t, tid, G::NT);
+    T* pq = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(u1s_dyn) + u1s_smem_bytes<G, NA>());
+    u1s_build_units<G, NA>(table, t, tid, G::NT);
     __syncthreads();
-    const U1SRing<T, NA> ring{ring_sm, table, s_full, s_empty, &s_fail};
+    const U1SRing<G, NA> ring{ring_sm, table, s_full, s_empty, &s_fail};
     const uint32_t N = t.N, V = N * N * N;
     Acc<T> accK, accG, accV, accKE, accGs, accGB;
     if (warp >= G::CW) {
@@ -900,7 +938,7 @@ __global__ void __launch_bounds__(U1SGeom<T>::NT, 1) k_u1f_stage(const U1Args<T>
             u1f_plaquettes<T, 1>(pq, ring_sm, j + 1, true, true, dx, tid, accGB);
             u1f_plaquettes<T, 2>(pq, ring_sm, j + 2, true, j + 1 < nz, dx, tid, accGB);
             u1f_consumer_barrier(32 * G::CW);
-            const U1SNb<T> S = u1f_raw<T>(ring_sm, j + 1, lane, warp);
+            const U1SNb<U1SGeom<T>> S = u1f_raw<T>(ring_sm, j + 1, lane, warp);
             const U1FQ<T> Q{pq, j + 1, lane, warp};
             const uint32_t n = ((t.z0 + j) * N + t.y0 + warp) * N + t.x0 + lane;
             T kv[8];
@@ -1113,16 +1151,16 @@ static cudaError_t launch_u1s_t(const U1Args<T>& A, int what, cudaStream_t s)
     const int grid = u1_staged_blocks(sizeof(T) == 8 ? CL_PREC_FP64 : CL_PREC_FP32, A.N, A.dz);
     static DevFlag attr[5];
     if (what == 0) {
-        constexpr size_t smem = u1s_smem_bytes<T, PQ_NA>();
+        constexpr size_t smem = u1s_smem_bytes<U1PGeom<T>, PQ_NA>();
         if (!attr[0]) {
             const cudaError_t e =
                 cudaFuncSetAttribute(k_u1s_plaquettes<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             attr[0] = true;
         }
-        k_u1s_plaquettes<T><<<grid, G::NT, smem, s>>>(A);
+        k_u1s_plaquettes<T><<<grid, U1PGeom<T>::NT, smem, s>>>(A);
     } else if (what == 3) {
-        constexpr size_t smem = u1s_smem_bytes<T, RQ_NA>();
+        constexpr size_t smem = u1s_smem_bytes<U1PGeom<T>, RQ_NA>();
         if (!A.cP[0] || !A.cP[1] || !A.cP[2]) return cudaErrorInvalidValue;
         static DevFlag rattr;
         if (!rattr) {
@@ -1131,7 +1169,7 @@ static cudaError_t launch_u1s_t(const U1Args<T>& A, int what, cudaStream_t s)
             if (e != cudaSuccess) return e;
             rattr = true;
         }
-        k_u1s_plaquette_rates<T><<<grid, G::NT, smem, s>>>(A);
+        k_u1s_plaquette_rates<T><<<grid, U1PGeom<T>::NT, smem, s>>>(A);
     } else if (what == 2) {
         constexpr size_t smem = u1f_smem_bytes<T>();
         const int form = A.lf ? (A.lf == 2 ? 4 : 3) : ((A.flags & P_FIRST_STAGE) && !(A.flags & P_ENERGY_ONLY) ? 2 : 1);
@@ -1151,7 +1189,7 @@ static cudaError_t launch_u1s_t(const U1Args<T>& A, int what, cudaStream_t s)
         else if (form == 2) k_u1f_stage<T, true, false><<<grid, G::NT, smem, s>>>(A);
         else k_u1f_stage<T, false, false><<<grid, G::NT, smem, s>>>(A);
     } else {
-        constexpr size_t smem = u1s_smem_bytes<T, SG_NA>();
+        constexpr size_t smem = u1s_smem_bytes<U1SGeom<T>, SG_NA>();
         // forms: 1 a Runge-Kutta stage, 2 the first stage of a step (Gauss tracking), 3 a
         // leapfrog pass, 4 the leapfrog's second pass (Gauss tracking)
         const int form = A.lf ? (A.lf == 2 ? 4 : 3) : ((A.flags & P_FIRST_STAGE) && !(A.flags & P_ENERGY_ONLY) ? 2 : 1);
