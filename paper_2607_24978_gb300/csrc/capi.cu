@@ -84,6 +84,8 @@ struct cl_lattice {
     bool u1_fused = false;          // U(1) stage as one fused launch (plaquettes in shared memory)
     bool u1_staged = false;         // U(1) launches with shared-memory staged neighbourhoods
     bool u1_sfused = false;         //   as one launch, the plaquette fields in shared memory
+    bool u1_lf_pq = false;          // axion-U(1) leapfrog: sin P, cos P of the current positions
+                                    //   saved by a staged pass (ku1 slots 2..4)
     int dims = 3;                   // spatial dimensions (1, 2: reduced lattice of N^dims sites)
     int red_grid = 1;               // blocks of the reduced-lattice kernels
     int red_dy = 0, red_pgrid = 0;  // (2+1) row-marching pass: rows per chunk and blocks (0: not used)
@@ -1050,6 +1052,10 @@ cl_status run_u1(cl_lattice* l, int what, double cA, double cB, int flags, int i
 template <typename T>
 cl_status run_u1_lf_t(cl_lattice* l, const PassCoef& pc, int s)
 {
+    // sin P and cos P saved by the previous pass (invalid after any other form's pass, e.g.
+    // when the pass variant changed with the leapfrog open)
+    const bool pq_saved = l->u1_lf_pq;
+    l->u1_lf_pq = false;
     U1Args<T> A{};
     u1_fill(l, A, s, s ^ 1);
     const int pin = pc.lf == 2 ? (s ^ 1) : s;
@@ -1085,7 +1091,7 @@ cl_status run_u1_lf_t(cl_lattice* l, const PassCoef& pc, int s)
             A.sP[i] = (T*)l->ku1[2 + i][1];
             A.cP[i] = (T*)l->ku1[2 + i][0];
         }
-        pq = pc.lf == 1 ? 0 : 3;
+        pq = pc.lf != 1 && pq_saved ? 3 : 0;
     }
     cudaError_t e = l->u1_staged ? launch_u1_staged(prec, &A, pq, l->stream) : launch_u1(prec, &A, 0, l->stream);
     if (e == cudaSuccess && pc.lf == 2 && !l->u1_staged) {
@@ -1099,12 +1105,32 @@ cl_status run_u1_lf_t(cl_lattice* l, const PassCoef& pc, int s)
     }
     if (e == cudaSuccess) e = l->u1_staged ? launch_u1_staged(prec, &A, 1, l->stream) : launch_u1(prec, &A, 1, l->stream);
     if (e != cudaSuccess) return fail(l, CL_ECUDA, "U(1) leapfrog launch failed: %s", cudaGetErrorString(e));
+    l->u1_lf_pq = l->u1_staged && pc.lf != 3;  // pass 3 drifts the positions
     return CL_OK;
 }
 
 cl_status run_u1_lf(cl_lattice* l, const PassCoef& pc, int s)
 {
     return is_fp64(l) ? run_u1_lf_t<double>(l, pc, s) : run_u1_lf_t<float>(l, pc, s);
+}
+
+// sin P and cos P of the open leapfrog's positions (buffer cur) into the slots that the staged
+// passes 2 and 3 read, when the pass that should have saved them ran in another form (the pass
+// variant changed with the leapfrog open); one plaquette launch, outside any step graph.
+template <typename T>
+cl_status u1_lf_save_pq_t(cl_lattice* l)
+{
+    U1Args<T> A{};
+    u1_fill(l, A, l->cur, l->cur ^ 1);
+    for (int i = 0; i < 3; ++i) {
+        A.sP[i] = (T*)l->ku1[2 + i][1];
+        A.cP[i] = (T*)l->ku1[2 + i][0];
+    }
+    A.flags = l->p.expansion ? P_EXPANSION : 0;
+    const cudaError_t e = launch_u1_staged(l->p.precision, &A, 0, l->stream);
+    if (e != cudaSuccess) return fail(l, CL_ECUDA, "U(1) plaquette launch failed: %s", cudaGetErrorString(e));
+    l->u1_lf_pq = true;
+    return CL_OK;
 }
 
 // Energies of members [m0, m1) of an ensemble only (a' from Eq. Friedmann2 with P_HUBBLE_INIT).
@@ -1912,6 +1938,10 @@ cl_status cl_step(cl_lattice* l, int32_t nsteps)
         cl_status s = open_leapfrog(l);
         if (s != CL_OK) return s;
         l->last_launches += is_u1_lf(l) ? (l->u1_sfused ? 1 : 2) : (l->gw ? 2 : 1);
+    } else if (is_u1_lf(l) && l->u1_staged && !l->u1_sfused && !l->u1_lf_pq) {
+        cl_status s = is_fp64(l) ? u1_lf_save_pq_t<double>(l) : u1_lf_save_pq_t<float>(l);
+        if (s != CL_OK) return s;
+        l->last_launches += 1;
     }
     const std::vector<PassCoef> sched = step_schedule(l);
     const int pps = (int)sched.size();

@@ -109,6 +109,37 @@ def test_leapfrog_parity(cl, N, variant, prec, tol, alpha):
     assert launches == (1 if variant == 3 else 2) + per_step * n
 
 
+@pytest.mark.parametrize("prec,tol,ftol", [(0, 1e-10, 1e-12), (2, 1e-4, 1e-5)])
+@pytest.mark.parametrize("first", [0, 3])
+def test_switching_to_the_staged_form_with_the_leapfrog_open(cl, prec, tol, ftol, first):
+    """Passes 2 and 3 of the staged form reuse the sin P and cos P that its pass 1 saved.
+    After steps in the gather (0) or single-launch (3) form, whose pass 1 saves nothing, the
+    first staged step saves them with one plaquette launch of its own: 3 + 4 steps across the
+    switch follow the oracle and agree with 7 staged steps to rounding (the forms differ only
+    in the order of their roundings)."""
+    N, L, alpha = 32, 24.0, 0.5
+    m = O.make_model(N, L, nf=1, alpha=alpha, kappa=KAPPA, expansion=True, gauge=1, alphaL=ALPHAL, ws2=WS2,
+                     m2=(M2, 0.0), lam=(LAM, 0.0))
+    st = start(m, 9, th_amp=0.5)
+    dtype = np.float64 if prec == 0 else np.float32
+    with lattice(cl, N, L, prec, alpha, variant=first) as g:
+        upload(cl, g, st, dtype)
+        g.cl_step(3)
+        g.cl_set_option(cl.CL_OPT_PASS_VARIANT, 2)
+        g.cl_step(4)
+        launches = g.cl_last_launch_count()
+        out = download(cl, g)
+    with lattice(cl, N, L, prec, alpha) as g:
+        upload(cl, g, st, dtype)
+        g.cl_step(7)
+        ref = download(cl, g)
+    O.step(m, st, O.VV2, 0.01, 7)
+    check_state(out, st, tol)
+    for k in ref:
+        assert rel_l2(out[k], ref[k]) < ftol, k
+    assert launches == 1 + 6 * 4
+
+
 @pytest.mark.parametrize("prec", [0, 2])
 def test_reads_leave_the_trajectory_alone_and_graphs_match_plain_launches(cl, prec):
     """Reading states, energies and spectra between steps keeps the leapfrog open (the
