@@ -351,7 +351,10 @@ cl_status cl_set_hubble_limit(cl_lattice* l, double limit);
  * choice where N is a multiple of 32, else 0), 1 = one fused launch per stage with the
  * plaquette fields in shared memory (N a multiple of 32; Runge-Kutta only, CL_EUNSUPPORTED
  * with the leapfrog), 3 = the staged neighbourhoods of 2 in one launch per stage or pass, the
- * plaquette fields computed into shared memory (N a multiple of 32).  All agree to rounding.  On a (2+1)-dimensional lattice the
+ * plaquette fields computed into shared memory (N a multiple of 32).  All agree to rounding,
+ * also across a change of form with the axion-U(1) leapfrog open (the first step after a
+ * change to 2 adds one plaquette launch that saves sin P and cos P of the open positions,
+ * which form 2 keeps from each step's first pass for its other two).  On a (2+1)-dimensional lattice the
  * leapfrog pass is 1 = row marching (the library's choice where N is a multiple of 128 in
  * FP32, 64 in FP64: each warp owns a strip of columns and a chunk of rows and keeps three
  * drifted rows in registers; CL_OPT_TILE_DZ its rows per chunk, CL_OPT_TILE_BY how many rows
