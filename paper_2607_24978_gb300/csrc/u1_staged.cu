@@ -64,8 +64,9 @@ using U1SGeom = U1SGeomT<T, sizeof(T) == 4 ? 16 : 8, 6, 1, 1>;
 // the plaquette launches, which stage half as many arrays: tiles twice as tall over half z
 // chunks, six producer warps, and in FP32 two sites a consumer thread (two independent
 // chains of shared-memory loads and trigonometry; measured at 192^3 FP32 with one site a
-// thread in 32 x 16 tiles: 113 us a launch, 61% of the issue slots active; two sites a
-// thread with four producer warps: 121 us, the consumers waiting on the copies)
+// thread in 32 x 16 tiles: 113 us a launch, 61% of the issue slots active; this geometry:
+// 104 us, 10% fewer instructions; with four producer warps: 121 us, the consumers waiting on
+// the copies)
 template <typename T>
 using U1PGeom = U1SGeomT<T, 2 * U1SGeom<T>::TY, 6, 2, sizeof(T) == 4 ? 2 : 1>;
 
