@@ -468,3 +468,50 @@ def test_u1_gauss_tracking_of_a_gauss_state(cl, prec, bound):
         e = g.cl_energies()
         assert 0.0 <= e["gauss_rms_max"] < bound
         assert e["gauss_rms_step"] <= e["gauss_rms_max"]
+
+
+@pytest.mark.parametrize("form", ["rk33", "leapfrog"])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-4)])
+def test_u1_staged_96_cubed_from_a_periodic_state(cl, form, prec, tol):
+    """The staged launches at 96^3, where the stage tiles (32 x 16, 32 x 8 in FP64) and the
+    plaquette launches' taller tiles over half z chunks cut the lattice into 3 x 6 and 3 x 3
+    tiles (3 x 12 and 3 x 6 in FP64) and the library's z chunks: a state that repeats every 16
+    sites evolves as the 16^3 oracle lattice tiled (translation invariance), RK3-3 and the
+    leapfrog, FP64 and FP32."""
+    integ, scheme = (cl.CL_INT_RK3_3, O.RK3_3) if form == "rk33" else (cl.CL_INT_VV2, O.VV2)
+    N, P, n = 96, 16, 4
+    reps = N // P
+    L = 0.75 * N
+    m = O.make_model(P, L * P / N, nf=1, alpha=0.5, kappa=KAPPA, expansion=True, gauge=1, alphaL=ALPHAL, ws2=WS2,
+                     m2=(M2, 0.0), lam=(LAM, 0.0))
+    st = random_state(m, 13, th_amp=0.5)
+    dtype = np.float64 if prec == 0 else np.float32
+    for arr in (st.phi, st.pi, st.links, st.efield):
+        arr[:] = arr.astype(dtype)
+    st.abt[:] = (1.0, math.sqrt(KAPPA * O.energies(m, st)["rho"] / 3.0), 0.0)
+    with cl.Lattice(N, L, 1, prec, integ, gauge=cl.CL_GAUGE_U1_AXION, expansion=True, alpha=0.5, kappa=KAPPA,
+                    dt=0.01) as g:
+        g.cl_set_potential(cl.CL_POT_POLY, [M2, LAM, 0.0, 0.0, 0.0])
+        g.cl_set_gauge_coupling(ALPHAL, WS2)
+        assert g.cl_get_option(cl.CL_OPT_PASS_VARIANT) == 2
+        g.cl_set_state(cl.CL_FIELD_PHI0, np.tile(st.phi[0], (reps,) * 3).astype(dtype))
+        g.cl_set_state(cl.CL_FIELD_PI0, np.tile(st.pi[0], (reps,) * 3).astype(dtype))
+        for i in range(3):
+            g.cl_set_state(cl.CL_FIELD_THETA1 + i, np.tile(st.links[i], (reps,) * 3).astype(dtype))
+            g.cl_set_state(cl.CL_FIELD_E1 + i, np.tile(st.efield[i], (reps,) * 3).astype(dtype))
+        g.cl_set_scalars(st.abt[0], st.abt[1], 0.0)
+        g.cl_step(n)
+        out = {"phi": g.cl_get_state(cl.CL_FIELD_PHI0), "pi": g.cl_get_state(cl.CL_FIELD_PI0),
+               "th": np.stack([g.cl_get_state(cl.CL_FIELD_THETA1 + i) for i in range(3)]),
+               "E": np.stack([g.cl_get_state(cl.CL_FIELD_E1 + i) for i in range(3)])}
+        e = g.cl_energies()
+    O.step(m, st, scheme, 0.01, n)
+    assert rel_l2(out["phi"], np.tile(st.phi[0], (reps,) * 3)) < tol
+    assert rel_l2(out["pi"], np.tile(st.pi[0], (reps,) * 3)) < tol
+    for i in range(3):
+        assert rel_l2(out["th"][i], np.tile(st.links[i], (reps,) * 3)) < tol
+        assert rel_l2(out["E"][i], np.tile(st.efield[i], (reps,) * 3)) < tol
+    eo = O.energies(m, st)
+    for k_gpu, k_orc in [("KE", "KEM"), ("GB", "GEM"), ("rho", "rho"), ("V", "V")]:
+        assert e[k_gpu] == pytest.approx(eo[k_orc], rel=max(tol, 1e-9)), k_gpu
+    assert e["a"] == pytest.approx(st.abt[0], rel=max(tol, 1e-10))
