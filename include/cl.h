@@ -167,8 +167,8 @@ typedef struct {
     double ricci;             /* background Ricci scalar R (Eq. eomR) of a non-minimally coupled
                                  lattice (cl_set_nonminimal); 0 otherwise                  */
     double gauss_rms_step;    /* U(1), tracked every step: rms Gauss violation of the latest
-                                 cl_step step's starting state (Runge-Kutta) or integer-time
-                                 end state (leapfrog),
+                                 cl_step step's starting state (the leapfrog's integer-time
+                                 starting state, its momenta at the integer time),
                                  dx sqrt(sum_n G(n)^2) / (a^(1-alpha) sqrt(sum_n E(n)^2))   */
     double gauss_rms_max;     /* U(1): the largest gauss_rms_step since the last
                                  cl_set_scalars or cl_init_vacuum                         */
@@ -275,8 +275,10 @@ cl_status cl_gauge_spectrum(cl_lattice* l, int32_t which, double dn, int32_t typ
  * fixed-point iterations after it.  Between calls the leapfrog stays open: the integer-time
  * momenta are kept beside the staggered ones, so reading fields, energies or spectra does
  * not change the trajectory; writing the state or the scalars closes it.  One step is three
- * passes of two launches each plus the Gauss reduction (the rms Gauss violation of every
- * step's integer-time end state is tracked in cl_energy::gauss_rms_step / _max).  One axion
+ * passes of two launches each (one each with CL_OPT_PASS_VARIANT 3), the rms Gauss violation
+ * of every step's integer-time starting state summed by the second pass (the gather form,
+ * variant 0, adds one reduction launch) and reported in cl_energy::gauss_rms_step / _max;
+ * the first step of a cl_step call from a closed state adds the opening pass.  One axion
  * field, CL_PREC_FP64 or CL_PREC_FP32.  Errors: CL_EINVAL (no gauge field, bad values). */
 cl_status cl_set_gauge_coupling(cl_lattice* l, double alphaL, double ws2);
 
