@@ -47,7 +47,8 @@ typedef enum {
     CL_ECUDA = 3,         /* a CUDA runtime or cuFFT call failed                               */
     CL_ENAN = 4,          /* a volume-averaged energy became non-finite                        */
     CL_ECONSTRAINT = 5,   /* Hubble-constraint violation above the limit set by cl_set_hubble_limit */
-    CL_ETIMEOUT = 6,      /* reserved: a bounded device wait gave up                           */
+    CL_ETIMEOUT = 6,      /* a bounded device wait of a pipelined kernel gave up (reported by
+                             the next synchronising call, like CL_ENAN)                        */
     CL_ESTATE = 7,        /* call not valid in the handle's current state                      */
     CL_EUNSUPPORTED = 8   /* valid request that this build does not implement                  */
 } cl_status;
@@ -215,10 +216,11 @@ cl_status cl_init_vacuum(cl_lattice* l, int32_t member, const cl_vacuum_params* 
 
 /* Queue nsteps time steps of the configured integrator on the handle's stream (replayed
  * from a captured CUDA graph when graphs are enabled).  Returns after queueing.
- * Errors: CL_EINVAL (nsteps < 0), CL_ECUDA. */
+ * Errors: CL_EINVAL (nsteps < 0), CL_ESTATE (cl_set_potential not called), CL_ECUDA. */
 cl_status cl_step(cl_lattice* l, int32_t nsteps);
 
-/* Wait for the handle's queued work; report device-side failures (CL_ENAN, CL_ECONSTRAINT). */
+/* Wait for the handle's queued work; report device-side failures (CL_ENAN, CL_ECONSTRAINT,
+ * CL_ETIMEOUT). */
 cl_status cl_sync(cl_lattice* l);
 
 /* Copy the energies of `count` members (starting at member 0; 1 <= count <= members, or
@@ -334,7 +336,8 @@ cl_status cl_set_hubble_limit(cl_lattice* l, double limit);
  * choice).  CL_OPT_TILE_DZ: planes per block (0 = library choice: the y tiles are cut into
  * the same z chunks so that one wave of blocks covers the lattice; -1 = a persistent grid
  * of one wave, each block a balanced contiguous range of planes; for the axion-U(1)
- * kernels, the planes each 32 x 8 tile marches through).  CL_OPT_STAGES: TMA stage buffers
+ * kernels, the planes of the z chunk each (x, y) tile marches through, where the staged
+ * plaquette launches, whose tiles are twice as tall, split every chunk in two).  CL_OPT_STAGES: TMA stage buffers
  * of the fused pass, 2..6, or -1 for the loader without TMA staging (0 = library choice;
  * rows that are not a multiple of 16 bytes always use the loader without TMA; ensembles
  * clamp to 2..4 with the ring kernel and 3..6 ringless).  On a Runge-Kutta scalar lattice
@@ -356,8 +359,8 @@ cl_status cl_set_hubble_limit(cl_lattice* l, double limit);
  * plaquette fields computed into shared memory (N a multiple of 32).  All agree to rounding,
  * also across a change of form with the axion-U(1) leapfrog open (the first step after a
  * change to 2 adds one plaquette launch that saves sin P and cos P of the open positions,
- * which form 2 keeps from each step's first pass for its other two).  On a (2+1)-dimensional lattice the
- * leapfrog pass is 1 = row marching (the library's choice where N is a multiple of 128 in
+ * which form 2 keeps from each step's first pass for its other two).  On a
+ * (2+1)-dimensional lattice the leapfrog pass is 1 = row marching (the library's choice where N is a multiple of 128 in
  * FP32, 64 in FP64: each warp owns a strip of columns and a chunk of rows and keeps three
  * drifted rows in registers; CL_OPT_TILE_DZ its rows per chunk, CL_OPT_TILE_BY how many rows
  * ahead it prefetches into L2, 0 = library choice) or 0 = one thread per site; both agree to
